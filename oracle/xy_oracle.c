@@ -1,0 +1,321 @@
+/*
+ * xy_oracle.c -- plain FP64 CPU reference ("oracle") for the checkerboard
+ * Metropolis simulation of the 2-d XY model.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and bench.py's CPU
+ * baseline may load this code.  It shares nothing with the CUDA library: it
+ * has its own Philox, its own indexing and its own observables, written
+ * straight from their definitions, slow and in double precision.
+ *
+ * What it computes (all citations are to the paper "GPU computing for 2-d
+ * spin systems: CUDA vs OpenGL"):
+ *   - the model, Eq. (1): H = -J sum_<ij> cos(theta_i - theta_j) on a
+ *     periodic Lx x Ly square lattice, each site bonded to its +x and +y
+ *     neighbour (2N bonds; on a side of length 2 the same pair is bonded
+ *     twice, exactly as the four-neighbour stencil sees it);
+ *   - single-site Metropolis: propose theta' = theta + delta*(2 u0 - 1),
+ *     wrapped once into [0, 2pi); accept iff u1 < exp(-beta dE) with
+ *     dE = -J sum_{4 nn j} [cos(theta' - theta_j) - cos(theta - theta_j)];
+ *     the accept/select of Sec. 3.2 (new = z*proposal + (1-z)*old);
+ *   - the per-sweep bond and spin sums used for the cross-checks of
+ *     Sec. 1.2 (energy and acceptance).
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
+ * random numbers: as easy as 1, 2, 3", SC'11, Sec. 3.3 and Table 2), keyed
+ * by the 64-bit seed (low word first) with counter (site, sweep, lattice id,
+ * domain); domain 0 draws the hot start, domain 1 the Metropolis words.
+ * Uniforms use the top 24 bits of a word: u = (w >> 8) * 2^-24.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TWO_PI 6.283185307179586476925286766559
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, from the published definition.                       */
+/* ------------------------------------------------------------------ */
+
+/* Round multipliers and Weyl key increments of Philox4x32 (SC'11, Table 2
+ * and Sec. 3.3). */
+static const uint32_t PHILOX_MULT_A = 0xD2511F53u;
+static const uint32_t PHILOX_MULT_B = 0xCD9E8D57u;
+static const uint32_t PHILOX_WEYL_A = 0x9E3779B9u;
+static const uint32_t PHILOX_WEYL_B = 0xBB67AE85u;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {           /* key schedule: bump before rounds 2..10 */
+            k0 += PHILOX_WEYL_A;
+            k1 += PHILOX_WEYL_B;
+        }
+        /* the S-box: two 32x32 -> 64 products, halves swapped and xored */
+        uint64_t prod_a = (uint64_t)PHILOX_MULT_A * (uint64_t)x0;
+        uint64_t prod_b = (uint64_t)PHILOX_MULT_B * (uint64_t)x2;
+        uint32_t hi_a = (uint32_t)(prod_a >> 32), lo_a = (uint32_t)prod_a;
+        uint32_t hi_b = (uint32_t)(prod_b >> 32), lo_b = (uint32_t)prod_b;
+        uint32_t y0 = hi_b ^ x1 ^ k0;
+        uint32_t y1 = lo_b;
+        uint32_t y2 = hi_a ^ x3 ^ k1;
+        uint32_t y3 = lo_a;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The four words drawn for one (site, sweep, lattice, domain). */
+static void site_words(uint64_t seed, uint32_t site, uint32_t sweep,
+                       uint32_t lattice_id, uint32_t domain, uint32_t w[4])
+{
+    uint32_t ctr[4] = { site, sweep, lattice_id, domain };
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    orc_philox4x32_10(ctr, key, w);
+}
+
+/* Exact 24-bit uniform in [0, 1). */
+static double u24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+
+/* Fill n x 4 words for counters (first + i, sweep, lattice_id, domain). */
+void orc_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id,
+                      uint32_t domain, uint32_t first, int64_t n, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        site_words(seed, first + (uint32_t)i, sweep, lattice_id, domain, out + 4 * i);
+}
+
+/* ------------------------------------------------------------------ */
+/* Lattice geometry (natural order s = y*Lx + x, periodic).            */
+/* ------------------------------------------------------------------ */
+
+static int64_t site_right(int Lx, int64_t s) { int64_t x = s % Lx; return s - x + (x + 1) % Lx; }
+static int64_t site_left (int Lx, int64_t s) { int64_t x = s % Lx; return s - x + (x + Lx - 1) % Lx; }
+static int64_t site_up   (int Lx, int Ly, int64_t s)
+{
+    int64_t y = s / Lx, x = s % Lx;
+    return ((y + 1) % Ly) * Lx + x;
+}
+static int64_t site_down (int Lx, int Ly, int64_t s)
+{
+    int64_t y = s / Lx, x = s % Lx;
+    return ((y + Ly - 1) % Ly) * Lx + x;
+}
+
+/* ------------------------------------------------------------------ */
+/* Observables: bond and spin sums of one configuration (FP64).        */
+/* out = { C, Ix, Iy, Mx, My } with                                    */
+/*   C  = sum_s cos(t_s - t_{s+x}) + cos(t_s - t_{s+y})   (2N bonds)   */
+/*   Ix = sum_s sin(t_s - t_{s+x}),  Iy = sum_s sin(t_s - t_{s+y})     */
+/*   Mx = sum_s cos t_s,             My = sum_s sin t_s                */
+/* e = -J C / N, |m| = |M| / N, Upsilon = (J C - beta J^2 (Ix^2+Iy^2))/(2N) */
+/* ------------------------------------------------------------------ */
+void orc_measure(int Lx, int Ly, const double *theta, double out[5])
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double C = 0, Ix = 0, Iy = 0, Mx = 0, My = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        double t = theta[s];
+        double tx = theta[site_right(Lx, s)];
+        double ty = theta[site_up(Lx, Ly, s)];
+        C  += cos(t - tx) + cos(t - ty);
+        Ix += sin(t - tx);
+        Iy += sin(t - ty);
+        Mx += cos(t);
+        My += sin(t);
+    }
+    out[0] = C; out[1] = Ix; out[2] = Iy; out[3] = Mx; out[4] = My;
+}
+
+/* Energy change of moving site s from theta[s] to theta_new, from the
+ * four-neighbour stencil (the quantity the Metropolis test uses). */
+double orc_delta_energy(int Lx, int Ly, const double *theta, int64_t s,
+                        double theta_new, double J)
+{
+    int64_t nb[4] = { site_right(Lx, s), site_left(Lx, s),
+                      site_up(Lx, Ly, s), site_down(Lx, Ly, s) };
+    double old = theta[s], dE = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double tj = theta[nb[k]];
+        dE -= J * (cos(theta_new - tj) - cos(old - tj));
+    }
+    return dE;
+}
+
+/* ------------------------------------------------------------------ */
+/* Start configurations.                                               */
+/* ------------------------------------------------------------------ */
+
+/* Hot start: theta_s = 2 pi u24(w0), words of domain 0, sweep 0.
+ * Cold start (hot == 0): all angles zero. */
+void orc_start(int Lx, int Ly, uint64_t seed, uint32_t lattice_id, int hot,
+               double *theta)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    for (int64_t s = 0; s < N; ++s) {
+        if (!hot) { theta[s] = 0.0; continue; }
+        uint32_t w[4];
+        site_words(seed, (uint32_t)s, 0u, lattice_id, 0u, w);
+        theta[s] = ORC_TWO_PI * u24(w[0]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* One Metropolis attempt at site s against `theta` (not modified).    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double theta_prop;   /* proposed angle, wrapped into [0, 2pi)        */
+    double u1;           /* accept uniform                               */
+    double p;            /* exp(-beta dE)                                */
+    int accept;          /* u1 < p                                       */
+} orc_step;
+
+static orc_step attempt(int Lx, int Ly, const double *theta, int64_t s,
+                        double beta, double J, double delta, uint64_t seed,
+                        uint32_t lattice_id, uint32_t sweep)
+{
+    uint32_t w[4];
+    site_words(seed, (uint32_t)s, sweep, lattice_id, 1u, w);
+    double u0 = u24(w[0]);
+    orc_step st;
+    st.u1 = u24(w[1]);
+    double prop = theta[s] + delta * (2.0 * u0 - 1.0);
+    if (prop < 0.0) prop += ORC_TWO_PI;
+    else if (prop >= ORC_TWO_PI) prop -= ORC_TWO_PI;
+    st.theta_prop = prop;
+    double dE = orc_delta_energy(Lx, Ly, theta, s, prop, J);
+    st.p = exp(-beta * dE);
+    st.accept = st.u1 < st.p;
+    return st;
+}
+
+/* Evaluate the Metropolis step of sweep `sweep` at each listed site against
+ * the given state, without applying it.  Any output pointer may be NULL. */
+void orc_attempt_sites(int Lx, int Ly, const double *theta, const int64_t *sites,
+                       int64_t n, double beta, double J, double delta,
+                       uint64_t seed, uint32_t lattice_id, uint32_t sweep,
+                       int nthreads, double *theta_prop, double *u1, double *p,
+                       uint8_t *accept)
+{
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        orc_step st = attempt(Lx, Ly, theta, sites[i], beta, J, delta, seed,
+                              lattice_id, sweep);
+        if (theta_prop) theta_prop[i] = st.theta_prop;
+        if (u1) u1[i] = st.u1;
+        if (p) p[i] = st.p;
+        if (accept) accept[i] = (uint8_t)st.accept;
+    }
+    (void)nthreads;
+}
+
+/* Half-sweep of colour c ((x + y) mod 2 == c): every site of that colour
+ * attempts one move against the same neighbours (they are all of the other
+ * colour), then the accepted moves are applied.  Per-site outputs (indexed
+ * by natural site id, NULL allowed) let a test compare each decision.
+ * Returns the number of accepted moves. */
+int64_t orc_half_sweep(int Lx, int Ly, double *theta, int colour, double beta,
+                       double J, double delta, uint64_t seed, uint32_t lattice_id,
+                       uint32_t sweep, int nthreads, double *theta_prop,
+                       double *u1, double *p, uint8_t *accept)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double *next = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!next) return -1;
+    memcpy(next, theta, sizeof(double) * (size_t)N);
+    int64_t count = 0;
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(static) reduction(+:count) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t x = s % Lx, y = s / Lx;
+        if ((int)((x + y) & 1) != colour) continue;
+        orc_step st = attempt(Lx, Ly, theta, s, beta, J, delta, seed,
+                              lattice_id, sweep);
+        if (theta_prop) theta_prop[s] = st.theta_prop;
+        if (u1) u1[s] = st.u1;
+        if (p) p[s] = st.p;
+        if (accept) accept[s] = (uint8_t)st.accept;
+        /* Sec. 3.2 select: new = z * proposal + (1 - z) * old, z in {0, 1} */
+        next[s] = st.accept ? st.theta_prop : theta[s];
+        count += st.accept;
+    }
+    (void)nthreads;
+    memcpy(theta, next, sizeof(double) * (size_t)N);
+    free(next);
+    return count;
+}
+
+/* One full sweep.  order 0: checkerboard (colour 0 then colour 1; needs even
+ * Lx and Ly).  order 1: typewriter (sites in natural order, each move applied
+ * at once).  Returns the number of accepted moves, or -1 on bad input. */
+int64_t orc_sweep(int Lx, int Ly, double *theta, double beta, double J,
+                  double delta, uint64_t seed, uint32_t lattice_id,
+                  uint32_t sweep, int order, int nthreads)
+{
+    if (order == 0) {
+        if ((Lx & 1) || (Ly & 1)) return -1;
+        int64_t a = orc_half_sweep(Lx, Ly, theta, 0, beta, J, delta, seed,
+                                   lattice_id, sweep, nthreads, NULL, NULL, NULL, NULL);
+        int64_t b = orc_half_sweep(Lx, Ly, theta, 1, beta, J, delta, seed,
+                                   lattice_id, sweep, nthreads, NULL, NULL, NULL, NULL);
+        if (a < 0 || b < 0) return -1;
+        return a + b;
+    }
+    int64_t N = (int64_t)Lx * Ly, count = 0;
+    for (int64_t s = 0; s < N; ++s) {
+        orc_step st = attempt(Lx, Ly, theta, s, beta, J, delta, seed,
+                              lattice_id, sweep);
+        if (st.accept) { theta[s] = st.theta_prop; ++count; }
+    }
+    return count;
+}
+
+/* Free-running chain: start (hot != 0: Philox hot start; 0: cold), then
+ * n_sweeps sweeps numbered first_sweep, first_sweep + 1, ...  After each
+ * sweep, records[6*i .. 6*i+5] = { C, Ix, Iy, Mx, My, accepted }.
+ * If theta_io is non-NULL and start < 0, the chain starts from theta_io;
+ * the final state is written back to theta_io when it is non-NULL. */
+int orc_run(int Lx, int Ly, uint64_t seed, uint32_t lattice_id, double beta,
+            double J, double delta, int start, int order, uint32_t first_sweep,
+            int64_t n_sweeps, int nthreads, double *theta_io, double *records)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double *theta = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!theta) return -1;
+    if (start < 0) {
+        if (!theta_io) { free(theta); return -1; }
+        memcpy(theta, theta_io, sizeof(double) * (size_t)N);
+    } else {
+        orc_start(Lx, Ly, seed, lattice_id, start, theta);
+    }
+    for (int64_t i = 0; i < n_sweeps; ++i) {
+        int64_t acc = orc_sweep(Lx, Ly, theta, beta, J, delta, seed, lattice_id,
+                                first_sweep + (uint32_t)i, order, nthreads);
+        if (acc < 0) { free(theta); return -1; }
+        if (records) {
+            orc_measure(Lx, Ly, theta, records + 6 * i);
+            records[6 * i + 5] = (double)acc;
+        }
+    }
+    if (theta_io) memcpy(theta_io, theta, sizeof(double) * (size_t)N);
+    free(theta);
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
