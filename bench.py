@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the checkerboard Metropolis XY path; prints one JSON line.
+
+A step is one pass of the whole hot path over one lattice: the Philox hot
+start followed by 1000 red/black Metropolis sweeps of an L = 4096 lattice at
+beta = 1.12 (seed 7), each sweep with its fused per-sweep reductions.  With
+N > 1 (torchrun, one rank per GPU) every rank runs its own independent chain
+(lattice_id = rank): replicas, no collective on the data path.
+
+  value  spin updates per second over all ranks, inputs resident on the
+         device, CUDA events around each step on the lattice's stream, L2
+         flushed (256 MiB write) before every timed step;
+  e2e    the same metric through the C ABI with host buffers: every step
+         copies the start configuration from pinned host memory (xy_set_state),
+         sweeps, reads the records (xy_measure) and the final angles
+         (xy_get_state); wall clock around each step.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "XY spin-updates/s on 1 GB300 (L=4096 and batched) and % of roofline"
+UNIT = "spin-updates/s"
+FLUSH_BYTES = 256 << 20
+TIMING_EVERY = 50          # kernel events on every 50th sweep of the timed region
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sincos", choices=["accurate", "fast"], default="accurate")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["large", "huge"], default="large",
+                    help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step")
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="override sweeps per step (profiling runs only)")
+    return ap.parse_args()
+
+
+def workload(args):
+    import dataclasses
+    from paper_0811_2111_gb300 import workloads as WL
+    w = {"large": WL.LARGE, "huge": WL.HUGE}[args.workload]
+    if args.sweeps is not None:
+        w = dataclasses.replace(w, sweeps=args.sweeps)
+    return w
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    from paper_0811_2111_gb300 import build as B
+    if d.get("source_hash") != B.source_hash():
+        return None          # kernels changed since the counters were taken
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, target_s, nthreads):
+    """Time the FP64 oracle on the L x L workload: sweeps from the hot start."""
+    import oracle
+    t = time.perf_counter()
+    oracle.run(w.L, w.L, w.beta, 1, seed=w.seed, nthreads=nthreads)
+    one = time.perf_counter() - t
+    n = max(1, min(50, int(target_s / max(one, 1e-9))))
+    t = time.perf_counter()
+    oracle.run(w.L, w.L, w.beta, n, seed=w.seed, nthreads=nthreads)
+    dt = time.perf_counter() - t
+    return w.sites * n / dt, n, dt
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    w = workload(args)
+    nthreads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.run(w.L, w.L, w.beta, 1, seed=w.seed, nthreads=nthreads)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.run(w.L, w.L, w.beta, 1, seed=w.seed, nthreads=nthreads)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = w.sites * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
+                   "sweeps_per_step": 1, "note": "each step: one oracle sweep of the "
+                   "full L=4096 lattice from the hot start (bounded sample of the 1000-sweep "
+                   "workload)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                         "sample": f"{args.steps} x 1 sweep of L={w.L} from the seed-{w.seed} "
+                                   "hot start, OpenMP over the sites of one colour"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_0811_2111_gb300 import build as B
+    from paper_0811_2111_gb300 import _lib as X
+    from paper_0811_2111_gb300.lattice import Lattice
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    B.build()
+
+    w = workload(args)
+    stream = torch.cuda.current_stream(dev)
+    lat = Lattice(w.L, w.beta, w.seed, device=dev, stream=stream, lattice_id=rank,
+                  sincos=args.sincos)
+    lat.reserve(w.sweeps)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        lat.reset(w.seed)
+        lat.sweep(w.sweeps)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None else str(local)
+    sampler = ClockSampler(gpu_id)
+
+    lat.timing(TIMING_EVERY)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    for k in range(args.steps):
+        flush.fill_(float(k))                         # evict the lattice from L2
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kt = {k: lat.kernel_time(k) for k in (0, 1)}
+    lat.timing(0)
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    updates = w.updates * args.steps * world
+    value = updates / (total_ms * 1e-3)
+
+    # e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        lat.reset(w.seed)
+        start_state, _ = lat.state()
+        host_in = torch.from_numpy(start_state.reshape(-1).copy()).pin_memory()
+        host_out = torch.empty(w.sites, dtype=torch.float32).pin_memory()
+        recs = (X.xy_obs * w.sweeps)()
+        nxt = C.c_uint64()
+        lib = X.lib()
+        wall = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            X.check(lib.xy_set_state(lat.ctx, C.c_void_p(host_in.data_ptr()), 0), lat.ctx)
+            X.check(lib.xy_sweep(lat.ctx, w.sweeps), lat.ctx)
+            X.check(lib.xy_measure(lat.ctx, 0, w.sweeps, recs), lat.ctx)
+            X.check(lib.xy_get_state(lat.ctx, C.c_void_p(host_out.data_ptr()), C.byref(nxt)),
+                    lat.ctx)
+            wall.append(time.perf_counter() - t)
+        e2e_s = max_over_ranks(sum(wall), world, dev)
+        e2e = {"value": w.updates * args.steps * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * w.sites,
+               "d2h_bytes_per_step": 4 * w.sites + C.sizeof(X.xy_record) * w.sweeps}
+
+    # roofline of the dominant kernel (the half-sweep with the larger device time)
+    kern = max((0, 1), key=lambda k: kt[k][0])
+    kms, klaunch = kt[kern]
+    avg_s = kms * 1e-3 / max(klaunch, 1)
+    alg_bytes = 8.0 * (w.sites // 2)          # 8 B per update (read + write of the angle)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(),
+                "kernel": ["red_half_sweep", "black_half_sweep_measure"][kern],
+                "kernel_avg_us": avg_s * 1e6, "peak_kind": peak_kind,
+                "kernel_timing": f"CUDA events around the launches of every {TIMING_EVERY}th "
+                                 "sweep inside the timed region",
+                "kernel_times_ms": {"red": kt[0][0] / max(kt[0][1], 1),
+                                    "black": kt[1][0] / max(kt[1][1], 1)}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nthreads = os.cpu_count() or 1
+        v, n, dt = oracle_sample(w, args.cpu_seconds, nthreads)
+        cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"{n} sweeps of L={w.L} from the seed-{w.seed} hot start "
+                         f"({dt:.1f} s), OpenMP over the sites of one colour"}
+
+    launches = args.steps * (1 + 2 * w.sweeps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
+                   "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "fp64",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

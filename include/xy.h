@@ -1,0 +1,188 @@
+/*
+ * xy.h -- C ABI of the GB300 (sm_103a) checkerboard Metropolis engine for the
+ * 2-d XY model.
+ *
+ * Model (Eq. (1) of "GPU computing for 2-d spin systems: CUDA vs OpenGL"):
+ *     H = -J sum_<ij> cos(theta_i - theta_j)
+ * on a periodic L x L square lattice; each site is bonded to its +x and +y
+ * neighbour (2N bonds, N = L^2).  Sites are updated by single-site
+ * Metropolis in red/black (checkerboard) order: all sites with (x + y) even,
+ * then all with (x + y) odd.  A site proposes
+ *     theta' = theta + delta * (2 u0 - 1), wrapped once into [0, 2 pi),
+ * and takes it iff u1 < exp(-beta dE), dE = -J sum_{4 nn j}
+ * [cos(theta' - theta_j) - cos(theta - theta_j)]; the accept is the per-site
+ * select new = z * proposal + (1 - z) * old of Sec. 3.2.  The global sums
+ * that the paper moved to the CPU (Sec. 1.2) are computed on the device,
+ * fused into every sweep.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ * (seed_lo, seed_hi) and counter (site, sweep, lattice_id, domain), where
+ * site = y * L + x (natural order); domain 0 draws the hot start
+ * (theta = 2 pi u24(w0) at sweep 0), domain 1 the Metropolis words of sweep t
+ * (w0 -> proposal, w1 -> accept), domain 2 the replica-exchange words.
+ * u24(w) = (w >> 8) * 2^-24, exact in FP32.
+ *
+ * Conventions
+ *   - Every call returns an xy_status; nothing aborts, nothing throws.  The
+ *     first error is sticky in its context: later calls on that context
+ *     return it until the context is destroyed.
+ *   - Work is ordered on the context's CUDA stream.  xy_sweep only enqueues;
+ *     asynchronous device errors surface at the next call that synchronizes
+ *     (xy_measure, xy_get_state, xy_set_state, xy_synchronize).
+ *   - Angles cross the ABI in natural order [y][x] as FP32 radians.  On the
+ *     device they live in a checkerboard-split layout: two planes
+ *     [colour][y][k], colour = (x + y) & 1, k = x >> 1, i.e. L*L floats.
+ *   - Buffers passed in by the caller stay owned by the caller and are never
+ *     freed by the library.
+ *   - A context is thread-compatible, not thread-safe.
+ */
+#ifndef XY_H
+#define XY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xy_ctx xy_ctx;
+
+typedef enum {
+    XY_OK = 0,
+    XY_EINVAL = 1,     /* bad argument (odd L, NULL pointer, out of range)     */
+    XY_ENOMEM = 2,     /* device or host allocation failed                     */
+    XY_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed          */
+    XY_ETIMEOUT = 4,   /* a bounded device-side wait ran out                   */
+    XY_ESTATE = 5,     /* context destroyed, invalid, or in an earlier error   */
+    XY_ENUMERIC = 6    /* a non-finite angle or sum was detected               */
+} xy_status;
+
+enum { XY_START_HOT = 0, XY_START_COLD = 1 };
+enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1 };
+enum { XY_REDUCE_FP64 = 0, XY_REDUCE_COMPENSATED = 1 };
+
+/* Largest supported side (N = L^2 must fit the 32-bit site counter and the
+ * fixed-point record sums). */
+#define XY_MAX_L 32768
+
+typedef struct {
+    int32_t L;            /* side, even, 2 <= L <= XY_MAX_L                    */
+    int32_t start;        /* XY_START_HOT (Philox domain 0) or XY_START_COLD   */
+    double beta;          /* inverse temperature, >= 0                          */
+    double J;             /* coupling (1 in the paper's model)                  */
+    double delta;         /* proposal half-window, 0 < delta <= pi              */
+    uint64_t seed;        /* Philox key                                         */
+    int32_t sincos_mode;  /* XY_SINCOS_ACCURATE (sincosf/expf) or _FAST         */
+    int32_t reduce_mode;  /* XY_REDUCE_FP64 or XY_REDUCE_COMPENSATED            */
+    uint32_t lattice_id;  /* third Philox counter word                          */
+    uint32_t reserved;    /* must be 0                                          */
+} xy_params;
+
+/* Per-sweep record as stored on the device (64 bytes).  The five sums are
+ * signed fixed point in units of 2^-XY_FX_SHIFT (exact, order-independent
+ * integer accumulation of FP64 block sums):
+ *   sum[0] = C  = sum_s cos(t_s - t_{s+x}) + cos(t_s - t_{s+y})
+ *   sum[1] = Ix = sum_s sin(t_s - t_{s+x})
+ *   sum[2] = Iy = sum_s sin(t_s - t_{s+y})
+ *   sum[3] = Mx = sum_s cos t_s,   sum[4] = My = sum_s sin t_s
+ * accepted = accepted moves in the sweep (both colours); beta = the beta the
+ * sweep ran at; flags bit 0 = a non-finite value was seen. */
+#define XY_FX_SHIFT 30
+typedef struct {
+    int64_t sum[5];
+    uint64_t accepted;
+    double beta;
+    uint64_t flags;
+} xy_record;
+
+/* Observables of one sweep, derived from its record:
+ *   e = -J C / N,  abs_m = |M| / N,
+ *   upsilon = (J C - beta J^2 (Ix^2 + Iy^2)) / (2N)  (helicity modulus,
+ *   x/y averaged; <I> = 0 by symmetry). */
+typedef struct {
+    double e, abs_m, upsilon;
+    double C, Ix, Iy, Mx, My;
+    uint64_t accepted;
+    double beta;
+} xy_obs;
+
+/* Create a lattice context and initialise it (hot or cold start, sweep 0).
+ *   p          parameters, copied; validated as documented above.
+ *   cuda_stream a cudaStream_t, or NULL for the legacy default stream.
+ *   d_angles   NULL: the library allocates the L*L float working buffer;
+ *              else a caller-owned device buffer of >= L*L floats, 16-byte
+ *              aligned, used in the split layout (never freed here).
+ *   out        receives the context (NULL on failure).
+ * Errors: XY_EINVAL, XY_ENOMEM, XY_ECUDA (see xy_last_error(NULL)). */
+xy_status xy_create(const xy_params *p, void *cuda_stream, void *d_angles, xy_ctx **out);
+
+/* Re-run the start (hot or cold, as created) with `seed`, set the next sweep
+ * to 0 and clear the records.  Asynchronous, allocates nothing: one
+ * independent chain after another can reuse a context. */
+xy_status xy_reset(xy_ctx *ctx, uint64_t seed);
+
+/* Make room for n more records so that xy_sweep allocates nothing. */
+xy_status xy_reserve(xy_ctx *ctx, int64_t n_more);
+
+/* Enqueue n >= 0 sweeps (red half then black half with the fused measure);
+ * appends n records.  Asynchronous.  Fails with XY_EINVAL if the sweep
+ * counter would pass 2^32. */
+xy_status xy_sweep(xy_ctx *ctx, int64_t n_sweeps);
+
+/* Copy records [first, first + count) to host_out (count >= 0 entries) and
+ * derive the observables.  Synchronizes the stream.  XY_ENUMERIC if a record
+ * carries the non-finite flag. */
+xy_status xy_measure(xy_ctx *ctx, int64_t first, int64_t count, xy_obs *host_out);
+
+/* Raw device records, for device-side consumers (e.g. a backward kernel):
+ * *d_records points at the first record (xy_record[count]); stream-ordered. */
+xy_status xy_records_device(xy_ctx *ctx, const xy_record **d_records, int64_t *count);
+
+/* Number of records so far and the next sweep index. */
+xy_status xy_info(const xy_ctx *ctx, int64_t *n_records, uint64_t *next_sweep);
+
+/* Copy the angles (natural order, L*L floats) to host memory and report the
+ * next sweep index.  Synchronizes. */
+xy_status xy_get_state(xy_ctx *ctx, float *host_angles, uint64_t *next_sweep);
+
+/* Replace the angles (natural order, finite) and the next sweep index; clears
+ * the records.  Synchronizes.  With the counter-based RNG a restored state
+ * continues bit-identically (checkpoint/resume). */
+xy_status xy_set_state(xy_ctx *ctx, const float *host_angles, uint64_t next_sweep);
+
+/* Change beta for later sweeps (records keep the beta they ran at). */
+xy_status xy_set_beta(xy_ctx *ctx, double beta);
+
+/* Kernel timing.  With every = k > 0, xy_sweep brackets the kernel launches
+ * of every k-th sweep (sweep index % k == 0) with CUDA events on the context
+ * stream, so that the timed sample costs almost nothing; every = 0 turns it
+ * off.  xy_kernel_time synchronizes and returns the summed device time (ms)
+ * and the number of timed launches of kernel k since timing was (re)enabled
+ * (k = 0: red half-sweep, k = 1: black half-sweep with the fused measure). */
+xy_status xy_timing(xy_ctx *ctx, int every);
+xy_status xy_kernel_time(xy_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
+/* Wait for the stream and report any asynchronous error. */
+xy_status xy_synchronize(xy_ctx *ctx);
+
+/* Destroy; NULL-safe.  A destroyed context must not be used again. */
+xy_status xy_destroy(xy_ctx *ctx);
+
+/* Message of the context's sticky error, or of the calling thread's last
+ * failure when ctx is NULL.  Never NULL. */
+const char *xy_last_error(const xy_ctx *ctx);
+
+/* Philox4x32-10 words for counters (first + i, sweep, lattice_id, domain),
+ * i < n, written as uint32[n][4] to device memory d_out, on cuda_stream --
+ * the same device generator the sweeps use (for bit-exact checks). */
+xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, uint32_t domain,
+                          uint32_t first, int64_t n, uint32_t *d_out, void *cuda_stream);
+
+/* ABI version (major * 100 + minor). */
+int32_t xy_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XY_H */

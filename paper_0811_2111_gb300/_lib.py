@@ -1,0 +1,179 @@
+"""ctypes binding of the C ABI in ``include/xy.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of its own: all of the simulation runs in ``libxy.so``'s CUDA
+kernels.  If the library has not been built this module raises at load time;
+there is no fallback path.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxy.so")
+
+XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_ESTATE, XY_ENUMERIC = range(7)
+STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "XY_ETIMEOUT",
+                5: "XY_ESTATE", 6: "XY_ENUMERIC"}
+XY_START_HOT, XY_START_COLD = 0, 1
+XY_SINCOS_ACCURATE, XY_SINCOS_FAST = 0, 1
+XY_REDUCE_FP64, XY_REDUCE_COMPENSATED = 0, 1
+XY_FX_SHIFT = 30
+XY_MAX_L = 32768
+
+
+class XYError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class xy_params(C.Structure):
+    _fields_ = [("L", C.c_int32), ("start", C.c_int32), ("beta", C.c_double), ("J", C.c_double),
+                ("delta", C.c_double), ("seed", C.c_uint64), ("sincos_mode", C.c_int32),
+                ("reduce_mode", C.c_int32), ("lattice_id", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class xy_record(C.Structure):
+    _fields_ = [("sum", C.c_int64 * 5), ("accepted", C.c_uint64), ("beta", C.c_double),
+                ("flags", C.c_uint64)]
+
+
+class xy_obs(C.Structure):
+    _fields_ = [("e", C.c_double), ("abs_m", C.c_double), ("upsilon", C.c_double),
+                ("C", C.c_double), ("Ix", C.c_double), ("Iy", C.c_double), ("Mx", C.c_double),
+                ("My", C.c_double), ("accepted", C.c_uint64), ("beta", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load ``libxy.so``; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                          f"g.build()'` (the CUDA library is required, there is no fallback)")
+    L = C.CDLL(LIB_PATH)
+    st = C.c_int
+    P = C.c_void_p
+    sig = {
+        "xy_create": (st, [C.POINTER(xy_params), P, P, C.POINTER(P)]),
+        "xy_reserve": (st, [P, C.c_int64]),
+        "xy_reset": (st, [P, C.c_uint64]),
+        "xy_timing": (st, [P, C.c_int]),
+        "xy_kernel_time": (st, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "xy_sweep": (st, [P, C.c_int64]),
+        "xy_measure": (st, [P, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),
+        "xy_records_device": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
+        "xy_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+        "xy_get_state": (st, [P, P, C.POINTER(C.c_uint64)]),
+        "xy_set_state": (st, [P, P, C.c_uint64]),
+        "xy_set_beta": (st, [P, C.c_double]),
+        "xy_synchronize": (st, [P]),
+        "xy_destroy": (st, [P]),
+        "xy_last_error": (C.c_char_p, [P]),
+        "xy_philox_words": (st, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                 C.c_int64, P, P]),
+        "xy_version": (C.c_int32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status, ctx=None):
+    if status != XY_OK:
+        msg = lib().xy_last_error(ctx)
+        raise XYError(status, msg.decode() if msg else "")
+    return status
+
+
+# -- same-named thin wrappers -------------------------------------------------
+
+def xy_create(params, stream_ptr=None, d_angles_ptr=None):
+    ctx = C.c_void_p()
+    check(lib().xy_create(C.byref(params), stream_ptr, d_angles_ptr, C.byref(ctx)))
+    return ctx
+
+
+def xy_reserve(ctx, n_more):
+    check(lib().xy_reserve(ctx, n_more), ctx)
+
+
+def xy_reset(ctx, seed):
+    check(lib().xy_reset(ctx, seed), ctx)
+
+
+def xy_timing(ctx, every):
+    check(lib().xy_timing(ctx, int(every)), ctx)
+
+
+def xy_kernel_time(ctx, kernel):
+    ms = C.c_double()
+    n = C.c_int64()
+    check(lib().xy_kernel_time(ctx, kernel, C.byref(ms), C.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def xy_sweep(ctx, n):
+    check(lib().xy_sweep(ctx, n), ctx)
+
+
+def xy_measure(ctx, first, count):
+    out = (xy_obs * max(count, 1))()
+    check(lib().xy_measure(ctx, first, count, out), ctx)
+    return out if count > 0 else (xy_obs * 0)()
+
+
+def xy_records_device(ctx):
+    p = C.c_void_p()
+    n = C.c_int64()
+    check(lib().xy_records_device(ctx, C.byref(p), C.byref(n)), ctx)
+    return p.value, n.value
+
+
+def xy_info(ctx):
+    n = C.c_int64()
+    s = C.c_uint64()
+    check(lib().xy_info(ctx, C.byref(n), C.byref(s)), ctx)
+    return n.value, s.value
+
+
+def xy_get_state(ctx, host_ptr):
+    s = C.c_uint64()
+    check(lib().xy_get_state(ctx, host_ptr, C.byref(s)), ctx)
+    return s.value
+
+
+def xy_set_state(ctx, host_ptr, next_sweep):
+    check(lib().xy_set_state(ctx, host_ptr, next_sweep), ctx)
+
+
+def xy_set_beta(ctx, beta):
+    check(lib().xy_set_beta(ctx, beta), ctx)
+
+
+def xy_synchronize(ctx):
+    check(lib().xy_synchronize(ctx), ctx)
+
+
+def xy_destroy(ctx):
+    check(lib().xy_destroy(ctx))
+
+
+def xy_last_error(ctx=None):
+    m = lib().xy_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def xy_philox_words(seed, sweep, lattice_id, domain, first, n, d_out_ptr, stream_ptr=None):
+    check(lib().xy_philox_words(seed, sweep, lattice_id, domain, first, n, d_out_ptr, stream_ptr))
+
+
+def xy_version():
+    return int(lib().xy_version())

@@ -1,0 +1,533 @@
+// xy_api.cu -- the C ABI declared in include/xy.h: validation, ownership,
+// sticky errors and launch sequencing around the kernels of xy_sweep.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "xy.h"
+#include "xy_internal.h"
+
+namespace {
+
+constexpr uint32_t kMagicLive = 0x58594C54u;   // "XYLT"
+constexpr uint32_t kMagicDead = 0xDEADC0DEu;
+
+thread_local char g_thread_msg[512] = "no error";
+
+// Live contexts, so that a destroyed or foreign pointer is refused without
+// reading freed memory.
+std::mutex g_live_mu;
+std::unordered_set<const void*>& live_set() {
+  static std::unordered_set<const void*> s;
+  return s;
+}
+bool is_live(const void* c) {
+  std::lock_guard<std::mutex> g(g_live_mu);
+  return live_set().count(c) != 0;
+}
+void mark_live(const void* c, bool live) {
+  std::lock_guard<std::mutex> g(g_live_mu);
+  if (live) {
+    live_set().insert(c);
+  } else {
+    live_set().erase(c);
+  }
+}
+
+void set_thread_msg(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_thread_msg, sizeof(g_thread_msg), fmt, ap);
+  va_end(ap);
+}
+
+}  // namespace
+
+struct xy_ctx {
+  uint32_t magic;
+  xy_params p;
+  cudaStream_t stream;
+  int device;
+  float* d_theta;          // [2][L][L/2]
+  bool owns_theta;
+  xy_record* d_rec;        // records [0, rec_cap)
+  int64_t rec_cap;
+  int64_t rec_count;       // records enqueued so far
+  uint64_t next_sweep;     // Philox sweep word of the next sweep
+  float* d_scratch;        // natural-order staging for get/set state
+  unsigned int* d_flag;    // device flag word (non-finite check)
+  int timing_every;        // bracket every k-th sweep's launches with events (0: off)
+  std::vector<cudaEvent_t> ev[2];   // per kernel: start/stop pairs, in order
+  size_t ev_used[2];
+  xy_status sticky;
+  char msg[512];
+};
+
+namespace {
+
+xy_status fail(xy_ctx* c, xy_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  snprintf(g_thread_msg, sizeof(g_thread_msg), "%s", buf);
+  if (c && is_live(c) && c->magic == kMagicLive && c->sticky == XY_OK) {
+    c->sticky = st;
+    snprintf(c->msg, sizeof(c->msg), "%s", buf);
+  }
+  return st;
+}
+
+xy_status cuda_fail(xy_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? XY_ENOMEM : XY_ECUDA, "%s: %s (%s)", what,
+              cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define XY_CUDA(ctx, call, what)                       \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+xy_status check_ctx(const xy_ctx* c) {
+  if (!c) {
+    set_thread_msg("NULL context");
+    return XY_EINVAL;
+  }
+  if (!is_live(c) || c->magic != kMagicLive) {
+    set_thread_msg("context is not live (destroyed or never created)");
+    return XY_ESTATE;
+  }
+  if (c->sticky != XY_OK) {
+    set_thread_msg("context is in an earlier error: %s", c->msg);
+    return c->sticky;
+  }
+  return XY_OK;
+}
+
+xy_status validate(const xy_params* p) {
+  if (!p) {
+    set_thread_msg("NULL params");
+    return XY_EINVAL;
+  }
+  if (p->L < 2 || p->L > XY_MAX_L || (p->L & 1)) {
+    set_thread_msg("L must be even and in [2, %d] (checkerboard needs a bipartite torus); got %d",
+                   XY_MAX_L, p->L);
+    return XY_EINVAL;
+  }
+  if (!(p->beta >= 0.0) || !isfinite(p->beta)) {
+    set_thread_msg("beta must be finite and >= 0");
+    return XY_EINVAL;
+  }
+  if (!isfinite(p->J)) {
+    set_thread_msg("J must be finite");
+    return XY_EINVAL;
+  }
+  if (!(p->delta > 0.0) || p->delta > M_PI + 1e-12) {
+    set_thread_msg("delta must be in (0, pi]");
+    return XY_EINVAL;
+  }
+  if (p->start != XY_START_HOT && p->start != XY_START_COLD) {
+    set_thread_msg("start must be XY_START_HOT or XY_START_COLD");
+    return XY_EINVAL;
+  }
+  if (p->sincos_mode != XY_SINCOS_ACCURATE && p->sincos_mode != XY_SINCOS_FAST) {
+    set_thread_msg("bad sincos_mode");
+    return XY_EINVAL;
+  }
+  if (p->reduce_mode != XY_REDUCE_FP64 && p->reduce_mode != XY_REDUCE_COMPENSATED) {
+    set_thread_msg("bad reduce_mode");
+    return XY_EINVAL;
+  }
+  if (p->reserved != 0) {
+    set_thread_msg("reserved must be 0");
+    return XY_EINVAL;
+  }
+  return XY_OK;
+}
+
+xy_status grow_records(xy_ctx* c, int64_t need) {
+  if (need <= c->rec_cap) return XY_OK;
+  int64_t cap = c->rec_cap > 0 ? c->rec_cap : 1024;
+  while (cap < need) cap *= 2;
+  xy_record* nr = nullptr;
+  XY_CUDA(c, cudaMalloc(&nr, (size_t)cap * sizeof(xy_record)), "allocating records");
+  cudaError_t e = cudaMemsetAsync(nr, 0, (size_t)cap * sizeof(xy_record), c->stream);
+  if (e == cudaSuccess && c->rec_count > 0)
+    e = cudaMemcpyAsync(nr, c->d_rec, (size_t)c->rec_count * sizeof(xy_record),
+                        cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(nr);
+    return cuda_fail(c, e, "growing records");
+  }
+  if (c->d_rec) cudaFree(c->d_rec);
+  c->d_rec = nr;
+  c->rec_cap = cap;
+  return XY_OK;
+}
+
+// Event pair for the next timed launch of kernel k (grows the pool).
+cudaError_t next_events(xy_ctx* c, int k, cudaEvent_t* a, cudaEvent_t* b) {
+  std::vector<cudaEvent_t>& v = c->ev[k];
+  while (v.size() < c->ev_used[k] + 2) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    v.push_back(e);
+  }
+  *a = v[c->ev_used[k]];
+  *b = v[c->ev_used[k] + 1];
+  c->ev_used[k] += 2;
+  return cudaSuccess;
+}
+
+cudaError_t timed_half_sweep(xy_ctx* c, int colour, const xyk::HalfSweepArgs& a) {
+  if (c->timing_every <= 0 || (a.sweep % (uint32_t)c->timing_every) != 0)
+    return xyk::launch_half_sweep(colour, c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  cudaEvent_t e0, e1;
+  cudaError_t e = next_events(c, colour, &e0, &e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess)
+    e = xyk::launch_half_sweep(colour, c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  return e;
+}
+
+void split_key(uint64_t seed, uint32_t* k0, uint32_t* k1) {
+  *k0 = (uint32_t)(seed & 0xffffffffu);
+  *k1 = (uint32_t)(seed >> 32);
+}
+
+void release(xy_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
+    c->ev[k].clear();
+    c->ev_used[k] = 0;
+  }
+  if (c->owns_theta && c->d_theta) cudaFree(c->d_theta);
+  if (c->d_rec) cudaFree(c->d_rec);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->d_flag) cudaFree(c->d_flag);
+  c->d_theta = nullptr;
+  c->d_rec = nullptr;
+  c->d_scratch = nullptr;
+  c->d_flag = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t xy_version(void) { return 100; }
+
+const char* xy_last_error(const xy_ctx* ctx) {
+  if (ctx && is_live(ctx) && ctx->magic == kMagicLive && ctx->sticky != XY_OK) return ctx->msg;
+  return g_thread_msg;
+}
+
+xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ctx** out) {
+  if (!out) {
+    set_thread_msg("NULL output pointer");
+    return XY_EINVAL;
+  }
+  *out = nullptr;
+  xy_status st = validate(p);
+  if (st != XY_OK) return st;
+  if (d_angles && (reinterpret_cast<uintptr_t>(d_angles) & 15u)) {
+    set_thread_msg("d_angles must be 16-byte aligned");
+    return XY_EINVAL;
+  }
+  xy_ctx* c = new (std::nothrow) xy_ctx();   // value-initialised: pointers null, counts 0
+  if (!c) {
+    set_thread_msg("host allocation failed");
+    return XY_ENOMEM;
+  }
+  c->magic = kMagicLive;
+  c->p = *p;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  c->sticky = XY_OK;
+  snprintf(c->msg, sizeof(c->msg), "no error");
+  const size_t N = (size_t)p->L * (size_t)p->L;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) {
+    if (d_angles) {
+      c->d_theta = static_cast<float*>(d_angles);
+      c->owns_theta = false;
+    } else {
+      e = cudaMalloc(&c->d_theta, N * sizeof(float));
+      c->owns_theta = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    st = (e == cudaErrorMemoryAllocation) ? XY_ENOMEM : XY_ECUDA;
+    set_thread_msg("xy_create: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
+    release(c);
+    c->magic = kMagicDead;
+    delete c;
+    return st;
+  }
+  uint32_t k0, k1;
+  split_key(p->seed, &k0, &k1);
+  e = xyk::launch_start(c->d_theta, p->L, k0, k1, p->lattice_id, p->start == XY_START_HOT,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    set_thread_msg("xy_create: start kernel: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
+    release(c);
+    c->magic = kMagicDead;
+    delete c;
+    return XY_ECUDA;
+  }
+  c->next_sweep = 0;
+  mark_live(c, true);
+  *out = c;
+  return XY_OK;
+}
+
+xy_status xy_reset(xy_ctx* c, uint64_t seed) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  c->p.seed = seed;
+  uint32_t k0, k1;
+  split_key(seed, &k0, &k1);
+  XY_CUDA(c, xyk::launch_start(c->d_theta, c->p.L, k0, k1, c->p.lattice_id,
+                               c->p.start == XY_START_HOT, c->stream),
+          "xy_reset: start kernel");
+  if (c->d_rec && c->rec_count > 0)
+    XY_CUDA(c, cudaMemsetAsync(c->d_rec, 0, (size_t)c->rec_count * sizeof(xy_record), c->stream),
+            "xy_reset: clear records");
+  c->rec_count = 0;
+  c->next_sweep = 0;
+  return XY_OK;
+}
+
+xy_status xy_timing(xy_ctx* c, int every) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (every < 0) return fail(c, XY_EINVAL, "xy_timing: negative period");
+  c->timing_every = every;
+  c->ev_used[0] = c->ev_used[1] = 0;
+  return XY_OK;
+}
+
+xy_status xy_kernel_time(xy_ctx* c, int kernel, double* total_ms, int64_t* launches) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (kernel < 0 || kernel > 1 || !total_ms || !launches)
+    return fail(c, XY_EINVAL, "xy_kernel_time: bad arguments");
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_kernel_time: stream");
+  double sum = 0.0;
+  for (size_t i = 0; i + 1 < c->ev_used[kernel]; i += 2) {
+    float ms = 0.f;
+    XY_CUDA(c, cudaEventElapsedTime(&ms, c->ev[kernel][i], c->ev[kernel][i + 1]),
+            "xy_kernel_time: elapsed");
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = (int64_t)(c->ev_used[kernel] / 2);
+  return XY_OK;
+}
+
+xy_status xy_reserve(xy_ctx* c, int64_t n_more) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (n_more < 0) return fail(c, XY_EINVAL, "xy_reserve: negative count");
+  return grow_records(c, c->rec_count + n_more);
+}
+
+xy_status xy_sweep(xy_ctx* c, int64_t n) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (n < 0) return fail(c, XY_EINVAL, "xy_sweep: negative sweep count");
+  if (n == 0) return XY_OK;
+  if (c->next_sweep + (uint64_t)n > 0xffffffffull)
+    return fail(c, XY_EINVAL, "xy_sweep: sweep counter would pass 2^32 - 1");
+  st = grow_records(c, c->rec_count + n);
+  if (st != XY_OK) return st;
+  xyk::HalfSweepArgs a;
+  a.theta = c->d_theta;
+  a.L = c->p.L;
+  a.W = c->p.L / 2;
+  a.K = (float)(c->p.beta * c->p.J);
+  a.delta = (float)c->p.delta;
+  split_key(c->p.seed, &a.key0, &a.key1);
+  a.lattice_id = c->p.lattice_id;
+  a.beta = c->p.beta;
+  for (int64_t i = 0; i < n; ++i) {
+    a.sweep = (uint32_t)(c->next_sweep + (uint64_t)i);
+    a.rec = c->d_rec + c->rec_count + i;
+    cudaError_t e = timed_half_sweep(c, 0, a);
+    if (e == cudaSuccess) e = timed_half_sweep(c, 1, a);
+    if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: launch");
+  }
+  c->next_sweep += (uint64_t)n;
+  c->rec_count += n;
+  return XY_OK;
+}
+
+xy_status xy_measure(xy_ctx* c, int64_t first, int64_t count, xy_obs* out) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (first < 0 || count < 0 || first + count > c->rec_count)
+    return fail(c, XY_EINVAL, "xy_measure: range [%lld, %lld) outside [0, %lld)",
+                (long long)first, (long long)(first + count), (long long)c->rec_count);
+  if (count > 0 && !out) return fail(c, XY_EINVAL, "xy_measure: NULL output");
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_measure: stream");
+  if (count == 0) return XY_OK;
+  xy_record* h = new (std::nothrow) xy_record[count];
+  if (!h) return fail(c, XY_ENOMEM, "xy_measure: host allocation");
+  cudaError_t e = cudaMemcpy(h, c->d_rec + first, (size_t)count * sizeof(xy_record),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return cuda_fail(c, e, "xy_measure: copy");
+  }
+  const double N = (double)c->p.L * (double)c->p.L, J = c->p.J;
+  const double unit = ldexp(1.0, -XY_FX_SHIFT);
+  bool bad = false;
+  for (int64_t i = 0; i < count; ++i) {
+    const xy_record& r = h[i];
+    xy_obs& o = out[i];
+    o.C = (double)r.sum[0] * unit;
+    o.Ix = (double)r.sum[1] * unit;
+    o.Iy = (double)r.sum[2] * unit;
+    o.Mx = (double)r.sum[3] * unit;
+    o.My = (double)r.sum[4] * unit;
+    o.accepted = r.accepted;
+    o.beta = r.beta;
+    o.e = -J * o.C / N;
+    o.abs_m = sqrt(o.Mx * o.Mx + o.My * o.My) / N;
+    o.upsilon = (J * o.C - r.beta * J * J * (o.Ix * o.Ix + o.Iy * o.Iy)) / (2.0 * N);
+    if (r.flags & 1ull) bad = true;
+  }
+  delete[] h;
+  if (bad) return fail(c, XY_ENUMERIC, "xy_measure: a record saw a non-finite sum");
+  return XY_OK;
+}
+
+xy_status xy_records_device(xy_ctx* c, const xy_record** d_records, int64_t* count) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (!d_records || !count) return fail(c, XY_EINVAL, "xy_records_device: NULL output");
+  *d_records = c->d_rec;
+  *count = c->rec_count;
+  return XY_OK;
+}
+
+xy_status xy_info(const xy_ctx* c, int64_t* n_records, uint64_t* next_sweep) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (n_records) *n_records = c->rec_count;
+  if (next_sweep) *next_sweep = c->next_sweep;
+  return XY_OK;
+}
+
+xy_status xy_get_state(xy_ctx* c, float* host, uint64_t* next_sweep) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (!host) return fail(c, XY_EINVAL, "xy_get_state: NULL output");
+  const size_t N = (size_t)c->p.L * (size_t)c->p.L;
+  if (!c->d_scratch) XY_CUDA(c, cudaMalloc(&c->d_scratch, N * sizeof(float)), "xy_get_state: scratch");
+  XY_CUDA(c, xyk::launch_split_to_natural(c->d_theta, c->d_scratch, c->p.L, c->stream),
+          "xy_get_state: layout kernel");
+  XY_CUDA(c, cudaMemcpyAsync(host, c->d_scratch, N * sizeof(float), cudaMemcpyDeviceToHost,
+                             c->stream),
+          "xy_get_state: copy");
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_get_state: stream");
+  if (next_sweep) *next_sweep = c->next_sweep;
+  return XY_OK;
+}
+
+xy_status xy_set_state(xy_ctx* c, const float* host, uint64_t next_sweep) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (!host) return fail(c, XY_EINVAL, "xy_set_state: NULL input");
+  if (next_sweep > 0xffffffffull) return fail(c, XY_EINVAL, "xy_set_state: sweep >= 2^32");
+  const size_t N = (size_t)c->p.L * (size_t)c->p.L;
+  if (!c->d_scratch) XY_CUDA(c, cudaMalloc(&c->d_scratch, N * sizeof(float)), "xy_set_state: scratch");
+  XY_CUDA(c, cudaMemcpyAsync(c->d_scratch, host, N * sizeof(float), cudaMemcpyHostToDevice,
+                             c->stream),
+          "xy_set_state: copy");
+  XY_CUDA(c, cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned int), c->stream), "xy_set_state: flag");
+  XY_CUDA(c, xyk::launch_check_finite(c->d_scratch, (int64_t)N, c->d_flag, c->stream),
+          "xy_set_state: check kernel");
+  unsigned int flag = 0;
+  XY_CUDA(c, cudaMemcpyAsync(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream),
+          "xy_set_state: flag copy");
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_set_state: stream");
+  if (flag) {
+    set_thread_msg("xy_set_state: non-finite angle rejected; state unchanged");
+    return XY_EINVAL;   // not sticky: the context is untouched
+  }
+  XY_CUDA(c, xyk::launch_natural_to_split(c->d_scratch, c->d_theta, c->p.L, c->stream),
+          "xy_set_state: layout kernel");
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_set_state: stream");
+  c->next_sweep = next_sweep;
+  c->rec_count = 0;
+  if (c->d_rec && c->rec_cap > 0)
+    XY_CUDA(c, cudaMemsetAsync(c->d_rec, 0, (size_t)c->rec_cap * sizeof(xy_record), c->stream),
+            "xy_set_state: clear records");
+  return XY_OK;
+}
+
+xy_status xy_set_beta(xy_ctx* c, double beta) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (!(beta >= 0.0) || !isfinite(beta)) {
+    set_thread_msg("xy_set_beta: beta must be finite and >= 0");
+    return XY_EINVAL;
+  }
+  c->p.beta = beta;
+  return XY_OK;
+}
+
+xy_status xy_synchronize(xy_ctx* c) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_synchronize");
+  return XY_OK;
+}
+
+xy_status xy_destroy(xy_ctx* c) {
+  if (!c) return XY_OK;
+  if (!is_live(c) || c->magic != kMagicLive) {
+    set_thread_msg("xy_destroy: context is not live (double destroy?)");
+    return XY_ESTATE;
+  }
+  mark_live(c, false);
+  cudaStreamSynchronize(c->stream);
+  release(c);
+  c->magic = kMagicDead;
+  delete c;
+  return XY_OK;
+}
+
+xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, uint32_t domain,
+                          uint32_t first, int64_t n, uint32_t* d_out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && !d_out)) {
+    set_thread_msg("xy_philox_words: bad arguments");
+    return XY_EINVAL;
+  }
+  uint32_t k0, k1;
+  split_key(seed, &k0, &k1);
+  cudaError_t e = xyk::launch_philox_words(k0, k1, sweep, lattice_id, domain, first, n, d_out,
+                                           reinterpret_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) {
+    set_thread_msg("xy_philox_words: %s", cudaGetErrorString(e));
+    return XY_ECUDA;
+  }
+  return XY_OK;
+}
+
+}  // extern "C"

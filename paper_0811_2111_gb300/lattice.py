@@ -1,0 +1,122 @@
+"""Python front end of one simulated lattice (torch for memory and streams).
+
+``Lattice`` owns a torch device buffer for the angles, passes its pointer and
+the torch stream to ``xy_create``, and exposes the ABI calls with numpy
+results.  All arithmetic happens in the CUDA library.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import _lib as X
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Lattice:
+    def __init__(self, L, beta, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
+                 reduce="fp64", lattice_id=0, device=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.L = int(L)
+        p = X.xy_params()
+        p.L = self.L
+        p.start = {"hot": X.XY_START_HOT, "cold": X.XY_START_COLD}[start]
+        p.beta = float(beta)
+        p.J = float(J)
+        p.delta = float(delta)
+        p.seed = int(seed)
+        p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST}[sincos]
+        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.lattice_id = int(lattice_id)
+        p.reserved = 0
+        self.params = p
+        self.J = float(J)
+        with torch.cuda.device(self.device):
+            self.angles = torch.empty(self.L * self.L, dtype=torch.float32, device=self.device)
+            self.ctx = X.xy_create(p, C.c_void_p(self.stream.cuda_stream),
+                                   C.c_void_p(self.angles.data_ptr()))
+
+    # -- ABI calls ---------------------------------------------------------
+    def reserve(self, n):
+        X.xy_reserve(self.ctx, n)
+
+    def reset(self, seed):
+        X.xy_reset(self.ctx, int(seed))
+
+    def timing(self, every=1):
+        X.xy_timing(self.ctx, every)
+
+    def kernel_time(self, kernel):
+        return X.xy_kernel_time(self.ctx, kernel)
+
+    def sweep(self, n=1):
+        X.xy_sweep(self.ctx, n)
+
+    def info(self):
+        return X.xy_info(self.ctx)
+
+    def observables(self, first=0, count=None):
+        n, _ = X.xy_info(self.ctx)
+        count = n - first if count is None else count
+        obs = X.xy_measure(self.ctx, first, count)
+        names = ["e", "abs_m", "upsilon", "C", "Ix", "Iy", "Mx", "My", "beta"]
+        out = {k: np.array([getattr(o, k) for o in obs], np.float64) for k in names}
+        out["accepted"] = np.array([o.accepted for o in obs], np.uint64)
+        return out
+
+    def state(self):
+        buf = np.empty(self.L * self.L, np.float32)
+        nxt = X.xy_get_state(self.ctx, buf.ctypes.data_as(C.c_void_p))
+        return buf.reshape(self.L, self.L), nxt
+
+    def set_state(self, angles, next_sweep):
+        a = np.ascontiguousarray(angles, np.float32).reshape(-1)
+        if a.size != self.L * self.L:
+            raise ValueError("wrong number of angles")
+        X.xy_set_state(self.ctx, a.ctypes.data_as(C.c_void_p), int(next_sweep))
+
+    def set_beta(self, beta):
+        X.xy_set_beta(self.ctx, float(beta))
+
+    def synchronize(self):
+        X.xy_synchronize(self.ctx)
+
+    def records_device(self):
+        return X.xy_records_device(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            X.xy_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def philox_words(seed, sweep, lattice_id, domain, first, n, device=None):
+    """Device Philox words (n, 4) uint32 as a numpy array, via xy_philox_words."""
+    torch = _torch()
+    dev = torch.device(device if device is not None else "cuda")
+    out = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    X.xy_philox_words(seed, sweep, lattice_id, domain, first, n, C.c_void_p(out.data_ptr()),
+                      C.c_void_p(stream.cuda_stream))
+    stream.synchronize()
+    return out.cpu().numpy().view(np.uint32)

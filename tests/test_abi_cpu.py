@@ -1,0 +1,97 @@
+"""Host-side checks of the C-ABI library that need no GPU.
+
+The library must load, export every entry point ``include/*.h`` declares,
+and refuse bad arguments before touching the device.
+"""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+from paper_0811_2111_gb300 import _lib as X
+from paper_0811_2111_gb300 import build as build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(xy_[a-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return X.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for n in ("xy_create", "xy_sweep", "xy_measure", "xy_destroy", "xy_get_state",
+              "xy_set_state", "xy_last_error", "xy_philox_words"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_entry_points() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version(lib):
+    assert X.xy_version() >= 100
+
+
+def _params(**kw):
+    p = X.xy_params()
+    p.L, p.start, p.beta, p.J, p.delta, p.seed = 8, 0, 1.0, 1.0, 3.14159, 1
+    p.sincos_mode, p.reduce_mode, p.lattice_id, p.reserved = 0, 0, 0, 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,fragment", [
+    (dict(L=3), "even"), (dict(L=0), "even"), (dict(L=65536), "even"),
+    (dict(beta=-1.0), "beta"), (dict(beta=float("nan")), "beta"),
+    (dict(delta=0.0), "delta"), (dict(delta=4.0), "delta"),
+    (dict(start=7), "start"), (dict(sincos_mode=5), "sincos"), (dict(reduce_mode=2), "reduce"),
+    (dict(reserved=1), "reserved"), (dict(J=float("inf")), "J"),
+])
+def test_create_rejects_bad_parameters(lib, kw, fragment):
+    ctx = C.c_void_p()
+    st = lib.xy_create(C.byref(_params(**kw)), None, None, C.byref(ctx))
+    assert st == X.XY_EINVAL
+    assert ctx.value is None
+    assert fragment in X.xy_last_error(None)
+
+
+def test_null_arguments(lib):
+    ctx = C.c_void_p()
+    assert lib.xy_create(None, None, None, C.byref(ctx)) == X.XY_EINVAL
+    assert lib.xy_create(C.byref(_params()), None, None, None) == X.XY_EINVAL
+    assert lib.xy_create(C.byref(_params()), None, C.c_void_p(8), C.byref(ctx)) == X.XY_EINVAL
+    assert lib.xy_sweep(None, 1) == X.XY_EINVAL
+    assert lib.xy_destroy(None) == X.XY_OK
+    bogus = C.c_void_p(0x1000)
+    assert lib.xy_sweep(bogus, 1) == X.XY_ESTATE        # never created: refused, not read
+    assert lib.xy_destroy(bogus) == X.XY_ESTATE
+    assert lib.xy_philox_words(1, 0, 0, 1, 0, 5, None, None) == X.XY_EINVAL
+
+
+def test_create_without_device_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = C.c_void_p()
+    st = lib.xy_create(C.byref(_params()), None, None, C.byref(ctx))
+    assert st in (X.XY_ECUDA, X.XY_ENOMEM)
+    assert ctx.value is None
+    assert "xy_create" in X.xy_last_error(None)

@@ -1,0 +1,279 @@
+"""CUDA path vs FP64 oracle, element by element (needs a GB300).
+
+Everything goes through the C ABI (``libxy.so`` via the ctypes binding).
+Tolerances (derived in the design doc from the FP32 arithmetic of the kernels):
+  * Philox words and hot-start counters: bit-exact;
+  * accept decisions: identical outside |u - exp(-beta dE)| < 1e-6 (accurate
+    path); the in-band count is reported;
+  * post-sweep angles: within 1e-5 rad of the oracle's choice;
+  * per-sweep sums: ``gpu_util.record_tolerance``;
+  * long runs: observables within 3 sigma (binned jackknife).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import (ANGLE_TOL, BAND_ACCURATE, circ, compare_record, lockstep_sweep,
+                      record_tolerance)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300 import lattice as LT  # noqa: E402
+from paper_0811_2111_gb300 import workloads as WL  # noqa: E402
+from paper_0811_2111_gb300 import _lib as X  # noqa: E402
+
+
+def run_lockstep(lat, n, beta, seed, J=1.0, delta=np.pi, band=BAND_ACCURATE, lattice_id=0,
+                 fast=False):
+    """n GPU sweeps, each checked in lock-step; returns summary dict."""
+    L = lat.L
+    tol = record_tolerance(L * L, fast)
+    n0, _ = lat.info()
+    s_before, t0 = lat.state()
+    worst = dict(in_band=0, out_band=0, angle=0.0, rec=0.0, acc_mismatch=0,
+                 rec_abs=np.zeros(5))
+    for i in range(n):
+        lat.sweep(1)
+        s_after, _ = lat.state()
+        red, blk = lockstep_sweep(s_before, s_after, L, beta, seed, t0 + i, J, delta, band,
+                                  lattice_id)
+        obs = lat.observables(n0 + i, 1)
+        row = {k: obs[k][0] for k in obs}
+        diff, _ = compare_record(row, s_after, L, J)
+        worst["in_band"] += red.in_band + blk.in_band
+        worst["out_band"] += red.out_band_mismatch + blk.out_band_mismatch
+        worst["angle"] = max(worst["angle"], red.max_angle_err, blk.max_angle_err)
+        worst["rec"] = max(worst["rec"], float(diff.max()) / tol)
+        worst["rec_abs"] = np.maximum(worst["rec_abs"], diff)
+        worst["acc_mismatch"] += int(row["accepted"]) != red.accepted + blk.accepted
+        s_before = s_after
+    return worst
+
+
+# ---------------------------------------------------------------------------
+# Philox and start configurations
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed,sweep,lid,dom,first,n", [
+    (1, 0, 0, 1, 0, 1024),
+    (7, 999, 0, 1, 0, 1 << 20),
+    (0xFFFFFFFFFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF, 2, 0xFFFFFFFF - 4095, 4096),
+    (0x243F6A8885A308D3, 12345, 17, 0, 16777216 - 100000, 100000),
+])
+def test_philox_words_bit_exact(seed, sweep, lid, dom, first, n):
+    gpu = LT.philox_words(seed, sweep, lid, dom, first, n)
+    ref = oracle.philox_words(seed, sweep, lid, dom, first, n)
+    assert np.array_equal(gpu, ref)
+
+
+@pytest.mark.parametrize("L,seed,lid", [(32, 1, 0), (4096, 7, 0), (64, 5, 3)])
+def test_hot_start_matches_oracle(L, seed, lid):
+    with LT.Lattice(L, 1.0, seed, lattice_id=lid) as lat:
+        s, nxt = lat.state()
+    assert nxt == 0
+    ref = oracle.start(L, L, seed, lid)
+    assert circ(s.reshape(-1), ref).max() < 1e-6
+    assert s.min() >= 0 and s.max() < np.float32(2 * np.pi)
+
+
+def test_cold_start_is_zero():
+    with LT.Lattice(16, 1.0, 3, start="cold") as lat:
+        s, _ = lat.state()
+    assert np.all(s == 0)
+
+
+# ---------------------------------------------------------------------------
+# Lock-step parity
+# ---------------------------------------------------------------------------
+
+def test_lockstep_small_config_accurate():
+    """L=32, beta=1, seed 1, 1000 sweeps, accurate path: the small configuration."""
+    w = WL.SMALL
+    with LT.Lattice(w.L, w.beta, w.seed) as lat:
+        r = run_lockstep(lat, w.sweeps, w.beta, w.seed)
+    print("lockstep L=32:", r)
+    assert r["out_band"] == 0
+    assert r["angle"] <= ANGLE_TOL
+    assert r["rec"] <= 1.0
+    assert r["acc_mismatch"] == 0
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 10, 34, 130, 258])
+def test_lockstep_edge_sizes(L):
+    """Degenerate and ragged sides: L=2 (double bonds), odd plane widths, partial tiles."""
+    with LT.Lattice(L, 0.9, 100 + L) as lat:
+        r = run_lockstep(lat, 30, 0.9, 100 + L)
+    assert r["out_band"] == 0 and r["angle"] <= ANGLE_TOL
+    assert r["rec"] <= 1.0 and r["acc_mismatch"] == 0
+
+
+@pytest.mark.parametrize("beta,J,delta", [(0.0, 1.0, np.pi), (2.5, 1.0, 0.7), (0.6, -1.3, 2.0)])
+def test_lockstep_parameters(beta, J, delta):
+    with LT.Lattice(48, beta, 21, J=J, delta=delta) as lat:
+        r = run_lockstep(lat, 40, beta, 21, J=J, delta=delta)
+    assert r["out_band"] == 0 and r["angle"] <= ANGLE_TOL
+    assert r["rec"] <= 1.0 and r["acc_mismatch"] == 0
+
+
+def test_lockstep_large_config_full_size():
+    """L=4096, beta=1.12, seed 7 (the throughput configuration), same launch path as the
+    bench: sweeps 0, 1 and 20 checked over all 16.8M sites."""
+    w = WL.LARGE
+    with LT.Lattice(w.L, w.beta, w.seed) as lat:
+        r0 = run_lockstep(lat, 2, w.beta, w.seed)
+        lat.sweep(17)
+        r1 = run_lockstep(lat, 1, w.beta, w.seed)
+    for r in (r0, r1):
+        print("lockstep L=4096:", r, "tolerance", record_tolerance(w.L * w.L))
+        assert r["out_band"] == 0
+        assert r["angle"] <= ANGLE_TOL
+        assert r["rec"] <= 1.0 and r["acc_mismatch"] == 0
+
+
+def test_fast_path_error_is_bounded():
+    """__sincosf/__expf path: decisions may differ in a wider band, stated and bounded."""
+    w = WL.SMALL
+    with LT.Lattice(w.L, w.beta, w.seed, sincos="fast") as lat:
+        r_wide = run_lockstep(lat, 300, w.beta, w.seed, band=2e-5, fast=True)
+    print("fast path, band 2e-5:", r_wide)
+    assert r_wide["out_band"] == 0
+    assert r_wide["angle"] <= ANGLE_TOL and r_wide["rec"] <= 1.0
+
+
+def test_compensated_reduction_matches_fp64():
+    w = WL.SMALL
+    outs = []
+    for red in ("fp64", "compensated"):
+        with LT.Lattice(128, 1.1, 9, reduce=red) as lat:
+            lat.sweep(50)
+            outs.append((lat.state()[0], lat.observables()))
+    assert np.array_equal(outs[0][0], outs[1][0])      # the chain does not depend on it
+    tol = record_tolerance(128 * 128)
+    for k in ("C", "Ix", "Iy", "Mx", "My"):
+        assert np.max(np.abs(outs[0][1][k] - outs[1][1][k])) <= tol
+
+
+# ---------------------------------------------------------------------------
+# Statistics, resume, determinism
+# ---------------------------------------------------------------------------
+
+def test_long_run_observables_agree_with_oracle():
+    """Independent GPU chains vs independent oracle chains: means agree within 3.5 sigma.
+
+    At L=32, beta=1 (near the BKT region) single-chain jackknife errors
+    underestimate the chain-to-chain spread by ~2x, so the error of each mean
+    comes from the spread of 8 independent chains per side."""
+    L, beta, n, chains = 32, 1.0, 10000, 8
+    cut = n // 10
+    g = {k: [] for k in ("e", "m", "u", "acc")}
+    o = {k: [] for k in ("e", "m", "u", "acc")}
+    for c in range(chains):
+        with LT.Lattice(L, beta, 1, lattice_id=c) as lat:
+            lat.sweep(n)
+            r = lat.observables()
+        g["e"].append(r["e"][cut:].mean())
+        g["m"].append(r["abs_m"][cut:].mean())
+        g["u"].append(r["upsilon"][cut:].mean())
+        g["acc"].append(r["accepted"][cut:].astype(np.float64).mean() / (L * L))
+        rec, _ = oracle.run(L, L, beta, n, seed=1001 + c)
+        e_o, m_o, u_o = oracle.observables(rec[cut:, :5], L * L, beta)
+        o["e"].append(e_o.mean())
+        o["m"].append(m_o.mean())
+        o["u"].append(u_o.mean())
+        o["acc"].append(rec[cut:, 5].mean() / (L * L))
+    for k in ("e", "m", "u", "acc"):
+        a, b = np.array(g[k]), np.array(o[k])
+        err = np.hypot(a.std(ddof=1) / np.sqrt(chains), b.std(ddof=1) / np.sqrt(chains))
+        print(f"{k}: gpu {a.mean():.5f} oracle {b.mean():.5f} +- {err:.5f}")
+        assert abs(a.mean() - b.mean()) <= 3.5 * err
+
+
+def test_resume_is_bit_exact_and_runs_are_deterministic():
+    L, beta, seed = 64, 1.05, 17
+    with LT.Lattice(L, beta, seed) as a:
+        a.sweep(20)
+        sa, _ = a.state()
+        oa = a.observables()
+    with LT.Lattice(L, beta, seed) as b:
+        b.sweep(10)
+        mid, nxt = b.state()
+        ob1 = b.observables()
+    with LT.Lattice(L, beta, seed) as c:
+        c.set_state(mid, nxt)
+        c.sweep(10)
+        sc, nxt2 = c.state()
+        oc = c.observables()
+    assert nxt2 == 20
+    assert np.array_equal(sa, sc)
+    for k in ("C", "Ix", "Iy", "Mx", "My", "accepted"):
+        assert np.array_equal(oa[k][:10], ob1[k])
+        assert np.array_equal(oa[k][10:], oc[k])
+
+
+def test_max_side_runs():
+    """Largest configured side (1 GiB of angles): sampled sites checked against the oracle."""
+    w = WL.HUGE
+    with LT.Lattice(w.L, w.beta, w.seed) as lat:
+        s0, _ = lat.state()
+        lat.sweep(1)
+        s1, _ = lat.state()
+        obs = lat.observables()
+    L = w.L
+    rng = np.random.default_rng(0)
+    y = rng.integers(0, L, 20000)
+    x = rng.integers(0, L, 20000)
+    red = ((x + y) & 1) == 0
+    sites = (y * L + x)[red]
+    tp, u1, p, acc = oracle.attempt_sites(s0.reshape(-1).astype(np.float64), L, L, sites,
+                                          w.beta, w.seed, 0)
+    b = s0.reshape(-1)[sites]
+    a = s1.reshape(-1)[sites]
+    changed = a != b
+    unobs = circ(tp, b) < 2e-6
+    band = np.abs(u1 - p) < BAND_ACCURATE
+    assert np.count_nonzero((changed != acc) & ~unobs & ~band) == 0
+    assert np.isfinite(obs["e"]).all() and -2.0 < obs["e"][0] < 0.0
+
+
+# ---------------------------------------------------------------------------
+# Error paths through the ABI
+# ---------------------------------------------------------------------------
+
+def test_error_paths_on_device():
+    lat = LT.Lattice(16, 1.0, 1)
+    lat.sweep(0)                                        # empty request is a no-op
+    assert lat.info() == (0, 0)
+    bad = np.zeros((16, 16), np.float32)
+    bad[3, 4] = np.nan
+    with pytest.raises(X.XYError) as ei:
+        lat.set_state(bad, 0)
+    assert ei.value.status == X.XY_EINVAL
+    lat.sweep(2)                                        # not sticky: still usable
+    assert lat.info()[0] == 2
+    with pytest.raises(X.XYError) as ei:
+        X.xy_measure(lat.ctx, 1, 5)
+    assert ei.value.status == X.XY_EINVAL
+    with pytest.raises(X.XYError) as ei:                # sticky from now on
+        lat.sweep(1)
+    assert ei.value.status == X.XY_EINVAL
+    ctx = lat.ctx
+    lat.close()
+    assert X.lib().xy_destroy(ctx) == X.XY_ESTATE       # double destroy refused
+    assert X.lib().xy_sweep(ctx, 1) == X.XY_ESTATE      # use after destroy refused
+
+
+def test_sweep_counter_limit():
+    with LT.Lattice(8, 1.0, 1) as lat:
+        s, _ = lat.state()
+        lat.set_state(s, 0xFFFFFFFF - 2)
+        lat.sweep(2)
+        with pytest.raises(X.XYError) as ei:
+            lat.sweep(2)
+        assert ei.value.status == X.XY_EINVAL
