@@ -32,6 +32,18 @@ sys.path.insert(0, ROOT)
 METRIC = "XY spin-updates/s on 1 GB300 (L=4096 and batched) and % of roofline"
 UNIT = "spin-updates/s"
 FLUSH_BYTES = 256 << 20
+
+# Algorithmic instruction count per site update (one issue slot each), the
+# work the method itself requires on this GPU:
+#   Philox4x32-10: 20 wide multiplies + 20 three-input xors, 2 + 2 of them shared
+#     by all sites of a sweep -> 36;
+#   proposal 2u0 - 1 and wrap -> 6;  neighbour sums (2 x 3 adds) -> 6;
+#   two unit vectors (own + proposal; neighbours reuse their own): 2 x 27 with the
+#     polynomial / CUDA sincosf-class path, 2 x 3 with the SFU intrinsics;
+#   dE, Boltzmann factor, accept test and select: 22 (expf) / 14 (__expf);
+#   per-sweep sums: 17 per black site -> 8.5 per update.
+ALG_INSTR_PER_UPDATE = {"accurate": 132.5, "libm": 132.5, "fast": 76.5}
+SMS, SMSP_PER_SM, LANES = 152, 4, 32       # GB300: 152 SMs x 4 schedulers x 32 lanes
 TIMING_EVERY = 50          # kernel events on every 50th sweep of the timed region
 
 
@@ -41,7 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--sincos", choices=["accurate", "fast"], default="accurate")
+    ap.add_argument("--sincos", choices=["accurate", "fast", "libm"], default="accurate")
+    ap.add_argument("--algorithm", choices=["auto", "fused", "two_pass"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -245,7 +258,8 @@ def run_ours(args):
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
     lat = Lattice(w.L, w.beta, w.seed, device=dev, stream=stream, lattice_id=rank,
-                  sincos=args.sincos)
+                  sincos=args.sincos, algorithm=args.algorithm)
+    fused = args.algorithm == "fused" or (args.algorithm == "auto" and w.L % 128 == 0)
     lat.reserve(w.sweeps)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -309,22 +323,33 @@ def run_ours(args):
                "h2d_bytes_per_step": 4 * w.sites,
                "d2h_bytes_per_step": 4 * w.sites + C.sizeof(X.xy_record) * w.sweeps}
 
-    # roofline of the dominant kernel (the half-sweep with the larger device time)
+    # roofline of the dominant kernel (the one with the larger device time)
     kern = max((0, 1), key=lambda k: kt[k][0])
     kms, klaunch = kt[kern]
     avg_s = kms * 1e-3 / max(klaunch, 1)
-    alg_bytes = 8.0 * (w.sites // 2)          # 8 B per update (read + write of the angle)
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / avg_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(),
-                "kernel": ["red_half_sweep", "black_half_sweep_measure"][kern],
-                "kernel_avg_us": avg_s * 1e6, "peak_kind": peak_kind,
+    updates_per_launch = w.sites if fused else w.sites // 2
+    alg_bytes = 8.0 * updates_per_launch     # 8 B per update: one read + one write of the angle
+    hbm_peak, peak_kind = measured_peaks()
+    hbm_achieved = alg_bytes / avg_s / 1e9
+    names = (["sweep_fused"] if fused else ["red_half_sweep", "black_half_sweep_measure"])
+    # issue-slot roofline: 152 SMs x 4 schedulers x 32 lanes per clock at the
+    # median SM clock sampled during the timed region (max clock if unsampled)
+    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    alu_peak = SMS * SMSP_PER_SM * LANES * clk * 1e6 / 1e12          # T instr/s
+    instr = ALG_INSTR_PER_UPDATE[args.sincos]
+    alu_achieved = instr * updates_per_launch / avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tinstr/s",
+                "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(),
+                "kernel": names[kern], "kernel_avg_us": avg_s * 1e6,
+                "algorithmic_instr_per_update": instr,
+                "peak_basis": f"{SMS} SMs x {SMSP_PER_SM} schedulers x {LANES} lanes x {clk:.0f} MHz",
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": alg_bytes},
                 "kernel_timing": f"CUDA events around the launches of every {TIMING_EVERY}th "
                                  "sweep inside the timed region",
-                "kernel_times_ms": {"red": kt[0][0] / max(kt[0][1], 1),
-                                    "black": kt[1][0] / max(kt[1][1], 1)}}
-
+                "kernel_avg_ms": {names[k]: kt[k][0] / max(kt[k][1], 1)
+                                  for k in range(len(names))}}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nthreads = os.cpu_count() or 1
@@ -333,7 +358,7 @@ def run_ours(args):
                "sample": f"{n} sweeps of L={w.L} from the seed-{w.seed} hot start "
                          f"({dt:.1f} s), OpenMP over the sites of one colour"}
 
-    launches = args.steps * (1 + 2 * w.sweeps)
+    launches = args.steps * (1 + (1 if fused else 2) * w.sweeps)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -341,6 +366,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
                    "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "fp64",
+                   "kernel": "fused single-pass" if fused else "two-pass red/black",
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -58,7 +58,17 @@ typedef enum {
 } xy_status;
 
 enum { XY_START_HOT = 0, XY_START_COLD = 1 };
-enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1 };
+/* Precision of the per-site unit vectors and Boltzmann factors (all FP32):
+ *   XY_SINCOS_ACCURATE  own Cody-Waite + Taylor sincos (<= 1 ulp-class) and expf;
+ *   XY_SINCOS_FAST      the SFU intrinsics __sincosf / __expf;
+ *   XY_SINCOS_LIBM      CUDA's sincosf / expf. */
+enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
+/* Sweep kernel: AUTO picks FUSED when L is a multiple of 128, else TWO_PASS.
+ *   XY_ALGO_FUSED     one launch per sweep (both colours + measure), the state
+ *                     ping-pongs between the caller's buffer and a library
+ *                     buffer of the same size (8 B moved per update);
+ *   XY_ALGO_TWO_PASS  one launch per colour, in place (12 B per update). */
+enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2 };
 enum { XY_REDUCE_FP64 = 0, XY_REDUCE_COMPENSATED = 1 };
 
 /* Largest supported side (N = L^2 must fit the 32-bit site counter and the
@@ -72,10 +82,10 @@ typedef struct {
     double J;             /* coupling (1 in the paper's model)                  */
     double delta;         /* proposal half-window, 0 < delta <= pi              */
     uint64_t seed;        /* Philox key                                         */
-    int32_t sincos_mode;  /* XY_SINCOS_ACCURATE (sincosf/expf) or _FAST         */
+    int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM                 */
     int32_t reduce_mode;  /* XY_REDUCE_FP64 or XY_REDUCE_COMPENSATED            */
     uint32_t lattice_id;  /* third Philox counter word                          */
-    uint32_t reserved;    /* must be 0                                          */
+    int32_t algorithm;    /* XY_ALGO_AUTO, _FUSED (needs L % 128 == 0), _TWO_PASS */
 } xy_params;
 
 /* Per-sweep record as stored on the device (64 bytes).  The five sums are
@@ -111,7 +121,8 @@ typedef struct {
  *   cuda_stream a cudaStream_t, or NULL for the legacy default stream.
  *   d_angles   NULL: the library allocates the L*L float working buffer;
  *              else a caller-owned device buffer of >= L*L floats, 16-byte
- *              aligned, used in the split layout (never freed here).
+ *              aligned, used in the split layout (never freed here).  The
+ *              fused kernel also allocates a second L*L float buffer.
  *   out        receives the context (NULL on failure).
  * Errors: XY_EINVAL, XY_ENOMEM, XY_ECUDA (see xy_last_error(NULL)). */
 xy_status xy_create(const xy_params *p, void *cuda_stream, void *d_angles, xy_ctx **out);
@@ -126,7 +137,8 @@ xy_status xy_reserve(xy_ctx *ctx, int64_t n_more);
 
 /* Enqueue n >= 0 sweeps (red half then black half with the fused measure);
  * appends n records.  Asynchronous.  Fails with XY_EINVAL if the sweep
- * counter would pass 2^32. */
+ * counter would pass 2^32.  With the fused kernel the state is back in the
+ * caller's buffer when the call returns (an odd n costs one device copy). */
 xy_status xy_sweep(xy_ctx *ctx, int64_t n_sweeps);
 
 /* Copy records [first, first + count) to host_out (count >= 0 entries) and
@@ -177,6 +189,12 @@ const char *xy_last_error(const xy_ctx *ctx);
  * the same device generator the sweeps use (for bit-exact checks). */
 xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, uint32_t domain,
                           uint32_t first, int64_t n, uint32_t *d_out, void *cuda_stream);
+
+/* Unit vectors (cos, sin) of n device angles with the sweep kernels' own
+ * sincos of precision `sincos_mode` (accuracy checks against CUDA and FP64):
+ * d_theta, d_cos, d_sin are device arrays of n floats; runs on cuda_stream. */
+xy_status xy_eval_unit_vector(int32_t sincos_mode, const float *d_theta, float *d_cos,
+                              float *d_sin, int64_t n, void *cuda_stream);
 
 /* ABI version (major * 100 + minor). */
 int32_t xy_version(void);

@@ -15,7 +15,8 @@ XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_ESTATE, XY_ENUMERIC = ran
 STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "XY_ETIMEOUT",
                 5: "XY_ESTATE", 6: "XY_ENUMERIC"}
 XY_START_HOT, XY_START_COLD = 0, 1
-XY_SINCOS_ACCURATE, XY_SINCOS_FAST = 0, 1
+XY_SINCOS_ACCURATE, XY_SINCOS_FAST, XY_SINCOS_LIBM = 0, 1, 2
+XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS = 0, 1, 2
 XY_REDUCE_FP64, XY_REDUCE_COMPENSATED = 0, 1
 XY_FX_SHIFT = 30
 XY_MAX_L = 32768
@@ -30,7 +31,7 @@ class XYError(RuntimeError):
 class xy_params(C.Structure):
     _fields_ = [("L", C.c_int32), ("start", C.c_int32), ("beta", C.c_double), ("J", C.c_double),
                 ("delta", C.c_double), ("seed", C.c_uint64), ("sincos_mode", C.c_int32),
-                ("reduce_mode", C.c_int32), ("lattice_id", C.c_uint32), ("reserved", C.c_uint32)]
+                ("reduce_mode", C.c_int32), ("lattice_id", C.c_uint32), ("algorithm", C.c_int32)]
 
 
 class xy_record(C.Structure):
@@ -77,6 +78,7 @@ def lib():
         "xy_philox_words": (st, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                  C.c_int64, P, P]),
         "xy_version": (C.c_int32, []),
+        "xy_eval_unit_vector": (st, [C.c_int32, P, P, P, C.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -173,6 +175,10 @@ def xy_last_error(ctx=None):
 
 def xy_philox_words(seed, sweep, lattice_id, domain, first, n, d_out_ptr, stream_ptr=None):
     check(lib().xy_philox_words(seed, sweep, lattice_id, domain, first, n, d_out_ptr, stream_ptr))
+
+
+def xy_eval_unit_vector(mode, d_theta_ptr, d_cos_ptr, d_sin_ptr, n, stream_ptr=None):
+    check(lib().xy_eval_unit_vector(mode, d_theta_ptr, d_cos_ptr, d_sin_ptr, n, stream_ptr))
 
 
 def xy_version():

@@ -56,8 +56,10 @@ struct xy_ctx {
   xy_params p;
   cudaStream_t stream;
   int device;
-  float* d_theta;          // [2][L][L/2]
+  float* d_theta;          // [2][L][L/2]: the state between calls
   bool owns_theta;
+  float* d_pong;           // second buffer of the fused kernel (library-owned)
+  bool fused;              // sweeps use the fused kernel
   xy_record* d_rec;        // records [0, rec_cap)
   int64_t rec_cap;
   int64_t rec_count;       // records enqueued so far
@@ -140,7 +142,8 @@ xy_status validate(const xy_params* p) {
     set_thread_msg("start must be XY_START_HOT or XY_START_COLD");
     return XY_EINVAL;
   }
-  if (p->sincos_mode != XY_SINCOS_ACCURATE && p->sincos_mode != XY_SINCOS_FAST) {
+  if (p->sincos_mode != XY_SINCOS_ACCURATE && p->sincos_mode != XY_SINCOS_FAST &&
+      p->sincos_mode != XY_SINCOS_LIBM) {
     set_thread_msg("bad sincos_mode");
     return XY_EINVAL;
   }
@@ -148,8 +151,13 @@ xy_status validate(const xy_params* p) {
     set_thread_msg("bad reduce_mode");
     return XY_EINVAL;
   }
-  if (p->reserved != 0) {
-    set_thread_msg("reserved must be 0");
+  if (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
+      p->algorithm != XY_ALGO_TWO_PASS) {
+    set_thread_msg("bad algorithm");
+    return XY_EINVAL;
+  }
+  if (p->algorithm == XY_ALGO_FUSED && !xyk::fused_supported(p->L)) {
+    set_thread_msg("the fused kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
   }
   return XY_OK;
@@ -203,9 +211,15 @@ cudaError_t timed_half_sweep(xy_ctx* c, int colour, const xyk::HalfSweepArgs& a)
   return e;
 }
 
-void split_key(uint64_t seed, uint32_t* k0, uint32_t* k1) {
-  *k0 = (uint32_t)(seed & 0xffffffffu);
-  *k1 = (uint32_t)(seed >> 32);
+cudaError_t timed_fused(xy_ctx* c, const xyk::FusedArgs& a) {
+  if (c->timing_every <= 0 || (a.sweep % (uint32_t)c->timing_every) != 0)
+    return xyk::launch_fused_sweep(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  cudaEvent_t e0, e1;
+  cudaError_t e = next_events(c, 0, &e0, &e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess) e = xyk::launch_fused_sweep(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  return e;
 }
 
 void release(xy_ctx* c) {
@@ -216,10 +230,12 @@ void release(xy_ctx* c) {
   }
   if (c->owns_theta && c->d_theta) cudaFree(c->d_theta);
   if (c->d_rec) cudaFree(c->d_rec);
+  if (c->d_pong) cudaFree(c->d_pong);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_flag) cudaFree(c->d_flag);
   c->d_theta = nullptr;
   c->d_rec = nullptr;
+  c->d_pong = nullptr;
   c->d_scratch = nullptr;
   c->d_flag = nullptr;
 }
@@ -228,7 +244,7 @@ void release(xy_ctx* c) {
 
 extern "C" {
 
-int32_t xy_version(void) { return 100; }
+int32_t xy_version(void) { return 101; }
 
 const char* xy_last_error(const xy_ctx* ctx) {
   if (ctx && is_live(ctx) && ctx->magic == kMagicLive && ctx->sticky != XY_OK) return ctx->msg;
@@ -269,6 +285,9 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
     }
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(unsigned int));
+  c->fused = p->algorithm == XY_ALGO_FUSED ||
+             (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
+  if (e == cudaSuccess && c->fused) e = cudaMalloc(&c->d_pong, N * sizeof(float));
   if (e != cudaSuccess) {
     st = (e == cudaErrorMemoryAllocation) ? XY_ENOMEM : XY_ECUDA;
     set_thread_msg("xy_create: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -277,10 +296,8 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
     delete c;
     return st;
   }
-  uint32_t k0, k1;
-  split_key(p->seed, &k0, &k1);
-  e = xyk::launch_start(c->d_theta, p->L, k0, k1, p->lattice_id, p->start == XY_START_HOT,
-                        c->stream);
+  e = xyk::launch_start(c->d_theta, p->L, xyd::make_round_keys(p->seed), p->lattice_id,
+                        p->start == XY_START_HOT, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     set_thread_msg("xy_create: start kernel: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -299,9 +316,7 @@ xy_status xy_reset(xy_ctx* c, uint64_t seed) {
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
   c->p.seed = seed;
-  uint32_t k0, k1;
-  split_key(seed, &k0, &k1);
-  XY_CUDA(c, xyk::launch_start(c->d_theta, c->p.L, k0, k1, c->p.lattice_id,
+  XY_CUDA(c, xyk::launch_start(c->d_theta, c->p.L, xyd::make_round_keys(seed), c->p.lattice_id,
                                c->p.start == XY_START_HOT, c->stream),
           "xy_reset: start kernel");
   if (c->d_rec && c->rec_count > 0)
@@ -355,21 +370,51 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     return fail(c, XY_EINVAL, "xy_sweep: sweep counter would pass 2^32 - 1");
   st = grow_records(c, c->rec_count + n);
   if (st != XY_OK) return st;
-  xyk::HalfSweepArgs a;
-  a.theta = c->d_theta;
-  a.L = c->p.L;
-  a.W = c->p.L / 2;
-  a.K = (float)(c->p.beta * c->p.J);
-  a.delta = (float)c->p.delta;
-  split_key(c->p.seed, &a.key0, &a.key1);
-  a.lattice_id = c->p.lattice_id;
-  a.beta = c->p.beta;
-  for (int64_t i = 0; i < n; ++i) {
-    a.sweep = (uint32_t)(c->next_sweep + (uint64_t)i);
-    a.rec = c->d_rec + c->rec_count + i;
-    cudaError_t e = timed_half_sweep(c, 0, a);
-    if (e == cudaSuccess) e = timed_half_sweep(c, 1, a);
-    if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: launch");
+  const xyd::RoundKeys rk = xyd::make_round_keys(c->p.seed);
+  if (c->fused) {
+    xyk::FusedArgs a;
+    a.L = c->p.L;
+    a.W = c->p.L / 2;
+    a.K = (float)(c->p.beta * c->p.J);
+    a.delta = (float)c->p.delta;
+    a.rk = rk;
+    a.lattice_id = c->p.lattice_id;
+    a.beta = c->p.beta;
+    float* cur = c->d_theta;
+    float* nxt = c->d_pong;
+    for (int64_t i = 0; i < n; ++i) {
+      a.src = cur;
+      a.dst = nxt;
+      a.sweep = (uint32_t)(c->next_sweep + (uint64_t)i);
+      a.rec = c->d_rec + c->rec_count + i;
+      cudaError_t e = timed_fused(c, a);
+      if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: fused launch");
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    if (cur != c->d_theta) {
+      const size_t bytes = (size_t)c->p.L * (size_t)c->p.L * sizeof(float);
+      XY_CUDA(c, cudaMemcpyAsync(c->d_theta, cur, bytes, cudaMemcpyDeviceToDevice, c->stream),
+              "xy_sweep: copy back");
+    }
+  } else {
+    xyk::HalfSweepArgs a;
+    a.theta = c->d_theta;
+    a.L = c->p.L;
+    a.W = c->p.L / 2;
+    a.K = (float)(c->p.beta * c->p.J);
+    a.delta = (float)c->p.delta;
+    a.rk = rk;
+    a.lattice_id = c->p.lattice_id;
+    a.beta = c->p.beta;
+    for (int64_t i = 0; i < n; ++i) {
+      a.sweep = (uint32_t)(c->next_sweep + (uint64_t)i);
+      a.rec = c->d_rec + c->rec_count + i;
+      cudaError_t e = timed_half_sweep(c, 0, a);
+      if (e == cudaSuccess) e = timed_half_sweep(c, 1, a);
+      if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: launch");
+    }
   }
   c->next_sweep += (uint64_t)n;
   c->rec_count += n;
@@ -513,15 +558,29 @@ xy_status xy_destroy(xy_ctx* c) {
   return XY_OK;
 }
 
+xy_status xy_eval_unit_vector(int32_t sincos_mode, const float* d_theta, float* d_cos,
+                              float* d_sin, int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!d_theta || !d_cos || !d_sin)) || sincos_mode < 0 || sincos_mode > 2) {
+    set_thread_msg("xy_eval_unit_vector: bad arguments");
+    return XY_EINVAL;
+  }
+  cudaError_t e = xyk::launch_eval_unit_vector(sincos_mode, d_theta, d_cos, d_sin, n,
+                                               reinterpret_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) {
+    set_thread_msg("xy_eval_unit_vector: %s", cudaGetErrorString(e));
+    return XY_ECUDA;
+  }
+  return XY_OK;
+}
+
 xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, uint32_t domain,
                           uint32_t first, int64_t n, uint32_t* d_out, void* cuda_stream) {
   if (n < 0 || (n > 0 && !d_out)) {
     set_thread_msg("xy_philox_words: bad arguments");
     return XY_EINVAL;
   }
-  uint32_t k0, k1;
-  split_key(seed, &k0, &k1);
-  cudaError_t e = xyk::launch_philox_words(k0, k1, sweep, lattice_id, domain, first, n, d_out,
+  cudaError_t e = xyk::launch_philox_words(xyd::make_round_keys(seed), sweep, lattice_id, domain,
+                                           first, n, d_out,
                                            reinterpret_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) {
     set_thread_msg("xy_philox_words: %s", cudaGetErrorString(e));

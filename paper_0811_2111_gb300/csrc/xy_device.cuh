@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "xy.h"
+
 namespace xyd {
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
@@ -17,16 +19,40 @@ constexpr uint32_t kMulB = 0xCD9E8D57u;
 constexpr uint32_t kWeylA = 0x9E3779B9u;
 constexpr uint32_t kWeylB = 0xBB67AE85u;
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int round = 0; round < 10; ++round) {
-    const uint32_t hi_a = __umulhi(kMulA, x.x);
-    const uint32_t lo_a = kMulA * x.x;
-    const uint32_t hi_b = __umulhi(kMulB, x.z);
-    const uint32_t lo_b = kMulB * x.z;
-    x = make_uint4(hi_b ^ x.y ^ k0, lo_b, hi_a ^ x.w ^ k1, lo_a);
+// 32x32 -> 64-bit product as one wide multiply.
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t* hi, uint32_t* lo) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+  *hi = (uint32_t)(p >> 32);
+  *lo = (uint32_t)p;
+}
+
+// The ten round keys of one seed, (k0 + r * kWeylA, k1 + r * kWeylB), computed
+// on the host and passed as kernel arguments so the xors read them directly.
+struct RoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
     k0 += kWeylA;
     k1 += kWeylB;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, const RoundKeys& rk) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    uint32_t hi_a, lo_a, hi_b, lo_b;
+    mul_wide(kMulA, x.x, &hi_a, &lo_a);
+    mul_wide(kMulB, x.z, &hi_b, &lo_b);
+    x = make_uint4(hi_b ^ x.y ^ rk.k0[round], lo_b, hi_a ^ x.w ^ rk.k1[round], lo_a);
   }
   return x;
 }
@@ -43,23 +69,6 @@ __device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * kU24
 // 2 u24(w) - 1 = ((w >> 8) - 2^23) / 2^23, exact in FP32, in [-1, 1).
 __device__ __forceinline__ float sym24(uint32_t w) {
   return (float)((int32_t)(w >> 8) - 8388608) * kR23;
-}
-
-// Precision switch: MODE 0 = CUDA's accurate sincosf/expf, MODE 1 = the
-// SFU intrinsics __sincosf/__expf.
-template <int MODE>
-__device__ __forceinline__ void sincos_m(float t, float* s, float* c) {
-  if (MODE == 0) {
-    sincosf(t, s, c);
-  } else {
-    __sincosf(t, s, c);
-  }
-}
-
-template <int MODE>
-__device__ __forceinline__ float exp_m(float x) {
-  if (MODE == 0) return expf(x);
-  return __expf(x);
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -84,6 +93,187 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
   while (v < 0) v += n;
   while (v >= n) v -= n;
   return v;
+}
+
+}  // namespace xyd
+
+namespace xyd {
+
+// Unit vector of an angle in [0, 2 pi] (or a little outside), written from the
+// mathematics: Cody-Waite reduction by pi/2 (W. J. Cody, W. Waite, "Software
+// Manual for the Elementary Functions", 1980) with a two-part constant whose
+// high part has three trailing zero bits (so q * hi is exact for |q| <= 7),
+// then the Taylor series of sin (to r^9) and cos (to r^10) on |r| <= pi/4,
+// whose truncation errors (< 2e-9 and < 2e-10) are far below FP32 rounding,
+// and the quadrant identities sin(r + q pi/2), cos(r + q pi/2).
+constexpr float kTwoOverPi = 0.636619772367581343f;
+constexpr float kPio2Hi = 1.57079601287841796875f;       // pi/2 with 21 significant bits
+constexpr float kPio2Lo = 3.13916473532088954e-07f;      // pi/2 - kPio2Hi
+constexpr float kRoundMagic = 12582912.0f;               // 1.5 * 2^23: x + M - M = rint(x)
+
+__device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out) {
+  const float qt = __fmaf_rn(t, kTwoOverPi, kRoundMagic);
+  const int q = __float_as_int(qt);                       // low bits = rint(t * 2/pi)
+  const float qf = __fsub_rn(qt, kRoundMagic);
+  float r = __fmaf_rn(-qf, kPio2Hi, t);                   // exact
+  r = __fmaf_rn(-qf, kPio2Lo, r);
+  const float r2 = __fmul_rn(r, r);
+  // sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!)))
+  float ps = __fmaf_rn(r2, 2.75573192239858907e-06f, -1.98412698412698413e-04f);
+  ps = __fmaf_rn(r2, ps, 8.33333333333333333e-03f);
+  ps = __fmaf_rn(r2, ps, -1.66666666666666667e-01f);
+  const float sr = __fmaf_rn(__fmul_rn(r, r2), ps, r);
+  // cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!))))
+  float pc = __fmaf_rn(r2, -2.75573192239858907e-07f, 2.48015873015873016e-05f);
+  pc = __fmaf_rn(r2, pc, -1.38888888888888889e-03f);
+  pc = __fmaf_rn(r2, pc, 4.16666666666666667e-02f);
+  pc = __fmaf_rn(r2, pc, -0.5f);
+  const float cr = __fmaf_rn(r2, pc, 1.0f);
+  // quadrant: odd q swaps sin and cos; sin negative for q mod 4 in {2, 3},
+  // cos negative for q mod 4 in {1, 2}
+  const bool swap = (q & 1) != 0;
+  const float s0 = swap ? cr : sr;
+  const float c0 = swap ? sr : cr;
+  *s_out = __int_as_float(__float_as_int(s0) ^ ((q & 2) << 30));
+  *c_out = __int_as_float(__float_as_int(c0) ^ (((q + 1) & 2) << 30));
+}
+
+// Precision switch of the fused kernels: 0 = the polynomial above with CUDA's
+// expf, 1 = the SFU intrinsics __sincosf/__expf, 2 = CUDA's sincosf/expf.
+template <int MODE>
+__device__ __forceinline__ void unit_vector(float t, float* s, float* c) {
+  if (MODE == 0) {
+    sincos_poly(t, s, c);
+  } else if (MODE == 1) {
+    __sincosf(t, s, c);
+  } else {
+    sincosf(t, s, c);
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ float boltzmann(float x) {
+  if (MODE == 1) return __expf(x);
+  return expf(x);
+}
+
+// Sum of the four neighbour components in one fixed order.
+__device__ __forceinline__ float nb_sum(float l, float r, float d, float u) {
+  return __fadd_rn(__fadd_rn(l, r), __fadd_rn(d, u));
+}
+
+// Per-site contributions of a black site b (unit vector (cb, sb)) to the
+// sweep sums, from its four red neighbours (left l, right r, down d, up u)
+// and the red site (cm, sm) that shares its (y, k) index:
+//   v0 = sum_4 cos(t_b - t_j)                 (its four bonds of C)
+//   v1 = sin(t_b - t_r) - sin(t_b - t_l)      (its two x bonds of Ix)
+//   v2 = sin(t_b - t_u) - sin(t_b - t_d)      (its two y bonds of Iy)
+//   v3, v4 = cb + cm, sb + sm                 (M of both sites)
+__device__ __forceinline__ void measure_terms(float cb, float sb, float cl, float sl, float cr,
+                                              float sr, float cd, float sd, float cu, float su,
+                                              float Sc, float Ss, float cm, float sm,
+                                              float v[5]) {
+  v[0] = __fmaf_rn(cb, Sc, __fmul_rn(sb, Ss));
+  v[1] = __fmaf_rn(sb, __fsub_rn(cr, cl), -__fmul_rn(cb, __fsub_rn(sr, sl)));
+  v[2] = __fmaf_rn(sb, __fsub_rn(cu, cd), -__fmul_rn(cb, __fsub_rn(su, sd)));
+  v[3] = __fadd_rn(cb, cm);
+  v[4] = __fadd_rn(sb, sm);
+}
+
+struct SiteResult {
+  float th, c, s;
+  bool accept;
+};
+
+// One Metropolis step of a site with angle t, unit vector (c0, s0) and
+// neighbour sum (Sc, Ss), from its Philox words w0 (proposal) and w1
+// (accept).  Rounding is pinned with explicit intrinsics so every kernel that
+// calls this gets bit-identical decisions.  The select is the per-site vector
+// accept of Sec. 3.2: new = z * proposal + (1 - z) * old.
+template <int MODE>
+__device__ __forceinline__ SiteResult metropolis_step(float t, float c0, float s0, float Sc,
+                                                      float Ss, uint32_t w0, uint32_t w1,
+                                                      float K, float delta) {
+  float tp = __fmaf_rn(delta, sym24(w0), t);
+  if (tp < 0.f) {
+    tp = __fadd_rn(tp, kTwoPi);
+  } else if (tp >= kTwoPi) {
+    tp = __fsub_rn(tp, kTwoPi);
+  }
+  float s1, c1;
+  unit_vector<MODE>(tp, &s1, &c1);
+  // X = -dE / J = (cos t' - cos t) Sc + (sin t' - sin t) Ss
+  const float X = __fmaf_rn(__fsub_rn(c1, c0), Sc, __fmul_rn(__fsub_rn(s1, s0), Ss));
+  const bool acc = u24(w1) < boltzmann<MODE>(__fmul_rn(K, X));
+  SiteResult r;
+  r.th = acc ? tp : t;
+  r.c = acc ? c1 : c0;
+  r.s = acc ? s1 : s0;
+  r.accept = acc;
+  return r;
+}
+
+}  // namespace xyd
+
+namespace xyd {
+
+// End-of-CTA reduction shared by the sweep kernels: per-thread FP32 partials
+// (or Neumaier pairs when RED == 1) -> warp shuffle -> FP64 over the CTA's
+// warps (compensated FP32 when RED == 1) -> exact fixed-point atomics into the
+// record.  `part` holds [warps][5][2] floats and `cnt` [warps] counters in
+// shared memory.  Must be reached by every thread of the CTA.
+template <int NWARPS, int RED, bool MEASURE>
+__device__ __forceinline__ void commit_block(float acc[5], float cmp[5], unsigned int n_acc,
+                                             float (*part)[5][2], unsigned int* cnt,
+                                             xy_record* rec, double beta, bool first_block) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned int warp_acc = __reduce_add_sync(0xffffffffu, n_acc);
+  if (MEASURE) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      acc[i] = warp_sum(acc[i]);
+      if (RED == 1) cmp[i] = warp_sum(cmp[i]);
+    }
+  }
+  if (lane == 0) {
+    cnt[warp] = warp_acc;
+    if (MEASURE) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        part[warp][i][0] = acc[i];
+        part[warp][i][1] = (RED == 1) ? cmp[i] : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  if (lane == 0) {
+    unsigned long long total = 0;
+    for (int w = 0; w < NWARPS; ++w) total += cnt[w];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&rec->accepted), total);
+    if (MEASURE && first_block) rec->beta = beta;
+  }
+  if (!MEASURE || lane >= 5) return;
+  // lanes 0..4 each own one of the five sums
+  double d;
+  if (RED == 0) {
+    d = 0.0;
+    for (int w = 0; w < NWARPS; ++w) d += (double)part[w][lane][0];
+  } else {
+    float hi = 0.f, lo = 0.f;
+    for (int w = 0; w < NWARPS; ++w) {
+      neumaier_add(hi, lo, part[w][lane][0]);
+      lo += part[w][lane][1];
+    }
+    d = (double)hi + (double)lo;
+  }
+  const double scaled = d * (double)(1ll << XY_FX_SHIFT);
+  if (!(fabs(scaled) < 9.0e18)) {
+    atomicOr(reinterpret_cast<unsigned long long*>(&rec->flags), 1ull);
+    return;
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(&rec->sum[lane]),
+            (unsigned long long)__double2ll_rn(scaled));
 }
 
 }  // namespace xyd

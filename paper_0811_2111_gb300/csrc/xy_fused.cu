@@ -1,0 +1,307 @@
+// xy_fused.cu -- one-launch checkerboard sweep (red half, black half and the
+// fused measure) reading the lattice from `src` and writing it to `dst`.
+//
+// Each CTA owns a tile of 32 rows x 64 plane columns (128 natural columns) of
+// both colours.  It stages both planes of the tile plus a halo of two rows and
+// one plane column into shared memory as (angle, cos, sin), then
+//   1. updates the red sites of the tile and of the ring at distance one
+//      around it (the ring sites belong to neighbouring tiles; they are
+//      recomputed here from the same old state and the same counter-based
+//      Philox words, so every copy makes the identical decision),
+//   2. updates the black sites of the tile against the new red values,
+//   3. accumulates the sweep sums over the tile's bonds and spins,
+// and writes the tile's new angles to `dst`.  Reading the old state from a
+// separate buffer is what lets one CTA use its neighbours' old angles while
+// those neighbours write their new ones (the ping-pong of the paper's GL
+// implementation, Sec. 3.1, applied to whole sweeps).
+//
+// Compared with the two-pass kernels each angle is read once and written once
+// per sweep (8 B per update instead of 12 B) and each site's unit vector is
+// computed once per sweep instead of once per half-sweep.
+//
+// Requires W = L/2 to be a multiple of 64 and L a multiple of 32 (L % 128 == 0).
+// Decisions are bit-identical to the two-pass kernels: both call the same
+// xyd::unit_vector / xyd::nb_sum / xyd::metropolis_step with pinned rounding.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xy_device.cuh"
+#include "xy_internal.h"
+
+namespace xyk {
+
+namespace {
+
+constexpr int kTileRows = 32;
+constexpr int kTileK = 64;                   // plane columns (2 per lane)
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kSRows = kTileRows + 4;        // rows y0-2 .. y0+33
+constexpr int kSCols = kTileK + 8;           // plane cols k0-4 .. k0+67 (k0-1 .. k0+64 used)
+constexpr int kBodyGroups = kTileK / 4;      // float4 groups of the tile columns
+constexpr int kStageItems = kBodyGroups + 1; // + one item for the two halo columns
+constexpr int kRing = 2 * kTileK + kTileRows;
+
+constexpr size_t kThBytes = sizeof(float) * 2 * kSRows * kSCols;
+constexpr size_t kCsBytes = sizeof(float2) * 2 * kSRows * kSCols;
+constexpr size_t kPartBytes = sizeof(float) * kWarps * 5 * 2;
+constexpr size_t kCntBytes = sizeof(unsigned int) * kWarps;
+constexpr size_t kSmemBytes = kThBytes + kCsBytes + kPartBytes + kCntBytes;
+
+typedef float ThArr[kSRows][kSCols];
+typedef float2 CsArr[kSRows][kSCols];
+
+__device__ __forceinline__ int wrap_once(int v, int n) {
+  v += (v < 0) ? n : 0;
+  v -= (v >= n) ? n : 0;
+  return v;
+}
+
+// The four neighbour unit vectors of the two sites at stage columns c0, c0+1
+// of row r in plane `nb` (the other colour), where a site at column c has its
+// same-row neighbours at c+q-1 and c+q.  A = (c0, c0+1) as one 16-byte load.
+struct PairNeighbours {
+  float Sc[2], Ss[2];
+  float2 l[2], r[2], d[2], u[2];
+};
+
+__device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, int q,
+                                                PairNeighbours& n) {
+  const float4 A = *reinterpret_cast<const float4*>(&nb[r][c0]);
+  const float2 extra = nb[r][q ? c0 + 2 : c0 - 1];
+  const float4 D = *reinterpret_cast<const float4*>(&nb[r - 1][c0]);
+  const float4 U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
+  const float2 a0 = make_float2(A.x, A.y), a1 = make_float2(A.z, A.w);
+  n.l[0] = q ? a0 : extra;
+  n.r[0] = q ? a1 : a0;
+  n.l[1] = q ? a1 : a0;
+  n.r[1] = q ? extra : a1;
+  n.d[0] = make_float2(D.x, D.y);
+  n.d[1] = make_float2(D.z, D.w);
+  n.u[0] = make_float2(U.x, U.y);
+  n.u[1] = make_float2(U.z, U.w);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    n.Sc[j] = xyd::nb_sum(n.l[j].x, n.r[j].x, n.d[j].x, n.u[j].x);
+    n.Ss[j] = xyd::nb_sum(n.l[j].y, n.r[j].y, n.d[j].y, n.u[j].y);
+  }
+}
+
+// One ring site (red, stage (r, c)): same arithmetic as the tile sites.
+template <int MODE>
+__device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c, int q,
+                                              uint32_t site, const FusedArgs& a) {
+  const float2 l = cs[1][r][c + q - 1], rt = cs[1][r][c + q];
+  const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
+  const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+  const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+  const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.rk);
+  const float2 own = cs[0][r][c];
+  const xyd::SiteResult res =
+      xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, w.x, w.y, a.K, a.delta);
+  th[0][r][c] = res.th;
+  cs[0][r][c] = make_float2(res.c, res.s);
+}
+
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  ThArr* th = reinterpret_cast<ThArr*>(smem);
+  CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + kThBytes + kCsBytes);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kThBytes + kCsBytes + kPartBytes);
+
+  const int L = a.L, W = a.W;
+  const int k0 = blockIdx.x * kTileK;
+  const int y0 = blockIdx.y * kTileRows;
+  const size_t plane = (size_t)L * (size_t)W;
+
+  // ---- stage both planes (angle + unit vector) ----
+  // items: (plane, row, group); groups 0..15 are the tile's float4 columns,
+  // group 16 the two halo columns k0-1 and k0+64 (rows 1..34 only).  All of a
+  // thread's loads are issued before any of its sincos so that their latencies
+  // overlap instead of adding up.
+  constexpr int kItems = 2 * kSRows * kStageItems;
+  constexpr int kPerThread = (kItems + kThreads - 1) / kThreads;
+  float4 v[kPerThread];
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const int g = threadIdx.x + i * kThreads;
+    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g >= kItems) continue;
+    const int p = g / (kSRows * kStageItems);
+    const int rem = g - p * (kSRows * kStageItems);
+    const int r = rem / kStageItems;
+    const int cg = rem - r * kStageItems;
+    if (p == 0 && (r == 0 || r == kSRows - 1)) continue;   // red is never needed 2 rows out
+    const float* row = a.src + p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
+    if (cg < kBodyGroups) {
+      v[i] = __ldg(reinterpret_cast<const float4*>(row + k0 + 4 * cg));
+    } else if (r >= 1 && r <= kSRows - 2) {
+      v[i].x = __ldg(row + wrap_once(k0 - 1, W));
+      v[i].y = __ldg(row + wrap_once(k0 + kTileK, W));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const int g = threadIdx.x + i * kThreads;
+    if (g >= kItems) continue;
+    const int p = g / (kSRows * kStageItems);
+    const int rem = g - p * (kSRows * kStageItems);
+    const int r = rem / kStageItems;
+    const int cg = rem - r * kStageItems;
+    if (p == 0 && (r == 0 || r == kSRows - 1)) continue;
+    if (cg < kBodyGroups) {
+      const int col = 4 + 4 * cg;
+      float s0, c0, s1, c1, s2, c2, s3, c3;
+      xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
+      xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
+      xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
+      xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+      *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
+      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+    } else if (r >= 1 && r <= kSRows - 2) {
+      float s, c;
+      xyd::unit_vector<MODE>(v[i].x, &s, &c);
+      th[p][r][3] = v[i].x;
+      cs[p][r][3] = make_float2(c, s);
+      xyd::unit_vector<MODE>(v[i].y, &s, &c);
+      th[p][r][kTileK + 4] = v[i].y;
+      cs[p][r][kTileK + 4] = make_float2(c, s);
+    }
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t uL = (uint32_t)L;
+  const int c0 = 2 * lane + 4;                             // stage column of the lane's pair
+  const int kp = k0 + 2 * lane;                            // plane column of the pair
+  unsigned int n_acc = 0;
+
+  // ---- red half: the tile (counted, written to dst) ----
+#pragma unroll 2
+  for (int rr = 0; rr < 4; ++rr) {
+    const int ty = warp * 4 + rr;
+    const int y = y0 + ty;
+    const int r = ty + 2;
+    const int q = y & 1;                                   // red: x = 2k + (y & 1)
+    PairNeighbours n;
+    pair_neighbours(cs[1], r, c0, q, n);
+    const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), a.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, a.K, a.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, a.K, a.delta);
+    n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
+    *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
+    *reinterpret_cast<float2*>(a.dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
+  }
+  // ---- red half: the ring at distance one (recomputed, not counted) ----
+  for (int i = threadIdx.x; i < kRing; i += kThreads) {
+    int ty, tk;
+    if (i < kTileK) {
+      ty = -1;
+      tk = i;
+    } else if (i < 2 * kTileK) {
+      ty = kTileRows;
+      tk = i - kTileK;
+    } else {
+      ty = i - 2 * kTileK;
+      tk = ((y0 + ty) & 1) ? -1 : kTileK;                  // left ring on odd rows, right on even
+    }
+    const int y = wrap_once(y0 + ty, L);
+    const int k = wrap_once(k0 + tk, W);
+    const int q = y & 1;
+    const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+    red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a);
+  }
+  __syncthreads();
+
+  // ---- black half of the tile, with the sweep sums ----
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float* dst_blk = a.dst + plane;
+#pragma unroll 2
+  for (int rr = 0; rr < 4; ++rr) {
+    const int ty = warp * 4 + rr;
+    const int y = y0 + ty;
+    const int r = ty + 2;
+    const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
+    PairNeighbours n;
+    pair_neighbours(cs[0], r, c0, q, n);
+    const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), a.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, a.K, a.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, a.K, a.delta);
+    n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+    *reinterpret_cast<float2*>(dst_blk + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
+    // red sites with the same (y, k): their spins enter M once each
+    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    float v0[5], v1[5];
+    xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
+                       n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
+    xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
+                       n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (RED == 0) {
+        acc[i] += v0[i] + v1[i];
+      } else {
+        xyd::neumaier_add(acc[i], cmp[i], v0[i]);
+        xyd::neumaier_add(acc[i], cmp[i], v1[i]);
+      }
+    }
+  }
+
+  xyd::commit_block<kWarps, RED, true>(acc, cmp, n_acc, part, cnt, a.rec, a.beta,
+                                       blockIdx.x == 0 && blockIdx.y == 0);
+}
+
+template <int MODE, int RED>
+cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
+  static bool configured[64] = {};   // attributes set once per instantiation and device
+  int dev = 0;
+  cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) return ge;
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  const dim3 grid(a.W / kTileK, a.L / kTileRows);
+  k_sweep_fused<MODE, RED><<<grid, kThreads, kSmemBytes, stream>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fused_supported(int L) { return L >= 128 && (L % 128) == 0; }
+
+cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
+                               cudaStream_t stream) {
+  if (!fused_supported(a.L)) return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_fused_one<0, 1>(a, stream) : launch_fused_one<0, 0>(a, stream);
+    case 1: return comp ? launch_fused_one<1, 1>(a, stream) : launch_fused_one<1, 0>(a, stream);
+    default: return comp ? launch_fused_one<2, 1>(a, stream) : launch_fused_one<2, 0>(a, stream);
+  }
+}
+
+}  // namespace xyk

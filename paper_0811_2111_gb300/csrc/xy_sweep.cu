@@ -12,8 +12,8 @@
 // turned into its unit vector once per half-sweep and read four times from
 // shared memory.
 //
-// Per site (Metropolis step; the select is the per-site vector accept of
-// Sec. 3.2):
+// Per site (Metropolis step, xyd::metropolis_step; the select is the
+// per-site vector accept of Sec. 3.2):
 //   S     = sum of the four neighbour unit vectors
 //   theta'= wrap(theta + delta (2 u0 - 1))                (Philox word 0)
 //   X     = (cos theta' - cos theta) S_c + (sin theta' - sin theta) S_s
@@ -83,7 +83,7 @@ k_half_sweep(HalfSweepArgs a) {
       // only columns k0-1 .. k0+128 are ever read
       if (col >= 3 && col <= kTileCols + 4) {
         float s, c;
-        xyd::sincos_m<MODE>(v[e], &s, &c);
+        xyd::unit_vector<MODE>(v[e], &s, &c);
         s_cos[r][col] = c;
         s_sin[r][col] = s;
       }
@@ -123,36 +123,23 @@ k_half_sweep(HalfSweepArgs a) {
       const float cr = s_cos[ty + 1][sc + q], sr = s_sin[ty + 1][sc + q];
       const float cd = s_cos[ty][sc], sd = s_sin[ty][sc];
       const float cu = s_cos[ty + 2][sc], su = s_sin[ty + 2][sc];
-      const float Sc = (cl + cr) + (cd + cu);
-      const float Ss = (sl + sr) + (sd + su);
+      const float Sc = xyd::nb_sum(cl, cr, cd, cu);
+      const float Ss = xyd::nb_sum(sl, sr, sd, su);
 
       const uint32_t x = 2u * (uint32_t)(kq + j) + (uint32_t)q;
       const uint32_t site = (uint32_t)y * (uint32_t)L + x;
-      const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.key0,
-                                         a.key1);
+      const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.rk);
       const float t = th[j];
-      float tp = fmaf(a.delta, xyd::sym24(w.x), t);
-      if (tp < 0.f) {
-        tp += xyd::kTwoPi;
-      } else if (tp >= xyd::kTwoPi) {
-        tp -= xyd::kTwoPi;
-      }
-      float s0, c0, s1, c1;
-      xyd::sincos_m<MODE>(t, &s0, &c0);
-      xyd::sincos_m<MODE>(tp, &s1, &c1);
-      const float X = (c1 - c0) * Sc + (s1 - s0) * Ss;
-      const bool accept = xyd::u24(w.y) < xyd::exp_m<MODE>(a.K * X);
-      th[j] = accept ? tp : t;
-      n_acc += accept ? 1u : 0u;
+      float s0, c0;
+      xyd::unit_vector<MODE>(t, &s0, &c0);
+      const xyd::SiteResult res = xyd::metropolis_step<MODE>(t, c0, s0, Sc, Ss, w.x, w.y, a.K,
+                                                             a.delta);
+      th[j] = res.th;
+      n_acc += res.accept ? 1u : 0u;
       if (measure) {
-        const float cb = accept ? c1 : c0, sb = accept ? s1 : s0;
-        const float v[5] = {
-            cb * Sc + sb * Ss,
-            sb * (cr - cl) - cb * (sr - sl),
-            sb * (cu - cd) - cb * (su - sd),
-            cb + s_cos[ty + 1][sc],
-            sb + s_sin[ty + 1][sc],
-        };
+        float v[5];
+        xyd::measure_terms(res.c, res.s, cl, sl, cr, sr, cd, sd, cu, su, Sc, Ss,
+                           s_cos[ty + 1][sc], s_sin[ty + 1][sc], v);
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
           if (RED == 0) {
@@ -172,66 +159,11 @@ k_half_sweep(HalfSweepArgs a) {
     }
   }
 
-  // ---- reductions ----
-  const unsigned int warp_acc = __reduce_add_sync(0xffffffffu, n_acc);
-  if (measure) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (RED == 0) {
-        acc[i] = xyd::warp_sum(acc[i]);
-      } else {
-        // compensated pair: reduce sums and corrections separately
-        acc[i] = xyd::warp_sum(acc[i]);
-        cmp[i] = xyd::warp_sum(cmp[i]);
-      }
-    }
-  }
-  if (lane == 0) {
-    s_cnt[warp] = warp_acc;
-    if (measure) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        s_part[warp][i][0] = acc[i];
-        s_part[warp][i][1] = cmp[i];
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long total = 0;
-    for (int wi = 0; wi < kThreads / 32; ++wi) total += s_cnt[wi];
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec->accepted), total);
-    if (measure) {
-      bool bad = false;
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        double d;
-        if (RED == 0) {
-          d = 0.0;
-          for (int wi = 0; wi < kThreads / 32; ++wi) d += (double)s_part[wi][i][0];
-        } else {
-          float hi = 0.f, lo = 0.f;
-          for (int wi = 0; wi < kThreads / 32; ++wi) {
-            xyd::neumaier_add(hi, lo, s_part[wi][i][0]);
-            lo += s_part[wi][i][1];
-          }
-          d = (double)hi + (double)lo;
-        }
-        const double scaled = d * (double)(1ll << XY_FX_SHIFT);
-        if (!(fabs(scaled) < 9.0e18)) {
-          bad = true;
-          continue;
-        }
-        atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec->sum[i]),
-                  (unsigned long long)__double2ll_rn(scaled));
-      }
-      if (bad) atomicOr(reinterpret_cast<unsigned long long*>(&a.rec->flags), 1ull);
-      if (blockIdx.x == 0 && blockIdx.y == 0) a.rec->beta = a.beta;
-    }
-  }
+  xyd::commit_block<kThreads / 32, RED, COLOUR == 1>(acc, cmp, n_acc, s_part, s_cnt, a.rec, a.beta,
+                                                    blockIdx.x == 0 && blockIdx.y == 0);
 }
 
-__global__ void k_start(float* __restrict__ theta, int L, uint32_t key0, uint32_t key1,
+__global__ void k_start(float* __restrict__ theta, int L, const xyd::RoundKeys rk,
                         uint32_t lattice_id, int hot) {
   const uint32_t N = (uint32_t)L * (uint32_t)L;
   const uint32_t W = (uint32_t)L / 2u;
@@ -243,8 +175,7 @@ __global__ void k_start(float* __restrict__ theta, int L, uint32_t key0, uint32_
     const uint32_t x = 2u * k + ((y + c) & 1u);
     float t = 0.f;
     if (hot) {
-      const uint4 w = xyd::philox4x32_10(make_uint4(y * (uint32_t)L + x, 0u, lattice_id, 0u),
-                                         key0, key1);
+      const uint4 w = xyd::philox4x32_10(make_uint4(y * (uint32_t)L + x, 0u, lattice_id, 0u), rk);
       t = (float)(w.x >> 8) * xyd::kHotScale;
     }
     theta[i] = t;
@@ -257,7 +188,13 @@ __global__ void k_natural_to_split(const float* __restrict__ nat, float* __restr
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
     const uint32_t y = s / (uint32_t)L, x = s - y * (uint32_t)L;
     const uint32_t c = (x + y) & 1u;
-    split[(size_t)c * (N / 2u) + (size_t)y * W + (x >> 1)] = nat[s];
+    // angles are taken modulo 2 pi (in double) so the kernels only see [0, 2 pi)
+    const double two_pi = 6.283185307179586476925;
+    double v = fmod((double)nat[s], two_pi);
+    if (v < 0.0) v += two_pi;
+    float f = (float)v;
+    if (f >= xyd::kTwoPi) f = 0.f;
+    split[(size_t)c * (N / 2u) + (size_t)y * W + (x >> 1)] = f;
   }
 }
 
@@ -271,12 +208,23 @@ __global__ void k_split_to_natural(const float* __restrict__ split, float* __res
   }
 }
 
-__global__ void k_philox_words(uint32_t key0, uint32_t key1, uint32_t sweep, uint32_t lattice_id,
+__global__ void k_philox_words(const xyd::RoundKeys rk, uint32_t sweep, uint32_t lattice_id,
                                uint32_t domain, uint32_t first, int64_t n, uint4* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    out[i] = xyd::philox4x32_10(make_uint4(first + (uint32_t)i, sweep, lattice_id, domain), key0,
-                                key1);
+    out[i] = xyd::philox4x32_10(make_uint4(first + (uint32_t)i, sweep, lattice_id, domain), rk);
+  }
+}
+
+template <int MODE>
+__global__ void k_eval_unit_vector(const float* __restrict__ t, float* __restrict__ c,
+                                   float* __restrict__ s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float sv, cv;
+    xyd::unit_vector<MODE>(t[i], &sv, &cv);
+    c[i] = cv;
+    s[i] = sv;
   }
 }
 
@@ -309,18 +257,24 @@ cudaError_t launch_one(const HalfSweepArgs& a, cudaStream_t stream) {
 cudaError_t launch_half_sweep(int colour, int sincos_mode, int reduce_mode,
                               const HalfSweepArgs& a, cudaStream_t stream) {
   if (colour == 0) {
-    return sincos_mode == 0 ? launch_one<0, 0, 0>(a, stream) : launch_one<0, 1, 0>(a, stream);
+    switch (sincos_mode) {
+      case 0: return launch_one<0, 0, 0>(a, stream);
+      case 1: return launch_one<0, 1, 0>(a, stream);
+      default: return launch_one<0, 2, 0>(a, stream);
+    }
   }
-  if (sincos_mode == 0) {
-    return reduce_mode == 0 ? launch_one<1, 0, 0>(a, stream) : launch_one<1, 0, 1>(a, stream);
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_one<1, 0, 1>(a, stream) : launch_one<1, 0, 0>(a, stream);
+    case 1: return comp ? launch_one<1, 1, 1>(a, stream) : launch_one<1, 1, 0>(a, stream);
+    default: return comp ? launch_one<1, 2, 1>(a, stream) : launch_one<1, 2, 0>(a, stream);
   }
-  return reduce_mode == 0 ? launch_one<1, 1, 0>(a, stream) : launch_one<1, 1, 1>(a, stream);
 }
 
-cudaError_t launch_start(float* theta, int L, uint32_t key0, uint32_t key1, uint32_t lattice_id,
+cudaError_t launch_start(float* theta, int L, const xyd::RoundKeys& rk, uint32_t lattice_id,
                          int hot, cudaStream_t stream) {
   const int64_t N = (int64_t)L * L;
-  k_start<<<grid_for(N, 256), 256, 0, stream>>>(theta, L, key0, key1, lattice_id, hot);
+  k_start<<<grid_for(N, 256), 256, 0, stream>>>(theta, L, rk, lattice_id, hot);
   return cudaGetLastError();
 }
 
@@ -334,12 +288,26 @@ cudaError_t launch_split_to_natural(const float* split, float* nat, int L, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_philox_words(uint32_t key0, uint32_t key1, uint32_t sweep, uint32_t lattice_id,
+cudaError_t launch_philox_words(const xyd::RoundKeys& rk, uint32_t sweep, uint32_t lattice_id,
                                 uint32_t domain, uint32_t first, int64_t n, uint32_t* out,
                                 cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  k_philox_words<<<grid_for(n, 256), 256, 0, stream>>>(key0, key1, sweep, lattice_id, domain,
+  k_philox_words<<<grid_for(n, 256), 256, 0, stream>>>(rk, sweep, lattice_id, domain,
                                                        first, n, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_unit_vector(int mode, const float* theta, float* c, float* s, int64_t n,
+                                    cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int g = grid_for(n, 256);
+  if (mode == 0) {
+    k_eval_unit_vector<0><<<g, 256, 0, stream>>>(theta, c, s, n);
+  } else if (mode == 1) {
+    k_eval_unit_vector<1><<<g, 256, 0, stream>>>(theta, c, s, n);
+  } else {
+    k_eval_unit_vector<2><<<g, 256, 0, stream>>>(theta, c, s, n);
+  }
   return cudaGetLastError();
 }
 

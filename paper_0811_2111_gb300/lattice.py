@@ -19,7 +19,7 @@ def _torch():
 
 class Lattice:
     def __init__(self, L, beta, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
-                 reduce="fp64", lattice_id=0, device=None, stream=None):
+                 reduce="fp64", lattice_id=0, algorithm="auto", device=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -33,10 +33,12 @@ class Lattice:
         p.J = float(J)
         p.delta = float(delta)
         p.seed = int(seed)
-        p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST}[sincos]
+        p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
+                         "libm": X.XY_SINCOS_LIBM}[sincos]
         p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
-        p.reserved = 0
+        p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
+                       "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
         self.params = p
         self.J = float(J)
         with torch.cuda.device(self.device):
@@ -108,6 +110,21 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def unit_vectors(theta, mode="accurate", device=None):
+    """(cos, sin) of float32 angles with the kernels' sincos (numpy in, numpy out)."""
+    torch = _torch()
+    dev = torch.device(device if device is not None else "cuda")
+    t = torch.as_tensor(np.ascontiguousarray(theta, np.float32)).to(dev)
+    c = torch.empty_like(t)
+    s = torch.empty_like(t)
+    stream = torch.cuda.current_stream(dev)
+    m = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST, "libm": X.XY_SINCOS_LIBM}[mode]
+    X.xy_eval_unit_vector(m, C.c_void_p(t.data_ptr()), C.c_void_p(c.data_ptr()),
+                          C.c_void_p(s.data_ptr()), t.numel(), C.c_void_p(stream.cuda_stream))
+    stream.synchronize()
+    return c.cpu().numpy(), s.cpu().numpy()
 
 
 def philox_words(seed, sweep, lattice_id, domain, first, n, device=None):

@@ -52,7 +52,7 @@ def test_version(lib):
 def _params(**kw):
     p = X.xy_params()
     p.L, p.start, p.beta, p.J, p.delta, p.seed = 8, 0, 1.0, 1.0, 3.14159, 1
-    p.sincos_mode, p.reduce_mode, p.lattice_id, p.reserved = 0, 0, 0, 0
+    p.sincos_mode, p.reduce_mode, p.lattice_id, p.algorithm = 0, 0, 0, 0
     for k, v in kw.items():
         setattr(p, k, v)
     return p
@@ -63,7 +63,8 @@ def _params(**kw):
     (dict(beta=-1.0), "beta"), (dict(beta=float("nan")), "beta"),
     (dict(delta=0.0), "delta"), (dict(delta=4.0), "delta"),
     (dict(start=7), "start"), (dict(sincos_mode=5), "sincos"), (dict(reduce_mode=2), "reduce"),
-    (dict(reserved=1), "reserved"), (dict(J=float("inf")), "J"),
+    (dict(algorithm=9), "algorithm"), (dict(algorithm=1, L=96), "multiple of 128"),
+    (dict(J=float("inf")), "J"),
 ])
 def test_create_rejects_bad_parameters(lib, kw, fragment):
     ctx = C.c_void_p()
