@@ -196,6 +196,33 @@ xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, ui
 xy_status xy_eval_unit_vector(int32_t sincos_mode, const float *d_theta, float *d_cos,
                               float *d_sin, int64_t n, void *cuda_stream);
 
+/* Sweeps without any allocation, for callers that cannot allocate device
+ * memory when they run (their device memory belongs to their own caching
+ * allocator, they cannot afford the device-wide synchronisation of cudaFree,
+ * or a run must not fail half way with out-of-memory).  The paper has no
+ * counterpart; this is a deployment convenience around the fused kernel.
+ *   p           parameters (start, algorithm and lattice state are not used:
+ *               the sweep starts from d_angles); L must be a multiple of 128
+ *               and at most 1024, else XY_EINVAL.
+ *   d_angles    caller-owned device buffer of L*L floats in the split layout
+ *               (as xy_create uses it), 16-byte aligned; read and rewritten:
+ *               it holds the state after the last sweep on return (stream order).
+ *   first_sweep Philox sweep word of the first sweep; sweeps first_sweep ..
+ *               first_sweep + n_sweeps - 1 are run.
+ *   d_records   caller-owned device array of n_sweeps records, cleared and filled.
+ *   cuda_stream stream to enqueue on (NULL: legacy default stream).
+ * The kernel's second lattice buffer is a fixed 4 MiB array inside the
+ * library, held by every GPU that loads it until the process exits.  Its
+ * device address is looked up on the first call on each device, so make the
+ * first call on a device before any stream capture.  All calls on a device
+ * share that array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Nothing here calls
+ * cudaMalloc, cudaFree or an allocating library routine.  Errors are returned
+ * before any work is enqueued; xy_noalloc_last_error() describes them. */
+xy_status xy_sweep_noalloc(const xy_params *p, float *d_angles, uint32_t first_sweep,
+                           int64_t n_sweeps, xy_record *d_records, void *cuda_stream);
+const char *xy_noalloc_last_error(void);
+
 /* ABI version (major * 100 + minor). */
 int32_t xy_version(void);
 

@@ -79,6 +79,8 @@ def lib():
                                  C.c_int64, P, P]),
         "xy_version": (C.c_int32, []),
         "xy_eval_unit_vector": (st, [C.c_int32, P, P, P, C.c_int64, P]),
+        "xy_sweep_noalloc": (st, [C.POINTER(xy_params), P, C.c_uint32, C.c_int64, P, P]),
+        "xy_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -179,6 +181,14 @@ def xy_philox_words(seed, sweep, lattice_id, domain, first, n, d_out_ptr, stream
 
 def xy_eval_unit_vector(mode, d_theta_ptr, d_cos_ptr, d_sin_ptr, n, stream_ptr=None):
     check(lib().xy_eval_unit_vector(mode, d_theta_ptr, d_cos_ptr, d_sin_ptr, n, stream_ptr))
+
+
+def xy_sweep_noalloc(params, d_angles_ptr, first_sweep, n_sweeps, d_records_ptr,
+                     stream_ptr=None):
+    st = lib().xy_sweep_noalloc(C.byref(params), d_angles_ptr, first_sweep, n_sweeps,
+                                d_records_ptr, stream_ptr)
+    if st != XY_OK:
+        raise XYError(st, lib().xy_noalloc_last_error().decode())
 
 
 def xy_version():
