@@ -190,6 +190,75 @@ const char *xy_last_error(const xy_ctx *ctx);
 xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, uint32_t domain,
                           uint32_t first, int64_t n, uint32_t *d_out, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices of uneven sides and temperatures swept
+ * together, one launch per round of sweeps, with optional replica exchange.
+ * The Sec. 3.2 remark that one RGBA texel holds four replicas "maybe at
+ * different temperatures" is the precedent; here each lattice keeps its own
+ * split-layout planes and the batch is cut into bands of rows, one CTA each,
+ * the bands of a lattice forming one thread-block cluster.  Every lattice i
+ * evolves exactly as a single-lattice context with the same L, beta, seed and
+ * lattice_id = lattice_id0 + i would (same Philox counters, same site update).
+ * Replica exchange: lattices sharing a ladder id (equal L required) are
+ * ordered by initial beta; after every round the pairs of positions
+ * (p, p+1), p = round mod 2, round mod 2 + 2, ..., swap temperatures iff
+ * u24(w0) < exp((beta_p - beta_{p+1})(E_p - E_{p+1})), E = -J C of the round's
+ * last sweep, Philox domain 2 with counter (ladder * 65536 + p, round,
+ * lattice_id0, 2).  Each round (round kernel + exchange kernel) is one
+ * captured CUDA graph replayed round after round.
+ * ------------------------------------------------------------------------ */
+#define XY_BATCH_MAX_L 256
+
+typedef struct xy_batch xy_batch;
+
+typedef struct {
+    int32_t n;                  /* number of lattices, >= 1                         */
+    const int32_t *L;           /* [n] even sides in [2, XY_BATCH_MAX_L] (copied)    */
+    const double *beta;         /* [n] initial inverse temperatures (copied)         */
+    const int32_t *ladder;      /* [n] ladder id per lattice (-1: none), or NULL     */
+    double J;                   /* coupling                                          */
+    double delta;               /* proposal half-window, (0, pi]                     */
+    uint64_t seed;              /* Philox key of every lattice                       */
+    int32_t start;              /* XY_START_HOT or XY_START_COLD                     */
+    int32_t sincos_mode;        /* as in xy_params                                   */
+    int32_t reduce_mode;        /* as in xy_params                                   */
+    uint32_t lattice_id0;       /* lattice i uses lattice id lattice_id0 + i         */
+    int32_t sweeps_per_round;   /* sweeps per launch (and between exchanges), >= 1   */
+    int32_t target_band_sites;  /* sites per CTA band of the work plan (0: 8192)     */
+} xy_batch_params;
+
+/* Create and hot/cold-start all lattices; the plan, ladders and buffers are
+ * built here.  Errors: XY_EINVAL (bad sizes, a ladder mixing sides), XY_ENOMEM,
+ * XY_ECUDA; xy_batch_last_error(NULL) describes them. */
+xy_status xy_batch_create(const xy_batch_params *p, void *cuda_stream, xy_batch **out);
+/* Make room for n_rounds more rounds of records (so xy_batch_run allocates nothing). */
+xy_status xy_batch_reserve(xy_batch *b, int64_t n_rounds);
+/* Enqueue `rounds` rounds: sweeps_per_round sweeps of every lattice, then one
+ * replica-exchange step.  Asynchronous; appends sweeps_per_round records per
+ * lattice per round. */
+xy_status xy_batch_run(xy_batch *b, int64_t rounds);
+/* Lattice count, records per lattice, next sweep index, CTAs per launch. */
+xy_status xy_batch_info(const xy_batch *b, int32_t *n_lattices, int64_t *n_records,
+                        uint64_t *next_sweep, int32_t *n_ctas);
+/* Observables of records [first, first + count) of one lattice (synchronizes). */
+xy_status xy_batch_measure(xy_batch *b, int32_t lattice, int64_t first, int64_t count,
+                           xy_obs *host_out);
+/* Device records, laid out [lattice][stride]; `count` valid per lattice. */
+xy_status xy_batch_records_device(xy_batch *b, const xy_record **d_records, int64_t *stride,
+                                  int64_t *count);
+/* Current beta of every lattice (host array of n; synchronizes). */
+xy_status xy_batch_betas(xy_batch *b, double *host_beta);
+/* Exchange bookkeeping per ladder slot (ladders in ascending id, positions in
+ * beta order): lattice at each slot, accepted and attempted swaps of the pair
+ * (slot, slot + 1).  Any output may be NULL; *n_slots receives the slot count. */
+xy_status xy_batch_exchange_stats(xy_batch *b, int32_t *n_slots, int32_t *slot_lattice,
+                                  uint64_t *accepted, uint64_t *attempted);
+/* Angles of one lattice in natural order (L*L floats; synchronizes). */
+xy_status xy_batch_get_state(xy_batch *b, int32_t lattice, float *host_angles);
+xy_status xy_batch_synchronize(xy_batch *b);
+xy_status xy_batch_destroy(xy_batch *b);          /* NULL-safe */
+const char *xy_batch_last_error(const xy_batch *b);
+
 /* Unit vectors (cos, sin) of n device angles with the sweep kernels' own
  * sincos of precision `sincos_mode` (accuracy checks against CUDA and FP64):
  * d_theta, d_cos, d_sin are device arrays of n floats; runs on cuda_stream. */

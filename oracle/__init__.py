@@ -63,6 +63,12 @@ def lib():
                               _optional(_D), _optional(_D)]
         L.orc_run.restype = C.c_int
         L.orc_max_threads.restype = C.c_int
+        _I32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+        L.orc_exchange.argtypes = [C.c_int, _I32, C.c_int, _I32, _D, _D, _D, C.c_uint32,
+                                   C.c_uint64, C.c_uint32, _optional(_U8)]
+        L.orc_pt_run.argtypes = [C.c_int, C.c_int, C.c_int, _D, C.c_double, C.c_double,
+                                 C.c_uint64, C.c_uint32, C.c_int, C.c_int, _D]
+        L.orc_pt_run.restype = C.c_int
         _lib = L
     return _lib
 
@@ -172,3 +178,29 @@ def run(Lx, Ly, beta, n_sweeps, seed, lattice_id=0, J=1.0, delta=np.pi, start=1,
     if r != 0:
         raise ValueError("oracle run failed (odd side with checkerboard order?)")
     return rec, th
+
+
+def exchange(ladder_start, pos_lattice, pos_beta, beta_of_lattice, energy, round_index, seed,
+             lattice_id0=0):
+    """One replica-exchange step; returns (pos_lattice, beta_of_lattice, swapped) updated copies."""
+    ls = np.ascontiguousarray(ladder_start, np.int32)
+    pl = np.array(pos_lattice, np.int32)
+    pb = np.ascontiguousarray(pos_beta, np.float64)
+    bl = np.array(beta_of_lattice, np.float64)
+    en = np.ascontiguousarray(energy, np.float64)
+    sw = np.zeros(pl.size, np.uint8)
+    lib().orc_exchange(ls.size, ls, pl.size, pl, pb, bl, en, round_index, seed, lattice_id0, sw)
+    return pl, bl, sw.astype(bool)
+
+
+def pt_run(Lx, Ly, betas, rounds, sweeps_per_round, seed, lattice_id0=0, J=1.0, delta=np.pi):
+    """Parallel tempering of one ladder; records (n, rounds*sweeps_per_round, 7):
+    C, Ix, Iy, Mx, My, accepted, beta of each lattice after each sweep."""
+    b = np.ascontiguousarray(betas, np.float64)
+    total = rounds * sweeps_per_round
+    rec = np.zeros((b.size, total, 7), np.float64)
+    r = lib().orc_pt_run(Lx, Ly, b.size, b, J, delta, seed, lattice_id0, sweeps_per_round,
+                         rounds, rec)
+    if r != 0:
+        raise ValueError("oracle parallel-tempering run failed")
+    return rec

@@ -22,7 +22,8 @@
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11, Sec. 3.3 and Table 2), keyed
  * by the 64-bit seed (low word first) with counter (site, sweep, lattice id,
- * domain); domain 0 draws the hot start, domain 1 the Metropolis words.
+ * domain); domain 0 draws the hot start, domain 1 the Metropolis words,
+ * domain 2 the replica-exchange words.
  * Uniforms use the top 24 bits of a word: u = (w >> 8) * 2^-24.
  */
 #include <math.h>
@@ -318,4 +319,91 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Replica exchange (parallel tempering) between neighbouring          */
+/* temperatures of a ladder.                                           */
+/* ------------------------------------------------------------------ */
+
+/* One exchange step.  Ladder l owns slots [ladder_start[l], ladder_start[l+1])
+ * (the last ladder ends at n_slots); slot s holds lattice pos_lattice[s] at
+ * temperature pos_beta[s] (ascending within a ladder).  In round r the pairs
+ * of positions (p, p+1) with p = r mod 2, r mod 2 + 2, ... are tried: with
+ * E = energy[lattice] (-J C of its last sweep) and w the Philox words of
+ * counter (l * 65536 + p, r, lattice_id0, 2), the two lattices trade
+ * temperatures iff u24(w0) < exp((beta_p - beta_{p+1}) (E_p - E_{p+1})),
+ * the Metropolis rule for swapping two replicas.  beta_of_lattice and
+ * pos_lattice are updated; swapped[slot] = 1 for the lower slot of a swap. */
+void orc_exchange(int n_ladders, const int *ladder_start, int n_slots, int *pos_lattice,
+                  const double *pos_beta, double *beta_of_lattice, const double *energy,
+                  uint32_t round, uint64_t seed, uint32_t lattice_id0, uint8_t *swapped)
+{
+    for (int s = 0; s < n_slots; ++s) if (swapped) swapped[s] = 0;
+    for (int l = 0; l < n_ladders; ++l) {
+        int begin = ladder_start[l];
+        int end = (l + 1 < n_ladders) ? ladder_start[l + 1] : n_slots;
+        for (int p = (int)(round & 1u); begin + p + 1 < end; p += 2) {
+            int a = pos_lattice[begin + p], b = pos_lattice[begin + p + 1];
+            double ba = pos_beta[begin + p], bb = pos_beta[begin + p + 1];
+            uint32_t w[4];
+            site_words(seed, (uint32_t)l * 65536u + (uint32_t)p, round, lattice_id0, 2u, w);
+            if (u24(w[0]) < exp((ba - bb) * (energy[a] - energy[b]))) {
+                pos_lattice[begin + p] = b;
+                pos_lattice[begin + p + 1] = a;
+                beta_of_lattice[b] = ba;
+                beta_of_lattice[a] = bb;
+                if (swapped) swapped[begin + p] = 1;
+            }
+        }
+    }
+}
+
+/* Parallel tempering of one ladder of n equal Lx x Ly lattices (checkerboard
+ * sweeps): lattice i starts hot with lattice id lattice_id0 + i at beta[i]
+ * (ascending); every round it runs sweeps_per_round sweeps at its current
+ * temperature, then one exchange step (round r) on the energies of the last
+ * sweep.  records[(i * total + t) * 7 + 0..6] = C, Ix, Iy, Mx, My, accepted,
+ * beta after sweep t of lattice i, total = rounds * sweeps_per_round. */
+int orc_pt_run(int Lx, int Ly, int n, const double *beta, double J, double delta,
+               uint64_t seed, uint32_t lattice_id0, int sweeps_per_round, int rounds,
+               double *records)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    int64_t total = (int64_t)rounds * sweeps_per_round;
+    double *theta = (double *)malloc(sizeof(double) * (size_t)(N * n));
+    double *bl = (double *)malloc(sizeof(double) * (size_t)n);
+    double *energy = (double *)malloc(sizeof(double) * (size_t)n);
+    int *pos = (int *)malloc(sizeof(int) * (size_t)n);
+    int start0 = 0;
+    if (!theta || !bl || !energy || !pos) {
+        free(theta); free(bl); free(energy); free(pos);
+        return -1;
+    }
+    for (int i = 0; i < n; ++i) {
+        orc_start(Lx, Ly, seed, lattice_id0 + (uint32_t)i, 1, theta + N * i);
+        bl[i] = beta[i];
+        pos[i] = i;
+    }
+    for (int r = 0; r < rounds; ++r) {
+        for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < sweeps_per_round; ++k) {
+                int64_t t = (int64_t)r * sweeps_per_round + k;
+                int64_t acc = orc_sweep(Lx, Ly, theta + N * i, bl[i], J, delta, seed,
+                                        lattice_id0 + (uint32_t)i, (uint32_t)t, 0, 1);
+                if (acc < 0) {
+                    free(theta); free(bl); free(energy); free(pos);
+                    return -1;
+                }
+                double *rec = records + (i * total + t) * 7;
+                orc_measure(Lx, Ly, theta + N * i, rec);
+                rec[5] = (double)acc;
+                rec[6] = bl[i];
+                if (k == sweeps_per_round - 1) energy[i] = -J * rec[0];
+            }
+        }
+        orc_exchange(1, &start0, n, pos, beta, bl, energy, (uint32_t)r, seed, lattice_id0, NULL);
+    }
+    free(theta); free(bl); free(energy); free(pos);
+    return 0;
 }

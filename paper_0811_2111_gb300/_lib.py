@@ -45,6 +45,16 @@ class xy_obs(C.Structure):
                 ("My", C.c_double), ("accepted", C.c_uint64), ("beta", C.c_double)]
 
 
+class xy_batch_params(C.Structure):
+    _fields_ = [("n", C.c_int32), ("L", C.POINTER(C.c_int32)), ("beta", C.POINTER(C.c_double)),
+                ("ladder", C.POINTER(C.c_int32)), ("J", C.c_double), ("delta", C.c_double),
+                ("seed", C.c_uint64), ("start", C.c_int32), ("sincos_mode", C.c_int32),
+                ("reduce_mode", C.c_int32), ("lattice_id0", C.c_uint32),
+                ("sweeps_per_round", C.c_int32), ("target_band_sites", C.c_int32)]
+
+
+XY_BATCH_MAX_L = 256
+
 _lib = None
 
 
@@ -80,6 +90,20 @@ def lib():
         "xy_version": (C.c_int32, []),
         "xy_eval_unit_vector": (st, [C.c_int32, P, P, P, C.c_int64, P]),
         "xy_sweep_noalloc": (st, [C.POINTER(xy_params), P, C.c_uint32, C.c_int64, P, P]),
+        "xy_batch_create": (st, [C.POINTER(xy_batch_params), P, C.POINTER(P)]),
+        "xy_batch_reserve": (st, [P, C.c_int64]),
+        "xy_batch_run": (st, [P, C.c_int64]),
+        "xy_batch_info": (st, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                               C.POINTER(C.c_uint64), C.POINTER(C.c_int32)]),
+        "xy_batch_measure": (st, [P, C.c_int32, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),
+        "xy_batch_records_device": (st, [P, C.POINTER(P), C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]),
+        "xy_batch_betas": (st, [P, P]),
+        "xy_batch_exchange_stats": (st, [P, C.POINTER(C.c_int32), P, P, P]),
+        "xy_batch_get_state": (st, [P, C.c_int32, P]),
+        "xy_batch_synchronize": (st, [P]),
+        "xy_batch_destroy": (st, [P]),
+        "xy_batch_last_error": (C.c_char_p, [P]),
         "xy_noalloc_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -193,3 +217,71 @@ def xy_sweep_noalloc(params, d_angles_ptr, first_sweep, n_sweeps, d_records_ptr,
 
 def xy_version():
     return int(lib().xy_version())
+
+
+# -- batches ------------------------------------------------------------------
+
+def batch_check(status, b=None):
+    if status != XY_OK:
+        msg = lib().xy_batch_last_error(b)
+        raise XYError(status, msg.decode() if msg else "")
+    return status
+
+
+def xy_batch_create(params, stream_ptr=None):
+    b = C.c_void_p()
+    batch_check(lib().xy_batch_create(C.byref(params), stream_ptr, C.byref(b)))
+    return b
+
+
+def xy_batch_reserve(b, n_rounds):
+    batch_check(lib().xy_batch_reserve(b, n_rounds), b)
+
+
+def xy_batch_run(b, rounds):
+    batch_check(lib().xy_batch_run(b, rounds), b)
+
+
+def xy_batch_info(b):
+    n = C.c_int32()
+    r = C.c_int64()
+    s = C.c_uint64()
+    c = C.c_int32()
+    batch_check(lib().xy_batch_info(b, C.byref(n), C.byref(r), C.byref(s), C.byref(c)), b)
+    return n.value, r.value, s.value, c.value
+
+
+def xy_batch_measure(b, lattice, first, count):
+    out = (xy_obs * max(count, 1))()
+    batch_check(lib().xy_batch_measure(b, lattice, first, count, out), b)
+    return out if count > 0 else (xy_obs * 0)()
+
+
+def xy_batch_records_device(b):
+    p = C.c_void_p()
+    stride = C.c_int64()
+    n = C.c_int64()
+    batch_check(lib().xy_batch_records_device(b, C.byref(p), C.byref(stride), C.byref(n)), b)
+    return p.value, stride.value, n.value
+
+
+def xy_batch_betas(b, host_ptr):
+    batch_check(lib().xy_batch_betas(b, host_ptr), b)
+
+
+def xy_batch_exchange_stats(b, slot_ptr, acc_ptr, att_ptr):
+    n = C.c_int32()
+    batch_check(lib().xy_batch_exchange_stats(b, C.byref(n), slot_ptr, acc_ptr, att_ptr), b)
+    return n.value
+
+
+def xy_batch_get_state(b, lattice, host_ptr):
+    batch_check(lib().xy_batch_get_state(b, lattice, host_ptr), b)
+
+
+def xy_batch_synchronize(b):
+    batch_check(lib().xy_batch_synchronize(b), b)
+
+
+def xy_batch_destroy(b):
+    batch_check(lib().xy_batch_destroy(b))

@@ -90,6 +90,7 @@ xy_status fail(xy_ctx* c, xy_status st, const char* fmt, ...) {
 }
 
 xy_status cuda_fail(xy_ctx* c, cudaError_t e, const char* what) {
+  (void)cudaGetLastError();   // do not leave a non-sticky error for the next launch check
   return fail(c, e == cudaErrorMemoryAllocation ? XY_ENOMEM : XY_ECUDA, "%s: %s (%s)", what,
               cudaGetErrorName(e), cudaGetErrorString(e));
 }

@@ -51,6 +51,62 @@ cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs
 cudaError_t launch_eval_unit_vector(int mode, const float* theta, float* c, float* s, int64_t n,
                                     cudaStream_t stream);
 
+// ---- batched lattices (xy_batch.cu) ----
+constexpr int kClusterSize = 8;      // CTAs per cluster of the batched round kernel
+
+// One CTA's band of rows [y_begin, y_end) of one lattice (lattice < 0: padding).
+struct BatchBand {
+  int32_t lattice;
+  int32_t y_begin;
+  int32_t y_end;
+  int32_t pad;
+};
+
+struct BatchArgs {
+  float* theta;                 // all lattices, split layout each, at offset[i] floats
+  const int64_t* offset;        // [n]
+  const int32_t* L;             // [n]
+  const double* beta;           // [n] current beta of each lattice
+  const BatchBand* bands;       // [grid]
+  xy_record* records;           // [n][rec_stride]
+  int64_t rec_stride;
+  uint32_t rec_sweep0;          // sweep index of each lattice's record 0
+  const uint32_t* counters;     // device: [0] first sweep of this launch, [1] round
+  int sweeps;                   // sweeps per launch
+  double J;
+  float delta;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id0;         // lattice i uses lattice id lattice_id0 + i
+  size_t cs_bytes;              // shared memory for the staged unit vectors
+};
+
+struct ExchangeArgs {
+  int n_pairs;                  // candidate pairs (all ladders)
+  const int32_t* pair_ladder;   // [n_pairs]
+  const int32_t* pair_pos;      // [n_pairs] lower position p of the pair
+  const int32_t* ladder_start;  // [n_ladders] first slot of each ladder in pos_*
+  int32_t* pos_lattice;         // [slots] lattice at each position (beta order)
+  const double* pos_beta;       // [slots] beta of each position
+  double* beta;                 // [n] beta of each lattice (updated)
+  const xy_record* records;
+  int64_t rec_stride;
+  uint32_t rec_sweep0;
+  uint32_t* counters;           // device: [0] first sweep of the round, [1] round; advanced
+  int sweeps;                   // sweeps per round (the last one's energies are compared)
+  double J;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id0;
+  unsigned long long* accepted; // [slots] per lower position
+  unsigned long long* attempted;
+};
+
+size_t batch_smem_bytes(int max_stage_floats2);
+// Set the kernel's shared-memory limit (once, outside any stream capture).
+cudaError_t prepare_batch_round(int sincos_mode, int reduce_mode, size_t smem);
+cudaError_t launch_batch_round(int sincos_mode, int reduce_mode, const BatchArgs& a, int n_ctas,
+                               cudaStream_t stream);
+cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
+
 // Red (colour 0) then black (colour 1) half-sweep; the black one also adds
 // the sweep's bond/spin sums to *rec.  sincos_mode / reduce_mode as in xy.h.
 cudaError_t launch_half_sweep(int colour, int sincos_mode, int reduce_mode,

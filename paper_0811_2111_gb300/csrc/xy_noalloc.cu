@@ -53,6 +53,7 @@ cudaError_t pong_address(float** out) {
 thread_local char g_msg[256] = "no error";
 
 xy_status fail(xy_status st, const char* what) {
+  (void)cudaGetLastError();   // leave no non-sticky error behind for later launch checks
   snprintf(g_msg, sizeof(g_msg), "xy_sweep_noalloc: %s", what);
   return st;
 }

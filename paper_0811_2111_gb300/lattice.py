@@ -137,3 +137,109 @@ def philox_words(seed, sweep, lattice_id, domain, first, n, device=None):
                       C.c_void_p(stream.cuda_stream))
     stream.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+class Batch:
+    """Many lattices swept together (``xy_batch_*``), optional replica exchange.
+
+    Ls, betas: per-lattice sides and initial inverse temperatures; ladders:
+    per-lattice ladder ids (-1 or None for no exchange)."""
+
+    def __init__(self, Ls, betas, seed, ladders=None, J=1.0, delta=math.pi, start="hot",
+                 sincos="accurate", reduce="fp64", lattice_id0=0, sweeps_per_round=10,
+                 target_band_sites=0, device=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = len(Ls)
+        self.Ls = np.ascontiguousarray(Ls, np.int32)
+        self._betas = np.ascontiguousarray(betas, np.float64)
+        self._ladders = None if ladders is None else np.ascontiguousarray(ladders, np.int32)
+        p = X.xy_batch_params()
+        p.n = n
+        p.L = self.Ls.ctypes.data_as(C.POINTER(C.c_int32))
+        p.beta = self._betas.ctypes.data_as(C.POINTER(C.c_double))
+        p.ladder = (None if self._ladders is None
+                    else self._ladders.ctypes.data_as(C.POINTER(C.c_int32)))
+        p.J = float(J)
+        p.delta = float(delta)
+        p.seed = int(seed)
+        p.start = {"hot": X.XY_START_HOT, "cold": X.XY_START_COLD}[start]
+        p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
+                         "libm": X.XY_SINCOS_LIBM}[sincos]
+        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.lattice_id0 = int(lattice_id0)
+        p.sweeps_per_round = int(sweeps_per_round)
+        p.target_band_sites = int(target_band_sites)
+        self.params = p
+        self.J = float(J)
+        self.sweeps_per_round = int(sweeps_per_round)
+        with torch.cuda.device(self.device):
+            self.b = X.xy_batch_create(p, C.c_void_p(self.stream.cuda_stream))
+
+    @property
+    def n(self):
+        return len(self.Ls)
+
+    def reserve(self, rounds):
+        X.xy_batch_reserve(self.b, rounds)
+
+    def run(self, rounds=1):
+        X.xy_batch_run(self.b, rounds)
+
+    def info(self):
+        return X.xy_batch_info(self.b)
+
+    def observables(self, lattice, first=0, count=None):
+        _, nrec, _, _ = X.xy_batch_info(self.b)
+        count = nrec - first if count is None else count
+        obs = X.xy_batch_measure(self.b, lattice, first, count)
+        names = ["e", "abs_m", "upsilon", "C", "Ix", "Iy", "Mx", "My", "beta"]
+        out = {k: np.array([getattr(o, k) for o in obs], np.float64) for k in names}
+        out["accepted"] = np.array([o.accepted for o in obs], np.uint64)
+        return out
+
+    def betas(self):
+        out = np.empty(self.n, np.float64)
+        X.xy_batch_betas(self.b, out.ctypes.data_as(C.c_void_p))
+        return out
+
+    def exchange_stats(self):
+        n = X.xy_batch_exchange_stats(self.b, None, None, None)
+        slots = np.zeros(max(n, 1), np.int32)
+        acc = np.zeros(max(n, 1), np.uint64)
+        att = np.zeros(max(n, 1), np.uint64)
+        X.xy_batch_exchange_stats(self.b, slots.ctypes.data_as(C.c_void_p),
+                                  acc.ctypes.data_as(C.c_void_p), att.ctypes.data_as(C.c_void_p))
+        return slots[:n], acc[:n], att[:n]
+
+    def state(self, lattice):
+        L = int(self.Ls[lattice])
+        buf = np.empty(L * L, np.float32)
+        X.xy_batch_get_state(self.b, lattice, buf.ctypes.data_as(C.c_void_p))
+        return buf.reshape(L, L)
+
+    def records_device(self):
+        return X.xy_batch_records_device(self.b)
+
+    def synchronize(self):
+        X.xy_batch_synchronize(self.b)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            X.xy_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -53,3 +53,17 @@ def random_angles(L, seed):
     """Uniform angles in [0, 2 pi) as float32 natural-order [L, L] (numpy PCG64)."""
     rng = np.random.default_rng(seed)
     return (rng.random((L, L)) * (2 * np.pi)).astype(np.float32) % np.float32(2 * np.pi)
+
+
+def batch_layout():
+    """The replica-exchange workload: 8 ladders, one per side in BATCH_LS; ladder l
+    holds 32 lattices on the beta-grid points b = l mod 2, l mod 2 + 2, ..., so every
+    grid point carries exactly 4 lattices and every side spans [0.8, 1.4].
+    Returns (Ls, betas, ladders) of the 256 lattices, ladder-major."""
+    Ls, betas, ladders = [], [], []
+    for l, L in enumerate(BATCH_LS):
+        for j in range(32):
+            Ls.append(L)
+            betas.append(BATCH_BETA_GRID[(l % 2) + 2 * j])
+            ladders.append(l)
+    return Ls, betas, ladders

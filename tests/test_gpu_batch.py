@@ -1,0 +1,141 @@
+"""Batched engine and replica exchange against the single-lattice path and the oracle (GPU).
+
+* A lattice in a batch evolves bit-identically to the same lattice alone
+  (same Philox counters, same site update), whatever the work plan.
+* Every replica-exchange step equals the oracle's step computed from the
+  GPU's own energies (both in FP64 from the same fixed-point sums).
+* A ladder of 2x2 tori samples each temperature's exact energy.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import exact_small as ex
+from gpu_util import record_tolerance
+from stats_util import jackknife_mean
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300.lattice import Batch, Lattice  # noqa: E402
+from paper_0811_2111_gb300 import _lib as X  # noqa: E402
+from paper_0811_2111_gb300 import workloads as WL  # noqa: E402
+
+LS = [2, 6, 16, 24, 48, 96, 128, 256]
+BETAS = [0.7, 0.9, 1.0, 1.1, 1.2, 0.95, 1.05, 1.12]
+
+
+def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5):
+    with Batch(LS, BETAS, seed, lattice_id0=lid0, sweeps_per_round=spr,
+               target_band_sites=target, sincos=sincos) as b:
+        b.run(rounds)
+        n_ctas = b.info()[3]
+        return [b.state(i) for i in range(len(LS))], [b.observables(i) for i in range(len(LS))], n_ctas
+
+
+@pytest.mark.parametrize("sincos", ["accurate", "fast"])
+def test_batch_matches_single_lattices(sincos):
+    states, obs, _ = run_batch(sincos=sincos)
+    for i, (L, beta) in enumerate(zip(LS, BETAS)):
+        with Lattice(L, beta, 23, lattice_id=5 + i, sincos=sincos, algorithm="two_pass") as lat:
+            lat.sweep(10)
+            s, _ = lat.state()
+            o = lat.observables()
+        assert np.array_equal(states[i], s), f"L={L}"
+        assert np.array_equal(obs[i]["accepted"], o["accepted"]), f"L={L}"
+        assert np.all(obs[i]["beta"] == beta)
+        tol = record_tolerance(L * L, fast=(sincos == "fast"))
+        for k in ("C", "Ix", "Iy", "Mx", "My"):
+            assert np.max(np.abs(obs[i][k] - o[k])) <= tol, (L, k)
+
+
+def test_batch_is_independent_of_the_work_plan():
+    ref_states, ref_obs, n0 = run_batch(target=8192)
+    for target in (256, 1024, 65536):
+        states, obs, n = run_batch(target=target)
+        for i in range(len(LS)):
+            assert np.array_equal(states[i], ref_states[i])
+            assert np.array_equal(obs[i]["accepted"], ref_obs[i]["accepted"])
+        print(f"target {target}: {n} CTAs (8192: {n0})")
+
+
+def test_replica_exchange_matches_oracle_step_by_step():
+    Ls = [16] * 9
+    betas = [0.8, 0.9, 1.0, 1.1, 1.0, 1.1, 1.2, 1.3, 1.05]
+    ladders = [0, 0, 0, 0, 3, 3, 3, 3, -1]
+    seed, lid0, spr = 31, 100, 3
+    # slot layout: ladders in ascending id, positions in ascending initial beta
+    ladder_ids = sorted(set(l for l in ladders if l >= 0))
+    ladder_start, pos_lattice, pos_beta = [], [], []
+    for l in ladder_ids:
+        members = sorted([i for i in range(len(Ls)) if ladders[i] == l], key=lambda i: betas[i])
+        ladder_start.append(len(pos_lattice))
+        pos_lattice += members
+        pos_beta += [betas[i] for i in members]
+    n_swaps = 0
+    with Batch(Ls, betas, seed, ladders=ladders, lattice_id0=lid0, sweeps_per_round=spr) as b:
+        slots, _, _ = b.exchange_stats()
+        assert list(slots) == pos_lattice
+        beta_now = b.betas()
+        for r in range(60):
+            b.run(1)
+            last = (r + 1) * spr - 1
+            energy = np.array([-b.J * b.observables(i, last, 1)["C"][0] for i in range(len(Ls))])
+            want_pos, want_beta, swapped = oracle.exchange(ladder_start, pos_lattice, pos_beta,
+                                                           beta_now, energy, r, seed, lid0)
+            slots, acc, att = b.exchange_stats()
+            beta_now = b.betas()
+            assert list(slots) == list(want_pos), f"round {r}"
+            assert np.array_equal(beta_now, want_beta), f"round {r}"
+            pos_lattice = list(want_pos)
+            n_swaps += int(swapped.sum())
+        assert acc.sum() == n_swaps
+        assert beta_now[8] == 1.05                        # not on a ladder: never moves
+    assert 0 < n_swaps < 60 * 4
+
+
+def test_replica_exchange_samples_exact_2x2_energies():
+    betas = [0.5, 1.0, 2.0]
+    with Batch([2, 2, 2], betas, 3, ladders=[0, 0, 0], sweeps_per_round=2) as b:
+        b.run(20000)
+        obs = [b.observables(i) for i in range(3)]
+    e = np.stack([o["e"] for o in obs])
+    bl = np.stack([o["beta"] for o in obs])
+    assert np.all(np.sort(bl, axis=0) == np.array(betas)[:, None])
+    for beta in betas:
+        series = e.T[bl.T == beta]
+        m, err = jackknife_mean(series[2000:])
+        print(f"beta {beta}: gpu {m:.5f} +- {err:.5f} exact {ex.e_2x2_bessel(beta):.5f}")
+        assert abs(m - ex.e_2x2_bessel(beta)) <= 3.5 * err + 1e-6
+
+
+def test_replica_exchange_configuration_runs():
+    """The batched workload: 256 lattices, 8 ladders of 32 over a 64-point beta grid."""
+    Ls, betas, ladders = WL.batch_layout()
+    with Batch(Ls, betas, WL.BATCH_SEED, ladders=ladders, sweeps_per_round=10) as b:
+        b.run(20)
+        n, nrec, nxt, n_ctas = b.info()
+        bl = b.betas()
+        slots, acc, att = b.exchange_stats()
+        e0 = b.observables(0)["e"]
+    assert n == 256 and nrec == 200 and nxt == 200
+    assert sorted(bl) == sorted(betas)                   # temperatures are only permuted
+    assert np.isfinite(e0).all() and -2.0 < e0[-1] < 0.0
+    rate = acc.sum() / max(att.sum(), 1)
+    print(f"{n_ctas} CTAs, exchange acceptance {rate:.3f}")
+    assert 0.05 < rate < 0.99
+
+
+def test_batch_error_paths():
+    with pytest.raises(X.XYError):
+        Batch([16, 18], [1.0, 1.0], 1, ladders=[0, 0])   # a ladder mixing sides
+    with pytest.raises(X.XYError):
+        Batch([512], [1.0], 1)                           # beyond the batch side limit
+    with pytest.raises(X.XYError):
+        Batch([15], [1.0], 1)                            # odd side

@@ -302,6 +302,44 @@ def test_coupling_scales_temperature():
 
 
 # ---------------------------------------------------------------------------
+# Replica exchange
+# ---------------------------------------------------------------------------
+
+def test_exchange_rule_reduces_to_metropolis_on_two_replicas():
+    """Swap iff u < exp((b_p - b_q)(E_p - E_q)): with equal energies every pair swaps,
+    and a pair whose swap would lower the joint weight swaps at that rate."""
+    ls = [0]
+    pos = [0, 1, 2, 3]
+    betas = [0.5, 0.7, 0.9, 1.1]
+    bl = list(betas)
+    pl, bl2, sw = oracle.exchange(ls, pos, betas, bl, [-3.0, -3.0, -3.0, -3.0], 0, seed=9)
+    assert sw[0] and sw[2] and not sw[1] and not sw[3]          # round 0 pairs (0,1), (2,3)
+    assert list(pl) == [1, 0, 3, 2] and list(bl2) == [0.7, 0.5, 1.1, 0.9]
+    # round 1 pairs (1,2) only
+    pl, bl3, sw = oracle.exchange(ls, pos, betas, bl, [-3.0] * 4, 1, seed=9)
+    assert list(sw) == [False, True, False, False]
+    # acceptance frequency of a disfavoured swap: exp((0.5-0.7)(-1-(-6))) = exp(-1)
+    acc = np.mean([oracle.exchange([0], [0, 1], [0.5, 0.7], [0.5, 0.7], [-1.0, -6.0], 2 * r,
+                                   seed=11)[2][0] for r in range(20000)])
+    assert abs(acc - math.exp(-1.0)) < 4 * math.sqrt(math.exp(-1) * (1 - math.exp(-1)) / 20000)
+
+
+def test_parallel_tempering_samples_each_temperature_exactly():
+    """A 3-temperature ladder of 2x2 tori: the energy series at each temperature
+    label must match that temperature's exact Bessel-sum value."""
+    betas = [0.5, 1.0, 2.0]
+    rec = oracle.pt_run(2, 2, betas, rounds=40000, sweeps_per_round=2, seed=3)
+    e = -rec[:, :, 0] / 4
+    b = rec[:, :, 6]
+    for beta in betas:
+        series = np.array([e[:, t][b[:, t] == beta][0] for t in range(e.shape[1])])
+        m, err = jackknife_mean(series[2000:])
+        assert within(m, err, ex.e_2x2_bessel(beta), extra=1e-6, k=3.5)
+    # every sweep carries each temperature exactly once
+    assert np.all(np.sort(b, axis=0) == np.array(betas)[:, None])
+
+
+# ---------------------------------------------------------------------------
 # Statistics helper
 # ---------------------------------------------------------------------------
 
