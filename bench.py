@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -59,8 +61,11 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["large", "huge"], default="large",
-                    help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step")
+    ap.add_argument("--workload", choices=["large", "huge", "batch"], default="large",
+                    help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step; "
+                         "batch: 256 lattices with replica exchange, 100 rounds/step")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="override sweeps per step (profiling runs only)")
     return ap.parse_args()
@@ -69,7 +74,7 @@ def parse():
 def workload(args):
     import dataclasses
     from paper_0811_2111_gb300 import workloads as WL
-    w = {"large": WL.LARGE, "huge": WL.HUGE}[args.workload]
+    w = {"large": WL.LARGE, "huge": WL.HUGE, "batch": WL.LARGE}[args.workload]
     if args.sweeps is not None:
         w = dataclasses.replace(w, sweeps=args.sweeps)
     return w
@@ -236,6 +241,97 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched workload: 256 lattices, 8 replica-exchange ladders
+# ---------------------------------------------------------------------------
+
+def measure_batch(dev, steps, warmup, sincos, rounds_per_step=100):
+    """Updates/s of the batched engine on the replica-exchange workload, next to the
+    same lattices swept one context at a time with the single-lattice kernels."""
+    import torch
+    from paper_0811_2111_gb300 import autotune
+    from paper_0811_2111_gb300 import workloads as WL
+    from paper_0811_2111_gb300.lattice import Batch, Lattice
+
+    Ls, betas, ladders = WL.batch_layout()
+    target = autotune.tune_batch(Ls, betas, ladders, sweeps_per_round=10, sincos=sincos,
+                                 device=dev)
+    sweeps = rounds_per_step * 10
+    sites = sum(L * L for L in Ls)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with Batch(Ls, betas, WL.BATCH_SEED, ladders=ladders, sweeps_per_round=10, sincos=sincos,
+               target_band_sites=target, device=dev) as b:
+        b.reserve(rounds_per_step * (steps + max(1, warmup)))
+        for _ in range(max(1, warmup)):
+            b.run(rounds_per_step)
+        torch.cuda.synchronize(dev)
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            b.run(rounds_per_step)
+            e1.record(b.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        slots, acc, att = b.exchange_stats()
+        n_ctas = b.info()[3]
+    value = sites * sweeps * steps / (sum(ms) * 1e-3)
+    # the same work as separate single-lattice contexts, one lattice at a time
+    per_L = {}
+    for L in sorted(set(Ls)):
+        with Lattice(L, 1.1, 1, sincos=sincos, device=dev) as lat:
+            lat.reserve(200)
+            lat.sweep(20)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.sweep(100)
+            e1.record(lat.stream)
+            e1.synchronize()
+            per_L[L] = e0.elapsed_time(e1) / 100          # ms per sweep
+    single_ms_per_sweep = sum(per_L[L] for L in Ls)
+    single_value = sites / (single_ms_per_sweep * 1e-3)
+    return {"workload": "xy_batch_256_lattices_L16-256_64beta_x4_exchange_every_10",
+            "value": value, "unit": UNIT, "ms_per_step": sum(ms) / steps,
+            "sweeps_per_step": sweeps, "lattices": len(Ls), "sites": sites,
+            "ctas_per_launch": n_ctas, "target_band_sites": target,
+            "exchange_acceptance": float(acc.sum() / max(att.sum(), 1)),
+            "single_lattice_kernels_value": single_value,
+            "speedup_vs_single_lattice_kernels": value / single_value,
+            "launches_per_step": 2 * rounds_per_step}
+
+
+def measure_differentiation(dev, sincos, therm=10000, meas=100000):
+    """The differentiated workload: 41 chains (beta 0.90 .. 1.30) of L=256, therm +
+    meas sweeps in one batch, then the backward kernel over the device series."""
+    import torch
+    from paper_0811_2111_gb300 import workloads as WL
+    from paper_0811_2111_gb300.autograd import chain_averages
+
+    betas = torch.tensor(WL.DIFF_BETAS, dtype=torch.float64, device=dev, requires_grad=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e, u = chain_averages(betas, WL.DIFF_L, WL.DIFF_SEED, therm, meas, sweeps_per_round=1000,
+                          sincos=sincos)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    (g,) = torch.autograd.grad(e.sum(), betas)
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    updates = len(WL.DIFF_BETAS) * WL.DIFF_L ** 2 * (therm + meas)
+    gb = g.detach().cpu().numpy()
+    b = np.array(WL.DIFF_BETAS)
+    cv = -(b ** 2) * gb
+    return {"workload": f"xy_diff_L{WL.DIFF_L}_41beta_{therm}+{meas}sweeps", "value":
+            updates / (t1 - t0), "unit": UNIT, "forward_s": t1 - t0, "backward_ms": 1e3 * (t2 - t1),
+            "specific_heat_peak": {"beta": float(b[int(np.argmax(cv))]), "c_v": float(cv.max())},
+            "timing": "wall clock around forward (chains + series kept on the device) and "
+                      "backward (FP64 covariance kernel)"}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -254,6 +350,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.build()
+    if args.workload == "batch":
+        return run_batch_line(args, dev, world, rank)
 
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
@@ -359,6 +457,10 @@ def run_ours(args):
                          f"({dt:.1f} s), OpenMP over the sites of one colour"}
 
     launches = args.steps * (1 + (1 if fused else 2) * w.sweeps)
+    extra = None
+    if not args.no_extra and world == 1:
+        extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
+                 "differentiation": measure_differentiation(dev, args.sincos)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -370,9 +472,34 @@ def run_ours(args):
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks,
+        "clocks": clocks, "other_workloads": extra,
     }
     lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batch_line(args, dev, world, rank):
+    """Main line for --workload batch (replicas of the whole batch with N > 1)."""
+    import torch
+    sampler = ClockSampler(str(dev.index or 0))
+    barrier(world)
+    sampler.start()
+    r = measure_batch(dev, args.steps, max(3, args.warmup), args.sincos)
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(r["ms_per_step"] * args.steps, world, dev)
+    value = r["sites"] * r["sweeps_per_step"] * args.steps * world / (total_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": r["workload"], "sincos": args.sincos,
+                                            "l2": "flushed before every timed step (256 MiB write)",
+                                            "parallelism": f"replicas x{world}"},
+            "batch": r, "gpu_launches": r["launches_per_step"] * args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

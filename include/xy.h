@@ -256,6 +256,18 @@ xy_status xy_batch_exchange_stats(xy_batch *b, int32_t *n_slots, int32_t *slot_l
 /* Angles of one lattice in natural order (L*L floats; synchronizes). */
 xy_status xy_batch_get_state(xy_batch *b, int32_t lattice, float *host_angles);
 xy_status xy_batch_synchronize(xy_batch *b);
+
+/* Series statistics and beta derivatives of every lattice of a batch over
+ * records [first, first + count), written to device memory d_out as
+ * double[n][XY_STATS_FIELDS] on the batch stream (asynchronous):
+ *   [0] <e>   [1] <Upsilon>   [2] <|m|>
+ *   [3] d<e>/dbeta       = -cov(e_s, E_s)
+ *   [4] d<Upsilon>/dbeta = -cov(Upsilon_s, E_s) - J^2 <Ix^2 + Iy^2> / (2N)
+ *   [5] -cov(Upsilon_s, E_s) alone   [6] var(E_s)/N (= c_v / beta^2)   [7] count
+ * with E_s = -J C_s; beta must not change inside the window (no exchange).
+ * FP64 throughout, one CTA per lattice, deterministic order. */
+#define XY_STATS_FIELDS 8
+xy_status xy_batch_series_stats(xy_batch *b, int64_t first, int64_t count, double *d_out);
 xy_status xy_batch_destroy(xy_batch *b);          /* NULL-safe */
 const char *xy_batch_last_error(const xy_batch *b);
 

@@ -204,3 +204,23 @@ def pt_run(Lx, Ly, betas, rounds, sweeps_per_round, seed, lattice_id0=0, J=1.0, 
     if r != 0:
         raise ValueError("oracle parallel-tempering run failed")
     return rec
+
+
+def beta_derivatives(sums, N, beta, J=1.0):
+    """Averages and beta derivatives of one fixed-beta chain from its per-sweep sums.
+
+    sums: (n, >=3) array of C, Ix, Iy per sweep.  From <O> = sum O e^{-beta E}/Z,
+    d<O>/dbeta = <dO/dbeta> - cov(O, E) with E = -J C; for e = E/N the first term
+    vanishes, for Upsilon = (J C - beta J^2 (Ix^2 + Iy^2))/(2N) it is
+    -J^2 <Ix^2 + Iy^2>/(2N).  Returns dict(e, upsilon, de, dupsilon, varE_over_N)."""
+    sums = np.asarray(sums, np.float64)
+    Cb, Ix, Iy = sums[:, 0], sums[:, 1], sums[:, 2]
+    E = -J * Cb
+    e = E / N
+    jj = Ix * Ix + Iy * Iy
+    ups = (J * Cb - beta * J * J * jj) / (2.0 * N)
+    dE = E - E.mean()
+    return {"e": e.mean(), "upsilon": ups.mean(),
+            "de": -np.mean((e - e.mean()) * dE),
+            "dupsilon": -np.mean((ups - ups.mean()) * dE) - J * J * jj.mean() / (2.0 * N),
+            "varE_over_N": np.mean(dE * dE) / N}

@@ -54,6 +54,7 @@ class xy_batch_params(C.Structure):
 
 
 XY_BATCH_MAX_L = 256
+XY_STATS_FIELDS = 8
 
 _lib = None
 
@@ -102,6 +103,7 @@ def lib():
         "xy_batch_exchange_stats": (st, [P, C.POINTER(C.c_int32), P, P, P]),
         "xy_batch_get_state": (st, [P, C.c_int32, P]),
         "xy_batch_synchronize": (st, [P]),
+        "xy_batch_series_stats": (st, [P, C.c_int64, C.c_int64, P]),
         "xy_batch_destroy": (st, [P]),
         "xy_batch_last_error": (C.c_char_p, [P]),
         "xy_noalloc_last_error": (C.c_char_p, []),
@@ -285,3 +287,7 @@ def xy_batch_synchronize(b):
 
 def xy_batch_destroy(b):
     batch_check(lib().xy_batch_destroy(b))
+
+
+def xy_batch_series_stats(b, first, count, d_out_ptr):
+    batch_check(lib().xy_batch_series_stats(b, first, count, d_out_ptr), b)

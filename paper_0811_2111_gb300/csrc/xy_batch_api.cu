@@ -603,6 +603,23 @@ xy_status xy_batch_get_state(xy_batch* b, int32_t lattice, float* host_angles) {
   return XY_OK;
 }
 
+xy_status xy_batch_series_stats(xy_batch* b, int64_t first, int64_t count, double* d_out) {
+  xy_status st = check_batch(b);
+  if (st != XY_OK) return st;
+  if (!d_out || first < 0 || count < 1 || first + count > b->rec_count)
+    return bfail(b, XY_EINVAL, "xy_batch_series_stats: bad window or NULL output");
+  xyk::StatsArgs a;
+  a.records = b->d_rec;
+  a.stride = b->rec_cap;
+  a.first = first;
+  a.count = count;
+  a.L = b->d_L;
+  a.J = b->p.J;
+  a.out = d_out;
+  B_CUDA(b, xyk::launch_series_stats(a, b->n, b->stream), "xy_batch_series_stats");
+  return XY_OK;
+}
+
 xy_status xy_batch_synchronize(xy_batch* b) {
   xy_status st = check_batch(b);
   if (st != XY_OK) return st;

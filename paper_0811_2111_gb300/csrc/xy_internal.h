@@ -107,6 +107,19 @@ cudaError_t launch_batch_round(int sincos_mode, int reduce_mode, const BatchArgs
                                cudaStream_t stream);
 cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
 
+// ---- series statistics / beta derivatives (xy_stats.cu) ----
+constexpr int kStatsFields = 8;
+struct StatsArgs {
+  const xy_record* records;   // [chains][stride]
+  int64_t stride;
+  int64_t first;              // first record of the window
+  int64_t count;              // records in the window (> 0)
+  const int32_t* L;           // [chains] device
+  double J;
+  double* out;                // [chains][kStatsFields] device
+};
+cudaError_t launch_series_stats(const StatsArgs& a, int n_chains, cudaStream_t stream);
+
 // Red (colour 0) then black (colour 1) half-sweep; the black one also adds
 // the sweep's bond/spin sums to *rec.  sincos_mode / reduce_mode as in xy.h.
 cudaError_t launch_half_sweep(int colour, int sincos_mode, int reduce_mode,

@@ -224,6 +224,13 @@ class Batch:
     def records_device(self):
         return X.xy_batch_records_device(self.b)
 
+    def series_stats(self, first, count):
+        """Device tensor (n, 8) float64 of xy_batch_series_stats (see include/xy.h)."""
+        torch = _torch()
+        out = torch.empty((self.n, X.XY_STATS_FIELDS), dtype=torch.float64, device=self.device)
+        X.xy_batch_series_stats(self.b, int(first), int(count), C.c_void_p(out.data_ptr()))
+        return out
+
     def synchronize(self):
         X.xy_batch_synchronize(self.b)
 
