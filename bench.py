@@ -317,18 +317,54 @@ def measure_differentiation(dev, sincos, therm=10000, meas=100000):
                           sincos=sincos)
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
+    stream = torch.cuda.current_stream(dev)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
     (g,) = torch.autograd.grad(e.sum(), betas)
+    b1.record(stream)
     torch.cuda.synchronize(dev)
     t2 = time.perf_counter()
+    backward_device_ms = b0.elapsed_time(b1)
     updates = len(WL.DIFF_BETAS) * WL.DIFF_L ** 2 * (therm + meas)
     gb = g.detach().cpu().numpy()
     b = np.array(WL.DIFF_BETAS)
     cv = -(b ** 2) * gb
     return {"workload": f"xy_diff_L{WL.DIFF_L}_41beta_{therm}+{meas}sweeps", "value":
             updates / (t1 - t0), "unit": UNIT, "forward_s": t1 - t0, "backward_ms": 1e3 * (t2 - t1),
+            "backward_device_ms": backward_device_ms,
             "specific_heat_peak": {"beta": float(b[int(np.argmax(cv))]), "c_v": float(cv.max())},
             "timing": "wall clock around forward (chains + series kept on the device) and "
                       "backward (FP64 covariance kernel)"}
+
+
+def measure_precision(dev, sweeps=200):
+    """The precision workload: L=16384 (1 GiB of angles), beta=1.12, seed 7,
+    `sweeps` sweeps per variant; updates/s of each sincos / reduction variant."""
+    import torch
+    from paper_0811_2111_gb300 import workloads as WL
+    from paper_0811_2111_gb300.lattice import Lattice
+
+    w = WL.HUGE
+    out = {"workload": w.name, "unit": UNIT, "variants": {}}
+    for sincos, reduce in (("accurate", "fp64"), ("fast", "fp64"), ("libm", "fp64"),
+                           ("accurate", "compensated")):
+        with Lattice(w.L, w.beta, w.seed, sincos=sincos, reduce=reduce, device=dev) as lat:
+            lat.reserve(sweeps + 3)
+            lat.sweep(3)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.sweep(sweeps)
+            e1.record(lat.stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            obs = lat.observables(3, sweeps)
+        out["variants"][f"{sincos}/{reduce}"] = {
+            "value": w.sites * sweeps / (ms * 1e-3), "ms_per_sweep": ms / sweeps,
+            "e_last": float(obs["e"][-1]), "upsilon_last": float(obs["upsilon"][-1])}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -460,7 +496,8 @@ def run_ours(args):
     extra = None
     if not args.no_extra and world == 1:
         extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
-                 "differentiation": measure_differentiation(dev, args.sincos)}
+                 "differentiation": measure_differentiation(dev, args.sincos),
+                 "precision": measure_precision(dev)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,

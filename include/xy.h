@@ -265,7 +265,8 @@ xy_status xy_batch_synchronize(xy_batch *b);
  *   [4] d<Upsilon>/dbeta = -cov(Upsilon_s, E_s) - J^2 <Ix^2 + Iy^2> / (2N)
  *   [5] -cov(Upsilon_s, E_s) alone   [6] var(E_s)/N (= c_v / beta^2)   [7] count
  * with E_s = -J C_s; beta must not change inside the window (no exchange).
- * FP64 throughout, one CTA per lattice, deterministic order. */
+ * FP64 throughout (moments shifted by the window's first sample), the series
+ * cut into segments across CTAs, sums in a fixed order (deterministic). */
 #define XY_STATS_FIELDS 8
 xy_status xy_batch_series_stats(xy_batch *b, int64_t first, int64_t count, double *d_out);
 xy_status xy_batch_destroy(xy_batch *b);          /* NULL-safe */

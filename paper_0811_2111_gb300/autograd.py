@@ -46,8 +46,6 @@ class XYChain(torch.autograd.Function):
             g = g + grad_e.to(dev, torch.float64) * stats[:, 3]
         if grad_u is not None:
             g = g + grad_u.to(dev, torch.float64) * stats[:, 4]
-        ctx.batch.close()
-        ctx.batch = None
         return g.to(ctx.beta_device), None, None, None, None, None, None, None, None
 
 

@@ -76,6 +76,7 @@ struct xy_batch {
   unsigned long long* d_acc = nullptr;
   unsigned long long* d_att = nullptr;
   float* d_scratch = nullptr;
+  double* d_partials = nullptr;   // series-statistics scratch
   // host shadows
   std::vector<int64_t> offset;
   std::vector<xyk::BatchBand> bands;
@@ -142,7 +143,8 @@ void free_all(xy_batch* b) {
   b->graph = nullptr;
   void* ptrs[] = {b->d_theta, b->d_offset, b->d_L, b->d_beta, b->d_bands, b->d_rec,
                   b->d_counters, b->d_pair_ladder, b->d_pair_pos, b->d_ladder_start,
-                  b->d_pos_lattice, b->d_pos_beta, b->d_acc, b->d_att, b->d_scratch};
+                  b->d_pos_lattice, b->d_pos_beta, b->d_acc, b->d_att, b->d_scratch,
+                  b->d_partials};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
@@ -435,6 +437,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   alloc((void**)&b->d_acc, sizeof(unsigned long long) * b->n_slots);
   alloc((void**)&b->d_att, sizeof(unsigned long long) * b->n_slots);
   alloc((void**)&b->d_scratch, sizeof(float) * (size_t)maxN);
+  alloc((void**)&b->d_partials, sizeof(double) * (size_t)b->n * xyk::kMaxSegments * xyk::kPartials);
   if (e != cudaSuccess) {
     bmsg("xy_batch_create: %s: %s", step, cudaGetErrorString(e));
     return fail_create(e == cudaErrorMemoryAllocation ? XY_ENOMEM : XY_ECUDA);
@@ -616,6 +619,7 @@ xy_status xy_batch_series_stats(xy_batch* b, int64_t first, int64_t count, doubl
   a.L = b->d_L;
   a.J = b->p.J;
   a.out = d_out;
+  a.partials = b->d_partials;
   B_CUDA(b, xyk::launch_series_stats(a, b->n, b->stream), "xy_batch_series_stats");
   return XY_OK;
 }

@@ -109,6 +109,8 @@ cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
 
 // ---- series statistics / beta derivatives (xy_stats.cu) ----
 constexpr int kStatsFields = 8;
+constexpr int kPartials = 8;          // moment sums per segment
+constexpr int kMaxSegments = 64;      // segments per chain
 struct StatsArgs {
   const xy_record* records;   // [chains][stride]
   int64_t stride;
@@ -117,6 +119,7 @@ struct StatsArgs {
   const int32_t* L;           // [chains] device
   double J;
   double* out;                // [chains][kStatsFields] device
+  double* partials;           // scratch [chains][kMaxSegments][kPartials] device
 };
 cudaError_t launch_series_stats(const StatsArgs& a, int n_chains, cudaStream_t stream);
 

@@ -10,9 +10,10 @@
 //     Upsilon_s = (J C_s - beta J^2 (Ix_s^2 + Iy_s^2)) / (2N)
 // the explicit term is -J^2 <Ix^2 + Iy^2> / (2N).
 //
-// One CTA per chain; two passes over the series (means, then centred
-// products), all sums in FP64 (per thread in series order, then a fixed
-// shared-memory tree), so results are deterministic.
+// The series of each chain is cut into up to kMaxSegments segments, one CTA
+// each (so all SMs share GB300's narrow FP64 pipes); every sum is FP64 in a
+// fixed order (per thread in series order, a fixed shared-memory tree, the
+// segments in order), so results are deterministic.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,55 +55,80 @@ __device__ __forceinline__ Sample sample(const xy_record& r, double N, double J)
   return s;
 }
 
-__global__ void __launch_bounds__(kThreads) k_series_stats(StatsArgs a) {
+// Pass 1: segment `blockIdx.y` of chain `blockIdx.x` accumulates moments of
+// the samples shifted by the window's first sample (K), which keeps the
+// one-pass covariance free of cancellation: per segment
+//   sums of dE, dE^2, de, de dE, du, du dE, jj, m   (dX = X - K_X).
+__global__ void __launch_bounds__(kThreads) k_series_partials(StatsArgs a) {
   __shared__ double sh[kThreads];
-  const int chain = blockIdx.x;
+  const int chain = blockIdx.x, seg = blockIdx.y, nseg = gridDim.y;
+  const xy_record* rec = a.records + (size_t)chain * a.stride + a.first;
+  const double N = (double)a.L[chain] * (double)a.L[chain];
+  const Sample k = sample(rec[0], N, a.J);
+  const int64_t n = a.count;
+  const int64_t lo = n * seg / nseg, hi = n * (seg + 1) / nseg;
+  double m[kPartials] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
+    const Sample s = sample(rec[i], N, a.J);
+    const double dE = s.E - k.E, de = s.e - k.e, du = s.ups - k.ups;
+    m[0] += dE;
+    m[1] += dE * dE;
+    m[2] += de;
+    m[3] += de * dE;
+    m[4] += du;
+    m[5] += du * dE;
+    m[6] += s.jj;
+    m[7] += s.m;
+  }
+  double* out = a.partials + ((size_t)chain * nseg + seg) * kPartials;
+  for (int j = 0; j < kPartials; ++j) {
+    const double t = block_sum(m[j], sh);
+    if (threadIdx.x == 0) out[j] = t;
+  }
+}
+
+// Pass 2: one thread per chain adds the segments in order and forms the
+// means, covariances and derivatives.
+__global__ void k_series_combine(StatsArgs a, int n_chains, int nseg) {
+  const int chain = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chain >= n_chains) return;
   const xy_record* rec = a.records + (size_t)chain * a.stride + a.first;
   const double N = (double)a.L[chain] * (double)a.L[chain];
   const double J = a.J;
-  const int64_t n = a.count;
-  double sE = 0, se = 0, su = 0, sj = 0, sm = 0;
-  for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-    const Sample s = sample(rec[i], N, J);
-    sE += s.E;
-    se += s.e;
-    su += s.ups;
-    sj += s.jj;
-    sm += s.m;
-  }
-  const double inv = 1.0 / (double)n;
-  const double mE = block_sum(sE, sh) * inv, me = block_sum(se, sh) * inv;
-  const double mu = block_sum(su, sh) * inv, mj = block_sum(sj, sh) * inv;
-  const double mm = block_sum(sm, sh) * inv;
-  double cEE = 0, ceE = 0, cuE = 0;
-  for (int64_t i = threadIdx.x; i < n; i += kThreads) {
-    const Sample s = sample(rec[i], N, J);
-    const double dE = s.E - mE;
-    cEE += dE * dE;
-    ceE += (s.e - me) * dE;
-    cuE += (s.ups - mu) * dE;
-  }
-  const double varE = block_sum(cEE, sh) * inv;
-  const double cov_eE = block_sum(ceE, sh) * inv;
-  const double cov_uE = block_sum(cuE, sh) * inv;
-  if (threadIdx.x == 0) {
-    double* o = a.out + (size_t)chain * kStatsFields;
-    o[0] = me;                                  // <e>
-    o[1] = mu;                                  // <Upsilon>
-    o[2] = mm;                                  // <|m|>
-    o[3] = -cov_eE;                             // d<e>/dbeta
-    o[4] = -cov_uE - J * J * mj / (2.0 * N);    // d<Upsilon>/dbeta
-    o[5] = -cov_uE;                             // covariance part alone
-    o[6] = varE / N;                            // var(E)/N = c_v / beta^2
-    o[7] = (double)n;
-  }
+  const Sample k = sample(rec[0], N, J);
+  double m[kPartials] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int sg = 0; sg < nseg; ++sg)
+    for (int j = 0; j < kPartials; ++j)
+      m[j] += a.partials[((size_t)chain * nseg + sg) * kPartials + j];
+  const double inv = 1.0 / (double)a.count;
+  const double mdE = m[0] * inv, mde = m[2] * inv, mdu = m[4] * inv;
+  const double varE = m[1] * inv - mdE * mdE;
+  const double cov_eE = m[3] * inv - mde * mdE;
+  const double cov_uE = m[5] * inv - mdu * mdE;
+  const double mj = m[6] * inv;
+  double* o = a.out + (size_t)chain * kStatsFields;
+  o[0] = k.e + mde;                           // <e>
+  o[1] = k.ups + mdu;                         // <Upsilon>
+  o[2] = m[7] * inv;                          // <|m|>
+  o[3] = -cov_eE;                             // d<e>/dbeta
+  o[4] = -cov_uE - J * J * mj / (2.0 * N);    // d<Upsilon>/dbeta
+  o[5] = -cov_uE;                             // covariance part alone
+  o[6] = varE / N;                            // var(E)/N = c_v / beta^2
+  o[7] = (double)a.count;
 }
 
 }  // namespace
 
 cudaError_t launch_series_stats(const StatsArgs& a, int n_chains, cudaStream_t stream) {
-  if (n_chains <= 0 || a.count <= 0) return cudaErrorInvalidValue;
-  k_series_stats<<<n_chains, kThreads, 0, stream>>>(a);
+  if (n_chains <= 0 || a.count <= 0 || !a.partials) return cudaErrorInvalidValue;
+  // enough segments to fill the GPU, at least a few hundred samples each
+  int nseg = (int)((a.count + 511) / 512);
+  if (nseg > kMaxSegments) nseg = kMaxSegments;
+  if (nseg < 1) nseg = 1;
+  k_series_partials<<<dim3(n_chains, nseg), kThreads, 0, stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_series_combine<<<(n_chains + 63) / 64, 64, 0, stream>>>(a, n_chains, nseg);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,71 @@
+"""Precision variants against the FP64 oracle on the identically seeded L=512
+lattice (beta=1.12, seed 7): the error of each sincos path and reduction is
+measured and bounded (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import ANGLE_TOL, compare_record, lockstep_sweep, record_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300.lattice import Lattice  # noqa: E402
+from paper_0811_2111_gb300 import workloads as WL  # noqa: E402
+
+BANDS = {"accurate": 1e-6, "libm": 1e-6, "fast": 2e-5}
+
+
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("libm", "fp64"),
+                                           ("fast", "fp64"), ("accurate", "compensated"),
+                                           ("fast", "compensated")])
+def test_precision_variant_errors_at_L512(sincos, reduce):
+    w = WL.PRECISION_CHECK
+    L, n = w.L, 20
+    fast = sincos == "fast"
+    stats = dict(out_1e6=0, out_band=0, in_band=0, angle=0.0, rec=np.zeros(5))
+    with Lattice(L, w.beta, w.seed, sincos=sincos, reduce=reduce) as lat:
+        before, t0 = lat.state()
+        for i in range(n):
+            lat.sweep(1)
+            after, _ = lat.state()
+            for band, key in ((1e-6, "out_1e6"), (BANDS[sincos], "out_band")):
+                red, blk = lockstep_sweep(before, after, L, w.beta, w.seed, t0 + i, band=band)
+                stats[key] += red.out_band_mismatch + blk.out_band_mismatch
+            stats["in_band"] += red.in_band + blk.in_band
+            stats["angle"] = max(stats["angle"], red.max_angle_err, blk.max_angle_err)
+            obs = lat.observables(i, 1)
+            diff, _ = compare_record({k: obs[k][0] for k in obs}, after, L)
+            stats["rec"] = np.maximum(stats["rec"], diff)
+            before = after
+    print(f"{sincos}/{reduce}: decisions outside 1e-6 band differing {stats['out_1e6']}, "
+          f"outside the {BANDS[sincos]:g} band {stats['out_band']}, max angle error "
+          f"{stats['angle']:.2e}, max |record - FP64| (C, Ix, Iy, Mx, My) {stats['rec']}")
+    assert stats["out_band"] == 0
+    assert stats["angle"] <= ANGLE_TOL
+    assert stats["rec"].max() <= record_tolerance(L * L, fast)
+
+
+def test_free_running_observables_vs_oracle_L512():
+    """Identically seeded free-running chains: GPU (accurate) and the FP64 oracle follow
+    the same trajectory until FP32 rounding flips a decision; their 200-sweep averages
+    of e, |m|, Upsilon are reported and agree to the statistical level."""
+    w = WL.PRECISION_CHECK
+    with Lattice(w.L, w.beta, w.seed) as lat:
+        lat.sweep(w.sweeps)
+        g = lat.observables()
+    rec, _ = oracle.run(w.L, w.L, w.beta, w.sweeps, seed=w.seed, nthreads=8)
+    e, m, u = oracle.observables(rec[:, :5], w.L * w.L, w.beta)
+    first_div = int(np.argmax(np.abs(g["e"] - e) > 1e-6)) if np.any(np.abs(g["e"] - e) > 1e-6) else w.sweeps
+    print(f"free-running L=512: per-sweep e identical to 1e-6 for the first {first_div} sweeps; "
+          f"mean e gpu {g['e'][100:].mean():.6f} oracle {e[100:].mean():.6f}; "
+          f"Upsilon gpu {g['upsilon'][100:].mean():.5f} oracle {u[100:].mean():.5f}")
+    assert first_div >= 1
+    assert abs(g["e"][100:].mean() - e[100:].mean()) < 5e-3
+    assert abs(g["abs_m"][100:].mean() - m[100:].mean()) < 5e-2
