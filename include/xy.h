@@ -67,7 +67,8 @@ enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
  *   XY_ALGO_FUSED     one launch per sweep (both colours + measure), the state
  *                     ping-pongs between the caller's buffer and a library
  *                     buffer of the same size (8 B moved per update);
- *   XY_ALGO_TWO_PASS  one launch per colour, in place (12 B per update). */
+ *   XY_ALGO_TWO_PASS  one launch per colour, in place (12 B per update).
+ * Both make bit-identical decisions. */
 enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2 };
 enum { XY_REDUCE_FP64 = 0, XY_REDUCE_COMPENSATED = 1 };
 

@@ -395,8 +395,9 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
       nxt = t;
     }
     if (cur != c->d_theta) {
-      const size_t bytes = (size_t)c->p.L * (size_t)c->p.L * sizeof(float);
-      XY_CUDA(c, cudaMemcpyAsync(c->d_theta, cur, bytes, cudaMemcpyDeviceToDevice, c->stream),
+      const size_t N = (size_t)c->p.L * (size_t)c->p.L;
+      XY_CUDA(c, cudaMemcpyAsync(c->d_theta, cur, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                 c->stream),
               "xy_sweep: copy back");
     }
   } else {

@@ -129,13 +129,15 @@ __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out)
   pc = __fmaf_rn(r2, pc, 4.16666666666666667e-02f);
   pc = __fmaf_rn(r2, pc, -0.5f);
   const float cr = __fmaf_rn(r2, pc, 1.0f);
-  // quadrant: odd q swaps sin and cos; sin negative for q mod 4 in {2, 3},
-  // cos negative for q mod 4 in {1, 2}
+  // quadrant: odd q swaps sin and cos; sin is negative for q mod 4 in {2, 3}
+  // (bit 1 of q) and cos for q mod 4 in {1, 2} (bit 1 of q + 1); both sign
+  // masks come from q << 30 (bit 31 = bit 1 of q).
+  const uint32_t qs = (uint32_t)q << 30;
   const bool swap = (q & 1) != 0;
   const float s0 = swap ? cr : sr;
   const float c0 = swap ? sr : cr;
-  *s_out = __int_as_float(__float_as_int(s0) ^ ((q & 2) << 30));
-  *c_out = __int_as_float(__float_as_int(c0) ^ (((q + 1) & 2) << 30));
+  *s_out = __uint_as_float(__float_as_uint(s0) ^ (qs & 0x80000000u));
+  *c_out = __uint_as_float(__float_as_uint(c0) ^ ((qs + 0x40000000u) & 0x80000000u));
 }
 
 // Precision switch of the fused kernels: 0 = the polynomial above with CUDA's
@@ -194,12 +196,11 @@ template <int MODE>
 __device__ __forceinline__ SiteResult metropolis_step(float t, float c0, float s0, float Sc,
                                                       float Ss, uint32_t w0, uint32_t w1,
                                                       float K, float delta) {
-  float tp = __fmaf_rn(delta, sym24(w0), t);
-  if (tp < 0.f) {
-    tp = __fadd_rn(tp, kTwoPi);
-  } else if (tp >= kTwoPi) {
-    tp = __fsub_rn(tp, kTwoPi);
-  }
+  // wrap once into [0, 2 pi): both candidates are formed and selected on the
+  // unwrapped value (no branches)
+  const float raw = __fmaf_rn(delta, sym24(w0), t);
+  const float up = __fadd_rn(raw, kTwoPi), down = __fsub_rn(raw, kTwoPi);
+  const float tp = raw < 0.f ? up : (raw >= kTwoPi ? down : raw);
   float s1, c1;
   unit_vector<MODE>(tp, &s1, &c1);
   // X = -dE / J = (cos t' - cos t) Sc + (sin t' - sin t) Ss

@@ -38,9 +38,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kSRows = kTileRows + 4;        // rows y0-2 .. y0+33
 constexpr int kSCols = kTileK + 8;           // plane cols k0-4 .. k0+67 (k0-1 .. k0+64 used)
-constexpr int kBodyGroups = kTileK / 4;      // float4 groups of the tile columns
-constexpr int kStageItems = kBodyGroups + 1; // + one item for the two halo columns
 constexpr int kRing = 2 * kTileK + kTileRows;
+constexpr int kStageRowsTotal = kSRows + (kSRows - 2);   // black rows + red rows staged
 
 constexpr size_t kThBytes = sizeof(float) * 2 * kSRows * kSCols;
 constexpr size_t kCsBytes = sizeof(float2) * 2 * kSRows * kSCols;
@@ -59,7 +58,7 @@ __device__ __forceinline__ int wrap_once(int v, int n) {
 
 // The four neighbour unit vectors of the two sites at stage columns c0, c0+1
 // of row r in plane `nb` (the other colour), where a site at column c has its
-// same-row neighbours at c+q-1 and c+q.  A = (c0, c0+1) as one 16-byte load.
+// same-row neighbours at c+q-1 and c+q.
 struct PairNeighbours {
   float Sc[2], Ss[2];
   float2 l[2], r[2], d[2], u[2];
@@ -67,15 +66,15 @@ struct PairNeighbours {
 
 __device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, int q,
                                                 PairNeighbours& n) {
-  const float4 A = *reinterpret_cast<const float4*>(&nb[r][c0]);
-  const float2 extra = nb[r][q ? c0 + 2 : c0 - 1];
+  // same-row neighbours of the two sites: columns c0+q-1, c0+q, c0+q+1 (q is
+  // uniform across the warp, so these are plain offset loads, no selects)
+  const float2 a = nb[r][c0 + q - 1], m = nb[r][c0 + q], b = nb[r][c0 + q + 1];
   const float4 D = *reinterpret_cast<const float4*>(&nb[r - 1][c0]);
   const float4 U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
-  const float2 a0 = make_float2(A.x, A.y), a1 = make_float2(A.z, A.w);
-  n.l[0] = q ? a0 : extra;
-  n.r[0] = q ? a1 : a0;
-  n.l[1] = q ? a1 : a0;
-  n.r[1] = q ? extra : a1;
+  n.l[0] = a;
+  n.r[0] = m;
+  n.l[1] = m;
+  n.r[1] = b;
   n.d[0] = make_float2(D.x, D.y);
   n.d[1] = make_float2(D.z, D.w);
   n.u[0] = make_float2(U.x, U.y);
@@ -117,58 +116,60 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
   const size_t plane = (size_t)L * (size_t)W;
 
   // ---- stage both planes (angle + unit vector) ----
-  // items: (plane, row, group); groups 0..15 are the tile's float4 columns,
-  // group 16 the two halo columns k0-1 and k0+64 (rows 1..34 only).  All of a
-  // thread's loads are issued before any of its sincos so that their latencies
-  // overlap instead of adding up.
-  constexpr int kItems = 2 * kSRows * kStageItems;
-  constexpr int kPerThread = (kItems + kThreads - 1) / kThreads;
-  float4 v[kPerThread];
+  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
+  // (stage rows 1..34; red is never needed two rows out).  Each warp takes two
+  // rows per step, 16 lanes per row, one float4 of the tile body per lane (so
+  // the addressing is a shift and an add); the two halo columns k0-1 and
+  // k0+64 (rows 1..34) are a separate pass.
+  {
+    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
+    const int half = lane_s >> 4, g = lane_s & 15;
+    constexpr int kSteps = (kStageRowsTotal + 2 * kWarps - 1) / (2 * kWarps);
+    // all of a lane's loads first, so their latencies overlap
+    float4 v[kSteps];
 #pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
-    const int g = threadIdx.x + i * kThreads;
-    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (g >= kItems) continue;
-    const int p = g / (kSRows * kStageItems);
-    const int rem = g - p * (kSRows * kStageItems);
-    const int r = rem / kStageItems;
-    const int cg = rem - r * kStageItems;
-    if (p == 0 && (r == 0 || r == kSRows - 1)) continue;   // red is never needed 2 rows out
-    const float* row = a.src + p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
-    if (cg < kBodyGroups) {
-      v[i] = __ldg(reinterpret_cast<const float4*>(row + k0 + 4 * cg));
-    } else if (r >= 1 && r <= kSRows - 2) {
-      v[i].x = __ldg(row + wrap_once(k0 - 1, W));
-      v[i].y = __ldg(row + wrap_once(k0 + kTileK, W));
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 2 * warp_s + half + 2 * kWarps * i;
+      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rr < kStageRowsTotal) {
+        const int p = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * g;
+        v[i] = __ldg(reinterpret_cast<const float4*>(a.src + row));
+      }
     }
-  }
 #pragma unroll
-  for (int i = 0; i < kPerThread; ++i) {
-    const int g = threadIdx.x + i * kThreads;
-    if (g >= kItems) continue;
-    const int p = g / (kSRows * kStageItems);
-    const int rem = g - p * (kSRows * kStageItems);
-    const int r = rem / kStageItems;
-    const int cg = rem - r * kStageItems;
-    if (p == 0 && (r == 0 || r == kSRows - 1)) continue;
-    if (cg < kBodyGroups) {
-      const int col = 4 + 4 * cg;
-      float s0, c0, s1, c1, s2, c2, s3, c3;
-      xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
-      xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
-      xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
-      xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
-      *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
-      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-    } else if (r >= 1 && r <= kSRows - 2) {
-      float s, c;
-      xyd::unit_vector<MODE>(v[i].x, &s, &c);
-      th[p][r][3] = v[i].x;
-      cs[p][r][3] = make_float2(c, s);
-      xyd::unit_vector<MODE>(v[i].y, &s, &c);
-      th[p][r][kTileK + 4] = v[i].y;
-      cs[p][r][kTileK + 4] = make_float2(c, s);
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 2 * warp_s + half + 2 * kWarps * i;
+      if (rr < kStageRowsTotal) {
+        const int p = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const int col = 4 + 4 * g;
+        float s0, c0, s1, c1, s2, c2, s3, c3;
+        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
+        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
+        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
+        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
+        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+      }
+    }
+    // halo columns: (plane, row 1..34, side), taken by the last warps, which
+    // have one row step fewer than the first ones
+    for (int h = kThreads - 1 - threadIdx.x; h < 2 * (kSRows - 2) * 2; h += kThreads) {
+      const int p = h / ((kSRows - 2) * 2);
+      const int rem = h - p * ((kSRows - 2) * 2);
+      const int r = 1 + (rem >> 1);
+      const int side = rem & 1;
+      const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
+      const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
+      const int col = side ? kTileK + 4 : 3;
+      const float v1 = __ldg(a.src + row + kk);
+      float sv, cv;
+      xyd::unit_vector<MODE>(v1, &sv, &cv);
+      th[p][r][col] = v1;
+      cs[p][r][col] = make_float2(cv, sv);
     }
   }
   __syncthreads();
@@ -203,23 +204,29 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
     *reinterpret_cast<float2*>(a.dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
-  for (int i = threadIdx.x; i < kRing; i += kThreads) {
-    int ty, tk;
-    if (i < kTileK) {
-      ty = -1;
-      tk = i;
-    } else if (i < 2 * kTileK) {
-      ty = kTileRows;
-      tk = i - kTileK;
-    } else {
-      ty = i - 2 * kTileK;
-      tk = ((y0 + ty) & 1) ? -1 : kTileK;                  // left ring on odd rows, right on even
+  // 160 sites spread evenly over the 8 warps (20 each) so no warp idles at
+  // the barrier that follows
+  {
+    constexpr int kPerWarp = (kRing + kWarps - 1) / kWarps;
+    const int i = warp * kPerWarp + lane;
+    if (lane < kPerWarp && i < kRing) {
+      int ty, tk;
+      if (i < kTileK) {
+        ty = -1;
+        tk = i;
+      } else if (i < 2 * kTileK) {
+        ty = kTileRows;
+        tk = i - kTileK;
+      } else {
+        ty = i - 2 * kTileK;
+        tk = ((y0 + ty) & 1) ? -1 : kTileK;                // left ring on odd rows, right on even
+      }
+      const int y = wrap_once(y0 + ty, L);
+      const int k = wrap_once(k0 + tk, W);
+      const int q = y & 1;
+      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a);
     }
-    const int y = wrap_once(y0 + ty, L);
-    const int k = wrap_once(k0 + tk, W);
-    const int q = y & 1;
-    const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-    red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a);
   }
   __syncthreads();
 
@@ -246,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
         xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, a.K, a.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
     *reinterpret_cast<float2*>(dst_blk + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
+
     // red sites with the same (y, k): their spins enter M once each
     const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     float v0[5], v1[5];
