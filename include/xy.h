@@ -226,6 +226,9 @@ typedef struct {
     uint32_t lattice_id0;       /* lattice i uses lattice id lattice_id0 + i         */
     int32_t sweeps_per_round;   /* sweeps per launch (and between exchanges), >= 1   */
     int32_t target_band_sites;  /* sites per CTA band of the work plan (0: 8192)     */
+    int32_t algorithm;          /* XY_ALGO_AUTO / _FUSED: one staging and one cluster
+                                   barrier per sweep, state ping-ponged between two
+                                   buffers; XY_ALGO_TWO_PASS: in place, two of each */
 } xy_batch_params;
 
 /* Create and hot/cold-start all lattices; the plan, ladders and buffers are

@@ -50,7 +50,8 @@ class xy_batch_params(C.Structure):
                 ("ladder", C.POINTER(C.c_int32)), ("J", C.c_double), ("delta", C.c_double),
                 ("seed", C.c_uint64), ("start", C.c_int32), ("sincos_mode", C.c_int32),
                 ("reduce_mode", C.c_int32), ("lattice_id0", C.c_uint32),
-                ("sweeps_per_round", C.c_int32), ("target_band_sites", C.c_int32)]
+                ("sweeps_per_round", C.c_int32), ("target_band_sites", C.c_int32),
+                ("algorithm", C.c_int32)]
 
 
 XY_BATCH_MAX_L = 256

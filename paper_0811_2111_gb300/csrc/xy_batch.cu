@@ -148,6 +148,179 @@ __global__ void __launch_bounds__(kThreads) k_batch_round(BatchArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fused variant: one staging and one cluster barrier per sweep.
+//
+// The state ping-pongs between two buffers by sweep parity (sweep t reads
+// buffer t mod 2 and writes the other).  Per sweep a CTA stages both colours of
+// its band's rows and two halo rows above and below (angle and unit vector),
+// updates the red sites of its rows and of the ring rows just outside them
+// (those belong to the neighbouring bands, which compute them identically from
+// the same old state and counter-based words), then its black sites against
+// the new red values, writes its rows to the other buffer and meets its
+// cluster once.  The same site function, counters and measure terms as every
+// other kernel: results are bit-identical to the two-pass variant.
+// ---------------------------------------------------------------------------
+constexpr int kFusedThreads = 512;
+constexpr int kFusedWarps = kFusedThreads / 32;
+
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kFusedThreads, 2) k_batch_fused(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const BatchBand band = a.bands[blockIdx.x];
+  const bool active = band.lattice >= 0;
+  const int L = active ? a.L[band.lattice] : 2;
+  const int W = L / 2;
+  const int R = band.y_end - band.y_begin;
+  const int SR = R + 4;                                   // stage rows y_begin-2 .. y_end+1
+  const size_t nst = (size_t)SR * (size_t)W;
+  float2* cs_r = reinterpret_cast<float2*>(smem);         // red plane unit vectors
+  float2* cs_b = cs_r + nst;                              // black plane unit vectors
+  float* th_r = reinterpret_cast<float*>(cs_b + nst);     // red plane angles
+  float* th_b = th_r + nst;                               // black plane angles
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + a.cs_bytes);
+  unsigned int* cnt =
+      reinterpret_cast<unsigned int*>(smem + a.cs_bytes + sizeof(float) * kFusedWarps * 10);
+
+  const size_t plane = (size_t)L * (size_t)W;
+  const int64_t off = active ? a.offset[band.lattice] : 0;
+  const uint32_t lid = active ? a.lattice_id0 + (uint32_t)band.lattice : 0u;
+  const double beta = active ? a.beta[band.lattice] : 0.0;
+  const float K = (float)(beta * a.J);
+  xy_record* rec = active ? a.records + (size_t)band.lattice * a.rec_stride : nullptr;
+  const uint32_t uL = (uint32_t)L;
+
+  const int tx_w = W < kFusedThreads ? W : kFusedThreads;
+  const int ty_n = kFusedThreads / tx_w;
+  const int tx = threadIdx.x % tx_w;
+  const int ty = threadIdx.x / tx_w;
+  const bool lane_on = ty < ty_n;
+
+  const uint32_t sweep0 = a.counters[0];
+  for (int sw = 0; sw < a.sweeps; ++sw) {
+    const uint32_t sweep = sweep0 + (uint32_t)sw;
+    if (active) {
+      const float* src = ((sweep & 1u) ? a.theta2 : a.theta) + off;
+      float* dst = ((sweep & 1u) ? a.theta : a.theta2) + off;
+      // 1. stage both planes (red is not needed on the outermost rows).  A
+      // band spans its lattice's full width W <= 128, so a thread owns column
+      // k = tx and rows ty, ty + ty_n, ...; all of a pass's loads are issued
+      // before any sincos so that their latencies overlap.
+      if (lane_on) {
+        constexpr int kPF = 10;
+        for (int base = ty; base < SR; base += kPF * ty_n) {
+          float vb[kPF], vr[kPF];
+#pragma unroll
+          for (int i = 0; i < kPF; ++i) {
+            const int sr = base + i * ty_n;
+            vb[i] = 0.f;
+            vr[i] = 0.f;
+            if (sr < SR) {
+              const size_t g = (size_t)wrap_row(band.y_begin - 2 + sr, L) * W + tx;
+              vb[i] = __ldcg(src + plane + g);
+              if (sr > 0 && sr < SR - 1) vr[i] = __ldcg(src + g);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kPF; ++i) {
+            const int sr = base + i * ty_n;
+            if (sr < SR) {
+              const size_t idx = (size_t)sr * W + tx;
+              float s, c;
+              xyd::unit_vector<MODE>(vb[i], &s, &c);
+              th_b[idx] = vb[i];
+              cs_b[idx] = make_float2(c, s);
+              if (sr > 0 && sr < SR - 1) {
+                xyd::unit_vector<MODE>(vr[i], &s, &c);
+                th_r[idx] = vr[i];
+                cs_r[idx] = make_float2(c, s);
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // 2. red: stage rows 1 .. SR-2 (the band and its two ring rows)
+      unsigned int n_acc = 0;
+      if (lane_on) {
+        for (int sr = 1 + ty; sr <= SR - 2; sr += ty_n) {
+          const int y = wrap_row(band.y_begin - 2 + sr, L);
+          const int q = y & 1;                              // red: x = 2k + (y & 1)
+          const bool own = sr >= 2 && sr <= R + 1;
+          const float2* row = cs_b + (size_t)sr * W;
+          for (int k = tx; k < W; k += tx_w) {
+            int kl = k + q - 1, kr = k + q;
+            kl += (kl < 0) ? W : 0;
+            kr -= (kr >= W) ? W : 0;
+            const float2 l = row[kl], rt = row[kr], d = row[k - W], u = row[k + W];
+            const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+            const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+            const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+            const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+            const size_t idx = (size_t)sr * W + k;
+            const float2 o = cs_r[idx];
+            const xyd::SiteResult res =
+                xyd::metropolis_step<MODE>(th_r[idx], o.x, o.y, Sc, Ss, w.x, w.y, K, a.delta);
+            th_r[idx] = res.th;
+            cs_r[idx] = make_float2(res.c, res.s);
+            if (own) {
+              n_acc += res.accept ? 1u : 0u;
+              dst[(size_t)y * W + k] = res.th;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // 3. black: the band rows (stage rows 2 .. R+1), with the sweep sums
+      float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (lane_on) {
+        for (int sr = 2 + ty; sr <= R + 1; sr += ty_n) {
+          const int y = band.y_begin - 2 + sr;
+          const int q = (y + 1) & 1;                        // black: x = 2k + ((y + 1) & 1)
+          const float2* row = cs_r + (size_t)sr * W;
+          for (int k = tx; k < W; k += tx_w) {
+            int kl = k + q - 1, kr = k + q;
+            kl += (kl < 0) ? W : 0;
+            kr -= (kr >= W) ? W : 0;
+            const float2 l = row[kl], rt = row[kr], d = row[k - W], u = row[k + W];
+            const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+            const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+            const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+            const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+            const size_t idx = (size_t)sr * W + k;
+            const float2 o = cs_b[idx];
+            const xyd::SiteResult res =
+                xyd::metropolis_step<MODE>(th_b[idx], o.x, o.y, Sc, Ss, w.x, w.y, K, a.delta);
+            n_acc += res.accept ? 1u : 0u;
+            dst[plane + (size_t)y * W + k] = res.th;
+            const float2 m = row[k];
+            float v[5];
+            xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc, Ss,
+                               m.x, m.y, v);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+              if (RED == 0) {
+                acc[i] += v[i];
+              } else {
+                xyd::neumaier_add(acc[i], cmp[i], v[i]);
+              }
+            }
+          }
+        }
+      }
+      xyd::commit_block<kFusedWarps, RED, true>(acc, cmp, n_acc, part, cnt,
+                                                rec + sweep - a.rec_sweep0, beta,
+                                                band.y_begin == 0);
+    }
+    // every band of the lattice has written this sweep before any reads it:
+    // the cluster barrier's arrive has release and its wait acquire semantics
+    // at cluster scope, which order the global stores before the next loads
+    cluster.sync();
+  }
+}
+
 // Replica exchange after a round (one CTA).  For every candidate pair of the
 // round's parity -- ladder l, positions p and p+1 of the ladder ordered by
 // beta, p = round mod 2, round mod 2 + 2, ... -- the pair swaps its two
@@ -209,7 +382,57 @@ cudaError_t launch_round_t(const BatchArgs& a, int n_ctas, size_t smem, cudaStre
   return cudaLaunchKernelEx(&cfg, k_batch_round<MODE, RED>, a);
 }
 
+template <int MODE, int RED>
+cudaError_t launch_fused_round_t(const BatchArgs& a, int n_ctas, size_t smem, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_ctas, 1, 1);
+  cfg.blockDim = dim3(kFusedThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterSize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch_fused<MODE, RED>, a);
+}
+
+const void* fused_kernel_ptr(int sincos_mode, int reduce_mode) {
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? (const void*)k_batch_fused<0, 1> : (const void*)k_batch_fused<0, 0>;
+    case 1: return comp ? (const void*)k_batch_fused<1, 1> : (const void*)k_batch_fused<1, 0>;
+    default: return comp ? (const void*)k_batch_fused<2, 1> : (const void*)k_batch_fused<2, 0>;
+  }
+}
+
 }  // namespace
+
+size_t batch_fused_tail_bytes() {
+  return sizeof(float) * kFusedWarps * 10 + sizeof(unsigned int) * kFusedWarps;
+}
+
+cudaError_t prepare_batch_fused(int sincos_mode, int reduce_mode, size_t smem) {
+  return cudaFuncSetAttribute(fused_kernel_ptr(sincos_mode, reduce_mode),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_batch_fused(int sincos_mode, int reduce_mode, const BatchArgs& a, int n_ctas,
+                               cudaStream_t stream) {
+  if (n_ctas <= 0 || n_ctas % kClusterSize != 0 || !a.theta2) return cudaErrorInvalidValue;
+  const size_t smem = a.cs_bytes + batch_fused_tail_bytes();
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_fused_round_t<0, 1>(a, n_ctas, smem, stream)
+                        : launch_fused_round_t<0, 0>(a, n_ctas, smem, stream);
+    case 1: return comp ? launch_fused_round_t<1, 1>(a, n_ctas, smem, stream)
+                        : launch_fused_round_t<1, 0>(a, n_ctas, smem, stream);
+    default: return comp ? launch_fused_round_t<2, 1>(a, n_ctas, smem, stream)
+                         : launch_fused_round_t<2, 0>(a, n_ctas, smem, stream);
+  }
+}
 
 size_t batch_smem_bytes(int max_stage_floats2) {
   return sizeof(float2) * (size_t)max_stage_floats2 + sizeof(float) * kWarps * 10 +

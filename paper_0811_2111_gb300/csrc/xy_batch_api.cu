@@ -62,6 +62,8 @@ struct xy_batch {
   cudaStream_t capture_stream;    // private stream used only to record the graph
   // device buffers
   float* d_theta = nullptr;
+  float* d_theta2 = nullptr;      // second buffer of the fused variant
+  bool fused = true;
   int64_t* d_offset = nullptr;
   int32_t* d_L = nullptr;
   double* d_beta = nullptr;
@@ -141,7 +143,7 @@ xy_status check_batch(const xy_batch* b) {
 void free_all(xy_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
-  void* ptrs[] = {b->d_theta, b->d_offset, b->d_L, b->d_beta, b->d_bands, b->d_rec,
+  void* ptrs[] = {b->d_theta, b->d_theta2, b->d_offset, b->d_L, b->d_beta, b->d_bands, b->d_rec,
                   b->d_counters, b->d_pair_ladder, b->d_pair_pos, b->d_ladder_start,
                   b->d_pos_lattice, b->d_pos_beta, b->d_acc, b->d_att, b->d_scratch,
                   b->d_partials};
@@ -154,7 +156,15 @@ void free_all(xy_batch* b) {
 // Bands: each lattice is cut into nb bands of whole rows (nb <= cluster size),
 // about target_sites sites per band; lattices are packed first-fit (largest
 // first) into clusters of kClusterSize CTAs, padded with idle CTAs.
-constexpr size_t kStageBudget = 96 * 1024;   // staging bytes per CTA: two CTAs fit an SM
+// Shared memory a CTA may use for its band: two CTAs must fit one SM (228 KB).
+constexpr size_t kStageBudget = 96 * 1024;          // two-pass: (r + 2) * L/2 unit vectors
+constexpr size_t kFusedStageBudget = 108 * 1024;    // fused: (r + 4) * L/2 * (2 angles + 2 vectors)
+
+size_t band_bytes(bool fused, int rows, int L) {
+  const size_t W = (size_t)(L / 2);
+  return fused ? (size_t)(rows + 4) * W * 2 * (sizeof(float) + sizeof(float2))
+               : (size_t)(rows + 2) * W * sizeof(float2);
+}
 
 void make_plan(xy_batch* b, int target_sites) {
   const int CS = xyk::kClusterSize;
@@ -163,8 +173,10 @@ void make_plan(xy_batch* b, int target_sites) {
   for (int i = 0; i < b->n; ++i) {
     const int Li = b->L[i];
     int nb = (int)((int64_t)Li * Li / std::max(target_sites, 1));
-    // a band of r rows stages (r + 2) * L/2 unit vectors
-    const int rows_max = (int)(kStageBudget / (sizeof(float2) * (size_t)(Li / 2))) - 2;
+    // the largest band that fits the per-CTA shared-memory budget
+    const size_t budget = b->fused ? kFusedStageBudget : kStageBudget;
+    int rows_max = 1;
+    while (rows_max < Li && band_bytes(b->fused, rows_max + 1, Li) <= budget) ++rows_max;
     nb = std::max(nb, (Li + rows_max - 1) / rows_max);
     nb = std::max(1, std::min(nb, std::min(CS, Li / 2)));
     const int r = (Li + nb - 1) / nb;
@@ -204,11 +216,9 @@ void make_plan(xy_batch* b, int target_sites) {
     while ((int)c.size() < CS) c.push_back(xyk::BatchBand{-1, 0, 0, 0});
     for (auto& band : c) {
       b->bands.push_back(band);
-      if (band.lattice >= 0) {
-        const size_t need = sizeof(float2) * (size_t)(band.y_end - band.y_begin + 2) *
-                            (size_t)(b->L[band.lattice] / 2);
-        b->cs_bytes = std::max(b->cs_bytes, need);
-      }
+      if (band.lattice >= 0)
+        b->cs_bytes = std::max(b->cs_bytes,
+                               band_bytes(b->fused, band.y_end - band.y_begin, b->L[band.lattice]));
     }
   }
   b->cs_bytes = (b->cs_bytes + 15) & ~(size_t)15;
@@ -240,6 +250,7 @@ xy_status grow(xy_batch* b, int64_t need) {
 xyk::BatchArgs round_args(const xy_batch* b) {
   xyk::BatchArgs a;
   a.theta = b->d_theta;
+  a.theta2 = b->d_theta2;
   a.offset = b->d_offset;
   a.L = b->d_L;
   a.beta = b->d_beta;
@@ -280,8 +291,10 @@ xyk::ExchangeArgs exchange_args(const xy_batch* b) {
 }
 
 cudaError_t enqueue_round(const xy_batch* b, cudaStream_t s) {
-  cudaError_t e = xyk::launch_batch_round(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
-                                          b->n_ctas, s);
+  cudaError_t e = b->fused ? xyk::launch_batch_fused(b->p.sincos_mode, b->p.reduce_mode,
+                                                     round_args(b), b->n_ctas, s)
+                           : xyk::launch_batch_round(b->p.sincos_mode, b->p.reduce_mode,
+                                                     round_args(b), b->n_ctas, s);
   if (e == cudaSuccess) e = xyk::launch_exchange(exchange_args(b), s);
   return e;
 }
@@ -326,8 +339,11 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   if (!(p->delta > 0.0) || p->delta > M_PI + 1e-12 || !isfinite(p->J) ||
       (p->start != XY_START_HOT && p->start != XY_START_COLD) || p->sincos_mode < 0 ||
       p->sincos_mode > 2 || p->reduce_mode < 0 || p->reduce_mode > 1 ||
-      p->sweeps_per_round < 1 || p->sweeps_per_round > 1000000 || p->target_band_sites < 0) {
-    bmsg("bad delta, J, start, sincos_mode, reduce_mode, sweeps_per_round or target_band_sites");
+      p->sweeps_per_round < 1 || p->sweeps_per_round > 1000000 || p->target_band_sites < 0 ||
+      (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
+       p->algorithm != XY_ALGO_TWO_PASS)) {
+    bmsg("bad delta, J, start, sincos_mode, reduce_mode, sweeps_per_round, target_band_sites "
+         "or algorithm");
     return XY_EINVAL;
   }
   for (int i = 0; i < p->n; ++i) {
@@ -373,6 +389,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   b->p.beta = nullptr;
   b->p.ladder = nullptr;
   b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b->fused = p->algorithm != XY_ALGO_TWO_PASS;
   batch_mark(b, true);
 
   auto fail_create = [&](xy_status st) {
@@ -424,6 +441,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
     if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
   };
   alloc((void**)&b->d_theta, sizeof(float) * (size_t)std::max<int64_t>(total, 4));
+  if (b->fused) alloc((void**)&b->d_theta2, sizeof(float) * (size_t)std::max<int64_t>(total, 4));
   alloc((void**)&b->d_offset, sizeof(int64_t) * b->n);
   alloc((void**)&b->d_L, sizeof(int32_t) * b->n);
   alloc((void**)&b->d_beta, sizeof(double) * b->n);
@@ -465,8 +483,10 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
                           p->start == XY_START_HOT, b->stream);
   if (e == cudaSuccess) {
     step = "kernel attributes";
-    e = xyk::prepare_batch_round(p->sincos_mode, p->reduce_mode,
-                                 b->cs_bytes + xyk::batch_smem_bytes(0));
+    e = b->fused ? xyk::prepare_batch_fused(p->sincos_mode, p->reduce_mode,
+                                            b->cs_bytes + xyk::batch_fused_tail_bytes())
+                 : xyk::prepare_batch_round(p->sincos_mode, p->reduce_mode,
+                                            b->cs_bytes + xyk::batch_smem_bytes(0));
   }
   if (e == cudaSuccess) {
     step = "synchronize";
@@ -598,8 +618,9 @@ xy_status xy_batch_get_state(xy_batch* b, int32_t lattice, float* host_angles) {
   if (lattice < 0 || lattice >= b->n || !host_angles)
     return bfail(b, XY_EINVAL, "xy_batch_get_state: bad lattice or NULL output");
   const int L = b->L[lattice];
-  B_CUDA(b, xyk::launch_split_to_natural(b->d_theta + b->offset[lattice], b->d_scratch, L,
-                                         b->stream), "xy_batch_get_state: layout");
+  const float* cur = (b->fused && (b->next_sweep & 1u)) ? b->d_theta2 : b->d_theta;
+  B_CUDA(b, xyk::launch_split_to_natural(cur + b->offset[lattice], b->d_scratch, L, b->stream),
+         "xy_batch_get_state: layout");
   B_CUDA(b, cudaMemcpyAsync(host_angles, b->d_scratch, sizeof(float) * (size_t)L * L,
                             cudaMemcpyDeviceToHost, b->stream), "xy_batch_get_state: copy");
   B_CUDA(b, cudaStreamSynchronize(b->stream), "xy_batch_get_state: stream");

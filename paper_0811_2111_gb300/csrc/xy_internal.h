@@ -64,6 +64,7 @@ struct BatchBand {
 
 struct BatchArgs {
   float* theta;                 // all lattices, split layout each, at offset[i] floats
+  float* theta2;                // second buffer of the fused variant (sweep parity), or null
   const int64_t* offset;        // [n]
   const int32_t* L;             // [n]
   const double* beta;           // [n] current beta of each lattice
@@ -106,6 +107,11 @@ cudaError_t prepare_batch_round(int sincos_mode, int reduce_mode, size_t smem);
 cudaError_t launch_batch_round(int sincos_mode, int reduce_mode, const BatchArgs& a, int n_ctas,
                                cudaStream_t stream);
 cudaError_t launch_exchange(const ExchangeArgs& a, cudaStream_t stream);
+// Fused variant (512-thread CTAs, one stage and one cluster barrier per sweep).
+size_t batch_fused_tail_bytes();
+cudaError_t prepare_batch_fused(int sincos_mode, int reduce_mode, size_t smem);
+cudaError_t launch_batch_fused(int sincos_mode, int reduce_mode, const BatchArgs& a, int n_ctas,
+                               cudaStream_t stream);
 
 // ---- series statistics / beta derivatives (xy_stats.cu) ----
 constexpr int kStatsFields = 8;

@@ -37,51 +37,53 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Per record: E = -J C and jj = Ix^2 + Iy^2 in FP64 (the only FP64 work per
+// record: three conversions and a handful of adds and fused multiply-adds; the
+// FP64 pipe is narrow on this GPU), |m| in FP32.  Every other moment follows
+// from these because e = E/N, C = -E/J and Upsilon is linear in C and jj:
+//   cov(e, E)       = var(E) / N
+//   cov(Upsilon, E) = (-var(E) - beta J^2 cov(jj, E)) / (2N)
 struct Sample {
-  double E, e, ups, jj, m;
+  double E, jj;
+  float m;
 };
 
-__device__ __forceinline__ Sample sample(const xy_record& r, double N, double J) {
+__device__ __forceinline__ Sample sample(const xy_record& r, double J, float invNf) {
   const double unit = 1.0 / (double)(1ll << XY_FX_SHIFT);
-  const double C = (double)r.sum[0] * unit, Ix = (double)r.sum[1] * unit;
-  const double Iy = (double)r.sum[2] * unit, Mx = (double)r.sum[3] * unit;
-  const double My = (double)r.sum[4] * unit;
+  const double C = (double)r.sum[0] * unit;
+  const double Ix = (double)r.sum[1] * unit, Iy = (double)r.sum[2] * unit;
+  const float unitf = 1.0f / (float)(1ll << XY_FX_SHIFT);
+  const float Mx = __ll2float_rn(r.sum[3]) * unitf, My = __ll2float_rn(r.sum[4]) * unitf;
   Sample s;
   s.E = -J * C;
-  s.e = s.E / N;
-  s.jj = Ix * Ix + Iy * Iy;
-  s.ups = (J * C - r.beta * J * J * s.jj) / (2.0 * N);
-  s.m = sqrt(Mx * Mx + My * My) / N;
+  s.jj = fma(Ix, Ix, Iy * Iy);
+  s.m = sqrtf(fmaf(Mx, Mx, My * My)) * invNf;
   return s;
 }
 
 // Pass 1: segment `blockIdx.y` of chain `blockIdx.x` accumulates moments of
-// the samples shifted by the window's first sample (K), which keeps the
-// one-pass covariance free of cancellation: per segment
-//   sums of dE, dE^2, de, de dE, du, du dE, jj, m   (dX = X - K_X).
+// the samples shifted by the window's first sample K (one-pass covariances
+// without cancellation): sums of dE, dE^2, djj, djj dE and |m|.
 __global__ void __launch_bounds__(kThreads) k_series_partials(StatsArgs a) {
   __shared__ double sh[kThreads];
   const int chain = blockIdx.x, seg = blockIdx.y, nseg = gridDim.y;
   const xy_record* rec = a.records + (size_t)chain * a.stride + a.first;
-  const double N = (double)a.L[chain] * (double)a.L[chain];
-  const Sample k = sample(rec[0], N, a.J);
+  const float invNf = 1.0f / ((float)a.L[chain] * (float)a.L[chain]);
+  const Sample k = sample(rec[0], a.J, invNf);
   const int64_t n = a.count;
   const int64_t lo = n * seg / nseg, hi = n * (seg + 1) / nseg;
   double m[kPartials] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
-    const Sample s = sample(rec[i], N, a.J);
-    const double dE = s.E - k.E, de = s.e - k.e, du = s.ups - k.ups;
+    const Sample s = sample(rec[i], a.J, invNf);
+    const double dE = s.E - k.E, dj = s.jj - k.jj;
     m[0] += dE;
-    m[1] += dE * dE;
-    m[2] += de;
-    m[3] += de * dE;
-    m[4] += du;
-    m[5] += du * dE;
-    m[6] += s.jj;
-    m[7] += s.m;
+    m[1] = fma(dE, dE, m[1]);
+    m[2] += dj;
+    m[3] = fma(dj, dE, m[3]);
+    m[4] += (double)s.m;
   }
   double* out = a.partials + ((size_t)chain * nseg + seg) * kPartials;
-  for (int j = 0; j < kPartials; ++j) {
+  for (int j = 0; j < 5; ++j) {
     const double t = block_sum(m[j], sh);
     if (threadIdx.x == 0) out[j] = t;
   }
@@ -95,25 +97,27 @@ __global__ void k_series_combine(StatsArgs a, int n_chains, int nseg) {
   const xy_record* rec = a.records + (size_t)chain * a.stride + a.first;
   const double N = (double)a.L[chain] * (double)a.L[chain];
   const double J = a.J;
-  const Sample k = sample(rec[0], N, J);
+  const double beta = rec[0].beta;
+  const Sample k = sample(rec[0], J, (float)(1.0 / N));
   double m[kPartials] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int sg = 0; sg < nseg; ++sg)
-    for (int j = 0; j < kPartials; ++j)
-      m[j] += a.partials[((size_t)chain * nseg + sg) * kPartials + j];
+    for (int j = 0; j < 5; ++j) m[j] += a.partials[((size_t)chain * nseg + sg) * kPartials + j];
   const double inv = 1.0 / (double)a.count;
-  const double mdE = m[0] * inv, mde = m[2] * inv, mdu = m[4] * inv;
+  const double mdE = m[0] * inv, mdj = m[2] * inv;
   const double varE = m[1] * inv - mdE * mdE;
-  const double cov_eE = m[3] * inv - mde * mdE;
-  const double cov_uE = m[5] * inv - mdu * mdE;
-  const double mj = m[6] * inv;
+  const double cov_jE = m[3] * inv - mdj * mdE;
+  const double meanE = k.E + mdE, meanjj = k.jj + mdj;
+  const double mean_e = meanE / N;
+  const double mean_u = (-meanE - beta * J * J * meanjj) / (2.0 * N);    // J C = -E
+  const double cov_uE = (-varE - beta * J * J * cov_jE) / (2.0 * N);
   double* o = a.out + (size_t)chain * kStatsFields;
-  o[0] = k.e + mde;                           // <e>
-  o[1] = k.ups + mdu;                         // <Upsilon>
-  o[2] = m[7] * inv;                          // <|m|>
-  o[3] = -cov_eE;                             // d<e>/dbeta
-  o[4] = -cov_uE - J * J * mj / (2.0 * N);    // d<Upsilon>/dbeta
-  o[5] = -cov_uE;                             // covariance part alone
-  o[6] = varE / N;                            // var(E)/N = c_v / beta^2
+  o[0] = mean_e;                                  // <e>
+  o[1] = mean_u;                                  // <Upsilon>
+  o[2] = m[4] * inv;                              // <|m|>
+  o[3] = -varE / N;                               // d<e>/dbeta = -cov(e, E)
+  o[4] = -cov_uE - J * J * meanjj / (2.0 * N);    // d<Upsilon>/dbeta
+  o[5] = -cov_uE;                                 // covariance part alone
+  o[6] = varE / N;                                // var(E)/N = c_v / beta^2
   o[7] = (double)a.count;
 }
 

@@ -147,7 +147,7 @@ class Batch:
 
     def __init__(self, Ls, betas, seed, ladders=None, J=1.0, delta=math.pi, start="hot",
                  sincos="accurate", reduce="fp64", lattice_id0=0, sweeps_per_round=10,
-                 target_band_sites=0, device=None, stream=None):
+                 target_band_sites=0, algorithm="auto", device=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -173,6 +173,8 @@ class Batch:
         p.lattice_id0 = int(lattice_id0)
         p.sweeps_per_round = int(sweeps_per_round)
         p.target_band_sites = int(target_band_sites)
+        p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
+                       "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
         self.params = p
         self.J = float(J)
         self.sweeps_per_round = int(sweeps_per_round)

@@ -31,17 +31,20 @@ LS = [2, 6, 16, 24, 48, 96, 128, 256]
 BETAS = [0.7, 0.9, 1.0, 1.1, 1.2, 0.95, 1.05, 1.12]
 
 
-def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5):
+def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5, algorithm="auto"):
     with Batch(LS, BETAS, seed, lattice_id0=lid0, sweeps_per_round=spr,
-               target_band_sites=target, sincos=sincos) as b:
+               target_band_sites=target, sincos=sincos, algorithm=algorithm) as b:
         b.run(rounds)
         n_ctas = b.info()[3]
         return [b.state(i) for i in range(len(LS))], [b.observables(i) for i in range(len(LS))], n_ctas
 
 
-@pytest.mark.parametrize("sincos", ["accurate", "fast"])
-def test_batch_matches_single_lattices(sincos):
-    states, obs, _ = run_batch(sincos=sincos)
+@pytest.mark.parametrize("sincos,algorithm", [("accurate", "fused"), ("fast", "fused"),
+                                              ("accurate", "two_pass")])
+def test_batch_matches_single_lattices(sincos, algorithm):
+    """Odd rounds of 5 sweeps (2 rounds) leave the fused variant's state in its
+    second buffer half way and in the first at the end; both are checked."""
+    states, obs, _ = run_batch(sincos=sincos, algorithm=algorithm)
     for i, (L, beta) in enumerate(zip(LS, BETAS)):
         with Lattice(L, beta, 23, lattice_id=5 + i, sincos=sincos, algorithm="two_pass") as lat:
             lat.sweep(10)
@@ -55,14 +58,26 @@ def test_batch_matches_single_lattices(sincos):
             assert np.max(np.abs(obs[i][k] - o[k])) <= tol, (L, k)
 
 
+def test_fused_batch_state_after_odd_sweeps():
+    with Batch([16, 256], [1.0, 1.1], 4, sweeps_per_round=3) as b:
+        b.run(1)
+        odd = [b.state(i) for i in range(2)]
+    for i, (L, beta) in enumerate(((16, 1.0), (256, 1.1))):
+        with Lattice(L, beta, 4, lattice_id=i, algorithm="two_pass") as lat:
+            lat.sweep(3)
+            s, _ = lat.state()
+        assert np.array_equal(odd[i], s)
+
+
 def test_batch_is_independent_of_the_work_plan():
     ref_states, ref_obs, n0 = run_batch(target=8192)
-    for target in (256, 1024, 65536):
-        states, obs, n = run_batch(target=target)
+    for target, algorithm in ((256, "auto"), (1024, "auto"), (65536, "auto"),
+                              (2048, "two_pass"), (256, "two_pass")):
+        states, obs, n = run_batch(target=target, algorithm=algorithm)
         for i in range(len(LS)):
             assert np.array_equal(states[i], ref_states[i])
             assert np.array_equal(obs[i]["accepted"], ref_obs[i]["accepted"])
-        print(f"target {target}: {n} CTAs (8192: {n0})")
+        print(f"target {target} {algorithm}: {n} CTAs (8192: {n0})")
 
 
 def test_replica_exchange_matches_oracle_step_by_step():
