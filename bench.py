@@ -345,6 +345,45 @@ def measure_differentiation(dev, sincos, therm=10000, meas=100000):
                       "backward (FP64 covariance kernel)"}
 
 
+def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
+    """The lattice sides of the paper's Table 1 (L = 128 ... 2048): fused-kernel
+    updates/s on the GPU against the FP64 oracle on one host core, whose ratio is
+    the analogue of the paper's "gain" over its serial code (which was HMC on a
+    2008 GPU against one Conroe core; context, not a target)."""
+    import torch
+    import oracle
+    from paper_0811_2111_gb300.lattice import Lattice
+
+    out = {}
+    for L in (128, 256, 512, 1024, 2048):
+        sweeps = max(50, int(2e9 // (L * L)))
+        with Lattice(L, 1.0, 3, sincos=sincos, device=dev) as lat:
+            lat.reserve(sweeps + 10)
+            lat.sweep(10)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.sweep(sweeps)
+            e1.record(lat.stream)
+            e1.synchronize()
+            gpu = L * L * sweeps / (e0.elapsed_time(e1) * 1e-3)
+        n = 1
+        t = time.perf_counter()
+        oracle.run(L, L, 1.0, n, seed=3, nthreads=1)
+        dt = time.perf_counter() - t
+        while dt < cpu_seconds and n < 4096:
+            n *= 2
+            t = time.perf_counter()
+            oracle.run(L, L, 1.0, n, seed=3, nthreads=1)
+            dt = time.perf_counter() - t
+        cpu = L * L * n / dt
+        out[str(L)] = {"gpu": gpu, "oracle_1core": cpu, "gain": gpu / cpu}
+    return {"unit": UNIT, "beta": 1.0, "sizes": out,
+            "paper_cuda_gain_for_context": {"128": 33, "256": 37, "512": 38, "1024": 30,
+                                            "2048": 30}}
+
+
 def measure_precision(dev, sweeps=200):
     """The precision workload: L=16384 (1 GiB of angles), beta=1.12, seed 7,
     `sweeps` sweeps per variant; updates/s of each sincos / reduction variant."""
@@ -504,7 +543,8 @@ def run_ours(args):
     if not args.no_extra and world == 1:
         extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
                  "differentiation": measure_differentiation(dev, args.sincos),
-                 "precision": measure_precision(dev)}
+                 "precision": measure_precision(dev),
+                 "table1_sizes": measure_table1_sizes(dev, args.sincos)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
