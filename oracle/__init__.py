@@ -69,6 +69,20 @@ def lib():
         L.orc_pt_run.argtypes = [C.c_int, C.c_int, C.c_int, _D, C.c_double, C.c_double,
                                  C.c_uint64, C.c_uint32, C.c_int, C.c_int, _D]
         L.orc_pt_run.restype = C.c_int
+        L.orc_hmc_momenta.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, _D]
+        L.orc_hmc_force.argtypes = [C.c_int, C.c_int, _D, C.c_double, C.c_double, _D]
+        L.orc_hmc_hamiltonian.argtypes = [C.c_int, C.c_int, _D, _D, C.c_double, C.c_double, _D]
+        L.orc_hmc_leapfrog.argtypes = [C.c_int, C.c_int, _D, _D, C.c_double, C.c_double,
+                                       C.c_double, C.c_int]
+        L.orc_hmc_leapfrog.restype = C.c_int
+        L.orc_hmc_trajectory.argtypes = [C.c_int, C.c_int, _D, C.c_double, C.c_double,
+                                         C.c_double, C.c_int, C.c_uint64, C.c_uint32,
+                                         C.c_uint32, _D, _optional(_D)]
+        L.orc_hmc_trajectory.restype = C.c_int
+        L.orc_hmc_run.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_double,
+                                  C.c_double, C.c_double, C.c_int, C.c_int, C.c_uint32,
+                                  C.c_int64, _optional(_D), _optional(_D)]
+        L.orc_hmc_run.restype = C.c_int
         _lib = L
     return _lib
 
@@ -224,3 +238,68 @@ def beta_derivatives(sums, N, beta, J=1.0):
             "de": -np.mean((e - e.mean()) * dE),
             "dupsilon": -np.mean((ups - ups.mean()) * dE) - J * J * jj.mean() / (2.0 * N),
             "varE_over_N": np.mean(dE * dE) / N}
+
+
+# ---------------------------------------------------------------------------
+# Hybrid Monte Carlo (Sec. 1.2): momenta, force, leap-frog, trajectories.
+# ---------------------------------------------------------------------------
+
+def _f64(a):
+    a = np.array(a, np.float64).reshape(-1)
+    return np.ascontiguousarray(a)
+
+
+def hmc_momenta(Lx, Ly, seed, traj, lattice_id=0):
+    """Gaussian momenta of trajectory `traj` (Box-Muller of domain-3 words)."""
+    p = np.zeros(Lx * Ly, np.float64)
+    lib().orc_hmc_momenta(Lx, Ly, seed, traj, lattice_id, p)
+    return p
+
+
+def hmc_force(theta, Lx, Ly, beta, J=1.0):
+    """F_s = -beta J sum_nn sin(theta_s - theta_j)."""
+    F = np.zeros(Lx * Ly, np.float64)
+    lib().orc_hmc_force(Lx, Ly, _f64(theta), beta, J, F)
+    return F
+
+
+def hmc_hamiltonian(theta, p, Lx, Ly, beta, J=1.0):
+    """(K, V): kinetic sum p^2/2 and potential beta H(theta)."""
+    out = np.zeros(2, np.float64)
+    lib().orc_hmc_hamiltonian(Lx, Ly, _f64(theta), _f64(p), beta, J, out)
+    return float(out[0]), float(out[1])
+
+
+def hmc_leapfrog(theta, p, Lx, Ly, beta, eps, n_steps, J=1.0):
+    """n_steps leap-frog steps; returns new (theta, p) copies (angles wrapped into [0, 2pi))."""
+    th, pp = _f64(theta), _f64(p)
+    if lib().orc_hmc_leapfrog(Lx, Ly, th, pp, beta, J, eps, n_steps) != 0:
+        raise MemoryError("oracle leap-frog failed")
+    return th, pp
+
+
+def hmc_trajectory(theta, Lx, Ly, beta, eps, n_steps, seed, traj, lattice_id=0, J=1.0):
+    """One trajectory from `theta`; returns (theta_after_test, p_end, dict(dH, accepted,
+    K0, V0, K1, V1))."""
+    th = _f64(theta)
+    out = np.zeros(6, np.float64)
+    pend = np.zeros(Lx * Ly, np.float64)
+    if lib().orc_hmc_trajectory(Lx, Ly, th, beta, J, eps, n_steps, seed, traj, lattice_id,
+                                out, pend) != 0:
+        raise MemoryError("oracle trajectory failed")
+    return th, pend, {"dH": out[0], "accepted": bool(out[1]), "K0": out[2], "V0": out[3],
+                      "K1": out[4], "V1": out[5]}
+
+
+def hmc_run(Lx, Ly, beta, eps, n_steps, n_traj, seed, lattice_id=0, J=1.0, start=1,
+            first_traj=0, theta=None):
+    """HMC chain; returns (records[n, 7], final_theta).
+
+    records[i] = (C, Ix, Iy, Mx, My, dH, accepted) after trajectory first_traj + i.
+    start: 1 hot, 0 cold, -1 from `theta`."""
+    th = np.zeros(Lx * Ly, np.float64) if theta is None else _f64(theta)
+    rec = np.zeros((n_traj, 7), np.float64)
+    if lib().orc_hmc_run(Lx, Ly, seed, lattice_id, beta, J, eps, n_steps, start, first_traj,
+                         n_traj, th, rec) != 0:
+        raise ValueError("oracle HMC run failed")
+    return rec, th

@@ -18,12 +18,15 @@
  *     dE = -J sum_{4 nn j} [cos(theta' - theta_j) - cos(theta - theta_j)];
  *     the accept/select of Sec. 3.2 (new = z*proposal + (1-z)*old);
  *   - the per-sweep bond and spin sums used for the cross-checks of
- *     Sec. 1.2 (energy and acceptance).
+ *     Sec. 1.2 (energy and acceptance);
+ *   - Hybrid Monte Carlo (Sec. 1.2): Gaussian momenta, leap-frog
+ *     integration, global Metropolis test (last section of this file).
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11, Sec. 3.3 and Table 2), keyed
  * by the 64-bit seed (low word first) with counter (site, sweep, lattice id,
  * domain); domain 0 draws the hot start, domain 1 the Metropolis words,
- * domain 2 the replica-exchange words.
+ * domain 2 the replica-exchange words, domain 3 the HMC momenta and
+ * domain 4 the HMC accept words.
  * Uniforms use the top 24 bits of a word: u = (w >> 8) * 2^-24.
  */
 #include <math.h>
@@ -405,5 +408,162 @@ int orc_pt_run(int Lx, int Ly, int n, const double *beta, double J, double delta
         orc_exchange(1, &start0, n, pos, beta, bl, energy, (uint32_t)r, seed, lattice_id0, NULL);
     }
     free(theta); free(bl); free(energy); free(pos);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Hybrid Monte Carlo, the method of Sec. 1.2: Gaussian momenta, the   */
+/* leap-frog integration of the equations of motion, and a global      */
+/* Metropolis test on the change of the fictitious Hamiltonian.        */
+/*                                                                     */
+/*   H_hmc(theta, p) = sum_s p_s^2 / 2 + beta H(theta)                 */
+/*   F_s = -d(beta H)/d theta_s = -beta J sum_{4 nn j} sin(t_s - t_j)  */
+/*                                                                     */
+/* The paper does not fix the step size, the number of steps or the    */
+/* Gaussian transform; here the momenta of trajectory t come from the  */
+/* words of domain 3, counter (site, t, lattice id, 3), by Box-Muller: */
+/*   u1 = ((w0 >> 8) + 1) 2^-24 in (0, 1],  u2 = (w1 >> 8) 2^-24,      */
+/*   p = sqrt(-2 ln u1) cos(2 pi u2),                                  */
+/* and the test uses u = u24(w0) of counter (0, t, lattice id, 4):     */
+/* accept iff u < exp(-dH).  Angles are wrapped into [0, 2pi) after    */
+/* every drift (H depends only on angle differences mod 2pi).          */
+/* ------------------------------------------------------------------ */
+
+static double wrap_2pi(double t)
+{
+    double w = t - ORC_TWO_PI * floor(t / ORC_TWO_PI);
+    if (w >= ORC_TWO_PI) w -= ORC_TWO_PI;   /* floor rounding at the edge */
+    if (w < 0.0) w += ORC_TWO_PI;
+    return w;
+}
+
+void orc_hmc_momenta(int Lx, int Ly, uint64_t seed, uint32_t traj, uint32_t lattice_id,
+                     double *p)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    for (int64_t s = 0; s < N; ++s) {
+        uint32_t w[4];
+        site_words(seed, (uint32_t)s, traj, lattice_id, 3u, w);
+        double u1 = (double)((w[0] >> 8) + 1u) * (1.0 / 16777216.0);
+        double u2 = u24(w[1]);
+        p[s] = sqrt(-2.0 * log(u1)) * cos(ORC_TWO_PI * u2);
+    }
+}
+
+/* F_s = -beta J sum over the four neighbours of sin(theta_s - theta_j). */
+void orc_hmc_force(int Lx, int Ly, const double *theta, double beta, double J, double *F)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    for (int64_t s = 0; s < N; ++s) {
+        int64_t nb[4] = { site_right(Lx, s), site_left(Lx, s),
+                          site_up(Lx, Ly, s), site_down(Lx, Ly, s) };
+        double f = 0.0;
+        for (int k = 0; k < 4; ++k) f -= sin(theta[s] - theta[nb[k]]);
+        F[s] = beta * J * f;
+    }
+}
+
+/* out = { K, V } with K = sum p^2 / 2 and V = beta H(theta) = -beta J C. */
+void orc_hmc_hamiltonian(int Lx, int Ly, const double *theta, const double *p, double beta,
+                         double J, double out[2])
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double K = 0.0, sums[5];
+    for (int64_t s = 0; s < N; ++s) K += 0.5 * p[s] * p[s];
+    orc_measure(Lx, Ly, theta, sums);
+    out[0] = K;
+    out[1] = -beta * J * sums[0];
+}
+
+/* n_steps leap-frog steps of size eps, in place:
+ *   p += eps/2 F(theta);
+ *   repeat n_steps times: theta += eps p (wrapped); p += eps F(theta),
+ *   with eps/2 instead of eps in the last kick.
+ * n_steps = 0 leaves both arrays unchanged.  Returns 0, or -1 on no memory. */
+int orc_hmc_leapfrog(int Lx, int Ly, double *theta, double *p, double beta, double J,
+                     double eps, int n_steps)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    if (n_steps <= 0) return 0;
+    double *F = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!F) return -1;
+    orc_hmc_force(Lx, Ly, theta, beta, J, F);
+    for (int64_t s = 0; s < N; ++s) p[s] += 0.5 * eps * F[s];
+    for (int k = 1; k <= n_steps; ++k) {
+        for (int64_t s = 0; s < N; ++s) theta[s] = wrap_2pi(theta[s] + eps * p[s]);
+        orc_hmc_force(Lx, Ly, theta, beta, J, F);
+        double h = (k == n_steps) ? 0.5 * eps : eps;
+        for (int64_t s = 0; s < N; ++s) p[s] += h * F[s];
+    }
+    free(F);
+    return 0;
+}
+
+/* One trajectory from `theta` (in place): draw the momenta of trajectory
+ * `traj`, integrate, test.  On rejection theta is restored.  out =
+ * { dH, accepted, K0, V0, K1, V1 }.  If p_out is non-NULL it receives the
+ * momenta at the end of the integration.  Returns 0 or -1. */
+int orc_hmc_trajectory(int Lx, int Ly, double *theta, double beta, double J, double eps,
+                       int n_steps, uint64_t seed, uint32_t traj, uint32_t lattice_id,
+                       double out[6], double *p_out)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double *p = (double *)malloc(sizeof(double) * (size_t)N);
+    double *theta0 = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!p || !theta0) { free(p); free(theta0); return -1; }
+    orc_hmc_momenta(Lx, Ly, seed, traj, lattice_id, p);
+    memcpy(theta0, theta, sizeof(double) * (size_t)N);
+    double h0[2], h1[2];
+    orc_hmc_hamiltonian(Lx, Ly, theta, p, beta, J, h0);
+    if (orc_hmc_leapfrog(Lx, Ly, theta, p, beta, J, eps, n_steps) != 0) {
+        free(p); free(theta0);
+        return -1;
+    }
+    orc_hmc_hamiltonian(Lx, Ly, theta, p, beta, J, h1);
+    double dH = (h1[0] + h1[1]) - (h0[0] + h0[1]);
+    uint32_t w[4];
+    site_words(seed, 0u, traj, lattice_id, 4u, w);
+    int accepted = u24(w[0]) < exp(-dH);
+    if (!accepted) memcpy(theta, theta0, sizeof(double) * (size_t)N);
+    if (p_out) memcpy(p_out, p, sizeof(double) * (size_t)N);
+    out[0] = dH; out[1] = (double)accepted;
+    out[2] = h0[0]; out[3] = h0[1]; out[4] = h1[0]; out[5] = h1[1];
+    free(p); free(theta0);
+    return 0;
+}
+
+/* A chain of n_traj trajectories numbered first_traj, first_traj + 1, ...
+ * from a hot (start = 1) or cold (0) start, or from theta_io (start < 0).
+ * After trajectory i, records[7*i .. 7*i+6] = { C, Ix, Iy, Mx, My, dH,
+ * accepted } of the state after the test.  The final state goes back to
+ * theta_io when it is non-NULL. */
+int orc_hmc_run(int Lx, int Ly, uint64_t seed, uint32_t lattice_id, double beta, double J,
+                double eps, int n_steps, int start, uint32_t first_traj, int64_t n_traj,
+                double *theta_io, double *records)
+{
+    int64_t N = (int64_t)Lx * Ly;
+    double *theta = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!theta) return -1;
+    if (start < 0) {
+        if (!theta_io) { free(theta); return -1; }
+        memcpy(theta, theta_io, sizeof(double) * (size_t)N);
+    } else {
+        orc_start(Lx, Ly, seed, lattice_id, start, theta);
+    }
+    for (int64_t i = 0; i < n_traj; ++i) {
+        double o[6];
+        if (orc_hmc_trajectory(Lx, Ly, theta, beta, J, eps, n_steps, seed,
+                               first_traj + (uint32_t)i, lattice_id, o, NULL) != 0) {
+            free(theta);
+            return -1;
+        }
+        if (records) {
+            orc_measure(Lx, Ly, theta, records + 7 * i);
+            records[7 * i + 5] = o[0];
+            records[7 * i + 6] = o[1];
+        }
+    }
+    if (theta_io) memcpy(theta_io, theta, sizeof(double) * (size_t)N);
+    free(theta);
     return 0;
 }
