@@ -56,6 +56,19 @@ class xy_batch_params(C.Structure):
 
 XY_BATCH_MAX_L = 256
 XY_STATS_FIELDS = 8
+XY_HMC_K_SHIFT = 24
+XY_HMC_KERNEL_AUTO, XY_HMC_KERNEL_TILED, XY_HMC_KERNEL_SITE = 0, 1, 2
+
+
+class xy_hmc_params(C.Structure):
+    _fields_ = [("L", C.c_int32), ("start", C.c_int32), ("beta", C.c_double), ("J", C.c_double),
+                ("eps", C.c_double), ("n_md", C.c_int32), ("sincos_mode", C.c_int32),
+                ("seed", C.c_uint64), ("lattice_id", C.c_uint32), ("kernel", C.c_int32)]
+
+
+class xy_hmc_record(C.Structure):
+    _fields_ = [("sum", C.c_int64 * 5), ("kinetic", C.c_int64 * 2), ("bonds", C.c_int64 * 2),
+                ("dH", C.c_double), ("beta", C.c_double), ("accepted", C.c_uint64)]
 
 _lib = None
 
@@ -108,6 +121,22 @@ def lib():
         "xy_batch_destroy": (st, [P]),
         "xy_batch_last_error": (C.c_char_p, [P]),
         "xy_noalloc_last_error": (C.c_char_p, []),
+        "xy_hmc_create": (st, [C.POINTER(xy_hmc_params), P, P, C.POINTER(P)]),
+        "xy_hmc_run": (st, [P, C.c_int64]),
+        "xy_hmc_integrate": (st, [P, C.c_int32]),
+        "xy_hmc_refresh": (st, [P]),
+        "xy_hmc_last_sums": (st, [P, P]),
+        "xy_hmc_measure": (st, [P, C.c_int64, C.c_int64, C.POINTER(xy_obs), P]),
+        "xy_hmc_records_device": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
+        "xy_hmc_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64),
+                             C.POINTER(C.c_uint64)]),
+        "xy_hmc_get_state": (st, [P, P, P, C.POINTER(C.c_uint64)]),
+        "xy_hmc_set_state": (st, [P, P, P, C.c_uint64]),
+        "xy_hmc_set_step": (st, [P, C.c_double, C.c_int32]),
+        "xy_hmc_set_beta": (st, [P, C.c_double]),
+        "xy_hmc_synchronize": (st, [P]),
+        "xy_hmc_destroy": (st, [P]),
+        "xy_hmc_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,3 +321,88 @@ def xy_batch_destroy(b):
 
 def xy_batch_series_stats(b, first, count, d_out_ptr):
     batch_check(lib().xy_batch_series_stats(b, first, count, d_out_ptr), b)
+
+
+# -- Hybrid Monte Carlo (include/xy_hmc.h) -------------------------------------
+
+def hmc_check(status, h=None):
+    if status != XY_OK:
+        msg = lib().xy_hmc_last_error(h)
+        raise XYError(status, msg.decode() if msg else "")
+    return status
+
+
+def xy_hmc_create(params, stream_ptr=None, d_angles_ptr=None):
+    h = C.c_void_p()
+    hmc_check(lib().xy_hmc_create(C.byref(params), stream_ptr, d_angles_ptr, C.byref(h)))
+    return h
+
+
+def xy_hmc_run(h, n_traj):
+    hmc_check(lib().xy_hmc_run(h, n_traj), h)
+
+
+def xy_hmc_integrate(h, n_steps):
+    hmc_check(lib().xy_hmc_integrate(h, n_steps), h)
+
+
+def xy_hmc_refresh(h):
+    hmc_check(lib().xy_hmc_refresh(h), h)
+
+
+def xy_hmc_last_sums(h):
+    out = (C.c_double * 12)()
+    hmc_check(lib().xy_hmc_last_sums(h, out), h)
+    return list(out)
+
+
+def xy_hmc_measure(h, first, count, dH_ptr=None):
+    out = (xy_obs * max(count, 1))()
+    hmc_check(lib().xy_hmc_measure(h, first, count, out, dH_ptr), h)
+    return out if count > 0 else (xy_obs * 0)()
+
+
+def xy_hmc_records_device(h):
+    p = C.c_void_p()
+    n = C.c_int64()
+    hmc_check(lib().xy_hmc_records_device(h, C.byref(p), C.byref(n)), h)
+    return p.value, n.value
+
+
+def xy_hmc_info(h):
+    r = C.c_int64()
+    t = C.c_uint64()
+    a = C.c_uint64()
+    hmc_check(lib().xy_hmc_info(h, C.byref(r), C.byref(t), C.byref(a)), h)
+    return r.value, t.value, a.value
+
+
+def xy_hmc_get_state(h, angles_ptr, momenta_ptr=None):
+    t = C.c_uint64()
+    hmc_check(lib().xy_hmc_get_state(h, angles_ptr, momenta_ptr, C.byref(t)), h)
+    return t.value
+
+
+def xy_hmc_set_state(h, angles_ptr, momenta_ptr, next_traj):
+    hmc_check(lib().xy_hmc_set_state(h, angles_ptr, momenta_ptr, next_traj), h)
+
+
+def xy_hmc_set_step(h, eps, n_md):
+    hmc_check(lib().xy_hmc_set_step(h, eps, n_md), h)
+
+
+def xy_hmc_set_beta(h, beta):
+    hmc_check(lib().xy_hmc_set_beta(h, beta), h)
+
+
+def xy_hmc_synchronize(h):
+    hmc_check(lib().xy_hmc_synchronize(h), h)
+
+
+def xy_hmc_destroy(h):
+    hmc_check(lib().xy_hmc_destroy(h))
+
+
+def xy_hmc_last_error(h=None):
+    m = lib().xy_hmc_last_error(h)
+    return m.decode() if m else ""

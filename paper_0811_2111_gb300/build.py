@@ -71,16 +71,18 @@ def build(force=False, verbose=False, extra=()):
 
 
 
-def source_hash():
-    """Hash of the kernel sources and headers (ties profiles to a kernel version)."""
+def source_hash(files=("xy_fused.cu", "xy_device.cuh")):
+    """Hash of a kernel's own source files under csrc/ (ties an ncu capture to
+    the kernel version it measured; the default is the fused sweep kernel)."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h"))):
-        if os.path.isfile(p):
-            h.update(os.path.basename(p).encode())
-            with open(p, "rb") as f:
-                h.update(f.read())
+    for name in files:
+        p = os.path.join(CSRC, name)
+        h.update(name.encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
+
 
 if __name__ == "__main__":
     v = "-v" in sys.argv

@@ -7,6 +7,7 @@
 
 #include "xy.h"
 #include "xy_device.cuh"
+#include "xy_hmc.h"
 
 namespace xyk {
 
@@ -150,5 +151,61 @@ cudaError_t launch_philox_words(const xyd::RoundKeys& rk, uint32_t sweep, uint32
 // Non-finite check of the split-layout angles: sets *flag to 1 if any is.
 cudaError_t launch_check_finite(const float* theta, int64_t n, unsigned int* flag,
                                 cudaStream_t stream);
+
+// ---- Hybrid Monte Carlo (xy_hmc.cu) ----
+// Fixed-point accumulators of one phase of a trajectory (start or end):
+// [0] K = sum p^2/2 (2^-24 units), [1..5] C, Ix, Iy, Mx, My (2^-30 units).
+constexpr int kHmcSums = 6;
+
+// Device-side control block of an HMC chain.  The accept kernel owns it
+// between graph launches; every other kernel only reads `cur` and `traj`.
+struct HmcCtl {
+  unsigned long long acc[2][kHmcSums];   // sums of the running trajectory
+  unsigned long long last[2][kHmcSums];  // sums of the last finished one
+  xy_hmc_record* records;                // record array (host updates it on growth)
+  unsigned long long rec;                // index of the next record
+  unsigned long long traj;               // next trajectory number
+  unsigned long long accepted;           // accepted trajectories so far
+  uint32_t cur;                          // angle buffer (0..2) holding the state
+  uint32_t pad;
+};
+
+// Kinds of leap-frog launch.
+enum HmcKind {
+  kHmcBeginDraw = 0,   // draw p, sums of (theta, p) -> acc[0], half kick, drift
+  kHmcBeginRead = 1,   // p from the buffer, otherwise as kHmcBeginDraw
+  kHmcStep = 2,        // full kick, drift
+  kHmcFinal = 3        // half kick, sums of (theta, p) -> acc[1], p written
+};
+
+struct HmcArgs {
+  float* th[3];          // the three angle buffers, natural order
+  float* p;              // momenta, natural order
+  HmcCtl* ctl;           // device control block
+  int L;
+  float K;               // beta * J
+  float eps;             // step
+  float a;               // kick coefficient of this launch (eps or eps / 2)
+  int k;                 // leap-frog step index of this launch (1-based for kHmcStep)
+  int n_md;              // steps of the trajectory (kHmcFinal reads theta_n)
+  xyd::RoundKeys rk;
+  uint32_t lattice_id;
+  int tiled;             // 1: tiled kernel (needs hmc_tiled_ok(L)), 0: one thread per site
+};
+
+// One leap-frog launch of `kind` with the tiled or the per-site kernel (both
+// give bit-identical results).
+cudaError_t launch_hmc(int kind, int sincos_mode, const HmcArgs& a, cudaStream_t stream);
+bool hmc_tiled_ok(int L);
+// The test (mode 0: Metropolis on dH, writes a record) or, mode 1, the plain
+// commit of an integration; both move acc to last and clear acc.
+cudaError_t launch_hmc_accept(int mode, const HmcArgs& a, double beta, double J,
+                              cudaStream_t stream);
+// Momenta of the current trajectory into a.p.
+cudaError_t launch_hmc_draw(const HmcArgs& a, cudaStream_t stream);
+// Hot or cold start into th[0] (natural order), cur = 0.
+cudaError_t launch_hmc_start(const HmcArgs& a, int hot, cudaStream_t stream);
+// Move the state into th[0] if it lives elsewhere, and set cur = 0.
+cudaError_t launch_hmc_canonical(const HmcArgs& a, cudaStream_t stream);
 
 }  // namespace xyk

@@ -96,3 +96,56 @@ def test_create_without_device_fails_cleanly(lib):
     assert st in (X.XY_ECUDA, X.XY_ENOMEM)
     assert ctx.value is None
     assert "xy_create" in X.xy_last_error(None)
+
+
+def _hmc_params(**kw):
+    p = X.xy_hmc_params()
+    p.L, p.start, p.beta, p.J, p.eps, p.n_md = 8, 0, 1.0, 1.0, 0.1, 10
+    p.sincos_mode, p.seed, p.lattice_id, p.kernel = 0, 1, 0, 0
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_hmc_record_layout():
+    assert C.sizeof(X.xy_hmc_record) == 96
+    assert C.sizeof(X.xy_hmc_params) == 56
+
+
+@pytest.mark.parametrize("kw,fragment", [
+    (dict(L=1), "L must"), (dict(L=65536), "L must"),
+    (dict(beta=-1.0), "beta"), (dict(beta=float("inf")), "beta"), (dict(J=float("nan")), "J"),
+    (dict(eps=0.0), "eps"), (dict(eps=float("nan")), "eps"), (dict(n_md=0), "n_md"),
+    (dict(start=3), "start"), (dict(sincos_mode=3), "sincos"), (dict(kernel=3), "kernel"),
+    (dict(kernel=1, L=96), "multiple of 128"),
+])
+def test_hmc_create_rejects_bad_parameters(lib, kw, fragment):
+    h = C.c_void_p()
+    st = lib.xy_hmc_create(C.byref(_hmc_params(**kw)), None, None, C.byref(h))
+    assert st == X.XY_EINVAL
+    assert h.value is None
+    assert fragment in X.xy_hmc_last_error(None)
+
+
+def test_hmc_null_and_foreign_handles(lib):
+    h = C.c_void_p()
+    assert lib.xy_hmc_create(None, None, None, C.byref(h)) == X.XY_EINVAL
+    assert lib.xy_hmc_create(C.byref(_hmc_params()), None, None, None) == X.XY_EINVAL
+    assert lib.xy_hmc_create(C.byref(_hmc_params()), None, C.c_void_p(8), C.byref(h)) == X.XY_EINVAL
+    assert lib.xy_hmc_run(None, 1) == X.XY_EINVAL
+    assert lib.xy_hmc_destroy(None) == X.XY_OK
+    bogus = C.c_void_p(0x2000)
+    assert lib.xy_hmc_run(bogus, 1) == X.XY_ESTATE
+    assert lib.xy_hmc_integrate(bogus, 1) == X.XY_ESTATE
+    assert lib.xy_hmc_destroy(bogus) == X.XY_ESTATE
+
+
+def test_hmc_create_without_device_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    st = lib.xy_hmc_create(C.byref(_hmc_params()), None, None, C.byref(h))
+    assert st in (X.XY_ECUDA, X.XY_ENOMEM)
+    assert h.value is None
+    assert "xy_hmc_create" in X.xy_hmc_last_error(None)

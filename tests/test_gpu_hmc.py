@@ -1,0 +1,264 @@
+"""Hybrid Monte Carlo on the GPU against the FP64 oracle (Sec. 1.2).
+
+* The hot start equals the Metropolis engine's; the momenta equal the
+  oracle's Box-Muller of the same Philox words to FP32 accuracy.
+* Leap-frog in lock step: from the same FP32 state, one GPU step equals one
+  FP64 oracle step to FP32 rounding, and n steps to the FP32 error amplified
+  by the dynamics.
+* The tiled kernel and the one-thread-per-site kernel agree bit for bit.
+* Whole trajectories: dH equals the oracle's dH from the same start within
+  the FP32 integration error, decisions agree outside the rounding band, the
+  record sums equal the oracle's sums of the GPU state, a rejected trajectory
+  leaves the state untouched bit for bit.
+* Ensembles: exact 2x2 energies, <exp(-dH)> = 1.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import exact_small as ex
+from gpu_util import record_tolerance
+from stats_util import jackknife_mean
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300 import _lib as X  # noqa: E402
+from paper_0811_2111_gb300.hmc import HMC  # noqa: E402
+from paper_0811_2111_gb300.lattice import Lattice  # noqa: E402
+
+TWO_PI = 2 * np.pi
+ANGLE_STEP_TOL = 2e-6     # one leap-frog step: FP32 rounding of theta + eps p and of F
+
+
+def circ(a, b):
+    d = np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)) % TWO_PI
+    return np.minimum(d, TWO_PI - d)
+
+
+def random_state(L, seed, p_scale=1.0):
+    rng = np.random.default_rng(seed)
+    th = rng.uniform(0, TWO_PI, L * L).astype(np.float32)
+    p = (p_scale * rng.normal(size=L * L)).astype(np.float32)
+    return th, p
+
+
+def test_hot_start_equals_metropolis_start():
+    for L in (6, 128):
+        with HMC(L, 1.0, 77, 0.1, 5, lattice_id=3) as h:
+            th, p, t = h.state()
+        with Lattice(L, 1.0, 77, lattice_id=3, algorithm="two_pass") as lat:
+            ref, _ = lat.state()
+        assert np.array_equal(th, ref)
+        assert np.all(p == 0) and t == 0
+
+
+@pytest.mark.parametrize("L", [2, 6, 130, 256])
+def test_momenta_match_oracle(L):
+    with HMC(L, 1.0, 12345, 0.1, 5, lattice_id=9) as h:
+        th, _, _ = h.state()
+        h.set_state(th, None, next_traj=41)
+        h.refresh()
+        _, p, _ = h.state()
+    want = oracle.hmc_momenta(L, L, 12345, 41, 9)
+    err = np.abs(p.reshape(-1).astype(np.float64) - want)
+    assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(want))), err.max()
+
+
+@pytest.mark.parametrize("L,kernel", [(2, "site"), (6, "site"), (34, "site"), (128, "tiled"),
+                                      (128, "site"), (256, "tiled")])
+@pytest.mark.parametrize("sincos", ["accurate", "fast"])
+def test_one_leapfrog_step_matches_oracle(L, kernel, sincos):
+    beta, eps = 1.1, 0.08
+    th, p = random_state(L, L + 5)
+    with HMC(L, beta, 3, eps, 1, sincos=sincos, kernel=kernel) as h:
+        h.set_state(th, p, 0)
+        h.integrate(1)
+        g_th, g_p, _ = h.state()
+    o_th, o_p = oracle.hmc_leapfrog(th, p, L, L, beta, eps, 1)
+    tol = ANGLE_STEP_TOL if sincos == "accurate" else 2e-5
+    assert np.max(circ(g_th.reshape(-1), o_th)) <= tol
+    dp = np.abs(g_p.reshape(-1) - o_p)
+    assert np.all(dp <= tol * (1.0 + np.abs(o_p))), dp.max()
+
+
+@pytest.mark.parametrize("L", [6, 128])
+def test_n_steps_match_oracle(L):
+    """Steps 2.. use the full-kick kernel; the FP32 error grows with the dynamics."""
+    beta, eps, n = 1.0, 0.05, 8
+    th, p = random_state(L, 99)
+    with HMC(L, beta, 3, eps, n) as h:
+        h.set_state(th, p, 0)
+        h.integrate(n)
+        g_th, g_p, _ = h.state()
+        sums = h.last_sums()
+    o_th, o_p = oracle.hmc_leapfrog(th, p, L, L, beta, eps, n)
+    assert np.max(circ(g_th.reshape(-1), o_th)) <= 2e-5
+    assert np.max(np.abs(g_p.reshape(-1) - o_p)) <= 2e-5 * (1 + np.abs(o_p).max())
+    K0, V0 = oracle.hmc_hamiltonian(th, p, L, L, beta)
+    K1, V1 = oracle.hmc_hamiltonian(o_th, o_p, L, L, beta)
+    N = L * L
+    assert abs(sums["start"]["K"] - K0) <= 1e-6 * N
+    assert abs(-beta * sums["start"]["C"] - V0) <= 1e-6 * N
+    assert abs(sums["end"]["K"] - K1) <= 2e-5 * N
+    assert abs(-beta * sums["end"]["C"] - V1) <= 2e-5 * N
+
+
+@pytest.mark.parametrize("L", [128, 256])
+def test_tiled_and_site_kernels_are_bit_identical(L):
+    out = {}
+    for kernel in ("tiled", "site"):
+        with HMC(L, 1.05, 8, 0.1, 7, kernel=kernel, lattice_id=2) as h:
+            h.run(6)
+            th, p, _ = h.state()
+            o = h.observables()
+            h.integrate(3)
+            th2, p2, _ = h.state()
+            out[kernel] = (th, p, o, th2, p2, h.last_sums())
+    a, b = out["tiled"], out["site"]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k in ("C", "Ix", "Iy", "Mx", "My", "dH"):
+        assert np.array_equal(a[2][k], b[2][k]), k
+    assert np.array_equal(a[2]["accepted"], b[2]["accepted"])
+    assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4])
+    assert a[5] == b[5]
+
+
+@pytest.mark.parametrize("L,eps,n_md", [(8, 0.2, 5), (32, 0.1, 10), (128, 0.05, 12)])
+def test_trajectories_match_oracle_step_by_step(L, eps, n_md):
+    """Each trajectory from the GPU's FP32 state: dH, decision and final state."""
+    beta, seed, lid = 1.0, 21, 4
+    N = L * L
+    dh_tol = 2e-6 * N ** 0.5 * n_md + 1e-5
+    band = 2 * dh_tol
+    mismatches = 0
+    with HMC(L, beta, seed, eps, n_md, lattice_id=lid) as h:
+        th, _, _ = h.state()
+        for t in range(12):
+            h.run(1)
+            g_th, _, _ = h.state()
+            o = h.observables(t, 1)
+            o_th, o_pend, info = oracle.hmc_trajectory(th, L, L, beta, eps, n_md, seed, t, lid)
+            assert abs(o["dH"][0] - info["dH"]) <= dh_tol, (t, o["dH"][0], info["dH"])
+            u = oracle.philox_words(seed, t, lid, 4, 0, 1)[0, 0] >> 8
+            u = u / 2.0 ** 24
+            gpu_acc = bool(o["accepted"][0])
+            if gpu_acc != info["accepted"]:
+                assert abs(u - np.exp(-info["dH"])) <= band, t
+                mismatches += 1
+            if gpu_acc:
+                if info["accepted"]:
+                    assert np.max(circ(g_th.reshape(-1), o_th)) <= 5e-5
+            else:
+                assert np.array_equal(g_th.reshape(-1), th.reshape(-1))
+            sums = oracle.measure(g_th.reshape(-1).astype(np.float64), L, L)
+            tol = record_tolerance(N)
+            for k, v in zip(("C", "Ix", "Iy", "Mx", "My"), sums):
+                assert abs(o[k][0] - v) <= tol, (t, k)
+            th = g_th
+    assert mismatches <= 1
+
+
+def test_rejection_leaves_state_untouched():
+    L = 64
+    with HMC(L, 1.0, 5, 0.9, 6) as h:
+        rejected = 0
+        for t in range(10):
+            before, _, _ = h.state()
+            h.run(1)
+            after, _, _ = h.state()
+            if not h.observables(t, 1)["accepted"][0]:
+                rejected += 1
+                assert np.array_equal(before, after)
+        _, _, acc = h.info()
+    assert rejected >= 5 and acc == 10 - rejected
+
+
+def test_reversibility_in_fp32():
+    L, beta, eps, n = 128, 1.0, 0.05, 20
+    th, p = random_state(L, 7)
+    with HMC(L, beta, 3, eps, n) as h:
+        h.set_state(th, p, 0)
+        h.integrate(n)
+        t1, p1, _ = h.state()
+        h.set_state(t1, -p1, 0)
+        h.integrate(n)
+        t2, p2, _ = h.state()
+    assert np.max(circ(t1.reshape(-1), th)) > 0.1
+    err_t = np.max(circ(t2.reshape(-1), th))
+    err_p = np.max(np.abs(-p2.reshape(-1) - p))
+    print(f"FP32 reversibility violation after {n}+{n} steps: angle {err_t:.2e}, momentum {err_p:.2e}")
+    assert err_t < 1e-4 and err_p < 1e-4
+
+
+@pytest.mark.parametrize("beta", [0.5, 1.0, 2.0])
+def test_hmc_samples_exact_2x2_energy(beta):
+    with HMC(2, beta, 31, 0.3, 4) as h:
+        h.run(20000)
+        e = h.observables()["e"]
+    m, err = jackknife_mean(e[2000:])
+    print(f"beta {beta}: gpu {m:.5f} +- {err:.5f} exact {ex.e_2x2_bessel(beta):.5f}")
+    assert abs(m - ex.e_2x2_bessel(beta)) <= 3.5 * err + 1e-6
+
+
+def test_creutz_equality_on_gpu():
+    with HMC(64, 1.0, 13, 0.1, 10) as h:
+        h.run(3000)
+        o = h.observables()
+    w = np.exp(-o["dH"][300:])
+    m, err = jackknife_mean(w)
+    rate = o["accepted"].mean()
+    print(f"<exp(-dH)> = {m:.4f} +- {err:.4f}, acceptance {rate:.3f}")
+    assert abs(m - 1.0) <= 3.5 * err
+    assert 0.3 < rate < 0.999
+
+
+def test_beta_zero_is_free_motion():
+    L, eps, n = 128, 0.25, 4
+    with HMC(L, 0.0, 3, eps, n) as h:
+        th0, _, _ = h.state()
+        h.run(5)
+        o = h.observables()
+    assert np.all(o["accepted"] == 1)
+    assert np.max(np.abs(o["dH"])) < 1e-6
+
+
+def test_large_lattice_one_step_matches_oracle():
+    """L = 4096 (the throughput size): one step from a random FP32 state."""
+    L, beta, eps = 4096, 1.12, 0.03
+    th, p = random_state(L, 5)
+    with HMC(L, beta, 7, eps, 1) as h:
+        h.set_state(th, p, 0)
+        h.integrate(1)
+        g_th, g_p, _ = h.state()
+    o_th, o_p = oracle.hmc_leapfrog(th, p, L, L, beta, eps, 1)
+    assert np.max(circ(g_th.reshape(-1), o_th)) <= ANGLE_STEP_TOL
+    assert np.max(np.abs(g_p.reshape(-1) - o_p) / (1 + np.abs(o_p))) <= ANGLE_STEP_TOL
+
+
+def test_error_paths():
+    """Refused arguments raise; as everywhere in the ABI the first error is
+    sticky in its context, so each case gets a fresh context."""
+    with HMC(16, 1.0, 1, 0.1, 3) as h:
+        with pytest.raises(X.XYError):
+            h.integrate(0)
+        with pytest.raises(X.XYError):
+            h.run(1)                                # sticky
+    with HMC(16, 1.0, 1, 0.1, 3) as h:
+        bad = np.zeros(256, np.float32)
+        bad[5] = np.nan
+        with pytest.raises(X.XYError):
+            h.set_state(bad)                        # refused before any work: not sticky
+        h.run(2)
+        assert h.info()[0] == 2
+    with HMC(16, 1.0, 1, 0.1, 3) as h:
+        with pytest.raises(X.XYError):
+            h.set_step(-1.0, 3)
+    with pytest.raises(X.XYError):
+        HMC(96, 1.0, 1, 0.1, 3, kernel="tiled")
