@@ -347,9 +347,10 @@ def measure_differentiation(dev, sincos, therm=10000, meas=100000):
 
 def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
     """The lattice sides of the paper's Table 1 (L = 128 ... 2048): fused-kernel
-    updates/s on the GPU against the FP64 oracle on one host core, whose ratio is
-    the analogue of the paper's "gain" over its serial code (which was HMC on a
-    2008 GPU against one Conroe core; context, not a target)."""
+    Metropolis updates/s and HMC leap-frog site-steps/s on the GPU against the
+    FP64 oracle on one host core; the HMC ratio is the analogue of the paper's
+    "gain" over its serial HMC code (2008 GPU against one Conroe core: context,
+    not a target)."""
     import torch
     import oracle
     from paper_0811_2111_gb300.lattice import Lattice
@@ -379,9 +380,122 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
             dt = time.perf_counter() - t
         cpu = L * L * n / dt
         out[str(L)] = {"gpu": gpu, "oracle_1core": cpu, "gain": gpu / cpu}
+        # the paper's own algorithm: HMC trajectories (unit length, eps ~ N^-1/4)
+        from paper_0811_2111_gb300 import workloads as WL
+        from paper_0811_2111_gb300.hmc import HMC
+        eps, n_md = WL.hmc_step_for(L)
+        n_traj = max(5, int(4e9 // (L * L * n_md)))
+        with HMC(L, 1.0, 3, eps, n_md, sincos=sincos, device=dev) as h:
+            h.run(5)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(h.stream)
+            h.run(n_traj)
+            e1.record(h.stream)
+            e1.synchronize()
+            hmc_gpu = L * L * n_md * n_traj / (e0.elapsed_time(e1) * 1e-3)
+            acc = float(h.observables(5)["accepted"].mean())
+        rng = np.random.default_rng(2)
+        th = rng.uniform(0, 2 * np.pi, L * L)
+        pm = rng.normal(size=L * L)
+        n = 1
+        while True:
+            t = time.perf_counter()
+            oracle.hmc_leapfrog(th, pm, L, L, 1.0, eps, n)
+            dt = time.perf_counter() - t
+            if dt >= cpu_seconds or n >= 4096:
+                break
+            n *= 2
+        hmc_cpu = L * L * n / dt
+        out[str(L)]["hmc"] = {"eps": eps, "n_md": n_md, "acceptance": acc,
+                              "gpu_site_steps": hmc_gpu, "oracle_1core_site_steps": hmc_cpu,
+                              "gain": hmc_gpu / hmc_cpu}
     return {"unit": UNIT, "beta": 1.0, "sizes": out,
             "paper_cuda_gain_for_context": {"128": 33, "256": 37, "512": 38, "1024": 30,
                                             "2048": 30}}
+
+
+# ---------------------------------------------------------------------------
+# Hybrid Monte Carlo (the paper's own algorithm)
+# ---------------------------------------------------------------------------
+
+HMC_BYTES_PER_SITE_STEP = 16.0   # leap-frog step kernel: 4 B angle + 4 B momentum read and written
+
+
+def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
+    """Leap-frog site-steps/s of HMC at L = 4096, beta = 1.12 (trajectories of 80
+    steps of 0.0125, from a state thermalised by 2000 Metropolis sweeps and 30
+    HMC trajectories), the step kernel's duration and HBM roofline, and the FP64
+    oracle's leap-frog on one host core."""
+    import torch
+    import oracle
+    from paper_0811_2111_gb300 import workloads as WL
+    from paper_0811_2111_gb300.hmc import HMC
+
+    from paper_0811_2111_gb300.lattice import Lattice
+
+    L, N = WL.HMC_L, WL.HMC_L * WL.HMC_L
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # thermalise with the Metropolis engine (cheap), then hand the state over
+    with Lattice(L, WL.HMC_BETA, WL.HMC_SEED, sincos=sincos, device=dev) as lat:
+        lat.reserve(WL.HMC_METROPOLIS_THERM)
+        lat.sweep(WL.HMC_METROPOLIS_THERM)
+        therm_state, _ = lat.state()
+    with HMC(L, WL.HMC_BETA, WL.HMC_SEED, WL.HMC_EPS, WL.HMC_NMD, sincos=sincos,
+             device=dev) as h:
+        h.set_state(therm_state, None, 0)
+        h.run(WL.HMC_THERM)
+        h.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(h.stream)
+        h.run(trajectories)
+        e1.record(h.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        o = h.observables(WL.HMC_THERM, trajectories)
+        # the step kernel alone: integrate(2) - integrate(1) = one step launch
+        reps = 20
+        t = {}
+        for n in (1, 2):
+            e0.record(h.stream)
+            for _ in range(reps):
+                h.integrate(n)
+            e1.record(h.stream)
+            e1.synchronize()
+            t[n] = e0.elapsed_time(e1) / reps
+    step_ms = t[2] - t[1]
+    achieved = HMC_BYTES_PER_SITE_STEP * N / (step_ms * 1e-3) / 1e9
+    hbm, peak_kind = measured_peaks()
+    # FP64 oracle leap-frog on one core (L = 512 sample)
+    Ls = 512
+    rng = np.random.default_rng(1)
+    th = rng.uniform(0, 2 * np.pi, Ls * Ls)
+    p = rng.normal(size=Ls * Ls)
+    n, dt = 1, 0.0
+    while True:
+        t0 = time.perf_counter()
+        oracle.hmc_leapfrog(th, p, Ls, Ls, WL.HMC_BETA, 0.05, n)
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds or n >= 256:
+            break
+        n *= 2
+    cpu = Ls * Ls * n / dt
+    value = N * WL.HMC_NMD * trajectories / (ms * 1e-3)
+    return {"workload": f"xy_hmc_L{L}_beta{WL.HMC_BETA}_eps{WL.HMC_EPS}_nmd{WL.HMC_NMD}",
+            "metric": "leap-frog site-steps/s", "value": value, "unit": "site-steps/s",
+            "trajectories_per_s": trajectories / (ms * 1e-3), "ms_per_trajectory": ms / trajectories,
+            "begin_final_accept_ms": t[1], "acceptance": float(o["accepted"].mean()),
+            "mean_exp_minus_dH": float(np.exp(-o["dH"]).mean()), "e": float(o["e"].mean()),
+            "roofline": {"kernel": "k_hmc_tile step (one leap-frog step per launch)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP, "ms_per_launch": step_ms},
+            "cpu_baseline": {"value": cpu, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"FP64 leap-frog, L={Ls}, {n} steps"},
+            "gain_vs_oracle_1core": value / cpu}
 
 
 def measure_precision(dev, sweeps=200):
@@ -544,7 +658,8 @@ def run_ours(args):
         extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
                  "differentiation": measure_differentiation(dev, args.sincos),
                  "precision": measure_precision(dev),
-                 "table1_sizes": measure_table1_sizes(dev, args.sincos)}
+                 "table1_sizes": measure_table1_sizes(dev, args.sincos),
+                 "hmc": measure_hmc(dev, args.sincos)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,

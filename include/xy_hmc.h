@@ -23,10 +23,11 @@
  * (0, t, lattice_id, 4).  The hot start is xy.h's (domain 0).
  *
  * Precision: angles and momenta FP32; the per-site terms of H_hmc and of the
- * bond/spin sums are formed in FP32 and each one is converted to 64-bit fixed
- * point before it is added (kinetic part 2^-24 units, the others 2^-30), so
- * every sum is exact, deterministic and independent of the launch shape; dH
- * and the test are FP64 on the device.
+ * bond/spin sums are formed in FP32 and each one is rounded to fixed point
+ * before it is added (the kinetic term p^2/2 to 2^-24, the bond term of C to
+ * 2^-30, the terms of Ix, Iy, Mx, My to 2^-21; sums are reported in 2^-24 and
+ * 2^-30 units), so every sum is exact, deterministic and independent of the
+ * launch shape; dH and the test are FP64 on the device.
  *
  * Layout: angles and momenta on the device in natural order [y][x] (L*L
  * floats each).  During a run the chain's state lives in one of three angle
@@ -64,13 +65,17 @@ typedef struct {
     int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM (force and sums) */
     uint64_t seed;        /* Philox key                                           */
     uint32_t lattice_id;  /* third Philox counter word                            */
-    int32_t kernel;       /* XY_HMC_KERNEL_AUTO, _TILED or _SITE (same results)   */
+    int32_t kernel;       /* XY_HMC_KERNEL_AUTO, _TILED, _SITE or _TILED2         */
 } xy_hmc_params;
 
-/* Leap-frog kernels: AUTO takes the tiled kernel (32 x 128 sites per CTA) when
- * L is a multiple of 128 and the one-thread-per-site kernel otherwise; TILED
- * requires L % 128 == 0.  Both give bit-identical angles, momenta and sums. */
-enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2 };
+/* Leap-frog kernels: TILED runs one step per launch on tiles of 32 x 128 sites
+ * (needs L % 128 == 0); TILED2 runs the full steps two per launch on the same
+ * tiles (temporal blocking: half the DRAM traffic, a recomputed halo of two);
+ * SITE is one thread per site (any L).  AUTO takes TILED when L % 128 == 0
+ * (measured fastest on GB300), else SITE.  All give bit-identical angles,
+ * momenta and sums. */
+enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2,
+       XY_HMC_KERNEL_TILED2 = 3 };
 
 /* One record per trajectory (96 bytes).
  *   sum       C, Ix, Iy, Mx, My of the state after the test (2^-30 units,
@@ -94,7 +99,7 @@ typedef struct {
  * momenta zero).
  *   p           parameters, copied and validated: L in [2, XY_MAX_L], beta >= 0
  *               and finite, J finite, eps > 0 and finite, n_md >= 1, sincos_mode
- *               and kernel valid (TILED needs L % 128 == 0); else XY_EINVAL.
+ *               and kernel valid (TILED, TILED2 need L % 128 == 0); else XY_EINVAL.
  *   cuda_stream a cudaStream_t, or NULL for the legacy default stream.
  *   d_angles    NULL: the library allocates all three angle buffers; else a
  *               caller-owned device buffer of >= L*L floats (16-byte aligned)

@@ -57,7 +57,7 @@ class xy_batch_params(C.Structure):
 XY_BATCH_MAX_L = 256
 XY_STATS_FIELDS = 8
 XY_HMC_K_SHIFT = 24
-XY_HMC_KERNEL_AUTO, XY_HMC_KERNEL_TILED, XY_HMC_KERNEL_SITE = 0, 1, 2
+XY_HMC_KERNEL_AUTO, XY_HMC_KERNEL_TILED, XY_HMC_KERNEL_SITE, XY_HMC_KERNEL_TILED2 = 0, 1, 2, 3
 
 
 class xy_hmc_params(C.Structure):

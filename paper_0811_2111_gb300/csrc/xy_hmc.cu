@@ -4,10 +4,12 @@
 //
 //   H_hmc = sum_s p_s^2 / 2 + beta H(theta),  F_s = -beta J sum_nn sin(t_s - t_j)
 //
-// A trajectory of n_md steps is n_md + 2 launches plus the test:
+// A trajectory of n_md steps is a chain of launches plus the test:
 //   begin   draw p (Philox domain 3, Box-Muller), sums of (theta_0, p_0),
 //           p += eps/2 F(theta_0), theta_1 = theta_0 + eps p
-//   step k  p += eps F(theta_k), theta_{k+1} = theta_k + eps p   (k = 1..n-1)
+//   step    p += eps F(theta_k), theta_{k+1} = theta_k + eps p; on the tiled
+//           path two such steps per launch (halo of two recomputed), one
+//           single step for an odd remainder
 //   final   p += eps/2 F(theta_n), sums of (theta_n, p_n)
 //   accept  one thread: dH from the exact fixed-point sums, u < exp(-dH)
 // Three angle buffers: the state stays untouched in buffer `cur` (restored on
@@ -71,21 +73,60 @@ __device__ __forceinline__ float hmc_force(float c, float s, float Sc, float Ss,
   return __fmul_rn(K, __fmaf_rn(c, Ss, -__fmul_rn(s, Sc)));
 }
 
+// Fixed-point rounding with FP32 operations only (GB300 runs float -> int64
+// conversions on its narrow FP64 pipe).  Adding 1.5 * 2^23 rounds any |x| <
+// 2^22 to the nearest integer (ties to even), which the low bits of the sum
+// then hold.  Larger values are split: x = h 2^21 + r with h the rounded
+// quotient, r exact in FP32 (|r| <= 2^20), then r is rounded the same way, so
+// h 2^21 + round(r) = round(x) exactly for |x| < 2^43.
+constexpr float kRoundMagic = 12582912.0f;            // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;           // its bit pattern
+constexpr float kTwo21 = 2097152.0f;
+
+// round(v 2^21) for |v 2^21| < 2^22.
+__device__ __forceinline__ int fx21(float v) {
+  return __float_as_int(__fmaf_rn(v, kTwo21, kRoundMagic)) - kRoundMagicBits;
+}
+
+// round(v 2^S) = h 2^21 + l for |v 2^S| < 2^43; h and l are added to hs, ls.
+template <int S>
+__device__ __forceinline__ void fx_split(float v, int& hs, int& ls) {
+  const float up = (float)(1ll << S);
+  const float t = __fmaf_rn(v, up / kTwo21, kRoundMagic);
+  const float hf = __fsub_rn(t, kRoundMagic);                          // exact
+  const float r = __fmaf_rn(v, up, -__fmul_rn(hf, kTwo21));            // exact
+  hs += __float_as_int(t) - kRoundMagicBits;
+  ls += __float_as_int(__fadd_rn(r, kRoundMagic)) - kRoundMagicBits;
+}
+
+// Per-thread fixed-point accumulators (int32 partial sums of at most 16 sites).
+struct HmcAcc {
+  int kh, kl;           // K = p^2/2 at 2^-24: h 2^21 + l
+  int ch, cl;           // C at 2^-30
+  int ix, iy, mx, my;   // at 2^-21
+};
+
+__device__ __forceinline__ void acc_zero(HmcAcc& a) {
+  a.kh = a.kl = a.ch = a.cl = a.ix = a.iy = a.mx = a.my = 0;
+}
+
 // Per-site terms of the sums, each rounded to fixed point before it is added:
 // K: p^2/2; C: cos(t - t_r) + cos(t - t_u); Ix: sin(t - t_r); Iy: sin(t - t_u);
-// Mx, My: c, s  (r = +x neighbour, u = +y neighbour).
+// Mx, My: c, s  (r = +x neighbour, u = +y neighbour).  The kinetic term is
+// capped at 2^18 (|p| < 724), far beyond any momentum of a working chain.
 __device__ __forceinline__ void hmc_terms(float p, float c, float s, float cr, float sr, float cu,
-                                          float su, long long v[kHmcSums]) {
+                                          float su, HmcAcc& acc) {
   const float cx = __fmaf_rn(c, cr, __fmul_rn(s, sr));
   const float cy = __fmaf_rn(c, cu, __fmul_rn(s, su));
   const float ix = __fmaf_rn(s, cr, -__fmul_rn(c, sr));
   const float iy = __fmaf_rn(s, cu, -__fmul_rn(c, su));
-  v[0] += __float2ll_rn(__fmul_rn(__fmul_rn(p, p), kKinFx));
-  v[1] += __float2ll_rn(__fmul_rn(__fadd_rn(cx, cy), kFx30));
-  v[2] += __float2ll_rn(__fmul_rn(ix, kFx30));
-  v[3] += __float2ll_rn(__fmul_rn(iy, kFx30));
-  v[4] += __float2ll_rn(__fmul_rn(c, kFx30));
-  v[5] += __float2ll_rn(__fmul_rn(s, kFx30));
+  const float kin = fminf(__fmul_rn(0.5f, __fmul_rn(p, p)), 262144.0f);
+  fx_split<24>(kin, acc.kh, acc.kl);
+  fx_split<30>(__fadd_rn(cx, cy), acc.ch, acc.cl);
+  acc.ix += fx21(ix);
+  acc.iy += fx21(iy);
+  acc.mx += fx21(c);
+  acc.my += fx21(s);
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
@@ -94,12 +135,19 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
   return v;
 }
 
-// Block sum of the six accumulators into dst (one 64-bit atomic each per CTA).
-// Called by every thread of the block.
+// Block sum of the accumulators into dst[0..5] (K at 2^-24, the others at
+// 2^-30; one 64-bit atomic each per CTA).  Called by every thread.
 template <int NWARPS>
-__device__ __forceinline__ void hmc_commit(long long v[kHmcSums], unsigned long long* dst,
+__device__ __forceinline__ void hmc_commit(const HmcAcc& a, unsigned long long* dst,
                                            long long (*sh)[kHmcSums]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long v[kHmcSums];
+  v[0] = ((long long)a.kh << 21) + (long long)a.kl;
+  v[1] = ((long long)a.ch << 21) + (long long)a.cl;
+  v[2] = (long long)a.ix << 9;
+  v[3] = (long long)a.iy << 9;
+  v[4] = (long long)a.mx << 9;
+  v[5] = (long long)a.my << 9;
 #pragma unroll
   for (int j = 0; j < kHmcSums; ++j) v[j] = warp_sum_ll(v[j]);
   if (lane == 0) {
@@ -120,19 +168,11 @@ __device__ __forceinline__ float* hmc_buf(const HmcArgs& a, int i) {
   return i == 0 ? a.th[0] : (i == 1 ? a.th[1] : a.th[2]);
 }
 
-// Source and destination angle buffers of a launch, from the state buffer `cur`.
-__device__ __forceinline__ void hmc_buffers(int kind, int k, int n_md, uint32_t cur, int* src,
-                                            int* dst) {
-  if (kind == kHmcBeginDraw || kind == kHmcBeginRead) {
-    *src = (int)cur;
-    *dst = (int)((cur + 1u) % 3u);
-  } else if (kind == kHmcStep) {
-    *src = (int)((cur + 1u + (uint32_t)((k - 1) & 1)) % 3u);
-    *dst = (int)((cur + 1u + (uint32_t)(k & 1)) % 3u);
-  } else {
-    *src = (int)((cur + 1u + (uint32_t)((n_md - 1) & 1)) % 3u);
-    *dst = *src;
-  }
+// Source and destination angle buffers of a launch, relative to the state
+// buffer `cur`.
+__device__ __forceinline__ void hmc_buffers(const HmcArgs& a, uint32_t cur, int* src, int* dst) {
+  *src = (int)((cur + (uint32_t)a.src_off) % 3u);
+  *dst = (int)((cur + (uint32_t)a.dst_off) % 3u);
 }
 
 // ---------------------------------------------------------------------------
@@ -150,7 +190,7 @@ constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kRowsPerThread = kTileRows / kTileWarps;   // 4
 
 template <int MODE, int KIND>
-__global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
+__global__ void __launch_bounds__(kTileThreads, KIND == kHmcStep ? 3 : 2) k_hmc_tile(HmcArgs a) {
   // cos / sin of tile rows -1 .. 32 (index row + 1); only each warp's first and
   // last row and the two halo rows are written and read
   __shared__ __align__(16) float sh_c[kTileRows + 2][kTileCols];
@@ -164,9 +204,8 @@ __global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
   const int x0 = blockIdx.x * kTileCols, y0 = blockIdx.y * kTileRows;
   const uint32_t cur = a.ctl->cur;
   int src, dst;
-  hmc_buffers(KIND, a.k, a.n_md, cur, &src, &dst);
+  hmc_buffers(a, cur, &src, &dst);
   const float* __restrict__ th_src = hmc_buf(a, src);
-  float* __restrict__ p_buf = a.p;
 
   // ---- loads: own 4 x 4 block, then halo sites ---------------------------
   const int xb = x0 + 4 * lane;
@@ -178,7 +217,7 @@ __global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
   if (KIND != kHmcBeginDraw) {
 #pragma unroll
     for (int r = 0; r < kRowsPerThread; ++r)
-      p4[r] = *reinterpret_cast<const float4*>(p_buf + (size_t)(yb + r) * L + xb);
+      p4[r] = *reinterpret_cast<const float4*>(a.p_in + (size_t)(yb + r) * L + xb);
   }
   // halo: threads 0..127 row y0-1, 128..255 row y0+32; threads 0..31 column
   // x0-1 and 32..63 column x0+128 (rows y0..y0+31)
@@ -248,7 +287,8 @@ __global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
   const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
   const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
 
-  long long acc[kHmcSums] = {0, 0, 0, 0, 0, 0};
+  HmcAcc acc;
+  acc_zero(acc);
   float4 tn[kRowsPerThread];
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r) {
@@ -296,7 +336,7 @@ __global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
   // ---- stores -------------------------------------------------------------
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r)
-    *reinterpret_cast<float4*>(p_buf + (size_t)(yb + r) * L + xb) = p4[r];
+    *reinterpret_cast<float4*>(a.p_out + (size_t)(yb + r) * L + xb) = p4[r];
   if (KIND != kHmcFinal) {
     float* __restrict__ th_dst = hmc_buf(a, dst);
 #pragma unroll
@@ -306,6 +346,142 @@ __global__ void __launch_bounds__(kTileThreads) k_hmc_tile(HmcArgs a) {
   if (KIND == kHmcBeginDraw || KIND == kHmcBeginRead)
     hmc_commit<kTileWarps>(acc, a.ctl->acc[0], red);
   if (KIND == kHmcFinal) hmc_commit<kTileWarps>(acc, a.ctl->acc[1], red);
+}
+
+// ---------------------------------------------------------------------------
+// Two full kick-drift steps per launch (temporal blocking).  A CTA of 256
+// threads owns 32 x 128 sites.  It stages the unit vectors of the tile plus a
+// halo of two (36 x 132) and the angles and momenta of the tile plus a halo of
+// one (34 x 130) in shared memory, runs the first step over tile + halo one,
+// then the second over the tile, and writes angles and momenta once: 8 bytes
+// read and 8 written per site for two steps (halo re-reads aside; the halo
+// rows are shared with the neighbouring tiles through L2).  The halo
+// steps recompute what the neighbouring CTAs compute, from the same inputs and
+// with the same arithmetic, so every copy agrees bit for bit.  Momenta are
+// read from one buffer and written to another (the halo reads old values).
+// ---------------------------------------------------------------------------
+constexpr int kP2Rows = 32;
+constexpr int kP2Cols = 128;
+constexpr int kP2Threads = 256;
+constexpr int kR2Rows = kP2Rows + 4, kR2Cols = kP2Cols + 4;    // halo two
+constexpr int kR1Rows = kP2Rows + 2, kR1Cols = kP2Cols + 2;    // halo one
+constexpr int kR2Sites = kR2Rows * kR2Cols;
+constexpr int kR1Sites = kR1Rows * kR1Cols;
+constexpr int kThIter = (kR2Sites + kP2Threads - 1) / kP2Threads;
+constexpr int kPIter = (kR1Sites + kP2Threads - 1) / kP2Threads;
+constexpr int kAIter = (kR1Sites + kP2Threads - 1) / kP2Threads;
+constexpr int kBIter = kP2Rows * kP2Cols / kP2Threads;
+constexpr size_t kCsBytes = sizeof(float2) * kR2Rows * kR2Cols;
+constexpr size_t kR1Bytes = sizeof(float) * kR1Rows * kR1Cols;
+constexpr size_t kP2Smem = kCsBytes + 2 * kR1Bytes;
+
+__device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <int MODE>
+__global__ void __launch_bounds__(kP2Threads, 3) k_hmc_tile2(HmcArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2 (*cs)[kR2Cols] = reinterpret_cast<float2 (*)[kR2Cols]>(smem);
+  float (*th)[kR1Cols] = reinterpret_cast<float (*)[kR1Cols]>(smem + kCsBytes);
+  float (*pm)[kR1Cols] = reinterpret_cast<float (*)[kR1Cols]>(smem + kCsBytes + kR1Bytes);
+
+  const int L = a.L;
+  const int x0 = blockIdx.x * kP2Cols, y0 = blockIdx.y * kP2Rows;
+  const int tid = threadIdx.x;
+  int src, dst;
+  hmc_buffers(a, a.ctl->cur, &src, &dst);
+  const float* __restrict__ th_src = hmc_buf(a, src);
+
+  // ---- staging: one site per thread and item, consecutive lanes on
+  // consecutive columns (coalesced loads, conflict-free shared stores);
+  // angles of tile + 2 -> unit vectors (and the angles of tile + 1), momenta
+  // of tile + 1.  All loads of a thread are issued before its sincos.
+  float tv[kThIter], pv[kPIter];
+#pragma unroll
+  for (int k = 0; k < kThIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR2Sites) {
+      const int row = i / kR2Cols, c = i - row * kR2Cols;
+      const int gy = wrap_near(y0 - 2 + row, L), gx = wrap_near(x0 - 2 + c, L);
+      tv[k] = th_src[(size_t)gy * L + gx];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR1Sites) {
+      const int row = i / kR1Cols, c = i - row * kR1Cols;
+      const int gy = wrap_near(y0 - 1 + row, L), gx = wrap_near(x0 - 1 + c, L);
+      pv[k] = a.p_in[(size_t)gy * L + gx];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kThIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR2Sites) {
+      const int row = i / kR2Cols, c = i - row * kR2Cols;
+      float sn, cn;
+      xyd::unit_vector<MODE>(tv[k], &sn, &cn);
+      cs[row][c] = make_float2(cn, sn);
+      if (row >= 1 && row <= kR1Rows && c >= 1 && c <= kR1Cols) th[row - 1][c - 1] = tv[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kPIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR1Sites) {
+      const int row = i / kR1Cols, c = i - row * kR1Cols;
+      pm[row][c] = pv[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- first step over tile + 1 --------------------------------------------
+  float2 nv[kAIter];
+#pragma unroll
+  for (int k = 0; k < kAIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR1Sites) {
+      const int r = i / kR1Cols, c = i - r * kR1Cols;   // halo-one frame
+      const float2 o = cs[r + 1][c + 1], l = cs[r + 1][c], rt = cs[r + 1][c + 2];
+      const float2 dn = cs[r][c + 1], up = cs[r + 2][c + 1];
+      const float Sc = xyd::nb_sum(l.x, rt.x, dn.x, up.x);
+      const float Ss = xyd::nb_sum(l.y, rt.y, dn.y, up.y);
+      const float p = __fmaf_rn(a.a, hmc_force(o.x, o.y, Sc, Ss, a.K), pm[r][c]);
+      const float t = hmc_wrap(__fmaf_rn(a.eps, p, th[r][c]));
+      pm[r][c] = p;
+      th[r][c] = t;
+      float sn, cn;
+      xyd::unit_vector<MODE>(t, &sn, &cn);
+      nv[k] = make_float2(cn, sn);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kAIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    if (i < kR1Sites) {
+      const int r = i / kR1Cols, c = i - r * kR1Cols;
+      cs[r + 1][c + 1] = nv[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- second step over the tile, written out ---------------------------
+  float* __restrict__ thd = hmc_buf(a, dst);
+#pragma unroll 4
+  for (int k = 0; k < kBIter; ++k) {
+    const int i = tid + k * kP2Threads;
+    const int r = i / kP2Cols, c = i - r * kP2Cols;      // tile frame
+    const float2 o = cs[r + 2][c + 2], l = cs[r + 2][c + 1], rt = cs[r + 2][c + 3];
+    const float2 dn = cs[r + 1][c + 2], up = cs[r + 3][c + 2];
+    const float Sc = xyd::nb_sum(l.x, rt.x, dn.x, up.x);
+    const float Ss = xyd::nb_sum(l.y, rt.y, dn.y, up.y);
+    const float p = __fmaf_rn(a.a, hmc_force(o.x, o.y, Sc, Ss, a.K), pm[r + 1][c + 1]);
+    const float t = hmc_wrap(__fmaf_rn(a.eps, p, th[r + 1][c + 1]));
+    const size_t g = (size_t)(y0 + r) * L + x0 + c;
+    thd[g] = t;
+    a.p_out[g] = p;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -321,9 +497,10 @@ __global__ void __launch_bounds__(kSiteThreads) k_hmc_site(HmcArgs a) {
   const uint32_t N = (uint32_t)L * (uint32_t)L;
   const uint32_t cur = a.ctl->cur;
   int src, dst;
-  hmc_buffers(KIND, a.k, a.n_md, cur, &src, &dst);
+  hmc_buffers(a, cur, &src, &dst);
   const float* __restrict__ th_src = hmc_buf(a, src);
-  long long acc[kHmcSums] = {0, 0, 0, 0, 0, 0};
+  HmcAcc acc;
+  acc_zero(acc);
   const uint32_t site = blockIdx.x * kSiteThreads + threadIdx.x;
   if (site < N) {
     const int y = (int)(site / (uint32_t)L), x = (int)(site - (uint32_t)y * (uint32_t)L);
@@ -338,7 +515,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_hmc_site(HmcArgs a) {
     xyd::unit_vector<MODE>(th_src[(size_t)yd * L + x], &sn[3], &cs[3]);
     xyd::unit_vector<MODE>(th_src[(size_t)yu * L + x], &sn[4], &cs[4]);
     float p = KIND == kHmcBeginDraw ? hmc_momentum(site, (uint32_t)a.ctl->traj, a.lattice_id, a.rk)
-                                    : a.p[site];
+                                    : a.p_in[site];
     const float Sc = xyd::nb_sum(cs[1], cs[2], cs[3], cs[4]);
     const float Ss = xyd::nb_sum(sn[1], sn[2], sn[3], sn[4]);
     const float F = hmc_force(cs[0], sn[0], Sc, Ss, a.K);
@@ -350,7 +527,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_hmc_site(HmcArgs a) {
     } else {
       hmc_buf(a, dst)[site] = hmc_wrap(__fmaf_rn(a.eps, p, t));
     }
-    a.p[site] = p;
+    a.p_out[site] = p;
   }
   if (KIND == kHmcBeginDraw || KIND == kHmcBeginRead)
     hmc_commit<kSiteThreads / 32>(acc, a.ctl->acc[0], red);
@@ -364,7 +541,7 @@ __global__ void k_hmc_accept(HmcArgs a, int mode, double beta, double J) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   HmcCtl* c = a.ctl;
   int fin, unused;
-  hmc_buffers(kHmcFinal, 0, a.n_md, c->cur, &fin, &unused);
+  hmc_buffers(a, c->cur, &fin, &unused);
   const long long dK = (long long)(c->acc[1][0] - c->acc[0][0]);
   const long long dC = (long long)(c->acc[1][1] - c->acc[0][1]);
   const double dH = (double)dK * 0x1p-24 - beta * J * ((double)dC * 0x1p-30);
@@ -398,7 +575,7 @@ __global__ void k_hmc_draw(HmcArgs a) {
   const uint32_t N = (uint32_t)a.L * (uint32_t)a.L;
   const uint32_t traj = (uint32_t)a.ctl->traj;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x)
-    a.p[s] = hmc_momentum(s, traj, a.lattice_id, a.rk);
+    a.p_out[s] = hmc_momentum(s, traj, a.lattice_id, a.rk);
 }
 
 __global__ void k_hmc_start(HmcArgs a, int hot) {
@@ -410,7 +587,7 @@ __global__ void k_hmc_start(HmcArgs a, int hot) {
       t = (float)(w.x >> 8) * xyd::kHotScale;
     }
     a.th[0][s] = t;
-    a.p[s] = 0.f;
+    a.p_out[s] = 0.f;
   }
 }
 
@@ -436,6 +613,12 @@ int grid_for(int64_t n, int threads) {
 
 template <int MODE>
 cudaError_t launch_mode(int kind, const HmcArgs& a, cudaStream_t stream) {
+  if (kind == kHmcStep2) {
+    if (!a.tiled || !a.pairs || a.p_in == a.p_out) return cudaErrorInvalidValue;
+    const dim3 grid(a.L / kP2Cols, a.L / kP2Rows);
+    k_hmc_tile2<MODE><<<grid, kP2Threads, kP2Smem, stream>>>(a);
+    return cudaGetLastError();
+  }
   if (a.tiled) {
     const dim3 grid(a.L / kTileCols, a.L / kTileRows);
     switch (kind) {
@@ -461,8 +644,24 @@ cudaError_t launch_mode(int kind, const HmcArgs& a, cudaStream_t stream) {
 
 bool hmc_tiled_ok(int L) { return L >= kTileCols && L % kTileCols == 0; }
 
+cudaError_t hmc_prepare(int sincos_mode) {
+  static bool done[3][64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int m = sincos_mode < 0 || sincos_mode > 2 ? 0 : sincos_mode;
+  if (dev >= 0 && dev < 64 && done[m][dev]) return cudaSuccess;
+  const void* f = m == 0 ? (const void*)k_hmc_tile2<0>
+                         : (m == 1 ? (const void*)k_hmc_tile2<1> : (const void*)k_hmc_tile2<2>);
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[m][dev] = true;
+  return e;
+}
+
 cudaError_t launch_hmc(int kind, int sincos_mode, const HmcArgs& a, cudaStream_t stream) {
-  if (kind < kHmcBeginDraw || kind > kHmcFinal) return cudaErrorInvalidValue;
+  if (kind < kHmcBeginDraw || kind > kHmcStep2) return cudaErrorInvalidValue;
   if (a.tiled && !hmc_tiled_ok(a.L)) return cudaErrorInvalidValue;
   switch (sincos_mode) {
     case 0: return launch_mode<0>(kind, a, stream);

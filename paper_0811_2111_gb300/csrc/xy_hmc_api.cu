@@ -58,7 +58,8 @@ struct xy_hmc {
   int device;
   float* th[3];                  // angle buffers (th[0] may be caller-owned)
   bool owns_th0;
-  float* d_p;                    // momenta
+  float* d_p;                    // momenta (between calls)
+  float* d_p2;                   // second momentum buffer of the two-step kernel
   xyk::HmcCtl* d_ctl;
   xy_hmc_record* d_rec;
   int64_t rec_cap;
@@ -141,51 +142,80 @@ xy_status validate(const xy_hmc_params* p) {
     return XY_EINVAL;
   }
   if (p->kernel != XY_HMC_KERNEL_AUTO && p->kernel != XY_HMC_KERNEL_TILED &&
-      p->kernel != XY_HMC_KERNEL_SITE) {
+      p->kernel != XY_HMC_KERNEL_SITE && p->kernel != XY_HMC_KERNEL_TILED2) {
     tmsg("bad kernel choice");
     return XY_EINVAL;
   }
-  if (p->kernel == XY_HMC_KERNEL_TILED && !xyk::hmc_tiled_ok(p->L)) {
+  if ((p->kernel == XY_HMC_KERNEL_TILED || p->kernel == XY_HMC_KERNEL_TILED2) &&
+      !xyk::hmc_tiled_ok(p->L)) {
     tmsg("the tiled kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
   }
   return XY_OK;
 }
 
-xyk::HmcArgs args_of(const xy_hmc* h, int n_md) {
+xyk::HmcArgs args_of(const xy_hmc* h) {
   xyk::HmcArgs a;
   for (int i = 0; i < 3; ++i) a.th[i] = h->th[i];
-  a.p = h->d_p;
+  a.p_in = h->d_p;
+  a.p_out = h->d_p;
   a.ctl = h->d_ctl;
   a.L = h->p.L;
   a.K = (float)(h->p.beta * h->p.J);
   a.eps = (float)h->p.eps;
   a.a = 0.5f * a.eps;
-  a.k = 0;
-  a.n_md = n_md;
+  a.src_off = 0;
+  a.dst_off = 0;
   a.rk = xyd::make_round_keys(h->p.seed);
   a.lattice_id = h->p.lattice_id;
-  a.tiled = h->p.kernel == XY_HMC_KERNEL_TILED ||
+  a.tiled = h->p.kernel == XY_HMC_KERNEL_TILED || h->p.kernel == XY_HMC_KERNEL_TILED2 ||
             (h->p.kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(h->p.L));
+  a.pairs = h->p.kernel == XY_HMC_KERNEL_TILED2;
   return a;
 }
 
 // Leap-frog of n steps from the state buffer (begin kind `begin`), then the
-// test (mode 0) or the commit of an integration (mode 1).
+// test (mode 0) or the commit of an integration (mode 1).  Angle buffers:
+// offset 0 (the state) -> 1, then 1 <-> 2 per launch; with two steps per
+// launch the momenta ping-pong between d_p and d_p2, and the final half kick
+// always leaves them in d_p.
 cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cudaStream_t s) {
-  xyk::HmcArgs a = args_of(h, n);
+  xyk::HmcArgs a = args_of(h);
   const int m = h->p.sincos_mode;
+  float* pcur = h->d_p;
+  float* pother = h->d_p2;
   a.a = 0.5f * a.eps;
+  a.src_off = 0;
+  a.dst_off = 1;
   cudaError_t e = xyk::launch_hmc(begin, m, a, s);
-  if (e != cudaSuccess) return e;
+  int off = 1;
   a.a = a.eps;
-  for (int k = 1; k < n && e == cudaSuccess; ++k) {
-    a.k = k;
-    e = xyk::launch_hmc(xyk::kHmcStep, m, a, s);
+  int left = n - 1;
+  while (e == cudaSuccess && left > 0) {
+    a.src_off = off;
+    a.dst_off = 3 - off;
+    if (a.pairs && left >= 2) {
+      a.p_in = pcur;
+      a.p_out = pother;
+      e = xyk::launch_hmc(xyk::kHmcStep2, m, a, s);
+      float* t = pcur;
+      pcur = pother;
+      pother = t;
+      left -= 2;
+    } else {
+      a.p_in = pcur;
+      a.p_out = pcur;
+      e = xyk::launch_hmc(xyk::kHmcStep, m, a, s);
+      left -= 1;
+    }
+    off = 3 - off;
   }
   if (e != cudaSuccess) return e;
   a.a = 0.5f * a.eps;
-  a.k = n;
+  a.src_off = off;
+  a.dst_off = off;
+  a.p_in = pcur;
+  a.p_out = h->d_p;
   e = xyk::launch_hmc(xyk::kHmcFinal, m, a, s);
   if (e != cudaSuccess) return e;
   return xyk::launch_hmc_accept(mode, a, h->p.beta, h->p.J, s);
@@ -197,7 +227,9 @@ cudaError_t capture(xy_hmc* h) {
     h->graph = nullptr;
   }
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+  cudaError_t e = xyk::hmc_prepare(h->p.sincos_mode);   // function attributes: not capturable
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   cudaError_t le = enqueue_trajectory(h, xyk::kHmcBeginDraw, h->p.n_md, 0, h->capture_stream);
   e = cudaStreamEndCapture(h->capture_stream, &g);
@@ -245,6 +277,7 @@ void release(xy_hmc* h) {
   for (int i = 0; i < 3; ++i)
     if (h->th[i] && (i > 0 || h->owns_th0)) cudaFree(h->th[i]);
   if (h->d_p) cudaFree(h->d_p);
+  if (h->d_p2) cudaFree(h->d_p2);
   if (h->d_ctl) cudaFree(h->d_ctl);
   if (h->d_rec) cudaFree(h->d_rec);
 }
@@ -293,8 +326,9 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
       if (!h->th[i]) e = cudaMalloc(&h->th[i], N * sizeof(float));
   }
   if (e == cudaSuccess) {
-    step = "momentum buffer";
+    step = "momentum buffers";
     e = cudaMalloc(&h->d_p, N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_p2, N * sizeof(float));
   }
   if (e == cudaSuccess) {
     step = "control block";
@@ -303,7 +337,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctl, 0, sizeof(xyk::HmcCtl), h->stream);
   if (e == cudaSuccess) {
     step = "start kernel";
-    e = xyk::launch_hmc_start(args_of(h, p->n_md), p->start == XY_START_HOT ? 1 : 0, h->stream);
+    e = xyk::launch_hmc_start(args_of(h), p->start == XY_START_HOT ? 1 : 0, h->stream);
   }
   if (e == cudaSuccess) {
     step = "synchronize";
@@ -336,7 +370,7 @@ xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
   if (!h->graph) H_CUDA(h, capture(h), "xy_hmc_run: graph capture");
   for (int64_t i = 0; i < n_traj; ++i)
     H_CUDA(h, cudaGraphLaunch(h->graph, h->stream), "xy_hmc_run: graph launch");
-  H_CUDA(h, xyk::launch_hmc_canonical(args_of(h, h->p.n_md), h->stream),
+  H_CUDA(h, xyk::launch_hmc_canonical(args_of(h), h->stream),
          "xy_hmc_run: state copy");
   h->rec_count += n_traj;
   h->next_traj += (uint64_t)n_traj;
@@ -348,9 +382,10 @@ xy_status xy_hmc_integrate(xy_hmc* h, int32_t n_steps) {
   if (st != XY_OK) return st;
   if (n_steps < 1 || n_steps > 1000000)
     return fail(h, XY_EINVAL, "xy_hmc_integrate: n_steps must be in [1, 1000000]");
+  H_CUDA(h, xyk::hmc_prepare(h->p.sincos_mode), "xy_hmc_integrate: kernel attributes");
   H_CUDA(h, enqueue_trajectory(h, xyk::kHmcBeginRead, n_steps, 1, h->stream),
          "xy_hmc_integrate: launch");
-  H_CUDA(h, xyk::launch_hmc_canonical(args_of(h, n_steps), h->stream),
+  H_CUDA(h, xyk::launch_hmc_canonical(args_of(h), h->stream),
          "xy_hmc_integrate: state copy");
   return XY_OK;
 }
@@ -358,7 +393,7 @@ xy_status xy_hmc_integrate(xy_hmc* h, int32_t n_steps) {
 xy_status xy_hmc_refresh(xy_hmc* h) {
   xy_status st = check(h);
   if (st != XY_OK) return st;
-  H_CUDA(h, xyk::launch_hmc_draw(args_of(h, h->p.n_md), h->stream), "xy_hmc_refresh");
+  H_CUDA(h, xyk::launch_hmc_draw(args_of(h), h->stream), "xy_hmc_refresh");
   return XY_OK;
 }
 

@@ -175,22 +175,29 @@ enum HmcKind {
   kHmcBeginDraw = 0,   // draw p, sums of (theta, p) -> acc[0], half kick, drift
   kHmcBeginRead = 1,   // p from the buffer, otherwise as kHmcBeginDraw
   kHmcStep = 2,        // full kick, drift
-  kHmcFinal = 3        // half kick, sums of (theta, p) -> acc[1], p written
+  kHmcFinal = 3,       // half kick, sums of (theta, p) -> acc[1], p written
+  kHmcStep2 = 4        // two full kick-drift steps in one launch (tiled only)
 };
 
+// Angle buffers are addressed relative to the state buffer `cur` (read on the
+// device): buffer (cur + off) % 3.  A trajectory reads offset 0 and writes 1
+// in its first launch, then alternates 1 <-> 2, so offset 0 (the state before
+// the trajectory) is never overwritten.
 struct HmcArgs {
   float* th[3];          // the three angle buffers, natural order
-  float* p;              // momenta, natural order
+  const float* p_in;     // momenta read by this launch (natural order)
+  float* p_out;          // momenta written (may equal p_in, except for kHmcStep2)
   HmcCtl* ctl;           // device control block
   int L;
   float K;               // beta * J
   float eps;             // step
   float a;               // kick coefficient of this launch (eps or eps / 2)
-  int k;                 // leap-frog step index of this launch (1-based for kHmcStep)
-  int n_md;              // steps of the trajectory (kHmcFinal reads theta_n)
+  int src_off;           // buffer offset read (the accept step: offset of theta_n)
+  int dst_off;           // buffer offset written
   xyd::RoundKeys rk;
   uint32_t lattice_id;
-  int tiled;             // 1: tiled kernel (needs hmc_tiled_ok(L)), 0: one thread per site
+  int tiled;             // 1: tiled kernels (needs hmc_tiled_ok(L)), 0: one thread per site
+  int pairs;             // 1: full steps two per launch (kHmcStep2; tiled only)
 };
 
 // One leap-frog launch of `kind` with the tiled or the per-site kernel (both
@@ -201,11 +208,13 @@ bool hmc_tiled_ok(int L);
 // commit of an integration; both move acc to last and clear acc.
 cudaError_t launch_hmc_accept(int mode, const HmcArgs& a, double beta, double J,
                               cudaStream_t stream);
-// Momenta of the current trajectory into a.p.
+// Momenta of the current trajectory into a.p_out.
 cudaError_t launch_hmc_draw(const HmcArgs& a, cudaStream_t stream);
-// Hot or cold start into th[0] (natural order), cur = 0.
+// Hot or cold start into th[0] (natural order), zero momenta into a.p_out.
 cudaError_t launch_hmc_start(const HmcArgs& a, int hot, cudaStream_t stream);
 // Move the state into th[0] if it lives elsewhere, and set cur = 0.
 cudaError_t launch_hmc_canonical(const HmcArgs& a, cudaStream_t stream);
+// Shared memory of the two-step kernel; set once per device before capture.
+cudaError_t hmc_prepare(int sincos_mode);
 
 }  // namespace xyk

@@ -49,6 +49,27 @@ DIFF_BETAS = tuple(np.round(np.linspace(0.9, 1.3, 41), 10).tolist())
 DIFF_SEED = 13
 
 
+# Hybrid Monte Carlo configuration (the paper's own algorithm, Sec. 1.2): the
+# throughput lattice and beta, unit trajectory length.  The step is scaled
+# with N^(-1/4), which keeps the mean energy violation, and so the acceptance,
+# roughly constant across sides (an L = 64 chain at eps = 0.1, 10 steps,
+# accepts ~0.83; L = 4096 has 4096 times the sites, eps / 8).
+HMC_L = 4096
+HMC_BETA = 1.12
+HMC_SEED = 7
+HMC_EPS = 0.0125
+HMC_NMD = 80
+HMC_METROPOLIS_THERM = 2000    # Metropolis sweeps that thermalise the HMC start
+HMC_THERM = 30                 # HMC trajectories discarded before timing
+
+
+def hmc_step_for(L, trajectory_length=1.0):
+    """(eps, n_md) with eps = 0.1 (64 / L)^(1/2) (i.e. N^(-1/4) scaling from L = 64)."""
+    eps = 0.1 * math.sqrt(64.0 / L)
+    n_md = max(1, int(round(trajectory_length / eps)))
+    return trajectory_length / n_md, n_md
+
+
 def random_angles(L, seed):
     """Uniform angles in [0, 2 pi) as float32 natural-order [L, L] (numpy PCG64)."""
     rng = np.random.default_rng(seed)

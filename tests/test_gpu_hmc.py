@@ -110,24 +110,28 @@ def test_n_steps_match_oracle(L):
     assert abs(-beta * sums["end"]["C"] - V1) <= 2e-5 * N
 
 
-@pytest.mark.parametrize("L", [128, 256])
-def test_tiled_and_site_kernels_are_bit_identical(L):
+@pytest.mark.parametrize("L,n_md", [(128, 7), (256, 7), (128, 1), (128, 2), (128, 4), (256, 5)])
+def test_tiled_and_site_kernels_are_bit_identical(L, n_md):
+    """The tiled kernel (one step per launch), the two-step kernel (full steps
+    two per launch, odd remainders singly) and the per-site kernel: same bits."""
     out = {}
-    for kernel in ("tiled", "site"):
-        with HMC(L, 1.05, 8, 0.1, 7, kernel=kernel, lattice_id=2) as h:
+    for kernel in ("tiled", "tiled2", "site"):
+        with HMC(L, 1.05, 8, 0.1, n_md, kernel=kernel, lattice_id=2) as h:
             h.run(6)
             th, p, _ = h.state()
             o = h.observables()
             h.integrate(3)
             th2, p2, _ = h.state()
             out[kernel] = (th, p, o, th2, p2, h.last_sums())
-    a, b = out["tiled"], out["site"]
-    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-    for k in ("C", "Ix", "Iy", "Mx", "My", "dH"):
-        assert np.array_equal(a[2][k], b[2][k]), k
-    assert np.array_equal(a[2]["accepted"], b[2]["accepted"])
-    assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4])
-    assert a[5] == b[5]
+    b = out["site"]
+    for name in ("tiled", "tiled2"):
+        a = out[name]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), name
+        for k in ("C", "Ix", "Iy", "Mx", "My", "dH"):
+            assert np.array_equal(a[2][k], b[2][k]), (name, k)
+        assert np.array_equal(a[2]["accepted"], b[2]["accepted"]), name
+        assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4]), name
+        assert a[5] == b[5], name
 
 
 @pytest.mark.parametrize("L,eps,n_md", [(8, 0.2, 5), (32, 0.1, 10), (128, 0.05, 12)])
@@ -260,5 +264,6 @@ def test_error_paths():
     with HMC(16, 1.0, 1, 0.1, 3) as h:
         with pytest.raises(X.XYError):
             h.set_step(-1.0, 3)
-    with pytest.raises(X.XYError):
-        HMC(96, 1.0, 1, 0.1, 3, kernel="tiled")
+    for kernel in ("tiled", "tiled2"):
+        with pytest.raises(X.XYError):
+            HMC(96, 1.0, 1, 0.1, 3, kernel=kernel)
