@@ -61,9 +61,10 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["large", "huge", "batch"], default="large",
+    ap.add_argument("--workload", choices=["large", "huge", "batch", "hmc"], default="large",
                     help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step; "
-                         "batch: 256 lattices with replica exchange, 100 rounds/step")
+                         "batch: 256 lattices with replica exchange, 100 rounds/step; "
+                         "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
@@ -380,6 +381,23 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
             dt = time.perf_counter() - t
         cpu = L * L * n / dt
         out[str(L)] = {"gpu": gpu, "oracle_1core": cpu, "gain": gpu / cpu}
+        if L <= 256:
+            # a single small lattice through the batched engine: one cluster-launched
+            # kernel runs 100 sweeps (bit-identical to the single-lattice kernels)
+            from paper_0811_2111_gb300.lattice import Batch
+            rounds = max(2, int(2e9 // (L * L * 100)))
+            with Batch([L], [1.0], 3, sweeps_per_round=100, sincos=sincos, device=dev) as b:
+                b.reserve(rounds + 2)
+                b.run(2)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(b.stream)
+                b.run(rounds)
+                e1.record(b.stream)
+                e1.synchronize()
+                out[str(L)]["gpu_batched_engine_100_sweeps_per_launch"] = (
+                    L * L * 100 * rounds / (e0.elapsed_time(e1) * 1e-3))
         # the paper's own algorithm: HMC trajectories (unit length, eps ~ N^-1/4)
         from paper_0811_2111_gb300 import workloads as WL
         from paper_0811_2111_gb300.hmc import HMC
@@ -548,6 +566,8 @@ def run_ours(args):
     B.build()
     if args.workload == "batch":
         return run_batch_line(args, dev, world, rank)
+    if args.workload == "hmc":
+        return run_hmc_line(args, dev, world, rank)
 
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
@@ -699,6 +719,65 @@ def run_batch_line(args, dev, world, rank):
                                             "l2": "flushed before every timed step (256 MiB write)",
                                             "parallelism": f"replicas x{world}"},
             "batch": r, "gpu_launches": r["launches_per_step"] * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_hmc_line(args, dev, world, rank, trajectories_per_step=10):
+    """Main line for --workload hmc: the paper's own algorithm (replicas with N > 1;
+    lattice id = rank)."""
+    import torch
+    from paper_0811_2111_gb300 import workloads as WL
+    from paper_0811_2111_gb300.hmc import HMC
+
+    from paper_0811_2111_gb300.lattice import Lattice
+
+    L, N = WL.HMC_L, WL.HMC_L * WL.HMC_L
+    sampler = ClockSampler(str(dev.index or 0))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with Lattice(L, WL.HMC_BETA, WL.HMC_SEED, sincos=args.sincos, lattice_id=rank,
+                 device=dev) as lat:
+        lat.reserve(WL.HMC_METROPOLIS_THERM)
+        lat.sweep(WL.HMC_METROPOLIS_THERM)
+        therm_state, _ = lat.state()
+    with HMC(L, WL.HMC_BETA, WL.HMC_SEED, WL.HMC_EPS, WL.HMC_NMD, sincos=args.sincos,
+             lattice_id=rank, device=dev) as h:
+        h.set_state(therm_state, None, 0)
+        for _ in range(max(3, args.warmup)):
+            h.run(trajectories_per_step)
+        h.synchronize()
+        barrier(world)
+        sampler.start()
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(h.stream)
+            h.run(trajectories_per_step)
+            e1.record(h.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        clocks = sampler.stop()
+        acc = float(h.observables()["accepted"][-args.steps * trajectories_per_step:].mean())
+    total_ms = max_over_ranks(sum(ms), world, dev)
+    steps_md = N * WL.HMC_NMD * trajectories_per_step * args.steps * world
+    line = {"metric": "HMC leap-frog site-steps/s", "value": steps_md / (total_ms * 1e-3),
+            "unit": "site-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"xy_hmc_L{L}_beta{WL.HMC_BETA}_eps{WL.HMC_EPS}_nmd{WL.HMC_NMD}",
+                       "trajectories_per_step": trajectories_per_step, "sincos": args.sincos,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "acceptance": acc,
+            "gpu_launches": ((WL.HMC_NMD + 2) * trajectories_per_step + 2) * args.steps,
+            "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
