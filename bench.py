@@ -398,6 +398,19 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
                 e1.synchronize()
                 out[str(L)]["gpu_batched_engine_100_sweeps_per_launch"] = (
                     L * L * 100 * rounds / (e0.elapsed_time(e1) * 1e-3))
+        # four replicas per site (the RGBA packing of Sec. 3.2), two-pass kernels
+        from paper_0811_2111_gb300.lattice import Quad
+        qs = max(20, int(2e9 // (4 * L * L)))
+        with Quad(L, [1.0, 1.0, 1.0, 1.0], 3, sincos=sincos, device=dev) as qd:
+            qd.sweep(5)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(qd.stream)
+            qd.sweep(qs)
+            e1.record(qd.stream)
+            e1.synchronize()
+            out[str(L)]["gpu_quad_4_replicas"] = 4 * L * L * qs / (e0.elapsed_time(e1) * 1e-3)
         # the paper's own algorithm: HMC trajectories (unit length, eps ~ N^-1/4)
         from paper_0811_2111_gb300 import workloads as WL
         from paper_0811_2111_gb300.hmc import HMC
@@ -514,6 +527,34 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
             "cpu_baseline": {"value": cpu, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"FP64 leap-frog, L={Ls}, {n} steps"},
             "gain_vs_oracle_1core": value / cpu}
+
+
+def measure_quad(dev, sincos, sweeps=200):
+    """Four replicas per site at L = 4096 (betas 1.00, 1.06, 1.12, 1.18): updates/s
+    over all replicas, against the single-lattice fused kernel of the main line."""
+    import torch
+    from paper_0811_2111_gb300.lattice import Quad
+
+    L = 4096
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=sincos, device=dev) as q:
+        q.sweep(10)
+        torch.cuda.synchronize(dev)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(q.stream)
+        q.sweep(sweeps)
+        e1.record(q.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        acc = [float(q.observables(r, 10)["accepted"].mean()) / (L * L) for r in range(4)]
+    value = 4 * L * L * sweeps / (ms * 1e-3)
+    return {"workload": "xy_quad_L4096_4replicas_beta1.00-1.18", "value": value, "unit": UNIT,
+            "ms_per_sweep": ms / sweeps, "acceptance": acc,
+            "bytes_per_update": 12.0,
+            "hbm_achieved_gbs": 12.0 * value / 1e9,
+            "launches_per_sweep": 2}
 
 
 def measure_precision(dev, sweeps=200):
@@ -679,7 +720,8 @@ def run_ours(args):
                  "differentiation": measure_differentiation(dev, args.sincos),
                  "precision": measure_precision(dev),
                  "table1_sizes": measure_table1_sizes(dev, args.sincos),
-                 "hmc": measure_hmc(dev, args.sincos)}
+                 "hmc": measure_hmc(dev, args.sincos),
+                 "quad": measure_quad(dev, args.sincos)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,

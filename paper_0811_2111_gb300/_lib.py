@@ -137,6 +137,14 @@ def lib():
         "xy_hmc_synchronize": (st, [P]),
         "xy_hmc_destroy": (st, [P]),
         "xy_hmc_last_error": (C.c_char_p, [P]),
+        "xy_quad_create": (st, [C.POINTER(xy_params), P, P, C.POINTER(P)]),
+        "xy_quad_sweep": (st, [P, C.c_int64]),
+        "xy_quad_measure": (st, [P, C.c_int32, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),
+        "xy_quad_get_state": (st, [P, C.c_int32, P, C.POINTER(C.c_uint64)]),
+        "xy_quad_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+        "xy_quad_synchronize": (st, [P]),
+        "xy_quad_destroy": (st, [P]),
+        "xy_quad_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -405,4 +413,59 @@ def xy_hmc_destroy(h):
 
 def xy_hmc_last_error(h=None):
     m = lib().xy_hmc_last_error(h)
+    return m.decode() if m else ""
+
+
+# -- four replicas per site (include/xy_quad.h) ---------------------------------
+
+XY_QUAD_REPLICAS = 4
+
+
+def quad_check(status, q=None):
+    if status != XY_OK:
+        msg = lib().xy_quad_last_error(q)
+        raise XYError(status, msg.decode() if msg else "")
+    return status
+
+
+def xy_quad_create(params, betas, stream_ptr=None):
+    q = C.c_void_p()
+    b = (C.c_double * 4)(*[float(v) for v in betas])
+    quad_check(lib().xy_quad_create(C.byref(params), b, stream_ptr, C.byref(q)))
+    return q
+
+
+def xy_quad_sweep(q, n):
+    quad_check(lib().xy_quad_sweep(q, n), q)
+
+
+def xy_quad_measure(q, replica, first, count):
+    out = (xy_obs * max(count, 1))()
+    quad_check(lib().xy_quad_measure(q, replica, first, count, out), q)
+    return out if count > 0 else (xy_obs * 0)()
+
+
+def xy_quad_get_state(q, replica, host_ptr):
+    t = C.c_uint64()
+    quad_check(lib().xy_quad_get_state(q, replica, host_ptr, C.byref(t)), q)
+    return t.value
+
+
+def xy_quad_info(q):
+    r = C.c_int64()
+    t = C.c_uint64()
+    quad_check(lib().xy_quad_info(q, C.byref(r), C.byref(t)), q)
+    return r.value, t.value
+
+
+def xy_quad_synchronize(q):
+    quad_check(lib().xy_quad_synchronize(q), q)
+
+
+def xy_quad_destroy(q):
+    quad_check(lib().xy_quad_destroy(q))
+
+
+def xy_quad_last_error(q=None):
+    m = lib().xy_quad_last_error(q)
     return m.decode() if m else ""

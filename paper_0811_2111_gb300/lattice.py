@@ -252,3 +252,74 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Quad:
+    """Four replicas of one L x L lattice packed per site (``xy_quad_*``, the RGBA
+    packing of Sec. 3.2): replica r has lattice id lattice_id + r and beta betas[r]."""
+
+    def __init__(self, L, betas, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
+                 reduce="fp64", lattice_id=0, device=None, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        if len(betas) != X.XY_QUAD_REPLICAS:
+            raise ValueError("need four betas")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.L = int(L)
+        p = X.xy_params()
+        p.L = self.L
+        p.start = {"hot": X.XY_START_HOT, "cold": X.XY_START_COLD}[start]
+        p.beta = 0.0
+        p.J = float(J)
+        p.delta = float(delta)
+        p.seed = int(seed)
+        p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
+                         "libm": X.XY_SINCOS_LIBM}[sincos]
+        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.lattice_id = int(lattice_id)
+        p.algorithm = X.XY_ALGO_AUTO
+        self.params = p
+        with torch.cuda.device(self.device):
+            self.q = X.xy_quad_create(p, betas, C.c_void_p(self.stream.cuda_stream))
+
+    def sweep(self, n=1):
+        X.xy_quad_sweep(self.q, n)
+
+    def info(self):
+        return X.xy_quad_info(self.q)
+
+    def observables(self, replica, first=0, count=None):
+        n, _ = X.xy_quad_info(self.q)
+        count = n - first if count is None else count
+        obs = X.xy_quad_measure(self.q, replica, first, count)
+        names = ["e", "abs_m", "upsilon", "C", "Ix", "Iy", "Mx", "My", "beta"]
+        out = {k: np.array([getattr(o, k) for o in obs], np.float64) for k in names}
+        out["accepted"] = np.array([o.accepted for o in obs], np.uint64)
+        return out
+
+    def state(self, replica):
+        buf = np.empty(self.L * self.L, np.float32)
+        nxt = X.xy_quad_get_state(self.q, replica, buf.ctypes.data_as(C.c_void_p))
+        return buf.reshape(self.L, self.L), nxt
+
+    def synchronize(self):
+        X.xy_quad_synchronize(self.q)
+
+    def close(self):
+        if getattr(self, "q", None) is not None:
+            X.xy_quad_destroy(self.q)
+            self.q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -149,3 +149,19 @@ def test_hmc_create_without_device_fails_cleanly(lib):
     assert st in (X.XY_ECUDA, X.XY_ENOMEM)
     assert h.value is None
     assert "xy_hmc_create" in X.xy_hmc_last_error(None)
+
+
+def test_quad_create_rejects_bad_parameters(lib):
+    q = C.c_void_p()
+    good = (C.c_double * 4)(1.0, 1.0, 1.0, 1.0)
+    for kw in (dict(L=3), dict(L=0), dict(delta=0.0), dict(start=5), dict(sincos_mode=7),
+               dict(reduce_mode=3), dict(J=float("nan"))):
+        assert lib.xy_quad_create(C.byref(_params(**kw)), good, None, C.byref(q)) == X.XY_EINVAL
+        assert q.value is None
+    bad = (C.c_double * 4)(1.0, float("nan"), 1.0, 1.0)
+    assert lib.xy_quad_create(C.byref(_params()), bad, None, C.byref(q)) == X.XY_EINVAL
+    assert "beta[1]" in X.xy_quad_last_error(None)
+    assert lib.xy_quad_create(C.byref(_params()), None, None, C.byref(q)) == X.XY_EINVAL
+    assert lib.xy_quad_sweep(None, 1) == X.XY_EINVAL
+    assert lib.xy_quad_destroy(None) == X.XY_OK
+    assert lib.xy_quad_sweep(C.c_void_p(0x3000), 1) == X.XY_ESTATE

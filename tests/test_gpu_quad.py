@@ -1,0 +1,87 @@
+"""Four replicas per site (the RGBA packing of Sec. 3.2) against single lattices.
+
+Replica r of a quad context must be the single lattice with lattice id
+lattice_id + r and beta betas[r], bit for bit in its angles and accept counts
+(the same Philox counters and per-site arithmetic), with record sums equal to
+the reduction's rounding; and, through that, it inherits the single lattice's
+lock-step parity with the oracle (checked directly on a small case too).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import ANGLE_TOL, lockstep_sweep, record_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300 import _lib as X  # noqa: E402
+from paper_0811_2111_gb300.lattice import Lattice, Quad  # noqa: E402
+
+BETAS = [0.7, 1.0, 1.12, 1.4]
+
+
+@pytest.mark.parametrize("L", [2, 6, 34, 64, 130, 256])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "fp64"),
+                                           ("accurate", "compensated")])
+def test_replicas_equal_single_lattices(L, sincos, reduce):
+    sweeps = 7
+    with Quad(L, BETAS, 19, sincos=sincos, reduce=reduce, lattice_id=40) as q:
+        q.sweep(sweeps)
+        states = [q.state(r)[0] for r in range(4)]
+        obs = [q.observables(r) for r in range(4)]
+    for r, beta in enumerate(BETAS):
+        with Lattice(L, beta, 19, sincos=sincos, reduce=reduce, lattice_id=40 + r,
+                     algorithm="two_pass") as lat:
+            lat.sweep(sweeps)
+            s, _ = lat.state()
+            o = lat.observables()
+        assert np.array_equal(states[r], s), (L, r)
+        assert np.array_equal(obs[r]["accepted"], o["accepted"]), (L, r)
+        assert np.all(obs[r]["beta"] == beta)
+        tol = record_tolerance(L * L, fast=(sincos == "fast"))
+        for k in ("C", "Ix", "Iy", "Mx", "My"):
+            assert np.max(np.abs(obs[r][k] - o[k])) <= tol, (L, r, k)
+
+
+def test_hot_start_and_cold_start():
+    with Quad(64, BETAS, 5, lattice_id=3) as q:
+        hot = [q.state(r)[0] for r in range(4)]
+    for r in range(4):
+        with Lattice(64, 1.0, 5, lattice_id=3 + r, algorithm="two_pass") as lat:
+            assert np.array_equal(hot[r], lat.state()[0])
+    with Quad(16, BETAS, 5, start="cold") as q:
+        assert all(np.all(q.state(r)[0] == 0) for r in range(4))
+
+
+def test_lockstep_with_oracle():
+    L, seed = 32, 3
+    with Quad(L, BETAS, seed, lattice_id=7) as q:
+        before = [q.state(r)[0] for r in range(4)]
+        for i in range(3):
+            q.sweep(1)
+            for r in range(4):
+                after = q.state(r)[0]
+                red, blk = lockstep_sweep(before[r], after, L, BETAS[r], seed, i, lattice_id=7 + r)
+                assert red.out_band_mismatch == 0 and blk.out_band_mismatch == 0
+                assert max(red.max_angle_err, blk.max_angle_err) <= ANGLE_TOL
+                before[r] = after
+
+
+def test_error_paths():
+    with pytest.raises(X.XYError):
+        Quad(15, BETAS, 1)
+    with pytest.raises(X.XYError):
+        Quad(16, [1.0, -1.0, 1.0, 1.0], 1)
+    with Quad(16, BETAS, 1) as q:
+        q.sweep(2)
+        with pytest.raises(X.XYError):
+            q.observables(4)
+    with Quad(16, BETAS, 1) as q:
+        with pytest.raises(X.XYError):
+            q.sweep(-1)
