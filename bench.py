@@ -520,7 +520,8 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
             "trajectories_per_s": trajectories / (ms * 1e-3), "ms_per_trajectory": ms / trajectories,
             "begin_final_accept_ms": t[1], "acceptance": float(o["accepted"].mean()),
             "mean_exp_minus_dH": float(np.exp(-o["dH"]).mean()), "e": float(o["e"].mean()),
-            "roofline": {"kernel": "k_hmc_tile step (one leap-frog step per launch)", "bound": "hbm",
+            "roofline": {"kernel": "k_hmc_step_tma (one leap-frog step per launch, TMA-staged)",
+                         "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm,
                          "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP, "ms_per_launch": step_ms},

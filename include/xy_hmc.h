@@ -65,17 +65,21 @@ typedef struct {
     int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM (force and sums) */
     uint64_t seed;        /* Philox key                                           */
     uint32_t lattice_id;  /* third Philox counter word                            */
-    int32_t kernel;       /* XY_HMC_KERNEL_AUTO, _TILED, _SITE or _TILED2         */
+    int32_t kernel;       /* XY_HMC_KERNEL_AUTO, _TILED, _SITE, _TILED2, _TILED_TMA */
 } xy_hmc_params;
 
 /* Leap-frog kernels: TILED runs one step per launch on tiles of 32 x 128 sites
- * (needs L % 128 == 0); TILED2 runs the full steps two per launch on the same
- * tiles (temporal blocking: half the DRAM traffic, a recomputed halo of two);
- * SITE is one thread per site (any L).  AUTO takes TILED when L % 128 == 0
- * (measured fastest on GB300), else SITE.  All give bit-identical angles,
- * momenta and sums. */
+ * (needs L % 128 == 0); TILED_TMA runs the full steps with a persistent grid
+ * that streams each tile into double-buffered shared memory with the tensor
+ * memory accelerator (needs L % 128 == 0 and the driver's tensor-map encoder;
+ * begin and final launches as TILED); TILED2 runs the full steps two per
+ * launch (temporal blocking: half the DRAM traffic, a recomputed halo of two);
+ * SITE is one thread per site (any L).  AUTO takes TILED_TMA when L % 128 == 0
+ * and the encoder is available (TILED if not), else SITE; on GB300 TILED_TMA
+ * measured 54.4 us per step at L = 4096 against 57.0 for TILED and 58.3 for
+ * TILED2.  All give bit-identical angles, momenta and sums. */
 enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2,
-       XY_HMC_KERNEL_TILED2 = 3 };
+       XY_HMC_KERNEL_TILED2 = 3, XY_HMC_KERNEL_TILED_TMA = 4 };
 
 /* One record per trajectory (96 bytes).
  *   sum       C, Ix, Iy, Mx, My of the state after the test (2^-30 units,
@@ -99,7 +103,8 @@ typedef struct {
  * momenta zero).
  *   p           parameters, copied and validated: L in [2, XY_MAX_L], beta >= 0
  *               and finite, J finite, eps > 0 and finite, n_md >= 1, sincos_mode
- *               and kernel valid (TILED, TILED2 need L % 128 == 0); else XY_EINVAL.
+ *               and kernel valid (TILED, TILED2, TILED_TMA need L % 128 == 0);
+ *               else XY_EINVAL.
  *   cuda_stream a cudaStream_t, or NULL for the legacy default stream.
  *   d_angles    NULL: the library allocates all three angle buffers; else a
  *               caller-owned device buffer of >= L*L floats (16-byte aligned)
@@ -130,6 +135,9 @@ xy_status xy_hmc_refresh(xy_hmc *h);
  * out[0..5] = K, C, Ix, Iy, Mx, My at its start, out[6..11] the same at its
  * end (K = sum p^2/2; H_hmc = K - beta J C). */
 xy_status xy_hmc_last_sums(xy_hmc *h, double out[12]);
+
+/* Calls that synchronize also check the device error word: a kernel whose
+ * bounded wait for its data ran out (TILED_TMA) makes them return XY_ETIMEOUT. */
 
 /* Observables of records [first, first + count) (synchronizes), as in
  * xy_measure: e, abs_m, upsilon, the five sums, accepted (0/1) and beta;

@@ -19,9 +19,11 @@
 // and converted to 64-bit fixed point before any addition: exact, and the
 // same for every launch shape (the tiled and per-site kernels agree bit for
 // bit in angles, momenta and sums).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "xy_internal.h"
 
@@ -349,6 +351,245 @@ __global__ void __launch_bounds__(kTileThreads, KIND == kHmcStep ? 3 : 2) k_hmc_
 }
 
 // ---------------------------------------------------------------------------
+// Persistent TMA step kernel: the same step as k_hmc_tile<MODE, kHmcStep>, but
+// a grid of about two CTAs per SM walks the tiles, and each CTA streams its
+// next tiles' angles and momenta (two 32 x 128 boxes, 32 KB) into a
+// double-buffered shared-memory stage with cp.async.bulk.tensor, completing on
+// an mbarrier, while it computes the current tile.  The one-site halo (320
+// floats) is read with plain loads issued before the wait.  Every wait is
+// bounded: thread 0 polls the stage's barrier a fixed number of times and
+// shares the outcome, so a CTA either proceeds or returns as a whole, setting
+// HmcCtl::error.
+// ---------------------------------------------------------------------------
+constexpr int kTmaBox = kTileRows * kTileCols;                 // floats per box
+constexpr uint32_t kTmaStageBytes = 2u * kTmaBox * sizeof(float);
+constexpr size_t kTmaSmem = 2 * (size_t)kTmaStageBytes;       // two stages
+constexpr long long kSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_hmc_step_tma(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+                   const __grid_constant__ CUtensorMap map2, const __grid_constant__ CUtensorMap mapp,
+                   HmcArgs a, int tiles_x, int n_tiles) {
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(16) float sh_c[kTileRows + 2][kTileCols];
+  __shared__ __align__(16) float sh_s[kTileRows + 2][kTileCols];
+  __shared__ float side_c[2][kTileRows];
+  __shared__ float side_s[2][kTileRows];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int stage_ok;
+
+  const int L = a.L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int src, dst;
+  hmc_buffers(a, a.ctl->cur, &src, &dst);
+  const CUtensorMap* mth = src == 0 ? &map0 : (src == 1 ? &map1 : &map2);
+  const float* __restrict__ th_src = hmc_buf(a, src);
+  float* __restrict__ th_dst = hmc_buf(a, dst);
+  // stage s: angles [32][128] then momenta [32][128]
+  auto stage_th = [&](int s) {
+    return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes);
+  };
+  auto stage_p = [&](int s) {
+    return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes +
+                                                 kTmaBox * sizeof(float));
+  };
+  // thread 0's bookkeeping: loads issued into / waited for on each stage
+  int issued[2] = {0, 0}, waited[2] = {0, 0};
+  auto issue = [&](int t, int s) {
+    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * kTileRows;
+    mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
+    tma_load_2d(stage_th(s), mth, x0, y0, &bar[s]);
+    tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
+    ++issued[s];
+  };
+  auto bounded_wait = [&](int s) {
+    const uint32_t parity = (uint32_t)(waited[s] & 1);
+    for (long long i = 0; i < kSpinLimit; ++i) {
+      if (mbar_try_wait(&bar[s], parity)) {
+        ++waited[s];
+        return true;
+      }
+    }
+    return false;
+  };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    fence_async_shared();
+    for (int s = 0; s < 2; ++s) {
+      const int t = blockIdx.x + s * gridDim.x;
+      if (t < n_tiles) issue(t, s);
+    }
+  }
+  __syncthreads();
+
+  int it = 0;
+  for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * kTileRows;
+    // halo loads first: rows y0-1, y0+32 (threads 0..127 / 128..255), columns
+    // x0-1 and x0+128 (threads 0..31 / 32..63)
+    const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1)
+                                   : (y0 + kTileRows == L ? 0 : y0 + kTileRows);
+    const float th_row = th_src[(size_t)hy * L + x0 + (tid & (kTileCols - 1))];
+    float th_side = 0.f;
+    const bool side = tid < 64;
+    if (side) {
+      const int sx = tid < 32 ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
+      th_side = th_src[(size_t)(y0 + (tid & 31)) * L + sx];
+    }
+    // wait for this tile's stage (bounded; one thread polls, all follow).  On
+    // a timeout the CTA flags the error, drains (bounded) whatever loads it
+    // still has in flight into its shared memory, and returns as a whole.
+    if (tid == 0) {
+      const bool ok = bounded_wait(s);
+      if (!ok) {
+        atomicOr(&a.ctl->error, 1u);
+        for (int q = 0; q < 2; ++q)
+          while (waited[q] < issued[q] && bounded_wait(q)) {
+          }
+      }
+      stage_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!stage_ok) return;
+
+    const int xb = 4 * lane, rb0 = kRowsPerThread * warp;
+    float4 t4[kRowsPerThread], p4[kRowsPerThread];
+    {
+      float (*sth)[kTileCols] = stage_th(s);
+      float (*sp)[kTileCols] = stage_p(s);
+#pragma unroll
+      for (int r = 0; r < kRowsPerThread; ++r) {
+        t4[r] = *reinterpret_cast<const float4*>(&sth[rb0 + r][xb]);
+        p4[r] = *reinterpret_cast<const float4*>(&sp[rb0 + r][xb]);
+      }
+    }
+    float c[kRowsPerThread][4], sn[kRowsPerThread][4];
+#pragma unroll
+    for (int r = 0; r < kRowsPerThread; ++r) {
+      xyd::unit_vector<MODE>(t4[r].x, &sn[r][0], &c[r][0]);
+      xyd::unit_vector<MODE>(t4[r].y, &sn[r][1], &c[r][1]);
+      xyd::unit_vector<MODE>(t4[r].z, &sn[r][2], &c[r][2]);
+      xyd::unit_vector<MODE>(t4[r].w, &sn[r][3], &c[r][3]);
+    }
+    {
+      float hs, hc;
+      xyd::unit_vector<MODE>(th_row, &hs, &hc);
+      const int row = tid < kTileCols ? 0 : kTileRows + 1;
+      sh_c[row][tid & (kTileCols - 1)] = hc;
+      sh_s[row][tid & (kTileCols - 1)] = hs;
+      if (side) {
+        xyd::unit_vector<MODE>(th_side, &hs, &hc);
+        side_c[tid >> 5][tid & 31] = hc;
+        side_s[tid >> 5][tid & 31] = hs;
+      }
+      const int rf = rb0 + 1, rl = rb0 + kRowsPerThread;
+      *reinterpret_cast<float4*>(&sh_c[rf][xb]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
+      *reinterpret_cast<float4*>(&sh_s[rf][xb]) = make_float4(sn[0][0], sn[0][1], sn[0][2], sn[0][3]);
+      *reinterpret_cast<float4*>(&sh_c[rl][xb]) = make_float4(c[3][0], c[3][1], c[3][2], c[3][3]);
+      *reinterpret_cast<float4*>(&sh_s[rl][xb]) = make_float4(sn[3][0], sn[3][1], sn[3][2], sn[3][3]);
+    }
+    __syncthreads();   // stage s fully read; edges visible
+    if (tid == 0) {
+      const int tn = t + 2 * gridDim.x;
+      if (tn < n_tiles) {
+        fence_async_shared();
+        issue(tn, s);
+      }
+    }
+
+    const float4 cdn = *reinterpret_cast<const float4*>(&sh_c[rb0][xb]);
+    const float4 sdn = *reinterpret_cast<const float4*>(&sh_s[rb0][xb]);
+    const float4 cup = *reinterpret_cast<const float4*>(&sh_c[rb0 + kRowsPerThread + 1][xb]);
+    const float4 sup = *reinterpret_cast<const float4*>(&sh_s[rb0 + kRowsPerThread + 1][xb]);
+    const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
+    const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
+#pragma unroll
+    for (int r = 0; r < kRowsPerThread; ++r) {
+      float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
+      float sl = __shfl_up_sync(0xffffffffu, sn[r][3], 1);
+      float cr = __shfl_down_sync(0xffffffffu, c[r][0], 1);
+      float sr = __shfl_down_sync(0xffffffffu, sn[r][0], 1);
+      const int row = rb0 + r;
+      if (lane == 0) {
+        cl = side_c[0][row];
+        sl = side_s[0][row];
+      }
+      if (lane == 31) {
+        cr = side_c[1][row];
+        sr = side_s[1][row];
+      }
+      float pr[4] = {p4[r].x, p4[r].y, p4[r].z, p4[r].w};
+      const float tr[4] = {t4[r].x, t4[r].y, t4[r].z, t4[r].w};
+      float out[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float nlc = j == 0 ? cl : c[r][j - 1], nls = j == 0 ? sl : sn[r][j - 1];
+        const float nrc = j == 3 ? cr : c[r][j + 1], nrs = j == 3 ? sr : sn[r][j + 1];
+        const float ndc = r == 0 ? cdn_a[j] : c[r - 1][j], nds = r == 0 ? sdn_a[j] : sn[r - 1][j];
+        const float nuc = r == kRowsPerThread - 1 ? cup_a[j] : c[r + 1][j];
+        const float nus = r == kRowsPerThread - 1 ? sup_a[j] : sn[r + 1][j];
+        const float Sc = xyd::nb_sum(nlc, nrc, ndc, nuc);
+        const float Ss = xyd::nb_sum(nls, nrs, nds, nus);
+        pr[j] = __fmaf_rn(a.a, hmc_force(c[r][j], sn[r][j], Sc, Ss, a.K), pr[j]);
+        out[j] = hmc_wrap(__fmaf_rn(a.eps, pr[j], tr[j]));
+      }
+      const size_t g = (size_t)(y0 + row) * L + x0 + xb;
+      *reinterpret_cast<float4*>(a.p_out + g) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+      *reinterpret_cast<float4*>(th_dst + g) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    __syncthreads();   // the edge arrays are rewritten by the next tile
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Two full kick-drift steps per launch (temporal blocking).  A CTA of 256
 // threads owns 32 x 128 sites.  It stages the unit vectors of the tile plus a
 // halo of two (36 x 132) and the angles and momenta of the tile plus a halo of
@@ -656,6 +897,12 @@ cudaError_t hmc_prepare(int sincos_mode) {
   e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const void* g = m == 0 ? (const void*)k_hmc_step_tma<0>
+                         : (m == 1 ? (const void*)k_hmc_step_tma<1> : (const void*)k_hmc_step_tma<2>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(g, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[m][dev] = true;
   return e;
 }
@@ -668,6 +915,27 @@ cudaError_t launch_hmc(int kind, int sincos_mode, const HmcArgs& a, cudaStream_t
     case 1: return launch_mode<1>(kind, a, stream);
     default: return launch_mode<2>(kind, a, stream);
   }
+}
+
+cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int ctas,
+                                cudaStream_t stream) {
+  if (!a.tiled || a.p_in != a.p_out || !maps4 || ctas < 1) return cudaErrorInvalidValue;
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps4);
+  const int tiles_x = a.L / kTileCols;
+  const int n_tiles = tiles_x * (a.L / kTileRows);
+  const int grid = ctas < n_tiles ? ctas : n_tiles;
+  switch (sincos_mode) {
+    case 0:
+      k_hmc_step_tma<0><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      break;
+    case 1:
+      k_hmc_step_tma<1><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      break;
+    default:
+      k_hmc_step_tma<2><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_accept(int mode, const HmcArgs& a, double beta, double J,

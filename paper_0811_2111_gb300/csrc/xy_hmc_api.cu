@@ -1,6 +1,8 @@
 // xy_hmc_api.cu -- the C ABI declared in include/xy_hmc.h: validation,
 // ownership, sticky errors, record growth and the per-trajectory CUDA graph
 // around the kernels of xy_hmc.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -51,6 +53,9 @@ void tmsg(const char* fmt, ...) {
 }  // namespace
 
 struct xy_hmc {
+  alignas(64) CUtensorMap maps[4];   // TMA maps: angle buffers 0..2, momenta (32 x 128 boxes)
+  bool use_tma;
+  int tma_ctas;                      // persistent grid of the TMA step kernel
   uint32_t magic;
   xy_hmc_params p;
   cudaStream_t stream;
@@ -114,6 +119,36 @@ xy_status check(const xy_hmc* h) {
   return XY_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of one L x L float buffer, boxes of 32 rows x 128 columns.
+bool encode_map(CUtensorMap* m, float* base, int L) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)L * sizeof(float)};
+  const cuuint32_t box[2] = {128u, 32u};
+  const cuuint32_t elem[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, elem,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool step_ok(double eps, int32_t n_md) { return eps > 0.0 && isfinite(eps) && n_md >= 1 && n_md <= 1000000; }
 
 xy_status validate(const xy_hmc_params* p) {
@@ -142,11 +177,13 @@ xy_status validate(const xy_hmc_params* p) {
     return XY_EINVAL;
   }
   if (p->kernel != XY_HMC_KERNEL_AUTO && p->kernel != XY_HMC_KERNEL_TILED &&
-      p->kernel != XY_HMC_KERNEL_SITE && p->kernel != XY_HMC_KERNEL_TILED2) {
+      p->kernel != XY_HMC_KERNEL_SITE && p->kernel != XY_HMC_KERNEL_TILED2 &&
+      p->kernel != XY_HMC_KERNEL_TILED_TMA) {
     tmsg("bad kernel choice");
     return XY_EINVAL;
   }
-  if ((p->kernel == XY_HMC_KERNEL_TILED || p->kernel == XY_HMC_KERNEL_TILED2) &&
+  if ((p->kernel == XY_HMC_KERNEL_TILED || p->kernel == XY_HMC_KERNEL_TILED2 ||
+       p->kernel == XY_HMC_KERNEL_TILED_TMA) &&
       !xyk::hmc_tiled_ok(p->L)) {
     tmsg("the tiled kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
@@ -169,6 +206,7 @@ xyk::HmcArgs args_of(const xy_hmc* h) {
   a.rk = xyd::make_round_keys(h->p.seed);
   a.lattice_id = h->p.lattice_id;
   a.tiled = h->p.kernel == XY_HMC_KERNEL_TILED || h->p.kernel == XY_HMC_KERNEL_TILED2 ||
+            h->p.kernel == XY_HMC_KERNEL_TILED_TMA ||
             (h->p.kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(h->p.L));
   a.pairs = h->p.kernel == XY_HMC_KERNEL_TILED2;
   return a;
@@ -205,7 +243,8 @@ cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cuda
     } else {
       a.p_in = pcur;
       a.p_out = pcur;
-      e = xyk::launch_hmc(xyk::kHmcStep, m, a, s);
+      e = h->use_tma ? xyk::launch_hmc_step_tma(m, a, h->maps, h->tma_ctas, s)
+                     : xyk::launch_hmc(xyk::kHmcStep, m, a, s);
       left -= 1;
     }
     off = 3 - off;
@@ -284,6 +323,11 @@ void release(xy_hmc* h) {
 
 xy_status sync(xy_hmc* h, const char* what) {
   H_CUDA(h, cudaStreamSynchronize(h->stream), what);
+  if (h->use_tma) {
+    uint32_t err = 0;
+    H_CUDA(h, cudaMemcpy(&err, &h->d_ctl->error, sizeof(err), cudaMemcpyDeviceToHost), what);
+    if (err) return fail(h, XY_ETIMEOUT, "%s: a kernel's bounded wait for its data ran out", what);
+  }
   return XY_OK;
 }
 
@@ -333,6 +377,20 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
   if (e == cudaSuccess) {
     step = "control block";
     e = cudaMalloc(&h->d_ctl, sizeof(xyk::HmcCtl));
+  }
+  const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA ||
+                        (p->kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(p->L));
+  if (e == cudaSuccess && want_tma) {
+    step = "tensor maps";
+    int n_sm = 0;
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    bool ok = e == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i) ok = encode_map(&h->maps[i], h->th[i], p->L);
+    if (ok) ok = encode_map(&h->maps[3], h->d_p, p->L);
+    // AUTO falls back to the plain tiled kernel without the encoder
+    if (e == cudaSuccess && !ok && p->kernel == XY_HMC_KERNEL_TILED_TMA) e = cudaErrorNotSupported;
+    h->use_tma = ok;
+    h->tma_ctas = 2 * (n_sm > 0 ? n_sm : 1);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctl, 0, sizeof(xyk::HmcCtl), h->stream);
   if (e == cudaSuccess) {

@@ -167,7 +167,7 @@ struct HmcCtl {
   unsigned long long traj;               // next trajectory number
   unsigned long long accepted;           // accepted trajectories so far
   uint32_t cur;                          // angle buffer (0..2) holding the state
-  uint32_t pad;
+  uint32_t error;                        // set by a kernel whose bounded wait ran out
 };
 
 // Kinds of leap-frog launch.
@@ -214,7 +214,12 @@ cudaError_t launch_hmc_draw(const HmcArgs& a, cudaStream_t stream);
 cudaError_t launch_hmc_start(const HmcArgs& a, int hot, cudaStream_t stream);
 // Move the state into th[0] if it lives elsewhere, and set cur = 0.
 cudaError_t launch_hmc_canonical(const HmcArgs& a, cudaStream_t stream);
-// Shared memory of the two-step kernel; set once per device before capture.
+// Shared memory of the two-step and TMA kernels; set once per device before capture.
 cudaError_t hmc_prepare(int sincos_mode);
+// One leap-frog step (kick, drift) with the persistent TMA kernel: tensor maps
+// (CUtensorMap, 128 bytes each) of the three angle buffers and of the momentum
+// buffer a.p_in (== a.p_out), boxes of 32 rows x 128 columns; grid = ctas.
+cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int ctas,
+                                cudaStream_t stream);
 
 }  // namespace xyk

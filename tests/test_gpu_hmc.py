@@ -115,7 +115,7 @@ def test_tiled_and_site_kernels_are_bit_identical(L, n_md):
     """The tiled kernel (one step per launch), the two-step kernel (full steps
     two per launch, odd remainders singly) and the per-site kernel: same bits."""
     out = {}
-    for kernel in ("tiled", "tiled2", "site"):
+    for kernel in ("tiled", "tiled2", "tiled_tma", "site"):
         with HMC(L, 1.05, 8, 0.1, n_md, kernel=kernel, lattice_id=2) as h:
             h.run(6)
             th, p, _ = h.state()
@@ -124,7 +124,7 @@ def test_tiled_and_site_kernels_are_bit_identical(L, n_md):
             th2, p2, _ = h.state()
             out[kernel] = (th, p, o, th2, p2, h.last_sums())
     b = out["site"]
-    for name in ("tiled", "tiled2"):
+    for name in ("tiled", "tiled2", "tiled_tma"):
         a = out[name]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), name
         for k in ("C", "Ix", "Iy", "Mx", "My", "dH"):
@@ -264,6 +264,6 @@ def test_error_paths():
     with HMC(16, 1.0, 1, 0.1, 3) as h:
         with pytest.raises(X.XYError):
             h.set_step(-1.0, 3)
-    for kernel in ("tiled", "tiled2"):
+    for kernel in ("tiled", "tiled2", "tiled_tma"):
         with pytest.raises(X.XYError):
             HMC(96, 1.0, 1, 0.1, 3, kernel=kernel)
