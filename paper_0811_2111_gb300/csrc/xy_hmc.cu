@@ -361,9 +361,19 @@ __global__ void __launch_bounds__(kTileThreads, KIND == kHmcStep ? 3 : 2) k_hmc_
 // shares the outcome, so a CTA either proceeds or returns as a whole, setting
 // HmcCtl::error.
 // ---------------------------------------------------------------------------
-constexpr int kTmaBox = kTileRows * kTileCols;                 // floats per box
-constexpr uint32_t kTmaStageBytes = 2u * kTmaBox * sizeof(float);
-constexpr size_t kTmaSmem = 2 * (size_t)kTmaStageBytes;       // two stages
+// ROWS rows per thread: tiles of 8 ROWS x 128 sites.  ROWS = 4 (the tile of
+// k_hmc_tile, two CTAs per SM) is the one launched: 16 x 128 tiles at four
+// CTAs per SM measured slower (57.4 against 54.1 us per step at L = 4096; the
+// halo grows from 8 % to 14 % of the sincos work and occupancy was not the
+// limit).
+template <int ROWS>
+struct TmaGeom {
+  static constexpr int kRows = 8 * ROWS;                               // tile rows
+  static constexpr int kBox = kRows * kTileCols;                       // floats per box
+  static constexpr uint32_t kStageBytes = 2u * kBox * sizeof(float);  // angles + momenta
+  static constexpr size_t kSmem = 2 * (size_t)kStageBytes;             // two stages
+  static constexpr int kMinBlocks = ROWS == 4 ? 2 : 4;
+};
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -409,16 +419,20 @@ __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kTileThreads, 2)
+template <int MODE, int ROWS>
+__global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     k_hmc_step_tma(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
                    const __grid_constant__ CUtensorMap map2, const __grid_constant__ CUtensorMap mapp,
                    HmcArgs a, int tiles_x, int n_tiles) {
+  using G = TmaGeom<ROWS>;
+  constexpr int TR = G::kRows;
+  constexpr uint32_t kTmaStageBytes = G::kStageBytes;
+  constexpr int kTmaBox = G::kBox;
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  __shared__ __align__(16) float sh_c[kTileRows + 2][kTileCols];
-  __shared__ __align__(16) float sh_s[kTileRows + 2][kTileCols];
-  __shared__ float side_c[2][kTileRows];
-  __shared__ float side_s[2][kTileRows];
+  __shared__ __align__(16) float sh_c[TR + 2][kTileCols];
+  __shared__ __align__(16) float sh_s[TR + 2][kTileCols];
+  __shared__ float side_c[2][TR];
+  __shared__ float side_s[2][TR];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int stage_ok;
 
@@ -440,7 +454,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   // thread 0's bookkeeping: loads issued into / waited for on each stage
   int issued[2] = {0, 0}, waited[2] = {0, 0};
   auto issue = [&](int t, int s) {
-    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * kTileRows;
+    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
     mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
     tma_load_2d(stage_th(s), mth, x0, y0, &bar[s]);
     tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
@@ -472,17 +486,18 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   int it = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
     const int s = it & 1;
-    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * kTileRows;
+    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
     // halo loads first: rows y0-1, y0+32 (threads 0..127 / 128..255), columns
     // x0-1 and x0+128 (threads 0..31 / 32..63)
     const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1)
-                                   : (y0 + kTileRows == L ? 0 : y0 + kTileRows);
+                                   : (y0 + TR == L ? 0 : y0 + TR);
     const float th_row = th_src[(size_t)hy * L + x0 + (tid & (kTileCols - 1))];
     float th_side = 0.f;
-    const bool side = tid < 64;
+    // side columns: threads 0..TR-1 column x0-1, TR..2TR-1 column x0+128
+    const bool side = tid < 2 * TR;
     if (side) {
-      const int sx = tid < 32 ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
-      th_side = th_src[(size_t)(y0 + (tid & 31)) * L + sx];
+      const int sx = tid < TR ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
+      th_side = th_src[(size_t)(y0 + (tid % TR)) * L + sx];
     }
     // wait for this tile's stage (bounded; one thread polls, all follow).  On
     // a timeout the CTA flags the error, drains (bounded) whatever loads it
@@ -500,20 +515,20 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     __syncthreads();
     if (!stage_ok) return;
 
-    const int xb = 4 * lane, rb0 = kRowsPerThread * warp;
-    float4 t4[kRowsPerThread], p4[kRowsPerThread];
+    const int xb = 4 * lane, rb0 = ROWS * warp;
+    float4 t4[ROWS], p4[ROWS];
     {
       float (*sth)[kTileCols] = stage_th(s);
       float (*sp)[kTileCols] = stage_p(s);
 #pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) {
+      for (int r = 0; r < ROWS; ++r) {
         t4[r] = *reinterpret_cast<const float4*>(&sth[rb0 + r][xb]);
         p4[r] = *reinterpret_cast<const float4*>(&sp[rb0 + r][xb]);
       }
     }
-    float c[kRowsPerThread][4], sn[kRowsPerThread][4];
+    float c[ROWS][4], sn[ROWS][4];
 #pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) {
+    for (int r = 0; r < ROWS; ++r) {
       xyd::unit_vector<MODE>(t4[r].x, &sn[r][0], &c[r][0]);
       xyd::unit_vector<MODE>(t4[r].y, &sn[r][1], &c[r][1]);
       xyd::unit_vector<MODE>(t4[r].z, &sn[r][2], &c[r][2]);
@@ -522,19 +537,21 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     {
       float hs, hc;
       xyd::unit_vector<MODE>(th_row, &hs, &hc);
-      const int row = tid < kTileCols ? 0 : kTileRows + 1;
+      const int row = tid < kTileCols ? 0 : TR + 1;
       sh_c[row][tid & (kTileCols - 1)] = hc;
       sh_s[row][tid & (kTileCols - 1)] = hs;
       if (side) {
         xyd::unit_vector<MODE>(th_side, &hs, &hc);
-        side_c[tid >> 5][tid & 31] = hc;
-        side_s[tid >> 5][tid & 31] = hs;
+        side_c[tid / TR][tid % TR] = hc;
+        side_s[tid / TR][tid % TR] = hs;
       }
-      const int rf = rb0 + 1, rl = rb0 + kRowsPerThread;
+      const int rf = rb0 + 1, rl = rb0 + ROWS;
       *reinterpret_cast<float4*>(&sh_c[rf][xb]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
       *reinterpret_cast<float4*>(&sh_s[rf][xb]) = make_float4(sn[0][0], sn[0][1], sn[0][2], sn[0][3]);
-      *reinterpret_cast<float4*>(&sh_c[rl][xb]) = make_float4(c[3][0], c[3][1], c[3][2], c[3][3]);
-      *reinterpret_cast<float4*>(&sh_s[rl][xb]) = make_float4(sn[3][0], sn[3][1], sn[3][2], sn[3][3]);
+      *reinterpret_cast<float4*>(&sh_c[rl][xb]) =
+          make_float4(c[ROWS - 1][0], c[ROWS - 1][1], c[ROWS - 1][2], c[ROWS - 1][3]);
+      *reinterpret_cast<float4*>(&sh_s[rl][xb]) =
+          make_float4(sn[ROWS - 1][0], sn[ROWS - 1][1], sn[ROWS - 1][2], sn[ROWS - 1][3]);
     }
     __syncthreads();   // stage s fully read; edges visible
     if (tid == 0) {
@@ -547,12 +564,12 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 
     const float4 cdn = *reinterpret_cast<const float4*>(&sh_c[rb0][xb]);
     const float4 sdn = *reinterpret_cast<const float4*>(&sh_s[rb0][xb]);
-    const float4 cup = *reinterpret_cast<const float4*>(&sh_c[rb0 + kRowsPerThread + 1][xb]);
-    const float4 sup = *reinterpret_cast<const float4*>(&sh_s[rb0 + kRowsPerThread + 1][xb]);
+    const float4 cup = *reinterpret_cast<const float4*>(&sh_c[rb0 + ROWS + 1][xb]);
+    const float4 sup = *reinterpret_cast<const float4*>(&sh_s[rb0 + ROWS + 1][xb]);
     const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
     const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
 #pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) {
+    for (int r = 0; r < ROWS; ++r) {
       float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
       float sl = __shfl_up_sync(0xffffffffu, sn[r][3], 1);
       float cr = __shfl_down_sync(0xffffffffu, c[r][0], 1);
@@ -574,8 +591,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const float nlc = j == 0 ? cl : c[r][j - 1], nls = j == 0 ? sl : sn[r][j - 1];
         const float nrc = j == 3 ? cr : c[r][j + 1], nrs = j == 3 ? sr : sn[r][j + 1];
         const float ndc = r == 0 ? cdn_a[j] : c[r - 1][j], nds = r == 0 ? sdn_a[j] : sn[r - 1][j];
-        const float nuc = r == kRowsPerThread - 1 ? cup_a[j] : c[r + 1][j];
-        const float nus = r == kRowsPerThread - 1 ? sup_a[j] : sn[r + 1][j];
+        const float nuc = r == ROWS - 1 ? cup_a[j] : c[r + 1][j];
+        const float nus = r == ROWS - 1 ? sup_a[j] : sn[r + 1][j];
         const float Sc = xyd::nb_sum(nlc, nrc, ndc, nuc);
         const float Ss = xyd::nb_sum(nls, nrs, nds, nus);
         pr[j] = __fmaf_rn(a.a, hmc_force(c[r][j], sn[r][j], Sc, Ss, a.K), pr[j]);
@@ -897,12 +914,13 @@ cudaError_t hmc_prepare(int sincos_mode) {
   e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  const void* g = m == 0 ? (const void*)k_hmc_step_tma<0>
-                         : (m == 1 ? (const void*)k_hmc_step_tma<1> : (const void*)k_hmc_step_tma<2>);
+  const void* g4 = m == 0 ? (const void*)k_hmc_step_tma<0, 4>
+                          : (m == 1 ? (const void*)k_hmc_step_tma<1, 4> : (const void*)k_hmc_step_tma<2, 4>);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+    e = cudaFuncSetAttribute(g4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaGeom<4>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(g, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(g4, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[m][dev] = true;
   return e;
 }
@@ -917,25 +935,33 @@ cudaError_t launch_hmc(int kind, int sincos_mode, const HmcArgs& a, cudaStream_t
   }
 }
 
-cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int ctas,
-                                cudaStream_t stream) {
-  if (!a.tiled || a.p_in != a.p_out || !maps4 || ctas < 1) return cudaErrorInvalidValue;
-  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps4);
+template <int ROWS>
+cudaError_t launch_tma_rows(int sincos_mode, const HmcArgs& a, const CUtensorMap* m, int ctas,
+                            cudaStream_t stream) {
   const int tiles_x = a.L / kTileCols;
-  const int n_tiles = tiles_x * (a.L / kTileRows);
+  const int n_tiles = tiles_x * (a.L / TmaGeom<ROWS>::kRows);
   const int grid = ctas < n_tiles ? ctas : n_tiles;
+  const size_t smem = TmaGeom<ROWS>::kSmem;
   switch (sincos_mode) {
     case 0:
-      k_hmc_step_tma<0><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      k_hmc_step_tma<0, ROWS><<<grid, kTileThreads, smem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
       break;
     case 1:
-      k_hmc_step_tma<1><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      k_hmc_step_tma<1, ROWS><<<grid, kTileThreads, smem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
       break;
     default:
-      k_hmc_step_tma<2><<<grid, kTileThreads, kTmaSmem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
+      k_hmc_step_tma<2, ROWS><<<grid, kTileThreads, smem, stream>>>(m[0], m[1], m[2], m[3], a, tiles_x, n_tiles);
       break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
+                                int ctas, cudaStream_t stream) {
+  if (!a.tiled || a.p_in != a.p_out || !maps4 || ctas < 1) return cudaErrorInvalidValue;
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps4);
+  if (box_rows == TmaGeom<4>::kRows) return launch_tma_rows<4>(sincos_mode, a, m, ctas, stream);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_hmc_accept(int mode, const HmcArgs& a, double beta, double J,

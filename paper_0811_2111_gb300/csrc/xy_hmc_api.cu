@@ -55,6 +55,7 @@ void tmsg(const char* fmt, ...) {
 struct xy_hmc {
   alignas(64) CUtensorMap maps[4];   // TMA maps: angle buffers 0..2, momenta (32 x 128 boxes)
   bool use_tma;
+  int tma_rows;                      // tile (and box) rows of the TMA step kernel: 32 or 16
   int tma_ctas;                      // persistent grid of the TMA step kernel
   uint32_t magic;
   xy_hmc_params p;
@@ -136,13 +137,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of one L x L float buffer, boxes of 32 rows x 128 columns.
-bool encode_map(CUtensorMap* m, float* base, int L) {
+// Tensor map of one L x L float buffer, boxes of box_rows rows x 128 columns.
+bool encode_map(CUtensorMap* m, float* base, int L, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)L};
   const cuuint64_t strides[1] = {(cuuint64_t)L * sizeof(float)};
-  const cuuint32_t box[2] = {128u, 32u};
+  const cuuint32_t box[2] = {128u, (cuuint32_t)box_rows};
   const cuuint32_t elem[2] = {1u, 1u};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, elem,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -243,7 +244,7 @@ cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cuda
     } else {
       a.p_in = pcur;
       a.p_out = pcur;
-      e = h->use_tma ? xyk::launch_hmc_step_tma(m, a, h->maps, h->tma_ctas, s)
+      e = h->use_tma ? xyk::launch_hmc_step_tma(m, a, h->maps, h->tma_rows, h->tma_ctas, s)
                      : xyk::launch_hmc(xyk::kHmcStep, m, a, s);
       left -= 1;
     }
@@ -385,8 +386,9 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     int n_sm = 0;
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     bool ok = e == cudaSuccess;
-    for (int i = 0; i < 3 && ok; ++i) ok = encode_map(&h->maps[i], h->th[i], p->L);
-    if (ok) ok = encode_map(&h->maps[3], h->d_p, p->L);
+    h->tma_rows = 32;   // 32 x 128 tiles measured faster than 16 x 128 (54.1 vs 57.4 us per step)
+    for (int i = 0; i < 3 && ok; ++i) ok = encode_map(&h->maps[i], h->th[i], p->L, h->tma_rows);
+    if (ok) ok = encode_map(&h->maps[3], h->d_p, p->L, h->tma_rows);
     // AUTO falls back to the plain tiled kernel without the encoder
     if (e == cudaSuccess && !ok && p->kernel == XY_HMC_KERNEL_TILED_TMA) e = cudaErrorNotSupported;
     h->use_tma = ok;

@@ -218,8 +218,9 @@ cudaError_t launch_hmc_canonical(const HmcArgs& a, cudaStream_t stream);
 cudaError_t hmc_prepare(int sincos_mode);
 // One leap-frog step (kick, drift) with the persistent TMA kernel: tensor maps
 // (CUtensorMap, 128 bytes each) of the three angle buffers and of the momentum
-// buffer a.p_in (== a.p_out), boxes of 32 rows x 128 columns; grid = ctas.
-cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int ctas,
-                                cudaStream_t stream);
+// buffer a.p_in (== a.p_out), boxes of box_rows (32) rows x 128 columns,
+// which is also the kernel's tile; grid = ctas.
+cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
+                                int ctas, cudaStream_t stream);
 
 }  // namespace xyk
