@@ -61,10 +61,11 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["large", "huge", "batch", "hmc"], default="large",
+    ap.add_argument("--workload", choices=["large", "huge", "batch", "hmc", "quad"], default="large",
                     help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step; "
                          "batch: 256 lattices with replica exchange, 100 rounds/step; "
-                         "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step")
+                         "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step; "
+                         "quad: four replicas per site at L=4096, 200 sweeps per step")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
@@ -610,6 +611,8 @@ def run_ours(args):
         return run_batch_line(args, dev, world, rank)
     if args.workload == "hmc":
         return run_hmc_line(args, dev, world, rank)
+    if args.workload == "quad":
+        return run_quad_line(args, dev, world, rank)
 
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
@@ -762,6 +765,52 @@ def run_batch_line(args, dev, world, rank):
                                             "l2": "flushed before every timed step (256 MiB write)",
                                             "parallelism": f"replicas x{world}"},
             "batch": r, "gpu_launches": r["launches_per_step"] * args.steps, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_quad_line(args, dev, world, rank, sweeps_per_step=200):
+    """Main line for --workload quad: four replicas per site (Sec. 3.2's RGBA
+    packing) at L = 4096, betas 1.00, 1.06, 1.12, 1.18 (replicas with N > 1)."""
+    import torch
+    from paper_0811_2111_gb300.lattice import Quad
+
+    L = 4096
+    sampler = ClockSampler(str(dev.index or 0))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=args.sincos, lattice_id=4 * rank,
+              device=dev) as q:
+        for _ in range(max(3, args.warmup)):
+            q.sweep(sweeps_per_step)
+        q.synchronize()
+        barrier(world)
+        sampler.start()
+        ms = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(q.stream)
+            q.sweep(sweeps_per_step)
+            e1.record(q.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(ms), world, dev)
+    updates = 4 * L * L * sweeps_per_step * args.steps * world
+    line = {"metric": METRIC, "value": updates / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "xy_quad_L4096_4replicas_beta1.00-1.18",
+                       "sweeps_per_step": sweeps_per_step, "sincos": args.sincos,
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": 2 * sweeps_per_step * args.steps + args.steps, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
