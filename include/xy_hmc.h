@@ -65,7 +65,7 @@ typedef struct {
     int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM (force and sums) */
     uint64_t seed;        /* Philox key                                           */
     uint32_t lattice_id;  /* third Philox counter word                            */
-    int32_t kernel;       /* XY_HMC_KERNEL_AUTO, _TILED, _SITE, _TILED2, _TILED_TMA */
+    int32_t kernel;       /* XY_HMC_KERNEL_* (see below)                        */
 } xy_hmc_params;
 
 /* Leap-frog kernels: TILED runs one step per launch on tiles of 32 x 128 sites
@@ -74,12 +74,17 @@ typedef struct {
  * memory accelerator (needs L % 128 == 0 and the driver's tensor-map encoder;
  * begin and final launches as TILED); TILED2 runs the full steps two per
  * launch (temporal blocking: half the DRAM traffic, a recomputed halo of two);
- * SITE is one thread per site (any L).  AUTO takes TILED_TMA when L % 128 == 0
- * and the encoder is available (TILED if not), else SITE; on GB300 TILED_TMA
- * measured 54.4 us per step at L = 4096 against 57.0 for TILED and 58.3 for
- * TILED2.  All give bit-identical angles, momenta and sums. */
+ * SITE is one thread per site (any L); CLUSTER runs a whole trajectory in one
+ * launch of one thread-block cluster that keeps the lattice in shared memory
+ * (L a power of two in [16, 256]; strips of 16 rows per CTA, neighbouring strips
+ * read through distributed shared memory).  AUTO takes CLUSTER for L = 128
+ * and 256, else TILED_TMA when L % 128 == 0 and the encoder is available
+ * (TILED if not), else SITE (the choices measured fastest on GB300: e.g.
+ * TILED_TMA 54.4 us per step at L = 4096 against 57.0 for TILED and 58.3 for
+ * TILED2; CLUSTER 2.8 us per step at L = 128 against 4.0 for TILED_TMA).  All
+ * give bit-identical angles, momenta and sums. */
 enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2,
-       XY_HMC_KERNEL_TILED2 = 3, XY_HMC_KERNEL_TILED_TMA = 4 };
+       XY_HMC_KERNEL_TILED2 = 3, XY_HMC_KERNEL_TILED_TMA = 4, XY_HMC_KERNEL_CLUSTER = 5 };
 
 /* One record per trajectory (96 bytes).
  *   sum       C, Ix, Iy, Mx, My of the state after the test (2^-30 units,
@@ -103,8 +108,8 @@ typedef struct {
  * momenta zero).
  *   p           parameters, copied and validated: L in [2, XY_MAX_L], beta >= 0
  *               and finite, J finite, eps > 0 and finite, n_md >= 1, sincos_mode
- *               and kernel valid (TILED, TILED2, TILED_TMA need L % 128 == 0);
- *               else XY_EINVAL.
+ *               and kernel valid (TILED, TILED2, TILED_TMA need L % 128 == 0,
+ *               CLUSTER a power of two in [16, 256]); else XY_EINVAL.
  *   cuda_stream a cudaStream_t, or NULL for the legacy default stream.
  *   d_angles    NULL: the library allocates all three angle buffers; else a
  *               caller-owned device buffer of >= L*L floats (16-byte aligned)

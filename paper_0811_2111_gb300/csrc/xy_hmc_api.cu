@@ -55,6 +55,7 @@ void tmsg(const char* fmt, ...) {
 struct xy_hmc {
   alignas(64) CUtensorMap maps[4];   // TMA maps: angle buffers 0..2, momenta (32 x 128 boxes)
   bool use_tma;
+  bool use_cluster;                  // whole trajectories in one cluster launch
   int tma_rows;                      // tile (and box) rows of the TMA step kernel: 32 or 16
   int tma_ctas;                      // persistent grid of the TMA step kernel
   uint32_t magic;
@@ -179,8 +180,12 @@ xy_status validate(const xy_hmc_params* p) {
   }
   if (p->kernel != XY_HMC_KERNEL_AUTO && p->kernel != XY_HMC_KERNEL_TILED &&
       p->kernel != XY_HMC_KERNEL_SITE && p->kernel != XY_HMC_KERNEL_TILED2 &&
-      p->kernel != XY_HMC_KERNEL_TILED_TMA) {
+      p->kernel != XY_HMC_KERNEL_TILED_TMA && p->kernel != XY_HMC_KERNEL_CLUSTER) {
     tmsg("bad kernel choice");
+    return XY_EINVAL;
+  }
+  if (p->kernel == XY_HMC_KERNEL_CLUSTER && !xyk::hmc_cluster_ok(p->L)) {
+    tmsg("the cluster kernel needs L to be a power of two in [16, 256]; got %d", p->L);
     return XY_EINVAL;
   }
   if ((p->kernel == XY_HMC_KERNEL_TILED || p->kernel == XY_HMC_KERNEL_TILED2 ||
@@ -221,6 +226,9 @@ xyk::HmcArgs args_of(const xy_hmc* h) {
 cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cudaStream_t s) {
   xyk::HmcArgs a = args_of(h);
   const int m = h->p.sincos_mode;
+  if (h->use_cluster)
+    return xyk::launch_hmc_cluster(m, a, n, begin == xyk::kHmcBeginDraw ? 1 : 0, mode, h->p.beta,
+                                   h->p.J, s);
   float* pcur = h->d_p;
   float* pother = h->d_p2;
   a.a = 0.5f * a.eps;
@@ -268,6 +276,7 @@ cudaError_t capture(xy_hmc* h) {
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = xyk::hmc_prepare(h->p.sincos_mode);   // function attributes: not capturable
+  if (e == cudaSuccess && h->use_cluster) e = xyk::hmc_cluster_prepare(h->p.sincos_mode);
   if (e != cudaSuccess) return e;
   e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
@@ -379,8 +388,13 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     step = "control block";
     e = cudaMalloc(&h->d_ctl, sizeof(xyk::HmcCtl));
   }
+  // AUTO: the cluster kernel where it measured faster than the others (L =
+  // 128, 256); below that the per-launch cost of any kernel dominates
+  h->use_cluster = p->kernel == XY_HMC_KERNEL_CLUSTER ||
+                   (p->kernel == XY_HMC_KERNEL_AUTO && (p->L == 128 || p->L == 256));
   const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA ||
-                        (p->kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(p->L));
+                        (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster &&
+                         xyk::hmc_tiled_ok(p->L));
   if (e == cudaSuccess && want_tma) {
     step = "tensor maps";
     int n_sm = 0;
@@ -443,6 +457,8 @@ xy_status xy_hmc_integrate(xy_hmc* h, int32_t n_steps) {
   if (n_steps < 1 || n_steps > 1000000)
     return fail(h, XY_EINVAL, "xy_hmc_integrate: n_steps must be in [1, 1000000]");
   H_CUDA(h, xyk::hmc_prepare(h->p.sincos_mode), "xy_hmc_integrate: kernel attributes");
+  if (h->use_cluster)
+    H_CUDA(h, xyk::hmc_cluster_prepare(h->p.sincos_mode), "xy_hmc_integrate: kernel attributes");
   H_CUDA(h, enqueue_trajectory(h, xyk::kHmcBeginRead, n_steps, 1, h->stream),
          "xy_hmc_integrate: launch");
   H_CUDA(h, xyk::launch_hmc_canonical(args_of(h), h->stream),

@@ -223,4 +223,12 @@ cudaError_t hmc_prepare(int sincos_mode);
 cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
                                 int ctas, cudaStream_t stream);
 
+// Whole trajectories in one cluster launch (xy_hmc_cluster.cu), for
+// hmc_cluster_ok(L): L a power of two in [16, 256].  draw: momenta from Philox
+// (else from a.p_in); mode as launch_hmc_accept.  The state stays in buffer cur.
+bool hmc_cluster_ok(int L);
+cudaError_t hmc_cluster_prepare(int sincos_mode);
+cudaError_t launch_hmc_cluster(int sincos_mode, const HmcArgs& a, int n_md, int draw, int mode,
+                               double beta, double J, cudaStream_t stream);
+
 }  // namespace xyk

@@ -42,7 +42,8 @@ class HMC:
         p.lattice_id = int(lattice_id)
         p.kernel = {"auto": X.XY_HMC_KERNEL_AUTO, "tiled": X.XY_HMC_KERNEL_TILED,
                     "site": X.XY_HMC_KERNEL_SITE, "tiled2": X.XY_HMC_KERNEL_TILED2,
-                    "tiled_tma": X.XY_HMC_KERNEL_TILED_TMA}[kernel]
+                    "tiled_tma": X.XY_HMC_KERNEL_TILED_TMA,
+                    "cluster": X.XY_HMC_KERNEL_CLUSTER}[kernel]
         self.params = p
         self.J = float(J)
         with torch.cuda.device(self.device):

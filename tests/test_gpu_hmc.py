@@ -110,12 +110,19 @@ def test_n_steps_match_oracle(L):
     assert abs(-beta * sums["end"]["C"] - V1) <= 2e-5 * N
 
 
-@pytest.mark.parametrize("L,n_md", [(128, 7), (256, 7), (128, 1), (128, 2), (128, 4), (256, 5)])
-def test_tiled_and_site_kernels_are_bit_identical(L, n_md):
+@pytest.mark.parametrize("L,n_md", [(128, 7), (256, 7), (128, 1), (128, 2), (128, 4), (256, 5),
+                                    (16, 3), (32, 4), (48, 4), (64, 7)])
+def test_kernels_are_bit_identical(L, n_md):
     """The tiled kernel (one step per launch), the two-step kernel (full steps
-    two per launch, odd remainders singly) and the per-site kernel: same bits."""
+    two per launch, odd remainders singly), the TMA-fed kernel, the cluster
+    kernel (a whole trajectory per launch) and the per-site kernel: same bits."""
+    kernels = ["site"]
+    if L % 128 == 0:
+        kernels += ["tiled", "tiled2", "tiled_tma"]
+    if L in (16, 32, 64, 128, 256):
+        kernels += ["cluster"]
     out = {}
-    for kernel in ("tiled", "tiled2", "tiled_tma", "site"):
+    for kernel in kernels:
         with HMC(L, 1.05, 8, 0.1, n_md, kernel=kernel, lattice_id=2) as h:
             h.run(6)
             th, p, _ = h.state()
@@ -124,7 +131,7 @@ def test_tiled_and_site_kernels_are_bit_identical(L, n_md):
             th2, p2, _ = h.state()
             out[kernel] = (th, p, o, th2, p2, h.last_sums())
     b = out["site"]
-    for name in ("tiled", "tiled2", "tiled_tma"):
+    for name in kernels[1:]:
         a = out[name]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), name
         for k in ("C", "Ix", "Iy", "Mx", "My", "dH"):
@@ -267,3 +274,41 @@ def test_error_paths():
     for kernel in ("tiled", "tiled2", "tiled_tma"):
         with pytest.raises(X.XYError):
             HMC(96, 1.0, 1, 0.1, 3, kernel=kernel)
+    for L in (8, 48, 512):
+        with pytest.raises(X.XYError):
+            HMC(L, 1.0, 1, 0.1, 3, kernel="cluster")
+
+
+def test_caller_owned_angle_buffer_holds_the_state():
+    """With d_angles given, the state is back in that buffer after every call
+    (the trajectory moves it between three buffers on the device)."""
+    import ctypes as C
+    L = 128
+    dev = torch.device("cuda")
+    buf = torch.empty(L * L, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    p = X.xy_hmc_params()
+    p.L, p.start, p.beta, p.J, p.eps, p.n_md = L, X.XY_START_COLD, 1.0, 1.0, 0.001, 1
+    p.sincos_mode, p.seed, p.lattice_id, p.kernel = 0, 11, 0, 0
+    h = X.xy_hmc_create(p, C.c_void_p(stream.cuda_stream), C.c_void_p(buf.data_ptr()))
+    try:
+        moved = rejected = 0
+        for t in range(40):
+            # tiny steps are accepted (the state moves), huge ones are often rejected
+            X.xy_hmc_set_step(h, 0.001 if t % 2 == 0 else 2.0, 1 if t % 2 == 0 else 5)
+            before = buf.cpu().numpy().copy()
+            X.xy_hmc_run(h, 1)
+            th = np.empty(L * L, np.float32)
+            X.xy_hmc_get_state(h, th.ctypes.data_as(C.c_void_p))
+            after = buf.cpu().numpy()
+            assert np.array_equal(after, th)
+            if np.array_equal(after, before):
+                rejected += 1
+            else:
+                moved += 1
+            if moved > 2 and rejected > 2:
+                break
+        assert moved > 0 and rejected > 0          # both buffer paths exercised
+    finally:
+        X.xy_hmc_destroy(h)
+    assert torch.isfinite(buf).all()                 # still the caller's, still valid
