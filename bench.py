@@ -168,6 +168,17 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def alu_roofline(updates_per_s, sincos, clk_mhz):
+    """Issue-slot roofline of a Metropolis workload: algorithmic instructions per
+    update x updates/s against 152 SMs x 4 schedulers x 32 lanes x clock."""
+    instr = ALG_INSTR_PER_UPDATE[sincos]
+    peak = SMS * SMSP_PER_SM * LANES * clk_mhz * 1e6 / 1e12
+    achieved = instr * updates_per_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+            "frac": achieved / peak, "algorithmic_instr_per_update": instr,
+            "basis": "whole-run throughput (launch gaps included)"}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -726,6 +737,11 @@ def run_ours(args):
                  "table1_sizes": measure_table1_sizes(dev, args.sincos),
                  "hmc": measure_hmc(dev, args.sincos),
                  "quad": measure_quad(dev, args.sincos)}
+        # the same issue-slot roofline as the main line, over a whole run of each
+        # Metropolis workload (launch gaps included: a lower bound on the kernels')
+        clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        for key in ("batch", "differentiation", "quad"):
+            extra[key]["roofline"] = alu_roofline(extra[key]["value"], args.sincos, clk)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
