@@ -363,6 +363,7 @@ xy_status xy_reserve(xy_ctx* c, int64_t n_more) {
 }
 
 xy_status xy_sweep(xy_ctx* c, int64_t n) {
+  xyk::NvtxRange range("xy_sweep");
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
   if (n < 0) return fail(c, XY_EINVAL, "xy_sweep: negative sweep count");

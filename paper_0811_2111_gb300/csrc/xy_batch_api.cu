@@ -509,6 +509,7 @@ xy_status xy_batch_reserve(xy_batch* b, int64_t n_rounds) {
 }
 
 xy_status xy_batch_run(xy_batch* b, int64_t rounds) {
+  xyk::NvtxRange range("xy_batch_run");
   xy_status st = check_batch(b);
   if (st != XY_OK) return st;
   if (rounds < 0) return bfail(b, XY_EINVAL, "xy_batch_run: negative round count");

@@ -433,6 +433,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
 }
 
 xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
+  xyk::NvtxRange range("xy_hmc_run");
   xy_status st = check(h);
   if (st != XY_OK) return st;
   if (n_traj < 0) return fail(h, XY_EINVAL, "xy_hmc_run: negative trajectory count");
@@ -452,6 +453,7 @@ xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
 }
 
 xy_status xy_hmc_integrate(xy_hmc* h, int32_t n_steps) {
+  xyk::NvtxRange range("xy_hmc_integrate");
   xy_status st = check(h);
   if (st != XY_OK) return st;
   if (n_steps < 1 || n_steps > 1000000)

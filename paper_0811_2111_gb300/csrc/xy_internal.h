@@ -5,11 +5,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "xy.h"
 #include "xy_device.cuh"
 #include "xy_hmc.h"
 
 namespace xyk {
+
+// Named range on the profiler timeline (NVTX) for the lifetime of the object:
+// the entry points that enqueue work open one, so nsys/ncu timelines show
+// which call launched which kernels.  Costs nothing without a tool attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Arguments of one half-sweep launch over a single lattice.
 struct HalfSweepArgs {

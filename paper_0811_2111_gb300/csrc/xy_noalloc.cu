@@ -64,6 +64,7 @@ extern "C" {
 
 xy_status xy_sweep_noalloc(const xy_params* p, float* d_angles, uint32_t first_sweep,
                            int64_t n_sweeps, xy_record* d_records, void* cuda_stream) {
+  xyk::NvtxRange range("xy_sweep_noalloc");
   if (!p || !d_angles || n_sweeps < 0 || (n_sweeps > 0 && !d_records))
     return fail(XY_EINVAL, "NULL pointer or negative sweep count");
   if (p->L < 128 || p->L > kNoAllocMaxL || (p->L % 128) != 0)

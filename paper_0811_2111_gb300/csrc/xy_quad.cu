@@ -396,6 +396,7 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
 }
 
 xy_status xy_quad_sweep(xy_quad* q, int64_t n) {
+  xyk::NvtxRange range("xy_quad_sweep");
   xy_status st = check(q);
   if (st != XY_OK) return st;
   if (n < 0) return fail(q, XY_EINVAL, "xy_quad_sweep: negative sweep count");

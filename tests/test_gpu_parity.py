@@ -77,6 +77,39 @@ def test_philox_words_bit_exact(seed, sweep, lid, dom, first, n):
     assert np.array_equal(gpu, ref)
 
 
+@pytest.mark.parametrize("seed", [0x123456789ABCDEF, 1, 0xFFFFFFFFFFFFFFFF])
+def test_philox_matches_curand(seed):
+    """An independent Philox4x32-10: cuRAND's host generator.  With seed s its
+    key is (s_lo, s_hi) and output 4 i + j is word j of counter (0, 0, i, 0)
+    (established on this GPU: the first outputs of the default ordering).  The
+    same counters from the GPU kernels (site 0, sweep 0, lattice id i, domain 0)
+    and from the oracle must give the same words."""
+    import ctypes as C
+    import ctypes.util
+    path = "/usr/local/cuda/lib64/libcurand.so"
+    if not os.path.exists(path):
+        path = ctypes.util.find_library("curand")
+    if not path:
+        pytest.skip("libcurand not found")
+    cur = C.CDLL(path)
+    n_ctr = 256
+    gen = C.c_void_p()
+    assert cur.curandCreateGenerator(C.byref(gen), 161) == 0        # PHILOX4_32_10
+    try:
+        assert cur.curandSetPseudoRandomGeneratorSeed(gen, C.c_ulonglong(seed)) == 0
+        out = torch.zeros(4 * n_ctr, dtype=torch.int32, device="cuda")
+        assert cur.curandGenerate(gen, C.c_void_p(out.data_ptr()), C.c_size_t(4 * n_ctr)) == 0
+        torch.cuda.synchronize()
+    finally:
+        cur.curandDestroyGenerator(gen)
+    lib = out.cpu().numpy().view(np.uint32).reshape(n_ctr, 4)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    ref = np.stack([oracle.philox4x32_10([0, 0, i, 0], key) for i in range(n_ctr)])
+    assert np.array_equal(lib, ref)
+    gpu = np.concatenate([LT.philox_words(seed, 0, i, 0, 0, 1) for i in range(0, n_ctr, 17)])
+    assert np.array_equal(gpu, ref[::17])
+
+
 @pytest.mark.parametrize("L,seed,lid", [(32, 1, 0), (4096, 7, 0), (64, 5, 3)])
 def test_hot_start_matches_oracle(L, seed, lid):
     with LT.Lattice(L, 1.0, seed, lattice_id=lid) as lat:
