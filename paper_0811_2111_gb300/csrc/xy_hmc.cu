@@ -286,12 +286,14 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   constexpr uint32_t kTmaStageBytes = G::kStageBytes;
   constexpr int kTmaBox = G::kBox;
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  __shared__ __align__(16) float sh_c[TR + 2][kTileCols];
-  __shared__ __align__(16) float sh_s[TR + 2][kTileCols];
-  __shared__ float side_c[2][TR];
-  __shared__ float side_s[2][TR];
+  // unit vectors of the rows other warps read, double-buffered by tile parity:
+  // lastrow[b][w + 1] = last row of warp w (lastrow[b][0]: the halo row above
+  // the tile), firstrow[b][w] = first row of warp w (firstrow[b][kTileWarps]:
+  // the halo row below); plus the halo columns
+  __shared__ __align__(16) float2 lastrow[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float2 firstrow[2][kTileWarps + 1][kTileCols];
+  __shared__ float2 side[2][2][TR];
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int stage_ok;
 
   const int L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   const CUtensorMap* mth = src == 0 ? &map0 : (src == 1 ? &map1 : &map2);
   const float* __restrict__ th_src = hmc_buf(a, src);
   float* __restrict__ th_dst = hmc_buf(a, dst);
-  // stage s: angles [32][128] then momenta [32][128]
+  // stage s: angles [TR][128] then momenta [TR][128]
   auto stage_th = [&](int s) {
     return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes);
   };
@@ -308,8 +310,8 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes +
                                                  kTmaBox * sizeof(float));
   };
-  // thread 0's bookkeeping: loads issued into / waited for on each stage
-  int issued[2] = {0, 0}, waited[2] = {0, 0};
+  // thread 0's count of loads issued per stage (for the drain on a timeout)
+  int issued[2] = {0, 0};
   auto issue = [&](int t, int s) {
     const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
     mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
@@ -317,14 +319,9 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
     ++issued[s];
   };
-  auto bounded_wait = [&](int s) {
-    const uint32_t parity = (uint32_t)(waited[s] & 1);
-    for (long long i = 0; i < kSpinLimit; ++i) {
-      if (mbar_try_wait(&bar[s], parity)) {
-        ++waited[s];
-        return true;
-      }
-    }
+  auto bounded_wait = [&](int s, uint32_t parity) {
+    for (long long i = 0; i < kSpinLimit; ++i)
+      if (mbar_try_wait(&bar[s], parity)) return true;
     return false;
   };
 
@@ -340,41 +337,34 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   }
   __syncthreads();
 
+  // A thread whose wait runs out flags the error and stops computing, but
+  // keeps meeting the CTA's barriers (so no thread waits on one that left);
+  // thread 0 then issues no more loads and drains the ones in flight.
+  bool ok = true;
   int it = 0;
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
-    const int s = it & 1;
+    const int s = it & 1, b = it & 1;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
     const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
-    // halo loads first: rows y0-1, y0+32 (threads 0..127 / 128..255), columns
-    // x0-1 and x0+128 (threads 0..31 / 32..63)
-    const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1)
-                                   : (y0 + TR == L ? 0 : y0 + TR);
+    // halo loads first: rows y0-1, y0+TR (threads 0..127 / 128..255), columns
+    // x0-1 and x0+128 (threads 0..TR-1 / TR..2TR-1)
+    const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1) : (y0 + TR == L ? 0 : y0 + TR);
     const float th_row = th_src[(size_t)hy * L + x0 + (tid & (kTileCols - 1))];
     float th_side = 0.f;
-    // side columns: threads 0..TR-1 column x0-1, TR..2TR-1 column x0+128
-    const bool side = tid < 2 * TR;
-    if (side) {
+    const bool is_side = tid < 2 * TR;
+    if (is_side) {
       const int sx = tid < TR ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
       th_side = th_src[(size_t)(y0 + (tid % TR)) * L + sx];
     }
-    // wait for this tile's stage (bounded; one thread polls, all follow).  On
-    // a timeout the CTA flags the error, drains (bounded) whatever loads it
-    // still has in flight into its shared memory, and returns as a whole.
-    if (tid == 0) {
-      const bool ok = bounded_wait(s);
-      if (!ok) {
-        atomicOr(&a.ctl->error, 1u);
-        for (int q = 0; q < 2; ++q)
-          while (waited[q] < issued[q] && bounded_wait(q)) {
-          }
-      }
-      stage_ok = ok ? 1 : 0;
+    if (ok && !bounded_wait(s, parity)) {
+      ok = false;
+      atomicOr(&a.ctl->error, 1u);
     }
-    __syncthreads();
-    if (!stage_ok) return;
 
     const int xb = 4 * lane, rb0 = ROWS * warp;
     float4 t4[ROWS], p4[ROWS];
-    {
+    float c[ROWS][4], sn[ROWS][4];
+    if (ok) {
       float (*sth)[kTileCols] = stage_th(s);
       float (*sp)[kTileCols] = stage_p(s);
 #pragma unroll
@@ -382,49 +372,49 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
         t4[r] = *reinterpret_cast<const float4*>(&sth[rb0 + r][xb]);
         p4[r] = *reinterpret_cast<const float4*>(&sp[rb0 + r][xb]);
       }
-    }
-    float c[ROWS][4], sn[ROWS][4];
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      xyd::unit_vector<MODE>(t4[r].x, &sn[r][0], &c[r][0]);
-      xyd::unit_vector<MODE>(t4[r].y, &sn[r][1], &c[r][1]);
-      xyd::unit_vector<MODE>(t4[r].z, &sn[r][2], &c[r][2]);
-      xyd::unit_vector<MODE>(t4[r].w, &sn[r][3], &c[r][3]);
-    }
-    {
+      for (int r = 0; r < ROWS; ++r) {
+        xyd::unit_vector<MODE>(t4[r].x, &sn[r][0], &c[r][0]);
+        xyd::unit_vector<MODE>(t4[r].y, &sn[r][1], &c[r][1]);
+        xyd::unit_vector<MODE>(t4[r].z, &sn[r][2], &c[r][2]);
+        xyd::unit_vector<MODE>(t4[r].w, &sn[r][3], &c[r][3]);
+      }
       float hs, hc;
       xyd::unit_vector<MODE>(th_row, &hs, &hc);
-      const int row = tid < kTileCols ? 0 : TR + 1;
-      sh_c[row][tid & (kTileCols - 1)] = hc;
-      sh_s[row][tid & (kTileCols - 1)] = hs;
-      if (side) {
-        xyd::unit_vector<MODE>(th_side, &hs, &hc);
-        side_c[tid / TR][tid % TR] = hc;
-        side_s[tid / TR][tid % TR] = hs;
+      if (tid < kTileCols) {
+        lastrow[b][0][tid] = make_float2(hc, hs);
+      } else {
+        firstrow[b][kTileWarps][tid - kTileCols] = make_float2(hc, hs);
       }
-      const int rf = rb0 + 1, rl = rb0 + ROWS;
-      *reinterpret_cast<float4*>(&sh_c[rf][xb]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
-      *reinterpret_cast<float4*>(&sh_s[rf][xb]) = make_float4(sn[0][0], sn[0][1], sn[0][2], sn[0][3]);
-      *reinterpret_cast<float4*>(&sh_c[rl][xb]) =
-          make_float4(c[ROWS - 1][0], c[ROWS - 1][1], c[ROWS - 1][2], c[ROWS - 1][3]);
-      *reinterpret_cast<float4*>(&sh_s[rl][xb]) =
-          make_float4(sn[ROWS - 1][0], sn[ROWS - 1][1], sn[ROWS - 1][2], sn[ROWS - 1][3]);
+      if (is_side) {
+        xyd::unit_vector<MODE>(th_side, &hs, &hc);
+        side[b][tid / TR][tid % TR] = make_float2(hc, hs);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        firstrow[b][warp][xb + j] = make_float2(c[0][j], sn[0][j]);
+        lastrow[b][warp + 1][xb + j] = make_float2(c[ROWS - 1][j], sn[ROWS - 1][j]);
+      }
     }
     __syncthreads();   // stage s fully read; edges visible
-    if (tid == 0) {
+    if (tid == 0 && ok) {
       const int tn = t + 2 * gridDim.x;
       if (tn < n_tiles) {
         fence_async_shared();
         issue(tn, s);
       }
     }
+    if (!ok) continue;
 
-    const float4 cdn = *reinterpret_cast<const float4*>(&sh_c[rb0][xb]);
-    const float4 sdn = *reinterpret_cast<const float4*>(&sh_s[rb0][xb]);
-    const float4 cup = *reinterpret_cast<const float4*>(&sh_c[rb0 + ROWS + 1][xb]);
-    const float4 sup = *reinterpret_cast<const float4*>(&sh_s[rb0 + ROWS + 1][xb]);
-    const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
-    const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
+    float cdn_a[4], sdn_a[4], cup_a[4], sup_a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 dn = lastrow[b][warp][xb + j], up = firstrow[b][warp + 1][xb + j];
+      cdn_a[j] = dn.x;
+      sdn_a[j] = dn.y;
+      cup_a[j] = up.x;
+      sup_a[j] = up.y;
+    }
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
@@ -433,12 +423,14 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
       float sr = __shfl_down_sync(0xffffffffu, sn[r][0], 1);
       const int row = rb0 + r;
       if (lane == 0) {
-        cl = side_c[0][row];
-        sl = side_s[0][row];
+        const float2 v = side[b][0][row];
+        cl = v.x;
+        sl = v.y;
       }
       if (lane == 31) {
-        cr = side_c[1][row];
-        sr = side_s[1][row];
+        const float2 v = side[b][1][row];
+        cr = v.x;
+        sr = v.y;
       }
       float pr[4] = {p4[r].x, p4[r].y, p4[r].z, p4[r].w};
       const float tr[4] = {t4[r].x, t4[r].y, t4[r].z, t4[r].w};
@@ -459,7 +451,12 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
       *reinterpret_cast<float4*>(a.p_out + g) = make_float4(pr[0], pr[1], pr[2], pr[3]);
       *reinterpret_cast<float4*>(th_dst + g) = make_float4(out[0], out[1], out[2], out[3]);
     }
-    __syncthreads();   // the edge arrays are rewritten by the next tile
+  }
+  // loads still in flight after a timeout land in this CTA's shared memory:
+  // wait for them (bounded) before the CTA exits
+  if (tid == 0 && !ok) {
+    for (int q = 0; q < 2; ++q)
+      if (issued[q] > 0) (void)bounded_wait(q, (uint32_t)((issued[q] - 1) & 1));
   }
 }
 
