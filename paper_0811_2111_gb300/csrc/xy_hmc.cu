@@ -214,9 +214,10 @@ __global__ void __launch_bounds__(kTileThreads, KIND == kHmcStep ? 3 : 2) k_hmc_
 // double-buffered shared-memory stage with cp.async.bulk.tensor, completing on
 // an mbarrier, while it computes the current tile.  The one-site halo (320
 // floats) is read with plain loads issued before the wait.  Every wait is
-// bounded: thread 0 polls the stage's barrier a fixed number of times and
-// shares the outcome, so a CTA either proceeds or returns as a whole, setting
-// HmcCtl::error.
+// bounded: each thread polls the stage's barrier a fixed number of times; a
+// thread that runs out flags HmcCtl::error and stops computing but keeps
+// meeting the CTA's barriers, and thread 0 then issues no more loads and
+// drains the ones in flight before the CTA exits.
 // ---------------------------------------------------------------------------
 // ROWS rows per thread: tiles of 8 ROWS x 128 sites.  ROWS = 4 (the tile of
 // k_hmc_tile, two CTAs per SM) is the one launched: 16 x 128 tiles at four
