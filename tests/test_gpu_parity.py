@@ -1,7 +1,7 @@
 """CUDA path vs FP64 oracle, element by element (needs a GB300).
 
 Everything goes through the C ABI (``libxy.so`` via the ctypes binding).
-Tolerances (derived in the design doc from the FP32 arithmetic of the kernels):
+Tolerances (each follows from the FP32 arithmetic of the kernels):
   * Philox words and hot-start counters: bit-exact;
   * accept decisions: identical outside |u - exp(-beta dE)| < 1e-6 (accurate
     path); the in-band count is reported;
