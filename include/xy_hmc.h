@@ -172,6 +172,16 @@ xy_status xy_hmc_set_state(xy_hmc *h, const float *host_angles, const float *hos
 xy_status xy_hmc_set_step(xy_hmc *h, double eps, int32_t n_md);
 xy_status xy_hmc_set_beta(xy_hmc *h, double beta);
 
+/* Self-test of the bounded device waits, with no GPU fault: a one-CTA kernel
+ * polls (at most `polls` times, 1 <= polls <= 2^24) an mbarrier that nothing
+ * ever completes, the same bounded poll the TILED_TMA kernel uses, sets an
+ * error word when the bound runs out, and the host reads it back.  Returns
+ * XY_ETIMEOUT when the wait ran out as it must (XY_OK would mean it did not),
+ * XY_EINVAL for a bad `polls`, XY_ECUDA on a CUDA error.  Synchronizes
+ * cuda_stream.  The paper has no counterpart; this exists to test the failure
+ * path. */
+xy_status xy_selftest_bounded_wait(void *cuda_stream, int64_t polls);
+
 xy_status xy_hmc_synchronize(xy_hmc *h);
 xy_status xy_hmc_destroy(xy_hmc *h);             /* NULL-safe */
 const char *xy_hmc_last_error(const xy_hmc *h);  /* thread-local message if h == NULL */

@@ -139,6 +139,7 @@ def lib():
         "xy_hmc_synchronize": (st, [P]),
         "xy_hmc_destroy": (st, [P]),
         "xy_hmc_last_error": (C.c_char_p, [P]),
+        "xy_selftest_bounded_wait": (st, [P, C.c_int64]),
         "xy_quad_create": (st, [C.POINTER(xy_params), P, P, C.POINTER(P)]),
         "xy_quad_sweep": (st, [P, C.c_int64]),
         "xy_quad_measure": (st, [P, C.c_int32, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),

@@ -260,6 +260,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
+// Poll an mbarrier phase at most `limit` times; false if it never completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             uint64_t* bar) {
   asm volatile(
@@ -321,9 +328,7 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     ++issued[s];
   };
   auto bounded_wait = [&](int s, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i)
-      if (mbar_try_wait(&bar[s], parity)) return true;
-    return false;
+    return mbar_wait_bounded(&bar[s], parity, kSpinLimit);
   };
 
   if (tid == 0) {
@@ -791,6 +796,27 @@ cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* m
   const CUtensorMap* m = static_cast<const CUtensorMap*>(maps4);
   if (box_rows == TmaGeom<4>::kRows) return launch_tma_rows<4>(sincos_mode, a, m, ctas, stream);
   return cudaErrorInvalidValue;
+}
+
+namespace {
+// The failure path of the bounded waits, exercised without a fault: wait on a
+// barrier that nothing ever completes, exactly as the TMA kernel waits on its
+// stage barriers, and set the error word when the bound runs out.
+__global__ void k_selftest_wait(unsigned int* error, long long polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const bool done = mbar_wait_bounded(&bar, 0u, polls);   // no arrival: must run out
+  if (!done && threadIdx.x == 0) atomicOr(error, 1u);
+}
+}  // namespace
+
+cudaError_t launch_selftest_wait(unsigned int* d_error, long long polls, cudaStream_t stream) {
+  k_selftest_wait<<<1, 32, 0, stream>>>(d_error, polls);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hmc_accept(int mode, const HmcArgs& a, double beta, double J,

@@ -652,6 +652,33 @@ xy_status xy_hmc_set_beta(xy_hmc* h, double beta) {
   return XY_OK;
 }
 
+xy_status xy_selftest_bounded_wait(void* cuda_stream, int64_t polls) {
+  if (polls < 1 || polls > (1 << 24)) {
+    tmsg("xy_selftest_bounded_wait: polls must be in [1, 2^24]");
+    return XY_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  unsigned int* d_err = nullptr;
+  unsigned int err = 0;
+  cudaError_t e = cudaMalloc(&d_err, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = xyk::launch_selftest_wait(d_err, (long long)polls, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (d_err) cudaFree(d_err);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    tmsg("xy_selftest_bounded_wait: %s", cudaGetErrorString(e));
+    return XY_ECUDA;
+  }
+  if (err) {
+    tmsg("xy_selftest_bounded_wait: the bounded wait ran out after %lld polls", (long long)polls);
+    return XY_ETIMEOUT;
+  }
+  tmsg("xy_selftest_bounded_wait: the wait completed, which it cannot");
+  return XY_OK;
+}
+
 xy_status xy_hmc_synchronize(xy_hmc* h) {
   xy_status st = check(h);
   if (st != XY_OK) return st;

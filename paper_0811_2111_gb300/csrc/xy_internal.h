@@ -235,6 +235,10 @@ cudaError_t hmc_prepare(int sincos_mode);
 cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
                                 int ctas, cudaStream_t stream);
 
+// One CTA waits, at most `polls` times, on an mbarrier nothing completes and
+// sets *d_error (the bounded-wait failure path, without a fault).
+cudaError_t launch_selftest_wait(unsigned int* d_error, long long polls, cudaStream_t stream);
+
 // Whole trajectories in one cluster launch (xy_hmc_cluster.cu), for
 // hmc_cluster_ok(L): L a power of two in [16, 256].  draw: momenta from Philox
 // (else from a.p_in); mode as launch_hmc_accept.  The state stays in buffer cur.

@@ -12,6 +12,8 @@
   leaves the state untouched bit for bit.
 * Ensembles: exact 2x2 energies, <exp(-dH)> = 1.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -312,3 +314,16 @@ def test_caller_owned_angle_buffer_holds_the_state():
     finally:
         X.xy_hmc_destroy(h)
     assert torch.isfinite(buf).all()                 # still the caller's, still valid
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """The failure path of the device waits, without a fault: a wait on an
+    mbarrier that nothing completes runs out after its bound, the error word
+    reaches the host as XY_ETIMEOUT, and the GPU stays usable."""
+    stream = torch.cuda.current_stream()
+    st = X.lib().xy_selftest_bounded_wait(C.c_void_p(stream.cuda_stream), 4096)
+    assert st == X.XY_ETIMEOUT, X.xy_hmc_last_error(None)
+    assert X.lib().xy_selftest_bounded_wait(None, 0) == X.XY_EINVAL
+    with HMC(128, 1.0, 3, 0.05, 4, kernel="tiled_tma") as h:   # still usable afterwards
+        h.run(2)
+        assert h.info()[0] == 2
