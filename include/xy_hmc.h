@@ -80,7 +80,7 @@ typedef struct {
  * read through distributed shared memory).  AUTO takes CLUSTER for L = 128
  * and 256, else TILED_TMA when L % 128 == 0 and the encoder is available
  * (TILED if not), else SITE (the choices measured fastest on GB300: e.g.
- * TILED_TMA 52.8 us per step at L = 4096 against 57.0 for TILED and 58.3 for
+ * TILED_TMA 51.4 us per step at L = 4096 against 57.0 for TILED and 58.3 for
  * TILED2; CLUSTER 2.8 us per step at L = 128 against 4.0 for TILED_TMA).  All
  * give bit-identical angles, momenta and sums. */
 enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2,

@@ -294,12 +294,14 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   constexpr uint32_t kTmaStageBytes = G::kStageBytes;
   constexpr int kTmaBox = G::kBox;
   extern __shared__ __align__(128) unsigned char tma_smem[];
-  // unit vectors of the rows other warps read, double-buffered by tile parity:
-  // lastrow[b][w + 1] = last row of warp w (lastrow[b][0]: the halo row above
-  // the tile), firstrow[b][w] = first row of warp w (firstrow[b][kTileWarps]:
-  // the halo row below); plus the halo columns
-  __shared__ __align__(16) float2 lastrow[2][kTileWarps + 1][kTileCols];
-  __shared__ __align__(16) float2 firstrow[2][kTileWarps + 1][kTileCols];
+  // unit vectors (cos and sin planes) of the rows other warps read,
+  // double-buffered by tile parity: lastrow[b][w + 1] = last row of warp w
+  // (lastrow[b][0]: the halo row above the tile), firstrow[b][w] = first row of
+  // warp w (firstrow[b][kTileWarps]: the halo row below); plus the halo columns
+  __shared__ __align__(16) float lastrow_c[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float lastrow_s[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float firstrow_c[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float firstrow_s[2][kTileWarps + 1][kTileCols];
   __shared__ float2 side[2][2][TR];
   __shared__ __align__(8) uint64_t bar[2];
 
@@ -388,19 +390,23 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
       float hs, hc;
       xyd::unit_vector<MODE>(th_row, &hs, &hc);
       if (tid < kTileCols) {
-        lastrow[b][0][tid] = make_float2(hc, hs);
+        lastrow_c[b][0][tid] = hc;
+        lastrow_s[b][0][tid] = hs;
       } else {
-        firstrow[b][kTileWarps][tid - kTileCols] = make_float2(hc, hs);
+        firstrow_c[b][kTileWarps][tid - kTileCols] = hc;
+        firstrow_s[b][kTileWarps][tid - kTileCols] = hs;
       }
       if (is_side) {
         xyd::unit_vector<MODE>(th_side, &hs, &hc);
         side[b][tid / TR][tid % TR] = make_float2(hc, hs);
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        firstrow[b][warp][xb + j] = make_float2(c[0][j], sn[0][j]);
-        lastrow[b][warp + 1][xb + j] = make_float2(c[ROWS - 1][j], sn[ROWS - 1][j]);
-      }
+      *reinterpret_cast<float4*>(&firstrow_c[b][warp][xb]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
+      *reinterpret_cast<float4*>(&firstrow_s[b][warp][xb]) =
+          make_float4(sn[0][0], sn[0][1], sn[0][2], sn[0][3]);
+      *reinterpret_cast<float4*>(&lastrow_c[b][warp + 1][xb]) =
+          make_float4(c[ROWS - 1][0], c[ROWS - 1][1], c[ROWS - 1][2], c[ROWS - 1][3]);
+      *reinterpret_cast<float4*>(&lastrow_s[b][warp + 1][xb]) =
+          make_float4(sn[ROWS - 1][0], sn[ROWS - 1][1], sn[ROWS - 1][2], sn[ROWS - 1][3]);
     }
     __syncthreads();   // stage s fully read; edges visible
     if (tid == 0 && ok) {
@@ -412,15 +418,12 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     }
     if (!ok) continue;
 
-    float cdn_a[4], sdn_a[4], cup_a[4], sup_a[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 dn = lastrow[b][warp][xb + j], up = firstrow[b][warp + 1][xb + j];
-      cdn_a[j] = dn.x;
-      sdn_a[j] = dn.y;
-      cup_a[j] = up.x;
-      sup_a[j] = up.y;
-    }
+    const float4 cdn = *reinterpret_cast<const float4*>(&lastrow_c[b][warp][xb]);
+    const float4 sdn = *reinterpret_cast<const float4*>(&lastrow_s[b][warp][xb]);
+    const float4 cup = *reinterpret_cast<const float4*>(&firstrow_c[b][warp + 1][xb]);
+    const float4 sup = *reinterpret_cast<const float4*>(&firstrow_s[b][warp + 1][xb]);
+    const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
+    const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
