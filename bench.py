@@ -44,7 +44,7 @@ FLUSH_BYTES = 256 << 20
 #     polynomial / CUDA sincosf-class path, 2 x 3 with the SFU intrinsics;
 #   dE, Boltzmann factor, accept test and select: 22 (expf) / 14 (__expf);
 #   per-sweep sums: 17 per black site -> 8.5 per update.
-ALG_INSTR_PER_UPDATE = {"accurate": 132.5, "libm": 132.5, "fast": 76.5}
+ALG_INSTR_PER_UPDATE = {"accurate": 128.5, "libm": 132.5, "fast": 76.5}
 SMS, SMSP_PER_SM, LANES = 152, 4, 32       # GB300: 152 SMs x 4 schedulers x 32 lanes
 TIMING_EVERY = 50          # kernel events on every 50th sweep of the timed region
 

@@ -59,7 +59,7 @@ typedef enum {
 
 enum { XY_START_HOT = 0, XY_START_COLD = 1 };
 /* Precision of the per-site unit vectors and Boltzmann factors (all FP32):
- *   XY_SINCOS_ACCURATE  own Cody-Waite + Taylor sincos (<= 1 ulp-class) and expf;
+ *   XY_SINCOS_ACCURATE  own Cody-Waite + minimax sincos (max error 6.8e-8) and expf;
  *   XY_SINCOS_FAST      the SFU intrinsics __sincosf / __expf;
  *   XY_SINCOS_LIBM      CUDA's sincosf / expf. */
 enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };

@@ -103,9 +103,10 @@ namespace xyd {
 // mathematics: Cody-Waite reduction by pi/2 (W. J. Cody, W. Waite, "Software
 // Manual for the Elementary Functions", 1980) with a two-part constant whose
 // high part has three trailing zero bits (so q * hi is exact for |q| <= 7),
-// then the Taylor series of sin (to r^9) and cos (to r^10) on |r| <= pi/4,
-// whose truncation errors (< 2e-9 and < 2e-10) are far below FP32 rounding,
-// and the quadrant identities sin(r + q pi/2), cos(r + q pi/2).
+// then minimax polynomials for sin (to r^7) and cos (to r^8) on |r| <= pi/4,
+// fitted for absolute error by Remez exchange (csrc/fit_sincos.py; truncation
+// errors 1.8e-9 and 5.4e-11, far below FP32 rounding), and the quadrant
+// identities sin(r + q pi/2), cos(r + q pi/2).
 constexpr float kTwoOverPi = 0.636619772367581343f;
 constexpr float kPio2Hi = 1.57079601287841796875f;       // pi/2 with 21 significant bits
 constexpr float kPio2Lo = 3.13916473532088954e-07f;      // pi/2 - kPio2Hi
@@ -118,15 +119,13 @@ __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out)
   float r = __fmaf_rn(-qf, kPio2Hi, t);                   // exact
   r = __fmaf_rn(-qf, kPio2Lo, r);
   const float r2 = __fmul_rn(r, r);
-  // sin r = r + r^3 (-1/3! + r^2 (1/5! + r^2 (-1/7! + r^2 / 9!)))
-  float ps = __fmaf_rn(r2, 2.75573192239858907e-06f, -1.98412698412698413e-04f);
-  ps = __fmaf_rn(r2, ps, 8.33333333333333333e-03f);
-  ps = __fmaf_rn(r2, ps, -1.66666666666666667e-01f);
+  // sin r = r + r^3 (c3 + r^2 (c5 + r^2 c7))
+  float ps = __fmaf_rn(r2, -0.000194956359337084f, 0.00833197869360447f);
+  ps = __fmaf_rn(r2, ps, -0.16666650772094727f);
   const float sr = __fmaf_rn(__fmul_rn(r, r2), ps, r);
-  // cos r = 1 + r^2 (-1/2! + r^2 (1/4! + r^2 (-1/6! + r^2 (1/8! - r^2 / 10!))))
-  float pc = __fmaf_rn(r2, -2.75573192239858907e-07f, 2.48015873015873016e-05f);
-  pc = __fmaf_rn(r2, pc, -1.38888888888888889e-03f);
-  pc = __fmaf_rn(r2, pc, 4.16666666666666667e-02f);
+  // cos r = 1 + r^2 (c2 + r^2 (c4 + r^2 (c6 + r^2 c8)))
+  float pc = __fmaf_rn(r2, 2.4390450562350452e-05f, -0.0013886763481423259f);
+  pc = __fmaf_rn(r2, pc, 0.04166662320494652f);
   pc = __fmaf_rn(r2, pc, -0.5f);
   const float cr = __fmaf_rn(r2, pc, 1.0f);
   // quadrant: odd q swaps sin and cos; sin is negative for q mod 4 in {2, 3}

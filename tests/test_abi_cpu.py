@@ -166,3 +166,45 @@ def test_quad_create_rejects_bad_parameters(lib):
     assert lib.xy_quad_sweep(None, 1) == X.XY_EINVAL
     assert lib.xy_quad_destroy(None) == X.XY_OK
     assert lib.xy_quad_sweep(C.c_void_p(0x3000), 1) == X.XY_ESTATE
+
+
+def test_sincos_polynomial_constants_are_the_fit():
+    """The kernel's polynomial coefficients are the Remez fit of
+    csrc/fit_sincos.py rounded to FP32, and the polynomial evaluated with the
+    kernel's FP32 operations (single-rounded FMAs) stays within 7e-8 of sin and
+    cos over [0, 2 pi]."""
+    import importlib.util
+    import numpy as np
+    path = os.path.join(ROOT, "paper_0811_2111_gb300", "csrc", "fit_sincos.py")
+    spec = importlib.util.spec_from_file_location("fit_sincos", path)
+    fs = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(fs)
+    cs, es, cc, ec = fs.fit()
+    assert es < 2e-9 and ec < 1e-10
+    src = open(os.path.join(ROOT, "paper_0811_2111_gb300", "csrc", "xy_device.cuh")).read()
+    body = src[src.index("sincos_poly"):src.index("quadrant: odd q")]
+    consts = [float(v) for v in re.findall(r"(-?\d+\.\d+(?:e-?\d+)?)f", body)]
+    for v in list(cs) + list(cc):
+        assert any(np.float32(v) == np.float32(k) for k in consts), v
+
+    f32 = np.float32
+
+    def fma(a, b, c):
+        return f32(np.float64(a) * np.float64(b) + np.float64(c))
+    S = [f32(v) for v in cs]
+    Cc = [f32(v) for v in cc]
+    hi, lo, magic = f32(1.57079601287841796875), f32(3.13916473532088954e-07), f32(12582912.0)
+    worst = 0.0
+    for t in np.linspace(0, 2 * np.pi, 20001).astype(np.float32):
+        qt = fma(t, f32(0.636619772367581343), magic)
+        q = int(np.frombuffer(qt.tobytes(), np.int32)[0])
+        qf = f32(qt - magic)
+        r = fma(-qf, lo, fma(-qf, hi, t))
+        r2 = f32(r * r)
+        sr = fma(f32(r * r2), fma(r2, fma(r2, S[2], S[1]), S[0]), r)
+        cr = fma(r2, fma(r2, fma(r2, fma(r2, Cc[3], Cc[2]), Cc[1]), Cc[0]), f32(1.0))
+        s0, c0 = (cr, sr) if q & 1 else (sr, cr)
+        s = -s0 if (q & 3) in (2, 3) else s0
+        c = -c0 if (q & 3) in (1, 2) else c0
+        worst = max(worst, abs(float(s) - np.sin(float(t))), abs(float(c) - np.cos(float(t))))
+    assert worst < 7e-8, worst
