@@ -90,6 +90,13 @@ struct xy_batch {
   int64_t rec_cap = 0;            // records per lattice
   int64_t rec_count = 0;          // sweeps recorded per lattice
   uint64_t next_sweep = 0;
+  // lattices whose side the single-lattice fused kernel takes (L % 128 == 0),
+  // grouped by side: one multi-lattice launch per group and sweep, on a branch
+  // of the round's graph parallel to the cluster kernel of the other lattices
+  std::vector<int> group_L, group_start, group_size;
+  int32_t* d_groups = nullptr;
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_cap = -1;         // rec_cap the graph was captured with
   xy_status sticky = XY_OK;
@@ -146,11 +153,16 @@ void free_all(xy_batch* b) {
   void* ptrs[] = {b->d_theta, b->d_theta2, b->d_offset, b->d_L, b->d_beta, b->d_bands, b->d_rec,
                   b->d_counters, b->d_pair_ladder, b->d_pair_pos, b->d_ladder_start,
                   b->d_pos_lattice, b->d_pos_beta, b->d_acc, b->d_att, b->d_scratch,
-                  b->d_partials};
+                  b->d_partials, b->d_groups};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   b->capture_stream = nullptr;
+  if (b->side_stream) cudaStreamDestroy(b->side_stream);
+  b->side_stream = nullptr;
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  b->ev_fork = b->ev_join = nullptr;
 }
 
 // Bands: each lattice is cut into nb bands of whole rows (nb <= cluster size),
@@ -168,9 +180,29 @@ size_t band_bytes(bool fused, int rows, int L) {
 
 void make_plan(xy_batch* b, int target_sites) {
   const int CS = xyk::kClusterSize;
-  std::vector<int> order(b->n);
-  std::vector<int> nbands(b->n), rows(b->n);
+  // fused algorithm: sides the single-lattice fused kernel takes go to groups
+  std::map<int, std::vector<int>> groups;
+  std::vector<int> banded;
   for (int i = 0; i < b->n; ++i) {
+    if (b->fused && xyk::fused_supported(b->L[i])) {
+      groups[b->L[i]].push_back(i);
+    } else {
+      banded.push_back(i);
+    }
+  }
+  b->group_L.clear();
+  b->group_start.clear();
+  b->group_size.clear();
+  int start = 0;
+  for (auto& kv : groups) {
+    b->group_L.push_back(kv.first);
+    b->group_start.push_back(start);
+    b->group_size.push_back((int)kv.second.size());
+    start += (int)kv.second.size();
+  }
+  std::vector<int> order;
+  std::vector<int> nbands(b->n, 0), rows(b->n, 0);
+  for (int i : banded) {
     const int Li = b->L[i];
     int nb = (int)((int64_t)Li * Li / std::max(target_sites, 1));
     // the largest band that fits the per-CTA shared-memory budget
@@ -183,7 +215,7 @@ void make_plan(xy_batch* b, int target_sites) {
     nb = (Li + r - 1) / r;
     nbands[i] = nb;
     rows[i] = r;
-    order[i] = i;
+    order.push_back(i);
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return nbands[a] > nbands[c]; });
   std::vector<std::vector<xyk::BatchBand>> clusters;
@@ -290,11 +322,52 @@ xyk::ExchangeArgs exchange_args(const xy_batch* b) {
   return x;
 }
 
+xyk::FusedBatchArgs group_args(const xy_batch* b, size_t g, int s) {
+  xyk::FusedBatchArgs f;
+  f.theta = b->d_theta;
+  f.theta2 = b->d_theta2;
+  f.offset = b->d_offset;
+  f.beta = b->d_beta;
+  f.lattices = b->d_groups + b->group_start[g];
+  f.records = b->d_rec;
+  f.rec_stride = b->rec_cap;
+  f.rec_sweep0 = 0;
+  f.counters = b->d_counters;
+  f.s = s;
+  f.L = b->group_L[g];
+  f.J = b->p.J;
+  f.delta = (float)b->p.delta;
+  f.rk = xyd::make_round_keys(b->p.seed);
+  f.lattice_id0 = b->p.lattice_id0;
+  return f;
+}
+
+// One round: the banded cluster kernel (all of its sweeps in one launch) and,
+// on a parallel branch, the grouped fused sweeps (one launch per group and
+// sweep); then the exchange kernel, which also advances the counters.
 cudaError_t enqueue_round(const xy_batch* b, cudaStream_t s) {
-  cudaError_t e = b->fused ? xyk::launch_batch_fused(b->p.sincos_mode, b->p.reduce_mode,
-                                                     round_args(b), b->n_ctas, s)
-                           : xyk::launch_batch_round(b->p.sincos_mode, b->p.reduce_mode,
-                                                     round_args(b), b->n_ctas, s);
+  cudaError_t e = cudaSuccess;
+  const bool groups = !b->group_L.empty();
+  const bool banded = b->n_ctas > 0;
+  cudaStream_t gs = s;
+  if (groups && banded) {
+    e = cudaEventRecord(b->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side_stream, b->ev_fork, 0);
+    gs = b->side_stream;
+  }
+  if (e == cudaSuccess && banded)
+    e = b->fused ? xyk::launch_batch_fused(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
+                                           b->n_ctas, s)
+                 : xyk::launch_batch_round(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
+                                           b->n_ctas, s);
+  for (int sw = 0; groups && sw < b->p.sweeps_per_round && e == cudaSuccess; ++sw)
+    for (size_t g = 0; g < b->group_L.size() && e == cudaSuccess; ++g)
+      e = xyk::launch_fused_batch_sweep(b->p.sincos_mode, b->p.reduce_mode, group_args(b, g, sw),
+                                        b->group_size[g], gs);
+  if (e == cudaSuccess && groups && banded) {
+    e = cudaEventRecord(b->ev_join, gs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
+  }
   if (e == cudaSuccess) e = xyk::launch_exchange(exchange_args(b), s);
   return e;
 }
@@ -456,6 +529,17 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   alloc((void**)&b->d_att, sizeof(unsigned long long) * b->n_slots);
   alloc((void**)&b->d_scratch, sizeof(float) * (size_t)maxN);
   alloc((void**)&b->d_partials, sizeof(double) * (size_t)b->n * xyk::kMaxSegments * xyk::kPartials);
+  std::vector<int32_t> group_lattices;
+  for (size_t g = 0; g < b->group_L.size(); ++g)
+    for (int i = 0; i < b->n; ++i)
+      if (b->L[i] == b->group_L[g]) group_lattices.push_back(i);
+  alloc((void**)&b->d_groups, sizeof(int32_t) * group_lattices.size());
+  if (e == cudaSuccess && !b->group_L.empty()) {
+    step = "side stream";
+    e = cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     bmsg("xy_batch_create: %s: %s", step, cudaGetErrorString(e));
     return fail_create(e == cudaErrorMemoryAllocation ? XY_ENOMEM : XY_ECUDA);
@@ -473,6 +557,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   h2d(b->d_ladder_start, ladder_start.data(), sizeof(int32_t) * b->n_ladders);
   h2d(b->d_pos_lattice, pos_lattice.data(), sizeof(int32_t) * b->n_slots);
   h2d(b->d_pos_beta, pos_beta.data(), sizeof(double) * b->n_slots);
+  h2d(b->d_groups, group_lattices.data(), sizeof(int32_t) * group_lattices.size());
   if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(uint32_t) * 2);
   if (e == cudaSuccess) e = cudaMemset(b->d_acc, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
   if (e == cudaSuccess) e = cudaMemset(b->d_att, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
@@ -487,6 +572,8 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
                                             b->cs_bytes + xyk::batch_fused_tail_bytes())
                  : xyk::prepare_batch_round(p->sincos_mode, p->reduce_mode,
                                             b->cs_bytes + xyk::batch_smem_bytes(0));
+    if (e == cudaSuccess && !b->group_L.empty())
+      e = xyk::prepare_fused_batch(p->sincos_mode, p->reduce_mode);
   }
   if (e == cudaSuccess) {
     step = "synchronize";

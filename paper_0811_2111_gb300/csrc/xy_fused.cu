@@ -87,14 +87,30 @@ __device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, 
 }
 
 // One ring site (red, stage (r, c)): same arithmetic as the tile sites.
+// The scalars of one fused sweep; the Philox round keys are passed separately
+// (by reference, so a kernel can leave them in its parameter space).
+struct FusedCore {
+  const float* src;
+  float* dst;
+  int L;
+  int W;
+  float K;
+  float delta;
+  uint32_t lattice_id;
+  uint32_t sweep;
+  xy_record* rec;
+  double beta;
+};
+
 template <int MODE>
 __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c, int q,
-                                              uint32_t site, const FusedArgs& a) {
+                                              uint32_t site, const FusedCore& a,
+                                              const xyd::RoundKeys& rk) {
   const float2 l = cs[1][r][c + q - 1], rt = cs[1][r][c + q];
   const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
   const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
   const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-  const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.rk);
+  const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), rk);
   const float2 own = cs[0][r][c];
   const xyd::SiteResult res =
       xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, w.x, w.y, a.K, a.delta);
@@ -102,8 +118,9 @@ __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c
   cs[0][r][c] = make_float2(res.c, res.s);
 }
 
+// One sweep of the tile (blockIdx.x, blockIdx.y) of one lattice.
 template <int MODE, int RED>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
+__device__ __forceinline__ void fused_sweep_body(const FusedCore& a, const xyd::RoundKeys& rk) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
   CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
@@ -190,8 +207,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
     PairNeighbours n;
     pair_neighbours(cs[1], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -225,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
       const int k = wrap_once(k0 + tk, W);
       const int q = y & 1;
       const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a);
+      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a, rk);
     }
   }
   __syncthreads();
@@ -243,8 +260,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
     PairNeighbours n;
     pair_neighbours(cs[0], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
@@ -277,6 +294,29 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
 }
 
 template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
+  const FusedCore c{a.src, a.dst, a.L, a.W, a.K, a.delta, a.lattice_id, a.sweep, a.rec, a.beta};
+  fused_sweep_body<MODE, RED>(c, a.rk);
+}
+
+// Many lattices of one side in one launch (blockIdx.z = lattice of the group),
+// for the batched engine: the sweep index comes from the device counters and
+// beta from the device (replica exchange moves it), the state ping-pongs
+// between the batch's two buffers by sweep parity.
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_batch(FusedBatchArgs b) {
+  const int i = b.lattices[blockIdx.z];
+  const uint32_t sweep = b.counters[0] + (uint32_t)b.s;
+  const float* base = (sweep & 1u) ? b.theta2 : b.theta;
+  float* out = (sweep & 1u) ? b.theta : b.theta2;
+  const double beta = b.beta[i];
+  const FusedCore c{base + b.offset[i], out + b.offset[i], b.L, b.L / 2, (float)(beta * b.J),
+                    b.delta, b.lattice_id0 + (uint32_t)i, sweep,
+                    b.records + (size_t)i * b.rec_stride + (sweep - b.rec_sweep0), beta};
+  fused_sweep_body<MODE, RED>(c, b.rk);
+}
+
+template <int MODE, int RED>
 cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
   static bool configured[64] = {};   // attributes set once per instantiation and device
   int dev = 0;
@@ -297,9 +337,53 @@ cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+template <int MODE, int RED>
+cudaError_t launch_fused_batch_one(const FusedBatchArgs& b, int n_lattices, cudaStream_t stream) {
+  // the attribute is set per device before any capture (prepare_fused_batch)
+  const dim3 grid(b.L / 2 / kTileK, b.L / kTileRows, n_lattices);
+  k_sweep_fused_batch<MODE, RED><<<grid, kThreads, kSmemBytes, stream>>>(b);
+  return cudaGetLastError();
+}
+
+template <int MODE, int RED>
+cudaError_t prepare_one() {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
 }  // namespace
 
 bool fused_supported(int L) { return L >= 128 && (L % 128) == 0; }
+
+cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode) {
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? prepare_one<0, 1>() : prepare_one<0, 0>();
+    case 1: return comp ? prepare_one<1, 1>() : prepare_one<1, 0>();
+    default: return comp ? prepare_one<2, 1>() : prepare_one<2, 0>();
+  }
+}
+
+cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
+                                     int n_lattices, cudaStream_t stream) {
+  if (!fused_supported(b.L) || n_lattices < 1) return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0:
+      return comp ? launch_fused_batch_one<0, 1>(b, n_lattices, stream)
+                  : launch_fused_batch_one<0, 0>(b, n_lattices, stream);
+    case 1:
+      return comp ? launch_fused_batch_one<1, 1>(b, n_lattices, stream)
+                  : launch_fused_batch_one<1, 0>(b, n_lattices, stream);
+    default:
+      return comp ? launch_fused_batch_one<2, 1>(b, n_lattices, stream)
+                  : launch_fused_batch_one<2, 0>(b, n_lattices, stream);
+  }
+}
 
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream) {

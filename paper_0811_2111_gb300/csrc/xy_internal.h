@@ -59,6 +59,29 @@ bool fused_supported(int L);
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream);
 
+// The fused sweep over many lattices of one side L (a multiple of 128) of a
+// batch, one launch per sweep: lattice lattices[z] for blockIdx.z = z.
+struct FusedBatchArgs {
+  float* theta;                 // batch buffer read on even sweeps, written on odd ones
+  float* theta2;                // the other buffer
+  const int64_t* offset;        // [n] floats from a buffer's start to lattice i
+  const double* beta;           // [n] current beta (device)
+  const int32_t* lattices;      // [n_lattices] lattices of this launch
+  xy_record* records;           // [n][rec_stride]
+  int64_t rec_stride;
+  uint32_t rec_sweep0;
+  const uint32_t* counters;     // [0] first sweep of the round
+  int s;                        // sweep of the round (sweep = counters[0] + s)
+  int L;
+  double J;
+  float delta;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id0;
+};
+cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode);
+cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
+                                     int n_lattices, cudaStream_t stream);
+
 // Unit vectors of n angles with the kernels' sincos of precision `mode`
 // (diagnostics and accuracy tests).
 cudaError_t launch_eval_unit_vector(int mode, const float* theta, float* c, float* s, int64_t n,
