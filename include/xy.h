@@ -226,9 +226,13 @@ typedef struct {
     uint32_t lattice_id0;       /* lattice i uses lattice id lattice_id0 + i         */
     int32_t sweeps_per_round;   /* sweeps per launch (and between exchanges), >= 1   */
     int32_t target_band_sites;  /* sites per CTA band of the work plan (0: 8192)     */
-    int32_t algorithm;          /* XY_ALGO_AUTO / _FUSED: one staging and one cluster
-                                   barrier per sweep, state ping-ponged between two
-                                   buffers; XY_ALGO_TWO_PASS: in place, two of each */
+    int32_t algorithm;          /* XY_ALGO_AUTO / _FUSED: state ping-ponged between two
+                                   buffers; lattices with L % 128 == 0 run the fused
+                                   sweep kernel (one launch per side and sweep), the
+                                   others a cluster kernel with one staging and one
+                                   cluster barrier per sweep, on parallel graph
+                                   branches; XY_ALGO_TWO_PASS: every lattice in place
+                                   in the cluster kernel, two of each per sweep */
 } xy_batch_params;
 
 /* Create and hot/cold-start all lattices; the plan, ladders and buffers are
