@@ -102,9 +102,9 @@ struct FusedCore {
   double beta;
 };
 
-template <int MODE>
+template <int MODE, class Args>
 __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c, int q,
-                                              uint32_t site, const FusedCore& a,
+                                              uint32_t site, const Args& a,
                                               const xyd::RoundKeys& rk) {
   const float2 l = cs[1][r][c + q - 1], rt = cs[1][r][c + q];
   const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
@@ -118,9 +118,12 @@ __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c
   cs[0][r][c] = make_float2(res.c, res.s);
 }
 
-// One sweep of the tile (blockIdx.x, blockIdx.y) of one lattice.
-template <int MODE, int RED>
-__device__ __forceinline__ void fused_sweep_body(const FusedCore& a, const xyd::RoundKeys& rk) {
+// One sweep of the tile (blockIdx.x, blockIdx.y) of one lattice.  Args is
+// FusedArgs (the single-lattice kernel passes its parameter, so every field is
+// read from parameter space where it is used) or FusedCore (built per CTA by
+// the batched kernel); both have the fields used here.
+template <int MODE, int RED, class Args>
+__device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
   CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
@@ -295,8 +298,7 @@ __device__ __forceinline__ void fused_sweep_body(const FusedCore& a, const xyd::
 
 template <int MODE, int RED>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
-  const FusedCore c{a.src, a.dst, a.L, a.W, a.K, a.delta, a.lattice_id, a.sweep, a.rec, a.beta};
-  fused_sweep_body<MODE, RED>(c, a.rk);
+  fused_sweep_body<MODE, RED>(a, a.rk);
 }
 
 // Many lattices of one side in one launch (blockIdx.z = lattice of the group),
