@@ -91,12 +91,16 @@ struct xy_batch {
   int64_t rec_count = 0;          // sweeps recorded per lattice
   uint64_t next_sweep = 0;
   // lattices whose side the single-lattice fused kernel takes (L % 128 == 0),
-  // grouped by side: one multi-lattice launch per group and sweep, on a branch
-  // of the round's graph parallel to the cluster kernel of the other lattices
+  // in groups of one side and about kGroupCtas CTAs per launch: each group
+  // sweeps (one launch per sweep) on its own branch of the round's graph, in
+  // parallel with the other groups and with the cluster kernel of the other
+  // lattices, so that the groups fill each other's partial waves
   std::vector<int> group_L, group_start, group_size;
+  std::vector<int32_t> group_lattices;
   int32_t* d_groups = nullptr;
-  cudaStream_t side_stream = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<cudaStream_t> branch_streams;
+  std::vector<cudaEvent_t> ev_joins;
+  cudaEvent_t ev_fork = nullptr;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_cap = -1;         // rec_cap the graph was captured with
   xy_status sticky = XY_OK;
@@ -158,11 +162,14 @@ void free_all(xy_batch* b) {
     if (q) cudaFree(q);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   b->capture_stream = nullptr;
-  if (b->side_stream) cudaStreamDestroy(b->side_stream);
-  b->side_stream = nullptr;
+  for (cudaStream_t st : b->branch_streams)
+    if (st) cudaStreamDestroy(st);
+  b->branch_streams.clear();
+  for (cudaEvent_t ev : b->ev_joins)
+    if (ev) cudaEventDestroy(ev);
+  b->ev_joins.clear();
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_join) cudaEventDestroy(b->ev_join);
-  b->ev_fork = b->ev_join = nullptr;
+  b->ev_fork = nullptr;
 }
 
 // Bands: each lattice is cut into nb bands of whole rows (nb <= cluster size),
@@ -171,6 +178,7 @@ void free_all(xy_batch* b) {
 // Shared memory a CTA may use for its band: two CTAs must fit one SM (228 KB).
 constexpr size_t kStageBudget = 96 * 1024;          // two-pass: (r + 2) * L/2 unit vectors
 constexpr size_t kFusedStageBudget = 108 * 1024;    // fused: (r + 4) * L/2 * (2 angles + 2 vectors)
+constexpr int kGroupCtas = 128;                     // CTAs per grouped fused launch (one branch each)
 
 size_t band_bytes(bool fused, int rows, int L) {
   const size_t W = (size_t)(L / 2);
@@ -193,12 +201,18 @@ void make_plan(xy_batch* b, int target_sites) {
   b->group_L.clear();
   b->group_start.clear();
   b->group_size.clear();
-  int start = 0;
+  b->group_lattices.clear();
   for (auto& kv : groups) {
-    b->group_L.push_back(kv.first);
-    b->group_start.push_back(start);
-    b->group_size.push_back((int)kv.second.size());
-    start += (int)kv.second.size();
+    const int L = kv.first;
+    const int tiles = (L / 2 / 64) * (L / 32);             // CTAs of one lattice's sweep
+    const int per = std::max(1, kGroupCtas / tiles);
+    for (size_t k = 0; k < kv.second.size(); k += per) {
+      const int n = (int)std::min<size_t>(per, kv.second.size() - k);
+      b->group_L.push_back(L);
+      b->group_start.push_back((int)b->group_lattices.size());
+      b->group_size.push_back(n);
+      for (int j = 0; j < n; ++j) b->group_lattices.push_back(kv.second[k + j]);
+    }
   }
   std::vector<int> order;
   std::vector<int> nbands(b->n, 0), rows(b->n, 0);
@@ -342,32 +356,28 @@ xyk::FusedBatchArgs group_args(const xy_batch* b, size_t g, int s) {
   return f;
 }
 
-// One round: the banded cluster kernel (all of its sweeps in one launch) and,
-// on a parallel branch, the grouped fused sweeps (one launch per group and
-// sweep); then the exchange kernel, which also advances the counters.
+// One round: the banded cluster kernel (all of its sweeps in one launch) on
+// the main branch and, on one parallel branch per group, the grouped fused
+// sweeps (one launch per sweep); then, after all branches, the exchange
+// kernel, which also advances the counters.
 cudaError_t enqueue_round(const xy_batch* b, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  const bool groups = !b->group_L.empty();
-  const bool banded = b->n_ctas > 0;
-  cudaStream_t gs = s;
-  if (groups && banded) {
-    e = cudaEventRecord(b->ev_fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side_stream, b->ev_fork, 0);
-    gs = b->side_stream;
+  const size_t ng = b->group_L.size();
+  if (ng > 0) e = cudaEventRecord(b->ev_fork, s);
+  for (size_t g = 0; g < ng && e == cudaSuccess; ++g) {
+    cudaStream_t gs = b->branch_streams[g];
+    e = cudaStreamWaitEvent(gs, b->ev_fork, 0);
+    for (int sw = 0; sw < b->p.sweeps_per_round && e == cudaSuccess; ++sw)
+      e = xyk::launch_fused_batch_sweep(b->p.sincos_mode, b->p.reduce_mode, group_args(b, g, sw),
+                                        b->group_size[g], gs);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_joins[g], gs);
   }
-  if (e == cudaSuccess && banded)
+  if (e == cudaSuccess && b->n_ctas > 0)
     e = b->fused ? xyk::launch_batch_fused(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
                                            b->n_ctas, s)
                  : xyk::launch_batch_round(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
                                            b->n_ctas, s);
-  for (int sw = 0; groups && sw < b->p.sweeps_per_round && e == cudaSuccess; ++sw)
-    for (size_t g = 0; g < b->group_L.size() && e == cudaSuccess; ++g)
-      e = xyk::launch_fused_batch_sweep(b->p.sincos_mode, b->p.reduce_mode, group_args(b, g, sw),
-                                        b->group_size[g], gs);
-  if (e == cudaSuccess && groups && banded) {
-    e = cudaEventRecord(b->ev_join, gs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join, 0);
-  }
+  for (size_t g = 0; g < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(s, b->ev_joins[g], 0);
   if (e == cudaSuccess) e = xyk::launch_exchange(exchange_args(b), s);
   return e;
 }
@@ -529,16 +539,18 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   alloc((void**)&b->d_att, sizeof(unsigned long long) * b->n_slots);
   alloc((void**)&b->d_scratch, sizeof(float) * (size_t)maxN);
   alloc((void**)&b->d_partials, sizeof(double) * (size_t)b->n * xyk::kMaxSegments * xyk::kPartials);
-  std::vector<int32_t> group_lattices;
-  for (size_t g = 0; g < b->group_L.size(); ++g)
-    for (int i = 0; i < b->n; ++i)
-      if (b->L[i] == b->group_L[g]) group_lattices.push_back(i);
-  alloc((void**)&b->d_groups, sizeof(int32_t) * group_lattices.size());
+  alloc((void**)&b->d_groups, sizeof(int32_t) * b->group_lattices.size());
   if (e == cudaSuccess && !b->group_L.empty()) {
-    step = "side stream";
-    e = cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
+    step = "branch streams";
+    e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    for (size_t g = 0; g < b->group_L.size() && e == cudaSuccess; ++g) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->branch_streams.push_back(st);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->ev_joins.push_back(ev);
+    }
   }
   if (e != cudaSuccess) {
     bmsg("xy_batch_create: %s: %s", step, cudaGetErrorString(e));
@@ -557,7 +569,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   h2d(b->d_ladder_start, ladder_start.data(), sizeof(int32_t) * b->n_ladders);
   h2d(b->d_pos_lattice, pos_lattice.data(), sizeof(int32_t) * b->n_slots);
   h2d(b->d_pos_beta, pos_beta.data(), sizeof(double) * b->n_slots);
-  h2d(b->d_groups, group_lattices.data(), sizeof(int32_t) * group_lattices.size());
+  h2d(b->d_groups, b->group_lattices.data(), sizeof(int32_t) * b->group_lattices.size());
   if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(uint32_t) * 2);
   if (e == cudaSuccess) e = cudaMemset(b->d_acc, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
   if (e == cudaSuccess) e = cudaMemset(b->d_att, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
