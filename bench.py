@@ -289,6 +289,7 @@ def measure_batch(dev, steps, warmup, sincos, rounds_per_step=100):
             ms.append(e0.elapsed_time(e1))
         slots, acc, att = b.exchange_stats()
         n_ctas = b.info()[3]
+        launches_per_round = b.launches_per_round()
     value = sites * sweeps * steps / (sum(ms) * 1e-3)
     # the same work as separate single-lattice contexts, one lattice at a time
     per_L = {}
@@ -313,7 +314,7 @@ def measure_batch(dev, steps, warmup, sincos, rounds_per_step=100):
             "exchange_acceptance": float(acc.sum() / max(att.sum(), 1)),
             "single_lattice_kernels_value": single_value,
             "speedup_vs_single_lattice_kernels": value / single_value,
-            "launches_per_step": 2 * rounds_per_step}
+            "launches_per_step": launches_per_round * rounds_per_step}
 
 
 def measure_differentiation(dev, sincos, therm=10000, meas=100000):

@@ -263,6 +263,10 @@ xy_status xy_batch_exchange_stats(xy_batch *b, int32_t *n_slots, int32_t *slot_l
                                   uint64_t *accepted, uint64_t *attempted);
 /* Angles of one lattice in natural order (L*L floats; synchronizes). */
 xy_status xy_batch_get_state(xy_batch *b, int32_t lattice, float *host_angles);
+/* Kernel launches one round replays: the grouped fused sweeps (groups x
+ * sweeps_per_round), the cluster kernel if any lattice is banded, and the
+ * exchange kernel. */
+xy_status xy_batch_launches_per_round(const xy_batch *b, int32_t *launches);
 xy_status xy_batch_synchronize(xy_batch *b);
 
 /* Series statistics and beta derivatives of every lattice of a batch over

@@ -119,6 +119,7 @@ def lib():
         "xy_batch_exchange_stats": (st, [P, C.POINTER(C.c_int32), P, P, P]),
         "xy_batch_get_state": (st, [P, C.c_int32, P]),
         "xy_batch_synchronize": (st, [P]),
+        "xy_batch_launches_per_round": (st, [P, C.POINTER(C.c_int32)]),
         "xy_batch_series_stats": (st, [P, C.c_int64, C.c_int64, P]),
         "xy_batch_destroy": (st, [P]),
         "xy_batch_last_error": (C.c_char_p, [P]),
@@ -320,6 +321,12 @@ def xy_batch_exchange_stats(b, slot_ptr, acc_ptr, att_ptr):
 
 def xy_batch_get_state(b, lattice, host_ptr):
     batch_check(lib().xy_batch_get_state(b, lattice, host_ptr), b)
+
+
+def xy_batch_launches_per_round(b):
+    n = C.c_int32()
+    batch_check(lib().xy_batch_launches_per_round(b, C.byref(n)), b)
+    return n.value
 
 
 def xy_batch_synchronize(b):

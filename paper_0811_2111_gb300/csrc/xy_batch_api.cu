@@ -637,6 +637,17 @@ xy_status xy_batch_info(const xy_batch* b, int32_t* n_lattices, int64_t* n_recor
   return XY_OK;
 }
 
+xy_status xy_batch_launches_per_round(const xy_batch* b, int32_t* launches) {
+  xy_status st = check_batch(b);
+  if (st != XY_OK) return st;
+  if (!launches) {
+    bmsg("xy_batch_launches_per_round: NULL output");
+    return XY_EINVAL;
+  }
+  *launches = (int32_t)b->group_L.size() * b->p.sweeps_per_round + (b->n_ctas > 0 ? 1 : 0) + 1;
+  return XY_OK;
+}
+
 xy_status xy_batch_measure(xy_batch* b, int32_t lattice, int64_t first, int64_t count,
                            xy_obs* out) {
   xy_status st = check_batch(b);

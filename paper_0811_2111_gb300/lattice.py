@@ -194,6 +194,9 @@ class Batch:
     def info(self):
         return X.xy_batch_info(self.b)
 
+    def launches_per_round(self):
+        return X.xy_batch_launches_per_round(self.b)
+
     def observables(self, lattice, first=0, count=None):
         _, nrec, _, _ = X.xy_batch_info(self.b)
         count = nrec - first if count is None else count

@@ -136,6 +136,8 @@ def test_replica_exchange_configuration_runs():
     with Batch(Ls, betas, WL.BATCH_SEED, ladders=ladders, sweeps_per_round=10) as b:
         b.run(20)
         n, nrec, nxt, n_ctas = b.info()
+        # L = 256: 16 CTAs per lattice, groups of 8; L = 128: 4 CTAs, one group of 32
+        assert b.launches_per_round() == (4 + 1) * 10 + 1 + 1
         bl = b.betas()
         slots, acc, att = b.exchange_stats()
         e0 = b.observables(0)["e"]
