@@ -206,12 +206,16 @@ void make_plan(xy_batch* b, int target_sites) {
     const int L = kv.first;
     const int tiles = (L / 2 / 64) * (L / 32);             // CTAs of one lattice's sweep
     const int per = std::max(1, kGroupCtas / tiles);
-    for (size_t k = 0; k < kv.second.size(); k += per) {
-      const int n = (int)std::min<size_t>(per, kv.second.size() - k);
+    // as few groups as `per` allows, their sizes differing by at most one
+    const int count = (int)kv.second.size();
+    const int ngroups = (count + per - 1) / per;
+    for (int g = 0, k = 0; g < ngroups; ++g) {
+      const int n = count / ngroups + (g < count % ngroups ? 1 : 0);
       b->group_L.push_back(L);
       b->group_start.push_back((int)b->group_lattices.size());
       b->group_size.push_back(n);
       for (int j = 0; j < n; ++j) b->group_lattices.push_back(kv.second[k + j]);
+      k += n;
     }
   }
   std::vector<int> order;
