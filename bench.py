@@ -543,15 +543,11 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
             "gain_vs_oracle_1core": value / cpu}
 
 
-def measure_quad(dev, sincos, sweeps=200):
-    """Four replicas per site at L = 4096 (betas 1.00, 1.06, 1.12, 1.18): updates/s
-    over all replicas, against the single-lattice fused kernel of the main line."""
+def _time_quad(dev, L, sincos, algorithm, sweeps, flush):
     import torch
     from paper_0811_2111_gb300.lattice import Quad
 
-    L = 4096
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=sincos, device=dev) as q:
+    with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=sincos, algorithm=algorithm, device=dev) as q:
         q.sweep(10)
         torch.cuda.synchronize(dev)
         flush.fill_(1.0)
@@ -563,12 +559,27 @@ def measure_quad(dev, sincos, sweeps=200):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         acc = [float(q.observables(r, 10)["accepted"].mean()) / (L * L) for r in range(4)]
-    value = 4 * L * L * sweeps / (ms * 1e-3)
+        algo = q.algorithm
+    return 4 * L * L * sweeps / (ms * 1e-3), ms / sweeps, acc, algo
+
+
+def measure_quad(dev, sincos, sweeps=200):
+    """Four replicas per site at L = 4096 (betas 1.00, 1.06, 1.12, 1.18): updates/s
+    over all replicas with the one-launch sweep, the two-pass kernels beside it."""
+    import torch
+
+    L = 4096
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    value, ms, acc, algo = _time_quad(dev, L, sincos, "auto", sweeps, flush)
+    value2, ms2, _, _ = _time_quad(dev, L, sincos, "two_pass", sweeps, flush)
+    fused = algo == "fused"
+    bpu = 8.0 if fused else 12.0
     return {"workload": "xy_quad_L4096_4replicas_beta1.00-1.18", "value": value, "unit": UNIT,
-            "ms_per_sweep": ms / sweeps, "acceptance": acc,
-            "bytes_per_update": 12.0,
-            "hbm_achieved_gbs": 12.0 * value / 1e9,
-            "launches_per_sweep": 2}
+            "algorithm": algo, "ms_per_sweep": ms, "acceptance": acc,
+            "bytes_per_update": bpu,
+            "hbm_achieved_gbs": bpu * value / 1e9,
+            "launches_per_sweep": 1 if fused else 2,
+            "two_pass": {"value": value2, "ms_per_sweep": ms2, "bytes_per_update": 12.0}}
 
 
 def measure_precision(dev, sweeps=200):
@@ -801,6 +812,7 @@ def run_quad_line(args, dev, world, rank, sweeps_per_step=200):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=args.sincos, lattice_id=4 * rank,
               device=dev) as q:
+        algo = q.algorithm
         for _ in range(max(3, args.warmup)):
             q.sweep(sweeps_per_step)
         q.synchronize()
@@ -819,15 +831,21 @@ def run_quad_line(args, dev, world, rank, sweeps_per_step=200):
         clocks = sampler.stop()
     total_ms = max_over_ranks(sum(ms), world, dev)
     updates = 4 * L * L * sweeps_per_step * args.steps * world
-    line = {"metric": METRIC, "value": updates / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+    value = updates / (total_ms * 1e-3)
+    per_sweep = 1 if algo == "fused" else 2
+    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "xy_quad_L4096_4replicas_beta1.00-1.18",
                        "sweeps_per_step": sweeps_per_step, "sincos": args.sincos,
+                       "kernel": "fused single-pass" if algo == "fused" else "two-pass red/black",
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "gpu_launches": 2 * sweeps_per_step * args.steps + args.steps, "clocks": clocks}
+            "roofline": alu_roofline(value / world, args.sincos, clk),
+            "gpu_launches": per_sweep * sweeps_per_step * args.steps + args.steps,
+            "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

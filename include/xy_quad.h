@@ -35,16 +35,24 @@ typedef struct xy_quad xy_quad;
 /* Create four replicas of side p->L (even, 2 <= L <= XY_MAX_L) and start
  * them (hot: Philox domain 0 with each replica's lattice id; cold: zero).
  *   p           L, start, J, delta, seed, sincos_mode, reduce_mode and
- *               lattice_id are used as in xy.h; p->beta and p->algorithm are
- *               ignored (the kernel is the two-pass one).
+ *               lattice_id are used as in xy.h; p->beta is ignored.
+ *               p->algorithm: XY_ALGO_FUSED -- one launch per sweep (both
+ *               colours and the sums; needs L % 32 == 0; a second float4
+ *               buffer, the state ping-ponging between the two);
+ *               XY_ALGO_TWO_PASS -- one launch per colour, in place;
+ *               XY_ALGO_AUTO -- fused where L % 32 == 0, else two-pass.
+ *               Both give the same angles and accept counts bit for bit.
  *   beta        four inverse temperatures (>= 0, finite), one per replica.
  *   cuda_stream cudaStream_t or NULL (legacy default stream).
- * Errors: XY_EINVAL, XY_ENOMEM, XY_ECUDA (xy_quad_last_error(NULL)). */
+ * Device memory: 16 L^2 bytes per buffer (two for the fused sweep) plus
+ * 8 L^2 bytes of scratch and the records.
+ * Errors: XY_EINVAL (bad parameter; XY_ALGO_FUSED with L % 32 != 0),
+ * XY_ENOMEM, XY_ECUDA (xy_quad_last_error(NULL)). */
 xy_status xy_quad_create(const xy_params *p, const double beta[4], void *cuda_stream,
                          xy_quad **out);
 
-/* Enqueue n_sweeps >= 0 sweeps of all four replicas (two launches per sweep);
- * appends n_sweeps records per replica. */
+/* Enqueue n_sweeps >= 0 sweeps of all four replicas (one launch per sweep
+ * fused, two otherwise); appends n_sweeps records per replica. */
 xy_status xy_quad_sweep(xy_quad *q, int64_t n_sweeps);
 
 /* Observables of replica r's records [first, first + count), as xy_measure
@@ -59,6 +67,9 @@ xy_status xy_quad_get_state(xy_quad *q, int32_t replica, float *host_angles,
 
 /* Records per replica so far and the next sweep index. */
 xy_status xy_quad_info(const xy_quad *q, int64_t *n_records, uint64_t *next_sweep);
+
+/* The sweep algorithm the context runs: XY_ALGO_FUSED or XY_ALGO_TWO_PASS. */
+xy_status xy_quad_algorithm(const xy_quad *q, int32_t *algorithm);
 
 xy_status xy_quad_synchronize(xy_quad *q);
 xy_status xy_quad_destroy(xy_quad *q);            /* NULL-safe */

@@ -146,6 +146,7 @@ def lib():
         "xy_quad_measure": (st, [P, C.c_int32, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),
         "xy_quad_get_state": (st, [P, C.c_int32, P, C.POINTER(C.c_uint64)]),
         "xy_quad_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+        "xy_quad_algorithm": (st, [P, C.POINTER(C.c_int32)]),
         "xy_quad_synchronize": (st, [P]),
         "xy_quad_destroy": (st, [P]),
         "xy_quad_last_error": (C.c_char_p, [P]),
@@ -466,6 +467,12 @@ def xy_quad_info(q):
     t = C.c_uint64()
     quad_check(lib().xy_quad_info(q, C.byref(r), C.byref(t)), q)
     return r.value, t.value
+
+
+def xy_quad_algorithm(q):
+    a = C.c_int32(0)
+    quad_check(lib().xy_quad_algorithm(q, C.byref(a)), q)
+    return a.value
 
 
 def xy_quad_synchronize(q):

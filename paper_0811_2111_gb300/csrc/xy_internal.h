@@ -55,6 +55,30 @@ struct FusedArgs {
 // Whether the fused kernel handles side L (L a positive multiple of 128).
 bool fused_supported(int L);
 
+// One fused sweep of four replicas per site (float4 sites, read as floats
+// [colour][y][4k + r]); replica r has lattice id lattice_id0 + r and K[r].
+struct QuadFusedArgs {
+  const float* src;      // [2][L][W] float4: state before the sweep
+  float* dst;            // [2][L][W] float4: state after the sweep (distinct buffer)
+  int L;
+  int W;
+  float K[4];
+  float delta;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id0;
+  uint32_t sweep;
+  xy_record* rec;        // the sweep's four records, replica r at rec + r
+  double beta[4];
+};
+
+// Whether the fused four-replica kernel handles side L (a positive multiple of 32).
+bool quad_fused_supported(int L);
+
+// One fused four-replica sweep; cudaErrorInvalidValue if !quad_fused_supported(a.L)
+// or src == dst.
+cudaError_t launch_quad_fused(int sincos_mode, int reduce_mode, const QuadFusedArgs& a,
+                              cudaStream_t stream);
+
 // One fused sweep; cudaErrorInvalidValue if !fused_supported(a.L).
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream);

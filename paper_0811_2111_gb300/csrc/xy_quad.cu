@@ -1,6 +1,7 @@
 // xy_quad.cu -- four replicas per site (the RGBA packing of Sec. 3.2): the
-// two-pass checkerboard half-sweep over float4 sites, and the C ABI of
-// include/xy_quad.h around it.
+// two-pass checkerboard half-sweep over float4 sites (any even L), and the C
+// ABI of include/xy_quad.h around it and around the one-launch sweep of
+// xy_quad_fused.cu (L % 32 == 0).
 //
 // Layout: [colour][y][k] of float4, component r = replica r.  A half-sweep of
 // colour c stages the other colour's tile plus a one-site halo as unit vectors
@@ -239,7 +240,10 @@ struct xy_quad {
   xy_params p;
   double beta[kR];
   cudaStream_t stream;
+  bool fused;              // one-launch sweeps, state ping-ponged between the two buffers
+  int cur;                 // which buffer holds the state (0: d_theta, 1: d_theta2)
   float4* d_theta;         // [2][L][L/2] float4
+  float4* d_theta2;        // the fused sweep's second buffer (NULL for two-pass)
   float* d_scratch;        // L*L floats: one replica, split then natural order
   float* d_nat;
   xy_record* d_rec;        // [sweep][replica]
@@ -294,8 +298,11 @@ xy_status check(const xy_quad* q) {
   return XY_OK;
 }
 
+float4* current(const xy_quad* q) { return q->cur ? q->d_theta2 : q->d_theta; }
+
 void release(xy_quad* q) {
   if (q->d_theta) cudaFree(q->d_theta);
+  if (q->d_theta2) cudaFree(q->d_theta2);
   if (q->d_scratch) cudaFree(q->d_scratch);
   if (q->d_nat) cudaFree(q->d_nat);
   if (q->d_rec) cudaFree(q->d_rec);
@@ -353,6 +360,15 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
     tmsg("bad J, delta, start, sincos_mode or reduce_mode");
     return XY_EINVAL;
   }
+  if (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
+      p->algorithm != XY_ALGO_TWO_PASS) {
+    tmsg("algorithm must be XY_ALGO_AUTO, XY_ALGO_FUSED or XY_ALGO_TWO_PASS; got %d", p->algorithm);
+    return XY_EINVAL;
+  }
+  if (p->algorithm == XY_ALGO_FUSED && !xyk::quad_fused_supported(p->L)) {
+    tmsg("XY_ALGO_FUSED needs L %% 32 == 0; got L = %d", p->L);
+    return XY_EINVAL;
+  }
   xy_quad* q = new (std::nothrow) xy_quad();
   if (!q) {
     tmsg("host allocation");
@@ -361,9 +377,12 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
   q->p = *p;
   for (int j = 0; j < kR; ++j) q->beta[j] = beta[j];
   q->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  q->fused = p->algorithm != XY_ALGO_TWO_PASS && xyk::quad_fused_supported(p->L);
+  q->cur = 0;
   const size_t N = (size_t)p->L * (size_t)p->L;
   const char* step = "angle buffer";
   cudaError_t e = cudaMalloc(&q->d_theta, N * sizeof(float4));
+  if (e == cudaSuccess && q->fused) e = cudaMalloc(&q->d_theta2, N * sizeof(float4));
   if (e == cudaSuccess) {
     step = "scratch buffers";
     e = cudaMalloc(&q->d_scratch, N * sizeof(float));
@@ -408,8 +427,32 @@ xy_status xy_quad_sweep(xy_quad* q, int64_t n) {
   Q_CUDA(q, cudaMemsetAsync(q->d_rec + q->rec_count * kR, 0, (size_t)n * kR * sizeof(xy_record),
                             q->stream),
          "xy_quad_sweep: record clear");
+  if (q->fused) {
+    xyk::QuadFusedArgs f;
+    f.L = q->p.L;
+    f.W = q->p.L / 2;
+    for (int j = 0; j < kR; ++j) {
+      f.K[j] = (float)(q->beta[j] * q->p.J);
+      f.beta[j] = q->beta[j];
+    }
+    f.delta = (float)q->p.delta;
+    f.rk = xyd::make_round_keys(q->p.seed);
+    f.lattice_id0 = q->p.lattice_id;
+    for (int64_t i = 0; i < n; ++i) {
+      f.src = reinterpret_cast<const float*>(current(q));
+      f.dst = reinterpret_cast<float*>(q->cur ? q->d_theta : q->d_theta2);
+      f.sweep = (uint32_t)(q->next_sweep + (uint64_t)i);
+      f.rec = q->d_rec + (q->rec_count + i) * kR;
+      Q_CUDA(q, xyk::launch_quad_fused(q->p.sincos_mode, q->p.reduce_mode, f, q->stream),
+             "xy_quad_sweep: fused sweep");
+      q->cur ^= 1;
+    }
+    q->next_sweep += (uint64_t)n;
+    q->rec_count += n;
+    return XY_OK;
+  }
   QuadArgs a;
-  a.theta = q->d_theta;
+  a.theta = current(q);
   a.L = q->p.L;
   a.W = q->p.L / 2;
   for (int j = 0; j < kR; ++j) {
@@ -476,7 +519,7 @@ xy_status xy_quad_get_state(xy_quad* q, int32_t replica, float* host, uint64_t* 
   if (replica < 0 || replica >= kR) return fail(q, XY_EINVAL, "xy_quad_get_state: replica out of range");
   if (!host) return fail(q, XY_EINVAL, "xy_quad_get_state: NULL output");
   const int64_t N = (int64_t)q->p.L * q->p.L;
-  k_quad_extract<<<grid_for(N, 256), 256, 0, q->stream>>>(q->d_theta, q->d_scratch, replica, N);
+  k_quad_extract<<<grid_for(N, 256), 256, 0, q->stream>>>(current(q), q->d_scratch, replica, N);
   Q_CUDA(q, cudaGetLastError(), "xy_quad_get_state: extract");
   Q_CUDA(q, xyk::launch_split_to_natural(q->d_scratch, q->d_nat, q->p.L, q->stream),
          "xy_quad_get_state: layout");
@@ -493,6 +536,17 @@ xy_status xy_quad_info(const xy_quad* q, int64_t* n_records, uint64_t* next_swee
   if (st != XY_OK) return st;
   if (n_records) *n_records = q->rec_count;
   if (next_sweep) *next_sweep = q->next_sweep;
+  return XY_OK;
+}
+
+xy_status xy_quad_algorithm(const xy_quad* q, int32_t* algorithm) {
+  xy_status st = check(q);
+  if (st != XY_OK) return st;
+  if (!algorithm) {
+    tmsg("xy_quad_algorithm: NULL output");
+    return XY_EINVAL;
+  }
+  *algorithm = q->fused ? XY_ALGO_FUSED : XY_ALGO_TWO_PASS;
   return XY_OK;
 }
 

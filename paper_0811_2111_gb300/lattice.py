@@ -262,7 +262,7 @@ class Quad:
     packing of Sec. 3.2): replica r has lattice id lattice_id + r and beta betas[r]."""
 
     def __init__(self, L, betas, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
-                 reduce="fp64", lattice_id=0, device=None, stream=None):
+                 reduce="fp64", lattice_id=0, algorithm="auto", device=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -282,10 +282,17 @@ class Quad:
                          "libm": X.XY_SINCOS_LIBM}[sincos]
         p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
-        p.algorithm = X.XY_ALGO_AUTO
+        p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
+                       "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
         self.params = p
         with torch.cuda.device(self.device):
             self.q = X.xy_quad_create(p, betas, C.c_void_p(self.stream.cuda_stream))
+
+    @property
+    def algorithm(self):
+        """"fused" (one launch per sweep) or "two_pass"."""
+        a = X.xy_quad_algorithm(self.q)
+        return "fused" if a == X.XY_ALGO_FUSED else "two_pass"
 
     def sweep(self, n=1):
         X.xy_quad_sweep(self.q, n)

@@ -156,9 +156,11 @@ def test_quad_create_rejects_bad_parameters(lib):
     q = C.c_void_p()
     good = (C.c_double * 4)(1.0, 1.0, 1.0, 1.0)
     for kw in (dict(L=3), dict(L=0), dict(delta=0.0), dict(start=5), dict(sincos_mode=7),
-               dict(reduce_mode=3), dict(J=float("nan"))):
+               dict(reduce_mode=3), dict(J=float("nan")), dict(algorithm=9),
+               dict(L=34, algorithm=X.XY_ALGO_FUSED)):
         assert lib.xy_quad_create(C.byref(_params(**kw)), good, None, C.byref(q)) == X.XY_EINVAL
         assert q.value is None
+    assert "L % 32" in X.xy_quad_last_error(None)   # the last case: fused needs L % 32 == 0
     bad = (C.c_double * 4)(1.0, float("nan"), 1.0, 1.0)
     assert lib.xy_quad_create(C.byref(_params()), bad, None, C.byref(q)) == X.XY_EINVAL
     assert "beta[1]" in X.xy_quad_last_error(None)
@@ -166,6 +168,8 @@ def test_quad_create_rejects_bad_parameters(lib):
     assert lib.xy_quad_sweep(None, 1) == X.XY_EINVAL
     assert lib.xy_quad_destroy(None) == X.XY_OK
     assert lib.xy_quad_sweep(C.c_void_p(0x3000), 1) == X.XY_ESTATE
+    a = C.c_int32(0)
+    assert lib.xy_quad_algorithm(None, C.byref(a)) == X.XY_EINVAL
 
 
 def test_sincos_polynomial_constants_are_the_fit():

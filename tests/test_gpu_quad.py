@@ -26,12 +26,14 @@ from paper_0811_2111_gb300.lattice import Lattice, Quad  # noqa: E402
 BETAS = [0.7, 1.0, 1.12, 1.4]
 
 
-@pytest.mark.parametrize("L", [2, 6, 34, 64, 130, 256])
+@pytest.mark.parametrize("L", [2, 6, 32, 34, 64, 96, 130, 256])
 @pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "fp64"),
-                                           ("accurate", "compensated")])
+                                           ("accurate", "compensated"), ("libm", "fp64")])
 def test_replicas_equal_single_lattices(L, sincos, reduce):
+    """AUTO: the fused sweep for L % 32 == 0 (32, 64, 96, 256), two-pass otherwise."""
     sweeps = 7
     with Quad(L, BETAS, 19, sincos=sincos, reduce=reduce, lattice_id=40) as q:
+        assert q.algorithm == ("fused" if L % 32 == 0 else "two_pass")
         q.sweep(sweeps)
         states = [q.state(r)[0] for r in range(4)]
         obs = [q.observables(r) for r in range(4)]
@@ -85,3 +87,48 @@ def test_error_paths():
     with Quad(16, BETAS, 1) as q:
         with pytest.raises(X.XYError):
             q.sweep(-1)
+
+
+@pytest.mark.parametrize("L", [32, 128, 512])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated")])
+def test_fused_equals_two_pass(L, sincos, reduce):
+    """The one-launch sweep (tiles of 32 rows x 16 sites, the red ring recomputed
+    at the tile edges, several tiles per row and column from L = 64 on) and the
+    two-pass kernels: the same angles and accept counts, sums to rounding."""
+    sweeps = 5
+    out = {}
+    for algo in ("fused", "two_pass"):
+        with Quad(L, BETAS, 23, sincos=sincos, reduce=reduce, lattice_id=5, algorithm=algo) as q:
+            assert q.algorithm == algo
+            q.sweep(sweeps)
+            out[algo] = ([q.state(r)[0] for r in range(4)], [q.observables(r) for r in range(4)],
+                         q.state(0)[1])
+    (sf, of, nf), (st, ot, nt) = out["fused"], out["two_pass"]
+    assert nf == nt == sweeps
+    tol = record_tolerance(L * L, fast=(sincos == "fast"))
+    for r in range(4):
+        assert np.array_equal(sf[r], st[r]), r
+        assert np.array_equal(of[r]["accepted"], ot[r]["accepted"]), r
+        assert np.all(of[r]["beta"] == BETAS[r])
+        for k in ("C", "Ix", "Iy", "Mx", "My"):
+            assert np.max(np.abs(of[r][k] - ot[r][k])) <= tol, (r, k)
+
+
+def test_fused_sweeps_in_pieces_equal_one_run():
+    """The ping-pong buffer parity carries over between calls: 3 + 1 + 4 sweeps
+    give the state of 8 sweeps in one call."""
+    with Quad(64, BETAS, 29, algorithm="fused") as a, Quad(64, BETAS, 29, algorithm="fused") as b:
+        for n in (3, 1, 4):
+            a.sweep(n)
+        b.sweep(8)
+        for r in range(4):
+            sa, na = a.state(r)
+            sb, nb = b.state(r)
+            assert na == nb == 8 and np.array_equal(sa, sb)
+
+
+def test_fused_algorithm_needs_l_multiple_of_32():
+    with pytest.raises(X.XYError):
+        Quad(34, BETAS, 1, algorithm="fused")
+    with Quad(34, BETAS, 1) as q:
+        assert q.algorithm == "two_pass"
