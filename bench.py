@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sincos", choices=["accurate", "fast", "libm"], default="accurate")
-    ap.add_argument("--algorithm", choices=["auto", "fused", "two_pass"], default="auto")
+    ap.add_argument("--algorithm", choices=["auto", "fused", "two_pass", "persistent"],
+                    default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,6 +71,9 @@ def parse():
                     help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
                     help="override sweeps per step (profiling runs only)")
+    ap.add_argument("--side", type=int, default=None,
+                    help="override the lattice side L of the large workload (e.g. the "
+                         "paper's Table 1 sides; profiling and scaling runs, not the headline)")
     return ap.parse_args()
 
 
@@ -79,6 +83,9 @@ def workload(args):
     w = {"large": WL.LARGE, "huge": WL.HUGE, "batch": WL.LARGE}[args.workload]
     if args.sweeps is not None:
         w = dataclasses.replace(w, sweeps=args.sweeps)
+    if args.side is not None:
+        w = dataclasses.replace(w, L=args.side,
+                                name=f"xy_L{args.side}_beta{w.beta}_seed{w.seed}_{w.sweeps}sweeps")
     return w
 
 
@@ -641,7 +648,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     lat = Lattice(w.L, w.beta, w.seed, device=dev, stream=stream, lattice_id=rank,
                   sincos=args.sincos, algorithm=args.algorithm)
-    fused = args.algorithm == "fused" or (args.algorithm == "auto" and w.L % 128 == 0)
+    persistent = lat.algorithm == "persistent"        # what AUTO resolved to
+    fused = lat.algorithm in ("fused", "persistent")
     lat.reserve(w.sweeps)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -709,11 +717,13 @@ def run_ours(args):
     kern = max((0, 1), key=lambda k: kt[k][0])
     kms, klaunch = kt[kern]
     avg_s = kms * 1e-3 / max(klaunch, 1)
-    updates_per_launch = w.sites if fused else w.sites // 2
+    sweeps_per_launch = w.sweeps if persistent else 1
+    updates_per_launch = (w.sites if fused else w.sites // 2) * sweeps_per_launch
     alg_bytes = 8.0 * updates_per_launch     # 8 B per update: one read + one write of the angle
     hbm_peak, peak_kind = measured_peaks()
     hbm_achieved = alg_bytes / avg_s / 1e9
-    names = (["sweep_fused"] if fused else ["red_half_sweep", "black_half_sweep_measure"])
+    names = (["sweep_fused_persist"] if persistent else
+             ["sweep_fused"] if fused else ["red_half_sweep", "black_half_sweep_measure"])
     # issue-slot roofline: 152 SMs x 4 schedulers x 32 lanes per clock at the
     # median SM clock sampled during the timed region (max clock if unsampled)
     clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
@@ -728,8 +738,11 @@ def run_ours(args):
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes},
-                "kernel_timing": f"CUDA events around the launches of every {TIMING_EVERY}th "
-                                 "sweep inside the timed region",
+                "kernel_timing": ("CUDA events around every launch (all sweeps of a step) "
+                                  "inside the timed region" if persistent else
+                                  f"CUDA events around the launches of every {TIMING_EVERY}th "
+                                  "sweep inside the timed region"),
+                "sweeps_per_launch": sweeps_per_launch,
                 "kernel_avg_ms": {names[k]: kt[k][0] / max(kt[k][1], 1)
                                   for k in range(len(names))}}
     cpu = None
@@ -740,7 +753,7 @@ def run_ours(args):
                "sample": f"{n} sweeps of L={w.L} from the seed-{w.seed} hot start "
                          f"({dt:.1f} s), OpenMP over the sites of one colour"}
 
-    launches = args.steps * (1 + (1 if fused else 2) * w.sweeps)
+    launches = args.steps * (2 if persistent else 1 + (1 if fused else 2) * w.sweeps)
     extra = None
     if not args.no_extra and world == 1:
         extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
@@ -761,7 +774,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
                    "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "fp64",
-                   "kernel": "fused single-pass" if fused else "two-pass red/black",
+                   "kernel": ("persistent fused (one cooperative launch per step)" if persistent
+                              else "fused single-pass" if fused else "two-pass red/black"),
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

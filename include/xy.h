@@ -63,13 +63,23 @@ enum { XY_START_HOT = 0, XY_START_COLD = 1 };
  *   XY_SINCOS_FAST      the SFU intrinsics __sincosf / __expf;
  *   XY_SINCOS_LIBM      CUDA's sincosf / expf. */
 enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
-/* Sweep kernel: AUTO picks FUSED when L is a multiple of 128, else TWO_PASS.
- *   XY_ALGO_FUSED     one launch per sweep (both colours + measure), the state
- *                     ping-pongs between the caller's buffer and a library
- *                     buffer of the same size (8 B moved per update);
- *   XY_ALGO_TWO_PASS  one launch per colour, in place (12 B per update).
- * Both make bit-identical decisions. */
-enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2 };
+/* Sweep kernel: AUTO picks PERSISTENT when L is a multiple of 128 up to 2048
+ * (falling back to one fused launch per sweep when the cooperative grid does
+ * not fit on the device), FUSED for larger multiples of 128, else TWO_PASS.
+ *   XY_ALGO_FUSED      one launch per sweep (both colours + measure), the state
+ *                      ping-pongs between the caller's buffer and a library
+ *                      buffer of the same size (8 B moved per update);
+ *   XY_ALGO_TWO_PASS   one launch per colour, in place (12 B per update);
+ *   XY_ALGO_PERSISTENT the fused sweep, all sweeps of one xy_sweep call in one
+ *                      cooperative launch: each tile of 32 x 128 sites starts
+ *                      sweep s once its eight neighbouring tiles have finished
+ *                      sweep s - 1 (per-tile counters in device memory, bounded
+ *                      waits; a wait that runs out is reported as XY_ETIMEOUT
+ *                      at the next synchronizing call).  Needs L % 128 == 0
+ *                      and every CTA of the grid resident (the launch fails
+ *                      with XY_ECUDA otherwise).
+ * All make bit-identical decisions. */
+enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2, XY_ALGO_PERSISTENT = 3 };
 enum { XY_REDUCE_FP64 = 0, XY_REDUCE_COMPENSATED = 1 };
 
 /* Largest supported side (N = L^2 must fit the 32-bit site counter and the
@@ -86,7 +96,7 @@ typedef struct {
     int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM                 */
     int32_t reduce_mode;  /* XY_REDUCE_FP64 or XY_REDUCE_COMPENSATED            */
     uint32_t lattice_id;  /* third Philox counter word                          */
-    int32_t algorithm;    /* XY_ALGO_AUTO, _FUSED (needs L % 128 == 0), _TWO_PASS */
+    int32_t algorithm;    /* XY_ALGO_AUTO, _FUSED or _PERSISTENT (need L % 128 == 0), _TWO_PASS */
 } xy_params;
 
 /* Per-sweep record as stored on the device (64 bytes).  The five sums are
@@ -153,6 +163,10 @@ xy_status xy_records_device(xy_ctx *ctx, const xy_record **d_records, int64_t *c
 
 /* Number of records so far and the next sweep index. */
 xy_status xy_info(const xy_ctx *ctx, int64_t *n_records, uint64_t *next_sweep);
+
+/* The sweep algorithm the context runs (what XY_ALGO_AUTO resolved to):
+ * XY_ALGO_FUSED, XY_ALGO_TWO_PASS or XY_ALGO_PERSISTENT. */
+xy_status xy_algorithm(const xy_ctx *ctx, int32_t *algorithm);
 
 /* Copy the angles (natural order, L*L floats) to host memory and report the
  * next sweep index.  Synchronizes. */

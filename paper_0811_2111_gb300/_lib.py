@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "X
                 5: "XY_ESTATE", 6: "XY_ENUMERIC"}
 XY_START_HOT, XY_START_COLD = 0, 1
 XY_SINCOS_ACCURATE, XY_SINCOS_FAST, XY_SINCOS_LIBM = 0, 1, 2
-XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS = 0, 1, 2
+XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS, XY_ALGO_PERSISTENT = 0, 1, 2, 3
 XY_REDUCE_FP64, XY_REDUCE_COMPENSATED = 0, 1
 XY_FX_SHIFT = 30
 XY_MAX_L = 32768
@@ -96,6 +96,7 @@ def lib():
         "xy_measure": (st, [P, C.c_int64, C.c_int64, C.POINTER(xy_obs)]),
         "xy_records_device": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "xy_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
+        "xy_algorithm": (st, [P, C.POINTER(C.c_int32)]),
         "xy_get_state": (st, [P, P, C.POINTER(C.c_uint64)]),
         "xy_set_state": (st, [P, P, C.c_uint64]),
         "xy_set_beta": (st, [P, C.c_double]),
@@ -215,6 +216,12 @@ def xy_info(ctx):
     s = C.c_uint64()
     check(lib().xy_info(ctx, C.byref(n), C.byref(s)), ctx)
     return n.value, s.value
+
+
+def xy_algorithm(ctx):
+    a = C.c_int32(0)
+    check(lib().xy_algorithm(ctx, C.byref(a)), ctx)
+    return a.value
 
 
 def xy_get_state(ctx, host_ptr):

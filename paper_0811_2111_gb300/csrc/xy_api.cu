@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <unordered_set>
@@ -51,6 +52,11 @@ void set_thread_msg(const char* fmt, ...) {
 
 }  // namespace
 
+// XY_ALGO_AUTO takes the persistent sweep up to this side: there a sweep is a
+// few waves of tiles and one launch per sweep pays its fill and drain every
+// sweep; beyond it the per-sweep launch is as fast or faster.
+constexpr int kAutoPersistentMaxL = 2048;
+
 struct xy_ctx {
   uint32_t magic;
   xy_params p;
@@ -60,6 +66,10 @@ struct xy_ctx {
   bool owns_theta;
   float* d_pong;           // second buffer of the fused kernel (library-owned)
   bool fused;              // sweeps use the fused kernel
+  bool persistent;         // ... all sweeps of an xy_sweep call in one cooperative launch
+  bool auto_persistent;    // chosen by XY_ALGO_AUTO: per-sweep launches if it does not fit
+  unsigned int* d_tiles;   // the persistent launch's per-tile sweep counters
+  unsigned int* d_wait;    // set by a persistent launch whose bounded wait ran out
   xy_record* d_rec;        // records [0, rec_cap)
   int64_t rec_cap;
   int64_t rec_count;       // records enqueued so far
@@ -153,11 +163,12 @@ xy_status validate(const xy_params* p) {
     return XY_EINVAL;
   }
   if (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
-      p->algorithm != XY_ALGO_TWO_PASS) {
+      p->algorithm != XY_ALGO_TWO_PASS && p->algorithm != XY_ALGO_PERSISTENT) {
     set_thread_msg("bad algorithm");
     return XY_EINVAL;
   }
-  if (p->algorithm == XY_ALGO_FUSED && !xyk::fused_supported(p->L)) {
+  if ((p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_PERSISTENT) &&
+      !xyk::fused_supported(p->L)) {
     set_thread_msg("the fused kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
   }
@@ -223,6 +234,29 @@ cudaError_t timed_fused(xy_ctx* c, const xyk::FusedArgs& a) {
   return e;
 }
 
+// After a synchronize: whether a persistent launch's bounded wait ran out.
+xy_status check_waits(xy_ctx* c, const char* where) {
+  if (!c->persistent || !c->d_wait) return XY_OK;
+  unsigned int w = 0;
+  XY_CUDA(c, cudaMemcpyAsync(&w, c->d_wait, sizeof(w), cudaMemcpyDeviceToHost, c->stream), where);
+  XY_CUDA(c, cudaStreamSynchronize(c->stream), where);
+  if (w) return fail(c, XY_ETIMEOUT, "%s: a persistent sweep's wait for a neighbouring tile ran out",
+                     where);
+  return XY_OK;
+}
+
+cudaError_t timed_persistent(xy_ctx* c, const xyk::FusedPersistArgs& a) {
+  if (c->timing_every <= 0)
+    return xyk::launch_fused_persistent(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  cudaEvent_t e0, e1;
+  cudaError_t e = next_events(c, 0, &e0, &e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess)
+    e = xyk::launch_fused_persistent(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  return e;
+}
+
 void release(xy_ctx* c) {
   for (int k = 0; k < 2; ++k) {
     for (cudaEvent_t e : c->ev[k]) cudaEventDestroy(e);
@@ -234,6 +268,10 @@ void release(xy_ctx* c) {
   if (c->d_pong) cudaFree(c->d_pong);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_flag) cudaFree(c->d_flag);
+  if (c->d_tiles) cudaFree(c->d_tiles);
+  if (c->d_wait) cudaFree(c->d_wait);
+  c->d_tiles = nullptr;
+  c->d_wait = nullptr;
   c->d_theta = nullptr;
   c->d_rec = nullptr;
   c->d_pong = nullptr;
@@ -286,9 +324,18 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
     }
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(unsigned int));
-  c->fused = p->algorithm == XY_ALGO_FUSED ||
+  c->persistent = p->algorithm == XY_ALGO_PERSISTENT ||
+                  (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L) &&
+                   p->L <= kAutoPersistentMaxL);
+  c->auto_persistent = c->persistent && p->algorithm == XY_ALGO_AUTO;
+  c->fused = p->algorithm == XY_ALGO_FUSED || c->persistent ||
              (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
   if (e == cudaSuccess && c->fused) e = cudaMalloc(&c->d_pong, N * sizeof(float));
+  if (e == cudaSuccess && c->persistent) {
+    e = cudaMalloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_wait, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wait, 0, sizeof(unsigned int), c->stream);
+  }
   if (e != cudaSuccess) {
     st = (e == cudaErrorMemoryAllocation) ? XY_ENOMEM : XY_ECUDA;
     set_thread_msg("xy_create: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -343,6 +390,8 @@ xy_status xy_kernel_time(xy_ctx* c, int kernel, double* total_ms, int64_t* launc
   if (kernel < 0 || kernel > 1 || !total_ms || !launches)
     return fail(c, XY_EINVAL, "xy_kernel_time: bad arguments");
   XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_kernel_time: stream");
+  st = check_waits(c, "xy_kernel_time");
+  if (st != XY_OK) return st;
   double sum = 0.0;
   for (size_t i = 0; i + 1 < c->ev_used[kernel]; i += 2) {
     float ms = 0.f;
@@ -373,7 +422,61 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
   st = grow_records(c, c->rec_count + n);
   if (st != XY_OK) return st;
   const xyd::RoundKeys rk = xyd::make_round_keys(c->p.seed);
-  if (c->fused) {
+  if (c->persistent) {
+    xyk::FusedPersistArgs a;
+    a.buf[0] = c->d_theta;
+    a.buf[1] = c->d_pong;
+    a.L = c->p.L;
+    a.W = c->p.L / 2;
+    a.K = (float)(c->p.beta * c->p.J);
+    a.delta = (float)c->p.delta;
+    a.rk = rk;
+    a.lattice_id = c->p.lattice_id;
+    a.beta = c->p.beta;
+    a.flags = c->d_tiles;
+    a.counter = c->d_tiles + xyk::fused_tiles(c->p.L);
+    a.error = c->d_wait;
+    // one launch per at most fused_persistent_max_sweeps sweeps (the kernel's
+    // work items are counted in 32 bits)
+    const int64_t chunk = xyk::fused_persistent_max_sweeps(c->p.L);
+    for (int64_t done = 0; done < n;) {
+      const int64_t m = std::min<int64_t>(n - done, chunk);
+      a.sweep0 = (uint32_t)(c->next_sweep + (uint64_t)done);
+      a.n_sweeps = (int)m;
+      a.rec = c->d_rec + c->rec_count + done;
+      cudaError_t e = timed_persistent(c, a);
+      if (e == cudaErrorCooperativeLaunchTooLarge && c->auto_persistent) {
+        // the grid does not fit beside other work on the device: the same
+        // sweeps as one fused launch each (bit-identical)
+        (void)cudaGetLastError();
+        xyk::FusedArgs f;
+        f.L = a.L;
+        f.W = a.W;
+        f.K = a.K;
+        f.delta = a.delta;
+        f.rk = a.rk;
+        f.lattice_id = a.lattice_id;
+        f.beta = a.beta;
+        for (int64_t i = 0; i < m; ++i) {
+          f.src = a.buf[i & 1];
+          f.dst = a.buf[(i + 1) & 1];
+          f.sweep = a.sweep0 + (uint32_t)i;
+          f.rec = a.rec + i;
+          e = timed_fused(c, f);
+          if (e != cudaSuccess) break;
+        }
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: persistent launch");
+      if (m & 1) std::swap(a.buf[0], a.buf[1]);
+      done += m;
+    }
+    if (a.buf[0] != c->d_theta) {
+      const size_t N = (size_t)c->p.L * (size_t)c->p.L;
+      XY_CUDA(c, cudaMemcpyAsync(c->d_theta, a.buf[0], N * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, c->stream),
+              "xy_sweep: copy back");
+    }
+  } else if (c->fused) {
     xyk::FusedArgs a;
     a.L = c->p.L;
     a.W = c->p.L / 2;
@@ -432,6 +535,8 @@ xy_status xy_measure(xy_ctx* c, int64_t first, int64_t count, xy_obs* out) {
                 (long long)first, (long long)(first + count), (long long)c->rec_count);
   if (count > 0 && !out) return fail(c, XY_EINVAL, "xy_measure: NULL output");
   XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_measure: stream");
+  st = check_waits(c, "xy_measure");
+  if (st != XY_OK) return st;
   if (count == 0) return XY_OK;
   xy_record* h = new (std::nothrow) xy_record[count];
   if (!h) return fail(c, XY_ENOMEM, "xy_measure: host allocation");
@@ -481,6 +586,17 @@ xy_status xy_info(const xy_ctx* c, int64_t* n_records, uint64_t* next_sweep) {
   return XY_OK;
 }
 
+xy_status xy_algorithm(const xy_ctx* c, int32_t* algorithm) {
+  xy_status st = check_ctx(c);
+  if (st != XY_OK) return st;
+  if (!algorithm) {
+    set_thread_msg("xy_algorithm: NULL output");
+    return XY_EINVAL;
+  }
+  *algorithm = c->persistent ? XY_ALGO_PERSISTENT : (c->fused ? XY_ALGO_FUSED : XY_ALGO_TWO_PASS);
+  return XY_OK;
+}
+
 xy_status xy_get_state(xy_ctx* c, float* host, uint64_t* next_sweep) {
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
@@ -493,6 +609,8 @@ xy_status xy_get_state(xy_ctx* c, float* host, uint64_t* next_sweep) {
                              c->stream),
           "xy_get_state: copy");
   XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_get_state: stream");
+  st = check_waits(c, "xy_get_state");
+  if (st != XY_OK) return st;
   if (next_sweep) *next_sweep = c->next_sweep;
   return XY_OK;
 }
@@ -544,6 +662,8 @@ xy_status xy_synchronize(xy_ctx* c) {
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
   XY_CUDA(c, cudaStreamSynchronize(c->stream), "xy_synchronize");
+  st = check_waits(c, "xy_synchronize");
+  if (st != XY_OK) return st;
   return XY_OK;
 }
 

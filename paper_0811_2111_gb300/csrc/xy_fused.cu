@@ -118,12 +118,24 @@ __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c
   cs[0][r][c] = make_float2(res.c, res.s);
 }
 
-// One sweep of the tile (blockIdx.x, blockIdx.y) of one lattice.  Args is
-// FusedArgs (the single-lattice kernel passes its parameter, so every field is
-// read from parameter space where it is used) or FusedCore (built per CTA by
-// the batched kernel); both have the fields used here.
-template <int MODE, int RED, class Args>
-__device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk) {
+// One sweep of the tile (bx, by) of one lattice.  Args is FusedArgs (the
+// single-lattice kernel passes its parameter, so every field is read from
+// parameter space where it is used) or FusedCore (built per CTA by the batched
+// and persistent kernels); both have the fields used here.  COHERENT: the
+// source was written earlier in the same launch by other CTAs (persistent
+// kernel), so it is read through L2 (ld.global.cg) rather than the
+// non-coherent path.  `mid` runs in every thread before the barrier between
+// the red and the black half, `end` after the tile's last store to dst and
+// before the CTA's closing barrier.
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+template <int MODE, int RED, bool COHERENT = false, class Args, class MidHook = NoHook,
+          class EndHook = NoHook>
+__device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk, int bx,
+                                                 int by, const MidHook& mid = MidHook(),
+                                                 const EndHook& end = EndHook()) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
   CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
@@ -131,8 +143,8 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kThBytes + kCsBytes + kPartBytes);
 
   const int L = a.L, W = a.W;
-  const int k0 = blockIdx.x * kTileK;
-  const int y0 = blockIdx.y * kTileRows;
+  const int k0 = bx * kTileK;
+  const int y0 = by * kTileRows;
   const size_t plane = (size_t)L * (size_t)W;
 
   // ---- stage both planes (angle + unit vector) ----
@@ -155,7 +167,8 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
         const int p = rr < kSRows ? 1 : 0;
         const int r = rr < kSRows ? rr : rr - kSRows + 1;
         const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * g;
-        v[i] = __ldg(reinterpret_cast<const float4*>(a.src + row));
+        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(a.src + row))
+                        : __ldg(reinterpret_cast<const float4*>(a.src + row));
       }
     }
 #pragma unroll
@@ -185,7 +198,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
       const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
       const int col = side ? kTileK + 4 : 3;
-      const float v1 = __ldg(a.src + row + kk);
+      const float v1 = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
       float sv, cv;
       xyd::unit_vector<MODE>(v1, &sv, &cv);
       th[p][r][col] = v1;
@@ -248,6 +261,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a, rk);
     }
   }
+  mid();
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
@@ -292,13 +306,14 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     }
   }
 
+  end();
   xyd::commit_block<kWarps, RED, true>(acc, cmp, n_acc, part, cnt, a.rec, a.beta,
-                                       blockIdx.x == 0 && blockIdx.y == 0);
+                                       bx == 0 && by == 0);
 }
 
 template <int MODE, int RED>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
-  fused_sweep_body<MODE, RED>(a, a.rk);
+  fused_sweep_body<MODE, RED>(a, a.rk, blockIdx.x, blockIdx.y);
 }
 
 // Many lattices of one side in one launch (blockIdx.z = lattice of the group),
@@ -315,7 +330,134 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_batch(FusedBatchArg
   const FusedCore c{base + b.offset[i], out + b.offset[i], b.L, b.L / 2, (float)(beta * b.J),
                     b.delta, b.lattice_id0 + (uint32_t)i, sweep,
                     b.records + (size_t)i * b.rec_stride + (sweep - b.rec_sweep0), beta};
-  fused_sweep_body<MODE, RED>(c, b.rk);
+  fused_sweep_body<MODE, RED>(c, b.rk, blockIdx.x, blockIdx.y);
+}
+
+// Polls of a neighbour's flag before a wait gives up (with a short sleep
+// between polls: about a second in all).
+constexpr long long kPersistSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void store_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// All n sweeps of one lattice in one cooperative launch (every CTA resident).
+// The work items (sweep s, tile position k) are handed out in increasing order
+// by one atomic counter, s-major, with the tile rows of a sweep visited folded
+// (0, T-1, 1, T-2, ...) so that a tile's periodic neighbours are never more
+// than two tile rows away in that order.  A tile's sweep s reads its own and
+// its eight neighbours' state after sweep s - 1 (the halo of two rows and one
+// column reaches into all eight) and overwrites the buffer they read during
+// sweep s - 1, so it starts once those nine tiles (its own sweep s - 1 may have
+// run on another CTA) have published flags[t] >= s; it publishes s + 1 after
+// its stores.  An item waits only on
+// items handed out before it, and every CTA holds at most its current item
+// and the next (fetched while the current one runs), so with every CTA
+// resident the waits always end; each is bounded anyway, and a wait that runs
+// out sets *error and ends the CTA (the CTAs that wait on it see *error and
+// end too).  Dynamic hand-out keeps the SMs evenly loaded as a launch per
+// sweep does, without the launch's fill and drain.  The arithmetic of a tile
+// is fused_sweep_body's, so the result is bit for bit that of n launches of
+// k_sweep_fused.
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersistArgs p) {
+  __shared__ int s_abort;
+  __shared__ int s_item[2];          // this tile's item and the next (alternating)
+  const int tiles_x = p.W / kTileK, tiles_y = p.L / kTileRows;
+  const int ntiles = tiles_x * tiles_y;
+  const int total = p.n_sweeps * ntiles;          // < 2^31 - 2^20 (the host splits longer runs)
+  FusedCore c;
+  c.L = p.L;
+  c.W = p.W;
+  c.K = p.K;
+  c.delta = p.delta;
+  c.lattice_id = p.lattice_id;
+  c.beta = p.beta;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_item[0] = (int)atomicAdd(p.counter, 1u);
+  }
+  __syncthreads();
+  int par = 0;
+  int item = s_item[0];
+  bool ready = false;                // this thread's counter of the item already seen set
+  while (item < total) {
+    const int s = item / ntiles;
+    const int k = item - s * ntiles;
+    const int prow = k / tiles_x;
+    const int bx = k - prow * tiles_x;
+    const int by = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+    if (s > 0 && threadIdx.x < 9 && !ready) {
+      // the eight neighbours and the tile itself (its sweep s - 1 may have run
+      // on another CTA)
+      const int d = threadIdx.x;
+      const int nx = wrap_once(bx + d % 3 - 1, tiles_x);
+      const int ny = wrap_once(by + d / 3 - 1, tiles_y);
+      const unsigned int* f = p.flags + (ny * tiles_x + nx);
+      long long it = 0;
+      while (load_acquire(f) < (unsigned int)s) {
+        // give up when the limit runs out, or early once another CTA has
+        // given up (so a failure does not cascade from wait to wait)
+        if (++it > kPersistSpinLimit ||
+            ((it & 255) == 0 && *reinterpret_cast<volatile unsigned int*>(p.error) != 0u)) {
+          atomicOr(p.error, 1u);
+          s_abort = 1;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __syncthreads();
+    if (s_abort) return;              // read by every thread between the same two barriers
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u);
+    c.src = p.buf[s & 1];
+    c.dst = p.buf[(s + 1) & 1];
+    c.sweep = p.sweep0 + (uint32_t)s;
+    c.rec = p.rec + s;
+    int* slot = &s_item[par ^ 1];
+    ready = false;
+    fused_sweep_body<MODE, RED, true>(
+        c, p.rk, bx, by,
+        // before the red/black barrier: the next item to the other slot
+        [&]() {
+          if (threadIdx.x == 0) *slot = next;
+        },
+        // after the black half: one early look at the next item's nine
+        // counters, so that its wait usually costs nothing
+        [&]() {
+          if (threadIdx.x < 9) {
+            const int ni = *slot;
+            if (ni < total) {
+              const int ns = ni / ntiles;
+              const int nk = ni - ns * ntiles;
+              const int nrow = nk / tiles_x;
+              const int nbx = nk - nrow * tiles_x;
+              const int nby = (nrow & 1) ? tiles_y - 1 - (nrow >> 1) : (nrow >> 1);
+              const int d = threadIdx.x;
+              const int nx = wrap_once(nbx + d % 3 - 1, tiles_x);
+              const int ny = wrap_once(nby + d / 3 - 1, tiles_y);
+              ready = ns == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
+            }
+          }
+        });
+    if (threadIdx.x == kThreads - 32) {
+      // a warp other than the pollers' publishes the tile: the closing barrier
+      // orders every thread's stores to dst before this GPU-scope fence, which
+      // is cumulative over them (the grid barrier of cooperative groups relies
+      // on the same order); then the flag
+      __threadfence();
+      store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
+    }
+    par ^= 1;
+    item = s_item[par];
+  }
 }
 
 template <int MODE, int RED>
@@ -357,6 +499,41 @@ cudaError_t prepare_one() {
   return e;
 }
 
+template <int MODE, int RED>
+cudaError_t launch_persist_one(const FusedPersistArgs& a, int grid, cudaStream_t stream) {
+  void* args[] = {const_cast<FusedPersistArgs*>(&a)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED>),
+                                     dim3(grid), dim3(kThreads), args, kSmemBytes, stream);
+}
+
+template <int MODE, int RED>
+cudaError_t persist_grid_one(int L, int* grid) {
+  static int per_sm[64] = {};        // resident CTAs per SM, per device (0: not yet set)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || per_sm[dev] == 0) {
+    auto fn = k_sweep_fused_persist<MODE, RED>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int n = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (dev >= 0 && dev < 64) per_sm[dev] = n;
+    else per_sm[0] = n;
+  }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int tiles = (L / 2 / kTileK) * (L / kTileRows);
+  const int resident = per_sm[(dev >= 0 && dev < 64) ? dev : 0] * sms;
+  *grid = tiles < resident ? tiles : resident;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 bool fused_supported(int L) { return L >= 128 && (L % 128) == 0; }
@@ -395,6 +572,43 @@ cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs
     case 0: return comp ? launch_fused_one<0, 1>(a, stream) : launch_fused_one<0, 0>(a, stream);
     case 1: return comp ? launch_fused_one<1, 1>(a, stream) : launch_fused_one<1, 0>(a, stream);
     default: return comp ? launch_fused_one<2, 1>(a, stream) : launch_fused_one<2, 0>(a, stream);
+  }
+}
+
+}  // namespace xyk
+
+namespace xyk {
+
+int fused_tiles(int L) { return fused_supported(L) ? (L / 2 / kTileK) * (L / kTileRows) : 0; }
+
+int fused_persistent_max_sweeps(int L) {
+  const int t = fused_tiles(L);
+  // n x tiles items, plus one fetch past the end per CTA, stay below 2^31
+  return t > 0 ? (int)((0x7fffffffu - (1u << 20)) / (unsigned)t) : 0;
+}
+
+cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const FusedPersistArgs& a,
+                                    cudaStream_t stream) {
+  if (!fused_supported(a.L) || a.W * 2 != a.L || a.n_sweeps < 1 ||
+      a.n_sweeps > fused_persistent_max_sweeps(a.L) || !a.flags || a.counter != a.flags + fused_tiles(a.L) ||
+      !a.error || a.buf[0] == a.buf[1])
+    return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  int grid = 0;
+  cudaError_t e;
+  switch (sincos_mode) {
+    case 0: e = comp ? persist_grid_one<0, 1>(a.L, &grid) : persist_grid_one<0, 0>(a.L, &grid); break;
+    case 1: e = comp ? persist_grid_one<1, 1>(a.L, &grid) : persist_grid_one<1, 0>(a.L, &grid); break;
+    default: e = comp ? persist_grid_one<2, 1>(a.L, &grid) : persist_grid_one<2, 0>(a.L, &grid); break;
+  }
+  if (e != cudaSuccess) return e;
+  // the tile counters and, after them, the work counter
+  e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned int) * ((size_t)fused_tiles(a.L) + 1), stream);
+  if (e != cudaSuccess) return e;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_persist_one<0, 1>(a, grid, stream) : launch_persist_one<0, 0>(a, grid, stream);
+    case 1: return comp ? launch_persist_one<1, 1>(a, grid, stream) : launch_persist_one<1, 0>(a, grid, stream);
+    default: return comp ? launch_persist_one<2, 1>(a, grid, stream) : launch_persist_one<2, 0>(a, grid, stream);
   }
 }
 

@@ -71,6 +71,39 @@ struct QuadFusedArgs {
   double beta[4];
 };
 
+// All n sweeps of one lattice in one cooperative launch of the fused sweep
+// (tiles wait on their eight neighbours' per-tile sweep counters).
+struct FusedPersistArgs {
+  float* buf[2];         // [2][L][W] each: buf[0] holds the state before the first
+                         // sweep; sweep s reads buf[s & 1] and writes buf[(s + 1) & 1]
+  int L;
+  int W;
+  float K;
+  float delta;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id;
+  uint32_t sweep0;       // Philox sweep word of the first sweep
+  int n_sweeps;
+  xy_record* rec;        // records of the n sweeps, zeroed
+  double beta;
+  unsigned int* flags;   // fused_tiles(L) tile counters, then the work counter
+                         // (zeroed by the launch)
+  unsigned int* counter; // == flags + fused_tiles(L)
+  unsigned int* error;   // set nonzero when a bounded wait runs out
+};
+
+// Tiles of one fused sweep of side L (0 if !fused_supported(L)).
+int fused_tiles(int L);
+
+// Most sweeps one persistent launch takes (n_sweeps x tiles < 2^31).
+int fused_persistent_max_sweeps(int L);
+
+// One cooperative launch of a.n_sweeps fused sweeps; zeroes the counters first.
+// cudaErrorInvalidValue on bad arguments; the launch's own error (e.g.
+// cudaErrorCooperativeLaunchTooLarge) otherwise.
+cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const FusedPersistArgs& a,
+                                    cudaStream_t stream);
+
 // Whether the fused four-replica kernel handles side L (a positive multiple of 32).
 bool quad_fused_supported(int L);
 

@@ -38,7 +38,8 @@ class Lattice:
         p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
-                       "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
+                       "two_pass": X.XY_ALGO_TWO_PASS,
+                       "persistent": X.XY_ALGO_PERSISTENT}[algorithm]
         self.params = p
         self.J = float(J)
         with torch.cuda.device(self.device):
@@ -64,6 +65,12 @@ class Lattice:
 
     def info(self):
         return X.xy_info(self.ctx)
+
+    @property
+    def algorithm(self):
+        """The sweep algorithm in use: "fused", "two_pass" or "persistent"."""
+        return {X.XY_ALGO_FUSED: "fused", X.XY_ALGO_TWO_PASS: "two_pass",
+                X.XY_ALGO_PERSISTENT: "persistent"}[X.xy_algorithm(self.ctx)]
 
     def observables(self, first=0, count=None):
         n, _ = X.xy_info(self.ctx)

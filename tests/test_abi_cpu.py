@@ -64,6 +64,7 @@ def _params(**kw):
     (dict(delta=0.0), "delta"), (dict(delta=4.0), "delta"),
     (dict(start=7), "start"), (dict(sincos_mode=5), "sincos"), (dict(reduce_mode=2), "reduce"),
     (dict(algorithm=9), "algorithm"), (dict(algorithm=1, L=96), "multiple of 128"),
+    (dict(algorithm=3, L=96), "multiple of 128"),
     (dict(J=float("inf")), "J"),
 ])
 def test_create_rejects_bad_parameters(lib, kw, fragment):
@@ -81,6 +82,8 @@ def test_null_arguments(lib):
     assert lib.xy_create(C.byref(_params()), None, C.c_void_p(8), C.byref(ctx)) == X.XY_EINVAL
     assert lib.xy_sweep(None, 1) == X.XY_EINVAL
     assert lib.xy_destroy(None) == X.XY_OK
+    algo = C.c_int32(-1)
+    assert lib.xy_algorithm(None, C.byref(algo)) == X.XY_EINVAL and algo.value == -1
     bogus = C.c_void_p(0x1000)
     assert lib.xy_sweep(bogus, 1) == X.XY_ESTATE        # never created: refused, not read
     assert lib.xy_destroy(bogus) == X.XY_ESTATE

@@ -212,7 +212,7 @@ def test_lockstep_parameters(beta, J, delta):
     assert r["rec"] <= 1.0 and r["acc_mismatch"] == 0
 
 
-@pytest.mark.parametrize("algorithm", ["fused", "two_pass"])
+@pytest.mark.parametrize("algorithm", ["fused", "two_pass", "persistent"])
 def test_lockstep_large_config_full_size(algorithm):
     """L=4096, beta=1.12, seed 7 (the throughput configuration); the fused kernel is the
     bench's launch path: sweeps 0, 1 and 20 checked over all 16.8M sites."""

@@ -1,0 +1,115 @@
+"""The persistent fused sweep (XY_ALGO_PERSISTENT): every sweep of an xy_sweep
+call in one cooperative launch, tiles ordered only by their neighbours'
+per-tile sweep counters.  Each tile runs the fused kernel's arithmetic, so the
+angles, the accept counts and the records (exact fixed-point sums of the same
+per-tile partial sums) must equal those of one fused launch per sweep, bit for
+bit, whatever the number of sweeps per call; and through the fused kernel it
+inherits the lock-step parity with the oracle (checked directly at L = 4096 in
+test_gpu_parity.py).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU container
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0811_2111_gb300 import build as _build  # noqa: E402
+
+_build.build()
+from paper_0811_2111_gb300 import _lib as X  # noqa: E402
+from paper_0811_2111_gb300.lattice import Lattice  # noqa: E402
+
+FIELDS = ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta")
+
+
+def _run(L, algorithm, calls, sincos="accurate", reduce="fp64", beta=1.12, seed=31, lid=2):
+    with Lattice(L, beta, seed, sincos=sincos, reduce=reduce, lattice_id=lid,
+                 algorithm=algorithm) as lat:
+        for n in calls:
+            lat.sweep(n)
+        s, nxt = lat.state()
+        obs = lat.observables()
+    return s, nxt, obs
+
+
+@pytest.mark.parametrize("L", [128, 256, 384, 512, 1024, 2048])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
+                                           ("libm", "fp64")])
+def test_persistent_equals_fused(L, sincos, reduce):
+    """L = 128: one tile column (left and right neighbour are the tile itself);
+    384: three tile columns and twelve rows; 512-2048: 64-1024 tiles, where
+    fewer tiles than the CTAs' current and fetched items make tiles wait on
+    their neighbours' and their own previous sweep, run on other CTAs."""
+    n = 25
+    sp, np_, op = _run(L, "persistent", (n,), sincos, reduce)
+    sf, nf, of = _run(L, "fused", (n,), sincos, reduce)
+    assert np_ == nf == n
+    assert np.array_equal(sp, sf)
+    for k in FIELDS:
+        assert np.array_equal(op[k], of[k]), k
+
+
+def test_more_tiles_than_resident_ctas():
+    """L = 4096: 4096 tiles on at most 3 x 152 resident CTAs (about nine tiles
+    per CTA per sweep); 12 sweeps in one launch, then 1 and 2 more."""
+    sp, np_, op = _run(4096, "persistent", (12, 1, 2))
+    sf, nf, of = _run(4096, "fused", (15,))
+    assert np_ == nf == 15
+    assert np.array_equal(sp, sf)
+    for k in FIELDS:
+        assert np.array_equal(op[k], of[k]), k
+
+
+def test_calls_split_anywhere():
+    """The state after odd and even sweep counts per call (the ping-pong buffer
+    parity), and one sweep per call, equal one call for all sweeps."""
+    ref, _, oref = _run(512, "persistent", (9,))
+    for calls in ((1, 1, 1, 1, 1, 1, 1, 1, 1), (2, 3, 4), (5, 4)):
+        s, n, o = _run(512, "persistent", calls)
+        assert n == 9 and np.array_equal(s, ref), calls
+        for k in FIELDS:
+            assert np.array_equal(o[k], oref[k]), (calls, k)
+
+
+def test_caller_owned_buffer():
+    L, beta, seed = 256, 0.9, 17
+    theta = torch.zeros(L * L, dtype=torch.float32, device="cuda")
+    p = X.xy_params()
+    p.L, p.start, p.beta, p.J, p.delta, p.seed = L, X.XY_START_HOT, beta, 1.0, np.pi, seed
+    p.sincos_mode, p.reduce_mode, p.lattice_id = X.XY_SINCOS_ACCURATE, X.XY_REDUCE_FP64, 0
+    p.algorithm = X.XY_ALGO_PERSISTENT
+    import ctypes as C
+    stream = torch.cuda.current_stream()
+    ctx = X.xy_create(p, C.c_void_p(stream.cuda_stream), C.c_void_p(theta.data_ptr()))
+    try:
+        X.check(X.lib().xy_sweep(ctx, 5), ctx)
+        X.check(X.lib().xy_synchronize(ctx), ctx)
+        host = np.empty(L * L, np.float32)
+        nxt = C.c_uint64()
+        X.check(X.lib().xy_get_state(ctx, host.ctypes.data_as(C.c_void_p), C.byref(nxt)), ctx)
+    finally:
+        X.check(X.lib().xy_destroy(ctx))
+    sf, _, _ = _run(L, "fused", (5,), beta=beta, seed=seed, lid=0)
+    assert nxt.value == 5 and np.array_equal(host.reshape(L, L), sf)
+
+
+def test_algorithm_needs_l_multiple_of_128():
+    with pytest.raises(X.XYError):
+        Lattice(130, 1.0, 1, algorithm="persistent")
+
+
+@pytest.mark.parametrize("L,expected", [(128, "persistent"), (2048, "persistent"),
+                                        (4096, "fused"), (130, "two_pass")])
+def test_auto_choice(L, expected):
+    """AUTO: the persistent sweep for multiples of 128 up to 2048 (where a sweep
+    is a few waves of tiles), one fused launch per sweep beyond, two-pass for
+    other even sides."""
+    with Lattice(L, 1.0, 1) as lat:
+        assert lat.algorithm == expected
+    for algo in ("fused", "persistent"):
+        if L % 128 == 0:
+            with Lattice(L, 1.0, 1, algorithm=algo) as lat:
+                assert lat.algorithm == algo
