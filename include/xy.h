@@ -63,7 +63,7 @@ enum { XY_START_HOT = 0, XY_START_COLD = 1 };
  *   XY_SINCOS_FAST      the SFU intrinsics __sincosf / __expf;
  *   XY_SINCOS_LIBM      CUDA's sincosf / expf. */
 enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
-/* Sweep kernel: AUTO picks PERSISTENT when L is a multiple of 128 up to 2048
+/* Sweep kernel: AUTO picks PERSISTENT when L is a multiple of 128 up to 4096
  * (falling back to one fused launch per sweep when the cooperative grid does
  * not fit on the device), FUSED for larger multiples of 128, else TWO_PASS.
  *   XY_ALGO_FUSED      one launch per sweep (both colours + measure), the state

@@ -52,10 +52,10 @@ void set_thread_msg(const char* fmt, ...) {
 
 }  // namespace
 
-// XY_ALGO_AUTO takes the persistent sweep up to this side: there a sweep is a
-// few waves of tiles and one launch per sweep pays its fill and drain every
-// sweep; beyond it the per-sweep launch is as fast or faster.
-constexpr int kAutoPersistentMaxL = 2048;
+// XY_ALGO_AUTO takes the persistent sweep up to this side: there a sweep is
+// at most nine waves of tiles and one launch per sweep pays its fill and drain
+// every sweep; beyond it (L = 8192: 36 waves) the per-sweep launch is faster.
+constexpr int kAutoPersistentMaxL = 4096;
 
 struct xy_ctx {
   uint32_t magic;

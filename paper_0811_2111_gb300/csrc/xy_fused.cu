@@ -237,12 +237,13 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     *reinterpret_cast<float2*>(a.dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
-  // 160 sites spread evenly over the 8 warps (20 each) so no warp idles at
-  // the barrier that follows
+  // 160 sites on the first five warps, one per lane: the ring takes one site
+  // update's time whichever way it is spread, and full warps issue no idle
+  // lanes (the other three warps wait at the barrier and leave their issue
+  // slots to the SM's other CTAs)
   {
-    constexpr int kPerWarp = (kRing + kWarps - 1) / kWarps;
-    const int i = warp * kPerWarp + lane;
-    if (lane < kPerWarp && i < kRing) {
+    const int i = threadIdx.x;
+    if (i < kRing) {
       int ty, tk;
       if (i < kTileK) {
         ty = -1;
@@ -369,6 +370,7 @@ template <int MODE, int RED>
 __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersistArgs p) {
   __shared__ int s_abort;
   __shared__ int s_item[2];          // this tile's item and the next (alternating)
+  __shared__ int s_ready[2];         // the next item's nine counters were all seen set
   const int tiles_x = p.W / kTileK, tiles_y = p.L / kTileRows;
   const int ntiles = tiles_x * tiles_y;
   const int total = p.n_sweeps * ntiles;          // < 2^31 - 2^20 (the host splits longer runs)
@@ -382,17 +384,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
   if (threadIdx.x == 0) {
     s_abort = 0;
     s_item[0] = (int)atomicAdd(p.counter, 1u);
+    s_ready[0] = 0;
   }
   __syncthreads();
   int par = 0;
   int item = s_item[0];
-  bool ready = false;                // this thread's counter of the item already seen set
   while (item < total) {
     const int s = item / ntiles;
     const int k = item - s * ntiles;
     const int prow = k / tiles_x;
     const int bx = k - prow * tiles_x;
     const int by = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+    // when the previous tile's early look found all nine counters set, this
+    // tile neither waits nor needs the barrier (the acquire loads came before
+    // the previous tile's closing barrier)
+    const bool ready = s_ready[par] != 0;
     if (s > 0 && threadIdx.x < 9 && !ready) {
       // the eight neighbours and the tile itself (its sweep s - 1 may have run
       // on another CTA)
@@ -413,8 +419,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
         __nanosleep(128);
       }
     }
-    __syncthreads();
-    if (s_abort) return;              // read by every thread between the same two barriers
+    if (!ready) {
+      __syncthreads();
+      if (s_abort) return;            // read by every thread between the same two barriers
+    }
     int next = 0;
     if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u);
     c.src = p.buf[s & 1];
@@ -422,7 +430,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
     c.sweep = p.sweep0 + (uint32_t)s;
     c.rec = p.rec + s;
     int* slot = &s_item[par ^ 1];
-    ready = false;
     fused_sweep_body<MODE, RED, true>(
         c, p.rk, bx, by,
         // before the red/black barrier: the next item to the other slot
@@ -430,11 +437,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
           if (threadIdx.x == 0) *slot = next;
         },
         // after the black half: one early look at the next item's nine
-        // counters, so that its wait usually costs nothing
+        // counters (warp 0), so that its wait usually costs nothing
         [&]() {
-          if (threadIdx.x < 9) {
+          if (threadIdx.x < 32) {
+            bool ok = threadIdx.x >= 9;
             const int ni = *slot;
-            if (ni < total) {
+            if (threadIdx.x < 9 && ni < total) {
               const int ns = ni / ntiles;
               const int nk = ni - ns * ntiles;
               const int nrow = nk / tiles_x;
@@ -443,8 +451,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
               const int d = threadIdx.x;
               const int nx = wrap_once(nbx + d % 3 - 1, tiles_x);
               const int ny = wrap_once(nby + d / 3 - 1, tiles_y);
-              ready = ns == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
+              ok = ns == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
             }
+            const unsigned int all = __ballot_sync(0xffffffffu, ok);
+            if (threadIdx.x == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
           }
         });
     if (threadIdx.x == kThreads - 32) {

@@ -214,8 +214,9 @@ def test_lockstep_parameters(beta, J, delta):
 
 @pytest.mark.parametrize("algorithm", ["fused", "two_pass", "persistent"])
 def test_lockstep_large_config_full_size(algorithm):
-    """L=4096, beta=1.12, seed 7 (the throughput configuration); the fused kernel is the
-    bench's launch path: sweeps 0, 1 and 20 checked over all 16.8M sites."""
+    """L=4096, beta=1.12, seed 7 (the throughput configuration; AUTO runs it with the
+    persistent sweep): sweeps 0, 1 and 20 checked over all 16.8M sites, sweeps
+    2-18 in one launch in between."""
     w = WL.LARGE
     with LT.Lattice(w.L, w.beta, w.seed, algorithm=algorithm) as lat:
         r0 = run_lockstep(lat, 2, w.beta, w.seed)

@@ -63,6 +63,19 @@ def test_more_tiles_than_resident_ctas():
         assert np.array_equal(op[k], of[k]), k
 
 
+def test_bench_launch_configuration():
+    """The throughput configuration as bench.py times it: L=4096, beta=1.12, seed 7,
+    1000 sweeps in one persistent launch, against 1000 fused launches (whose
+    sweeps are checked against the oracle in lock step in test_gpu_parity.py):
+    the same final state, accept counts and records, bit for bit."""
+    sp, np_, op = _run(4096, "persistent", (1000,), seed=7, lid=0)
+    sf, nf, of = _run(4096, "fused", (1000,), seed=7, lid=0)
+    assert np_ == nf == 1000
+    assert np.array_equal(sp, sf)
+    for k in FIELDS:
+        assert np.array_equal(op[k], of[k]), k
+
+
 def test_calls_split_anywhere():
     """The state after odd and even sweep counts per call (the ping-pong buffer
     parity), and one sweep per call, equal one call for all sweeps."""
@@ -101,12 +114,12 @@ def test_algorithm_needs_l_multiple_of_128():
         Lattice(130, 1.0, 1, algorithm="persistent")
 
 
-@pytest.mark.parametrize("L,expected", [(128, "persistent"), (2048, "persistent"),
-                                        (4096, "fused"), (130, "two_pass")])
+@pytest.mark.parametrize("L,expected", [(128, "persistent"), (4096, "persistent"),
+                                        (8192, "fused"), (130, "two_pass")])
 def test_auto_choice(L, expected):
-    """AUTO: the persistent sweep for multiples of 128 up to 2048 (where a sweep
-    is a few waves of tiles), one fused launch per sweep beyond, two-pass for
-    other even sides."""
+    """AUTO: the persistent sweep for multiples of 128 up to 4096 (where a sweep
+    is at most nine waves of tiles), one fused launch per sweep beyond,
+    two-pass for other even sides."""
     with Lattice(L, 1.0, 1) as lat:
         assert lat.algorithm == expected
     for algo in ("fused", "persistent"):
