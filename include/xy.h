@@ -168,6 +168,16 @@ xy_status xy_info(const xy_ctx *ctx, int64_t *n_records, uint64_t *next_sweep);
  * XY_ALGO_FUSED, XY_ALGO_TWO_PASS or XY_ALGO_PERSISTENT. */
 xy_status xy_algorithm(const xy_ctx *ctx, int32_t *algorithm);
 
+/* Self-test of the persistent sweep's failure path (no context involved):
+ * one persistent launch at L = 128 whose first sweep is never handed out, so
+ * every wait of the second sweep runs out after `polls` polls (1 <= polls <=
+ * 2^24; each poll sleeps ~128 ns) and the kernel ends with its error word set.
+ * Returns XY_ETIMEOUT when that happened (the expected result), XY_OK if the
+ * waits completed (a bug), XY_EINVAL / XY_ECUDA otherwise.  Stream-ordered on
+ * cuda_stream, synchronizes it; allocates and frees ~130 KB of device memory.
+ * Exists to test the failure path; the paper has no counterpart. */
+xy_status xy_selftest_persistent_wait(void *cuda_stream, int64_t polls);
+
 /* Copy the angles (natural order, L*L floats) to host memory and report the
  * next sweep index.  Synchronizes. */
 xy_status xy_get_state(xy_ctx *ctx, float *host_angles, uint64_t *next_sweep);

@@ -97,6 +97,7 @@ def lib():
         "xy_records_device": (st, [P, C.POINTER(P), C.POINTER(C.c_int64)]),
         "xy_info": (st, [P, C.POINTER(C.c_int64), C.POINTER(C.c_uint64)]),
         "xy_algorithm": (st, [P, C.POINTER(C.c_int32)]),
+        "xy_selftest_persistent_wait": (st, [P, C.c_int64]),
         "xy_get_state": (st, [P, P, C.POINTER(C.c_uint64)]),
         "xy_set_state": (st, [P, P, C.c_uint64]),
         "xy_set_beta": (st, [P, C.c_double]),

@@ -436,6 +436,8 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.flags = c->d_tiles;
     a.counter = c->d_tiles + xyk::fused_tiles(c->p.L);
     a.error = c->d_wait;
+    a.spin_limit = xyk::fused_persistent_spin_limit();
+    a.skip_items = 0;
     // one launch per at most fused_persistent_max_sweeps sweeps (the kernel's
     // work items are counted in 32 bits)
     const int64_t chunk = xyk::fused_persistent_max_sweeps(c->p.L);
@@ -594,6 +596,68 @@ xy_status xy_algorithm(const xy_ctx* c, int32_t* algorithm) {
     return XY_EINVAL;
   }
   *algorithm = c->persistent ? XY_ALGO_PERSISTENT : (c->fused ? XY_ALGO_FUSED : XY_ALGO_TWO_PASS);
+  return XY_OK;
+}
+
+xy_status xy_selftest_persistent_wait(void* cuda_stream, int64_t polls) {
+  if (polls < 1 || polls > (1 << 24)) {
+    set_thread_msg("xy_selftest_persistent_wait: polls must be in [1, 2^24]");
+    return XY_EINVAL;
+  }
+  // L = 128 (four tiles), two sweeps of which the first is never handed out:
+  // every tile of the second waits for counters that nothing sets
+  const int L = 128;
+  const size_t N = (size_t)L * L;
+  const int tiles = xyk::fused_tiles(L);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  float* buf = nullptr;
+  unsigned int* words = nullptr;      // tile counters, work counter, error word
+  xy_record* rec = nullptr;
+  unsigned int err = 0;
+  cudaError_t e = cudaMalloc(&buf, 2 * N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&words, sizeof(unsigned int) * (size_t)(tiles + 2));
+  if (e == cudaSuccess) e = cudaMalloc(&rec, 2 * sizeof(xy_record));
+  if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 2 * N * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * (size_t)(tiles + 2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, 2 * sizeof(xy_record), s);
+  if (e == cudaSuccess) {
+    xyk::FusedPersistArgs a;
+    a.buf[0] = buf;
+    a.buf[1] = buf + N;
+    a.L = L;
+    a.W = L / 2;
+    a.K = 1.f;
+    a.delta = (float)M_PI;
+    a.rk = xyd::make_round_keys(1);
+    a.lattice_id = 0;
+    a.sweep0 = 0;
+    a.n_sweeps = 2;
+    a.rec = rec;
+    a.beta = 1.0;
+    a.flags = words;
+    a.counter = words + tiles;
+    a.error = words + tiles + 1;
+    a.spin_limit = (long long)polls;
+    a.skip_items = tiles;
+    e = xyk::launch_fused_persistent(XY_SINCOS_ACCURATE, XY_REDUCE_FP64, a, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&err, a.error, sizeof(err), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (buf) cudaFree(buf);
+  if (words) cudaFree(words);
+  if (rec) cudaFree(rec);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    set_thread_msg("xy_selftest_persistent_wait: %s", cudaGetErrorString(e));
+    return XY_ECUDA;
+  }
+  if (err) {
+    set_thread_msg("xy_selftest_persistent_wait: the waits ran out after %lld polls",
+                   (long long)polls);
+    return XY_ETIMEOUT;
+  }
+  set_thread_msg("xy_selftest_persistent_wait: the waits completed, which they cannot");
   return XY_OK;
 }
 

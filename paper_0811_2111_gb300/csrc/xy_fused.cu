@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
   c.beta = p.beta;
   if (threadIdx.x == 0) {
     s_abort = 0;
-    s_item[0] = (int)atomicAdd(p.counter, 1u);
+    s_item[0] = (int)atomicAdd(p.counter, 1u) + p.skip_items;
     s_ready[0] = 0;
   }
   __syncthreads();
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
       while (load_acquire(f) < (unsigned int)s) {
         // give up when the limit runs out, or early once another CTA has
         // given up (so a failure does not cascade from wait to wait)
-        if (++it > kPersistSpinLimit ||
+        if (++it > p.spin_limit ||
             ((it & 255) == 0 && *reinterpret_cast<volatile unsigned int*>(p.error) != 0u)) {
           atomicOr(p.error, 1u);
           s_abort = 1;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
       if (s_abort) return;            // read by every thread between the same two barriers
     }
     int next = 0;
-    if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u);
+    if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u) + p.skip_items;
     c.src = p.buf[s & 1];
     c.dst = p.buf[(s + 1) & 1];
     c.sweep = p.sweep0 + (uint32_t)s;
@@ -591,6 +591,8 @@ namespace xyk {
 
 int fused_tiles(int L) { return fused_supported(L) ? (L / 2 / kTileK) * (L / kTileRows) : 0; }
 
+long long fused_persistent_spin_limit() { return kPersistSpinLimit; }
+
 int fused_persistent_max_sweeps(int L) {
   const int t = fused_tiles(L);
   // n x tiles items, plus one fetch past the end per CTA, stay below 2^31
@@ -601,7 +603,8 @@ cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const Fuse
                                     cudaStream_t stream) {
   if (!fused_supported(a.L) || a.W * 2 != a.L || a.n_sweeps < 1 ||
       a.n_sweeps > fused_persistent_max_sweeps(a.L) || !a.flags || a.counter != a.flags + fused_tiles(a.L) ||
-      !a.error || a.buf[0] == a.buf[1])
+      !a.error || a.buf[0] == a.buf[1] || a.spin_limit < 1 || a.skip_items < 0 ||
+      a.skip_items > a.n_sweeps * fused_tiles(a.L))
     return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   int grid = 0;

@@ -90,7 +90,13 @@ struct FusedPersistArgs {
                          // (zeroed by the launch)
   unsigned int* counter; // == flags + fused_tiles(L)
   unsigned int* error;   // set nonzero when a bounded wait runs out
+  long long spin_limit;  // polls before a wait gives up (fused_persistent_spin_limit())
+  int skip_items;        // work items not handed out (0; > 0 only to test the
+                         // failure path: their counters are then never set)
 };
+
+// The default bound of the persistent kernel's waits, in polls (about a second).
+long long fused_persistent_spin_limit();
 
 // Tiles of one fused sweep of side L (0 if !fused_supported(L)).
 int fused_tiles(int L);

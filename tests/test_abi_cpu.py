@@ -84,6 +84,9 @@ def test_null_arguments(lib):
     assert lib.xy_destroy(None) == X.XY_OK
     algo = C.c_int32(-1)
     assert lib.xy_algorithm(None, C.byref(algo)) == X.XY_EINVAL and algo.value == -1
+    # polls out of range: rejected before any CUDA call
+    assert lib.xy_selftest_persistent_wait(None, 0) == X.XY_EINVAL
+    assert lib.xy_selftest_persistent_wait(None, (1 << 24) + 1) == X.XY_EINVAL
     bogus = C.c_void_p(0x1000)
     assert lib.xy_sweep(bogus, 1) == X.XY_ESTATE        # never created: refused, not read
     assert lib.xy_destroy(bogus) == X.XY_ESTATE

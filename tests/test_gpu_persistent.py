@@ -126,3 +126,21 @@ def test_auto_choice(L, expected):
         if L % 128 == 0:
             with Lattice(L, 1.0, 1, algorithm=algo) as lat:
                 assert lat.algorithm == algo
+
+
+def test_wait_runs_out_and_reports_timeout():
+    """The failure path, made on purpose without a fault: a persistent launch
+    whose first sweep is never handed out, so every wait of its second sweep
+    runs out after 4096 polls; the kernel ends with its error word set and the
+    call reports XY_ETIMEOUT.  The device stays usable: a persistent run right
+    after is still bit for bit the fused one."""
+    import ctypes as C
+    stream = torch.cuda.current_stream()
+    st = X.lib().xy_selftest_persistent_wait(C.c_void_p(stream.cuda_stream), 4096)
+    assert st == X.XY_ETIMEOUT, X.xy_last_error(None)
+    assert "ran out" in X.xy_last_error(None)
+    sp, _, op = _run(256, "persistent", (5,))
+    sf, _, of = _run(256, "fused", (5,))
+    assert np.array_equal(sp, sf)
+    for k in FIELDS:
+        assert np.array_equal(op[k], of[k]), k
