@@ -77,14 +77,21 @@ typedef struct {
  * SITE is one thread per site (any L); CLUSTER runs a whole trajectory in one
  * launch of one thread-block cluster that keeps the lattice in shared memory
  * (L a power of two in [16, 256]; strips of 16 rows per CTA, neighbouring strips
- * read through distributed shared memory).  AUTO takes CLUSTER for L = 128
+ * read through distributed shared memory); PERSISTENT runs all kick-drift
+ * steps of a trajectory in one cooperative launch of the TILED_TMA step, tiles
+ * handed out in order and each starting once its eight neighbours and itself
+ * have finished the previous step (per-tile counters in device memory, bounded
+ * waits reported as XY_ETIMEOUT; needs what TILED_TMA needs and every CTA of
+ * the grid resident; bit-identical, but measured slower than TILED_TMA on
+ * GB300: 256 against 331 G site-steps/s at L = 4096).  AUTO takes CLUSTER for L = 128
  * and 256, else TILED_TMA when L % 128 == 0 and the encoder is available
  * (TILED if not), else SITE (the choices measured fastest on GB300: e.g.
  * TILED_TMA 51.4 us per step at L = 4096 against 57.0 for TILED and 58.3 for
  * TILED2; CLUSTER 2.8 us per step at L = 128 against 4.0 for TILED_TMA).  All
  * give bit-identical angles, momenta and sums. */
 enum { XY_HMC_KERNEL_AUTO = 0, XY_HMC_KERNEL_TILED = 1, XY_HMC_KERNEL_SITE = 2,
-       XY_HMC_KERNEL_TILED2 = 3, XY_HMC_KERNEL_TILED_TMA = 4, XY_HMC_KERNEL_CLUSTER = 5 };
+       XY_HMC_KERNEL_TILED2 = 3, XY_HMC_KERNEL_TILED_TMA = 4, XY_HMC_KERNEL_CLUSTER = 5,
+       XY_HMC_KERNEL_PERSISTENT = 6 };
 
 /* One record per trajectory (96 bytes).
  *   sum       C, Ix, Iy, Mx, My of the state after the test (2^-30 units,

@@ -60,6 +60,7 @@ XY_HMC_K_SHIFT = 24
 XY_HMC_KERNEL_AUTO, XY_HMC_KERNEL_TILED, XY_HMC_KERNEL_SITE, XY_HMC_KERNEL_TILED2 = 0, 1, 2, 3
 XY_HMC_KERNEL_TILED_TMA = 4
 XY_HMC_KERNEL_CLUSTER = 5
+XY_HMC_KERNEL_PERSISTENT = 6
 
 
 class xy_hmc_params(C.Structure):

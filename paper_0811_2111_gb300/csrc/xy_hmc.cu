@@ -470,6 +470,356 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
 }
 
 // ---------------------------------------------------------------------------
+// All kick-drift steps of a trajectory in one cooperative launch (every CTA
+// resident).  The work items (step j, tile) are ordered step-major, with the
+// tile rows of a step visited folded (0, T-1, 1, T-2, ...) so that a tile's
+// periodic neighbours are never more than two tile rows apart in that order;
+// iteration i of CTA b takes item b + i * gridDim.x, so every CTA gets the
+// same number of tiles to within one over the whole trajectory.  Step j of a
+// tile reads the angles of the tile and of its one-site halo after step j - 1
+// (its eight neighbours), its own momenta (updated in place by its step j - 1,
+// which may have run on another CTA) and overwrites the angle buffer those
+// nine tiles read during step j - 1, so it starts once the nine have published
+// flags >= j.  A tile is published (j + 1) after the next tile's first CTA
+// barrier, when its stores have long landed and the fence is cheap, or before
+// that tile waits; either way without waiting on anything else.  Thread 0
+// streams the next-but-one tile's angle and momentum boxes into the free TMA
+// stage once that item's nine counters are found set (relaxed loads issued
+// when the stage frees, looked at once the current tile is computed, then an
+// acquire fence; at large L they are always set); otherwise the load is
+// issued at the item's own turn, after a bounded wait.  Every wait is bounded
+// (counters and stage barriers); a wait that runs out sets HmcCtl::error, the
+// CTA drains its loads in flight (bounded) and ends, and CTAs waiting on it see
+// the error word and end too.  Items wait only on items of the step before,
+// and a finished item is published without waiting, so with every CTA
+// resident every wait ends.  Per tile the arithmetic is k_hmc_step_tma's, so
+// the trajectory is bit for bit that of one step launch per step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int hmc_load_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned int hmc_load_relaxed(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ void hmc_store_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Orders what this thread observed through the generic proxy (the counters
+// and the data they publish) before its later async-proxy (TMA) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ int hmc_wrap_tile(int v, int n) {
+  v += (v < 0) ? n : 0;
+  v -= (v >= n) ? n : 0;
+  return v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
+    k_hmc_steps_persist(const __grid_constant__ CUtensorMap map0,
+                        const __grid_constant__ CUtensorMap map1,
+                        const __grid_constant__ CUtensorMap map2,
+                        const __grid_constant__ CUtensorMap mapp, HmcStepsArgs q, int tiles_x,
+                        int n_tiles) {
+  using G = TmaGeom<4>;
+  constexpr int ROWS = 4;
+  constexpr int TR = G::kRows;
+  constexpr uint32_t kTmaStageBytes = G::kStageBytes;
+  constexpr int kTmaBox = G::kBox;
+  constexpr int kPublisher = kTileThreads - 32;   // lane 0 of the last warp
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  __shared__ __align__(16) float lastrow_c[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float lastrow_s[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float firstrow_c[2][kTileWarps + 1][kTileCols];
+  __shared__ __align__(16) float firstrow_s[2][kTileWarps + 1][kTileCols];
+  __shared__ float2 side[2][2][TR];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_issued[2];        // the stage's load for its next item is in flight
+  __shared__ int s_abort;
+
+  const HmcArgs& a = q.a;
+  const int L = a.L;
+  const int tiles_y = L / TR;
+  const int total = q.n_steps * n_tiles;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t cur = a.ctl->cur;
+  auto stage_th = [&](int s) {
+    return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes);
+  };
+  auto stage_p = [&](int s) {
+    return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes +
+                                                 kTmaBox * sizeof(float));
+  };
+  // item -> (step, tile x, tile y); iteration it of this CTA takes item
+  // blockIdx.x + it * gridDim.x
+  auto decode = [&](int item, int* j, int* tx, int* ty) {
+    *j = item / n_tiles;
+    const int k = item - *j * n_tiles;
+    const int prow = k / tiles_x;
+    *tx = k - prow * tiles_x;
+    *ty = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+  };
+  // angle buffers of step j: read (cur + 1 or 2), written (cur + 2 or 1)
+  auto src_of = [&](int j) { return (int)((cur + (j & 1 ? 2u : 1u)) % 3u); };
+  auto dst_of = [&](int j) { return (int)((cur + (j & 1 ? 1u : 2u)) % 3u); };
+  int issued[2] = {0, 0};            // thread 0: loads issued per stage (for the drain)
+  auto issue = [&](int item, int s) {
+    int j, tx, ty;
+    decode(item, &j, &tx, &ty);
+    const int sb = src_of(j);
+    const CUtensorMap* mth = sb == 0 ? &map0 : (sb == 1 ? &map1 : &map2);
+    fence_proxy_async_global();
+    mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
+    tma_load_2d(stage_th(s), mth, tx * kTileCols, ty * TR, &bar[s]);
+    tma_load_2d(stage_p(s), &mapp, tx * kTileCols, ty * TR, &bar[s]);
+    ++issued[s];
+  };
+  auto drain = [&]() {
+    if (tid == 0)
+      for (int s = 0; s < 2; ++s)
+        if (issued[s] > 0) (void)mbar_wait_bounded(&bar[s], (uint32_t)((issued[s] - 1) & 1),
+                                                   q.spin_limit);
+  };
+  // the previous tile, stored but not yet published (its counter slot and value)
+  int pend_slot = -1;
+  unsigned int pend_val = 0;
+  // publish it: the caller has passed a CTA barrier after every thread's stores
+  // of that tile; the GPU-scope fence is cumulative over them
+  auto publish = [&]() {
+    if (tid == kPublisher && pend_slot >= 0) {
+      __threadfence();
+      hmc_store_release(q.flags + pend_slot, pend_val);
+    }
+    pend_slot = -1;
+  };
+
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    fence_async_shared();
+    for (int s = 0; s < 2; ++s) {
+      const int item = blockIdx.x + s * gridDim.x;
+      s_issued[s] = 0;
+      int j, tx, ty;
+      if (item < total) {
+        decode(item, &j, &tx, &ty);
+        if (j == 0) {            // the first step reads the begin launch's output
+          issue(item, s);
+          s_issued[s] = 1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  for (int it = 0;; ++it) {
+    const int item = blockIdx.x + it * gridDim.x;
+    if (item >= total) break;
+    const int s = it & 1, b = it & 1;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    int j, tx, ty;
+    decode(item, &j, &tx, &ty);
+    const int x0 = tx * kTileCols, y0 = ty * TR;
+
+    if (!s_issued[s]) {
+      // its load was not issued ahead: publish the previous tile (this wait may
+      // be for it), wait for the nine counters, then load
+      __syncthreads();
+      publish();
+      if (j > 0 && tid < 9) {
+        const int nx = hmc_wrap_tile(tx + tid % 3 - 1, tiles_x);
+        const int ny = hmc_wrap_tile(ty + tid / 3 - 1, tiles_y);
+        const unsigned int* f = q.flags + (ny * tiles_x + nx);
+        long long n = 0;
+        while (hmc_load_acquire(f) < (unsigned int)j) {
+          if (++n > q.spin_limit ||
+              ((n & 255) == 0 && *reinterpret_cast<volatile unsigned int*>(&a.ctl->error) != 0u)) {
+            atomicOr(&a.ctl->error, 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+      __syncthreads();
+      if (s_abort) {
+        drain();
+        return;
+      }
+      if (tid == 0) issue(item, s);
+    }
+
+    const float* __restrict__ th_src = hmc_buf(a, src_of(j));
+    float* __restrict__ th_dst = hmc_buf(a, dst_of(j));
+    // halo: rows y0-1, y0+TR (threads 0..127 / 128..255), columns x0-1 and
+    // x0+128 (threads 0..TR-1 / TR..2TR-1), through L2 (written in this launch)
+    const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1) : (y0 + TR == L ? 0 : y0 + TR);
+    const float th_row = __ldcg(th_src + (size_t)hy * L + x0 + (tid & (kTileCols - 1)));
+    float th_side = 0.f;
+    const bool is_side = tid < 2 * TR;
+    if (is_side) {
+      const int sx = tid < TR ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
+      th_side = __ldcg(th_src + (size_t)(y0 + (tid % TR)) * L + sx);
+    }
+    if (!mbar_wait_bounded(&bar[s], parity, q.spin_limit)) {
+      atomicOr(&a.ctl->error, 1u);
+      s_abort = 1;
+    }
+
+    const int xb = 4 * lane, rb0 = ROWS * warp;
+    float4 t4[ROWS], p4[ROWS];
+    float c[ROWS][4], sn[ROWS][4];
+    {
+      float (*sth)[kTileCols] = stage_th(s);
+      float (*sp)[kTileCols] = stage_p(s);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        t4[r] = *reinterpret_cast<const float4*>(&sth[rb0 + r][xb]);
+        p4[r] = *reinterpret_cast<const float4*>(&sp[rb0 + r][xb]);
+      }
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        xyd::unit_vector<MODE>(t4[r].x, &sn[r][0], &c[r][0]);
+        xyd::unit_vector<MODE>(t4[r].y, &sn[r][1], &c[r][1]);
+        xyd::unit_vector<MODE>(t4[r].z, &sn[r][2], &c[r][2]);
+        xyd::unit_vector<MODE>(t4[r].w, &sn[r][3], &c[r][3]);
+      }
+      float hs, hc;
+      xyd::unit_vector<MODE>(th_row, &hs, &hc);
+      if (tid < kTileCols) {
+        lastrow_c[b][0][tid] = hc;
+        lastrow_s[b][0][tid] = hs;
+      } else {
+        firstrow_c[b][kTileWarps][tid - kTileCols] = hc;
+        firstrow_s[b][kTileWarps][tid - kTileCols] = hs;
+      }
+      if (is_side) {
+        xyd::unit_vector<MODE>(th_side, &hs, &hc);
+        side[b][tid / TR][tid % TR] = make_float2(hc, hs);
+      }
+      *reinterpret_cast<float4*>(&firstrow_c[b][warp][xb]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
+      *reinterpret_cast<float4*>(&firstrow_s[b][warp][xb]) =
+          make_float4(sn[0][0], sn[0][1], sn[0][2], sn[0][3]);
+      *reinterpret_cast<float4*>(&lastrow_c[b][warp + 1][xb]) =
+          make_float4(c[ROWS - 1][0], c[ROWS - 1][1], c[ROWS - 1][2], c[ROWS - 1][3]);
+      *reinterpret_cast<float4*>(&lastrow_s[b][warp + 1][xb]) =
+          make_float4(sn[ROWS - 1][0], sn[ROWS - 1][1], sn[ROWS - 1][2], sn[ROWS - 1][3]);
+    }
+    __syncthreads();   // stage s fully read; edges visible; the previous tile's stores done
+    if (s_abort) {
+      drain();
+      return;
+    }
+    publish();
+    // the item after next: its nine counters are loaded now (relaxed, all in
+    // flight together) and looked at once this tile is computed
+    const int next = item + 2 * gridDim.x;
+    unsigned int fl[9];
+    int nj = 0;
+    if (tid == 0) {
+      s_issued[s] = 0;
+      if (next < total) {
+        int ntx, nty;
+        decode(next, &nj, &ntx, &nty);
+        if (nj > 0) {
+#pragma unroll
+          for (int d = 0; d < 9; ++d) {
+            const int nx = hmc_wrap_tile(ntx + d % 3 - 1, tiles_x);
+            const int ny = hmc_wrap_tile(nty + d / 3 - 1, tiles_y);
+            fl[d] = hmc_load_relaxed(q.flags + (ny * tiles_x + nx));
+          }
+        }
+      }
+    }
+
+    const float4 cdn = *reinterpret_cast<const float4*>(&lastrow_c[b][warp][xb]);
+    const float4 sdn = *reinterpret_cast<const float4*>(&lastrow_s[b][warp][xb]);
+    const float4 cup = *reinterpret_cast<const float4*>(&firstrow_c[b][warp + 1][xb]);
+    const float4 sup = *reinterpret_cast<const float4*>(&firstrow_s[b][warp + 1][xb]);
+    const float cdn_a[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sdn_a[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
+    const float cup_a[4] = {cup.x, cup.y, cup.z, cup.w}, sup_a[4] = {sup.x, sup.y, sup.z, sup.w};
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
+      float sl = __shfl_up_sync(0xffffffffu, sn[r][3], 1);
+      float cr = __shfl_down_sync(0xffffffffu, c[r][0], 1);
+      float sr = __shfl_down_sync(0xffffffffu, sn[r][0], 1);
+      const int row = rb0 + r;
+      if (lane == 0) {
+        const float2 v = side[b][0][row];
+        cl = v.x;
+        sl = v.y;
+      }
+      if (lane == 31) {
+        const float2 v = side[b][1][row];
+        cr = v.x;
+        sr = v.y;
+      }
+      float pr[4] = {p4[r].x, p4[r].y, p4[r].z, p4[r].w};
+      const float tr[4] = {t4[r].x, t4[r].y, t4[r].z, t4[r].w};
+      float out[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float nlc = jj == 0 ? cl : c[r][jj - 1], nls = jj == 0 ? sl : sn[r][jj - 1];
+        const float nrc = jj == 3 ? cr : c[r][jj + 1], nrs = jj == 3 ? sr : sn[r][jj + 1];
+        const float ndc = r == 0 ? cdn_a[jj] : c[r - 1][jj], nds = r == 0 ? sdn_a[jj] : sn[r - 1][jj];
+        const float nuc = r == ROWS - 1 ? cup_a[jj] : c[r + 1][jj];
+        const float nus = r == ROWS - 1 ? sup_a[jj] : sn[r + 1][jj];
+        const float Sc = xyd::nb_sum(nlc, nrc, ndc, nuc);
+        const float Ss = xyd::nb_sum(nls, nrs, nds, nus);
+        pr[jj] = __fmaf_rn(a.a, hmc_force(c[r][jj], sn[r][jj], Sc, Ss, a.K), pr[jj]);
+        out[jj] = hmc_wrap(__fmaf_rn(a.eps, pr[jj], tr[jj]));
+      }
+      p4[r] = make_float4(pr[0], pr[1], pr[2], pr[3]);
+      t4[r] = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    if (tid == 0 && next < total) {
+      bool ready = true;
+      if (nj > 0) {
+#pragma unroll
+        for (int d = 0; d < 9; ++d) ready = ready && fl[d] >= (unsigned int)nj;
+      }
+      if (ready) {
+        // the relaxed loads saw every counter set: this acquire fence makes
+        // the stores they publish visible to thread 0, and issue()'s proxy
+        // fence to its TMA reads
+        fence_acq_rel_gpu();
+        fence_async_shared();
+        issue(next, s);
+        s_issued[s] = 1;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      const size_t g = (size_t)(y0 + rb0 + r) * L + x0 + xb;
+      *reinterpret_cast<float4*>(a.p_out + g) = p4[r];
+      *reinterpret_cast<float4*>(th_dst + g) = t4[r];
+    }
+    // published after the next tile's first barrier (its stores have landed
+    // by then), or before that tile waits
+    pend_slot = ty * tiles_x + tx;
+    pend_val = (unsigned int)(j + 1);
+  }
+  __syncthreads();
+  publish();
+}
+
+// ---------------------------------------------------------------------------
 // Two full kick-drift steps per launch (temporal blocking).  A CTA of 256
 // threads owns 32 x 128 sites.  It stages the unit vectors of the tile plus a
 // halo of two (36 x 132) and the angles and momenta of the tile plus a halo of
@@ -800,6 +1150,45 @@ cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* m
   if (box_rows == TmaGeom<4>::kRows) return launch_tma_rows<4>(sincos_mode, a, m, ctas, stream);
   return cudaErrorInvalidValue;
 }
+
+cudaError_t launch_hmc_steps_persist(int sincos_mode, const HmcStepsArgs& q, const void* maps4,
+                                     cudaStream_t stream) {
+  const HmcArgs& a = q.a;
+  if (!a.tiled || a.p_in != a.p_out || !maps4 || q.n_steps < 1 || !q.flags ||
+      q.spin_limit < 1 || (a.L % kTileCols) != 0 || (a.L % TmaGeom<4>::kRows) != 0)
+    return cudaErrorInvalidValue;
+  const int tiles_x = a.L / kTileCols;
+  const int n_tiles = tiles_x * (a.L / TmaGeom<4>::kRows);
+  if ((long long)q.n_steps * n_tiles > 0x7fffffffll - (1ll << 20)) return cudaErrorInvalidValue;
+  const void* fn = sincos_mode == 0 ? (const void*)k_hmc_steps_persist<0>
+                                    : (sincos_mode == 1 ? (const void*)k_hmc_steps_persist<1>
+                                                        : (const void*)k_hmc_steps_persist<2>);
+  const size_t smem = TmaGeom<4>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTileThreads, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int grid = n_tiles < per_sm * sms ? n_tiles : per_sm * sms;
+  e = cudaMemsetAsync(q.flags, 0, sizeof(unsigned int) * (size_t)n_tiles, stream);
+  if (e != cudaSuccess) return e;
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps4);
+  HmcStepsArgs qq = q;
+  int tx = tiles_x, nt = n_tiles;
+  void* args[] = {const_cast<CUtensorMap*>(&m[0]), const_cast<CUtensorMap*>(&m[1]),
+                  const_cast<CUtensorMap*>(&m[2]), const_cast<CUtensorMap*>(&m[3]), &qq, &tx, &nt};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kTileThreads), args, smem, stream);
+}
+
+int hmc_persist_tiles(int L) {
+  return (L % kTileCols == 0 && L % TmaGeom<4>::kRows == 0) ? (L / kTileCols) * (L / TmaGeom<4>::kRows)
+                                                             : 0;
+}
+
+long long hmc_persist_spin_limit() { return kSpinLimit; }
 
 namespace {
 // The failure path of the bounded waits, exercised without a fault: wait on a

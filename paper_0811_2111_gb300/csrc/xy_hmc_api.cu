@@ -55,6 +55,8 @@ void tmsg(const char* fmt, ...) {
 struct xy_hmc {
   alignas(64) CUtensorMap maps[4];   // TMA maps: angle buffers 0..2, momenta (32 x 128 boxes)
   bool use_tma;
+  bool use_persist;                  // a trajectory's steps in one cooperative TMA launch
+  unsigned int* d_tiles;             // its per-tile step counters
   bool use_cluster;                  // whole trajectories in one cluster launch
   int tma_rows;                      // tile (and box) rows of the TMA step kernel: 32 or 16
   int tma_ctas;                      // persistent grid of the TMA step kernel
@@ -180,7 +182,8 @@ xy_status validate(const xy_hmc_params* p) {
   }
   if (p->kernel != XY_HMC_KERNEL_AUTO && p->kernel != XY_HMC_KERNEL_TILED &&
       p->kernel != XY_HMC_KERNEL_SITE && p->kernel != XY_HMC_KERNEL_TILED2 &&
-      p->kernel != XY_HMC_KERNEL_TILED_TMA && p->kernel != XY_HMC_KERNEL_CLUSTER) {
+      p->kernel != XY_HMC_KERNEL_TILED_TMA && p->kernel != XY_HMC_KERNEL_CLUSTER &&
+      p->kernel != XY_HMC_KERNEL_PERSISTENT) {
     tmsg("bad kernel choice");
     return XY_EINVAL;
   }
@@ -189,7 +192,7 @@ xy_status validate(const xy_hmc_params* p) {
     return XY_EINVAL;
   }
   if ((p->kernel == XY_HMC_KERNEL_TILED || p->kernel == XY_HMC_KERNEL_TILED2 ||
-       p->kernel == XY_HMC_KERNEL_TILED_TMA) &&
+       p->kernel == XY_HMC_KERNEL_TILED_TMA || p->kernel == XY_HMC_KERNEL_PERSISTENT) &&
       !xyk::hmc_tiled_ok(p->L)) {
     tmsg("the tiled kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
@@ -212,7 +215,7 @@ xyk::HmcArgs args_of(const xy_hmc* h) {
   a.rk = xyd::make_round_keys(h->p.seed);
   a.lattice_id = h->p.lattice_id;
   a.tiled = h->p.kernel == XY_HMC_KERNEL_TILED || h->p.kernel == XY_HMC_KERNEL_TILED2 ||
-            h->p.kernel == XY_HMC_KERNEL_TILED_TMA ||
+            h->p.kernel == XY_HMC_KERNEL_TILED_TMA || h->p.kernel == XY_HMC_KERNEL_PERSISTENT ||
             (h->p.kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(h->p.L));
   a.pairs = h->p.kernel == XY_HMC_KERNEL_TILED2;
   return a;
@@ -249,6 +252,19 @@ cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cuda
       pcur = pother;
       pother = t;
       left -= 2;
+    } else if (h->use_persist) {
+      // every remaining step in one launch; step j reads offset 1 + (j & 1)
+      a.p_in = pcur;
+      a.p_out = pcur;
+      xyk::HmcStepsArgs q;
+      q.a = a;
+      q.n_steps = left;
+      q.flags = h->d_tiles;
+      q.spin_limit = xyk::hmc_persist_spin_limit();
+      e = xyk::launch_hmc_steps_persist(m, q, h->maps, s);
+      if (left & 1) off = 3 - off;
+      left = 0;
+      continue;
     } else {
       a.p_in = pcur;
       a.p_out = pcur;
@@ -329,6 +345,7 @@ void release(xy_hmc* h) {
   if (h->d_p2) cudaFree(h->d_p2);
   if (h->d_ctl) cudaFree(h->d_ctl);
   if (h->d_rec) cudaFree(h->d_rec);
+  if (h->d_tiles) cudaFree(h->d_tiles);
 }
 
 xy_status sync(xy_hmc* h, const char* what) {
@@ -392,7 +409,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
   // 128, 256); below that the per-launch cost of any kernel dominates
   h->use_cluster = p->kernel == XY_HMC_KERNEL_CLUSTER ||
                    (p->kernel == XY_HMC_KERNEL_AUTO && (p->L == 128 || p->L == 256));
-  const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA ||
+  const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA || p->kernel == XY_HMC_KERNEL_PERSISTENT ||
                         (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster &&
                          xyk::hmc_tiled_ok(p->L));
   if (e == cudaSuccess && want_tma) {
@@ -407,6 +424,17 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     if (e == cudaSuccess && !ok && p->kernel == XY_HMC_KERNEL_TILED_TMA) e = cudaErrorNotSupported;
     h->use_tma = ok;
     h->tma_ctas = 2 * (n_sm > 0 ? n_sm : 1);
+  }
+  // the trajectory-long persistent launch of the TMA step (needs the encoder)
+  const bool want_persist = p->kernel == XY_HMC_KERNEL_PERSISTENT;
+  if (e == cudaSuccess && want_persist) {
+    step = "persistent step counters";
+    if (!h->use_tma) {
+      e = cudaErrorNotSupported;
+    } else {
+      e = cudaMalloc(&h->d_tiles, sizeof(unsigned int) * (size_t)xyk::hmc_persist_tiles(p->L));
+      h->use_persist = e == cudaSuccess;
+    }
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ctl, 0, sizeof(xyk::HmcCtl), h->stream);
   if (e == cudaSuccess) {
@@ -442,9 +470,18 @@ xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
     return fail(h, XY_EINVAL, "xy_hmc_run: trajectory counter would pass 2^32 - 1");
   st = grow_records(h, h->rec_count + n_traj);
   if (st != XY_OK) return st;
-  if (!h->graph) H_CUDA(h, capture(h), "xy_hmc_run: graph capture");
-  for (int64_t i = 0; i < n_traj; ++i)
-    H_CUDA(h, cudaGraphLaunch(h->graph, h->stream), "xy_hmc_run: graph launch");
+  if (h->use_persist) {
+    // a trajectory is five launches here (begin, the counters' memset, the
+    // steps, final, accept): launched directly, no graph
+    H_CUDA(h, xyk::hmc_prepare(h->p.sincos_mode), "xy_hmc_run: kernel attributes");
+    for (int64_t i = 0; i < n_traj; ++i)
+      H_CUDA(h, enqueue_trajectory(h, xyk::kHmcBeginDraw, h->p.n_md, 0, h->stream),
+             "xy_hmc_run: launch");
+  } else {
+    if (!h->graph) H_CUDA(h, capture(h), "xy_hmc_run: graph capture");
+    for (int64_t i = 0; i < n_traj; ++i)
+      H_CUDA(h, cudaGraphLaunch(h->graph, h->stream), "xy_hmc_run: graph launch");
+  }
   H_CUDA(h, xyk::launch_hmc_canonical(args_of(h), h->stream),
          "xy_hmc_run: state copy");
   h->rec_count += n_traj;

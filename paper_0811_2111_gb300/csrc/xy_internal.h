@@ -318,6 +318,19 @@ cudaError_t hmc_prepare(int sincos_mode);
 // (CUtensorMap, 128 bytes each) of the three angle buffers and of the momentum
 // buffer a.p_in (== a.p_out), boxes of box_rows (32) rows x 128 columns,
 // which is also the kernel's tile; grid = ctas.
+// All kick-drift steps of a trajectory in one cooperative launch of the TMA
+// step (per-tile step counters, bounded waits; see xy_hmc.cu).
+struct HmcStepsArgs {
+  HmcArgs a;             // a.a = eps, p_in == p_out (momenta in place), tiled
+  int n_steps;           // kick-drift steps (step j reads buffer cur + 1 + (j & 1))
+  unsigned int* flags;   // hmc_persist_tiles(L) tile counters (zeroed by the launch)
+  long long spin_limit;  // polls before a wait gives up
+};
+cudaError_t launch_hmc_steps_persist(int sincos_mode, const HmcStepsArgs& q, const void* maps4,
+                                     cudaStream_t stream);
+int hmc_persist_tiles(int L);
+long long hmc_persist_spin_limit();
+
 cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
                                 int ctas, cudaStream_t stream);
 

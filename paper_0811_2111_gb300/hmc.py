@@ -43,7 +43,8 @@ class HMC:
         p.kernel = {"auto": X.XY_HMC_KERNEL_AUTO, "tiled": X.XY_HMC_KERNEL_TILED,
                     "site": X.XY_HMC_KERNEL_SITE, "tiled2": X.XY_HMC_KERNEL_TILED2,
                     "tiled_tma": X.XY_HMC_KERNEL_TILED_TMA,
-                    "cluster": X.XY_HMC_KERNEL_CLUSTER}[kernel]
+                    "cluster": X.XY_HMC_KERNEL_CLUSTER,
+                    "persistent": X.XY_HMC_KERNEL_PERSISTENT}[kernel]
         self.params = p
         self.J = float(J)
         with torch.cuda.device(self.device):

@@ -122,9 +122,10 @@ def test_hmc_record_layout():
     (dict(L=1), "L must"), (dict(L=65536), "L must"),
     (dict(beta=-1.0), "beta"), (dict(beta=float("inf")), "beta"), (dict(J=float("nan")), "J"),
     (dict(eps=0.0), "eps"), (dict(eps=float("nan")), "eps"), (dict(n_md=0), "n_md"),
-    (dict(start=3), "start"), (dict(sincos_mode=3), "sincos"), (dict(kernel=6), "kernel"), (dict(kernel=5, L=512), "cluster"),
+    (dict(start=3), "start"), (dict(sincos_mode=3), "sincos"), (dict(kernel=7), "kernel"), (dict(kernel=5, L=512), "cluster"),
     (dict(kernel=5, L=48), "cluster"),
     (dict(kernel=1, L=96), "multiple of 128"), (dict(kernel=3, L=96), "multiple of 128"),
+    (dict(kernel=6, L=96), "multiple of 128"),
 ])
 def test_hmc_create_rejects_bad_parameters(lib, kw, fragment):
     h = C.c_void_p()

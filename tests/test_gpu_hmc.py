@@ -116,11 +116,12 @@ def test_n_steps_match_oracle(L):
                                     (16, 3), (32, 4), (48, 4), (64, 7)])
 def test_kernels_are_bit_identical(L, n_md):
     """The tiled kernel (one step per launch), the two-step kernel (full steps
-    two per launch, odd remainders singly), the TMA-fed kernel, the cluster
-    kernel (a whole trajectory per launch) and the per-site kernel: same bits."""
+    two per launch, odd remainders singly), the TMA-fed kernel, the persistent
+    TMA kernel (a trajectory's steps in one launch), the cluster kernel (a
+    whole trajectory per launch) and the per-site kernel: same bits."""
     kernels = ["site"]
     if L % 128 == 0:
-        kernels += ["tiled", "tiled2", "tiled_tma"]
+        kernels += ["tiled", "tiled2", "tiled_tma", "persistent"]
     if L in (16, 32, 64, 128, 256):
         kernels += ["cluster"]
     out = {}
@@ -327,3 +328,27 @@ def test_bounded_wait_runs_out_and_reports_timeout():
     with HMC(128, 1.0, 3, 0.05, 4, kernel="tiled_tma") as h:   # still usable afterwards
         h.run(2)
         assert h.info()[0] == 2
+
+
+@pytest.mark.parametrize("L,n_md", [(512, 9), (1024, 20), (4096, 12)])
+def test_persistent_steps_equal_tma_steps(L, n_md):
+    """The trajectory-long persistent launch against one TMA step launch per
+    step, at sides where tiles wait on each other (L = 512: 64 tiles on 64
+    CTAs) and where they never do (L = 4096: 4096 tiles on 304 CTAs): angles,
+    momenta, records and sums bit for bit, over accepted and rejected
+    trajectories and a plain integration."""
+    out = {}
+    for kernel in ("tiled_tma", "persistent"):
+        with HMC(L, 1.1, 13, 0.6 / n_md, n_md, kernel=kernel, lattice_id=1) as h:
+            h.run(4)
+            th, p, _ = h.state()
+            o = h.observables()
+            h.integrate(n_md + 1)
+            th2, p2, _ = h.state()
+            out[kernel] = (th, p, o, th2, p2, h.last_sums())
+    a, b = out["persistent"], out["tiled_tma"]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k in ("C", "Ix", "Iy", "Mx", "My", "dH", "accepted"):
+        assert np.array_equal(a[2][k], b[2][k]), k
+    assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4])
+    assert a[5] == b[5]
