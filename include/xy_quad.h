@@ -40,19 +40,32 @@ typedef struct xy_quad xy_quad;
  *               colours and the sums; needs L % 32 == 0; a second float4
  *               buffer, the state ping-ponging between the two);
  *               XY_ALGO_TWO_PASS -- one launch per colour, in place;
- *               XY_ALGO_AUTO -- fused where L % 32 == 0, else two-pass.
- *               Both give the same angles and accept counts bit for bit.
+ *               XY_ALGO_PERSISTENT -- the fused sweep, all sweeps of one
+ *               xy_quad_sweep call in one cooperative launch, each tile of
+ *               32 rows x 16 sites starting once its eight neighbours and
+ *               itself have finished the previous sweep (per-tile counters in
+ *               device memory, bounded waits reported as XY_ETIMEOUT at the
+ *               next synchronizing call; needs L % 32 == 0 and every CTA of
+ *               the grid resident, XY_ECUDA otherwise);
+ *               XY_ALGO_AUTO -- persistent where L % 32 == 0 and L <= 1024
+ *               (falling back to one fused launch per sweep when the
+ *               cooperative grid does not fit), fused for larger multiples of
+ *               32, else two-pass.
+ *               All give the same angles, accept counts and (fused and
+ *               persistent) records bit for bit.
  *   beta        four inverse temperatures (>= 0, finite), one per replica.
  *   cuda_stream cudaStream_t or NULL (legacy default stream).
  * Device memory: 16 L^2 bytes per buffer (two for the fused sweep) plus
  * 8 L^2 bytes of scratch and the records.
- * Errors: XY_EINVAL (bad parameter; XY_ALGO_FUSED with L % 32 != 0),
+ * Errors: XY_EINVAL (bad parameter; XY_ALGO_FUSED or _PERSISTENT with
+ * L % 32 != 0),
  * XY_ENOMEM, XY_ECUDA (xy_quad_last_error(NULL)). */
 xy_status xy_quad_create(const xy_params *p, const double beta[4], void *cuda_stream,
                          xy_quad **out);
 
-/* Enqueue n_sweeps >= 0 sweeps of all four replicas (one launch per sweep
- * fused, two otherwise); appends n_sweeps records per replica. */
+/* Enqueue n_sweeps >= 0 sweeps of all four replicas (one launch per call
+ * persistent, one per sweep fused, two per sweep otherwise); appends n_sweeps
+ * records per replica. */
 xy_status xy_quad_sweep(xy_quad *q, int64_t n_sweeps);
 
 /* Observables of replica r's records [first, first + count), as xy_measure
@@ -68,7 +81,8 @@ xy_status xy_quad_get_state(xy_quad *q, int32_t replica, float *host_angles,
 /* Records per replica so far and the next sweep index. */
 xy_status xy_quad_info(const xy_quad *q, int64_t *n_records, uint64_t *next_sweep);
 
-/* The sweep algorithm the context runs: XY_ALGO_FUSED or XY_ALGO_TWO_PASS. */
+/* The sweep algorithm the context runs: XY_ALGO_FUSED, XY_ALGO_TWO_PASS or
+ * XY_ALGO_PERSISTENT. */
 xy_status xy_quad_algorithm(const xy_quad *q, int32_t *algorithm);
 
 xy_status xy_quad_synchronize(xy_quad *q);

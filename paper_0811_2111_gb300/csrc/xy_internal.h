@@ -110,6 +110,26 @@ int fused_persistent_max_sweeps(int L);
 cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const FusedPersistArgs& a,
                                     cudaStream_t stream);
 
+// All sweeps of a call of the four-replica fused sweep in one cooperative
+// launch (tiles ordered by per-tile sweep counters, bounded waits).
+struct QuadPersistArgs {
+  QuadFusedArgs a;       // L, W, K, delta, rk, lattice_id0, beta (src, dst, sweep, rec unused)
+  float* buf[2];         // buf[0] holds the state before the first sweep; sweep s
+                         // reads buf[s & 1] and writes buf[(s + 1) & 1]
+  uint32_t sweep0;       // Philox sweep word of the first sweep
+  int n_sweeps;
+  xy_record* rec;        // records of the n sweeps, [sweep][replica], zeroed
+  unsigned int* flags;   // quad_persistent_tiles(L) tile counters, then the work counter
+  unsigned int* counter; // == flags + quad_persistent_tiles(L)
+  unsigned int* error;   // set nonzero when a bounded wait runs out
+  long long spin_limit;  // polls before a wait gives up (quad_persistent_spin_limit())
+};
+int quad_persistent_tiles(int L);
+int quad_persistent_max_sweeps(int L);
+long long quad_persistent_spin_limit();
+cudaError_t launch_quad_persistent(int sincos_mode, int reduce_mode, const QuadPersistArgs& p,
+                                   cudaStream_t stream);
+
 // Whether the fused four-replica kernel handles side L (a positive multiple of 32).
 bool quad_fused_supported(int L);
 

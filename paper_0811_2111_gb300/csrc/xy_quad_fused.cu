@@ -110,8 +110,21 @@ __device__ __forceinline__ void pair_nb(const CsArr& nb, int r, int c0, int q, P
   }
 }
 
-template <int MODE, int RED>
-__global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
+// One sweep of the tile (bx, by): the constants come from `a` (read where they
+// are used), the sweep's buffers, Philox sweep word and records from the
+// arguments.  COHERENT: `src` was written earlier in the same launch by other
+// CTAs (persistent kernel), so it is read through L2 (ld.global.cg).  `mid`
+// runs in every thread before the barrier between the red and the black half,
+// `end` after the tile's last store to dst and before the sums' barrier.
+template <int MODE, int RED, bool COHERENT, class MidHook = NoHook, class EndHook = NoHook>
+__device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const float* src,
+                                                float* dst, uint32_t sweep, xy_record* rec,
+                                                int bx, int by, const MidHook& mid = MidHook(),
+                                                const EndHook& end = EndHook()) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
   CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
@@ -121,9 +134,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
 
   const int L = a.L, W = a.W;
   const int F = 4 * W;                                     // elements per plane row
-  const int f0 = blockIdx.x * kTileF;                      // first element of the tile
+  const int f0 = bx * kTileF;                      // first element of the tile
   const int ks0 = f0 >> 2;                                 // its first site column
-  const int y0 = blockIdx.y * kTileRows;
+  const int y0 = by * kTileRows;
   const size_t plane = (size_t)L * (size_t)F;
 
   // ---- stage both planes (angle + unit vector) ----
@@ -144,7 +157,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
         const int p = rr < kSRows ? 1 : 0;
         const int r = rr < kSRows ? rr : rr - kSRows + 1;
         const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g;
-        v[i] = __ldg(reinterpret_cast<const float4*>(a.src + row));
+        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(src + row))
+                        : __ldg(reinterpret_cast<const float4*>(src + row));
       }
     }
 #pragma unroll
@@ -172,7 +186,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
       const int ks = side ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
       const size_t at = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + 4 * (size_t)ks;
       const int col = side ? kTileF + 4 : 0;
-      const float4 t = __ldg(reinterpret_cast<const float4*>(a.src + at));
+      const float4 t = COHERENT ? __ldcg(reinterpret_cast<const float4*>(src + at))
+                                : __ldg(reinterpret_cast<const float4*>(src + at));
       float s0, c0, s1, c1, s2, c2, s3, c3;
       xyd::unit_vector<MODE>(t.x, &s0, &c0);
       xyd::unit_vector<MODE>(t.y, &s1, &c1);
@@ -206,8 +221,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     PairNb n;
     pair_nb(cs[1], r, c0, q, n);
     const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, sweep, id1, 1u), a.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     n_acc[1] += r1.accept ? 1u : 0u;
     *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
-    *reinterpret_cast<float2*>(a.dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
+    *reinterpret_cast<float2*>(dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
   // elements 0..63: row -1; 64..127: row 32; 128..255: the halo site of rows
@@ -248,13 +263,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
     const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
     const uint4 w =
-        xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+        xyd::philox4x32_10(make_uint4(site, sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
                                                            w.x, w.y, replica_k(a, j), a.delta);
     th[0][r][sc] = res.th;
     cs[0][r][sc] = make_float2(res.c, res.s);
   }
+  mid();
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
@@ -263,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   for (int e = 0; e < 2; ++e)
 #pragma unroll
     for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
-  float* dst_blk = a.dst + plane;
+  float* dst_blk = dst + plane;
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -273,8 +289,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     PairNb n;
     pair_nb(cs[0], r, c0, q, n);
     const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, sweep, id1, 1u), a.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
@@ -304,6 +320,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     }
   }
 
+  end();
   // ---- per-replica sums: lanes of one parity -> warps -> FP64 -> records ----
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -327,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   }
   __syncthreads();
   if (warp != 0) return;
-  const bool first_block = blockIdx.x == 0 && blockIdx.y == 0;
+  const bool first_block = bx == 0 && by == 0;
   if (lane < kR) {
     unsigned long long total = 0;
     for (int w = 0; w < kWarps; ++w) total += cnt[w][lane];
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[lane].accepted), total);
-    if (first_block) a.rec[lane].beta = a.beta[lane];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&rec[lane].accepted), total);
+    if (first_block) rec[lane].beta = a.beta[lane];
   }
   if (lane >= kR * 5) return;
   // lanes 0..19 each own one (replica, sum)
@@ -351,11 +368,146 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   }
   const double scaled = d * (double)(1ll << XY_FX_SHIFT);
   if (!(fabs(scaled) < 9.0e18)) {
-    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec[jr].flags), 1ull);
+    atomicOr(reinterpret_cast<unsigned long long*>(&rec[jr].flags), 1ull);
     return;
   }
-  atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[jr].sum[si]),
+  atomicAdd(reinterpret_cast<unsigned long long*>(&rec[jr].sum[si]),
             (unsigned long long)__double2ll_rn(scaled));
+}
+
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
+  quad_sweep_body<MODE, RED, false>(a, a.src, a.dst, a.sweep, a.rec, blockIdx.x, blockIdx.y);
+}
+
+// Polls of a tile counter before a wait gives up (with a short sleep between
+// polls: about a second in all).
+constexpr long long kQuadSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned int q_load_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void q_store_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// All sweeps of a call in one cooperative launch (every CTA resident), the
+// scheme of the single-lattice persistent sweep: work items (sweep s, tile)
+// handed out in increasing order by one atomic counter, sweep-major, tile rows
+// folded (0, T-1, 1, T-2, ...); a tile's sweep s starts once its eight
+// neighbours and itself have published counters >= s (its halo of two rows and
+// one site reaches into all eight, and it overwrites the buffer they read
+// during sweep s - 1); it is published (s + 1) by warp 7 after the closing
+// barrier and a GPU-scope fence.  Warp 0 looks at the next item's nine
+// counters once, after the black half, and when all are set the next tile
+// neither waits nor takes the barrier in front of it.  Every wait is bounded;
+// one that runs out sets *error and ends the CTA, and waiting CTAs that see
+// *error end too.  The tile arithmetic is quad_sweep_body's, so the result is
+// bit for bit that of one k_quad_fused launch per sweep.
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kThreads, 3) k_quad_fused_persist(QuadPersistArgs p) {
+  __shared__ int s_abort;
+  __shared__ int s_item[2];
+  __shared__ int s_ready[2];
+  const int tiles_x = 4 * p.a.W / kTileF, tiles_y = p.a.L / kTileRows;
+  const int ntiles = tiles_x * tiles_y;
+  const int total = p.n_sweeps * ntiles;          // < 2^31 - 2^20 (the host splits longer runs)
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_item[0] = (int)atomicAdd(p.counter, 1u);
+    s_ready[0] = 0;
+  }
+  __syncthreads();
+  int par = 0;
+  int item = s_item[0];
+  while (item < total) {
+    const int s = item / ntiles;
+    const int k = item - s * ntiles;
+    const int prow = k / tiles_x;
+    const int bx = k - prow * tiles_x;
+    const int by = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+    const bool ready = s_ready[par] != 0;
+    if (s > 0 && threadIdx.x < 9 && !ready) {
+      const int d = threadIdx.x;
+      const int nx = wrap_once(bx + d % 3 - 1, tiles_x);
+      const int ny = wrap_once(by + d / 3 - 1, tiles_y);
+      const unsigned int* f = p.flags + (ny * tiles_x + nx);
+      long long it = 0;
+      while (q_load_acquire(f) < (unsigned int)s) {
+        if (++it > p.spin_limit ||
+            ((it & 255) == 0 && *reinterpret_cast<volatile unsigned int*>(p.error) != 0u)) {
+          atomicOr(p.error, 1u);
+          s_abort = 1;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    if (!ready) {
+      __syncthreads();
+      if (s_abort) return;            // read by every thread between the same two barriers
+    }
+    int next = 0;
+    if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u);
+    int* slot = &s_item[par ^ 1];
+    quad_sweep_body<MODE, RED, true>(
+        p.a, p.buf[s & 1], p.buf[(s + 1) & 1], p.sweep0 + (uint32_t)s, p.rec + (size_t)s * kR,
+        bx, by,
+        [&]() {
+          if (threadIdx.x == 0) *slot = next;
+        },
+        [&]() {
+          if (threadIdx.x < 32) {
+            bool ok = threadIdx.x >= 9;
+            const int ni = *slot;
+            if (threadIdx.x < 9 && ni < total) {
+              const int ns = ni / ntiles;
+              const int nk = ni - ns * ntiles;
+              const int nrow = nk / tiles_x;
+              const int nbx = nk - nrow * tiles_x;
+              const int nby = (nrow & 1) ? tiles_y - 1 - (nrow >> 1) : (nrow >> 1);
+              const int d = threadIdx.x;
+              const int nx = wrap_once(nbx + d % 3 - 1, tiles_x);
+              const int ny = wrap_once(nby + d / 3 - 1, tiles_y);
+              ok = ns == 0 || q_load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
+            }
+            const unsigned int all = __ballot_sync(0xffffffffu, ok);
+            if (threadIdx.x == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
+          }
+        });
+    if (threadIdx.x == kThreads - 32) {
+      // the closing barrier orders every thread's stores to dst before this
+      // GPU-scope fence, which is cumulative over them; then the counter
+      __threadfence();
+      q_store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
+    }
+    par ^= 1;
+    item = s_item[par];
+  }
+}
+
+template <int MODE, int RED>
+cudaError_t launch_persist_one(const QuadPersistArgs& p, cudaStream_t stream) {
+  auto fn = k_quad_fused_persist<MODE, RED>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, kSmemBytes);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int tiles = quad_persistent_tiles(p.a.L);
+  const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
+  // the tile counters and, after them, the work counter
+  e = cudaMemsetAsync(p.flags, 0, sizeof(unsigned int) * ((size_t)tiles + 1), stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<QuadPersistArgs*>(&p)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3(grid), dim3(kThreads),
+                                     args, kSmemBytes, stream);
 }
 
 template <int MODE, int RED>
@@ -391,6 +543,34 @@ cudaError_t launch_quad_fused(int sincos_mode, int reduce_mode, const QuadFusedA
     case 0: return comp ? launch_one<0, 1>(a, stream) : launch_one<0, 0>(a, stream);
     case 1: return comp ? launch_one<1, 1>(a, stream) : launch_one<1, 0>(a, stream);
     default: return comp ? launch_one<2, 1>(a, stream) : launch_one<2, 0>(a, stream);
+  }
+}
+
+}  // namespace xyk
+
+namespace xyk {
+
+int quad_persistent_tiles(int L) { return quad_fused_supported(L) ? (L / 32) * (L / kTileRows) : 0; }
+
+int quad_persistent_max_sweeps(int L) {
+  const int t = quad_persistent_tiles(L);
+  return t > 0 ? (int)((0x7fffffffu - (1u << 20)) / (unsigned)t) : 0;
+}
+
+long long quad_persistent_spin_limit() { return kQuadSpinLimit; }
+
+cudaError_t launch_quad_persistent(int sincos_mode, int reduce_mode, const QuadPersistArgs& p,
+                                   cudaStream_t stream) {
+  const int tiles = quad_persistent_tiles(p.a.L);
+  if (tiles == 0 || p.a.W * 2 != p.a.L || p.n_sweeps < 1 ||
+      p.n_sweeps > quad_persistent_max_sweeps(p.a.L) || p.buf[0] == p.buf[1] || !p.flags ||
+      p.counter != p.flags + tiles || !p.error || p.spin_limit < 1)
+    return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_persist_one<0, 1>(p, stream) : launch_persist_one<0, 0>(p, stream);
+    case 1: return comp ? launch_persist_one<1, 1>(p, stream) : launch_persist_one<1, 0>(p, stream);
+    default: return comp ? launch_persist_one<2, 1>(p, stream) : launch_persist_one<2, 0>(p, stream);
   }
 }
 

@@ -290,16 +290,17 @@ class Quad:
         p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
-                       "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
+                       "two_pass": X.XY_ALGO_TWO_PASS,
+                       "persistent": X.XY_ALGO_PERSISTENT}[algorithm]
         self.params = p
         with torch.cuda.device(self.device):
             self.q = X.xy_quad_create(p, betas, C.c_void_p(self.stream.cuda_stream))
 
     @property
     def algorithm(self):
-        """"fused" (one launch per sweep) or "two_pass"."""
-        a = X.xy_quad_algorithm(self.q)
-        return "fused" if a == X.XY_ALGO_FUSED else "two_pass"
+        """"persistent" (one launch per call), "fused" (one per sweep) or "two_pass"."""
+        return {X.XY_ALGO_FUSED: "fused", X.XY_ALGO_TWO_PASS: "two_pass",
+                X.XY_ALGO_PERSISTENT: "persistent"}[X.xy_quad_algorithm(self.q)]
 
     def sweep(self, n=1):
         X.xy_quad_sweep(self.q, n)

@@ -164,7 +164,7 @@ def test_quad_create_rejects_bad_parameters(lib):
     good = (C.c_double * 4)(1.0, 1.0, 1.0, 1.0)
     for kw in (dict(L=3), dict(L=0), dict(delta=0.0), dict(start=5), dict(sincos_mode=7),
                dict(reduce_mode=3), dict(J=float("nan")), dict(algorithm=9),
-               dict(L=34, algorithm=X.XY_ALGO_FUSED)):
+               dict(L=34, algorithm=X.XY_ALGO_PERSISTENT), dict(L=34, algorithm=X.XY_ALGO_FUSED)):
         assert lib.xy_quad_create(C.byref(_params(**kw)), good, None, C.byref(q)) == X.XY_EINVAL
         assert q.value is None
     assert "L % 32" in X.xy_quad_last_error(None)   # the last case: fused needs L % 32 == 0

@@ -30,10 +30,10 @@ BETAS = [0.7, 1.0, 1.12, 1.4]
 @pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "fp64"),
                                            ("accurate", "compensated"), ("libm", "fp64")])
 def test_replicas_equal_single_lattices(L, sincos, reduce):
-    """AUTO: the fused sweep for L % 32 == 0 (32, 64, 96, 256), two-pass otherwise."""
+    """AUTO: the persistent sweep for L % 32 == 0 (32, 64, 96, 256), two-pass otherwise."""
     sweeps = 7
     with Quad(L, BETAS, 19, sincos=sincos, reduce=reduce, lattice_id=40) as q:
-        assert q.algorithm == ("fused" if L % 32 == 0 else "two_pass")
+        assert q.algorithm == ("persistent" if L % 32 == 0 else "two_pass")
         q.sweep(sweeps)
         states = [q.state(r)[0] for r in range(4)]
         obs = [q.observables(r) for r in range(4)]
@@ -128,7 +128,46 @@ def test_fused_sweeps_in_pieces_equal_one_run():
 
 
 def test_fused_algorithm_needs_l_multiple_of_32():
-    with pytest.raises(X.XYError):
-        Quad(34, BETAS, 1, algorithm="fused")
+    for algo in ("fused", "persistent"):
+        with pytest.raises(X.XYError):
+            Quad(34, BETAS, 1, algorithm=algo)
     with Quad(34, BETAS, 1) as q:
         assert q.algorithm == "two_pass"
+    with Quad(1024, BETAS, 1) as q:
+        assert q.algorithm == "persistent"
+    with Quad(2048, BETAS, 1) as q:
+        assert q.algorithm == "fused"
+
+
+@pytest.mark.parametrize("L", [32, 64, 128, 512, 2048])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
+                                           ("libm", "fp64")])
+def test_persistent_equals_fused(L, sincos, reduce):
+    """All sweeps of a call in one cooperative launch against one fused launch
+    per sweep: angles, accept counts and records bit for bit (the same tile
+    arithmetic and per-tile partial sums; L = 32: one tile, its own neighbour
+    in every direction; 2048: 4096 tiles)."""
+    n = 13
+    out = {}
+    for algo in ("persistent", "fused"):
+        with Quad(L, BETAS, 37, sincos=sincos, reduce=reduce, lattice_id=3, algorithm=algo) as q:
+            assert q.algorithm == algo
+            q.sweep(n)
+            out[algo] = ([q.state(r)[0] for r in range(4)], [q.observables(r) for r in range(4)])
+    (sp, op), (sf, of) = out["persistent"], out["fused"]
+    for r in range(4):
+        assert np.array_equal(sp[r], sf[r]), r
+        for k in ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta"):
+            assert np.array_equal(op[r][k], of[r][k]), (r, k)
+
+
+def test_persistent_calls_split_anywhere():
+    with Quad(128, BETAS, 41, algorithm="persistent") as a, \
+            Quad(128, BETAS, 41, algorithm="persistent") as b:
+        for n in (1, 4, 3, 1):
+            a.sweep(n)
+        b.sweep(9)
+        for r in range(4):
+            sa, na = a.state(r)
+            sb, nb = b.state(r)
+            assert na == nb == 9 and np.array_equal(sa, sb)
