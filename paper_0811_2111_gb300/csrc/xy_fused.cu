@@ -459,10 +459,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
         });
     if (threadIdx.x == kThreads - 32) {
       // a warp other than the pollers' publishes the tile: the closing barrier
-      // orders every thread's stores to dst before this GPU-scope fence, which
-      // is cumulative over them (the grid barrier of cooperative groups relies
-      // on the same order); then the flag
-      __threadfence();
+      // orders every thread's stores to dst before this GPU-scope release,
+      // which is cumulative over the writes that happen before it
       store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
     }
     par ^= 1;

@@ -400,8 +400,8 @@ __device__ __forceinline__ void q_store_release(unsigned int* p, unsigned int v)
 // folded (0, T-1, 1, T-2, ...); a tile's sweep s starts once its eight
 // neighbours and itself have published counters >= s (its halo of two rows and
 // one site reaches into all eight, and it overwrites the buffer they read
-// during sweep s - 1); it is published (s + 1) by warp 7 after the closing
-// barrier and a GPU-scope fence.  Warp 0 looks at the next item's nine
+// during sweep s - 1); it is published (s + 1) by warp 7 with a GPU-scope
+// release store after the closing barrier.  Warp 0 looks at the next item's nine
 // counters once, after the black half, and when all are set the next tile
 // neither waits nor takes the barrier in front of it.  Every wait is bounded;
 // one that runs out sets *error and ends the CTA, and waiting CTAs that see
@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused_persist(QuadPersistA
         });
     if (threadIdx.x == kThreads - 32) {
       // the closing barrier orders every thread's stores to dst before this
-      // GPU-scope fence, which is cumulative over them; then the counter
-      __threadfence();
+      // GPU-scope release, which is cumulative over the writes that happen
+      // before it
       q_store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
     }
     par ^= 1;
