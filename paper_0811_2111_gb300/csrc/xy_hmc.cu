@@ -597,12 +597,9 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
   int pend_slot = -1;
   unsigned int pend_val = 0;
   // publish it: the caller has passed a CTA barrier after every thread's stores
-  // of that tile; the GPU-scope fence is cumulative over them
+  // of that tile; the GPU-scope release is cumulative over them
   auto publish = [&]() {
-    if (tid == kPublisher && pend_slot >= 0) {
-      __threadfence();
-      hmc_store_release(q.flags + pend_slot, pend_val);
-    }
+    if (tid == kPublisher && pend_slot >= 0) hmc_store_release(q.flags + pend_slot, pend_val);
     pend_slot = -1;
   };
 
