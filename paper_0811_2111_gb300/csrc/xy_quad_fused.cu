@@ -114,17 +114,33 @@ struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
-// One sweep of the tile (bx, by): the constants come from `a` (read where they
-// are used), the sweep's buffers, Philox sweep word and records from the
-// arguments.  COHERENT: `src` was written earlier in the same launch by other
-// CTAs (persistent kernel), so it is read through L2 (ld.global.cg).  `mid`
-// runs in every thread before the barrier between the red and the black half,
-// `end` after the tile's last store to dst and before the sums' barrier.
-template <int MODE, int RED, bool COHERENT, class MidHook = NoHook, class EndHook = NoHook>
-__device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const float* src,
-                                                float* dst, uint32_t sweep, xy_record* rec,
-                                                int bx, int by, const MidHook& mid = MidHook(),
+// A work item of the persistent kernel: its sweep's buffers, Philox sweep word
+// and records, and the launch's constants (left in parameter space).
+struct QuadItem {
+  const QuadFusedArgs& base;
+  const float* src;
+  float* dst;
+  uint32_t sweep;
+  xy_record* rec;
+};
+
+// The constants of a sweep (L, W, K, delta, rk, lattice_id0, beta).
+__device__ __forceinline__ const QuadFusedArgs& constants(const QuadFusedArgs& a) { return a; }
+__device__ __forceinline__ const QuadFusedArgs& constants(const QuadItem& a) { return a.base; }
+
+// One sweep of the tile (bx, by) of the sweep `a` describes (a QuadFusedArgs:
+// the per-sweep kernel passes its parameter, so every field is read from
+// parameter space where it is used; the persistent kernel a per-item copy).
+// COHERENT: `src` was written earlier in the same launch by other CTAs
+// (persistent kernel), so it is read through L2 (ld.global.cg).  `mid` runs in
+// every thread before the barrier between the red and the black half, `end`
+// after the tile's last store to dst and before the sums' barrier.
+template <int MODE, int RED, bool COHERENT, class Args, class MidHook = NoHook,
+          class EndHook = NoHook>
+__device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by,
+                                                const MidHook& mid = MidHook(),
                                                 const EndHook& end = EndHook()) {
+  const QuadFusedArgs& a = constants(item);
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
   CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
@@ -157,8 +173,8 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
         const int p = rr < kSRows ? 1 : 0;
         const int r = rr < kSRows ? rr : rr - kSRows + 1;
         const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g;
-        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(src + row))
-                        : __ldg(reinterpret_cast<const float4*>(src + row));
+        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(item.src + row))
+                        : __ldg(reinterpret_cast<const float4*>(item.src + row));
       }
     }
 #pragma unroll
@@ -186,8 +202,8 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
       const int ks = side ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
       const size_t at = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + 4 * (size_t)ks;
       const int col = side ? kTileF + 4 : 0;
-      const float4 t = COHERENT ? __ldcg(reinterpret_cast<const float4*>(src + at))
-                                : __ldg(reinterpret_cast<const float4*>(src + at));
+      const float4 t = COHERENT ? __ldcg(reinterpret_cast<const float4*>(item.src + at))
+                                : __ldg(reinterpret_cast<const float4*>(item.src + at));
       float s0, c0, s1, c1, s2, c2, s3, c3;
       xyd::unit_vector<MODE>(t.x, &s0, &c0);
       xyd::unit_vector<MODE>(t.y, &s1, &c1);
@@ -221,8 +237,8 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
     PairNb n;
     pair_nb(cs[1], r, c0, q, n);
     const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, sweep, id1, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, item.sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, item.sweep, id1, 1u), a.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -233,7 +249,7 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
     n_acc[1] += r1.accept ? 1u : 0u;
     *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
-    *reinterpret_cast<float2*>(dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
+    *reinterpret_cast<float2*>(item.dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
   // elements 0..63: row -1; 64..127: row 32; 128..255: the halo site of rows
@@ -263,7 +279,7 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
     const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
     const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
     const uint4 w =
-        xyd::philox4x32_10(make_uint4(site, sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+        xyd::philox4x32_10(make_uint4(site, item.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
                                                            w.x, w.y, replica_k(a, j), a.delta);
@@ -279,7 +295,7 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
   for (int e = 0; e < 2; ++e)
 #pragma unroll
     for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
-  float* dst_blk = dst + plane;
+  float* dst_blk = item.dst + plane;
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -289,8 +305,8 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
     PairNb n;
     pair_nb(cs[0], r, c0, q, n);
     const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, sweep, id1, 1u), a.rk);
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, item.sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, item.sweep, id1, 1u), a.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
@@ -348,8 +364,8 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
   if (lane < kR) {
     unsigned long long total = 0;
     for (int w = 0; w < kWarps; ++w) total += cnt[w][lane];
-    atomicAdd(reinterpret_cast<unsigned long long*>(&rec[lane].accepted), total);
-    if (first_block) rec[lane].beta = a.beta[lane];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&item.rec[lane].accepted), total);
+    if (first_block) item.rec[lane].beta = a.beta[lane];
   }
   if (lane >= kR * 5) return;
   // lanes 0..19 each own one (replica, sum)
@@ -368,16 +384,264 @@ __device__ __forceinline__ void quad_sweep_body(const QuadFusedArgs& a, const fl
   }
   const double scaled = d * (double)(1ll << XY_FX_SHIFT);
   if (!(fabs(scaled) < 9.0e18)) {
-    atomicOr(reinterpret_cast<unsigned long long*>(&rec[jr].flags), 1ull);
+    atomicOr(reinterpret_cast<unsigned long long*>(&item.rec[jr].flags), 1ull);
     return;
   }
-  atomicAdd(reinterpret_cast<unsigned long long*>(&rec[jr].sum[si]),
+  atomicAdd(reinterpret_cast<unsigned long long*>(&item.rec[jr].sum[si]),
             (unsigned long long)__double2ll_rn(scaled));
 }
 
+// The per-sweep kernel keeps its own copy of the tile arithmetic of
+// quad_sweep_body (identical statements; the two are tested bit for bit
+// against each other): compiled through the shared template body it issued
+// 2.5 % more instructions (363.7 M against 354.6 M warp instructions per
+// L = 4096 launch) and took 4 % longer.
 template <int MODE, int RED>
 __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
-  quad_sweep_body<MODE, RED, false>(a, a.src, a.dst, a.sweep, a.rec, blockIdx.x, blockIdx.y);
+  extern __shared__ __align__(16) unsigned char smem[];
+  ThArr* th = reinterpret_cast<ThArr*>(smem);
+  CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
+  float(*part)[kR][5][2] = reinterpret_cast<float(*)[kR][5][2]>(smem + kThBytes + kCsBytes);
+  unsigned int(*cnt)[kR] =
+      reinterpret_cast<unsigned int(*)[kR]>(smem + kThBytes + kCsBytes + kPartBytes);
+
+  const int L = a.L, W = a.W;
+  const int F = 4 * W;                                     // elements per plane row
+  const int f0 = blockIdx.x * kTileF;                      // first element of the tile
+  const int ks0 = f0 >> 2;                                 // its first site column
+  const int y0 = blockIdx.y * kTileRows;
+  const size_t plane = (size_t)L * (size_t)F;
+
+  // ---- stage both planes (angle + unit vector) ----
+  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
+  // (stage rows 1..34); 16 lanes per row, one float4 (one site, four
+  // replicas) per lane; the halo sites ks0 - 1 and ks0 + 16 (rows 1..34) are
+  // a separate pass taken by the last warps.
+  {
+    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
+    const int half = lane_s >> 4, g = lane_s & 15;
+    constexpr int kSteps = (kStageRowsTotal + 2 * kWarps - 1) / (2 * kWarps);
+    float4 v[kSteps];
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 2 * warp_s + half + 2 * kWarps * i;
+      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rr < kStageRowsTotal) {
+        const int p = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g;
+        v[i] = __ldg(reinterpret_cast<const float4*>(a.src + row));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 2 * warp_s + half + 2 * kWarps * i;
+      if (rr < kStageRowsTotal) {
+        const int p = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const int col = 4 + 4 * g;
+        float s0, c0, s1, c1, s2, c2, s3, c3;
+        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
+        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
+        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
+        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
+        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+      }
+    }
+    for (int h = kThreads - 1 - threadIdx.x; h < 2 * (kSRows - 2) * 2; h += kThreads) {
+      const int p = h / ((kSRows - 2) * 2);
+      const int rem = h - p * ((kSRows - 2) * 2);
+      const int r = 1 + (rem >> 1);
+      const int side = rem & 1;
+      const int ks = side ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
+      const size_t at = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + 4 * (size_t)ks;
+      const int col = side ? kTileF + 4 : 0;
+      const float4 t = __ldg(reinterpret_cast<const float4*>(a.src + at));
+      float s0, c0, s1, c1, s2, c2, s3, c3;
+      xyd::unit_vector<MODE>(t.x, &s0, &c0);
+      xyd::unit_vector<MODE>(t.y, &s1, &c1);
+      xyd::unit_vector<MODE>(t.z, &s2, &c2);
+      xyd::unit_vector<MODE>(t.w, &s3, &c3);
+      *reinterpret_cast<float4*>(&th[p][r][col]) = t;
+      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+    }
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t uL = (uint32_t)L;
+  const int c0 = 2 * lane + 4;                             // stage column of the lane's pair
+  const int fp = f0 + 2 * lane;                            // element of the pair
+  const int j0 = fp & 3;                                   // its replicas j0, j0 + 1
+  const uint32_t kq = (uint32_t)(fp >> 2);                 // its site column
+  const uint32_t id0 = a.lattice_id0 + (uint32_t)j0, id1 = id0 + 1u;
+  const float K0 = (lane & 1) ? a.K[2] : a.K[0];
+  const float K1 = (lane & 1) ? a.K[3] : a.K[1];
+  unsigned int n_acc[2] = {0u, 0u};
+
+  // ---- red half: the tile (counted, written to dst) ----
+#pragma unroll 2
+  for (int rr = 0; rr < 4; ++rr) {
+    const int ty = warp * 4 + rr;
+    const int y = y0 + ty;
+    const int r = ty + 2;
+    const int q = y & 1;                                   // red: x = 2k + (y & 1)
+    PairNb n;
+    pair_nb(cs[1], r, c0, q, n);
+    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K0, a.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K1, a.delta);
+    n_acc[0] += r0.accept ? 1u : 0u;
+    n_acc[1] += r1.accept ? 1u : 0u;
+    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
+    *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
+    *reinterpret_cast<float2*>(a.dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
+  }
+  // ---- red half: the ring at distance one (recomputed, not counted) ----
+  // elements 0..63: row -1; 64..127: row 32; 128..255: the halo site of rows
+  // 0..31 on the side the black tile reaches (left on odd rows, right on even)
+  {
+    const int i = threadIdx.x;
+    int ty, sc;
+    if (i < kTileF) {
+      ty = -1;
+      sc = 4 + i;
+    } else if (i < 2 * kTileF) {
+      ty = kTileRows;
+      sc = 4 + i - kTileF;
+    } else {
+      const int e = i - 2 * kTileF;
+      ty = e >> 2;
+      sc = (((y0 + ty) & 1) ? 0 : kTileF + 4) + (e & 3);
+    }
+    const int r = ty + 2;
+    const int y = wrap_once(y0 + ty, L);
+    const int q = y & 1;
+    const int ks = wrap_once(ks0 + ((sc - 4) >> 2), W);   // floor: stage columns 0..3 -> ks0 - 1
+    const int j = sc & 3;
+    const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)ks + (uint32_t)q;
+    const float2 l = cs[1][r][sc + 4 * q - 4], rt = cs[1][r][sc + 4 * q];
+    const float2 d = cs[1][r - 1][sc], u = cs[1][r + 1][sc];
+    const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+    const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+    const uint4 w =
+        xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+    const float2 own = cs[0][r][sc];
+    const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
+                                                           w.x, w.y, replica_k(a, j), a.delta);
+    th[0][r][sc] = res.th;
+    cs[0][r][sc] = make_float2(res.c, res.s);
+  }
+  __syncthreads();
+
+  // ---- black half of the tile, with the sweep sums ----
+  float acc[2][5], cmp[2][5];
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
+  float* dst_blk = a.dst + plane;
+#pragma unroll 2
+  for (int rr = 0; rr < 4; ++rr) {
+    const int ty = warp * 4 + rr;
+    const int y = y0 + ty;
+    const int r = ty + 2;
+    const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
+    PairNb n;
+    pair_nb(cs[0], r, c0, q, n);
+    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K0, a.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K1, a.delta);
+    n_acc[0] += r0.accept ? 1u : 0u;
+    n_acc[1] += r1.accept ? 1u : 0u;
+    *reinterpret_cast<float2*>(dst_blk + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
+
+    // red elements with the same (y, k, replica): their spins enter M once each
+    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    float v0[5], v1[5];
+    xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
+                       n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
+    xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
+                       n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (RED == 0) {
+        acc[0][i] += v0[i];
+        acc[1][i] += v1[i];
+      } else {
+        xyd::neumaier_add(acc[0][i], cmp[0][i], v0[i]);
+        xyd::neumaier_add(acc[1][i], cmp[1][i], v1[i]);
+      }
+    }
+  }
+
+  // ---- per-replica sums: lanes of one parity -> warps -> FP64 -> records ----
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    n_acc[e] = parity_sum(n_acc[e]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      acc[e][i] = parity_sum(acc[e][i]);
+      if (RED == 1) cmp[e][i] = parity_sum(cmp[e][i]);
+    }
+  }
+  if (lane < 2) {                                          // lane 0: replicas 0, 1; lane 1: 2, 3
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      cnt[warp][j0 + e] = n_acc[e];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        part[warp][j0 + e][i][0] = acc[e][i];
+        part[warp][j0 + e][i][1] = (RED == 1) ? cmp[e][i] : 0.f;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  const bool first_block = blockIdx.x == 0 && blockIdx.y == 0;
+  if (lane < kR) {
+    unsigned long long total = 0;
+    for (int w = 0; w < kWarps; ++w) total += cnt[w][lane];
+    atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[lane].accepted), total);
+    if (first_block) a.rec[lane].beta = a.beta[lane];
+  }
+  if (lane >= kR * 5) return;
+  // lanes 0..19 each own one (replica, sum)
+  const int jr = lane / 5, si = lane - 5 * jr;
+  double d;
+  if (RED == 0) {
+    d = 0.0;
+    for (int w = 0; w < kWarps; ++w) d += (double)part[w][jr][si][0];
+  } else {
+    float hi = 0.f, lo = 0.f;
+    for (int w = 0; w < kWarps; ++w) {
+      xyd::neumaier_add(hi, lo, part[w][jr][si][0]);
+      lo += part[w][jr][si][1];
+    }
+    d = (double)hi + (double)lo;
+  }
+  const double scaled = d * (double)(1ll << XY_FX_SHIFT);
+  if (!(fabs(scaled) < 9.0e18)) {
+    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec[jr].flags), 1ull);
+    return;
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[jr].sum[si]),
+            (unsigned long long)__double2ll_rn(scaled));
 }
 
 // Polls of a tile counter before a wait gives up (with a short sleep between
@@ -453,9 +717,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused_persist(QuadPersistA
     int next = 0;
     if (threadIdx.x == 0) next = (int)atomicAdd(p.counter, 1u);
     int* slot = &s_item[par ^ 1];
+    const QuadItem c{p.a, p.buf[s & 1], p.buf[(s + 1) & 1], p.sweep0 + (uint32_t)s,
+                     p.rec + (size_t)s * kR};
     quad_sweep_body<MODE, RED, true>(
-        p.a, p.buf[s & 1], p.buf[(s + 1) & 1], p.sweep0 + (uint32_t)s, p.rec + (size_t)s * kR,
-        bx, by,
+        c, bx, by,
         [&]() {
           if (threadIdx.x == 0) *slot = next;
         },
