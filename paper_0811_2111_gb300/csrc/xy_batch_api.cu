@@ -188,11 +188,12 @@ size_t band_bytes(bool fused, int rows, int L) {
 
 void make_plan(xy_batch* b, int target_sites) {
   const int CS = xyk::kClusterSize;
-  // fused algorithm: sides the single-lattice fused kernel takes go to groups
+  // fused algorithm: sides the single-lattice fused kernel takes (L % 128 ==
+  // 0), and the other multiples of 32 on the narrow tiles, go to groups
   std::map<int, std::vector<int>> groups;
   std::vector<int> banded;
   for (int i = 0; i < b->n; ++i) {
-    if (b->fused && xyk::fused_supported(b->L[i])) {
+    if (b->fused && (xyk::fused_supported(b->L[i]) || xyk::narrow_supported(b->L[i]))) {
       groups[b->L[i]].push_back(i);
     } else {
       banded.push_back(i);
@@ -204,7 +205,8 @@ void make_plan(xy_batch* b, int target_sites) {
   b->group_lattices.clear();
   for (auto& kv : groups) {
     const int L = kv.first;
-    const int tiles = (L / 2 / 64) * (L / 32);             // CTAs of one lattice's sweep
+    const int tiles = xyk::fused_supported(L) ? (L / 2 / 64) * (L / 32)   // CTAs of one
+                                              : xyk::narrow_tiles(L);      // lattice's sweep
     const int per = std::max(1, kGroupCtas / tiles);
     // as few groups as `per` allows, their sizes differing by at most one
     const int count = (int)kv.second.size();
@@ -372,8 +374,11 @@ cudaError_t enqueue_round(const xy_batch* b, cudaStream_t s) {
     cudaStream_t gs = b->branch_streams[g];
     e = cudaStreamWaitEvent(gs, b->ev_fork, 0);
     for (int sw = 0; sw < b->p.sweeps_per_round && e == cudaSuccess; ++sw)
-      e = xyk::launch_fused_batch_sweep(b->p.sincos_mode, b->p.reduce_mode, group_args(b, g, sw),
-                                        b->group_size[g], gs);
+      e = xyk::fused_supported(b->group_L[g])
+              ? xyk::launch_fused_batch_sweep(b->p.sincos_mode, b->p.reduce_mode,
+                                              group_args(b, g, sw), b->group_size[g], gs)
+              : xyk::launch_narrow_batch_sweep(b->p.sincos_mode, b->p.reduce_mode,
+                                               group_args(b, g, sw), b->group_size[g], gs);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_joins[g], gs);
   }
   if (e == cudaSuccess && b->n_ctas > 0)
@@ -590,6 +595,8 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
                                             b->cs_bytes + xyk::batch_smem_bytes(0));
     if (e == cudaSuccess && !b->group_L.empty())
       e = xyk::prepare_fused_batch(p->sincos_mode, p->reduce_mode);
+    if (e == cudaSuccess && !b->group_L.empty())
+      e = xyk::prepare_narrow_batch(p->sincos_mode, p->reduce_mode);
   }
   if (e == cudaSuccess) {
     step = "synchronize";

@@ -165,6 +165,14 @@ cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode);
 cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
                                      int n_lattices, cudaStream_t stream);
 
+// The same sweep on narrow tiles (32 rows x 16 plane columns, xy_narrow.cu)
+// for batch lattices of side L % 32 == 0 that the fused tiles do not fit.
+bool narrow_supported(int L);
+int narrow_tiles(int L);                       // CTAs of one lattice's sweep
+cudaError_t prepare_narrow_batch(int sincos_mode, int reduce_mode);
+cudaError_t launch_narrow_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
+                                      int n_lattices, cudaStream_t stream);
+
 // Unit vectors of n angles with the kernels' sincos of precision `mode`
 // (diagnostics and accuracy tests).
 cudaError_t launch_eval_unit_vector(int mode, const float* theta, float* c, float* s, int64_t n,

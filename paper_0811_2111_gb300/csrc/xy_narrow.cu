@@ -1,0 +1,311 @@
+// xy_narrow.cu -- the one-launch checkerboard sweep on narrow tiles, for the
+// batched engine's lattices whose side is a multiple of 32 but not of 128
+// (L = 32, 64, 96, ...), which the 32 x 64 tiles of xy_fused.cu do not fit.
+//
+// The scheme is xy_fused.cu's (one launch per sweep, src -> dst ping-pong):
+// a CTA owns a tile of 32 rows x 16 plane columns (32 natural columns) of both
+// colours, stages both planes plus two halo rows and one halo plane column as
+// (angle, cos, sin), updates the red sites of the tile and of the ring at
+// distance one around it (recomputed from the same old state and the same
+// counter-based Philox words as the neighbouring tiles' own updates, hence
+// identical), then the black sites against the new red ones with the sweep
+// sums, and writes the tile to dst.  Here each thread takes one pair of
+// adjacent plane columns of one row per colour (8 lanes per row, a warp per 4
+// rows), the staging 4 lanes per row.  Every site runs the single-lattice
+// arithmetic (xyd::metropolis_step etc.), so each lattice is bit for bit what
+// the single-lattice kernels make of it.
+//
+// Requires W = L/2 to be a multiple of 16 and L a multiple of 32 (L % 32 == 0).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "xy_device.cuh"
+#include "xy_internal.h"
+
+namespace xyk {
+
+namespace {
+
+constexpr int kNTileRows = 32;
+constexpr int kNTileK = 16;                   // plane columns
+constexpr int kNThreads = 256;
+constexpr int kNWarps = kNThreads / 32;
+constexpr int kNSRows = kNTileRows + 4;       // rows y0-2 .. y0+33
+constexpr int kNSCols = kNTileK + 8;          // plane cols k0-4 .. k0+19 (k0-1 .. k0+16 used)
+constexpr int kNRing = 2 * kNTileK + kNTileRows;          // 64 red ring sites
+constexpr int kNStageRowsTotal = kNSRows + (kNSRows - 2);  // black rows + red rows staged
+
+constexpr size_t kNThBytes = sizeof(float) * 2 * kNSRows * kNSCols;
+constexpr size_t kNCsBytes = sizeof(float2) * 2 * kNSRows * kNSCols;
+constexpr size_t kNPartBytes = sizeof(float) * kNWarps * 5 * 2;
+constexpr size_t kNCntBytes = sizeof(unsigned int) * kNWarps;
+constexpr size_t kNSmemBytes = kNThBytes + kNCsBytes + kNPartBytes + kNCntBytes;
+
+typedef float NThArr[kNSRows][kNSCols];
+typedef float2 NCsArr[kNSRows][kNSCols];
+
+__device__ __forceinline__ int nwrap(int v, int n) {
+  v += (v < 0) ? n : 0;
+  v -= (v >= n) ? n : 0;
+  return v;
+}
+
+// The four neighbour unit vectors of the two sites at stage columns c0, c0+1
+// of row r in plane `nb` (the other colour): same-row neighbours of a site at
+// column c are c+q-1 and c+q.
+struct NPair {
+  float Sc[2], Ss[2];
+  float2 l[2], r[2], d[2], u[2];
+};
+
+__device__ __forceinline__ void npair_neighbours(const NCsArr& nb, int r, int c0, int q, NPair& n) {
+  const float2 a = nb[r][c0 + q - 1], m = nb[r][c0 + q], b = nb[r][c0 + q + 1];
+  const float4 D = *reinterpret_cast<const float4*>(&nb[r - 1][c0]);
+  const float4 U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
+  n.l[0] = a;
+  n.r[0] = m;
+  n.l[1] = m;
+  n.r[1] = b;
+  n.d[0] = make_float2(D.x, D.y);
+  n.d[1] = make_float2(D.z, D.w);
+  n.u[0] = make_float2(U.x, U.y);
+  n.u[1] = make_float2(U.z, U.w);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    n.Sc[j] = xyd::nb_sum(n.l[j].x, n.r[j].x, n.d[j].x, n.u[j].x);
+    n.Ss[j] = xyd::nb_sum(n.l[j].y, n.r[j].y, n.d[j].y, n.u[j].y);
+  }
+}
+
+// One lattice of a batch group (blockIdx.z), one sweep: the sweep index comes
+// from the device counters and beta from the device (replica exchange moves
+// it); the state ping-pongs between the batch's two buffers by sweep parity.
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kNThreads, 3) k_sweep_narrow_batch(FusedBatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  NThArr* th = reinterpret_cast<NThArr*>(smem);
+  NCsArr* cs = reinterpret_cast<NCsArr*>(smem + kNThBytes);
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + kNThBytes + kNCsBytes);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kNThBytes + kNCsBytes + kNPartBytes);
+
+  const int li = b.lattices[blockIdx.z];
+  const uint32_t sweep = b.counters[0] + (uint32_t)b.s;
+  const float* src = ((sweep & 1u) ? b.theta2 : b.theta) + b.offset[li];
+  float* dst = ((sweep & 1u) ? b.theta : b.theta2) + b.offset[li];
+  const double beta = b.beta[li];
+  const float K = (float)(beta * b.J);
+  const uint32_t lid = b.lattice_id0 + (uint32_t)li;
+  xy_record* rec = b.records + (size_t)li * b.rec_stride + (sweep - b.rec_sweep0);
+
+  const int L = b.L, W = b.L / 2;
+  const int k0 = blockIdx.x * kNTileK;
+  const int y0 = blockIdx.y * kNTileRows;
+  const size_t plane = (size_t)L * (size_t)W;
+
+  // ---- stage both planes (angle + unit vector) ----
+  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
+  // (stage rows 1..34); 4 lanes per row, one float4 per lane; the halo
+  // columns k0-1 and k0+16 (rows 1..34) are a separate pass.
+  {
+    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
+    const int sub = lane_s >> 2, g = lane_s & 3;
+    constexpr int kRowsPerStep = 8 * kNWarps;
+    constexpr int kSteps = (kNStageRowsTotal + kRowsPerStep - 1) / kRowsPerStep;
+    float4 v[kSteps];
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 8 * warp_s + sub + kRowsPerStep * i;
+      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (rr < kNStageRowsTotal) {
+        const int p = rr < kNSRows ? 1 : 0;
+        const int r = rr < kNSRows ? rr : rr - kNSRows + 1;
+        const size_t row = p * plane + (size_t)nwrap(y0 - 2 + r, L) * W + k0 + 4 * g;
+        v[i] = __ldg(reinterpret_cast<const float4*>(src + row));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+      const int rr = 8 * warp_s + sub + kRowsPerStep * i;
+      if (rr < kNStageRowsTotal) {
+        const int p = rr < kNSRows ? 1 : 0;
+        const int r = rr < kNSRows ? rr : rr - kNSRows + 1;
+        const int col = 4 + 4 * g;
+        float s0, c0, s1, c1, s2, c2, s3, c3;
+        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
+        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
+        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
+        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
+        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+      }
+    }
+    for (int h = kNThreads - 1 - threadIdx.x; h < 2 * (kNSRows - 2) * 2; h += kNThreads) {
+      const int p = h / ((kNSRows - 2) * 2);
+      const int rem = h - p * ((kNSRows - 2) * 2);
+      const int r = 1 + (rem >> 1);
+      const int side = rem & 1;
+      const size_t row = p * plane + (size_t)nwrap(y0 - 2 + r, L) * W;
+      const int kk = side ? nwrap(k0 + kNTileK, W) : nwrap(k0 - 1, W);
+      const int col = side ? kNTileK + 4 : 3;
+      const float v1 = __ldg(src + row + kk);
+      float sv, cv;
+      xyd::unit_vector<MODE>(v1, &sv, &cv);
+      th[p][r][col] = v1;
+      cs[p][r][col] = make_float2(cv, sv);
+    }
+  }
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t uL = (uint32_t)L;
+  const int pr = lane & 7;                               // the thread's pair in its row
+  const int ty = warp * 4 + (lane >> 3);                 // its tile row
+  const int y = y0 + ty;
+  const int r = ty + 2;
+  const int c0 = 2 * pr + 4;                             // stage column of the pair
+  const int kp = k0 + 2 * pr;                            // plane column of the pair
+  unsigned int n_acc = 0;
+
+  // ---- red half: the tile (counted, written to dst) ----
+  {
+    const int q = y & 1;                                 // red: x = 2k + (y & 1)
+    NPair n;
+    npair_neighbours(cs[1], r, c0, q, n);
+    const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, sweep, lid, 1u), b.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K, b.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K, b.delta);
+    n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
+    *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
+    *reinterpret_cast<float2*>(dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
+  }
+  // ---- red half: the ring at distance one (recomputed, not counted) ----
+  // 64 sites on the first two warps, one per lane
+  if (threadIdx.x < kNRing) {
+    const int i = threadIdx.x;
+    int gy, tk;
+    if (i < kNTileK) {
+      gy = -1;
+      tk = i;
+    } else if (i < 2 * kNTileK) {
+      gy = kNTileRows;
+      tk = i - kNTileK;
+    } else {
+      gy = i - 2 * kNTileK;
+      tk = ((y0 + gy) & 1) ? -1 : kNTileK;               // left ring on odd rows, right on even
+    }
+    const int yy = nwrap(y0 + gy, L);
+    const int kk = nwrap(k0 + tk, W);
+    const int q = yy & 1;
+    const int rr = gy + 2, c = tk + 4;
+    const uint32_t site = (uint32_t)yy * uL + 2u * (uint32_t)kk + (uint32_t)q;
+    const float2 l = cs[1][rr][c + q - 1], rt = cs[1][rr][c + q];
+    const float2 d = cs[1][rr - 1][c], u = cs[1][rr + 1][c];
+    const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+    const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+    const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), b.rk);
+    const float2 own = cs[0][rr][c];
+    const xyd::SiteResult res =
+        xyd::metropolis_step<MODE>(th[0][rr][c], own.x, own.y, Sc, Ss, w.x, w.y, K, b.delta);
+    th[0][rr][c] = res.th;
+    cs[0][rr][c] = make_float2(res.c, res.s);
+  }
+  __syncthreads();
+
+  // ---- black half of the tile, with the sweep sums ----
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  {
+    const int q = (y + 1) & 1;                           // black: x = 2k + ((y + 1) & 1)
+    NPair n;
+    npair_neighbours(cs[0], r, c0, q, n);
+    const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
+    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
+    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, sweep, lid, 1u), b.rk);
+    const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
+    const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K, b.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K, b.delta);
+    n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+    *reinterpret_cast<float2*>(dst + plane + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
+
+    // red sites with the same (y, k): their spins enter M once each
+    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    float v0[5], v1[5];
+    xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
+                       n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
+    xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
+                       n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      if (RED == 0) {
+        acc[i] += v0[i] + v1[i];
+      } else {
+        xyd::neumaier_add(acc[i], cmp[i], v0[i]);
+        xyd::neumaier_add(acc[i], cmp[i], v1[i]);
+      }
+    }
+  }
+  xyd::commit_block<kNWarps, RED, true>(acc, cmp, n_acc, part, cnt, rec, beta,
+                                        blockIdx.x == 0 && blockIdx.y == 0);
+}
+
+template <int MODE, int RED>
+cudaError_t prepare_narrow_one() {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_narrow_batch<MODE, RED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_narrow_batch<MODE, RED>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
+template <int MODE, int RED>
+cudaError_t launch_narrow_one(const FusedBatchArgs& b, int n_lattices, cudaStream_t stream) {
+  const dim3 grid(b.L / 2 / kNTileK, b.L / kNTileRows, n_lattices);
+  k_sweep_narrow_batch<MODE, RED><<<grid, kNThreads, kNSmemBytes, stream>>>(b);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool narrow_supported(int L) { return L >= 32 && (L % 32) == 0; }
+
+int narrow_tiles(int L) { return narrow_supported(L) ? (L / 2 / kNTileK) * (L / kNTileRows) : 0; }
+
+cudaError_t prepare_narrow_batch(int sincos_mode, int reduce_mode) {
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? prepare_narrow_one<0, 1>() : prepare_narrow_one<0, 0>();
+    case 1: return comp ? prepare_narrow_one<1, 1>() : prepare_narrow_one<1, 0>();
+    default: return comp ? prepare_narrow_one<2, 1>() : prepare_narrow_one<2, 0>();
+  }
+}
+
+cudaError_t launch_narrow_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
+                                      int n_lattices, cudaStream_t stream) {
+  if (!narrow_supported(b.L) || n_lattices < 1) return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0:
+      return comp ? launch_narrow_one<0, 1>(b, n_lattices, stream)
+                  : launch_narrow_one<0, 0>(b, n_lattices, stream);
+    case 1:
+      return comp ? launch_narrow_one<1, 1>(b, n_lattices, stream)
+                  : launch_narrow_one<1, 0>(b, n_lattices, stream);
+    default:
+      return comp ? launch_narrow_one<2, 1>(b, n_lattices, stream)
+                  : launch_narrow_one<2, 0>(b, n_lattices, stream);
+  }
+}
+
+}  // namespace xyk

@@ -58,6 +58,34 @@ def test_batch_matches_single_lattices(sincos, algorithm):
             assert np.max(np.abs(obs[i][k] - o[k])) <= tol, (L, k)
 
 
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
+                                           ("libm", "fp64")])
+def test_narrow_tiles_match_single_lattices(sincos, reduce):
+    """Sides that are multiples of 32 but not of 128 run on the narrow tiles
+    (32 rows x 16 plane columns): one tile (32), 2 x 2 (64), 3 x 3 (96), 5 x 5
+    (160, not a power of two) and 6 x 6 (192) tiles per lattice, several lattices
+    of a side in one launch, against the single-lattice two-pass kernels."""
+    Ls = [32, 64, 96, 160, 192, 32, 96]
+    betas = [0.8, 1.0, 1.12, 1.3, 0.9, 1.2, 0.7]
+    with Batch(Ls, betas, 31, lattice_id0=3, sweeps_per_round=3, sincos=sincos,
+               reduce=reduce) as b:
+        b.run(3)
+        states = [b.state(i) for i in range(len(Ls))]
+        obs = [b.observables(i) for i in range(len(Ls))]
+        assert b.info()[3] == 0                       # no lattice left for the cluster launch
+    for i, (L, beta) in enumerate(zip(Ls, betas)):
+        with Lattice(L, beta, 31, lattice_id=3 + i, sincos=sincos, reduce=reduce,
+                     algorithm="two_pass") as lat:
+            lat.sweep(9)
+            s, _ = lat.state()
+            o = lat.observables()
+        assert np.array_equal(states[i], s), f"L={L}"
+        assert np.array_equal(obs[i]["accepted"], o["accepted"]), f"L={L}"
+        tol = record_tolerance(L * L, fast=(sincos == "fast"))
+        for k in ("C", "Ix", "Iy", "Mx", "My"):
+            assert np.max(np.abs(obs[i][k] - o[k])) <= tol, (L, k)
+
+
 def test_fused_batch_state_after_odd_sweeps():
     with Batch([16, 256], [1.0, 1.1], 4, sweeps_per_round=3) as b:
         b.run(1)
@@ -136,8 +164,10 @@ def test_replica_exchange_configuration_runs():
     with Batch(Ls, betas, WL.BATCH_SEED, ladders=ladders, sweeps_per_round=10) as b:
         b.run(20)
         n, nrec, nxt, n_ctas = b.info()
-        # L = 256: 16 CTAs per lattice, groups of 8; L = 128: 4 CTAs, one group of 32
-        assert b.launches_per_round() == (4 + 1) * 10 + 1 + 1
+        # fused tiles: L = 256 (16 CTAs per lattice, 4 groups of 8), L = 128 (4 CTAs,
+        # one group); narrow tiles: L = 96 (9 CTAs, 3 groups of 11, 11, 10), 64 (4,
+        # one group), 32 (1, one group); L = 16, 24, 48 in the cluster launch
+        assert b.launches_per_round() == (4 + 1 + 3 + 1 + 1) * 10 + 1 + 1
         bl = b.betas()
         slots, acc, att = b.exchange_stats()
         e0 = b.observables(0)["e"]
