@@ -10,10 +10,10 @@
 // counter-based Philox words as the neighbouring tiles' own updates, hence
 // identical), then the black sites against the new red ones with the sweep
 // sums, and writes the tile to dst.  Here each thread takes one pair of
-// adjacent plane columns of one row per colour (8 lanes per row, a warp per 4
-// rows), the staging 4 lanes per row.  Every site runs the single-lattice
-// arithmetic (xyd::metropolis_step etc.), so each lattice is bit for bit what
-// the single-lattice kernels make of it.
+// adjacent plane columns in two rows (ty and ty + 16) per colour (8 lanes per
+// row, four warps of 4 rows each), the staging 4 lanes per row.  Every site
+// runs the single-lattice arithmetic (xyd::metropolis_step etc.), so each
+// lattice is bit for bit what the single-lattice kernels make of it.
 //
 // Requires W = L/2 to be a multiple of 16 and L a multiple of 32 (L % 32 == 0).
 #include <cuda_runtime.h>
@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kNTileRows = 32;
 constexpr int kNTileK = 16;                   // plane columns
-constexpr int kNThreads = 256;
+constexpr int kNThreads = 128;
 constexpr int kNWarps = kNThreads / 32;
 constexpr int kNSRows = kNTileRows + 4;       // rows y0-2 .. y0+33
 constexpr int kNSCols = kNTileK + 8;          // plane cols k0-4 .. k0+19 (k0-1 .. k0+16 used)
@@ -81,7 +81,7 @@ __device__ __forceinline__ void npair_neighbours(const NCsArr& nb, int r, int c0
 // from the device counters and beta from the device (replica exchange moves
 // it); the state ping-pongs between the batch's two buffers by sweep parity.
 template <int MODE, int RED>
-__global__ void __launch_bounds__(kNThreads, 3) k_sweep_narrow_batch(FusedBatchArgs b) {
+__global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchArgs b) {
   extern __shared__ __align__(16) unsigned char smem[];
   NThArr* th = reinterpret_cast<NThArr*>(smem);
   NCsArr* cs = reinterpret_cast<NCsArr*>(smem + kNThBytes);
@@ -159,16 +159,17 @@ __global__ void __launch_bounds__(kNThreads, 3) k_sweep_narrow_batch(FusedBatchA
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t uL = (uint32_t)L;
-  const int pr = lane & 7;                               // the thread's pair in its row
-  const int ty = warp * 4 + (lane >> 3);                 // its tile row
-  const int y = y0 + ty;
-  const int r = ty + 2;
+  const int pr = lane & 7;                               // the thread's pair in its rows
   const int c0 = 2 * pr + 4;                             // stage column of the pair
   const int kp = k0 + 2 * pr;                            // plane column of the pair
   unsigned int n_acc = 0;
 
   // ---- red half: the tile (counted, written to dst) ----
-  {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int ty = warp * 4 + (lane >> 3) + 16 * half;   // the tile row
+    const int y = y0 + ty;
+    const int r = ty + 2;
     const int q = y & 1;                                 // red: x = 2k + (y & 1)
     NPair n;
     npair_neighbours(cs[1], r, c0, q, n);
@@ -222,7 +223,11 @@ __global__ void __launch_bounds__(kNThreads, 3) k_sweep_narrow_batch(FusedBatchA
   // ---- black half of the tile, with the sweep sums ----
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  {
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int ty = warp * 4 + (lane >> 3) + 16 * half;   // the tile row
+    const int y = y0 + ty;
+    const int r = ty + 2;
     const int q = (y + 1) & 1;                           // black: x = 2k + ((y + 1) & 1)
     NPair n;
     npair_neighbours(cs[0], r, c0, q, n);
