@@ -402,8 +402,8 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
         cpu = L * L * n / dt
         out[str(L)] = {"gpu": gpu, "oracle_1core": cpu, "gain": gpu / cpu}
         if L <= 256:
-            # a single small lattice through the batched engine: one cluster-launched
-            # kernel runs 100 sweeps (bit-identical to the single-lattice kernels)
+            # a single lattice through the batched engine: one graph launch runs 100
+            # sweeps of fused tiles (bit-identical to the single-lattice kernels)
             from paper_0811_2111_gb300.lattice import Batch
             rounds = max(2, int(2e9 // (L * L * 100)))
             with Batch([L], [1.0], 3, sweeps_per_round=100, sincos=sincos, device=dev) as b:

@@ -98,6 +98,10 @@ struct xy_batch {
   std::vector<int> group_L, group_start, group_size;
   std::vector<int32_t> group_lattices;
   int32_t* d_groups = nullptr;
+  // lattices small enough for one CTA's shared memory: a whole round per launch
+  std::vector<int32_t> small_lattices;
+  int32_t* d_small = nullptr;
+  size_t small_smem = 0;
   std::vector<cudaStream_t> branch_streams;
   std::vector<cudaEvent_t> ev_joins;
   cudaEvent_t ev_fork = nullptr;
@@ -157,7 +161,7 @@ void free_all(xy_batch* b) {
   void* ptrs[] = {b->d_theta, b->d_theta2, b->d_offset, b->d_L, b->d_beta, b->d_bands, b->d_rec,
                   b->d_counters, b->d_pair_ladder, b->d_pair_pos, b->d_ladder_start,
                   b->d_pos_lattice, b->d_pos_beta, b->d_acc, b->d_att, b->d_scratch,
-                  b->d_partials, b->d_groups};
+                  b->d_partials, b->d_groups, b->d_small};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
@@ -189,16 +193,29 @@ size_t band_bytes(bool fused, int rows, int L) {
 void make_plan(xy_batch* b, int target_sites) {
   const int CS = xyk::kClusterSize;
   // fused algorithm: sides the single-lattice fused kernel takes (L % 128 ==
-  // 0), and the other multiples of 32 on the narrow tiles, go to groups
+  // 0) go to groups; lattices that fit one CTA's shared memory run whole
+  // rounds in one launch; the other multiples of 32 go to groups on the narrow
+  // tiles; the rest to the cluster-launched bands
   std::map<int, std::vector<int>> groups;
   std::vector<int> banded;
+  b->small_lattices.clear();
+  b->small_smem = 0;
   for (int i = 0; i < b->n; ++i) {
-    if (b->fused && (xyk::fused_supported(b->L[i]) || xyk::narrow_supported(b->L[i]))) {
-      groups[b->L[i]].push_back(i);
+    const int Li = b->L[i];
+    if (b->fused && xyk::fused_supported(Li)) {
+      groups[Li].push_back(i);
+    } else if (b->fused && xyk::small_supported(Li)) {
+      b->small_lattices.push_back(i);
+      b->small_smem = std::max(b->small_smem, xyk::small_smem_bytes(Li));
+    } else if (b->fused && xyk::narrow_supported(Li)) {
+      groups[Li].push_back(i);
     } else {
       banded.push_back(i);
     }
   }
+  // the largest lattices first, so they start first
+  std::stable_sort(b->small_lattices.begin(), b->small_lattices.end(),
+                   [&](int x, int y) { return b->L[x] > b->L[y]; });
   b->group_L.clear();
   b->group_start.clear();
   b->group_size.clear();
@@ -381,6 +398,26 @@ cudaError_t enqueue_round(const xy_batch* b, cudaStream_t s) {
                                                group_args(b, g, sw), b->group_size[g], gs);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_joins[g], gs);
   }
+  if (e == cudaSuccess && !b->small_lattices.empty()) {
+    xyk::SmallBatchArgs sa;
+    sa.theta = b->d_theta;
+    sa.theta2 = b->d_theta2;
+    sa.offset = b->d_offset;
+    sa.L = b->d_L;
+    sa.beta = b->d_beta;
+    sa.lattices = b->d_small;
+    sa.records = b->d_rec;
+    sa.rec_stride = b->rec_cap;
+    sa.rec_sweep0 = 0;
+    sa.counters = b->d_counters;
+    sa.sweeps = b->p.sweeps_per_round;
+    sa.J = b->p.J;
+    sa.delta = (float)b->p.delta;
+    sa.rk = xyd::make_round_keys(b->p.seed);
+    sa.lattice_id0 = b->p.lattice_id0;
+    e = xyk::launch_small_batch(b->p.sincos_mode, b->p.reduce_mode, sa,
+                                (int)b->small_lattices.size(), b->small_smem, s);
+  }
   if (e == cudaSuccess && b->n_ctas > 0)
     e = b->fused ? xyk::launch_batch_fused(b->p.sincos_mode, b->p.reduce_mode, round_args(b),
                                            b->n_ctas, s)
@@ -549,6 +586,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   alloc((void**)&b->d_scratch, sizeof(float) * (size_t)maxN);
   alloc((void**)&b->d_partials, sizeof(double) * (size_t)b->n * xyk::kMaxSegments * xyk::kPartials);
   alloc((void**)&b->d_groups, sizeof(int32_t) * b->group_lattices.size());
+  alloc((void**)&b->d_small, sizeof(int32_t) * b->small_lattices.size());
   if (e == cudaSuccess && !b->group_L.empty()) {
     step = "branch streams";
     e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
@@ -579,6 +617,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   h2d(b->d_pos_lattice, pos_lattice.data(), sizeof(int32_t) * b->n_slots);
   h2d(b->d_pos_beta, pos_beta.data(), sizeof(double) * b->n_slots);
   h2d(b->d_groups, b->group_lattices.data(), sizeof(int32_t) * b->group_lattices.size());
+  h2d(b->d_small, b->small_lattices.data(), sizeof(int32_t) * b->small_lattices.size());
   if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(uint32_t) * 2);
   if (e == cudaSuccess) e = cudaMemset(b->d_acc, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
   if (e == cudaSuccess) e = cudaMemset(b->d_att, 0, sizeof(unsigned long long) * std::max(b->n_slots, 1));
@@ -597,6 +636,8 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
       e = xyk::prepare_fused_batch(p->sincos_mode, p->reduce_mode);
     if (e == cudaSuccess && !b->group_L.empty())
       e = xyk::prepare_narrow_batch(p->sincos_mode, p->reduce_mode);
+    if (e == cudaSuccess && !b->small_lattices.empty())
+      e = xyk::prepare_small_batch(p->sincos_mode, p->reduce_mode, b->small_smem);
   }
   if (e == cudaSuccess) {
     step = "synchronize";
@@ -655,7 +696,8 @@ xy_status xy_batch_launches_per_round(const xy_batch* b, int32_t* launches) {
     bmsg("xy_batch_launches_per_round: NULL output");
     return XY_EINVAL;
   }
-  *launches = (int32_t)b->group_L.size() * b->p.sweeps_per_round + (b->n_ctas > 0 ? 1 : 0) + 1;
+  *launches = (int32_t)b->group_L.size() * b->p.sweeps_per_round + (b->n_ctas > 0 ? 1 : 0) +
+              (b->small_lattices.empty() ? 0 : 1) + 1;
   return XY_OK;
 }
 

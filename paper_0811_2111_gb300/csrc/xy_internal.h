@@ -173,6 +173,32 @@ cudaError_t prepare_narrow_batch(int sincos_mode, int reduce_mode);
 cudaError_t launch_narrow_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
                                       int n_lattices, cudaStream_t stream);
 
+// Whole lattices in one CTA's shared memory, all sweeps of a round per launch
+// (xy_narrow.cu), for batch lattices with small_supported(L).
+struct SmallBatchArgs {
+  float* theta;                 // batch buffer read on even sweeps, written on odd ones
+  float* theta2;                // the other buffer
+  const int64_t* offset;        // [n] floats from a buffer's start to lattice i
+  const int32_t* L;             // [n]
+  const double* beta;           // [n] current beta (device)
+  const int32_t* lattices;      // [grid] the lattice of each CTA
+  xy_record* records;           // [n][rec_stride]
+  int64_t rec_stride;
+  uint32_t rec_sweep0;
+  const uint32_t* counters;     // [0] first sweep of the round
+  int sweeps;                   // sweeps of the round
+  double J;
+  float delta;
+  xyd::RoundKeys rk;
+  uint32_t lattice_id0;
+};
+constexpr size_t kSmallBudget = 112 * 1024;    // shared memory of one lattice (L <= 96)
+size_t small_smem_bytes(int L);
+bool small_supported(int L);
+cudaError_t prepare_small_batch(int sincos_mode, int reduce_mode, size_t smem);
+cudaError_t launch_small_batch(int sincos_mode, int reduce_mode, const SmallBatchArgs& a,
+                               int n_lattices, size_t smem, cudaStream_t stream);
+
 // Unit vectors of n angles with the kernels' sincos of precision `mode`
 // (diagnostics and accuracy tests).
 cudaError_t launch_eval_unit_vector(int mode, const float* theta, float* c, float* s, int64_t n,

@@ -314,3 +314,192 @@ cudaError_t launch_narrow_batch_sweep(int sincos_mode, int reduce_mode, const Fu
 }
 
 }  // namespace xyk
+
+// ---------------------------------------------------------------------------
+// Whole lattices in one CTA: the batch's lattices small enough for one CTA's
+// shared memory (12 bytes per site: angle and unit vector) run all sweeps of a
+// round in one launch, one CTA per lattice, the lattice never leaving shared
+// memory between the round's first read and last write.  A half-sweep is a
+// pass over the sites of one colour against the other colour's unit vectors
+// (periodic neighbours straight from shared memory: no halo, no recomputed
+// ring), with a barrier between the halves.  Each site's unit vector is
+// computed once at the start and then carried: after an update it is the one
+// xyd::metropolis_step returns (the proposal's if accepted, else the old
+// one), which is exactly what recomputing it from the stored angle would give,
+// so every site update -- and each lattice's state -- is bit for bit that of
+// the single-lattice kernels, at one sincos per update instead of two.
+// ---------------------------------------------------------------------------
+namespace xyk {
+
+namespace {
+
+constexpr int kSThreads = 256;
+constexpr int kSWarps = kSThreads / 32;
+constexpr size_t kSTailBytes = sizeof(float) * kSWarps * 5 * 2 + sizeof(unsigned int) * kSWarps;
+
+template <int MODE, int RED>
+__global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int li = a.lattices[blockIdx.x];
+  const int L = a.L[li], W = L / 2;
+  const int half = L * W;                                   // sites per colour
+  float* th = reinterpret_cast<float*>(smem);               // [2][L][W]
+  float2* cs = reinterpret_cast<float2*>(smem + (((size_t)2 * half * sizeof(float) + 15) & ~(size_t)15));
+  unsigned char* tail = reinterpret_cast<unsigned char*>(cs + 2 * half);
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(tail);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(tail + sizeof(float) * kSWarps * 5 * 2);
+
+  const uint32_t sweep0 = a.counters[0];
+  const uint32_t last = sweep0 + (uint32_t)a.sweeps - 1u;
+  const float* src = ((sweep0 & 1u) ? a.theta2 : a.theta) + a.offset[li];
+  float* dst = ((last & 1u) ? a.theta : a.theta2) + a.offset[li];
+  const double beta = a.beta[li];
+  const float K = (float)(beta * a.J);
+  const uint32_t lid = a.lattice_id0 + (uint32_t)li;
+  const uint32_t uL = (uint32_t)L;
+  // a half-sweep spreads one colour's L*W sites evenly over the threads (a
+  // warp may straddle rows): thread t starts at flat index t = y0*W + k0 and
+  // steps by kSThreads = dy*W + dk, the (y, k) carried without a division
+  const int y0 = threadIdx.x / W, k0 = threadIdx.x % W;
+  const int dy = kSThreads / W, dk = kSThreads % W;
+  auto step_site = [&](int& y, int& k) {
+    k += dk;
+    y += dy;
+    if (k >= W) {
+      k -= W;
+      ++y;
+    }
+  };
+
+  for (int i = threadIdx.x; i < 2 * half; i += kSThreads) {
+    const float t = __ldg(src + i);
+    float s, c;
+    xyd::unit_vector<MODE>(t, &s, &c);
+    th[i] = t;
+    cs[i] = make_float2(c, s);
+  }
+  __syncthreads();
+
+  for (int sw = 0; sw < a.sweeps; ++sw) {
+    const uint32_t sweep = sweep0 + (uint32_t)sw;
+    unsigned int n_acc = 0;
+    // ---- red half: red site (y, k) is x = 2k + (y & 1); its black
+    // neighbours (y, k+q-1), (y, k+q), (y-1, k), (y+1, k) ----
+    for (int o = threadIdx.x, y = y0, k = k0; o < half; o += kSThreads) {
+      const int q = y & 1;
+      const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+      int kl = k + q - 1, kr = k + q;
+      kl += kl < 0 ? W : 0;
+      kr -= kr >= W ? W : 0;
+      const float2 l = cs[half + y * W + kl], rt = cs[half + y * W + kr];
+      const float2 d = cs[half + yd * W + k], u = cs[half + yu * W + k];
+      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+      const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+      const float2 own = cs[o];
+      const xyd::SiteResult res =
+          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, w.x, w.y, K, a.delta);
+      th[o] = res.th;
+      cs[o] = make_float2(res.c, res.s);
+      n_acc += res.accept ? 1u : 0u;
+      step_site(y, k);
+    }
+    __syncthreads();
+    // ---- black half, with the sweep sums: black site (y, k) is
+    // x = 2k + ((y + 1) & 1); its red neighbours as above ----
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int i = threadIdx.x, y = y0, k = k0; i < half; i += kSThreads) {
+      const int q = (y + 1) & 1;
+      const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+      int kl = k + q - 1, kr = k + q;
+      kl += kl < 0 ? W : 0;
+      kr -= kr >= W ? W : 0;
+      const float2 l = cs[y * W + kl], rt = cs[y * W + kr];
+      const float2 d = cs[yd * W + k], u = cs[yu * W + k];
+      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
+      const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+      const int o = half + i;
+      const float2 own = cs[o];
+      const xyd::SiteResult res =
+          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, w.x, w.y, K, a.delta);
+      th[o] = res.th;
+      cs[o] = make_float2(res.c, res.s);
+      n_acc += res.accept ? 1u : 0u;
+      // the red site with the same (y, k): its spin enters M once
+      const float2 m = cs[i];
+      float v[5];
+      xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc, Ss, m.x,
+                         m.y, v);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        if (RED == 0) {
+          acc[j] += v[j];
+        } else {
+          xyd::neumaier_add(acc[j], cmp[j], v[j]);
+        }
+      }
+      step_site(y, k);
+    }
+    // (its barrier also ends the black half before the next sweep's red half)
+    xyd::commit_block<kSWarps, RED, true>(
+        acc, cmp, n_acc, part, cnt,
+        a.records + (size_t)li * a.rec_stride + (sweep - a.rec_sweep0), beta, true);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * half; i += kSThreads) dst[i] = th[i];
+}
+
+template <int MODE, int RED>
+cudaError_t launch_small_one(const SmallBatchArgs& a, int n_lattices, size_t smem,
+                             cudaStream_t stream) {
+  k_batch_small<MODE, RED><<<n_lattices, kSThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE, int RED>
+cudaError_t prepare_small_one(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch_small<MODE, RED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_small<MODE, RED>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
+}  // namespace
+
+size_t small_smem_bytes(int L) {
+  const size_t half = (size_t)L * (size_t)(L / 2);
+  return ((2 * half * sizeof(float) + 15) & ~(size_t)15) + 2 * half * sizeof(float2) + kSTailBytes;
+}
+
+bool small_supported(int L) { return L >= 2 && (L % 2) == 0 && small_smem_bytes(L) <= kSmallBudget; }
+
+cudaError_t prepare_small_batch(int sincos_mode, int reduce_mode, size_t smem) {
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? prepare_small_one<0, 1>(smem) : prepare_small_one<0, 0>(smem);
+    case 1: return comp ? prepare_small_one<1, 1>(smem) : prepare_small_one<1, 0>(smem);
+    default: return comp ? prepare_small_one<2, 1>(smem) : prepare_small_one<2, 0>(smem);
+  }
+}
+
+cudaError_t launch_small_batch(int sincos_mode, int reduce_mode, const SmallBatchArgs& a,
+                               int n_lattices, size_t smem, cudaStream_t stream) {
+  if (n_lattices < 1 || a.sweeps < 1 || smem > kSmallBudget) return cudaErrorInvalidValue;
+  const bool comp = reduce_mode != 0;
+  switch (sincos_mode) {
+    case 0: return comp ? launch_small_one<0, 1>(a, n_lattices, smem, stream)
+                        : launch_small_one<0, 0>(a, n_lattices, smem, stream);
+    case 1: return comp ? launch_small_one<1, 1>(a, n_lattices, smem, stream)
+                        : launch_small_one<1, 0>(a, n_lattices, smem, stream);
+    default: return comp ? launch_small_one<2, 1>(a, n_lattices, smem, stream)
+                         : launch_small_one<2, 0>(a, n_lattices, smem, stream);
+  }
+}
+
+}  // namespace xyk

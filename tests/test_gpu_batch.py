@@ -27,8 +27,9 @@ from paper_0811_2111_gb300.lattice import Batch, Lattice  # noqa: E402
 from paper_0811_2111_gb300 import _lib as X  # noqa: E402
 from paper_0811_2111_gb300 import workloads as WL  # noqa: E402
 
-LS = [2, 6, 16, 24, 48, 96, 128, 256]
-BETAS = [0.7, 0.9, 1.0, 1.1, 1.2, 0.95, 1.05, 1.12]
+# whole-lattice path (2 ... 96), large tiles (128, 256), cluster bands (100, 130)
+LS = [2, 6, 16, 24, 48, 96, 128, 256, 100, 130]
+BETAS = [0.7, 0.9, 1.0, 1.1, 1.2, 0.95, 1.05, 1.12, 0.85, 1.15]
 
 
 def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5, algorithm="auto"):
@@ -61,12 +62,13 @@ def test_batch_matches_single_lattices(sincos, algorithm):
 @pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
                                            ("libm", "fp64")])
 def test_narrow_tiles_match_single_lattices(sincos, reduce):
-    """Sides that are multiples of 32 but not of 128 run on the narrow tiles
-    (32 rows x 16 plane columns): one tile (32), 2 x 2 (64), 3 x 3 (96), 5 x 5
-    (160, not a power of two) and 6 x 6 (192) tiles per lattice, several lattices
-    of a side in one launch, against the single-lattice two-pass kernels."""
-    Ls = [32, 64, 96, 160, 192, 32, 96]
-    betas = [0.8, 1.0, 1.12, 1.3, 0.9, 1.2, 0.7]
+    """Sides that are multiples of 32 but neither of 128 nor small enough for
+    one CTA run on the narrow tiles (32 rows x 16 plane columns): 5 x 5 (160,
+    not a power of two), 6 x 6 (192) and 7 x 7 (224) tiles per lattice, several
+    lattices of a side in one launch; next to them whole lattices (32, 64, 96,
+    and 96 twice); all against the single-lattice two-pass kernels."""
+    Ls = [160, 192, 224, 160, 32, 64, 96, 96]
+    betas = [0.8, 1.0, 1.12, 1.3, 0.9, 1.2, 0.7, 1.05]
     with Batch(Ls, betas, 31, lattice_id0=3, sweeps_per_round=3, sincos=sincos,
                reduce=reduce) as b:
         b.run(3)
@@ -165,9 +167,9 @@ def test_replica_exchange_configuration_runs():
         b.run(20)
         n, nrec, nxt, n_ctas = b.info()
         # fused tiles: L = 256 (16 CTAs per lattice, 4 groups of 8), L = 128 (4 CTAs,
-        # one group); narrow tiles: L = 96 (9 CTAs, 3 groups of 11, 11, 10), 64 (4,
-        # one group), 32 (1, one group); L = 16, 24, 48 in the cluster launch
-        assert b.launches_per_round() == (4 + 1 + 3 + 1 + 1) * 10 + 1 + 1
+        # one group), one launch per sweep each; L = 16 ... 96 whole lattices in one
+        # launch per round; then the exchange
+        assert b.launches_per_round() == (4 + 1) * 10 + 1 + 1
         bl = b.betas()
         slots, acc, att = b.exchange_stats()
         e0 = b.observables(0)["e"]
