@@ -38,13 +38,14 @@ FLUSH_BYTES = 256 << 20
 # Algorithmic instruction count per site update (one issue slot each), the
 # work the method itself requires on this GPU:
 #   Philox4x32-10: 20 wide multiplies + 20 three-input xors, 2 + 2 of them shared
-#     by all sites of a sweep -> 36;
+#     by all sites of a sweep -> 36 per block, and one block serves two updates
+#     (the sites x and x + 2 of a row share it) -> 18;
 #   proposal 2u0 - 1 and wrap -> 6;  neighbour sums (2 x 3 adds) -> 6;
 #   two unit vectors (own + proposal; neighbours reuse their own): 2 x 27 with the
 #     polynomial / CUDA sincosf-class path, 2 x 3 with the SFU intrinsics;
 #   dE, Boltzmann factor, accept test and select: 22 (expf) / 14 (__expf);
 #   per-sweep sums: 17 per black site -> 8.5 per update.
-ALG_INSTR_PER_UPDATE = {"accurate": 128.5, "libm": 132.5, "fast": 76.5}
+ALG_INSTR_PER_UPDATE = {"accurate": 110.5, "libm": 114.5, "fast": 58.5}
 SMS, SMSP_PER_SM, LANES = 152, 4, 32       # GB300: 152 SMs x 4 schedulers x 32 lanes
 TIMING_EVERY = 50          # kernel events on every 50th sweep of the timed region
 

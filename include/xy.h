@@ -16,10 +16,14 @@
  * fused into every sweep.
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
- * (seed_lo, seed_hi) and counter (site, sweep, lattice_id, domain), where
+ * (seed_lo, seed_hi) and counter (c, sweep, lattice_id, domain), where
  * site = y * L + x (natural order); domain 0 draws the hot start
- * (theta = 2 pi u24(w0) at sweep 0), domain 1 the Metropolis words of sweep t
- * (w0 -> proposal, w1 -> accept), domain 2 the replica-exchange words.
+ * (c = site, theta = 2 pi u24(w0) at sweep 0), domain 1 the Metropolis words
+ * of sweep t, domain 2 the replica-exchange words.  The Metropolis draws use
+ * all four words of a block for two sites: the sites x and x + 2 of a row
+ * with x & 2 == 0 share c = y * L + x, the first taking (w0 -> proposal,
+ * w1 -> accept), the second (w2 -> proposal, w3 -> accept); so a site's
+ * counter is c = site - (x & 2), and its words are w2, w3 iff x & 2.
  * u24(w) = (w >> 8) * 2^-24, exact in FP32.
  *
  * Conventions

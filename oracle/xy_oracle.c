@@ -26,7 +26,9 @@
  * by the 64-bit seed (low word first) with counter (site, sweep, lattice id,
  * domain); domain 0 draws the hot start, domain 1 the Metropolis words,
  * domain 2 the replica-exchange words, domain 3 the HMC momenta and
- * domain 4 the HMC accept words.
+ * domain 4 the HMC accept words.  A Metropolis block serves two sites of a
+ * row, x and x + 2 with x & 2 == 0, under the counter of the first: the
+ * first site takes words 0 and 1, the second words 2 and 3.
  * Uniforms use the top 24 bits of a word: u = (w >> 8) * 2^-24.
  */
 #include <math.h>
@@ -184,11 +186,14 @@ static orc_step attempt(int Lx, int Ly, const double *theta, int64_t s,
                         double beta, double J, double delta, uint64_t seed,
                         uint32_t lattice_id, uint32_t sweep)
 {
+    /* the block of the pair (x - (x & 2), x - (x & 2) + 2) in row y */
+    int64_t x = s % Lx;
+    int upper = (x & 2) != 0;
     uint32_t w[4];
-    site_words(seed, (uint32_t)s, sweep, lattice_id, 1u, w);
-    double u0 = u24(w[0]);
+    site_words(seed, (uint32_t)(s - (x & 2)), sweep, lattice_id, 1u, w);
+    double u0 = u24(w[2 * upper]);
     orc_step st;
-    st.u1 = u24(w[1]);
+    st.u1 = u24(w[2 * upper + 1]);
     double prop = theta[s] + delta * (2.0 * u0 - 1.0);
     if (prop < 0.0) prop += ORC_TWO_PI;
     else if (prop >= ORC_TWO_PI) prop -= ORC_TWO_PI;

@@ -19,8 +19,9 @@
 // Every CTA of a cluster reaches every barrier (padding CTAs included).
 //
 // The site update is the same pinned-rounding device function the single
-// lattice kernels use, with the same Philox counters (site, sweep, lattice id,
-// 1): a lattice evolves bit-identically whether it runs alone or in a batch.
+// lattice kernels use, with the same Philox counters (the site's Metropolis
+// counter, sweep, lattice id, 1) and words: a lattice evolves bit-identically
+// whether it runs alone or in a batch.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -105,14 +106,16 @@ __global__ void __launch_bounds__(kThreads) k_batch_round(BatchArgs a) {
               const float2 l = row[kl], rt = row[kr], d = down[k], u = up[k];
               const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
               const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-              const uint32_t site = (uint32_t)y * (uint32_t)L + 2u * (uint32_t)k + (uint32_t)q;
-              const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+              const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+              const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * (uint32_t)L + x, x);
+              const uint4 w = xyd::philox4x32_10(make_uint4(ctr, sweep, lid, 1u), a.rk);
+              const uint2 uw = xyd::metropolis_words(w, x);
               float* tp = own + (size_t)y * W + k;
               const float t = __ldcg(tp);
               float s0, c0;
               xyd::unit_vector<MODE>(t, &s0, &c0);
               const xyd::SiteResult res =
-                  xyd::metropolis_step<MODE>(t, c0, s0, Sc, Ss, w.x, w.y, K, a.delta);
+                  xyd::metropolis_step<MODE>(t, c0, s0, Sc, Ss, uw.x, uw.y, K, a.delta);
               *tp = res.th;
               n_acc += res.accept ? 1u : 0u;
               if (colour == 1) {
@@ -256,12 +259,14 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_batch_fused(BatchArgs a) {
             const float2 l = row[kl], rt = row[kr], d = row[k - W], u = row[k + W];
             const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
             const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-            const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-            const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+            const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+            const uint4 w = xyd::philox4x32_10(
+                make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+            const uint2 uw = xyd::metropolis_words(w, x);
             const size_t idx = (size_t)sr * W + k;
             const float2 o = cs_r[idx];
             const xyd::SiteResult res =
-                xyd::metropolis_step<MODE>(th_r[idx], o.x, o.y, Sc, Ss, w.x, w.y, K, a.delta);
+                xyd::metropolis_step<MODE>(th_r[idx], o.x, o.y, Sc, Ss, uw.x, uw.y, K, a.delta);
             th_r[idx] = res.th;
             cs_r[idx] = make_float2(res.c, res.s);
             if (own) {
@@ -287,12 +292,14 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_batch_fused(BatchArgs a) {
             const float2 l = row[kl], rt = row[kr], d = row[k - W], u = row[k + W];
             const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
             const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-            const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-            const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+            const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+            const uint4 w = xyd::philox4x32_10(
+                make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+            const uint2 uw = xyd::metropolis_words(w, x);
             const size_t idx = (size_t)sr * W + k;
             const float2 o = cs_b[idx];
             const xyd::SiteResult res =
-                xyd::metropolis_step<MODE>(th_b[idx], o.x, o.y, Sc, Ss, w.x, w.y, K, a.delta);
+                xyd::metropolis_step<MODE>(th_b[idx], o.x, o.y, Sc, Ss, uw.x, uw.y, K, a.delta);
             n_acc += res.accept ? 1u : 0u;
             dst[plane + (size_t)y * W + k] = res.th;
             const float2 m = row[k];

@@ -13,7 +13,8 @@ namespace xyd {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
 // as 1, 2, 3", SC'11): two 32x32->64 products per round, the high halves
 // xored into the other lanes with the round key, the key advanced by a Weyl
-// sequence.  Counter x = (site, sweep, lattice_id, domain); key = seed words.
+// sequence.  Counter x = (site, sweep, lattice_id, domain); key = seed words
+// (the Metropolis draws pair two sites per counter: metropolis_counter).
 constexpr uint32_t kMulA = 0xD2511F53u;
 constexpr uint32_t kMulB = 0xCD9E8D57u;
 constexpr uint32_t kWeylA = 0x9E3779B9u;
@@ -55,6 +56,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 x, const RoundKeys& rk) {
     x = make_uint4(hi_b ^ x.y ^ rk.k0[round], lo_b, hi_a ^ x.w ^ rk.k1[round], lo_a);
   }
   return x;
+}
+
+// The Metropolis draws (domain 1) use all four words of a block: the sites x
+// and x + 2 of a row with x & 2 == 0 (plane columns 2m and 2m + 1 of one
+// colour) share the block with counter (y*L + x, sweep, lattice_id, 1), the
+// first taking words (w.x, w.y), the second (w.z, w.w).  Site s = y*L + x thus
+// has counter s - (x & 2) and the upper pair iff x & 2: one generator call per
+// two updates where a thread updates both sites of a pair.
+__device__ __forceinline__ uint32_t metropolis_counter(uint32_t site, uint32_t x) {
+  return site - (x & 2u);
+}
+
+__device__ __forceinline__ uint2 metropolis_words(const uint4& w, uint32_t x) {
+  return (x & 2u) ? make_uint2(w.z, w.w) : make_uint2(w.x, w.y);
 }
 
 constexpr float kTwoPi = 6.28318530717958647692f;

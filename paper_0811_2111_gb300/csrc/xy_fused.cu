@@ -104,16 +104,18 @@ struct FusedCore {
 
 template <int MODE, class Args>
 __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c, int q,
-                                              uint32_t site, const Args& a,
+                                              uint32_t site, uint32_t x, const Args& a,
                                               const xyd::RoundKeys& rk) {
   const float2 l = cs[1][r][c + q - 1], rt = cs[1][r][c + q];
   const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
   const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
   const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-  const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), rk);
+  const uint4 w = xyd::philox4x32_10(
+      make_uint4(xyd::metropolis_counter(site, x), a.sweep, a.lattice_id, 1u), rk);
+  const uint2 uw = xyd::metropolis_words(w, x);
   const float2 own = cs[0][r][c];
   const xyd::SiteResult res =
-      xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, w.x, w.y, a.K, a.delta);
+      xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
   th[0][r][c] = res.th;
   cs[0][r][c] = make_float2(res.c, res.s);
 }
@@ -223,14 +225,14 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     PairNeighbours n;
     pair_neighbours(cs[1], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), rk);
+    // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
+    const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
-        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, a.K, a.delta);
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
     const xyd::SiteResult r1 =
-        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, a.K, a.delta);
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, a.K, a.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
     *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
@@ -258,8 +260,8 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       const int y = wrap_once(y0 + ty, L);
       const int k = wrap_once(k0 + tk, W);
       const int q = y & 1;
-      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, site, a, rk);
+      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, (uint32_t)y * uL + x, x, a, rk);
     }
   }
   mid();
@@ -278,14 +280,14 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     PairNeighbours n;
     pair_neighbours(cs[0], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, a.sweep, a.lattice_id, 1u), rk);
+    // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
+    const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
-        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, a.K, a.delta);
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
     const xyd::SiteResult r1 =
-        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, a.K, a.delta);
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, a.K, a.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
     *reinterpret_cast<float2*>(dst_blk + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
 

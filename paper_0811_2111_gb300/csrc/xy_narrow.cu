@@ -174,14 +174,14 @@ __global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchA
     NPair n;
     npair_neighbours(cs[1], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, sweep, lid, 1u), b.rk);
+    // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
+    const uint4 w = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
-        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K, b.delta);
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, K, b.delta);
     const xyd::SiteResult r1 =
-        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K, b.delta);
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, K, b.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
     *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
@@ -206,15 +206,18 @@ __global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchA
     const int kk = nwrap(k0 + tk, W);
     const int q = yy & 1;
     const int rr = gy + 2, c = tk + 4;
-    const uint32_t site = (uint32_t)yy * uL + 2u * (uint32_t)kk + (uint32_t)q;
+    const uint32_t x = 2u * (uint32_t)kk + (uint32_t)q;
+    const uint32_t site = (uint32_t)yy * uL + x;
     const float2 l = cs[1][rr][c + q - 1], rt = cs[1][rr][c + q];
     const float2 d = cs[1][rr - 1][c], u = cs[1][rr + 1][c];
     const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
     const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-    const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), b.rk);
+    const uint4 w =
+        xyd::philox4x32_10(make_uint4(xyd::metropolis_counter(site, x), sweep, lid, 1u), b.rk);
+    const uint2 uw = xyd::metropolis_words(w, x);
     const float2 own = cs[0][rr][c];
     const xyd::SiteResult res =
-        xyd::metropolis_step<MODE>(th[0][rr][c], own.x, own.y, Sc, Ss, w.x, w.y, K, b.delta);
+        xyd::metropolis_step<MODE>(th[0][rr][c], own.x, own.y, Sc, Ss, uw.x, uw.y, K, b.delta);
     th[0][rr][c] = res.th;
     cs[0][rr][c] = make_float2(res.c, res.s);
   }
@@ -232,14 +235,14 @@ __global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchA
     NPair n;
     npair_neighbours(cs[0], r, c0, q, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site0 + 2u, sweep, lid, 1u), b.rk);
+    // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
+    const uint4 w = xyd::philox4x32_10(make_uint4(site0, sweep, lid, 1u), b.rk);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
-        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w0.x, w0.y, K, b.delta);
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, K, b.delta);
     const xyd::SiteResult r1 =
-        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K, b.delta);
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, K, b.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
     *reinterpret_cast<float2*>(dst + plane + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
 
@@ -395,11 +398,13 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       const float2 d = cs[half + yd * W + k], u = cs[half + yu * W + k];
       const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
       const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-      const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+      const uint4 w = xyd::philox4x32_10(
+          make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+      const uint2 uw = xyd::metropolis_words(w, x);
       const float2 own = cs[o];
       const xyd::SiteResult res =
-          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, w.x, w.y, K, a.delta);
+          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
       th[o] = res.th;
       cs[o] = make_float2(res.c, res.s);
       n_acc += res.accept ? 1u : 0u;
@@ -420,12 +425,14 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       const float2 d = cs[yd * W + k], u = cs[yu * W + k];
       const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
       const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-      const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)k + (uint32_t)q;
-      const uint4 w = xyd::philox4x32_10(make_uint4(site, sweep, lid, 1u), a.rk);
+      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+      const uint4 w = xyd::philox4x32_10(
+          make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+      const uint2 uw = xyd::metropolis_words(w, x);
       const int o = half + i;
       const float2 own = cs[o];
       const xyd::SiteResult res =
-          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, w.x, w.y, K, a.delta);
+          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
       th[o] = res.th;
       cs[o] = make_float2(res.c, res.s);
       n_acc += res.accept ? 1u : 0u;

@@ -11,7 +11,7 @@
 // steps are independent (four-way instruction-level parallelism), and the
 // accept is the vector select of Sec. 3.2, one component per replica.  Replica
 // r runs the single-lattice arithmetic (xyd::metropolis_step with its own
-// Philox counter (site, sweep, lattice_id + r, 1) and its own beta), so it is
+// Metropolis words under lattice id lattice_id + r and its own beta), so it is
 // bit-identical to that lattice swept by the kernels of xy_sweep.cu.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -109,14 +109,15 @@ __global__ void __launch_bounds__(kThreads) k_quad_half(QuadArgs a) {
     const float4 cm = s_cos[ty + 1][sc], sm = s_sin[ty + 1][sc];
     float4* p = own + (size_t)y * W + k;
     const float4 th = *p;
-    const uint32_t site = (uint32_t)y * (uint32_t)L + 2u * (uint32_t)k + (uint32_t)q;
+    const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+    const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * (uint32_t)L + x, x);
     float out[kR];
 #pragma unroll
     for (int j = 0; j < kR; ++j) {
       const float Sc = xyd::nb_sum(comp(cl, j), comp(cr, j), comp(cd, j), comp(cu, j));
       const float Ss = xyd::nb_sum(comp(sl, j), comp(sr, j), comp(sd, j), comp(su, j));
-      const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id0 + (uint32_t)j, 1u),
-                                         a.rk);
+      const uint2 w = xyd::metropolis_words(
+          xyd::philox4x32_10(make_uint4(ctr, a.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk), x);
       const float t = comp(th, j);
       float s0, c0;
       xyd::unit_vector<MODE>(t, &s0, &c0);

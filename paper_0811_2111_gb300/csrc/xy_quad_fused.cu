@@ -16,9 +16,9 @@
 //   2. updates the black elements against the new red ones,
 //   3. accumulates each replica's sweep sums,
 // and writes the tile's new angles to `dst`.  Every element runs the
-// single-lattice arithmetic (xyd::metropolis_step with Philox counter
-// (site, sweep, lattice_id0 + r, 1) and K_r = beta_r J), so replica r is bit
-// for bit the single lattice with lattice id lattice_id0 + r.
+// single-lattice arithmetic (xyd::metropolis_step with the site's Metropolis
+// words under lattice id lattice_id0 + r, and K_r = beta_r J), so replica r is
+// bit for bit the single lattice with lattice id lattice_id0 + r.
 //
 // A lane updates two adjacent elements -- two replicas of one site -- so its
 // same-row neighbours are two aligned float4 loads of (cos, sin) pairs.
@@ -236,9 +236,12 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const int q = y & 1;                                   // red: x = 2k + (y & 1)
     PairNb n;
     pair_nb(cs[1], r, c0, q, n);
-    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, item.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, item.sweep, id1, 1u), a.rk);
+    const uint32_t x = 2u * kq + (uint32_t)q;
+    const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
+    const uint2 w0 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id0, 1u), a.rk), x);
+    const uint2 w1 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id1, 1u), a.rk), x);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -273,16 +276,18 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const int q = y & 1;
     const int ks = wrap_once(ks0 + ((sc - 4) >> 2), W);   // floor: stage columns 0..3 -> ks0 - 1
     const int j = sc & 3;
-    const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)ks + (uint32_t)q;
+    const uint32_t x = 2u * (uint32_t)ks + (uint32_t)q;
+    const uint32_t site = (uint32_t)y * uL + x;
     const float2 l = cs[1][r][sc + 4 * q - 4], rt = cs[1][r][sc + 4 * q];
     const float2 d = cs[1][r - 1][sc], u = cs[1][r + 1][sc];
     const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
     const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-    const uint4 w =
-        xyd::philox4x32_10(make_uint4(site, item.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+    const uint4 w = xyd::philox4x32_10(
+        make_uint4(xyd::metropolis_counter(site, x), item.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+    const uint2 uw = xyd::metropolis_words(w, x);
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
-                                                           w.x, w.y, replica_k(a, j), a.delta);
+                                                           uw.x, uw.y, replica_k(a, j), a.delta);
     th[0][r][sc] = res.th;
     cs[0][r][sc] = make_float2(res.c, res.s);
   }
@@ -304,9 +309,12 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
     PairNb n;
     pair_nb(cs[0], r, c0, q, n);
-    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, item.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, item.sweep, id1, 1u), a.rk);
+    const uint32_t x = 2u * kq + (uint32_t)q;
+    const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
+    const uint2 w0 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id0, 1u), a.rk), x);
+    const uint2 w1 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id1, 1u), a.rk), x);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
@@ -491,9 +499,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     const int q = y & 1;                                   // red: x = 2k + (y & 1)
     PairNb n;
     pair_nb(cs[1], r, c0, q, n);
-    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const uint32_t x = 2u * kq + (uint32_t)q;
+    const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
+    const uint2 w0 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id0, 1u), a.rk), x);
+    const uint2 w1 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id1, 1u), a.rk), x);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -528,16 +539,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     const int q = y & 1;
     const int ks = wrap_once(ks0 + ((sc - 4) >> 2), W);   // floor: stage columns 0..3 -> ks0 - 1
     const int j = sc & 3;
-    const uint32_t site = (uint32_t)y * uL + 2u * (uint32_t)ks + (uint32_t)q;
+    const uint32_t x = 2u * (uint32_t)ks + (uint32_t)q;
+    const uint32_t site = (uint32_t)y * uL + x;
     const float2 l = cs[1][r][sc + 4 * q - 4], rt = cs[1][r][sc + 4 * q];
     const float2 d = cs[1][r - 1][sc], u = cs[1][r + 1][sc];
     const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
     const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-    const uint4 w =
-        xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+    const uint4 w = xyd::philox4x32_10(
+        make_uint4(xyd::metropolis_counter(site, x), a.sweep, a.lattice_id0 + (uint32_t)j, 1u), a.rk);
+    const uint2 uw = xyd::metropolis_words(w, x);
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
-                                                           w.x, w.y, replica_k(a, j), a.delta);
+                                                           uw.x, uw.y, replica_k(a, j), a.delta);
     th[0][r][sc] = res.th;
     cs[0][r][sc] = make_float2(res.c, res.s);
   }
@@ -558,9 +571,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
     PairNb n;
     pair_nb(cs[0], r, c0, q, n);
-    const uint32_t site = (uint32_t)y * uL + 2u * kq + (uint32_t)q;
-    const uint4 w0 = xyd::philox4x32_10(make_uint4(site, a.sweep, id0, 1u), a.rk);
-    const uint4 w1 = xyd::philox4x32_10(make_uint4(site, a.sweep, id1, 1u), a.rk);
+    const uint32_t x = 2u * kq + (uint32_t)q;
+    const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
+    const uint2 w0 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id0, 1u), a.rk), x);
+    const uint2 w1 =
+        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id1, 1u), a.rk), x);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =

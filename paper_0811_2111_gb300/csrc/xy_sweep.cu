@@ -113,6 +113,7 @@ k_half_sweep(HalfSweepArgs a) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) th[j] = (kq + j < W) ? rowp[kq + j] : 0.f;
     }
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (kq + j >= W) continue;
@@ -126,13 +127,17 @@ k_half_sweep(HalfSweepArgs a) {
       const float Sc = xyd::nb_sum(cl, cr, cd, cu);
       const float Ss = xyd::nb_sum(sl, sr, sd, su);
 
+      // kq is a multiple of 4: columns kq + {0, 1} and kq + {2, 3} are pairs
+      // (x and x + 2 with x & 2 == 0), one block drawn for each
       const uint32_t x = 2u * (uint32_t)(kq + j) + (uint32_t)q;
       const uint32_t site = (uint32_t)y * (uint32_t)L + x;
-      const uint4 w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.rk);
+      if ((j & 1) == 0)
+        w = xyd::philox4x32_10(make_uint4(site, a.sweep, a.lattice_id, 1u), a.rk);
+      const uint2 uw = xyd::metropolis_words(w, x);
       const float t = th[j];
       float s0, c0;
       xyd::unit_vector<MODE>(t, &s0, &c0);
-      const xyd::SiteResult res = xyd::metropolis_step<MODE>(t, c0, s0, Sc, Ss, w.x, w.y, a.K,
+      const xyd::SiteResult res = xyd::metropolis_step<MODE>(t, c0, s0, Sc, Ss, uw.x, uw.y, a.K,
                                                              a.delta);
       th[j] = res.th;
       n_acc += res.accept ? 1u : 0u;

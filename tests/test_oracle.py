@@ -109,6 +109,33 @@ def test_philox_words_layout():
         assert np.array_equal(w[i], ref)
 
 
+@pytest.mark.parametrize("L", [8, 6])
+def test_metropolis_words_pair_sites_and_are_never_reused(L):
+    """A sweep's Metropolis draws: the sites x and x + 2 of a row (x & 2 == 0)
+    share one block, the first taking words 0/1, the second 2/3; so every
+    word of the generator is used at most once per sweep, every site reads
+    its accept uniform from that position and its proposal is
+    theta + delta (2 u0 - 1) with u0 the word before it (L = 6: the pair
+    x = 4, 6 is cut by the edge and x = 4 takes the lower words alone)."""
+    seed, sweep, lid, delta = 0xABCDEF12345, 5, 2, 2.0
+    theta = oracle.start(L, L, seed=seed, lattice_id=lid)
+    sites = np.arange(L * L)
+    tp, u1, p, acc = oracle.attempt_sites(theta, L, L, sites, 1.0, seed, sweep, lattice_id=lid,
+                                          delta=delta)
+    used = set()
+    for s in sites:
+        y, x = divmod(int(s), L)
+        base, upper = y * L + (x & ~2), (x >> 1) & 1
+        w = oracle.philox_words(seed, sweep, lid, 1, base, 1)[0]
+        assert (base, upper) not in used
+        used.add((base, upper))
+        u = (w >> 8) * 2.0 ** -24
+        assert u1[s] == u[2 * upper + 1]
+        want = (theta[s] + delta * (2.0 * u[2 * upper] - 1.0)) % TWO_PI
+        assert abs(tp[s] - want) < 1e-12
+    assert len(used) == L * L
+
+
 # ---------------------------------------------------------------------------
 # Start configurations
 # ---------------------------------------------------------------------------
