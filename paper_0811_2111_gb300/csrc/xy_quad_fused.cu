@@ -238,10 +238,15 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     pair_nb(cs[1], r, c0, q, n);
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
-    const uint2 w0 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id0, 1u), a.rk), x);
-    const uint2 w1 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id1, 1u), a.rk), x);
+    // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
+    // (x & 2 == lane & 2): each draws one replica's block, keeps its own
+    // half and passes the other half across
+    const bool up = (x & 2u) != 0u;
+    const uint4 wb = xyd::philox4x32_10(make_uint4(ctr, item.sweep, up ? id1 : id0, 1u), a.rk);
+    const uint32_t g0 = __shfl_xor_sync(0xffffffffu, up ? wb.x : wb.z, 2);
+    const uint32_t g1 = __shfl_xor_sync(0xffffffffu, up ? wb.y : wb.w, 2);
+    const uint2 w0 = up ? make_uint2(g0, g1) : make_uint2(wb.x, wb.y);
+    const uint2 w1 = up ? make_uint2(wb.z, wb.w) : make_uint2(g0, g1);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -311,10 +316,15 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     pair_nb(cs[0], r, c0, q, n);
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
-    const uint2 w0 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id0, 1u), a.rk), x);
-    const uint2 w1 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, item.sweep, id1, 1u), a.rk), x);
+    // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
+    // (x & 2 == lane & 2): each draws one replica's block, keeps its own
+    // half and passes the other half across
+    const bool up = (x & 2u) != 0u;
+    const uint4 wb = xyd::philox4x32_10(make_uint4(ctr, item.sweep, up ? id1 : id0, 1u), a.rk);
+    const uint32_t g0 = __shfl_xor_sync(0xffffffffu, up ? wb.x : wb.z, 2);
+    const uint32_t g1 = __shfl_xor_sync(0xffffffffu, up ? wb.y : wb.w, 2);
+    const uint2 w0 = up ? make_uint2(g0, g1) : make_uint2(wb.x, wb.y);
+    const uint2 w1 = up ? make_uint2(wb.z, wb.w) : make_uint2(g0, g1);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
@@ -501,10 +511,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     pair_nb(cs[1], r, c0, q, n);
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
-    const uint2 w0 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id0, 1u), a.rk), x);
-    const uint2 w1 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id1, 1u), a.rk), x);
+    // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
+    // (x & 2 == lane & 2): each draws one replica's block, keeps its own
+    // half and passes the other half across
+    const bool up = (x & 2u) != 0u;
+    const uint4 wb = xyd::philox4x32_10(make_uint4(ctr, a.sweep, up ? id1 : id0, 1u), a.rk);
+    const uint32_t g0 = __shfl_xor_sync(0xffffffffu, up ? wb.x : wb.z, 2);
+    const uint32_t g1 = __shfl_xor_sync(0xffffffffu, up ? wb.y : wb.w, 2);
+    const uint2 w0 = up ? make_uint2(g0, g1) : make_uint2(wb.x, wb.y);
+    const uint2 w1 = up ? make_uint2(wb.z, wb.w) : make_uint2(g0, g1);
     const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     const xyd::SiteResult r0 =
@@ -573,10 +588,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     pair_nb(cs[0], r, c0, q, n);
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
-    const uint2 w0 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id0, 1u), a.rk), x);
-    const uint2 w1 =
-        xyd::metropolis_words(xyd::philox4x32_10(make_uint4(ctr, a.sweep, id1, 1u), a.rk), x);
+    // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
+    // (x & 2 == lane & 2): each draws one replica's block, keeps its own
+    // half and passes the other half across
+    const bool up = (x & 2u) != 0u;
+    const uint4 wb = xyd::philox4x32_10(make_uint4(ctr, a.sweep, up ? id1 : id0, 1u), a.rk);
+    const uint32_t g0 = __shfl_xor_sync(0xffffffffu, up ? wb.x : wb.z, 2);
+    const uint32_t g1 = __shfl_xor_sync(0xffffffffu, up ? wb.y : wb.w, 2);
+    const uint2 w0 = up ? make_uint2(g0, g1) : make_uint2(wb.x, wb.y);
+    const uint2 w1 = up ? make_uint2(wb.z, wb.w) : make_uint2(g0, g1);
     const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
     const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
     const xyd::SiteResult r0 =
