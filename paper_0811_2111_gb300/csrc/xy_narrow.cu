@@ -373,6 +373,22 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       ++y;
     }
   };
+  // with W even a thread takes both sites of a pair, (y, 2m) and (y, 2m + 1)
+  // -- the sites x and x + 2 that share one Philox block -- stepping over the
+  // L*W/2 pairs the same way; with W odd (L % 4 == 2) a site at a time
+  const bool paired = (W & 1) == 0;
+  const int Wp = paired ? W / 2 : 1;
+  const int npairs = half / 2;
+  const int py0 = threadIdx.x / Wp, pm0 = threadIdx.x % Wp;
+  const int pdy = kSThreads / Wp, pdm = kSThreads % Wp;
+  auto step_pair = [&](int& y, int& m) {
+    m += pdm;
+    y += pdy;
+    if (m >= Wp) {
+      m -= Wp;
+      ++y;
+    }
+  };
 
   for (int i = threadIdx.x; i < 2 * half; i += kSThreads) {
     const float t = __ldg(src + i);
@@ -386,61 +402,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
   for (int sw = 0; sw < a.sweeps; ++sw) {
     const uint32_t sweep = sweep0 + (uint32_t)sw;
     unsigned int n_acc = 0;
-    // ---- red half: red site (y, k) is x = 2k + (y & 1); its black
-    // neighbours (y, k+q-1), (y, k+q), (y-1, k), (y+1, k) ----
-    for (int o = threadIdx.x, y = y0, k = k0; o < half; o += kSThreads) {
-      const int q = y & 1;
-      const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
-      int kl = k + q - 1, kr = k + q;
-      kl += kl < 0 ? W : 0;
-      kr -= kr >= W ? W : 0;
-      const float2 l = cs[half + y * W + kl], rt = cs[half + y * W + kr];
-      const float2 d = cs[half + yd * W + k], u = cs[half + yu * W + k];
-      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
-      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
-      const uint4 w = xyd::philox4x32_10(
-          make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
-      const uint2 uw = xyd::metropolis_words(w, x);
-      const float2 own = cs[o];
-      const xyd::SiteResult res =
-          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
-      th[o] = res.th;
-      cs[o] = make_float2(res.c, res.s);
-      n_acc += res.accept ? 1u : 0u;
-      step_site(y, k);
-    }
-    __syncthreads();
-    // ---- black half, with the sweep sums: black site (y, k) is
-    // x = 2k + ((y + 1) & 1); its red neighbours as above ----
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int i = threadIdx.x, y = y0, k = k0; i < half; i += kSThreads) {
-      const int q = (y + 1) & 1;
-      const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
-      int kl = k + q - 1, kr = k + q;
-      kl += kl < 0 ? W : 0;
-      kr -= kr >= W ? W : 0;
-      const float2 l = cs[y * W + kl], rt = cs[y * W + kr];
-      const float2 d = cs[yd * W + k], u = cs[yu * W + k];
-      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
-      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
-      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
-      const uint4 w = xyd::philox4x32_10(
-          make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
-      const uint2 uw = xyd::metropolis_words(w, x);
-      const int o = half + i;
-      const float2 own = cs[o];
-      const xyd::SiteResult res =
-          xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
-      th[o] = res.th;
-      cs[o] = make_float2(res.c, res.s);
-      n_acc += res.accept ? 1u : 0u;
-      // the red site with the same (y, k): its spin enters M once
-      const float2 m = cs[i];
-      float v[5];
-      xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc, Ss, m.x,
-                         m.y, v);
+    auto add_terms = [&](const float* v) {
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
         if (RED == 0) {
@@ -449,7 +413,137 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
           xyd::neumaier_add(acc[j], cmp[j], v[j]);
         }
       }
-      step_site(y, k);
+    };
+    if (paired) {
+      // ---- red half, a pair per step: sites k = 2m and k + 1 of row y
+      // (flat index o = 2P); left/right neighbours k+q-1, k+q for the first,
+      // k+q, k+q+1 for the second ----
+      for (int P = threadIdx.x, y = py0, m = pm0; P < npairs; P += kSThreads) {
+        const int k = 2 * m, o = 2 * P;
+        const int q = y & 1;
+        const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+        int kl = k + q - 1, kr = k + q + 1;
+        kl += kl < 0 ? W : 0;
+        kr -= kr >= W ? W : 0;
+        const float2* row = cs + half + y * W;
+        const float2 lf = row[kl], md = row[k + q], rg = row[kr];
+        const float4 dn = *reinterpret_cast<const float4*>(cs + half + yd * W + k);
+        const float4 up = *reinterpret_cast<const float4*>(cs + half + yu * W + k);
+        const float Sc0 = xyd::nb_sum(lf.x, md.x, dn.x, up.x);
+        const float Ss0 = xyd::nb_sum(lf.y, md.y, dn.y, up.y);
+        const float Sc1 = xyd::nb_sum(md.x, rg.x, dn.z, up.z);
+        const float Ss1 = xyd::nb_sum(md.y, rg.y, dn.w, up.w);
+        const uint32_t x0 = 2u * (uint32_t)k + (uint32_t)q;          // x0 & 2 == 0
+        const uint4 w =
+            xyd::philox4x32_10(make_uint4((uint32_t)y * uL + x0, sweep, lid, 1u), a.rk);
+        const float2 t = *reinterpret_cast<const float2*>(th + o);
+        const float4 own = *reinterpret_cast<const float4*>(cs + o);
+        const xyd::SiteResult r0 =
+            xyd::metropolis_step<MODE>(t.x, own.x, own.y, Sc0, Ss0, w.x, w.y, K, a.delta);
+        const xyd::SiteResult r1 =
+            xyd::metropolis_step<MODE>(t.y, own.z, own.w, Sc1, Ss1, w.z, w.w, K, a.delta);
+        *reinterpret_cast<float2*>(th + o) = make_float2(r0.th, r1.th);
+        *reinterpret_cast<float4*>(cs + o) = make_float4(r0.c, r0.s, r1.c, r1.s);
+        n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+        step_pair(y, m);
+      }
+      __syncthreads();
+      // ---- black half, a pair per step, with the sweep sums ----
+      for (int P = threadIdx.x, y = py0, m = pm0; P < npairs; P += kSThreads) {
+        const int k = 2 * m, o = half + 2 * P;
+        const int q = (y + 1) & 1;
+        const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+        int kl = k + q - 1, kr = k + q + 1;
+        kl += kl < 0 ? W : 0;
+        kr -= kr >= W ? W : 0;
+        const float2* row = cs + y * W;
+        const float2 lf = row[kl], md = row[k + q], rg = row[kr];
+        const float4 dn = *reinterpret_cast<const float4*>(cs + yd * W + k);
+        const float4 up = *reinterpret_cast<const float4*>(cs + yu * W + k);
+        const float Sc0 = xyd::nb_sum(lf.x, md.x, dn.x, up.x);
+        const float Ss0 = xyd::nb_sum(lf.y, md.y, dn.y, up.y);
+        const float Sc1 = xyd::nb_sum(md.x, rg.x, dn.z, up.z);
+        const float Ss1 = xyd::nb_sum(md.y, rg.y, dn.w, up.w);
+        const uint32_t x0 = 2u * (uint32_t)k + (uint32_t)q;          // x0 & 2 == 0
+        const uint4 w =
+            xyd::philox4x32_10(make_uint4((uint32_t)y * uL + x0, sweep, lid, 1u), a.rk);
+        const float2 t = *reinterpret_cast<const float2*>(th + o);
+        const float4 own = *reinterpret_cast<const float4*>(cs + o);
+        const xyd::SiteResult r0 =
+            xyd::metropolis_step<MODE>(t.x, own.x, own.y, Sc0, Ss0, w.x, w.y, K, a.delta);
+        const xyd::SiteResult r1 =
+            xyd::metropolis_step<MODE>(t.y, own.z, own.w, Sc1, Ss1, w.z, w.w, K, a.delta);
+        *reinterpret_cast<float2*>(th + o) = make_float2(r0.th, r1.th);
+        *reinterpret_cast<float4*>(cs + o) = make_float4(r0.c, r0.s, r1.c, r1.s);
+        n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
+        // the red sites with the same (y, k) and (y, k + 1) enter M once each
+        const float4 mr = *reinterpret_cast<const float4*>(cs + 2 * P);
+        float v[5];
+        xyd::measure_terms(r0.c, r0.s, lf.x, lf.y, md.x, md.y, dn.x, dn.y, up.x, up.y, Sc0, Ss0,
+                           mr.x, mr.y, v);
+        add_terms(v);
+        xyd::measure_terms(r1.c, r1.s, md.x, md.y, rg.x, rg.y, dn.z, dn.w, up.z, up.w, Sc1, Ss1,
+                           mr.z, mr.w, v);
+        add_terms(v);
+        step_pair(y, m);
+      }
+    } else {
+      // ---- red half: red site (y, k) is x = 2k + (y & 1); its black
+      // neighbours (y, k+q-1), (y, k+q), (y-1, k), (y+1, k) ----
+      for (int o = threadIdx.x, y = y0, k = k0; o < half; o += kSThreads) {
+        const int q = y & 1;
+        const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+        int kl = k + q - 1, kr = k + q;
+        kl += kl < 0 ? W : 0;
+        kr -= kr >= W ? W : 0;
+        const float2 l = cs[half + y * W + kl], rt = cs[half + y * W + kr];
+        const float2 d = cs[half + yd * W + k], u = cs[half + yu * W + k];
+        const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+        const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+        const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+        const uint4 w = xyd::philox4x32_10(
+            make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+        const uint2 uw = xyd::metropolis_words(w, x);
+        const float2 own = cs[o];
+        const xyd::SiteResult res =
+            xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
+        th[o] = res.th;
+        cs[o] = make_float2(res.c, res.s);
+        n_acc += res.accept ? 1u : 0u;
+        step_site(y, k);
+      }
+      __syncthreads();
+      // ---- black half, with the sweep sums: black site (y, k) is
+      // x = 2k + ((y + 1) & 1); its red neighbours as above ----
+      for (int i = threadIdx.x, y = y0, k = k0; i < half; i += kSThreads) {
+        const int q = (y + 1) & 1;
+        const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
+        int kl = k + q - 1, kr = k + q;
+        kl += kl < 0 ? W : 0;
+        kr -= kr >= W ? W : 0;
+        const float2 l = cs[y * W + kl], rt = cs[y * W + kr];
+        const float2 d = cs[yd * W + k], u = cs[yu * W + k];
+        const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+        const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+        const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+        const uint4 w = xyd::philox4x32_10(
+            make_uint4(xyd::metropolis_counter((uint32_t)y * uL + x, x), sweep, lid, 1u), a.rk);
+        const uint2 uw = xyd::metropolis_words(w, x);
+        const int o = half + i;
+        const float2 own = cs[o];
+        const xyd::SiteResult res =
+            xyd::metropolis_step<MODE>(th[o], own.x, own.y, Sc, Ss, uw.x, uw.y, K, a.delta);
+        th[o] = res.th;
+        cs[o] = make_float2(res.c, res.s);
+        n_acc += res.accept ? 1u : 0u;
+        // the red site with the same (y, k): its spin enters M once
+        const float2 m = cs[i];
+        float v[5];
+        xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc, Ss, m.x,
+                           m.y, v);
+        add_terms(v);
+        step_site(y, k);
+      }
     }
     // (its barrier also ends the black half before the next sweep's red half)
     xyd::commit_block<kSWarps, RED, true>(
