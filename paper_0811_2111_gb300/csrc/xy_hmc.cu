@@ -320,10 +320,17 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     return reinterpret_cast<float (*)[kTileCols]>(tma_smem + s * kTmaStageBytes +
                                                  kTmaBox * sizeof(float));
   };
+  // Consecutive steps (buffer offsets 1, 2, 1, ...) walk the tiles in
+  // opposite orders, so a step starts with the tiles the launch before it
+  // wrote last, which are still in L2.  Every tile reads only the source
+  // buffer and its own momenta, so the order changes no result.
+  const bool rev = (a.src_off & 1) != 0;
+  auto tile_at = [&](int t) { return rev ? n_tiles - 1 - t : t; };
   // thread 0's count of loads issued per stage (for the drain on a timeout)
   int issued[2] = {0, 0};
   auto issue = [&](int t, int s) {
-    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
+    const int tt = tile_at(t);
+    const int x0 = (tt % tiles_x) * kTileCols, y0 = (tt / tiles_x) * TR;
     mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
     tma_load_2d(stage_th(s), mth, x0, y0, &bar[s]);
     tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
@@ -353,7 +360,8 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
     const int s = it & 1, b = it & 1;
     const uint32_t parity = (uint32_t)((it >> 1) & 1);
-    const int x0 = (t % tiles_x) * kTileCols, y0 = (t / tiles_x) * TR;
+    const int tt = tile_at(t);
+    const int x0 = (tt % tiles_x) * kTileCols, y0 = (tt / tiles_x) * TR;
     // halo loads first: rows y0-1, y0+TR (threads 0..127 / 128..255), columns
     // x0-1 and x0+128 (threads 0..TR-1 / TR..2TR-1)
     const int hy = tid < kTileCols ? (y0 == 0 ? L - 1 : y0 - 1) : (y0 + TR == L ? 0 : y0 + TR);
