@@ -28,7 +28,10 @@
  * domain 2 the replica-exchange words, domain 3 the HMC momenta and
  * domain 4 the HMC accept words.  A Metropolis block serves two sites of a
  * row, x and x + 2 with x & 2 == 0, under the counter of the first: the
- * first site takes words 0 and 1, the second words 2 and 3.
+ * first site takes words 0 and 1, the second words 2 and 3.  The paper fixes
+ * no generator (its flat random numbers came from the host, Sec. 1.2), so
+ * this layout is a reading: every word is used once per sweep, and a thread
+ * that updates both sites of a pair needs one block for two updates.
  * Uniforms use the top 24 bits of a word: u = (w >> 8) * 2^-24.
  */
 #include <math.h>
