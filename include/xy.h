@@ -224,10 +224,10 @@ xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, ui
  * together, one launch per round of sweeps, with optional replica exchange.
  * The Sec. 3.2 remark that one RGBA texel holds four replicas "maybe at
  * different temperatures" is the precedent; here each lattice keeps its own
- * split-layout planes and the batch is cut into bands of rows, one CTA each,
- * the bands of a lattice forming one thread-block cluster.  Every lattice i
- * evolves exactly as a single-lattice context with the same L, beta, seed and
- * lattice_id = lattice_id0 + i would (same Philox counters, same site update).
+ * split-layout planes and the plan gives every lattice one of four kernels
+ * (see `algorithm`).  Every lattice i evolves exactly as a single-lattice
+ * context with the same L, beta, seed and lattice_id = lattice_id0 + i would
+ * (same Philox counters and words, same site update).
  * Replica exchange: lattices sharing a ladder id (equal L required) are
  * ordered by initial beta; after every round the pairs of positions
  * (p, p+1), p = round mod 2, round mod 2 + 2, ..., swap temperatures iff
@@ -256,11 +256,16 @@ typedef struct {
     int32_t target_band_sites;  /* sites per CTA band of the work plan (0: 8192)     */
     int32_t algorithm;          /* XY_ALGO_AUTO / _FUSED: state ping-ponged between two
                                    buffers; lattices with L % 128 == 0 run the fused
-                                   sweep kernel (one launch per side and sweep), the
-                                   others a cluster kernel with one staging and one
-                                   cluster barrier per sweep, on parallel graph
-                                   branches; XY_ALGO_TWO_PASS: every lattice in place
-                                   in the cluster kernel, two of each per sweep */
+                                   sweep kernel's tiles and other multiples of 32 its
+                                   narrow tiles, in groups of about 128 CTAs (one launch
+                                   per group and sweep, groups on parallel graph
+                                   branches); lattices small enough for one CTA's shared
+                                   memory (L <= 96) run whole, one CTA each, all sweeps
+                                   of the round in one launch; the rest are cut into
+                                   bands of rows, the bands of a lattice one thread-
+                                   block cluster, one staging and one cluster barrier
+                                   per sweep; XY_ALGO_TWO_PASS: every lattice in place
+                                   in the cluster kernel, two barriers per sweep */
 } xy_batch_params;
 
 /* Create and hot/cold-start all lattices; the plan, ladders and buffers are
@@ -291,9 +296,9 @@ xy_status xy_batch_exchange_stats(xy_batch *b, int32_t *n_slots, int32_t *slot_l
                                   uint64_t *accepted, uint64_t *attempted);
 /* Angles of one lattice in natural order (L*L floats; synchronizes). */
 xy_status xy_batch_get_state(xy_batch *b, int32_t lattice, float *host_angles);
-/* Kernel launches one round replays: the grouped fused sweeps (groups x
- * sweeps_per_round), the cluster kernel if any lattice is banded, and the
- * exchange kernel. */
+/* Kernel launches one round replays: the grouped tile sweeps (groups x
+ * sweeps_per_round), the whole-lattice launch if any lattice runs whole, the
+ * cluster kernel if any lattice is banded, and the exchange kernel. */
 xy_status xy_batch_launches_per_round(const xy_batch *b, int32_t *launches);
 xy_status xy_batch_synchronize(xy_batch *b);
 
