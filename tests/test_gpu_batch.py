@@ -66,10 +66,11 @@ def test_narrow_tiles_match_single_lattices(sincos, reduce):
     one CTA run on the narrow tiles (32 rows x 16 plane columns): 5 x 5 (160,
     not a power of two), 6 x 6 (192) and 7 x 7 (224) tiles per lattice, several
     lattices of a side in one launch; next to them whole lattices (32, 64, 96,
-    and 96 twice, a thread per Philox pair; 30 and 90, L/2 odd, a thread per
-    site); all against the single-lattice two-pass kernels."""
-    Ls = [160, 192, 224, 160, 32, 64, 96, 96, 30, 90]
-    betas = [0.8, 1.0, 1.12, 1.3, 0.9, 1.2, 0.7, 1.05, 0.95, 1.15]
+    and 96 twice, and 4, one pair per row, a thread per Philox pair; 30 and
+    90, L/2 odd, a thread per site); all against the single-lattice two-pass
+    kernels."""
+    Ls = [160, 192, 224, 160, 32, 64, 96, 96, 30, 90, 4]
+    betas = [0.8, 1.0, 1.12, 1.3, 0.9, 1.2, 0.7, 1.05, 0.95, 1.15, 1.0]
     with Batch(Ls, betas, 31, lattice_id0=3, sweeps_per_round=3, sincos=sincos,
                reduce=reduce) as b:
         b.run(3)
