@@ -627,17 +627,21 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
     e = xyk::launch_start(b->d_theta + b->offset[i], b->L[i], rk, p->lattice_id0 + (uint32_t)i,
                           p->start == XY_START_HOT, b->stream);
   if (e == cudaSuccess) {
+    // A kernel's dynamic shared-memory limit is one value for the whole
+    // process, so it is set to the budget every plan stays within, not to this
+    // batch's need: a later batch of smaller lattices must not lower it under
+    // the launches an earlier batch has captured.
     step = "kernel attributes";
     e = b->fused ? xyk::prepare_batch_fused(p->sincos_mode, p->reduce_mode,
-                                            b->cs_bytes + xyk::batch_fused_tail_bytes())
+                                            kFusedStageBudget + xyk::batch_fused_tail_bytes())
                  : xyk::prepare_batch_round(p->sincos_mode, p->reduce_mode,
-                                            b->cs_bytes + xyk::batch_smem_bytes(0));
+                                            kStageBudget + xyk::batch_smem_bytes(0));
     if (e == cudaSuccess && !b->group_L.empty())
       e = xyk::prepare_fused_batch(p->sincos_mode, p->reduce_mode);
     if (e == cudaSuccess && !b->group_L.empty())
       e = xyk::prepare_narrow_batch(p->sincos_mode, p->reduce_mode);
     if (e == cudaSuccess && !b->small_lattices.empty())
-      e = xyk::prepare_small_batch(p->sincos_mode, p->reduce_mode, b->small_smem);
+      e = xyk::prepare_small_batch(p->sincos_mode, p->reduce_mode, xyk::kSmallBudget);
   }
   if (e == cudaSuccess) {
     step = "synchronize";

@@ -190,3 +190,21 @@ def test_batch_error_paths():
         Batch([512], [1.0], 1)                           # beyond the batch side limit
     with pytest.raises(X.XYError):
         Batch([15], [1.0], 1)                            # odd side
+
+
+def test_batches_alive_together_keep_their_launch_limits():
+    """A kernel's shared-memory limit is one value per process: a batch
+    created after another, with smaller lattices on the same kernels (whole
+    lattices 16 < 96, cluster bands 130 < 200), leaves the first one runnable
+    and its lattices as they would be alone."""
+    with Batch([96, 200], [1.0, 1.1], 5, sweeps_per_round=2) as a:
+        with Batch([16, 130], [1.0, 1.1], 6, sweeps_per_round=2) as b:
+            b.run(1)
+            a.run(1)
+            b.run(1)
+            states = [a.state(i) for i in range(2)]
+    for i, (L, beta) in enumerate(((96, 1.0), (200, 1.1))):
+        with Lattice(L, beta, 5, lattice_id=i, algorithm="two_pass") as lat:
+            lat.sweep(2)
+            s, _ = lat.state()
+        assert np.array_equal(states[i], s), f"L={L}"
