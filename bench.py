@@ -249,9 +249,9 @@ def run_reference(args):
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
-                   "sweeps_per_step": 1, "note": "each step: one oracle sweep of the "
-                   "full L=4096 lattice from the hot start (bounded sample of the 1000-sweep "
-                   "workload)"},
+                   "sweeps_per_step": 1, "note": f"each step: one oracle sweep of the "
+                   f"full L={w.L} lattice from the hot start (bounded sample of the "
+                   f"{w.sweeps}-sweep workload)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                          "sample": f"{args.steps} x 1 sweep of L={w.L} from the seed-{w.seed} "
                                    "hot start, OpenMP over the sites of one colour"},

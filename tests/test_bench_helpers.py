@@ -1,6 +1,7 @@
 """bench.py's bookkeeping on CPU: the issue-slot roofline arithmetic, the
-workload overrides, and that the committed DRAM-traffic record belongs to the
-kernel source as it is now (the bench reports traffic only then)."""
+workload overrides, that the committed DRAM-traffic record belongs to the
+kernel source as it is now (the bench reports traffic only then), and the
+reference arm's line (the oracle timed on the host cores)."""
 import argparse
 import json
 import os
@@ -47,3 +48,23 @@ def test_traffic_record_matches_the_kernel_source():
     assert bench.profiled_traffic() == d["dram_bytes_per_launch"]
     # about the algorithmic 8 B per update of the bench step it records
     assert 0.5 < d["dram_bytes_per_launch"] / d["algorithmic_bytes_per_launch"] < 1.5
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` times the oracle on the host cores (no GPU
+    needed) and prints the contract's line: impl, metric, value, unit, the
+    cpu_baseline it describes and an e2e with zero copies."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1", "--side", "64"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["config"]["L"] == 64 and "L=64" in d["config"]["note"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert "L=64" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
