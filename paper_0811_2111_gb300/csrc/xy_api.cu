@@ -15,6 +15,7 @@
 
 #include "xy.h"
 #include "xy_internal.h"
+#include "xy_trace.h"
 
 namespace {
 
@@ -412,6 +413,7 @@ xy_status xy_reserve(xy_ctx* c, int64_t n_more) {
 }
 
 xy_status xy_sweep(xy_ctx* c, int64_t n) {
+  const xyk::TraceRange trace("xy_sweep");
   xyk::NvtxRange range("xy_sweep");
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
@@ -530,6 +532,7 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
 }
 
 xy_status xy_measure(xy_ctx* c, int64_t first, int64_t count, xy_obs* out) {
+  const xyk::TraceRange trace("xy_measure");
   xy_status st = check_ctx(c);
   if (st != XY_OK) return st;
   if (first < 0 || count < 0 || first + count > c->rec_count)

@@ -18,6 +18,7 @@
 
 #include "xy.h"
 #include "xy_internal.h"
+#include "xy_trace.h"
 
 namespace {
 
@@ -664,6 +665,7 @@ xy_status xy_batch_reserve(xy_batch* b, int64_t n_rounds) {
 }
 
 xy_status xy_batch_run(xy_batch* b, int64_t rounds) {
+  const xyk::TraceRange trace("xy_batch_run");
   xyk::NvtxRange range("xy_batch_run");
   xy_status st = check_batch(b);
   if (st != XY_OK) return st;

@@ -17,6 +17,7 @@
 
 #include "xy_hmc.h"
 #include "xy_internal.h"
+#include "xy_trace.h"
 
 namespace {
 
@@ -461,6 +462,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
 }
 
 xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
+  const xyk::TraceRange trace("xy_hmc_run");
   xyk::NvtxRange range("xy_hmc_run");
   xy_status st = check(h);
   if (st != XY_OK) return st;
@@ -490,6 +492,7 @@ xy_status xy_hmc_run(xy_hmc* h, int64_t n_traj) {
 }
 
 xy_status xy_hmc_integrate(xy_hmc* h, int32_t n_steps) {
+  const xyk::TraceRange trace("xy_hmc_integrate");
   xyk::NvtxRange range("xy_hmc_integrate");
   xy_status st = check(h);
   if (st != XY_OK) return st;

@@ -27,6 +27,7 @@
 
 #include "xy_device.cuh"
 #include "xy_internal.h"
+#include "xy_trace.h"
 #include "xy_quad.h"
 
 namespace {
@@ -449,6 +450,7 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
 }
 
 xy_status xy_quad_sweep(xy_quad* q, int64_t n) {
+  const xyk::TraceRange trace("xy_quad_sweep");
   xyk::NvtxRange range("xy_quad_sweep");
   xy_status st = check(q);
   if (st != XY_OK) return st;
