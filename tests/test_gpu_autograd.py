@@ -56,21 +56,35 @@ def test_derivative_of_2x2_energy_is_exact(beta):
 
 
 def test_autograd_matches_finite_differences():
-    """Backward at beta vs (<e>(beta + 0.01) - <e>(beta - 0.01)) / 0.02, 8 chains each."""
+    """Backward at beta vs (<O>(beta + 0.01) - <O>(beta - 0.01)) / 0.02 for O = e and
+    O = Upsilon, 8 chains each; the covariance-only part of d<Upsilon>/dbeta (the
+    explicit-beta term -J^2 <Ix^2 + Iy^2> / (2N) left out) is reported beside it."""
     L, chains, therm, meas = 16, 8, 2000, 60000
     grid = [0.99, 1.0, 1.01]
     betas = torch.tensor([b for b in grid for _ in range(chains)], dtype=torch.float64,
                          requires_grad=True)
     e, u = chain_averages(betas, L, 11, therm, meas, sweeps_per_round=1000)
-    (g_e,) = torch.autograd.grad(e.sum(), betas)
-    e = e.detach().cpu().numpy().reshape(3, chains)
-    d = g_e.cpu().numpy().reshape(3, chains)
-    fd = (e[2] - e[0]) / 0.02
-    fd_err = np.hypot(e[2].std(ddof=1), e[0].std(ddof=1)) / np.sqrt(chains) / 0.02
-    bw, bw_err = d[1].mean(), d[1].std(ddof=1) / np.sqrt(chains)
-    print(f"d<e>/dbeta: backward {bw:.4f} +- {bw_err:.4f}, finite difference "
-          f"{fd.mean():.4f} +- {fd_err:.4f}")
-    assert abs(bw - fd.mean()) <= 3.5 * np.hypot(bw_err, fd_err)
+    (g_e,) = torch.autograd.grad(e.sum(), betas, retain_graph=True)
+    (g_u,) = torch.autograd.grad(u.sum(), betas)
+    with Batch([L] * chains, [grid[1]] * chains, 11, sweeps_per_round=1000,
+               lattice_id0=chains) as b:
+        b.run((therm + meas) // 1000)
+        s = b.series_stats(therm, meas).cpu().numpy()
+    for name, val, grad in (("e", e, g_e), ("Y", u, g_u)):
+        v = val.detach().cpu().numpy().reshape(3, chains)
+        d = grad.cpu().numpy().reshape(3, chains)
+        fd = (v[2] - v[0]) / 0.02
+        fd_err = np.hypot(v[2].std(ddof=1), v[0].std(ddof=1)) / np.sqrt(chains) / 0.02
+        bw, bw_err = d[1].mean(), d[1].std(ddof=1) / np.sqrt(chains)
+        extra = ""
+        if name == "Y":
+            extra = f" (covariance only {s[:, 5].mean():.4f})"
+            # the same chains' full and covariance-only parts differ by the
+            # explicit-beta term, which is negative
+            assert np.all(s[:, 4] < s[:, 5])
+        print(f"d<{name}>/dbeta: backward {bw:.4f} +- {bw_err:.4f}, finite difference "
+              f"{fd.mean():.4f} +- {fd_err:.4f}{extra}")
+        assert abs(bw - fd.mean()) <= 3.5 * np.hypot(bw_err, fd_err), name
 
 
 def test_autograd_matches_oracle_chains():

@@ -162,6 +162,31 @@ def test_replica_exchange_samples_exact_2x2_energies():
         assert abs(m - ex.e_2x2_bessel(beta)) <= 3.5 * err + 1e-6
 
 
+def test_replica_exchange_ladder_energies_match_oracle_chains():
+    """One L = 16 ladder of the replica-exchange workload's kind (8 lattices on every
+    eighth point of its 64-point beta grid, exchange every 10 sweeps): <e> at each
+    beta, collected from whichever lattice holds that beta, against the oracle's
+    parallel-tempering chains (independent seed) within 3.5 sigma, binned jackknife."""
+    L, spr, rounds, therm = 16, 10, 2000, 200
+    betas = [WL.BATCH_BETA_GRID[4 + 8 * i] for i in range(8)]
+    with Batch([L] * 8, betas, 41, ladders=[0] * 8, sweeps_per_round=spr) as b:
+        b.run(rounds)
+        obs = [b.observables(i) for i in range(8)]
+    e_g = np.stack([o["e"] for o in obs])
+    b_g = np.stack([o["beta"] for o in obs])
+    rec = oracle.pt_run(L, L, betas, rounds, spr, seed=4242)
+    e_o = -rec[:, :, 0] / (L * L)
+    b_o = rec[:, :, 6]
+    for beta in betas:
+        sg = e_g.T[b_g.T == beta]
+        so = e_o.T[b_o.T == beta]
+        assert sg.size == so.size == rounds * spr
+        mg, eg = jackknife_mean(sg[therm * spr:])
+        mo, eo = jackknife_mean(so[therm * spr:])
+        print(f"beta {beta:.4f}: gpu {mg:.5f} +- {eg:.5f}, oracle {mo:.5f} +- {eo:.5f}")
+        assert abs(mg - mo) <= 3.5 * np.hypot(eg, eo)
+
+
 def test_replica_exchange_configuration_runs():
     """The batched workload: 256 lattices, 8 ladders of 32 over a 64-point beta grid."""
     Ls, betas, ladders = WL.batch_layout()
