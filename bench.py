@@ -63,11 +63,13 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["large", "huge", "batch", "hmc", "quad"], default="large",
+    ap.add_argument("--workload", choices=["large", "huge", "batch", "hmc", "quad", "peaks"],
+                    default="large",
                     help="large: L=4096, 1000 sweeps/step; huge: L=16384, 200 sweeps/step; "
                          "batch: 256 lattices with replica exchange, 100 rounds/step; "
                          "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step; "
-                         "quad: four replicas per site at L=4096, 200 sweeps per step")
+                         "quad: four replicas per site at L=4096, 200 sweeps per step; "
+                         "peaks: the instruction-rate microbenchmarks alone")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
@@ -176,14 +178,18 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def alu_roofline(updates_per_s, sincos, clk_mhz):
+def alu_roofline(updates_per_s, sincos, clk_mhz, issue_per_sm_clk=None):
     """Issue-slot roofline of a Metropolis workload: algorithmic instructions per
-    update x updates/s against 152 SMs x 4 schedulers x 32 lanes x clock."""
+    update x updates/s against SMs x the measured issue rate per SM and clock
+    (xy_peak_measure's issue kind; nominal 4 schedulers x 32 lanes if unmeasured)
+    x the SM clock."""
     instr = ALG_INSTR_PER_UPDATE[sincos]
-    peak = SMS * SMSP_PER_SM * LANES * clk_mhz * 1e6 / 1e12
+    per_clk = issue_per_sm_clk or SMSP_PER_SM * LANES
+    peak = SMS * per_clk * clk_mhz * 1e6 / 1e12
     achieved = instr * updates_per_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
             "frac": achieved / peak, "algorithmic_instr_per_update": instr,
+            "peak_kind": "measured" if issue_per_sm_clk else "nominal",
             "basis": "whole-run throughput (launch gaps included)"}
 
 
@@ -194,6 +200,39 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+# Loop iterations per thread of each instruction-rate microbenchmark
+# (include/xy_peaks.h), sized for launches of a few milliseconds on GB300.
+PEAK_ITERS = {"ffma": 32768, "imad": 16384, "imad_wide": 8192, "imad_hi": 16384,
+              "lop3": 16384, "iadd": 16384, "mufu_sin": 4096, "mufu_ex2": 4096, "f2i": 4096,
+              "dfma": 512, "issue": 16384, "philox": 512, "unit_vector": 1536,
+              "unit_vector_sfu": 2048, "expf": 3072}
+
+
+def measure_peaks(dev, kinds=None, reps=5):
+    """Measured instruction rates of this GPU (xy_peak_measure): per kind the
+    operations per second over the GPU and per SM per clock at the median SM
+    clock sampled while they ran."""
+    from paper_0811_2111_gb300 import _lib as X
+    import torch
+    kinds = kinds or list(PEAK_ITERS)
+    stream = torch.cuda.current_stream(dev)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sampler = ClockSampler(str(dev.index or 0))
+    sampler.start()
+    raw = {}
+    for k in kinds:
+        rate, ms, ops = X.xy_peak_measure(k, PEAK_ITERS[k], reps, C.c_void_p(stream.cuda_stream))
+        raw[k] = (rate, ms)
+    clocks = sampler.stop()
+    clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    out = {"sm_mhz": clk, "sms": sms, "clock_reasons": clocks.get("reasons"), "kinds": {}}
+    for k, (rate, ms) in raw.items():
+        out["kinds"][k] = {"ops_per_s": rate, "per_sm_per_clock": rate / (sms * clk * 1e6),
+                           "best_ms": ms}
+    return out
 
 
 def profiled_traffic():
@@ -644,6 +683,12 @@ def run_ours(args):
         return run_hmc_line(args, dev, world, rank)
     if args.workload == "quad":
         return run_quad_line(args, dev, world, rank)
+    if args.workload == "peaks":
+        p = measure_peaks(dev)
+        if rank == 0:
+            print(json.dumps({"metric": "instruction rates (xy_peak_measure)", "peaks": p}),
+                  flush=True)
+        return 0
 
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
@@ -661,6 +706,10 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
+
+    # the instruction-rate microbenchmarks: the roofline's measured peaks
+    peaks = measure_peaks(dev)
+    issue_clk = peaks["kinds"]["issue"]["per_sm_per_clock"]
 
     props = torch.cuda.get_device_properties(dev)
     gpu_id = getattr(props, "uuid", None)
@@ -725,17 +774,24 @@ def run_ours(args):
     hbm_achieved = alg_bytes / avg_s / 1e9
     names = (["sweep_fused_persist"] if persistent else
              ["sweep_fused"] if fused else ["red_half_sweep", "black_half_sweep_measure"])
-    # issue-slot roofline: 152 SMs x 4 schedulers x 32 lanes per clock at the
-    # median SM clock sampled during the timed region (max clock if unsampled)
+    # issue-slot roofline: the measured issue rate per SM and clock
+    # (xy_peak_measure, issue kind) x SMs x the median SM clock sampled during
+    # the timed region (max clock if unsampled)
     clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
-    alu_peak = SMS * SMSP_PER_SM * LANES * clk * 1e6 / 1e12          # T instr/s
+    alu_peak = SMS * issue_clk * clk * 1e6 / 1e12                     # T instr/s
+    nominal_peak = SMS * SMSP_PER_SM * LANES * clk * 1e6 / 1e12
     instr = ALG_INSTR_PER_UPDATE[args.sincos]
     alu_achieved = instr * updates_per_launch / avg_s / 1e12
     roofline = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tinstr/s",
                 "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(),
                 "kernel": names[kern], "kernel_avg_us": avg_s * 1e6,
                 "algorithmic_instr_per_update": instr,
-                "peak_basis": f"{SMS} SMs x {SMSP_PER_SM} schedulers x {LANES} lanes x {clk:.0f} MHz",
+                "peak_kind": "measured",
+                "peak_basis": (f"{SMS} SMs x {issue_clk:.2f} thread-instructions per SM and clock "
+                               f"(xy_peak_measure issue kind, measured at "
+                               f"{peaks['sm_mhz']:.0f} MHz in this run) x {clk:.0f} MHz"),
+                "peak_nominal": nominal_peak,
+                "frac_of_nominal": alu_achieved / nominal_peak,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
                         "frac": hbm_achieved / hbm_peak, "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": alg_bytes},
@@ -767,7 +823,8 @@ def run_ours(args):
         # Metropolis workload (launch gaps included: a lower bound on the kernels')
         clk = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
         for key in ("batch", "differentiation", "quad"):
-            extra[key]["roofline"] = alu_roofline(extra[key]["value"], args.sincos, clk)
+            extra[key]["roofline"] = alu_roofline(extra[key]["value"], args.sincos, clk,
+                                                  issue_clk)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
@@ -780,7 +837,7 @@ def run_ours(args):
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks, "other_workloads": extra,
+        "clocks": clocks, "peaks": peaks, "other_workloads": extra,
     }
     lat.close()
     if rank == 0:
@@ -823,6 +880,7 @@ def run_quad_line(args, dev, world, rank, sweeps_per_step=200):
     from paper_0811_2111_gb300.lattice import Quad
 
     L = 4096
+    issue_clk = measure_peaks(dev, kinds=["issue"])["kinds"]["issue"]["per_sm_per_clock"]
     sampler = ClockSampler(str(dev.index or 0))
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     with Quad(L, [1.0, 1.06, 1.12, 1.18], 7, sincos=args.sincos, lattice_id=4 * rank,
@@ -858,7 +916,7 @@ def run_quad_line(args, dev, world, rank, sweeps_per_step=200):
                        "kernel": "fused single-pass" if algo == "fused" else "two-pass red/black",
                        "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": alu_roofline(value / world, args.sincos, clk),
+            "roofline": alu_roofline(value / world, args.sincos, clk, issue_clk),
             "gpu_launches": per_sweep * sweeps_per_step * args.steps + args.steps,
             "clocks": clocks}
     if rank == 0:

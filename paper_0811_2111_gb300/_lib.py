@@ -153,6 +153,9 @@ def lib():
         "xy_quad_synchronize": (st, [P]),
         "xy_quad_destroy": (st, [P]),
         "xy_quad_last_error": (C.c_char_p, [P]),
+        "xy_peak_measure": (st, [C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "xy_peak_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -271,6 +274,23 @@ def xy_sweep_noalloc(params, d_angles_ptr, first_sweep, n_sweeps, d_records_ptr,
 
 def xy_version():
     return int(lib().xy_version())
+
+
+# -- instruction-rate microbenchmarks (include/xy_peaks.h) --------------------
+
+PEAK_KINDS = ("ffma", "imad", "imad_wide", "imad_hi", "lop3", "iadd", "mufu_sin", "mufu_ex2",
+              "f2i", "dfma", "issue", "philox", "unit_vector", "unit_vector_sfu", "expf")
+
+
+def xy_peak_measure(kind, iters, reps=5, stream_ptr=None):
+    """(ops/s over the GPU, best launch ms, ops per launch) of one xy_peak_kind."""
+    k = PEAK_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    rate, ms, ops = C.c_double(), C.c_double(), C.c_double()
+    st = lib().xy_peak_measure(k, int(iters), int(reps), stream_ptr, C.byref(rate), C.byref(ms),
+                               C.byref(ops))
+    if st != XY_OK:
+        raise XYError(st, lib().xy_peak_last_error().decode())
+    return rate.value, ms.value, ops.value
 
 
 # -- batches ------------------------------------------------------------------

@@ -219,3 +219,16 @@ def test_sincos_polynomial_constants_are_the_fit():
         c = -c0 if (q & 3) in (1, 2) else c0
         worst = max(worst, abs(float(s) - np.sin(float(t))), abs(float(c) - np.cos(float(t))))
     assert worst < 7e-8, worst
+
+
+def test_peak_measure_refuses_bad_arguments_before_the_device(lib):
+    rate = C.c_double()
+    for kind, iters, reps in ((-1, 16, 1), (len(X.PEAK_KINDS), 16, 1), (0, 0, 1),
+                              (0, (1 << 20) + 1, 1), (0, 16, 0), (0, 16, 101)):
+        st = lib.xy_peak_measure(kind, iters, reps, None, C.byref(rate), None, None)
+        assert st == X.XY_EINVAL, (kind, iters, reps)
+    assert lib.xy_peak_measure(0, 16, 1, None, None, None, None) == X.XY_EINVAL
+    assert b"bad kind" in lib.xy_peak_last_error()
+    # one microbenchmark per kind and one iteration table entry per kind
+    import bench
+    assert tuple(bench.PEAK_ITERS) == X.PEAK_KINDS

@@ -30,7 +30,7 @@ from paper_0811_2111_gb300.lattice import Lattice  # noqa: E402
 def _device_records(ptr, n):
     """Copy of n xy_record structs (8 words of 64 bits each) at a device address."""
     class _View:
-        __cuda_array_interface__ = {"shape": (n, 8), "typestr": "<i8", "data": (ptr, True),
+        __cuda_array_interface__ = {"shape": (n, 8), "typestr": "<i8", "data": (ptr, False),
                                     "version": 3}
     return torch.as_tensor(_View(), device="cuda").clone()
 
