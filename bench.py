@@ -70,6 +70,9 @@ def parse():
                          "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step; "
                          "quad: four replicas per site at L=4096, 200 sweeps per step; "
                          "peaks: the instruction-rate microbenchmarks alone")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, choices=[0, 2, 3],
+                    help="work plan of the fused sweep: tile CTAs per SM (0: the library's "
+                         "default)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads reported beside the main line")
     ap.add_argument("--sweeps", type=int, default=None,
@@ -207,7 +210,8 @@ def measured_peaks():
 PEAK_ITERS = {"ffma": 32768, "imad": 16384, "imad_wide": 8192, "imad_hi": 16384,
               "lop3": 16384, "iadd": 16384, "mufu_sin": 4096, "mufu_ex2": 4096, "f2i": 4096,
               "dfma": 512, "issue": 16384, "philox": 512, "unit_vector": 1536,
-              "unit_vector_sfu": 2048, "expf": 3072}
+              "unit_vector_sfu": 2048, "expf": 3072, "unit_vector_table": 2048,
+              "unit_vector_table_smem": 2048}
 
 
 def measure_peaks(dev, kinds=None, reps=5):
@@ -638,7 +642,7 @@ def measure_precision(dev, sweeps=200):
 
     w = WL.HUGE
     out = {"workload": w.name, "unit": UNIT, "variants": {}}
-    for sincos, reduce in (("accurate", "fp64"), ("fast", "fp64"), ("libm", "fp64"),
+    for sincos, reduce in (("accurate", "exact"), ("fast", "exact"), ("libm", "exact"),
                            ("accurate", "compensated")):
         with Lattice(w.L, w.beta, w.seed, sincos=sincos, reduce=reduce, device=dev) as lat:
             lat.reserve(sweeps + 3)
@@ -693,7 +697,7 @@ def run_ours(args):
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
     lat = Lattice(w.L, w.beta, w.seed, device=dev, stream=stream, lattice_id=rank,
-                  sincos=args.sincos, algorithm=args.algorithm)
+                  sincos=args.sincos, algorithm=args.algorithm, ctas_per_sm=args.ctas_per_sm)
     persistent = lat.algorithm == "persistent"        # what AUTO resolved to
     fused = lat.algorithm in ("fused", "persistent")
     lat.reserve(w.sweeps)
@@ -831,9 +835,10 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
-                   "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "fp64",
+                   "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "exact",
                    "kernel": ("persistent fused (one cooperative launch per step)" if persistent
                               else "fused single-pass" if fused else "two-pass red/black"),
+                   "ctas_per_sm": args.ctas_per_sm or 3,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -84,7 +84,17 @@ enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
  *                      with XY_ECUDA otherwise).
  * All make bit-identical decisions. */
 enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2, XY_ALGO_PERSISTENT = 3 };
-enum { XY_REDUCE_FP64 = 0, XY_REDUCE_COMPENSATED = 1 };
+/* Per-sweep sums (records below):
+ *   XY_REDUCE_EXACT        every per-site term is rounded to fixed point
+ *                          (2^-19 for the four bond cosines of a site, 2^-20
+ *                          for the other terms: one FMA each) before any
+ *                          addition, and the integers are added exactly, so
+ *                          a record is independent of the order of addition:
+ *                          every algorithm and batch plan gives the same bits;
+ *   XY_REDUCE_COMPENSATED  Neumaier-compensated FP32 sums per CTA, FP64 over
+ *                          the CTA's partials, then fixed point (results may
+ *                          differ in the last bits between algorithms). */
+enum { XY_REDUCE_EXACT = 0, XY_REDUCE_COMPENSATED = 1 };
 
 /* Largest supported side (N = L^2 must fit the 32-bit site counter and the
  * fixed-point record sums). */
@@ -98,14 +108,20 @@ typedef struct {
     double delta;         /* proposal half-window, 0 < delta <= pi              */
     uint64_t seed;        /* Philox key                                         */
     int32_t sincos_mode;  /* XY_SINCOS_ACCURATE, _FAST or _LIBM                 */
-    int32_t reduce_mode;  /* XY_REDUCE_FP64 or XY_REDUCE_COMPENSATED            */
+    int32_t reduce_mode;  /* XY_REDUCE_EXACT or XY_REDUCE_COMPENSATED           */
     uint32_t lattice_id;  /* third Philox counter word                          */
     int32_t algorithm;    /* XY_ALGO_AUTO, _FUSED or _PERSISTENT (need L % 128 == 0), _TWO_PASS */
+    int32_t ctas_per_sm;  /* work plan of the fused and persistent sweeps: 3 CTAs of the
+                             tile kernel per SM (at most 80 registers a thread), 2 (at
+                             most 128: more independent work in flight per warp, fewer
+                             warps), or 0 for the library's default (3).  Results do not
+                             depend on it; xy_tune-style callers time both. */
 } xy_params;
 
 /* Per-sweep record as stored on the device (64 bytes).  The five sums are
- * signed fixed point in units of 2^-XY_FX_SHIFT (exact, order-independent
- * integer accumulation of FP64 block sums):
+ * signed fixed point in units of 2^-XY_FX_SHIFT, accumulated with integer
+ * atomics (order-independent; with XY_REDUCE_EXACT exact sums of the
+ * per-site terms rounded to 2^-19 / 2^-20):
  *   sum[0] = C  = sum_s cos(t_s - t_{s+x}) + cos(t_s - t_{s+y})
  *   sum[1] = Ix = sum_s sin(t_s - t_{s+x})
  *   sum[2] = Iy = sum_s sin(t_s - t_{s+y})
@@ -181,6 +197,14 @@ xy_status xy_algorithm(const xy_ctx *ctx, int32_t *algorithm);
  * cuda_stream, synchronizes it; allocates and frees ~130 KB of device memory.
  * Exists to test the failure path; the paper has no counterpart. */
 xy_status xy_selftest_persistent_wait(void *cuda_stream, int64_t polls);
+
+/* Test hook of the out-of-memory paths: the k-th device allocation made by
+ * the library after this call (k >= 1; counted across every engine and thread
+ * of the process) fails as if the device were out of memory, without reaching
+ * the driver; k = 0 disarms the hook.  The failing call returns XY_ENOMEM,
+ * frees what it had allocated and leaves the device usable.  Returns XY_EINVAL
+ * for k < 0.  Exists to test the failure path; the paper has no counterpart. */
+xy_status xy_debug_fail_alloc(int32_t k);
 
 /* Copy the angles (natural order, L*L floats) to host memory and report the
  * next sweep index.  Synchronizes. */

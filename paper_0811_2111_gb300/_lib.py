@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "X
 XY_START_HOT, XY_START_COLD = 0, 1
 XY_SINCOS_ACCURATE, XY_SINCOS_FAST, XY_SINCOS_LIBM = 0, 1, 2
 XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS, XY_ALGO_PERSISTENT = 0, 1, 2, 3
-XY_REDUCE_FP64, XY_REDUCE_COMPENSATED = 0, 1
+XY_REDUCE_EXACT, XY_REDUCE_COMPENSATED = 0, 1
 XY_FX_SHIFT = 30
 XY_MAX_L = 32768
 
@@ -31,7 +31,8 @@ class XYError(RuntimeError):
 class xy_params(C.Structure):
     _fields_ = [("L", C.c_int32), ("start", C.c_int32), ("beta", C.c_double), ("J", C.c_double),
                 ("delta", C.c_double), ("seed", C.c_uint64), ("sincos_mode", C.c_int32),
-                ("reduce_mode", C.c_int32), ("lattice_id", C.c_uint32), ("algorithm", C.c_int32)]
+                ("reduce_mode", C.c_int32), ("lattice_id", C.c_uint32), ("algorithm", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
 
 
 class xy_record(C.Structure):
@@ -156,6 +157,7 @@ def lib():
         "xy_peak_measure": (st, [C.c_int32, C.c_int32, C.c_int32, P, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "xy_peak_last_error": (C.c_char_p, []),
+        "xy_debug_fail_alloc": (st, [C.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -279,7 +281,8 @@ def xy_version():
 # -- instruction-rate microbenchmarks (include/xy_peaks.h) --------------------
 
 PEAK_KINDS = ("ffma", "imad", "imad_wide", "imad_hi", "lop3", "iadd", "mufu_sin", "mufu_ex2",
-              "f2i", "dfma", "issue", "philox", "unit_vector", "unit_vector_sfu", "expf")
+              "f2i", "dfma", "issue", "philox", "unit_vector", "unit_vector_sfu", "expf",
+              "unit_vector_table", "unit_vector_table_smem")
 
 
 def xy_peak_measure(kind, iters, reps=5, stream_ptr=None):

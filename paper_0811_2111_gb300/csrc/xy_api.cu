@@ -159,13 +159,17 @@ xy_status validate(const xy_params* p) {
     set_thread_msg("bad sincos_mode");
     return XY_EINVAL;
   }
-  if (p->reduce_mode != XY_REDUCE_FP64 && p->reduce_mode != XY_REDUCE_COMPENSATED) {
+  if (p->reduce_mode != XY_REDUCE_EXACT && p->reduce_mode != XY_REDUCE_COMPENSATED) {
     set_thread_msg("bad reduce_mode");
     return XY_EINVAL;
   }
   if (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
       p->algorithm != XY_ALGO_TWO_PASS && p->algorithm != XY_ALGO_PERSISTENT) {
     set_thread_msg("bad algorithm");
+    return XY_EINVAL;
+  }
+  if (p->ctas_per_sm != 0 && p->ctas_per_sm != 2 && p->ctas_per_sm != 3) {
+    set_thread_msg("ctas_per_sm must be 0 (default), 2 or 3; got %d", p->ctas_per_sm);
     return XY_EINVAL;
   }
   if ((p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_PERSISTENT) &&
@@ -181,7 +185,7 @@ xy_status grow_records(xy_ctx* c, int64_t need) {
   int64_t cap = c->rec_cap > 0 ? c->rec_cap : 1024;
   while (cap < need) cap *= 2;
   xy_record* nr = nullptr;
-  XY_CUDA(c, cudaMalloc(&nr, (size_t)cap * sizeof(xy_record)), "allocating records");
+  XY_CUDA(c, xyk::dev_malloc(&nr, (size_t)cap * sizeof(xy_record)), "allocating records");
   cudaError_t e = cudaMemsetAsync(nr, 0, (size_t)cap * sizeof(xy_record), c->stream);
   if (e == cudaSuccess && c->rec_count > 0)
     e = cudaMemcpyAsync(nr, c->d_rec, (size_t)c->rec_count * sizeof(xy_record),
@@ -320,21 +324,21 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
       c->d_theta = static_cast<float*>(d_angles);
       c->owns_theta = false;
     } else {
-      e = cudaMalloc(&c->d_theta, N * sizeof(float));
+      e = xyk::dev_malloc(&c->d_theta, N * sizeof(float));
       c->owns_theta = true;
     }
   }
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_flag, sizeof(unsigned int));
+  if (e == cudaSuccess) e = xyk::dev_malloc(&c->d_flag, sizeof(unsigned int));
   c->persistent = p->algorithm == XY_ALGO_PERSISTENT ||
                   (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L) &&
                    p->L <= kAutoPersistentMaxL);
   c->auto_persistent = c->persistent && p->algorithm == XY_ALGO_AUTO;
   c->fused = p->algorithm == XY_ALGO_FUSED || c->persistent ||
              (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
-  if (e == cudaSuccess && c->fused) e = cudaMalloc(&c->d_pong, N * sizeof(float));
+  if (e == cudaSuccess && c->fused) e = xyk::dev_malloc(&c->d_pong, N * sizeof(float));
   if (e == cudaSuccess && c->persistent) {
-    e = cudaMalloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_wait, sizeof(unsigned int));
+    e = xyk::dev_malloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
+    if (e == cudaSuccess) e = xyk::dev_malloc(&c->d_wait, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wait, 0, sizeof(unsigned int), c->stream);
   }
   if (e != cudaSuccess) {
@@ -440,6 +444,7 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.error = c->d_wait;
     a.spin_limit = xyk::fused_persistent_spin_limit();
     a.skip_items = 0;
+    a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : 3;
     // one launch per at most fused_persistent_max_sweeps sweeps (the kernel's
     // work items are counted in 32 bits)
     const int64_t chunk = xyk::fused_persistent_max_sweeps(c->p.L);
@@ -461,6 +466,7 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
         f.rk = a.rk;
         f.lattice_id = a.lattice_id;
         f.beta = a.beta;
+        f.minb = a.minb;
         for (int64_t i = 0; i < m; ++i) {
           f.src = a.buf[i & 1];
           f.dst = a.buf[(i + 1) & 1];
@@ -489,6 +495,7 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.rk = rk;
     a.lattice_id = c->p.lattice_id;
     a.beta = c->p.beta;
+    a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : 3;
     float* cur = c->d_theta;
     float* nxt = c->d_pong;
     for (int64_t i = 0; i < n; ++i) {
@@ -617,9 +624,9 @@ xy_status xy_selftest_persistent_wait(void* cuda_stream, int64_t polls) {
   unsigned int* words = nullptr;      // tile counters, work counter, error word
   xy_record* rec = nullptr;
   unsigned int err = 0;
-  cudaError_t e = cudaMalloc(&buf, 2 * N * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&words, sizeof(unsigned int) * (size_t)(tiles + 2));
-  if (e == cudaSuccess) e = cudaMalloc(&rec, 2 * sizeof(xy_record));
+  cudaError_t e = xyk::dev_malloc(&buf, 2 * N * sizeof(float));
+  if (e == cudaSuccess) e = xyk::dev_malloc(&words, sizeof(unsigned int) * (size_t)(tiles + 2));
+  if (e == cudaSuccess) e = xyk::dev_malloc(&rec, 2 * sizeof(xy_record));
   if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 2 * N * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(words, 0, sizeof(unsigned int) * (size_t)(tiles + 2), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(rec, 0, 2 * sizeof(xy_record), s);
@@ -642,7 +649,7 @@ xy_status xy_selftest_persistent_wait(void* cuda_stream, int64_t polls) {
     a.error = words + tiles + 1;
     a.spin_limit = (long long)polls;
     a.skip_items = tiles;
-    e = xyk::launch_fused_persistent(XY_SINCOS_ACCURATE, XY_REDUCE_FP64, a, s);
+    e = xyk::launch_fused_persistent(XY_SINCOS_ACCURATE, XY_REDUCE_EXACT, a, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&err, a.error, sizeof(err), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -669,7 +676,7 @@ xy_status xy_get_state(xy_ctx* c, float* host, uint64_t* next_sweep) {
   if (st != XY_OK) return st;
   if (!host) return fail(c, XY_EINVAL, "xy_get_state: NULL output");
   const size_t N = (size_t)c->p.L * (size_t)c->p.L;
-  if (!c->d_scratch) XY_CUDA(c, cudaMalloc(&c->d_scratch, N * sizeof(float)), "xy_get_state: scratch");
+  if (!c->d_scratch) XY_CUDA(c, xyk::dev_malloc(&c->d_scratch, N * sizeof(float)), "xy_get_state: scratch");
   XY_CUDA(c, xyk::launch_split_to_natural(c->d_theta, c->d_scratch, c->p.L, c->stream),
           "xy_get_state: layout kernel");
   XY_CUDA(c, cudaMemcpyAsync(host, c->d_scratch, N * sizeof(float), cudaMemcpyDeviceToHost,
@@ -688,7 +695,7 @@ xy_status xy_set_state(xy_ctx* c, const float* host, uint64_t next_sweep) {
   if (!host) return fail(c, XY_EINVAL, "xy_set_state: NULL input");
   if (next_sweep > 0xffffffffull) return fail(c, XY_EINVAL, "xy_set_state: sweep >= 2^32");
   const size_t N = (size_t)c->p.L * (size_t)c->p.L;
-  if (!c->d_scratch) XY_CUDA(c, cudaMalloc(&c->d_scratch, N * sizeof(float)), "xy_set_state: scratch");
+  if (!c->d_scratch) XY_CUDA(c, xyk::dev_malloc(&c->d_scratch, N * sizeof(float)), "xy_set_state: scratch");
   XY_CUDA(c, cudaMemcpyAsync(c->d_scratch, host, N * sizeof(float), cudaMemcpyHostToDevice,
                              c->stream),
           "xy_set_state: copy");

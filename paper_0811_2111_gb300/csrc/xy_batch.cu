@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_round(BatchArgs a) {
         __syncthreads();
         // 2. update this colour's sites of the band
         unsigned int n_acc = 0;
-        float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        xyd::SweepSums<RED> sums;
+        sums.init();
         if (lane_on) {
           for (int r = ty; r < rows; r += ty_n) {
             const int y = band.y_begin + r;
@@ -123,25 +123,20 @@ __global__ void __launch_bounds__(kThreads) k_batch_round(BatchArgs a) {
                 float v[5];
                 xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc,
                                    Ss, m.x, m.y, v);
-#pragma unroll
-                for (int i = 0; i < 5; ++i) {
-                  if (RED == 0) {
-                    acc[i] += v[i];
-                  } else {
-                    xyd::neumaier_add(acc[i], cmp[i], v[i]);
-                  }
-                }
+                sums.add(v);
               }
             }
           }
         }
         // 3. the sweep's record (the red half adds only its accept count)
+        // a thread may hold more than 31 terms here: the wide warp reduction
         if (colour == 0) {
-          xyd::commit_block<kWarps, RED, false>(acc, cmp, n_acc, part, cnt, rec + sweep - a.rec_sweep0,
-                                                beta, false);
+          xyd::commit_sums<kWarps, RED, false, true>(sums, n_acc, part, cnt,
+                                                     rec + sweep - a.rec_sweep0, beta, false);
         } else {
-          xyd::commit_block<kWarps, RED, true>(acc, cmp, n_acc, part, cnt, rec + sweep - a.rec_sweep0,
-                                               beta, band.y_begin == 0);
+          xyd::commit_sums<kWarps, RED, true, true>(sums, n_acc, part, cnt,
+                                                    rec + sweep - a.rec_sweep0, beta,
+                                                    band.y_begin == 0);
         }
         __threadfence();
       }
@@ -278,8 +273,8 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_batch_fused(BatchArgs a) {
       }
       __syncthreads();
       // 3. black: the band rows (stage rows 2 .. R+1), with the sweep sums
-      float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      xyd::SweepSums<RED> sums;
+      sums.init();
       if (lane_on) {
         for (int sr = 2 + ty; sr <= R + 1; sr += ty_n) {
           const int y = band.y_begin - 2 + sr;
@@ -306,20 +301,14 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_batch_fused(BatchArgs a) {
             float v[5];
             xyd::measure_terms(res.c, res.s, l.x, l.y, rt.x, rt.y, d.x, d.y, u.x, u.y, Sc, Ss,
                                m.x, m.y, v);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-              if (RED == 0) {
-                acc[i] += v[i];
-              } else {
-                xyd::neumaier_add(acc[i], cmp[i], v[i]);
-              }
-            }
+            sums.add(v);
           }
         }
       }
-      xyd::commit_block<kFusedWarps, RED, true>(acc, cmp, n_acc, part, cnt,
-                                                rec + sweep - a.rec_sweep0, beta,
-                                                band.y_begin == 0);
+      // a thread may hold more than 31 terms here: the wide warp reduction
+      xyd::commit_sums<kFusedWarps, RED, true, true>(sums, n_acc, part, cnt,
+                                                     rec + sweep - a.rec_sweep0, beta,
+                                                     band.y_begin == 0);
     }
     // every band of the lattice has written this sweep before any reads it:
     // the cluster barrier's arrive has release and its wait acquire semantics

@@ -300,7 +300,7 @@ xy_status grow(xy_batch* b, int64_t need) {
   int64_t cap = std::max<int64_t>(b->rec_cap > 0 ? b->rec_cap : 256, 16);
   while (cap < need) cap *= 2;
   xy_record* nr = nullptr;
-  B_CUDA(b, cudaMalloc(&nr, sizeof(xy_record) * (size_t)cap * b->n), "batch records");
+  B_CUDA(b, xyk::dev_malloc(&nr, sizeof(xy_record) * (size_t)cap * b->n), "batch records");
   cudaError_t e = cudaMemsetAsync(nr, 0, sizeof(xy_record) * (size_t)cap * b->n, b->stream);
   if (e == cudaSuccess && b->rec_count > 0)
     e = cudaMemcpy2DAsync(nr, sizeof(xy_record) * cap, b->d_rec, sizeof(xy_record) * b->rec_cap,
@@ -568,7 +568,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) step = "allocations";
   auto alloc = [&](void** ptr, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) e = xyk::dev_malloc(ptr, std::max<size_t>(bytes, 16));
   };
   alloc((void**)&b->d_theta, sizeof(float) * (size_t)std::max<int64_t>(total, 4));
   if (b->fused) alloc((void**)&b->d_theta2, sizeof(float) * (size_t)std::max<int64_t>(total, 4));

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "xy.h"
+#include "xy_sincos_table.h"
 
 namespace xyd {
 
@@ -154,6 +155,29 @@ __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out)
   *c_out = __uint_as_float(__float_as_uint(c0) ^ ((qs + 0x40000000u) & 0x80000000u));
 }
 
+// Unit vector by table and rotation: t = k h + r with h = 2 pi / 1024,
+// k = rint(t / h) and |r| <= h / 2 (Cody-Waite reduction with a two-part h
+// whose high part has 13 significant bits, so k h_hi is exact); then
+//   (cos t, sin t) = (C_k cos r - S_k sin r, S_k cos r + C_k sin r)
+// with (C_k, S_k) from the table (xy_sincos_table.h: FP32 cos and sin of
+// 2 pi k / 1024, each within 0.6 ulp), cos r ~ 1 - r^2 / 2 and sin r ~ r
+// (truncation errors r^4 / 24 < 4e-12 and r^3 / 6 < 5e-9), the small
+// corrections formed first and added to the table value last, so the result
+// is within about one FP32 rounding of the table value's own error.
+// `tab` points at the 1024 (C, S) pairs, in shared or global memory.
+__device__ __forceinline__ void sincos_table(float t, const float2* tab, float* s_out,
+                                             float* c_out) {
+  const float qt = __fmaf_rn(t, __uint_as_float(kTabInvStepBits), kRoundMagic);
+  const int k = __float_as_int(qt) & (kSinCosTableSize - 1);   // k mod 1024
+  const float kf = __fsub_rn(qt, kRoundMagic);
+  float r = __fmaf_rn(-kf, __uint_as_float(kTabStepHiBits), t);   // exact
+  r = __fmaf_rn(-kf, __uint_as_float(kTabStepLoBits), r);
+  const float2 e = tab[k];
+  const float r2h = __fmul_rn(__fmul_rn(r, -0.5f), r);              // cos r - 1
+  *c_out = __fadd_rn(e.x, __fmaf_rn(e.x, r2h, -__fmul_rn(e.y, r)));
+  *s_out = __fadd_rn(e.y, __fmaf_rn(e.y, r2h, __fmul_rn(e.x, r)));
+}
+
 // Precision switch of the fused kernels: 0 = the polynomial above with CUDA's
 // expf, 1 = the SFU intrinsics __sincosf/__expf, 2 = CUDA's sincosf/expf.
 template <int MODE>
@@ -211,8 +235,11 @@ __device__ __forceinline__ SiteResult metropolis_step(float t, float c0, float s
                                                       float Ss, uint32_t w0, uint32_t w1,
                                                       float K, float delta) {
   // wrap once into [0, 2 pi): both candidates are formed and selected on the
-  // unwrapped value (no branches)
-  const float raw = __fmaf_rn(delta, sym24(w0), t);
+  // unwrapped value (no branches).  delta * sym24(w0) is formed as
+  // (delta 2^-23) * ((w0 >> 8) - 2^23): both products are exact, so the FMA
+  // rounds the same real number, and delta 2^-23 is common to every site of a
+  // kernel (one multiply per thread instead of one per site).
+  const float raw = __fmaf_rn(delta * kR23, (float)((int32_t)(w0 >> 8) - 8388608), t);
   const float up = __fadd_rn(raw, kTwoPi), down = __fsub_rn(raw, kTwoPi);
   const float tp = raw < 0.f ? up : (raw >= kTwoPi ? down : raw);
   float s1, c1;
@@ -232,22 +259,204 @@ __device__ __forceinline__ SiteResult metropolis_step(float t, float c0, float s
 
 namespace xyd {
 
-// End-of-CTA reduction shared by the sweep kernels: per-thread FP32 partials
-// (or Neumaier pairs when RED == 1) -> warp shuffle -> FP64 over the CTA's
-// warps (compensated FP32 when RED == 1) -> exact fixed-point atomics into the
-// record.  `part` holds [warps][5][2] floats and `cnt` [warps] counters in
-// shared memory.  Must be reached by every thread of the CTA.
-template <int NWARPS, int RED, bool MEASURE>
+// ---- exact per-sweep sums (reduce mode 0) ----
+// Each per-site term of the sweep sums is rounded to a signed integer before
+// any addition: one FMA adds v * 2^shift to 1.5 * 2^23, whose unit in the
+// last place is 1, so the result's mantissa holds v * 2^shift rounded half
+// to even (exact for |v| 2^shift < 2^22), and the integers are added exactly.
+// The sums are then independent of the order of addition: every kernel, tile
+// shape and launch plan produces the same record bits for the same state.
+// Shifts: 19 for v0 (four bond cosines, |v0| <= 4) and 20 for v1..v4
+// (|v| <= 2), so |v| 2^shift <= 2^21; the record keeps 2^-XY_FX_SHIFT units.
+__host__ __device__ constexpr int fx_term_shift(int i) { return i == 0 ? 19 : 20; }
+constexpr float kFxScaleC = 524288.0f;        // 2^19
+constexpr float kFxScale = 1048576.0f;        // 2^20
+constexpr uint32_t kRoundMagicBits = 0x4B400000u;   // bit pattern of 1.5 * 2^23
+
+// Per-thread sums of the terms' bit patterns (modulo 2^32) and their count.
+struct FxSums {
+  uint32_t s[5];
+  uint32_t n;
+};
+
+__device__ __forceinline__ void fx_init(FxSums& f) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f.s[i] = 0u;
+  f.n = 0u;
+}
+
+__device__ __forceinline__ uint32_t fx_bits(float v, float scale) {
+  return __float_as_uint(__fmaf_rn(v, scale, kRoundMagic));
+}
+
+// One black site's five terms.
+__device__ __forceinline__ void fx_add(FxSums& f, const float v[5]) {
+  f.s[0] += fx_bits(v[0], kFxScaleC);
+#pragma unroll
+  for (int i = 1; i < 5; ++i) f.s[i] += fx_bits(v[i], kFxScale);
+  f.n += 1u;
+}
+
+// Two black sites' terms (three-input integer adds).
+__device__ __forceinline__ void fx_add2(FxSums& f, const float a[5], const float b[5]) {
+  f.s[0] += fx_bits(a[0], kFxScaleC) + fx_bits(b[0], kFxScaleC);
+#pragma unroll
+  for (int i = 1; i < 5; ++i) f.s[i] += fx_bits(a[i], kFxScale) + fx_bits(b[i], kFxScale);
+  f.n += 2u;
+}
+
+// The thread's sum of term i in units of 2^-fx_term_shift(i).  Exact while
+// the thread holds at most 1023 terms.
+__device__ __forceinline__ int32_t fx_value(const FxSums& f, int i) {
+  return (int32_t)(f.s[i] - f.n * kRoundMagicBits);
+}
+
+// Whether a non-finite value entered the thread's terms.  Every site of the
+// lattice enters some black site's v0 (its own, or a neighbour's), and a NaN
+// or infinite term moves the bit-pattern sum by a nonzero multiple of 2^22
+// (modulo 2^32, for fewer than 512 such terms), far outside the finite range
+// |sum| <= n 2^21.
+__device__ __forceinline__ bool fx_nonfinite(const FxSums& f) {
+  const int32_t v = fx_value(f, 0);
+  const uint32_t mag = v < 0 ? (uint32_t)(-(int64_t)v) : (uint32_t)v;
+  return mag > (f.n << 21);
+}
+
+// End-of-CTA commit of exact sums: warp reduction of the integers
+// (redux.sync; WIDE splits each 32-bit value into 16-bit halves first, for
+// threads that may hold more than 31 terms), int64 over the CTA's warps, and
+// one 64-bit atomic per sum into the record, rescaled to 2^-XY_FX_SHIFT.
+// `part` holds [warps][5][2] 32-bit words and `cnt` [warps] counters in shared
+// memory.  Must be reached by every thread of the CTA.
+template <int NWARPS, bool WIDE>
+__device__ __forceinline__ void commit_block_fx(const FxSums& f, unsigned int n_acc,
+                                                float (*part)[5][2], unsigned int* cnt,
+                                                xy_record* rec, double beta, bool first_block,
+                                                bool measure) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned int warp_acc = __reduce_add_sync(0xffffffffu, n_acc);
+  long long ws[5] = {0, 0, 0, 0, 0};
+  bool bad = false;
+  if (measure) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int32_t v = fx_value(f, i);
+      if (!WIDE) {
+        ws[i] = (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)v);
+      } else {
+        const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)v & 0xffffu);
+        const int32_t hi = (int32_t)__reduce_add_sync(0xffffffffu, (uint32_t)(v >> 16));
+        ws[i] = (long long)hi * 65536ll + (long long)lo;
+      }
+    }
+    bad = __any_sync(0xffffffffu, fx_nonfinite(f));
+  }
+  if (lane == 0) {
+    cnt[warp] = warp_acc | (bad ? 0x80000000u : 0u);
+    if (measure) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        reinterpret_cast<uint32_t*>(part[warp][i])[0] = (uint32_t)(unsigned long long)ws[i];
+        reinterpret_cast<uint32_t*>(part[warp][i])[1] = (uint32_t)((unsigned long long)ws[i] >> 32);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  if (lane == 0) {
+    unsigned long long total = 0;
+    bool any_bad = false;
+    for (int w = 0; w < NWARPS; ++w) {
+      total += cnt[w] & 0x7fffffffu;
+      any_bad |= (cnt[w] & 0x80000000u) != 0u;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&rec->accepted), total);
+    if (any_bad) atomicOr(reinterpret_cast<unsigned long long*>(&rec->flags), 1ull);
+    if (measure && first_block) rec->beta = beta;
+  }
+  if (!measure || lane >= 5) return;
+  // lanes 0..4 each own one of the five sums
+  unsigned long long t = 0;
+  for (int w = 0; w < NWARPS; ++w) {
+    const uint32_t* pw = reinterpret_cast<const uint32_t*>(part[w][lane]);
+    t += (unsigned long long)pw[0] | ((unsigned long long)pw[1] << 32);
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(&rec->sum[lane]),
+            t << (XY_FX_SHIFT - fx_term_shift(lane)));
+}
+
+// Per-thread sums of a sweep kernel: exact fixed point (RED == 0) or
+// Neumaier-compensated FP32 pairs (RED == 1), with one commit for both.
+template <int RED>
+struct SweepSums {
+  FxSums fx;
+  float acc[5], cmp[5];
+  __device__ __forceinline__ void init() {
+    if (RED == 0) {
+      fx_init(fx);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) acc[i] = cmp[i] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void add(const float v[5]) {
+    if (RED == 0) {
+      fx_add(fx, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) neumaier_add(acc[i], cmp[i], v[i]);
+    }
+  }
+  __device__ __forceinline__ void add2(const float a[5], const float b[5]) {
+    if (RED == 0) {
+      fx_add2(fx, a, b);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        neumaier_add(acc[i], cmp[i], a[i]);
+        neumaier_add(acc[i], cmp[i], b[i]);
+      }
+    }
+  }
+};
+
+template <int NWARPS, int RED, bool MEASURE, bool WIDE = false>
+__device__ __forceinline__ void commit_block(float acc[5], float cmp[5], unsigned int n_acc,
+                                             float (*part)[5][2], unsigned int* cnt,
+                                             xy_record* rec, double beta, bool first_block);
+
+template <int NWARPS, int RED, bool MEASURE, bool WIDE = false>
+__device__ __forceinline__ void commit_sums(SweepSums<RED>& s, unsigned int n_acc,
+                                            float (*part)[5][2], unsigned int* cnt,
+                                            xy_record* rec, double beta, bool first_block) {
+  if (RED == 0) {
+    commit_block_fx<NWARPS, WIDE>(s.fx, n_acc, part, cnt, rec, beta, first_block, MEASURE);
+  } else {
+    commit_block<NWARPS, 1, MEASURE>(s.acc, s.cmp, n_acc, part, cnt, rec, beta, first_block);
+  }
+}
+
+}  // namespace xyd
+
+namespace xyd {
+
+// End-of-CTA reduction of the compensated sums (reduce mode 1): per-thread
+// Neumaier pairs -> warp shuffle -> compensated FP32 over the CTA's warps ->
+// FP64 -> fixed-point atomics into the record.  `part` holds [warps][5][2]
+// floats and `cnt` [warps] counters in shared memory.  Must be reached by
+// every thread of the CTA.  (Reduce mode 0 commits through commit_block_fx.)
+template <int NWARPS, int RED, bool MEASURE, bool WIDE>
 __device__ __forceinline__ void commit_block(float acc[5], float cmp[5], unsigned int n_acc,
                                              float (*part)[5][2], unsigned int* cnt,
                                              xy_record* rec, double beta, bool first_block) {
+  static_assert(RED == 1, "reduce mode 0 commits through commit_block_fx");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned int warp_acc = __reduce_add_sync(0xffffffffu, n_acc);
   if (MEASURE) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       acc[i] = warp_sum(acc[i]);
-      if (RED == 1) cmp[i] = warp_sum(cmp[i]);
+      cmp[i] = warp_sum(cmp[i]);
     }
   }
   if (lane == 0) {
@@ -256,7 +465,7 @@ __device__ __forceinline__ void commit_block(float acc[5], float cmp[5], unsigne
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
         part[warp][i][0] = acc[i];
-        part[warp][i][1] = (RED == 1) ? cmp[i] : 0.f;
+        part[warp][i][1] = cmp[i];
       }
     }
   }
@@ -270,18 +479,12 @@ __device__ __forceinline__ void commit_block(float acc[5], float cmp[5], unsigne
   }
   if (!MEASURE || lane >= 5) return;
   // lanes 0..4 each own one of the five sums
-  double d;
-  if (RED == 0) {
-    d = 0.0;
-    for (int w = 0; w < NWARPS; ++w) d += (double)part[w][lane][0];
-  } else {
-    float hi = 0.f, lo = 0.f;
-    for (int w = 0; w < NWARPS; ++w) {
-      neumaier_add(hi, lo, part[w][lane][0]);
-      lo += part[w][lane][1];
-    }
-    d = (double)hi + (double)lo;
+  float hi = 0.f, lo = 0.f;
+  for (int w = 0; w < NWARPS; ++w) {
+    neumaier_add(hi, lo, part[w][lane][0]);
+    lo += part[w][lane][1];
   }
+  const double d = (double)hi + (double)lo;
   const double scaled = d * (double)(1ll << XY_FX_SHIFT);
   if (!(fabs(scaled) < 9.0e18)) {
     atomicOr(reinterpret_cast<unsigned long long*>(&rec->flags), 1ull);

@@ -50,6 +50,9 @@ constexpr size_t kSmemBytes = kThBytes + kCsBytes + kPartBytes + kCntBytes;
 typedef float ThArr[kSRows][kSCols];
 typedef float2 CsArr[kSRows][kSCols];
 
+// Tiles of one sweep of side L (L % 128 == 0).
+inline int fused_tiles_of(int L) { return (L / 2 / kTileK) * (L / kTileRows); }
+
 __device__ __forceinline__ int wrap_once(int v, int n) {
   v += (v < 0) ? n : 0;
   v -= (v >= n) ? n : 0;
@@ -57,8 +60,11 @@ __device__ __forceinline__ int wrap_once(int v, int n) {
 }
 
 // The four neighbour unit vectors of the two sites at stage columns c0, c0+1
-// of row r in plane `nb` (the other colour), where a site at column c has its
-// same-row neighbours at c+q-1 and c+q.
+// (c0 even) of row r in plane `nb` (the other colour), where a site at column
+// c has its same-row neighbours at c+q-1 and c+q.  The three same-row columns
+// c0+q-1 .. c0+q+1 are the aligned pair (c0, c0+1) and one edge column, c0-1
+// (q = 0) or c0+2 (q = 1); q is a compile-time constant where the row loops
+// are unrolled (rows alternate q), so no selects are issued.
 struct PairNeighbours {
   float Sc[2], Ss[2];
   float2 l[2], r[2], d[2], u[2];
@@ -66,15 +72,22 @@ struct PairNeighbours {
 
 __device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, int q,
                                                 PairNeighbours& n) {
-  // same-row neighbours of the two sites: columns c0+q-1, c0+q, c0+q+1 (q is
-  // uniform across the warp, so these are plain offset loads, no selects)
-  const float2 a = nb[r][c0 + q - 1], m = nb[r][c0 + q], b = nb[r][c0 + q + 1];
+  const float4 P = *reinterpret_cast<const float4*>(&nb[r][c0]);
+  const float2 e = nb[r][q ? c0 + 2 : c0 - 1];
+  const float2 p0 = make_float2(P.x, P.y), p1 = make_float2(P.z, P.w);
   const float4 D = *reinterpret_cast<const float4*>(&nb[r - 1][c0]);
   const float4 U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
-  n.l[0] = a;
-  n.r[0] = m;
-  n.l[1] = m;
-  n.r[1] = b;
+  if (q) {
+    n.l[0] = p0;
+    n.r[0] = p1;
+    n.l[1] = p1;
+    n.r[1] = e;
+  } else {
+    n.l[0] = e;
+    n.r[0] = p0;
+    n.l[1] = p0;
+    n.r[1] = p1;
+  }
   n.d[0] = make_float2(D.x, D.y);
   n.d[1] = make_float2(D.z, D.w);
   n.u[0] = make_float2(U.x, U.y);
@@ -116,8 +129,7 @@ __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c
   const float2 own = cs[0][r][c];
   const xyd::SiteResult res =
       xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
-  th[0][r][c] = res.th;
-  cs[0][r][c] = make_float2(res.c, res.s);
+  cs[0][r][c] = make_float2(res.c, res.s);   // the black half reads the unit vector only
 }
 
 // One sweep of the tile (bx, by) of one lattice.  Args is FusedArgs (the
@@ -126,17 +138,19 @@ __device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c
 // and persistent kernels); both have the fields used here.  COHERENT: the
 // source was written earlier in the same launch by other CTAs (persistent
 // kernel), so it is read through L2 (ld.global.cg) rather than the
-// non-coherent path.  `mid` runs in every thread before the barrier between
-// the red and the black half, `end` after the tile's last store to dst and
-// before the CTA's closing barrier.
+// non-coherent path.  `pre` runs in every thread before the barrier that ends
+// the staging, `mid` before the barrier between the red and the black half,
+// `end` after the tile's last store to dst and before the CTA's closing
+// barrier.
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
-template <int MODE, int RED, bool COHERENT = false, class Args, class MidHook = NoHook,
-          class EndHook = NoHook>
+template <int MODE, int RED, bool COHERENT = false, class Args, class PreHook = NoHook,
+          class MidHook = NoHook, class EndHook = NoHook>
 __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk, int bx,
-                                                 int by, const MidHook& mid = MidHook(),
+                                                 int by, const PreHook& pre = PreHook(),
+                                                 const MidHook& mid = MidHook(),
                                                  const EndHook& end = EndHook()) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThArr* th = reinterpret_cast<ThArr*>(smem);
@@ -150,63 +164,93 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   const size_t plane = (size_t)L * (size_t)W;
 
   // ---- stage both planes (angle + unit vector) ----
-  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
-  // (stage rows 1..34; red is never needed two rows out).  Each warp takes two
-  // rows per step, 16 lanes per row, one float4 of the tile body per lane (so
-  // the addressing is a shift and an add); the two halo columns k0-1 and
-  // k0+64 (rows 1..34) are a separate pass.
+  // Staged rows: the black plane's 36 (stage rows 0..35) then the red plane's
+  // 34 (stage rows 1..34; red is never needed two rows out), 70 rows of 64
+  // plane columns, plus the halo columns k0-1 and k0+64 of stage rows 1..34 of
+  // both planes (136 sites): 4616 unit vectors over 256 threads.  Thread t
+  // takes the float4 column group t & 15 of staged rows (t >> 4) + 16 i,
+  // i = 0..3 (rows 0..63; half a warp per row, so the addressing is a shift
+  // and an add), then threads 0..191 one float2 of rows 64..69 and threads
+  // 184..255 one or two halo sites: at most 19 unit vectors per thread against
+  // a mean of 18.03.  Every load is issued before the first unit vector.
   {
-    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
-    const int half = lane_s >> 4, g = lane_s & 15;
-    constexpr int kSteps = (kStageRowsTotal + 2 * kWarps - 1) / (2 * kWarps);
-    // all of a lane's loads first, so their latencies overlap
-    float4 v[kSteps];
+    const int t = threadIdx.x;
+    const int cg = t & 15;
+    float4 v[4];
 #pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * g;
-        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(a.src + row))
-                        : __ldg(reinterpret_cast<const float4*>(a.src + row));
+    for (int i = 0; i < 4; ++i) {
+      const int rr = (t >> 4) + 16 * i;
+      const int p = rr < kSRows ? 1 : 0;
+      const int r = rr < kSRows ? rr : rr - kSRows + 1;
+      const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * cg;
+      v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(a.src + row))
+                      : __ldg(reinterpret_cast<const float4*>(a.src + row));
+    }
+    // the tail rows 64..69 are red stage rows 29..34
+    const bool has_tail = t < 192;
+    const int tail_r = 29 + (t >> 5), tail_c = t & 31;
+    float2 vt = make_float2(0.f, 0.f);
+    if (has_tail) {
+      const size_t row = (size_t)wrap_once(y0 - 2 + tail_r, L) * W + k0 + 2 * tail_c;
+      vt = COHERENT ? __ldcg(reinterpret_cast<const float2*>(a.src + row))
+                    : __ldg(reinterpret_cast<const float2*>(a.src + row));
+    }
+    // halo sites h = 0..135: plane h / 68, stage row 1 + (h % 68) / 2, side h & 1
+    const int nh = t >= 192 ? 2 : (t >= 184 ? 1 : 0);
+    float vh[2] = {0.f, 0.f};
+    int hp[2] = {0, 0}, hr[2] = {0, 0}, hcol[2] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (j < nh) {
+        const int h = t >= 192 ? (j == 0 ? t - 192 : t - 128) : t - 56;
+        const int p = h >= 2 * (kSRows - 2) ? 1 : 0;
+        const int rem = h - p * 2 * (kSRows - 2);
+        const int r = 1 + (rem >> 1);
+        const int side = rem & 1;
+        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
+        const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
+        hp[j] = p;
+        hr[j] = r;
+        hcol[j] = side ? kTileK + 4 : 3;
+        vh[j] = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
       }
     }
 #pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const int col = 4 + 4 * g;
-        float s0, c0, s1, c1, s2, c2, s3, c3;
-        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
-        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
-        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
-        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+    for (int i = 0; i < 4; ++i) {
+      const int rr = (t >> 4) + 16 * i;
+      const int p = rr < kSRows ? 1 : 0;
+      const int r = rr < kSRows ? rr : rr - kSRows + 1;
+      const int col = 4 + 4 * cg;
+      float s0, c0, s1, c1, s2, c2, s3, c3;
+      xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
+      xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
+      xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
+      xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
+      // angles are read only for the sites the tile updates: the red rows
+      // and the black tile rows 2..33 (a warp-uniform test)
+      if (p == 0 || (r >= 2 && r < kSRows - 2))
         *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
-        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-      }
+      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
     }
-    // halo columns: (plane, row 1..34, side), taken by the last warps, which
-    // have one row step fewer than the first ones
-    for (int h = kThreads - 1 - threadIdx.x; h < 2 * (kSRows - 2) * 2; h += kThreads) {
-      const int p = h / ((kSRows - 2) * 2);
-      const int rem = h - p * ((kSRows - 2) * 2);
-      const int r = 1 + (rem >> 1);
-      const int side = rem & 1;
-      const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
-      const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
-      const int col = side ? kTileK + 4 : 3;
-      const float v1 = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
-      float sv, cv;
-      xyd::unit_vector<MODE>(v1, &sv, &cv);
-      th[p][r][col] = v1;
-      cs[p][r][col] = make_float2(cv, sv);
+    if (has_tail) {
+      float s0, c0, s1, c1;
+      xyd::unit_vector<MODE>(vt.x, &s0, &c0);
+      xyd::unit_vector<MODE>(vt.y, &s1, &c1);
+      *reinterpret_cast<float2*>(&th[0][tail_r][4 + 2 * tail_c]) = vt;
+      *reinterpret_cast<float4*>(&cs[0][tail_r][4 + 2 * tail_c]) = make_float4(c0, s0, c1, s1);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      if (j < nh) {
+        float sv, cv;
+        xyd::unit_vector<MODE>(vh[j], &sv, &cv);
+        if (hp[j] == 0) th[0][hr[j]][hcol[j]] = vh[j];     // red side-ring angles
+        cs[hp[j]][hr[j]][hcol[j]] = make_float2(cv, sv);
+      }
     }
   }
+  pre();
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -216,7 +260,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   unsigned int n_acc = 0;
 
   // ---- red half: the tile (counted, written to dst) ----
-#pragma unroll 2
+#pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
     const int y = y0 + ty;
@@ -234,7 +278,6 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const xyd::SiteResult r1 =
         xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, a.K, a.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
-    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
     *reinterpret_cast<float2*>(a.dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
   }
@@ -268,10 +311,10 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  xyd::SweepSums<RED> sums;
+  sums.init();
   float* dst_blk = a.dst + plane;
-#pragma unroll 2
+#pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
     const int y = y0 + ty;
@@ -298,24 +341,19 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
     xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
                        n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (RED == 0) {
-        acc[i] += v0[i] + v1[i];
-      } else {
-        xyd::neumaier_add(acc[i], cmp[i], v0[i]);
-        xyd::neumaier_add(acc[i], cmp[i], v1[i]);
-      }
-    }
+    sums.add2(v0, v1);
   }
 
   end();
-  xyd::commit_block<kWarps, RED, true>(acc, cmp, n_acc, part, cnt, a.rec, a.beta,
-                                       bx == 0 && by == 0);
+  // 8 black sites per thread: the per-warp integer sums fit 32 bits
+  xyd::commit_sums<kWarps, RED, true>(sums, n_acc, part, cnt, a.rec, a.beta,
+                                      bx == 0 && by == 0);
 }
 
-template <int MODE, int RED>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused(FusedArgs a) {
+// MINB: CTAs per SM the kernel is compiled for (3: at most 80 registers a
+// thread; 2: at most 128, more independent work in flight per warp).
+template <int MODE, int RED, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused(FusedArgs a) {
   fused_sweep_body<MODE, RED>(a, a.rk, blockIdx.x, blockIdx.y);
 }
 
@@ -350,6 +388,24 @@ __device__ __forceinline__ void store_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// A work item decoded once by the thread that fetched it: the item, its
+// sweep and its tile position (so no other thread divides).
+struct PersistItem {
+  int item, s, bx, by;
+};
+
+__device__ __forceinline__ PersistItem decode_item(int item, int ntiles, int tiles_x,
+                                                   int tiles_y) {
+  PersistItem it;
+  it.item = item;
+  it.s = item / ntiles;
+  const int k = item - it.s * ntiles;
+  const int prow = k / tiles_x;
+  it.bx = k - prow * tiles_x;
+  it.by = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+  return it;
+}
+
 // All n sweeps of one lattice in one cooperative launch (every CTA resident).
 // The work items (sweep s, tile position k) are handed out in increasing order
 // by one atomic counter, s-major, with the tile rows of a sweep visited folded
@@ -365,13 +421,17 @@ __device__ __forceinline__ void store_release(unsigned int* p, unsigned int v) {
 // resident the waits always end; each is bounded anyway, and a wait that runs
 // out sets *error and ends the CTA (the CTAs that wait on it see *error and
 // end too).  Dynamic hand-out keeps the SMs evenly loaded as a launch per
-// sweep does, without the launch's fill and drain.  The arithmetic of a tile
-// is fused_sweep_body's, so the result is bit for bit that of n launches of
-// k_sweep_fused.
-template <int MODE, int RED>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersistArgs p) {
+// sweep does, without the launch's fill and drain.  Thread 0 fetches the next
+// item at the start of a tile and decodes it before the staging barrier; the
+// last warp, idle while the first five update the red ring, looks at that
+// item's nine counters before the red/black barrier, and when all were set
+// the next tile starts without waiting or a barrier.  The arithmetic of a
+// tile is fused_sweep_body's, so the result is bit for bit that of n launches
+// of k_sweep_fused.
+template <int MODE, int RED, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPersistArgs p) {
   __shared__ int s_abort;
-  __shared__ int s_item[2];          // this tile's item and the next (alternating)
+  __shared__ PersistItem s_item[2];  // this tile's item and the next (alternating)
   __shared__ int s_ready[2];         // the next item's nine counters were all seen set
   const int tiles_x = p.W / kTileK, tiles_y = p.L / kTileRows;
   const int ntiles = tiles_x * tiles_y;
@@ -385,18 +445,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
   c.beta = p.beta;
   if (threadIdx.x == 0) {
     s_abort = 0;
-    s_item[0] = (int)atomicAdd(p.counter, 1u) + p.skip_items;
+    s_item[0] = decode_item((int)atomicAdd(p.counter, 1u) + p.skip_items, ntiles, tiles_x,
+                            tiles_y);
     s_ready[0] = 0;
   }
   __syncthreads();
   int par = 0;
-  int item = s_item[0];
-  while (item < total) {
-    const int s = item / ntiles;
-    const int k = item - s * ntiles;
-    const int prow = k / tiles_x;
-    const int bx = k - prow * tiles_x;
-    const int by = (prow & 1) ? tiles_y - 1 - (prow >> 1) : (prow >> 1);
+  PersistItem cur = s_item[0];
+  while (cur.item < total) {
+    const int s = cur.s, bx = cur.bx, by = cur.by;
     // when the previous tile's early look found all nine counters set, this
     // tile neither waits nor needs the barrier (the acquire loads came before
     // the previous tile's closing barrier)
@@ -431,64 +488,69 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_persist(FusedPersis
     c.dst = p.buf[(s + 1) & 1];
     c.sweep = p.sweep0 + (uint32_t)s;
     c.rec = p.rec + s;
-    int* slot = &s_item[par ^ 1];
+    PersistItem* slot = &s_item[par ^ 1];
     fused_sweep_body<MODE, RED, true>(
         c, p.rk, bx, by,
-        // before the red/black barrier: the next item to the other slot
+        // before the staging barrier: the next item, decoded, to the other slot
+        // (the atomic was issued before the staging loads, so it has returned)
         [&]() {
-          if (threadIdx.x == 0) *slot = next;
+          if (threadIdx.x == 0) *slot = decode_item(next, ntiles, tiles_x, tiles_y);
         },
-        // after the black half: one early look at the next item's nine
-        // counters (warp 0), so that its wait usually costs nothing
+        // before the red/black barrier, in the last warp (idle while the first
+        // five update the ring): one early look at the next item's nine
+        // counters, so that its wait usually costs nothing.  The acquire loads'
+        // latency overlaps the ring instead of holding the CTA at its closing
+        // barrier.
         [&]() {
-          if (threadIdx.x < 32) {
-            bool ok = threadIdx.x >= 9;
-            const int ni = *slot;
-            if (threadIdx.x < 9 && ni < total) {
-              const int ns = ni / ntiles;
-              const int nk = ni - ns * ntiles;
-              const int nrow = nk / tiles_x;
-              const int nbx = nk - nrow * tiles_x;
-              const int nby = (nrow & 1) ? tiles_y - 1 - (nrow >> 1) : (nrow >> 1);
-              const int d = threadIdx.x;
-              const int nx = wrap_once(nbx + d % 3 - 1, tiles_x);
-              const int ny = wrap_once(nby + d / 3 - 1, tiles_y);
-              ok = ns == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
+          if (threadIdx.x >= kThreads - 32) {
+            const int l = threadIdx.x - (kThreads - 32);
+            bool ok = l >= 9;
+            const PersistItem ni = *slot;
+            if (l < 9 && ni.item < total) {
+              const int nx = wrap_once(ni.bx + l % 3 - 1, tiles_x);
+              const int ny = wrap_once(ni.by + l / 3 - 1, tiles_y);
+              ok = ni.s == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ni.s;
             }
             const unsigned int all = __ballot_sync(0xffffffffu, ok);
-            if (threadIdx.x == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
+            if (l == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
           }
         });
-    if (threadIdx.x == kThreads - 32) {
+    if (threadIdx.x == kThreads - 64) {
       // a warp other than the pollers' publishes the tile: the closing barrier
       // orders every thread's stores to dst before this GPU-scope release,
       // which is cumulative over the writes that happen before it
       store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
     }
     par ^= 1;
-    item = s_item[par];
+    cur = s_item[par];
   }
 }
 
-template <int MODE, int RED>
+template <int MODE, int RED, int MINB>
 cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
   static bool configured[64] = {};   // attributes set once per instantiation and device
   int dev = 0;
   cudaError_t ge = cudaGetDevice(&dev);
   if (ge != cudaSuccess) return ge;
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED>,
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED>,
+    e = cudaFuncSetAttribute(k_sweep_fused<MODE, RED, MINB>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   const dim3 grid(a.W / kTileK, a.L / kTileRows);
-  k_sweep_fused<MODE, RED><<<grid, kThreads, kSmemBytes, stream>>>(a);
+  k_sweep_fused<MODE, RED, MINB><<<grid, kThreads, kSmemBytes, stream>>>(a);
   return cudaGetLastError();
+}
+
+template <int MODE, int RED>
+cudaError_t launch_fused_plan(const FusedArgs& a, cudaStream_t stream) {
+  return a.minb == 2 ? launch_fused_one<MODE, RED, 2>(a, stream)
+                     : launch_fused_one<MODE, RED, 3>(a, stream);
 }
 
 template <int MODE, int RED>
@@ -509,21 +571,22 @@ cudaError_t prepare_one() {
   return e;
 }
 
-template <int MODE, int RED>
+template <int MODE, int RED, int MINB>
 cudaError_t launch_persist_one(const FusedPersistArgs& a, int grid, cudaStream_t stream) {
   void* args[] = {const_cast<FusedPersistArgs*>(&a)};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED>),
-                                     dim3(grid), dim3(kThreads), args, kSmemBytes, stream);
+  return cudaLaunchCooperativeKernel(
+      reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED, MINB>), dim3(grid),
+      dim3(kThreads), args, kSmemBytes, stream);
 }
 
-template <int MODE, int RED>
+template <int MODE, int RED, int MINB>
 cudaError_t persist_grid_one(int L, int* grid) {
   static int per_sm[64] = {};        // resident CTAs per SM, per device (0: not yet set)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || per_sm[dev] == 0) {
-    auto fn = k_sweep_fused_persist<MODE, RED>;
+    auto fn = k_sweep_fused_persist<MODE, RED, MINB>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -542,6 +605,23 @@ cudaError_t persist_grid_one(int L, int* grid) {
   const int resident = per_sm[(dev >= 0 && dev < 64) ? dev : 0] * sms;
   *grid = tiles < resident ? tiles : resident;
   return cudaSuccess;
+}
+
+// The persistent launch of one instantiation: grid, then the launch.
+template <int MODE, int RED, int MINB>
+cudaError_t persist_plan(const FusedPersistArgs& a, cudaStream_t stream) {
+  int grid = 0;
+  cudaError_t e = persist_grid_one<MODE, RED, MINB>(a.L, &grid);
+  if (e != cudaSuccess) return e;
+  // the tile counters and, after them, the work counter
+  e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned int) * ((size_t)fused_tiles_of(a.L) + 1), stream);
+  if (e != cudaSuccess) return e;
+  return launch_persist_one<MODE, RED, MINB>(a, grid, stream);
+}
+
+template <int MODE, int RED>
+cudaError_t persist_dispatch(const FusedPersistArgs& a, cudaStream_t stream) {
+  return a.minb == 2 ? persist_plan<MODE, RED, 2>(a, stream) : persist_plan<MODE, RED, 3>(a, stream);
 }
 
 }  // namespace
@@ -576,12 +656,12 @@ cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const Fus
 
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream) {
-  if (!fused_supported(a.L)) return cudaErrorInvalidValue;
+  if (!fused_supported(a.L) || (a.minb != 2 && a.minb != 3)) return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   switch (sincos_mode) {
-    case 0: return comp ? launch_fused_one<0, 1>(a, stream) : launch_fused_one<0, 0>(a, stream);
-    case 1: return comp ? launch_fused_one<1, 1>(a, stream) : launch_fused_one<1, 0>(a, stream);
-    default: return comp ? launch_fused_one<2, 1>(a, stream) : launch_fused_one<2, 0>(a, stream);
+    case 0: return comp ? launch_fused_plan<0, 1>(a, stream) : launch_fused_plan<0, 0>(a, stream);
+    case 1: return comp ? launch_fused_plan<1, 1>(a, stream) : launch_fused_plan<1, 0>(a, stream);
+    default: return comp ? launch_fused_plan<2, 1>(a, stream) : launch_fused_plan<2, 0>(a, stream);
   }
 }
 
@@ -604,24 +684,13 @@ cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const Fuse
   if (!fused_supported(a.L) || a.W * 2 != a.L || a.n_sweeps < 1 ||
       a.n_sweeps > fused_persistent_max_sweeps(a.L) || !a.flags || a.counter != a.flags + fused_tiles(a.L) ||
       !a.error || a.buf[0] == a.buf[1] || a.spin_limit < 1 || a.skip_items < 0 ||
-      a.skip_items > a.n_sweeps * fused_tiles(a.L))
+      a.skip_items > a.n_sweeps * fused_tiles(a.L) || (a.minb != 2 && a.minb != 3))
     return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
-  int grid = 0;
-  cudaError_t e;
   switch (sincos_mode) {
-    case 0: e = comp ? persist_grid_one<0, 1>(a.L, &grid) : persist_grid_one<0, 0>(a.L, &grid); break;
-    case 1: e = comp ? persist_grid_one<1, 1>(a.L, &grid) : persist_grid_one<1, 0>(a.L, &grid); break;
-    default: e = comp ? persist_grid_one<2, 1>(a.L, &grid) : persist_grid_one<2, 0>(a.L, &grid); break;
-  }
-  if (e != cudaSuccess) return e;
-  // the tile counters and, after them, the work counter
-  e = cudaMemsetAsync(a.flags, 0, sizeof(unsigned int) * ((size_t)fused_tiles(a.L) + 1), stream);
-  if (e != cudaSuccess) return e;
-  switch (sincos_mode) {
-    case 0: return comp ? launch_persist_one<0, 1>(a, grid, stream) : launch_persist_one<0, 0>(a, grid, stream);
-    case 1: return comp ? launch_persist_one<1, 1>(a, grid, stream) : launch_persist_one<1, 0>(a, grid, stream);
-    default: return comp ? launch_persist_one<2, 1>(a, grid, stream) : launch_persist_one<2, 0>(a, grid, stream);
+    case 0: return comp ? persist_dispatch<0, 1>(a, stream) : persist_dispatch<0, 0>(a, stream);
+    case 1: return comp ? persist_dispatch<1, 1>(a, stream) : persist_dispatch<1, 0>(a, stream);
+    default: return comp ? persist_dispatch<2, 1>(a, stream) : persist_dispatch<2, 0>(a, stream);
   }
 }
 

@@ -314,7 +314,7 @@ xy_status grow_records(xy_hmc* h, int64_t need) {
   int64_t cap = h->rec_cap > 0 ? h->rec_cap : 256;
   while (cap < need) cap *= 2;
   xy_hmc_record* nr = nullptr;
-  H_CUDA(h, cudaMalloc(&nr, (size_t)cap * sizeof(xy_hmc_record)), "record buffer");
+  H_CUDA(h, xyk::dev_malloc(&nr, (size_t)cap * sizeof(xy_hmc_record)), "record buffer");
   if (h->rec_count > 0) {
     cudaError_t e = cudaMemcpyAsync(nr, h->d_rec, (size_t)h->rec_count * sizeof(xy_hmc_record),
                                     cudaMemcpyDeviceToDevice, h->stream);
@@ -395,16 +395,16 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     step = "angle buffers";
     h->th[0] = static_cast<float*>(d_angles);
     for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-      if (!h->th[i]) e = cudaMalloc(&h->th[i], N * sizeof(float));
+      if (!h->th[i]) e = xyk::dev_malloc(&h->th[i], N * sizeof(float));
   }
   if (e == cudaSuccess) {
     step = "momentum buffers";
-    e = cudaMalloc(&h->d_p, N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_p2, N * sizeof(float));
+    e = xyk::dev_malloc(&h->d_p, N * sizeof(float));
+    if (e == cudaSuccess) e = xyk::dev_malloc(&h->d_p2, N * sizeof(float));
   }
   if (e == cudaSuccess) {
     step = "control block";
-    e = cudaMalloc(&h->d_ctl, sizeof(xyk::HmcCtl));
+    e = xyk::dev_malloc(&h->d_ctl, sizeof(xyk::HmcCtl));
   }
   // AUTO: the cluster kernel where it measured faster than the others (L =
   // 128, 256); below that the per-launch cost of any kernel dominates
@@ -433,7 +433,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     if (!h->use_tma) {
       e = cudaErrorNotSupported;
     } else {
-      e = cudaMalloc(&h->d_tiles, sizeof(unsigned int) * (size_t)xyk::hmc_persist_tiles(p->L));
+      e = xyk::dev_malloc(&h->d_tiles, sizeof(unsigned int) * (size_t)xyk::hmc_persist_tiles(p->L));
       h->use_persist = e == cudaSuccess;
     }
   }
@@ -700,7 +700,7 @@ xy_status xy_selftest_bounded_wait(void* cuda_stream, int64_t polls) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   unsigned int* d_err = nullptr;
   unsigned int err = 0;
-  cudaError_t e = cudaMalloc(&d_err, sizeof(unsigned int));
+  cudaError_t e = xyk::dev_malloc(&d_err, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned int), s);
   if (e == cudaSuccess) e = xyk::launch_selftest_wait(d_err, (long long)polls, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, s);

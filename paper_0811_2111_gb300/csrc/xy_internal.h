@@ -23,6 +23,15 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Every device allocation of the library (xy_alloc.cu): cudaMalloc, unless a
+// test armed xy_debug_fail_alloc, in which case the chosen allocation fails
+// with cudaErrorMemoryAllocation.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+
 // Arguments of one half-sweep launch over a single lattice.
 struct HalfSweepArgs {
   float* theta;          // [2][L][W] split layout, W = L / 2
@@ -50,6 +59,7 @@ struct FusedArgs {
   uint32_t sweep;
   xy_record* rec;
   double beta;
+  int minb = 3;          // tile kernel instances per SM (2 or 3: the register budget)
 };
 
 // Whether the fused kernel handles side L (L a positive multiple of 128).
@@ -93,6 +103,7 @@ struct FusedPersistArgs {
   long long spin_limit;  // polls before a wait gives up (fused_persistent_spin_limit())
   int skip_items;        // work items not handed out (0; > 0 only to test the
                          // failure path: their counters are then never set)
+  int minb = 3;          // resident CTAs per SM the kernel is compiled for (2 or 3)
 };
 
 // The default bound of the persistent kernel's waits, in polls (about a second).

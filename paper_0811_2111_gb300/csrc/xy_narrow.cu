@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchA
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  xyd::SweepSums<RED> sums;                      // 4 black sites per thread
+  sums.init();
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int ty = warp * 4 + (lane >> 3) + 16 * half;   // the tile row
@@ -253,18 +253,10 @@ __global__ void __launch_bounds__(kNThreads, 6) k_sweep_narrow_batch(FusedBatchA
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
     xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
                        n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (RED == 0) {
-        acc[i] += v0[i] + v1[i];
-      } else {
-        xyd::neumaier_add(acc[i], cmp[i], v0[i]);
-        xyd::neumaier_add(acc[i], cmp[i], v1[i]);
-      }
-    }
+    sums.add2(v0, v1);
   }
-  xyd::commit_block<kNWarps, RED, true>(acc, cmp, n_acc, part, cnt, rec, beta,
-                                        blockIdx.x == 0 && blockIdx.y == 0);
+  xyd::commit_sums<kNWarps, RED, true>(sums, n_acc, part, cnt, rec, beta,
+                                       blockIdx.x == 0 && blockIdx.y == 0);
 }
 
 template <int MODE, int RED>
@@ -402,18 +394,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
   for (int sw = 0; sw < a.sweeps; ++sw) {
     const uint32_t sweep = sweep0 + (uint32_t)sw;
     unsigned int n_acc = 0;
-    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    auto add_terms = [&](const float* v) {
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        if (RED == 0) {
-          acc[j] += v[j];
-        } else {
-          xyd::neumaier_add(acc[j], cmp[j], v[j]);
-        }
-      }
-    };
+    // at most L^2 / 2 / 256 = 18 black sites per thread (L <= 96)
+    xyd::SweepSums<RED> sums;
+    sums.init();
+    auto add_terms = [&](const float* v) { sums.add(v); };
     if (paired) {
       // ---- red half, a pair per step: sites k = 2m and k + 1 of row y
       // (flat index o = 2P); left/right neighbours k+q-1, k+q for the first,
@@ -546,8 +530,8 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       }
     }
     // (its barrier also ends the black half before the next sweep's red half)
-    xyd::commit_block<kSWarps, RED, true>(
-        acc, cmp, n_acc, part, cnt,
+    xyd::commit_sums<kSWarps, RED, true>(
+        sums, n_acc, part, cnt,
         a.records + (size_t)li * a.rec_stride + (sweep - a.rec_sweep0), beta, true);
   }
   __syncthreads();

@@ -88,11 +88,9 @@ __global__ void __launch_bounds__(kThreads) k_quad_half(QuadArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool measure = (COLOUR == 1);
   unsigned int n_acc[kR] = {0u, 0u, 0u, 0u};
-  float acc[kR][5], cmp[kR][5];
+  xyd::SweepSums<RED> sums[kR];                  // at most 4 black sites per replica and thread
 #pragma unroll
-  for (int j = 0; j < kR; ++j)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) acc[j][i] = cmp[j][i] = 0.f;
+  for (int j = 0; j < kR; ++j) sums[j].init();
 
   const int k = k0 + lane;
   const int sc = lane + 1;                               // stage column of (y, k)
@@ -131,14 +129,7 @@ __global__ void __launch_bounds__(kThreads) k_quad_half(QuadArgs a) {
         xyd::measure_terms(res.c, res.s, comp(cl, j), comp(sl, j), comp(cr, j), comp(sr, j),
                            comp(cd, j), comp(sd, j), comp(cu, j), comp(su, j), Sc, Ss, comp(cm, j),
                            comp(sm, j), v);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          if (RED == 0) {
-            acc[j][i] += v[i];
-          } else {
-            xyd::neumaier_add(acc[j][i], cmp[j][i], v[i]);
-          }
-        }
+        sums[j].add(v);
       }
     }
     *p = make_float4(out[0], out[1], out[2], out[3]);
@@ -147,8 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_quad_half(QuadArgs a) {
   const bool first = blockIdx.x == 0 && blockIdx.y == 0;
 #pragma unroll
   for (int j = 0; j < kR; ++j)
-    xyd::commit_block<kWarps, RED, COLOUR == 1>(acc[j], cmp[j], n_acc[j], s_part[j], s_cnt[j],
-                                                a.rec + j, a.beta[j], first);
+    xyd::commit_sums<kWarps, RED, COLOUR == 1>(sums[j], n_acc[j], s_part[j], s_cnt[j], a.rec + j,
+                                               a.beta[j], first);
 }
 
 __global__ void k_quad_start(float4* theta, int L, const xyd::RoundKeys rk, uint32_t lattice_id0,
@@ -339,7 +330,7 @@ xy_status grow(xy_quad* q, int64_t sweeps) {
   int64_t cap = q->rec_cap > 0 ? q->rec_cap : 1024;
   while (cap < sweeps) cap *= 2;
   xy_record* nr = nullptr;
-  Q_CUDA(q, cudaMalloc(&nr, (size_t)cap * kR * sizeof(xy_record)), "record buffer");
+  Q_CUDA(q, xyk::dev_malloc(&nr, (size_t)cap * kR * sizeof(xy_record)), "record buffer");
   if (q->rec_count > 0) {
     cudaError_t e = cudaMemcpyAsync(nr, q->d_rec, (size_t)q->rec_count * kR * sizeof(xy_record),
                                     cudaMemcpyDeviceToDevice, q->stream);
@@ -411,17 +402,17 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
   q->cur = 0;
   const size_t N = (size_t)p->L * (size_t)p->L;
   const char* step = "angle buffer";
-  cudaError_t e = cudaMalloc(&q->d_theta, N * sizeof(float4));
-  if (e == cudaSuccess && q->fused) e = cudaMalloc(&q->d_theta2, N * sizeof(float4));
+  cudaError_t e = xyk::dev_malloc(&q->d_theta, N * sizeof(float4));
+  if (e == cudaSuccess && q->fused) e = xyk::dev_malloc(&q->d_theta2, N * sizeof(float4));
   if (e == cudaSuccess && q->persistent) {
     const size_t words = (size_t)xyk::quad_persistent_tiles(p->L) + 2;
-    e = cudaMalloc(&q->d_tiles, words * sizeof(unsigned int));
+    e = xyk::dev_malloc(&q->d_tiles, words * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(q->d_tiles, 0, words * sizeof(unsigned int), q->stream);
   }
   if (e == cudaSuccess) {
     step = "scratch buffers";
-    e = cudaMalloc(&q->d_scratch, N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&q->d_nat, N * sizeof(float));
+    e = xyk::dev_malloc(&q->d_scratch, N * sizeof(float));
+    if (e == cudaSuccess) e = xyk::dev_malloc(&q->d_nat, N * sizeof(float));
   }
   if (e == cudaSuccess) {
     step = "start kernel";

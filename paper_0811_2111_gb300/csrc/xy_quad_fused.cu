@@ -73,6 +73,119 @@ __device__ __forceinline__ unsigned int parity_sum(unsigned int v) {
   return v;
 }
 
+// Per-thread sums of the two replicas a lane holds: exact fixed point
+// (RED == 0, see xyd::FxSums) or Neumaier-compensated FP32 pairs (RED == 1).
+template <int RED>
+struct QuadSums {
+  xyd::FxSums fx[2];
+  float acc[2][5], cmp[2][5];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      if (RED == 0) {
+        xyd::fx_init(fx[e]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
+      }
+    }
+  }
+  __device__ __forceinline__ void add(const float v0[5], const float v1[5]) {
+    if (RED == 0) {
+      xyd::fx_add(fx[0], v0);
+      xyd::fx_add(fx[1], v1);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        xyd::neumaier_add(acc[0][i], cmp[0][i], v0[i]);
+        xyd::neumaier_add(acc[1][i], cmp[1][i], v1[i]);
+      }
+    }
+  }
+};
+
+// One tile's per-replica sums into the sweep's kR records: the 16 lanes of
+// one parity (they hold the same two replicas, j0 and j0 + 1) -> warps ->
+// one atomic per (replica, sum).  Exact integers for RED == 0 (a lane holds
+// at most 4 terms per replica, so the 16-lane sums fit 32 bits), FP64 of the
+// compensated pairs for RED == 1.  Must be reached by every thread.
+template <int RED>
+__device__ __forceinline__ void quad_commit(QuadSums<RED>& sums, unsigned int n_acc[2],
+                                            float (*part)[kR][5][2], unsigned int (*cnt)[kR],
+                                            xy_record* rec, const double* beta,
+                                            bool first_block, int j0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool bad[2] = {false, false};
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    n_acc[e] = parity_sum(n_acc[e]);
+    if (RED == 0) {
+      // lanes of one parity hold the same replicas: or of their flags
+      const unsigned int b = __ballot_sync(0xffffffffu, xyd::fx_nonfinite(sums.fx[e]));
+      bad[e] = (b & ((lane & 1) ? 0xaaaaaaaau : 0x55555555u)) != 0u;
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        sums.fx[e].s[i] = parity_sum((unsigned int)xyd::fx_value(sums.fx[e], i));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        sums.acc[e][i] = parity_sum(sums.acc[e][i]);
+        sums.cmp[e][i] = parity_sum(sums.cmp[e][i]);
+      }
+    }
+  }
+  if (lane < 2) {                                          // lane 0: replicas 0, 1; lane 1: 2, 3
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      cnt[warp][j0 + e] = n_acc[e] | (bad[e] ? 0x80000000u : 0u);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        if (RED == 0) {
+          part[warp][j0 + e][i][0] = __uint_as_float(sums.fx[e].s[i]);
+        } else {
+          part[warp][j0 + e][i][0] = sums.acc[e][i];
+          part[warp][j0 + e][i][1] = sums.cmp[e][i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  if (lane < kR) {
+    unsigned long long total = 0;
+    bool any_bad = false;
+    for (int w = 0; w < kWarps; ++w) {
+      total += cnt[w][lane] & 0x7fffffffu;
+      any_bad |= (cnt[w][lane] & 0x80000000u) != 0u;
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(&rec[lane].accepted), total);
+    if (any_bad) atomicOr(reinterpret_cast<unsigned long long*>(&rec[lane].flags), 1ull);
+    if (first_block) rec[lane].beta = beta[lane];
+  }
+  if (lane >= kR * 5) return;
+  // lanes 0..19 each own one (replica, sum)
+  const int jr = lane / 5, si = lane - 5 * jr;
+  if (RED == 0) {
+    long long t = 0;
+    for (int w = 0; w < kWarps; ++w) t += (int32_t)__float_as_uint(part[w][jr][si][0]);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&rec[jr].sum[si]),
+              (unsigned long long)t << (XY_FX_SHIFT - xyd::fx_term_shift(si)));
+    return;
+  }
+  float hi = 0.f, lo = 0.f;
+  for (int w = 0; w < kWarps; ++w) {
+    xyd::neumaier_add(hi, lo, part[w][jr][si][0]);
+    lo += part[w][jr][si][1];
+  }
+  const double scaled = ((double)hi + (double)lo) * (double)(1ll << XY_FX_SHIFT);
+  if (!(fabs(scaled) < 9.0e18)) {
+    atomicOr(reinterpret_cast<unsigned long long*>(&rec[jr].flags), 1ull);
+    return;
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(&rec[jr].sum[si]),
+            (unsigned long long)__double2ll_rn(scaled));
+}
+
 // K of replica j (j in 0..3, not known at compile time) without indexing the
 // parameter array.
 __device__ __forceinline__ float replica_k(const QuadFusedArgs& a, int j) {
@@ -300,11 +413,8 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
-  float acc[2][5], cmp[2][5];
-#pragma unroll
-  for (int e = 0; e < 2; ++e)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
+  QuadSums<RED> sums;
+  sums.init();
   float* dst_blk = item.dst + plane;
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
@@ -342,71 +452,12 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
     xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
                        n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (RED == 0) {
-        acc[0][i] += v0[i];
-        acc[1][i] += v1[i];
-      } else {
-        xyd::neumaier_add(acc[0][i], cmp[0][i], v0[i]);
-        xyd::neumaier_add(acc[1][i], cmp[1][i], v1[i]);
-      }
-    }
+    sums.add(v0, v1);
   }
 
   end();
-  // ---- per-replica sums: lanes of one parity -> warps -> FP64 -> records ----
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    n_acc[e] = parity_sum(n_acc[e]);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      acc[e][i] = parity_sum(acc[e][i]);
-      if (RED == 1) cmp[e][i] = parity_sum(cmp[e][i]);
-    }
-  }
-  if (lane < 2) {                                          // lane 0: replicas 0, 1; lane 1: 2, 3
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      cnt[warp][j0 + e] = n_acc[e];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        part[warp][j0 + e][i][0] = acc[e][i];
-        part[warp][j0 + e][i][1] = (RED == 1) ? cmp[e][i] : 0.f;
-      }
-    }
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  const bool first_block = bx == 0 && by == 0;
-  if (lane < kR) {
-    unsigned long long total = 0;
-    for (int w = 0; w < kWarps; ++w) total += cnt[w][lane];
-    atomicAdd(reinterpret_cast<unsigned long long*>(&item.rec[lane].accepted), total);
-    if (first_block) item.rec[lane].beta = a.beta[lane];
-  }
-  if (lane >= kR * 5) return;
-  // lanes 0..19 each own one (replica, sum)
-  const int jr = lane / 5, si = lane - 5 * jr;
-  double d;
-  if (RED == 0) {
-    d = 0.0;
-    for (int w = 0; w < kWarps; ++w) d += (double)part[w][jr][si][0];
-  } else {
-    float hi = 0.f, lo = 0.f;
-    for (int w = 0; w < kWarps; ++w) {
-      xyd::neumaier_add(hi, lo, part[w][jr][si][0]);
-      lo += part[w][jr][si][1];
-    }
-    d = (double)hi + (double)lo;
-  }
-  const double scaled = d * (double)(1ll << XY_FX_SHIFT);
-  if (!(fabs(scaled) < 9.0e18)) {
-    atomicOr(reinterpret_cast<unsigned long long*>(&item.rec[jr].flags), 1ull);
-    return;
-  }
-  atomicAdd(reinterpret_cast<unsigned long long*>(&item.rec[jr].sum[si]),
-            (unsigned long long)__double2ll_rn(scaled));
+  // ---- per-replica sums -> records ----
+  quad_commit<RED>(sums, n_acc, part, cnt, item.rec, a.beta, bx == 0 && by == 0, j0);
 }
 
 // The per-sweep kernel keeps its own copy of the tile arithmetic of
@@ -572,11 +623,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   __syncthreads();
 
   // ---- black half of the tile, with the sweep sums ----
-  float acc[2][5], cmp[2][5];
-#pragma unroll
-  for (int e = 0; e < 2; ++e)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) acc[e][i] = cmp[e][i] = 0.f;
+  QuadSums<RED> sums;
+  sums.init();
   float* dst_blk = a.dst + plane;
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
@@ -614,70 +662,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
     xyd::measure_terms(r1.c, r1.s, n.l[1].x, n.l[1].y, n.r[1].x, n.r[1].y, n.d[1].x, n.d[1].y,
                        n.u[1].x, n.u[1].y, n.Sc[1], n.Ss[1], m.z, m.w, v1);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      if (RED == 0) {
-        acc[0][i] += v0[i];
-        acc[1][i] += v1[i];
-      } else {
-        xyd::neumaier_add(acc[0][i], cmp[0][i], v0[i]);
-        xyd::neumaier_add(acc[1][i], cmp[1][i], v1[i]);
-      }
-    }
+    sums.add(v0, v1);
   }
 
-  // ---- per-replica sums: lanes of one parity -> warps -> FP64 -> records ----
-#pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    n_acc[e] = parity_sum(n_acc[e]);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      acc[e][i] = parity_sum(acc[e][i]);
-      if (RED == 1) cmp[e][i] = parity_sum(cmp[e][i]);
-    }
-  }
-  if (lane < 2) {                                          // lane 0: replicas 0, 1; lane 1: 2, 3
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      cnt[warp][j0 + e] = n_acc[e];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        part[warp][j0 + e][i][0] = acc[e][i];
-        part[warp][j0 + e][i][1] = (RED == 1) ? cmp[e][i] : 0.f;
-      }
-    }
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  const bool first_block = blockIdx.x == 0 && blockIdx.y == 0;
-  if (lane < kR) {
-    unsigned long long total = 0;
-    for (int w = 0; w < kWarps; ++w) total += cnt[w][lane];
-    atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[lane].accepted), total);
-    if (first_block) a.rec[lane].beta = a.beta[lane];
-  }
-  if (lane >= kR * 5) return;
-  // lanes 0..19 each own one (replica, sum)
-  const int jr = lane / 5, si = lane - 5 * jr;
-  double d;
-  if (RED == 0) {
-    d = 0.0;
-    for (int w = 0; w < kWarps; ++w) d += (double)part[w][jr][si][0];
-  } else {
-    float hi = 0.f, lo = 0.f;
-    for (int w = 0; w < kWarps; ++w) {
-      xyd::neumaier_add(hi, lo, part[w][jr][si][0]);
-      lo += part[w][jr][si][1];
-    }
-    d = (double)hi + (double)lo;
-  }
-  const double scaled = d * (double)(1ll << XY_FX_SHIFT);
-  if (!(fabs(scaled) < 9.0e18)) {
-    atomicOr(reinterpret_cast<unsigned long long*>(&a.rec[jr].flags), 1ull);
-    return;
-  }
-  atomicAdd(reinterpret_cast<unsigned long long*>(&a.rec[jr].sum[si]),
-            (unsigned long long)__double2ll_rn(scaled));
+  // ---- per-replica sums -> records ----
+  quad_commit<RED>(sums, n_acc, part, cnt, a.rec, a.beta,
+                   blockIdx.x == 0 && blockIdx.y == 0, j0);
 }
 
 // Polls of a tile counter before a wait gives up (with a short sleep between

@@ -26,9 +26,10 @@
 //   Ix += sin(t_b - t_right) - sin(t_b - t_left)
 //   Iy += sin(t_b - t_up)    - sin(t_b - t_down)
 //   M  += unit vector of the black site + of the red site with the same (y, k).
-// Reduction: FP32 per thread (<= 16 sites), FP32 warp shuffle, FP64 across
-// the CTA's warps, then an exact 64-bit fixed-point atomic add into the
-// record (order independent, so the record does not depend on CTA timing).
+// Reduction (xyd::commit_sums): every term rounded to fixed point before any
+// addition, exact integer sums per thread, warp and CTA, then one 64-bit
+// atomic add per sum into the record: the record depends on neither the
+// order of addition nor the kernel (compensated FP32 in reduce mode 1).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,8 +94,8 @@ k_half_sweep(HalfSweepArgs a) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned int n_acc = 0;
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float cmp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // Neumaier corrections (RED == 1)
+  xyd::SweepSums<RED> sums;                    // at most 16 black sites per thread
+  sums.init();
   const bool measure = (COLOUR == 1);
 
   for (int rr = 0; rr < 4; ++rr) {
@@ -145,14 +146,7 @@ k_half_sweep(HalfSweepArgs a) {
         float v[5];
         xyd::measure_terms(res.c, res.s, cl, sl, cr, sr, cd, sd, cu, su, Sc, Ss,
                            s_cos[ty + 1][sc], s_sin[ty + 1][sc], v);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-          if (RED == 0) {
-            acc[i] += v[i];
-          } else {
-            xyd::neumaier_add(acc[i], cmp[i], v[i]);
-          }
-        }
+        sums.add(v);
       }
     }
     if (full) {
@@ -164,8 +158,8 @@ k_half_sweep(HalfSweepArgs a) {
     }
   }
 
-  xyd::commit_block<kThreads / 32, RED, COLOUR == 1>(acc, cmp, n_acc, s_part, s_cnt, a.rec, a.beta,
-                                                    blockIdx.x == 0 && blockIdx.y == 0);
+  xyd::commit_sums<kThreads / 32, RED, COLOUR == 1>(sums, n_acc, s_part, s_cnt, a.rec, a.beta,
+                                                   blockIdx.x == 0 && blockIdx.y == 0);
 }
 
 __global__ void k_start(float* __restrict__ theta, int L, const xyd::RoundKeys rk,

@@ -19,7 +19,8 @@ def _torch():
 
 class Lattice:
     def __init__(self, L, beta, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
-                 reduce="fp64", lattice_id=0, algorithm="auto", device=None, stream=None):
+                 reduce="exact", lattice_id=0, algorithm="auto", device=None, stream=None,
+                 ctas_per_sm=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -35,11 +36,12 @@ class Lattice:
         p.seed = int(seed)
         p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
                          "libm": X.XY_SINCOS_LIBM}[sincos]
-        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.reduce_mode = {"exact": X.XY_REDUCE_EXACT, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
                        "two_pass": X.XY_ALGO_TWO_PASS,
                        "persistent": X.XY_ALGO_PERSISTENT}[algorithm]
+        p.ctas_per_sm = int(ctas_per_sm)
         self.params = p
         self.J = float(J)
         with torch.cuda.device(self.device):
@@ -153,7 +155,7 @@ class Batch:
     per-lattice ladder ids (-1 or None for no exchange)."""
 
     def __init__(self, Ls, betas, seed, ladders=None, J=1.0, delta=math.pi, start="hot",
-                 sincos="accurate", reduce="fp64", lattice_id0=0, sweeps_per_round=10,
+                 sincos="accurate", reduce="exact", lattice_id0=0, sweeps_per_round=10,
                  target_band_sites=0, algorithm="auto", device=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
@@ -176,7 +178,7 @@ class Batch:
         p.start = {"hot": X.XY_START_HOT, "cold": X.XY_START_COLD}[start]
         p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
                          "libm": X.XY_SINCOS_LIBM}[sincos]
-        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.reduce_mode = {"exact": X.XY_REDUCE_EXACT, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id0 = int(lattice_id0)
         p.sweeps_per_round = int(sweeps_per_round)
         p.target_band_sites = int(target_band_sites)
@@ -269,7 +271,7 @@ class Quad:
     packing of Sec. 3.2): replica r has lattice id lattice_id + r and beta betas[r]."""
 
     def __init__(self, L, betas, seed, J=1.0, delta=math.pi, start="hot", sincos="accurate",
-                 reduce="fp64", lattice_id=0, algorithm="auto", device=None, stream=None):
+                 reduce="exact", lattice_id=0, algorithm="auto", device=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -287,7 +289,7 @@ class Quad:
         p.seed = int(seed)
         p.sincos_mode = {"accurate": X.XY_SINCOS_ACCURATE, "fast": X.XY_SINCOS_FAST,
                          "libm": X.XY_SINCOS_LIBM}[sincos]
-        p.reduce_mode = {"fp64": X.XY_REDUCE_FP64, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
+        p.reduce_mode = {"exact": X.XY_REDUCE_EXACT, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
                        "two_pass": X.XY_ALGO_TWO_PASS,

@@ -80,20 +80,32 @@ def lockstep_sweep(before32, after32, L, beta, seed, sweep, J=1.0, delta=np.pi,
     return red, blk
 
 
-def record_tolerance(N, fast=False):
+# Per sincos path: the standard deviation of one black site's term error
+# against FP64 on the same state (the rounding of the term to fixed point,
+# 2^-19 / sqrt(12) for the four bond cosines, plus the FP32 evaluation from
+# FP32 unit vectors), and a bound on the systematic error per bond from the
+# unit vectors' mean length bias (measured mean |v|^2 - 1: -1e-9 for the
+# polynomial, +1.8e-8 for CUDA's sincosf, a few 1e-8 for __sincosf, whose
+# per-value error is up to 7e-7).
+RECORD_ERR = {"accurate": (7e-7, 2e-9), "libm": (7e-7, 4e-8), "fast": (1.5e-6, 3e-7)}
+
+
+def record_tolerance(N, fast=False, sincos=None, reduce="exact"):
     """Absolute tolerance of a record's sums against the oracle on the same state.
 
-    Two parts.  (1) Rounding of the FP32 partial sums (<= 16 terms per
-    thread, 32 threads per warp, then FP64): ~1e-4 per warp partial, adding
-    randomly over N/1024 warps; 2e-3 per sqrt(1024 sites) is ten times that.
-    (2) The per-term error of the FP32 unit vectors: sincosf is faithfully
-    rounded but its error need not average to zero, so it can add up
-    linearly over the N sites: allowed 1e-7 per site for the accurate path
-    (measured mean ~2e-8 per site at L=4096) and 1e-6 per site for the
-    SFU path (__sincosf absolute error ~4e-7 per value).  A single wrong bond
-    moves C by O(1); a wrong stencil moves it by O(N)."""
-    per_site = 1e-6 if fast else 1e-7
-    return 2e-3 * max(1.0, np.sqrt(N / 1024.0)) + per_site * N
+    Exact sums (reduce "exact"): the record is the exact sum of the N/2 black
+    sites' terms, each rounded to fixed point, so the error is the sum of the
+    per-term errors: 6 sigma sqrt(N/2) for the random part and 2N x the bias
+    bound for the systematic part (2N bonds).  At L = 4096 (accurate sincos)
+    that is 0.08, below the change of C from a single wrong bond, |cos a -
+    cos b|, for all but a small fraction of angle pairs.  Compensated FP32
+    sums add their own rounding, ~2e-3 per sqrt(1024 sites)."""
+    mode = sincos or ("fast" if fast else "accurate")
+    sigma, bias = RECORD_ERR[mode]
+    tol = 6.0 * sigma * np.sqrt(N / 2.0) + 2.0 * N * bias
+    if reduce == "compensated":
+        tol += 2e-3 * max(1.0, np.sqrt(N / 1024.0))
+    return tol
 
 
 def compare_record(obs_row, state32, L, J=1.0):

@@ -232,3 +232,12 @@ def test_peak_measure_refuses_bad_arguments_before_the_device(lib):
     # one microbenchmark per kind and one iteration table entry per kind
     import bench
     assert tuple(bench.PEAK_ITERS) == X.PEAK_KINDS
+
+
+def test_create_refuses_a_bad_work_plan(lib):
+    """ctas_per_sm must be 0 (default), 2 or 3; refused before the device is touched."""
+    for bad in (1, 4, -1):
+        ctx = C.c_void_p()
+        st = lib.xy_create(C.byref(_params(L=128, ctas_per_sm=bad)), None, None, C.byref(ctx))
+        assert st == X.XY_EINVAL, bad
+        assert b"ctas_per_sm" in lib.xy_last_error(None)

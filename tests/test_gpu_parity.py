@@ -35,10 +35,10 @@ from paper_0811_2111_gb300 import _lib as X  # noqa: E402
 
 
 def run_lockstep(lat, n, beta, seed, J=1.0, delta=np.pi, band=BAND_ACCURATE, lattice_id=0,
-                 fast=False):
+                 fast=False, sincos=None):
     """n GPU sweeps, each checked in lock-step; returns summary dict."""
     L = lat.L
-    tol = record_tolerance(L * L, fast)
+    tol = record_tolerance(L * L, fast, sincos=sincos)
     n0, _ = lat.info()
     s_before, t0 = lat.state()
     worst = dict(in_band=0, out_band=0, angle=0.0, rec=0.0, acc_mismatch=0,
@@ -176,14 +176,15 @@ def test_fused_and_two_pass_are_bit_identical(sincos):
             out[algo] = (lat.state(), lat.observables())
     (st, nt), ot = out["two_pass"]
     assert nt == 25
-    tol = record_tolerance(256 * 256, fast=(sincos == "fast"))
     for algo in ("fused",):
         (sf, nf), of = out[algo]
         assert nf == nt
         assert np.array_equal(sf, st), algo
         assert np.array_equal(of["accepted"], ot["accepted"]), algo
+        # exact sums: the fused and two-pass kernels form the same per-site
+        # terms, so the records are identical
         for k in ("C", "Ix", "Iy", "Mx", "My"):
-            assert np.max(np.abs(of[k] - ot[k])) <= tol
+            assert np.array_equal(of[k], ot[k]), (algo, k)
 
 
 def test_unit_vector_accuracy():
@@ -229,6 +230,36 @@ def test_lockstep_large_config_full_size(algorithm):
         assert r["rec"] <= 1.0 and r["acc_mismatch"] == 0
 
 
+def test_record_check_catches_one_wrong_bond_at_full_size():
+    """L=4096: the GPU record of a sweep is within record_tolerance of the oracle's
+    sums on the same state, and an oracle with one wrong bond (the x bond of one site
+    taken to its y neighbour instead, the change of C and of Ix at least 0.5) falls
+    outside it."""
+    w = WL.LARGE
+    L = w.L
+    tol = record_tolerance(L * L)
+    with LT.Lattice(L, w.beta, w.seed) as lat:
+        lat.sweep(3)
+        state, _ = lat.state()
+        obs = lat.observables(2, 1)
+    got = np.array([obs[k][0] for k in ("C", "Ix", "Iy", "Mx", "My")])
+    th = state.reshape(-1).astype(np.float64)
+    ref = oracle.measure(th, L, L)
+    assert np.max(np.abs(got - ref)) <= tol
+    s = np.arange(L * L)
+    right = (s // L) * L + (s + 1) % L
+    down = (s + L) % (L * L)
+    dC = np.cos(th - th[down]) - np.cos(th - th[right])
+    dI = np.sin(th - th[down]) - np.sin(th - th[right])
+    site = int(np.flatnonzero((np.abs(dC) >= 0.5) & (np.abs(dI) >= 0.5))[0])
+    planted = ref.copy()
+    planted[0] += dC[site]
+    planted[1] += dI[site]
+    print(f"L=4096 record vs oracle: max |diff| {np.max(np.abs(got - ref)):.3e}, tolerance "
+          f"{tol:.3e}; one wrong bond moves C by {dC[site]:+.3f}, Ix by {dI[site]:+.3f}")
+    assert abs(got[0] - planted[0]) > tol and abs(got[1] - planted[1]) > tol
+
+
 def test_fast_path_error_is_bounded():
     """__sincosf/__expf path: decisions may differ in a wider band, stated and bounded."""
     w = WL.SMALL
@@ -239,15 +270,15 @@ def test_fast_path_error_is_bounded():
     assert r_wide["angle"] <= ANGLE_TOL and r_wide["rec"] <= 1.0
 
 
-def test_compensated_reduction_matches_fp64():
+def test_compensated_reduction_matches_exact():
     w = WL.SMALL
     outs = []
-    for red in ("fp64", "compensated"):
+    for red in ("exact", "compensated"):
         with LT.Lattice(128, 1.1, 9, reduce=red) as lat:
             lat.sweep(50)
             outs.append((lat.state()[0], lat.observables()))
     assert np.array_equal(outs[0][0], outs[1][0])      # the chain does not depend on it
-    tol = record_tolerance(128 * 128)
+    tol = record_tolerance(128 * 128, reduce="compensated")
     for k in ("C", "Ix", "Iy", "Mx", "My"):
         assert np.max(np.abs(outs[0][1][k] - outs[1][1][k])) <= tol
 

@@ -25,9 +25,10 @@ from paper_0811_2111_gb300.lattice import Lattice  # noqa: E402
 FIELDS = ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta")
 
 
-def _run(L, algorithm, calls, sincos="accurate", reduce="fp64", beta=1.12, seed=31, lid=2):
+def _run(L, algorithm, calls, sincos="accurate", reduce="exact", beta=1.12, seed=31, lid=2,
+         ctas_per_sm=0):
     with Lattice(L, beta, seed, sincos=sincos, reduce=reduce, lattice_id=lid,
-                 algorithm=algorithm) as lat:
+                 algorithm=algorithm, ctas_per_sm=ctas_per_sm) as lat:
         for n in calls:
             lat.sweep(n)
         s, nxt = lat.state()
@@ -36,8 +37,8 @@ def _run(L, algorithm, calls, sincos="accurate", reduce="fp64", beta=1.12, seed=
 
 
 @pytest.mark.parametrize("L", [128, 256, 384, 512, 1024, 2048])
-@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
-                                           ("libm", "fp64")])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated"),
+                                           ("libm", "exact")])
 def test_persistent_equals_fused(L, sincos, reduce):
     """L = 128: one tile column (left and right neighbour are the tile itself);
     384: three tile columns and twelve rows; 512-2048: 64-1024 tiles, where
@@ -76,6 +77,19 @@ def test_bench_launch_configuration():
         assert np.array_equal(op[k], of[k]), k
 
 
+@pytest.mark.parametrize("algorithm", ["persistent", "fused"])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated")])
+def test_work_plans_are_bit_identical(algorithm, sincos, reduce):
+    """The tile kernel compiled for 2 CTAs per SM (up to 128 registers) and for 3
+    (up to 80): the same angles, accept counts and records; L = 4096, 20 sweeps."""
+    s2, n2, o2 = _run(4096, algorithm, (20,), sincos, reduce, ctas_per_sm=2)
+    s3, n3, o3 = _run(4096, algorithm, (20,), sincos, reduce, ctas_per_sm=3)
+    assert n2 == n3 == 20
+    assert np.array_equal(s2, s3)
+    for k in FIELDS:
+        assert np.array_equal(o2[k], o3[k]), k
+
+
 def test_calls_split_anywhere():
     """The state after odd and even sweep counts per call (the ping-pong buffer
     parity), and one sweep per call, equal one call for all sweeps."""
@@ -92,7 +106,7 @@ def test_caller_owned_buffer():
     theta = torch.zeros(L * L, dtype=torch.float32, device="cuda")
     p = X.xy_params()
     p.L, p.start, p.beta, p.J, p.delta, p.seed = L, X.XY_START_HOT, beta, 1.0, np.pi, seed
-    p.sincos_mode, p.reduce_mode, p.lattice_id = X.XY_SINCOS_ACCURATE, X.XY_REDUCE_FP64, 0
+    p.sincos_mode, p.reduce_mode, p.lattice_id = X.XY_SINCOS_ACCURATE, X.XY_REDUCE_EXACT, 0
     p.algorithm = X.XY_ALGO_PERSISTENT
     import ctypes as C
     stream = torch.cuda.current_stream()

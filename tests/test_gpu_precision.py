@@ -23,8 +23,8 @@ from paper_0811_2111_gb300 import workloads as WL  # noqa: E402
 BANDS = {"accurate": 1e-6, "libm": 1e-6, "fast": 2e-5}
 
 
-@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("libm", "fp64"),
-                                           ("fast", "fp64"), ("accurate", "compensated"),
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("libm", "exact"),
+                                           ("fast", "exact"), ("accurate", "compensated"),
                                            ("fast", "compensated")])
 def test_precision_variant_errors_at_L512(sincos, reduce):
     w = WL.PRECISION_CHECK
@@ -50,7 +50,7 @@ def test_precision_variant_errors_at_L512(sincos, reduce):
           f"{stats['angle']:.2e}, max |record - FP64| (C, Ix, Iy, Mx, My) {stats['rec']}")
     assert stats["out_band"] == 0
     assert stats["angle"] <= ANGLE_TOL
-    assert stats["rec"].max() <= record_tolerance(L * L, fast)
+    assert stats["rec"].max() <= record_tolerance(L * L, sincos=sincos, reduce=reduce)
 
 
 def test_free_running_observables_vs_oracle_L512():

@@ -27,8 +27,8 @@ BETAS = [0.7, 1.0, 1.12, 1.4]
 
 
 @pytest.mark.parametrize("L", [2, 6, 32, 34, 64, 96, 130, 256])
-@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "fp64"),
-                                           ("accurate", "compensated"), ("libm", "fp64")])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "exact"),
+                                           ("accurate", "compensated"), ("libm", "exact")])
 def test_replicas_equal_single_lattices(L, sincos, reduce):
     """AUTO: the persistent sweep for L % 32 == 0 (32, 64, 96, 256), two-pass otherwise."""
     sweeps = 7
@@ -46,9 +46,12 @@ def test_replicas_equal_single_lattices(L, sincos, reduce):
         assert np.array_equal(states[r], s), (L, r)
         assert np.array_equal(obs[r]["accepted"], o["accepted"]), (L, r)
         assert np.all(obs[r]["beta"] == beta)
-        tol = record_tolerance(L * L, fast=(sincos == "fast"))
+        tol = record_tolerance(L * L, sincos=sincos, reduce=reduce)
         for k in ("C", "Ix", "Iy", "Mx", "My"):
-            assert np.max(np.abs(obs[r][k] - o[k])) <= tol, (L, r, k)
+            if reduce == "exact":       # the same per-site terms: the same record bits
+                assert np.array_equal(obs[r][k], o[k]), (L, r, k)
+            else:
+                assert np.max(np.abs(obs[r][k] - o[k])) <= tol, (L, r, k)
 
 
 def test_hot_start_and_cold_start():
@@ -90,7 +93,7 @@ def test_error_paths():
 
 
 @pytest.mark.parametrize("L", [32, 128, 512])
-@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated")])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated")])
 def test_fused_equals_two_pass(L, sincos, reduce):
     """The one-launch sweep (tiles of 32 rows x 16 sites, the red ring recomputed
     at the tile edges, several tiles per row and column from L = 64 on) and the
@@ -105,13 +108,16 @@ def test_fused_equals_two_pass(L, sincos, reduce):
                          q.state(0)[1])
     (sf, of, nf), (st, ot, nt) = out["fused"], out["two_pass"]
     assert nf == nt == sweeps
-    tol = record_tolerance(L * L, fast=(sincos == "fast"))
+    tol = record_tolerance(L * L, sincos=sincos, reduce=reduce)
     for r in range(4):
         assert np.array_equal(sf[r], st[r]), r
         assert np.array_equal(of[r]["accepted"], ot[r]["accepted"]), r
         assert np.all(of[r]["beta"] == BETAS[r])
         for k in ("C", "Ix", "Iy", "Mx", "My"):
-            assert np.max(np.abs(of[r][k] - ot[r][k])) <= tol, (r, k)
+            if reduce == "exact":
+                assert np.array_equal(of[r][k], ot[r][k]), (r, k)
+            else:
+                assert np.max(np.abs(of[r][k] - ot[r][k])) <= tol, (r, k)
 
 
 def test_fused_sweeps_in_pieces_equal_one_run():
@@ -140,8 +146,8 @@ def test_fused_algorithm_needs_l_multiple_of_32():
 
 
 @pytest.mark.parametrize("L", [32, 64, 128, 512, 2048])
-@pytest.mark.parametrize("sincos,reduce", [("accurate", "fp64"), ("fast", "compensated"),
-                                           ("libm", "fp64")])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated"),
+                                           ("libm", "exact")])
 def test_persistent_equals_fused(L, sincos, reduce):
     """All sweeps of a call in one cooperative launch against one fused launch
     per sweep: angles, accept counts and records bit for bit (the same tile
