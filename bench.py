@@ -40,12 +40,15 @@ FLUSH_BYTES = 256 << 20
 #   Philox4x32-10: 20 wide multiplies + 20 three-input xors, 2 + 2 of them shared
 #     by all sites of a sweep -> 36 per block, and one block serves two updates
 #     (the sites x and x + 2 of a row share it) -> 18;
-#   proposal 2u0 - 1 and wrap -> 6;  neighbour sums (2 x 3 adds) -> 6;
-#   two unit vectors (own + proposal; neighbours reuse their own): 2 x 27 with the
-#     polynomial / CUDA sincosf-class path, 2 x 3 with the SFU intrinsics;
+#   proposal theta + (delta 2^-23) ((w0 >> 8) - 2^23) and wrap -> 5;
+#   neighbour sums (2 x 3 adds) -> 6;
+#   two unit vectors (own + proposal; neighbours reuse their own): 2 x 25 with the
+#     polynomial (reduction 4, minimax polynomials 9, quadrant 6, shared square
+#     and products), 2 x 3 with the SFU intrinsics, 2 x 27 with CUDA's sincosf;
 #   dE, Boltzmann factor, accept test and select: 22 (expf) / 14 (__expf);
-#   per-sweep sums: 17 per black site -> 8.5 per update.
-ALG_INSTR_PER_UPDATE = {"accurate": 110.5, "libm": 114.5, "fast": 58.5}
+#   per-sweep sums: 12 products and sums, 5 roundings to fixed point and 2.5
+#     integer adds per black site -> 9.75 per update.
+ALG_INSTR_PER_UPDATE = {"accurate": 110.75, "libm": 114.75, "fast": 58.75}
 SMS, SMSP_PER_SM, LANES = 152, 4, 32       # GB300: 152 SMs x 4 schedulers x 32 lanes
 TIMING_EVERY = 50          # kernel events on every 50th sweep of the timed region
 
@@ -57,7 +60,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sincos", choices=["accurate", "fast", "libm"], default="accurate")
-    ap.add_argument("--algorithm", choices=["auto", "fused", "two_pass", "persistent"],
+    ap.add_argument("--algorithm", choices=["auto", "fused", "two_pass", "persistent", "fused2"],
                     default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
@@ -210,8 +213,7 @@ def measured_peaks():
 PEAK_ITERS = {"ffma": 32768, "imad": 16384, "imad_wide": 8192, "imad_hi": 16384,
               "lop3": 16384, "iadd": 16384, "mufu_sin": 4096, "mufu_ex2": 4096, "f2i": 4096,
               "dfma": 512, "issue": 16384, "philox": 512, "unit_vector": 1536,
-              "unit_vector_sfu": 2048, "expf": 3072, "unit_vector_table": 2048,
-              "unit_vector_table_smem": 2048}
+              "unit_vector_sfu": 2048, "expf": 3072}
 
 
 def measure_peaks(dev, kinds=None, reps=5):
@@ -317,13 +319,14 @@ def measure_batch(dev, steps, warmup, sincos, rounds_per_step=100):
     from paper_0811_2111_gb300.lattice import Batch, Lattice
 
     Ls, betas, ladders = WL.batch_layout()
-    target = autotune.tune_batch(Ls, betas, ladders, sweeps_per_round=10, sincos=sincos,
-                                 device=dev)
+    plan = autotune.tune_batch(Ls, betas, ladders, sweeps_per_round=10, sincos=sincos,
+                               device=dev, use_cache=False)
     sweeps = rounds_per_step * 10
     sites = sum(L * L for L in Ls)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     with Batch(Ls, betas, WL.BATCH_SEED, ladders=ladders, sweeps_per_round=10, sincos=sincos,
-               target_band_sites=target, device=dev) as b:
+               target_band_sites=plan["target_band_sites"], group_ctas=plan["group_ctas"],
+               ctas_per_sm=plan["ctas_per_sm"], device=dev) as b:
         b.reserve(rounds_per_step * (steps + max(1, warmup)))
         for _ in range(max(1, warmup)):
             b.run(rounds_per_step)
@@ -361,7 +364,10 @@ def measure_batch(dev, steps, warmup, sincos, rounds_per_step=100):
     return {"workload": "xy_batch_256_lattices_L16-256_64beta_x4_exchange_every_10",
             "value": value, "unit": UNIT, "ms_per_step": sum(ms) / steps,
             "sweeps_per_step": sweeps, "lattices": len(Ls), "sites": sites,
-            "ctas_per_launch": n_ctas, "target_band_sites": target,
+            "ctas_per_launch": n_ctas, "target_band_sites": plan["target_band_sites"],
+            "plan": {"group_ctas": plan["group_ctas"], "ctas_per_sm": plan["ctas_per_sm"],
+                     "target_band_sites": plan["target_band_sites"],
+                     "candidates_ms_per_round": plan["ms_per_round"]},
             "exchange_acceptance": float(acc.sum() / max(att.sum(), 1)),
             "single_lattice_kernels_value": single_value,
             "speedup_vs_single_lattice_kernels": value / single_value,
@@ -696,10 +702,22 @@ def run_ours(args):
 
     w = workload(args)
     stream = torch.cuda.current_stream(dev)
+    # the work plan: timed candidates (autotune.tune_lattice) unless both the
+    # algorithm and the CTAs per SM were given
+    tuned = None
+    algorithm, ctas = args.algorithm, args.ctas_per_sm
+    if args.algorithm == "auto" or args.ctas_per_sm == 0:
+        from paper_0811_2111_gb300 import autotune
+        tuned = autotune.tune_lattice(w.L, w.beta, args.sincos, device=dev, use_cache=False)
+        if args.algorithm == "auto" and tuned["algorithm"] != "two_pass":
+            algorithm = tuned["algorithm"]
+        if args.ctas_per_sm == 0:
+            ctas = tuned["ctas_per_sm"]
     lat = Lattice(w.L, w.beta, w.seed, device=dev, stream=stream, lattice_id=rank,
-                  sincos=args.sincos, algorithm=args.algorithm, ctas_per_sm=args.ctas_per_sm)
+                  sincos=args.sincos, algorithm=algorithm, ctas_per_sm=ctas)
     persistent = lat.algorithm == "persistent"        # what AUTO resolved to
-    fused = lat.algorithm in ("fused", "persistent")
+    two = lat.algorithm == "fused2"                     # two sweeps per launch
+    fused = lat.algorithm in ("fused", "persistent", "fused2")
     lat.reserve(w.sweeps)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -771,12 +789,12 @@ def run_ours(args):
     kern = max((0, 1), key=lambda k: kt[k][0])
     kms, klaunch = kt[kern]
     avg_s = kms * 1e-3 / max(klaunch, 1)
-    sweeps_per_launch = w.sweeps if persistent else 1
+    sweeps_per_launch = w.sweeps if persistent else (2 if two else 1)
     updates_per_launch = (w.sites if fused else w.sites // 2) * sweeps_per_launch
     alg_bytes = 8.0 * updates_per_launch     # 8 B per update: one read + one write of the angle
     hbm_peak, peak_kind = measured_peaks()
     hbm_achieved = alg_bytes / avg_s / 1e9
-    names = (["sweep_fused_persist"] if persistent else
+    names = (["sweep_fused_persist"] if persistent else ["sweep_fused2"] if two else
              ["sweep_fused"] if fused else ["red_half_sweep", "black_half_sweep_measure"])
     # issue-slot roofline: the measured issue rate per SM and clock
     # (xy_peak_measure, issue kind) x SMs x the median SM clock sampled during
@@ -814,7 +832,8 @@ def run_ours(args):
                "sample": f"{n} sweeps of L={w.L} from the seed-{w.seed} hot start "
                          f"({dt:.1f} s), OpenMP over the sites of one colour"}
 
-    launches = args.steps * (2 if persistent else 1 + (1 if fused else 2) * w.sweeps)
+    launches = args.steps * (2 if persistent else
+                             1 + ((w.sweeps + 1) // 2 if two else (1 if fused else 2) * w.sweeps))
     extra = None
     if not args.no_extra and world == 1:
         extra = {"batch": measure_batch(dev, 3, 1, args.sincos),
@@ -837,8 +856,12 @@ def run_ours(args):
         "config": {"workload": w.name, "L": w.L, "beta": w.beta, "seed": w.seed,
                    "sweeps_per_step": w.sweeps, "sincos": args.sincos, "reduce": "exact",
                    "kernel": ("persistent fused (one cooperative launch per step)" if persistent
+                              else "two sweeps per launch (temporal blocking)" if two
                               else "fused single-pass" if fused else "two-pass red/black"),
-                   "ctas_per_sm": args.ctas_per_sm or 3,
+                   "ctas_per_sm": ctas or 3,
+                   "plan": ("tuned" if tuned else "given") + f": {lat.algorithm}, "
+                           f"{ctas or 3} CTAs per SM",
+                   "plan_candidates_ms_per_sweep": tuned["ms_per_sweep"] if tuned else None,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -81,9 +81,16 @@ enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
  *                      waits; a wait that runs out is reported as XY_ETIMEOUT
  *                      at the next synchronizing call).  Needs L % 128 == 0
  *                      and every CTA of the grid resident (the launch fails
- *                      with XY_ECUDA otherwise).
+ *                      with XY_ECUDA otherwise);
+ *   XY_ALGO_FUSED2     two sweeps per launch (temporal blocking): each tile is
+ *                      staged with a halo of four rows and columns and runs
+ *                      both sweeps' half-sweeps in shared memory on shrinking
+ *                      regions (half the DRAM traffic, 15 % recomputed halo
+ *                      updates); an odd last sweep of a call runs as FUSED.
+ *                      Needs L % 128 == 0; never chosen by AUTO.
  * All make bit-identical decisions. */
-enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2, XY_ALGO_PERSISTENT = 3 };
+enum { XY_ALGO_AUTO = 0, XY_ALGO_FUSED = 1, XY_ALGO_TWO_PASS = 2, XY_ALGO_PERSISTENT = 3,
+       XY_ALGO_FUSED2 = 4 };
 /* Per-sweep sums (records below):
  *   XY_REDUCE_EXACT        every per-site term is rounded to fixed point
  *                          (2^-19 for the four bond cosines of a site, 2^-20
@@ -290,6 +297,10 @@ typedef struct {
                                    block cluster, one staging and one cluster barrier
                                    per sweep; XY_ALGO_TWO_PASS: every lattice in place
                                    in the cluster kernel, two barriers per sweep */
+    int32_t group_ctas;         /* work plan: CTAs per grouped tile launch (each group one
+                                   graph branch; 0: 128, at most 4096)               */
+    int32_t ctas_per_sm;        /* work plan: the grouped tile kernel compiled for 3 or 2
+                                   CTAs per SM, as xy_params.ctas_per_sm (0: 3)      */
 } xy_batch_params;
 
 /* Create and hot/cold-start all lattices; the plan, ladders and buffers are

@@ -47,10 +47,7 @@ typedef enum {
     XY_PEAK_UNIT_VECTOR = 12,     /* the accurate unit vector of the sweep kernels */
     XY_PEAK_UNIT_VECTOR_SFU = 13, /* __sincosf                                     */
     XY_PEAK_EXPF = 14,       /* CUDA expf, the accurate path's Boltzmann factor   */
-    XY_PEAK_UNIT_VECTOR_TABLE = 15,      /* table-and-rotation unit vector, table read
-                                            through the L1 cache                      */
-    XY_PEAK_UNIT_VECTOR_TABLE_SMEM = 16, /* the same, table copied to shared memory   */
-    XY_PEAK_KINDS = 17
+    XY_PEAK_KINDS = 15
 } xy_peak_kind;
 
 /* Runs microbenchmark `kind` (an xy_peak_kind) with `iters` loop iterations

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "X
                 5: "XY_ESTATE", 6: "XY_ENUMERIC"}
 XY_START_HOT, XY_START_COLD = 0, 1
 XY_SINCOS_ACCURATE, XY_SINCOS_FAST, XY_SINCOS_LIBM = 0, 1, 2
-XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS, XY_ALGO_PERSISTENT = 0, 1, 2, 3
+XY_ALGO_AUTO, XY_ALGO_FUSED, XY_ALGO_TWO_PASS, XY_ALGO_PERSISTENT, XY_ALGO_FUSED2 = 0, 1, 2, 3, 4
 XY_REDUCE_EXACT, XY_REDUCE_COMPENSATED = 0, 1
 XY_FX_SHIFT = 30
 XY_MAX_L = 32768
@@ -52,7 +52,7 @@ class xy_batch_params(C.Structure):
                 ("seed", C.c_uint64), ("start", C.c_int32), ("sincos_mode", C.c_int32),
                 ("reduce_mode", C.c_int32), ("lattice_id0", C.c_uint32),
                 ("sweeps_per_round", C.c_int32), ("target_band_sites", C.c_int32),
-                ("algorithm", C.c_int32)]
+                ("algorithm", C.c_int32), ("group_ctas", C.c_int32), ("ctas_per_sm", C.c_int32)]
 
 
 XY_BATCH_MAX_L = 256
@@ -281,8 +281,7 @@ def xy_version():
 # -- instruction-rate microbenchmarks (include/xy_peaks.h) --------------------
 
 PEAK_KINDS = ("ffma", "imad", "imad_wide", "imad_hi", "lop3", "iadd", "mufu_sin", "mufu_ex2",
-              "f2i", "dfma", "issue", "philox", "unit_vector", "unit_vector_sfu", "expf",
-              "unit_vector_table", "unit_vector_table_smem")
+              "f2i", "dfma", "issue", "philox", "unit_vector", "unit_vector_sfu", "expf")
 
 
 def xy_peak_measure(kind, iters, reps=5, stream_ptr=None):

@@ -164,7 +164,8 @@ xy_status validate(const xy_params* p) {
     return XY_EINVAL;
   }
   if (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
-      p->algorithm != XY_ALGO_TWO_PASS && p->algorithm != XY_ALGO_PERSISTENT) {
+      p->algorithm != XY_ALGO_TWO_PASS && p->algorithm != XY_ALGO_PERSISTENT &&
+      p->algorithm != XY_ALGO_FUSED2) {
     set_thread_msg("bad algorithm");
     return XY_EINVAL;
   }
@@ -172,7 +173,8 @@ xy_status validate(const xy_params* p) {
     set_thread_msg("ctas_per_sm must be 0 (default), 2 or 3; got %d", p->ctas_per_sm);
     return XY_EINVAL;
   }
-  if ((p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_PERSISTENT) &&
+  if ((p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_PERSISTENT ||
+       p->algorithm == XY_ALGO_FUSED2) &&
       !xyk::fused_supported(p->L)) {
     set_thread_msg("the fused kernel needs L to be a multiple of 128; got %d", p->L);
     return XY_EINVAL;
@@ -235,6 +237,18 @@ cudaError_t timed_fused(xy_ctx* c, const xyk::FusedArgs& a) {
   cudaError_t e = next_events(c, 0, &e0, &e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
   if (e == cudaSuccess) e = xyk::launch_fused_sweep(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+  return e;
+}
+
+cudaError_t timed_fused2(xy_ctx* c, const xyk::FusedArgs& a) {
+  if (c->timing_every <= 0 || (a.sweep / 2u % (uint32_t)c->timing_every) != 0)
+    return xyk::launch_fused2_sweeps(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
+  cudaEvent_t e0, e1;
+  cudaError_t e = next_events(c, 0, &e0, &e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+  if (e == cudaSuccess)
+    e = xyk::launch_fused2_sweeps(c->p.sincos_mode, c->p.reduce_mode, a, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
   return e;
 }
@@ -333,8 +347,8 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
                   (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L) &&
                    p->L <= kAutoPersistentMaxL);
   c->auto_persistent = c->persistent && p->algorithm == XY_ALGO_AUTO;
-  c->fused = p->algorithm == XY_ALGO_FUSED || c->persistent ||
-             (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
+  c->fused = p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_FUSED2 ||
+             c->persistent || (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
   if (e == cudaSuccess && c->fused) e = xyk::dev_malloc(&c->d_pong, N * sizeof(float));
   if (e == cudaSuccess && c->persistent) {
     e = xyk::dev_malloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
@@ -498,16 +512,20 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : 3;
     float* cur = c->d_theta;
     float* nxt = c->d_pong;
-    for (int64_t i = 0; i < n; ++i) {
+    const bool two = c->p.algorithm == XY_ALGO_FUSED2;
+    for (int64_t i = 0; i < n;) {
       a.src = cur;
       a.dst = nxt;
       a.sweep = (uint32_t)(c->next_sweep + (uint64_t)i);
       a.rec = c->d_rec + c->rec_count + i;
-      cudaError_t e = timed_fused(c, a);
+      // two sweeps per launch where two are left (XY_ALGO_FUSED2)
+      const int step = (two && i + 1 < n) ? 2 : 1;
+      cudaError_t e = step == 2 ? timed_fused2(c, a) : timed_fused(c, a);
       if (e != cudaSuccess) return cuda_fail(c, e, "xy_sweep: fused launch");
       float* t = cur;
       cur = nxt;
       nxt = t;
+      i += step;
     }
     if (cur != c->d_theta) {
       const size_t N = (size_t)c->p.L * (size_t)c->p.L;
@@ -605,7 +623,9 @@ xy_status xy_algorithm(const xy_ctx* c, int32_t* algorithm) {
     set_thread_msg("xy_algorithm: NULL output");
     return XY_EINVAL;
   }
-  *algorithm = c->persistent ? XY_ALGO_PERSISTENT : (c->fused ? XY_ALGO_FUSED : XY_ALGO_TWO_PASS);
+  *algorithm = c->persistent ? XY_ALGO_PERSISTENT
+                : c->p.algorithm == XY_ALGO_FUSED2 ? XY_ALGO_FUSED2
+                : (c->fused ? XY_ALGO_FUSED : XY_ALGO_TWO_PASS);
   return XY_OK;
 }
 

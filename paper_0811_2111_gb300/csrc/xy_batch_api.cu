@@ -183,7 +183,7 @@ void free_all(xy_batch* b) {
 // Shared memory a CTA may use for its band: two CTAs must fit one SM (228 KB).
 constexpr size_t kStageBudget = 96 * 1024;          // two-pass: (r + 2) * L/2 unit vectors
 constexpr size_t kFusedStageBudget = 108 * 1024;    // fused: (r + 4) * L/2 * (2 angles + 2 vectors)
-constexpr int kGroupCtas = 128;                     // CTAs per grouped fused launch (one branch each)
+constexpr int kGroupCtas = 128;                     // default CTAs per grouped launch (one branch each)
 
 size_t band_bytes(bool fused, int rows, int L) {
   const size_t W = (size_t)(L / 2);
@@ -225,7 +225,8 @@ void make_plan(xy_batch* b, int target_sites) {
     const int L = kv.first;
     const int tiles = xyk::fused_supported(L) ? (L / 2 / 64) * (L / 32)   // CTAs of one
                                               : xyk::narrow_tiles(L);      // lattice's sweep
-    const int per = std::max(1, kGroupCtas / tiles);
+    const int group_ctas = b->p.group_ctas > 0 ? b->p.group_ctas : kGroupCtas;
+    const int per = std::max(1, group_ctas / tiles);
     // as few groups as `per` allows, their sizes differing by at most one
     const int count = (int)kv.second.size();
     const int ngroups = (count + per - 1) / per;
@@ -377,6 +378,7 @@ xyk::FusedBatchArgs group_args(const xy_batch* b, size_t g, int s) {
   f.delta = (float)b->p.delta;
   f.rk = xyd::make_round_keys(b->p.seed);
   f.lattice_id0 = b->p.lattice_id0;
+  f.minb = b->p.ctas_per_sm ? b->p.ctas_per_sm : 3;
   return f;
 }
 
@@ -471,9 +473,10 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
       p->sincos_mode > 2 || p->reduce_mode < 0 || p->reduce_mode > 1 ||
       p->sweeps_per_round < 1 || p->sweeps_per_round > 1000000 || p->target_band_sites < 0 ||
       (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
-       p->algorithm != XY_ALGO_TWO_PASS)) {
-    bmsg("bad delta, J, start, sincos_mode, reduce_mode, sweeps_per_round, target_band_sites "
-         "or algorithm");
+       p->algorithm != XY_ALGO_TWO_PASS) || p->group_ctas < 0 || p->group_ctas > 4096 ||
+      (p->ctas_per_sm != 0 && p->ctas_per_sm != 2 && p->ctas_per_sm != 3)) {
+    bmsg("bad delta, J, start, sincos_mode, reduce_mode, sweeps_per_round, target_band_sites, "
+         "algorithm, group_ctas or ctas_per_sm");
     return XY_EINVAL;
   }
   for (int i = 0; i < p->n; ++i) {

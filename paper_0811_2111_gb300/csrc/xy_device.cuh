@@ -7,7 +7,6 @@
 #include <stdint.h>
 
 #include "xy.h"
-#include "xy_sincos_table.h"
 
 namespace xyd {
 
@@ -155,30 +154,7 @@ __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out)
   *c_out = __uint_as_float(__float_as_uint(c0) ^ ((qs + 0x40000000u) & 0x80000000u));
 }
 
-// Unit vector by table and rotation: t = k h + r with h = 2 pi / 1024,
-// k = rint(t / h) and |r| <= h / 2 (Cody-Waite reduction with a two-part h
-// whose high part has 13 significant bits, so k h_hi is exact); then
-//   (cos t, sin t) = (C_k cos r - S_k sin r, S_k cos r + C_k sin r)
-// with (C_k, S_k) from the table (xy_sincos_table.h: FP32 cos and sin of
-// 2 pi k / 1024, each within 0.6 ulp), cos r ~ 1 - r^2 / 2 and sin r ~ r
-// (truncation errors r^4 / 24 < 4e-12 and r^3 / 6 < 5e-9), the small
-// corrections formed first and added to the table value last, so the result
-// is within about one FP32 rounding of the table value's own error.
-// `tab` points at the 1024 (C, S) pairs, in shared or global memory.
-__device__ __forceinline__ void sincos_table(float t, const float2* tab, float* s_out,
-                                             float* c_out) {
-  const float qt = __fmaf_rn(t, __uint_as_float(kTabInvStepBits), kRoundMagic);
-  const int k = __float_as_int(qt) & (kSinCosTableSize - 1);   // k mod 1024
-  const float kf = __fsub_rn(qt, kRoundMagic);
-  float r = __fmaf_rn(-kf, __uint_as_float(kTabStepHiBits), t);   // exact
-  r = __fmaf_rn(-kf, __uint_as_float(kTabStepLoBits), r);
-  const float2 e = tab[k];
-  const float r2h = __fmul_rn(__fmul_rn(r, -0.5f), r);              // cos r - 1
-  *c_out = __fadd_rn(e.x, __fmaf_rn(e.x, r2h, -__fmul_rn(e.y, r)));
-  *s_out = __fadd_rn(e.y, __fmaf_rn(e.y, r2h, __fmul_rn(e.x, r)));
-}
-
-// Precision switch of the fused kernels: 0 = the polynomial above with CUDA's
+// Precision switch of the kernels: 0 = the polynomial above with CUDA's
 // expf, 1 = the SFU intrinsics __sincosf/__expf, 2 = CUDA's sincosf/expf.
 template <int MODE>
 __device__ __forceinline__ void unit_vector(float t, float* s, float* c) {

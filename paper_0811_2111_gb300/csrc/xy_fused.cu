@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused(FusedArgs a) {
 // for the batched engine: the sweep index comes from the device counters and
 // beta from the device (replica exchange moves it), the state ping-pongs
 // between the batch's two buffers by sweep parity.
-template <int MODE, int RED>
-__global__ void __launch_bounds__(kThreads, 3) k_sweep_fused_batch(FusedBatchArgs b) {
+template <int MODE, int RED, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_batch(FusedBatchArgs b) {
   const int i = b.lattices[blockIdx.z];
   const uint32_t sweep = b.counters[0] + (uint32_t)b.s;
   const float* base = (sweep & 1u) ? b.theta2 : b.theta;
@@ -555,20 +555,29 @@ cudaError_t launch_fused_plan(const FusedArgs& a, cudaStream_t stream) {
 
 template <int MODE, int RED>
 cudaError_t launch_fused_batch_one(const FusedBatchArgs& b, int n_lattices, cudaStream_t stream) {
-  // the attribute is set per device before any capture (prepare_fused_batch)
+  // the attributes are set per device before any capture (prepare_fused_batch)
   const dim3 grid(b.L / 2 / kTileK, b.L / kTileRows, n_lattices);
-  k_sweep_fused_batch<MODE, RED><<<grid, kThreads, kSmemBytes, stream>>>(b);
+  if (b.minb == 2)
+    k_sweep_fused_batch<MODE, RED, 2><<<grid, kThreads, kSmemBytes, stream>>>(b);
+  else
+    k_sweep_fused_batch<MODE, RED, 3><<<grid, kThreads, kSmemBytes, stream>>>(b);
   return cudaGetLastError();
+}
+
+template <int MODE, int RED, int MINB>
+cudaError_t prepare_plan() {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED, MINB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED, MINB>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 template <int MODE, int RED>
 cudaError_t prepare_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_sweep_fused_batch<MODE, RED>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  return e;
+  cudaError_t e = prepare_plan<MODE, RED, 3>();
+  return e == cudaSuccess ? prepare_plan<MODE, RED, 2>() : e;
 }
 
 template <int MODE, int RED, int MINB>
@@ -639,7 +648,8 @@ cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode) {
 
 cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
                                      int n_lattices, cudaStream_t stream) {
-  if (!fused_supported(b.L) || n_lattices < 1) return cudaErrorInvalidValue;
+  if (!fused_supported(b.L) || n_lattices < 1 || (b.minb != 2 && b.minb != 3))
+    return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   switch (sincos_mode) {
     case 0:

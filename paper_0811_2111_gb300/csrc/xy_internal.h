@@ -149,6 +149,12 @@ bool quad_fused_supported(int L);
 cudaError_t launch_quad_fused(int sincos_mode, int reduce_mode, const QuadFusedArgs& a,
                               cudaStream_t stream);
 
+// Two sweeps (a.sweep, a.sweep + 1) of a.src into a.dst in one launch, their
+// records at a.rec and a.rec + 1 (xy_fused2.cu); cudaErrorInvalidValue if
+// !fused_supported(a.L) or src == dst.
+cudaError_t launch_fused2_sweeps(int sincos_mode, int reduce_mode, const FusedArgs& a,
+                                 cudaStream_t stream);
+
 // One fused sweep; cudaErrorInvalidValue if !fused_supported(a.L).
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream);
@@ -171,6 +177,7 @@ struct FusedBatchArgs {
   float delta;
   xyd::RoundKeys rk;
   uint32_t lattice_id0;
+  int minb = 3;                 // fused tiles: CTAs per SM the kernel is compiled for (2 or 3)
 };
 cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode);
 cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,

@@ -53,15 +53,8 @@ __global__ void __launch_bounds__(kThreads) k_peak(uint32_t seed, int trips, xyd
   const uint32_t b = seed | 1u, c = seed ^ 0x9e3779b9u;
   const float fb = 1.0f + (float)(seed & 7u) * 1e-7f, fc = 1e-7f * (float)(seed >> 29);
   uint32_t acc = 0;
-  const float2* gtab = reinterpret_cast<const float2*>(xyd::kSinCosTableBits);
-  __shared__ float2 stab[KIND == XY_PEAK_UNIT_VECTOR_TABLE_SMEM ? xyd::kSinCosTableSize : 1];
-  if (KIND == XY_PEAK_UNIT_VECTOR_TABLE_SMEM) {
-    for (int i = threadIdx.x; i < xyd::kSinCosTableSize; i += blockDim.x) stab[i] = __ldg(gtab + i);
-    __syncthreads();
-  }
   if (KIND == XY_PEAK_FFMA || KIND == XY_PEAK_MUFU_SIN || KIND == XY_PEAK_MUFU_EX2 ||
-      KIND == XY_PEAK_UNIT_VECTOR || KIND == XY_PEAK_UNIT_VECTOR_SFU || KIND == XY_PEAK_EXPF ||
-      KIND == XY_PEAK_UNIT_VECTOR_TABLE || KIND == XY_PEAK_UNIT_VECTOR_TABLE_SMEM) {
+      KIND == XY_PEAK_UNIT_VECTOR || KIND == XY_PEAK_UNIT_VECTOR_SFU || KIND == XY_PEAK_EXPF) {
     float f[CH];
 #pragma unroll
     for (int j = 0; j < CH; ++j) f[j] = (float)((t + 97u * j) & 1023u) * (1.0f / 1024.0f);
@@ -83,13 +76,6 @@ __global__ void __launch_bounds__(kThreads) k_peak(uint32_t seed, int trips, xyd
           } else if (KIND == XY_PEAK_UNIT_VECTOR_SFU) {
             float s, co;
             __sincosf(f[j], &s, &co);
-            f[j] = s + co;
-          } else if (KIND == XY_PEAK_UNIT_VECTOR_TABLE || KIND == XY_PEAK_UNIT_VECTOR_TABLE_SMEM) {
-            float s, co;
-            // the chain value s + co lies in [-1.42, 1.42]: keep the argument
-            // in [0, 2 pi) as the sweep kernels do
-            xyd::sincos_table(f[j] + 2.0f,
-                              KIND == XY_PEAK_UNIT_VECTOR_TABLE_SMEM ? stab : gtab, &s, &co);
             f[j] = s + co;
           } else {
             f[j] = __fmaf_rn(expf(f[j]), 0.25f, -0.5f);
@@ -222,8 +208,6 @@ PeakKernel kernel_of(int kind) {
     case XY_PEAK_UNIT_VECTOR: return k_peak<XY_PEAK_UNIT_VECTOR>;
     case XY_PEAK_UNIT_VECTOR_SFU: return k_peak<XY_PEAK_UNIT_VECTOR_SFU>;
     case XY_PEAK_EXPF: return k_peak<XY_PEAK_EXPF>;
-    case XY_PEAK_UNIT_VECTOR_TABLE: return k_peak<XY_PEAK_UNIT_VECTOR_TABLE>;
-    case XY_PEAK_UNIT_VECTOR_TABLE_SMEM: return k_peak<XY_PEAK_UNIT_VECTOR_TABLE_SMEM>;
     default: return nullptr;
   }
 }

@@ -39,8 +39,8 @@ class Lattice:
         p.reduce_mode = {"exact": X.XY_REDUCE_EXACT, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
-                       "two_pass": X.XY_ALGO_TWO_PASS,
-                       "persistent": X.XY_ALGO_PERSISTENT}[algorithm]
+                       "two_pass": X.XY_ALGO_TWO_PASS, "persistent": X.XY_ALGO_PERSISTENT,
+                       "fused2": X.XY_ALGO_FUSED2}[algorithm]
         p.ctas_per_sm = int(ctas_per_sm)
         self.params = p
         self.J = float(J)
@@ -70,9 +70,10 @@ class Lattice:
 
     @property
     def algorithm(self):
-        """The sweep algorithm in use: "fused", "two_pass" or "persistent"."""
+        """The sweep algorithm in use: "fused", "two_pass", "persistent" or "fused2"."""
         return {X.XY_ALGO_FUSED: "fused", X.XY_ALGO_TWO_PASS: "two_pass",
-                X.XY_ALGO_PERSISTENT: "persistent"}[X.xy_algorithm(self.ctx)]
+                X.XY_ALGO_PERSISTENT: "persistent",
+                X.XY_ALGO_FUSED2: "fused2"}[X.xy_algorithm(self.ctx)]
 
     def observables(self, first=0, count=None):
         n, _ = X.xy_info(self.ctx)
@@ -156,7 +157,8 @@ class Batch:
 
     def __init__(self, Ls, betas, seed, ladders=None, J=1.0, delta=math.pi, start="hot",
                  sincos="accurate", reduce="exact", lattice_id0=0, sweeps_per_round=10,
-                 target_band_sites=0, algorithm="auto", device=None, stream=None):
+                 target_band_sites=0, algorithm="auto", device=None, stream=None,
+                 group_ctas=0, ctas_per_sm=0):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -184,6 +186,8 @@ class Batch:
         p.target_band_sites = int(target_band_sites)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
                        "two_pass": X.XY_ALGO_TWO_PASS}[algorithm]
+        p.group_ctas = int(group_ctas)
+        p.ctas_per_sm = int(ctas_per_sm)
         self.params = p
         self.J = float(J)
         self.sweeps_per_round = int(sweeps_per_round)
@@ -292,8 +296,8 @@ class Quad:
         p.reduce_mode = {"exact": X.XY_REDUCE_EXACT, "compensated": X.XY_REDUCE_COMPENSATED}[reduce]
         p.lattice_id = int(lattice_id)
         p.algorithm = {"auto": X.XY_ALGO_AUTO, "fused": X.XY_ALGO_FUSED,
-                       "two_pass": X.XY_ALGO_TWO_PASS,
-                       "persistent": X.XY_ALGO_PERSISTENT}[algorithm]
+                       "two_pass": X.XY_ALGO_TWO_PASS, "persistent": X.XY_ALGO_PERSISTENT,
+                       "fused2": X.XY_ALGO_FUSED2}[algorithm]
         self.params = p
         with torch.cuda.device(self.device):
             self.q = X.xy_quad_create(p, betas, C.c_void_p(self.stream.cuda_stream))

@@ -241,3 +241,18 @@ def test_create_refuses_a_bad_work_plan(lib):
         st = lib.xy_create(C.byref(_params(L=128, ctas_per_sm=bad)), None, None, C.byref(ctx))
         assert st == X.XY_EINVAL, bad
         assert b"ctas_per_sm" in lib.xy_last_error(None)
+
+
+
+def test_batch_create_refuses_a_bad_work_plan(lib):
+    """group_ctas in [0, 4096] and ctas_per_sm in {0, 2, 3}, checked before the device."""
+    Ls = (C.c_int32 * 2)(16, 16)
+    betas = (C.c_double * 2)(1.0, 1.1)
+    for field, bad in (("group_ctas", -1), ("group_ctas", 4097), ("ctas_per_sm", 1),
+                       ("ctas_per_sm", 4)):
+        p = X.xy_batch_params()
+        p.n, p.L, p.beta, p.J, p.delta, p.seed = 2, Ls, betas, 1.0, 3.14159, 1
+        p.sweeps_per_round = 1
+        setattr(p, field, bad)
+        b = C.c_void_p()
+        assert lib.xy_batch_create(C.byref(p), None, C.byref(b)) == X.XY_EINVAL, (field, bad)

@@ -32,9 +32,11 @@ LS = [2, 6, 16, 24, 48, 96, 128, 256, 100, 130]
 BETAS = [0.7, 0.9, 1.0, 1.1, 1.2, 0.95, 1.05, 1.12, 0.85, 1.15]
 
 
-def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5, algorithm="auto"):
+def run_batch(target=0, sincos="accurate", rounds=2, spr=5, seed=23, lid0=5, algorithm="auto",
+              group_ctas=0, ctas_per_sm=0):
     with Batch(LS, BETAS, seed, lattice_id0=lid0, sweeps_per_round=spr,
-               target_band_sites=target, sincos=sincos, algorithm=algorithm) as b:
+               target_band_sites=target, sincos=sincos, algorithm=algorithm,
+               group_ctas=group_ctas, ctas_per_sm=ctas_per_sm) as b:
         b.run(rounds)
         n_ctas = b.info()[3]
         return [b.state(i) for i in range(len(LS))], [b.observables(i) for i in range(len(LS))], n_ctas
@@ -105,16 +107,21 @@ def test_fused_batch_state_after_odd_sweeps():
 
 
 def test_batch_is_independent_of_the_work_plan():
+    """Band sizes, the two-pass algorithm, the CTAs per grouped tile launch (1 to
+    more than all tiles) and the tile kernel's CTAs per SM: the same bits."""
     ref_states, ref_obs, n0 = run_batch(target=8192)
-    for target, algorithm in ((256, "auto"), (1024, "auto"), (65536, "auto"),
-                              (2048, "two_pass"), (256, "two_pass")):
-        states, obs, n = run_batch(target=target, algorithm=algorithm)
+    for target, algorithm, group, ctas in ((256, "auto", 0, 0), (1024, "auto", 0, 0),
+                                           (65536, "auto", 0, 0), (2048, "two_pass", 0, 0),
+                                           (256, "two_pass", 0, 0), (8192, "auto", 1, 0),
+                                           (8192, "auto", 4096, 2), (8192, "auto", 64, 2)):
+        states, obs, n = run_batch(target=target, algorithm=algorithm, group_ctas=group,
+                                   ctas_per_sm=ctas)
         for i in range(len(LS)):
             assert np.array_equal(states[i], ref_states[i])
             assert np.array_equal(obs[i]["accepted"], ref_obs[i]["accepted"])
             for k in ("C", "Ix", "Iy", "Mx", "My"):
                 assert np.array_equal(obs[i][k], ref_obs[i][k]), (target, algorithm, k)
-        print(f"target {target} {algorithm}: {n} CTAs (8192: {n0})")
+        print(f"target {target} {algorithm} group {group} ctas {ctas}: {n} CTAs (8192: {n0})")
 
 
 def test_replica_exchange_matches_oracle_step_by_step():

@@ -90,6 +90,23 @@ def test_work_plans_are_bit_identical(algorithm, sincos, reduce):
         assert np.array_equal(o2[k], o3[k]), k
 
 
+@pytest.mark.parametrize("L", [128, 256, 512, 4096])
+@pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated"),
+                                           ("libm", "exact")])
+def test_two_sweep_launches_equal_one_sweep_launches(L, sincos, reduce):
+    """Temporal blocking (XY_ALGO_FUSED2: a tile staged with a halo of four, both
+    sweeps' half-sweeps in shared memory on shrinking regions): angles, accept
+    counts and records bit for bit those of one launch per sweep, for an even
+    and an odd number of sweeps per call (the odd last one runs one-sweep).
+    L = 128: the halo of one tile column wraps onto the tile itself."""
+    s2, n2, o2 = _run(L, "fused2", (6, 3, 2), sincos, reduce)
+    s1, n1, o1 = _run(L, "fused", (11,), sincos, reduce)
+    assert n2 == n1 == 11
+    assert np.array_equal(s2, s1)
+    for k in FIELDS:
+        assert np.array_equal(o2[k], o1[k]), k
+
+
 def test_calls_split_anywhere():
     """The state after odd and even sweep counts per call (the ping-pong buffer
     parity), and one sweep per call, equal one call for all sweeps."""
