@@ -524,6 +524,12 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
 HMC_BYTES_PER_SITE_STEP = 16.0   # leap-frog step kernel: 4 B angle + 4 B momentum read and written
 
 
+# DRAM bytes of one L = 4096 HMC step launch with the caches as the program
+# leaves them (ncu --cache-control none, four launches: 79.6-84.2 MB read,
+# 110.8-112.3 MB written; profiles/hmc_step_tma_L4096_full.md).
+HMC_DRAM_BYTES_PER_STEP = 191.5e6
+
+
 def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
     """Leap-frog site-steps/s of HMC at L = 4096, beta = 1.12 (trajectories of 80
     steps of 0.0125, from a state thermalised by 2000 Metropolis sweeps and 30
@@ -594,7 +600,13 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
                          "bound": "hbm",
                          "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm,
-                         "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP, "ms_per_launch": step_ms},
+                         "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP, "ms_per_launch": step_ms,
+                         # consecutive steps walk the tiles in opposite orders, so a step
+                         # starts on what the last one left in L2: DRAM moves less than the
+                         # algorithmic bytes (ncu, profiles/hmc_step_tma_L4096_full.md)
+                         "dram_bytes_per_step": HMC_DRAM_BYTES_PER_STEP,
+                         "dram_achieved": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9,
+                         "dram_frac": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9 / hbm},
             "cpu_baseline": {"value": cpu, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"FP64 leap-frog, L={Ls}, {n} steps"},
             "gain_vs_oracle_1core": value / cpu}

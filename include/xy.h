@@ -205,6 +205,19 @@ xy_status xy_algorithm(const xy_ctx *ctx, int32_t *algorithm);
  * Exists to test the failure path; the paper has no counterpart. */
 xy_status xy_selftest_persistent_wait(void *cuda_stream, int64_t polls);
 
+/* The library's debug build (libxy_debug.so, compiled with -DXY_DEBUG) guards
+ * the index arithmetic of its two-pass sweep, layout and whole-lattice batch
+ * kernels: a check that fails sets a bit of a device word and skips the
+ * access instead of trapping.  xy_debug_build returns 1 in that build, 0 in
+ * the release build.  xy_debug_checks synchronizes the device and returns the
+ * failed checks since the last call (bits 0-4: two-pass staging loads, stage
+ * stores, row loads and stores, stage reads, layout indices; bits 8-9:
+ * whole-lattice pair and site positions) and clears them; always 0 in the
+ * release build.  XY_EINVAL for a NULL output, XY_ECUDA if the words cannot
+ * be read.  Test aids; the paper has no counterpart. */
+int32_t xy_debug_build(void);
+xy_status xy_debug_checks(uint32_t *failed);
+
 /* Test hook of the out-of-memory paths: the k-th device allocation made by
  * the library after this call (k >= 1; counted across every engine and thread
  * of the process) fails as if the device were out of memory, without reaching

@@ -9,7 +9,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libxy.so")
+# The library this process uses: libxy.so, or the debug build (libxy_debug.so)
+# when XY_GB300_LIB names it (the debug-build test runs in a child process).
+LIB_PATH = os.environ.get("XY_GB300_LIB") or os.path.join(HERE, "libxy.so")
 
 XY_OK, XY_EINVAL, XY_ENOMEM, XY_ECUDA, XY_ETIMEOUT, XY_ESTATE, XY_ENUMERIC = range(7)
 STATUS_NAMES = {0: "XY_OK", 1: "XY_EINVAL", 2: "XY_ENOMEM", 3: "XY_ECUDA", 4: "XY_ETIMEOUT",
@@ -158,6 +160,8 @@ def lib():
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "xy_peak_last_error": (C.c_char_p, []),
         "xy_debug_fail_alloc": (st, [C.c_int32]),
+        "xy_debug_build": (C.c_int32, []),
+        "xy_debug_checks": (st, [C.POINTER(C.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -15,6 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxy.so")
+# The debug build: device-side index checks that record and skip (xy_debug.h).
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libxy_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -35,21 +38,26 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)])
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force=False, verbose=False, extra=()):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), debug=False):
+    """Build libxy.so (or, with debug=True, libxy_debug.so with -DXY_DEBUG)."""
+    lib = LIB_DEBUG if debug else LIB
+    bdir = BUILD_DEBUG if debug else BUILD
+    if debug:
+        extra = ("-DXY_DEBUG",) + tuple(extra)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     objs = []
     cmds = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
 
@@ -64,10 +72,10 @@ def build(force=False, verbose=False, extra=()):
     if verbose:
         for o in outs:
             sys.stdout.write(o)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 

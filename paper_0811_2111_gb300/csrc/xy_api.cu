@@ -304,6 +304,29 @@ extern "C" {
 
 int32_t xy_version(void) { return 101; }
 
+int32_t xy_debug_build(void) {
+#ifdef XY_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+xy_status xy_debug_checks(uint32_t* failed) {
+  if (!failed) {
+    set_thread_msg("xy_debug_checks: NULL output");
+    return XY_EINVAL;
+  }
+  const unsigned int a = xyk::debug_take_sweep(), b = xyk::debug_take_narrow();
+  if (a == 0xffffffffu || b == 0xffffffffu) {
+    (void)cudaGetLastError();
+    set_thread_msg("xy_debug_checks: reading the device words failed");
+    return XY_ECUDA;
+  }
+  *failed = (a & 0xffu) | ((b & 0xffu) << 8);
+  return XY_OK;
+}
+
 const char* xy_last_error(const xy_ctx* ctx) {
   if (ctx && is_live(ctx) && ctx->magic == kMagicLive && ctx->sticky != XY_OK) return ctx->msg;
   return g_thread_msg;

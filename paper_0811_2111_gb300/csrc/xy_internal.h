@@ -32,6 +32,11 @@ inline cudaError_t dev_malloc(T** p, size_t bytes) {
   return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
 }
 
+// The debug build's device-side check words (xy_debug.h) of the instrumented
+// translation units, read and cleared (0 in the release build).
+unsigned int debug_take_sweep();    // xy_sweep.cu: two-pass sweep, layout kernels
+unsigned int debug_take_narrow();   // xy_narrow.cu: whole-lattice batch kernel
+
 // Arguments of one half-sweep launch over a single lattice.
 struct HalfSweepArgs {
   float* theta;          // [2][L][W] split layout, W = L / 2

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "xy_debug.h"
 #include "xy_device.cuh"
 #include "xy_internal.h"
 
@@ -403,6 +404,11 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       // (flat index o = 2P); left/right neighbours k+q-1, k+q for the first,
       // k+q, k+q+1 for the second ----
       for (int P = threadIdx.x, y = py0, m = pm0; P < npairs; P += kSThreads) {
+        // debug build: the carried (y, m) is the pair's position, in range
+        if (!XY_DCHECK(y >= 0 && y < L && m >= 0 && m < Wp && y * Wp + m == P, 0)) {
+          step_pair(y, m);
+          continue;
+        }
         const int k = 2 * m, o = 2 * P;
         const int q = y & 1;
         const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
@@ -434,6 +440,11 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       __syncthreads();
       // ---- black half, a pair per step, with the sweep sums ----
       for (int P = threadIdx.x, y = py0, m = pm0; P < npairs; P += kSThreads) {
+        // debug build: the carried (y, m) is the pair's position, in range
+        if (!XY_DCHECK(y >= 0 && y < L && m >= 0 && m < Wp && y * Wp + m == P, 0)) {
+          step_pair(y, m);
+          continue;
+        }
         const int k = 2 * m, o = half + 2 * P;
         const int q = (y + 1) & 1;
         const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
@@ -475,6 +486,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       // ---- red half: red site (y, k) is x = 2k + (y & 1); its black
       // neighbours (y, k+q-1), (y, k+q), (y-1, k), (y+1, k) ----
       for (int o = threadIdx.x, y = y0, k = k0; o < half; o += kSThreads) {
+        if (!XY_DCHECK(y >= 0 && y < L && k >= 0 && k < W && y * W + k == o, 1)) {
+          step_site(y, k);
+          continue;
+        }
         const int q = y & 1;
         const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
         int kl = k + q - 1, kr = k + q;
@@ -500,6 +515,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_batch_small(SmallBatchArgs a) 
       // ---- black half, with the sweep sums: black site (y, k) is
       // x = 2k + ((y + 1) & 1); its red neighbours as above ----
       for (int i = threadIdx.x, y = y0, k = k0; i < half; i += kSThreads) {
+        if (!XY_DCHECK(y >= 0 && y < L && k >= 0 && k < W && y * W + k == i, 1)) {
+          step_site(y, k);
+          continue;
+        }
         const int q = (y + 1) & 1;
         const int yd = y == 0 ? L - 1 : y - 1, yu = y == L - 1 ? 0 : y + 1;
         int kl = k + q - 1, kr = k + q;
@@ -586,5 +605,13 @@ cudaError_t launch_small_batch(int sincos_mode, int reduce_mode, const SmallBatc
                          : launch_small_one<2, 0>(a, n_lattices, smem, stream);
   }
 }
+
+}  // namespace xyk
+
+namespace xyk {
+
+// The debug word of this translation unit (whole-lattice and narrow batch
+// kernels; bits 0-1), read and cleared.  0 in the release build.
+unsigned int debug_take_narrow() { return xy_debug_take_word(); }
 
 }  // namespace xyk

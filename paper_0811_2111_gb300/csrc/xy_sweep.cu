@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "xy_debug.h"
 #include "xy_device.cuh"
 #include "xy_internal.h"
 
@@ -70,13 +71,19 @@ k_half_sweep(HalfSweepArgs a) {
     const int gy = xyd::wrap_index(y0 - 1 + r, L);
     const int kk = k0 - 4 + 4 * cg;
     const float* row = other + (size_t)gy * W;
-    float v[4];
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (vec4) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(row + xyd::wrap_index(kk, W)));
-      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+      const int kw = xyd::wrap_index(kk, W);
+      if (XY_DCHECK(gy >= 0 && gy < L && kw >= 0 && kw + 3 < W, 0)) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(row + kw));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+      }
     } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = __ldg(row + xyd::wrap_index(kk + e, W));
+      for (int e = 0; e < 4; ++e) {
+        const int kw = xyd::wrap_index(kk + e, W);
+        if (XY_DCHECK(gy >= 0 && gy < L && kw >= 0 && kw < W, 0)) v[e] = __ldg(row + kw);
+      }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -85,8 +92,10 @@ k_half_sweep(HalfSweepArgs a) {
       if (col >= 3 && col <= kTileCols + 4) {
         float s, c;
         xyd::unit_vector<MODE>(v[e], &s, &c);
-        s_cos[r][col] = c;
-        s_sin[r][col] = s;
+        if (XY_DCHECK(r >= 0 && r < kStageRows, 1)) {
+          s_cos[r][col] = c;
+          s_sin[r][col] = s;
+        }
       }
     }
   }
@@ -105,20 +114,26 @@ k_half_sweep(HalfSweepArgs a) {
     const int q = (y + COLOUR) & 1;                      // x = 2k + q
     const int kq = k0 + lane * 4;
     float* rowp = own + (size_t)y * W;
-    float th[4];
+    float th[4] = {0.f, 0.f, 0.f, 0.f};
     const bool full = vec4 && (kq + 3 < W);
     if (full) {
-      const float4 t = *reinterpret_cast<const float4*>(rowp + kq);
-      th[0] = t.x; th[1] = t.y; th[2] = t.z; th[3] = t.w;
+      if (XY_DCHECK(y >= 0 && y < L && kq >= 0, 2)) {
+        const float4 t = *reinterpret_cast<const float4*>(rowp + kq);
+        th[0] = t.x; th[1] = t.y; th[2] = t.z; th[3] = t.w;
+      }
     } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) th[j] = (kq + j < W) ? rowp[kq + j] : 0.f;
+      for (int j = 0; j < 4; ++j)
+        if (kq + j < W && XY_DCHECK(y >= 0 && y < L && kq + j >= 0, 2)) th[j] = rowp[kq + j];
     }
     uint4 w = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (kq + j >= W) continue;
       const int sc = lane * 4 + j + 4;                   // stage column of (y, k)
+      // the stage rows ty .. ty + 2 and columns sc + q - 1 .. sc + q are read
+      if (!XY_DCHECK(ty >= 0 && ty + 2 < kStageRows && sc + q - 1 >= 0 && sc + q < kStageCols, 3))
+        continue;
       // neighbours in the other plane: same row at k+q-1 (left) and k+q
       // (right), rows y-1 (down) and y+1 (up) at k
       const float cl = s_cos[ty + 1][sc + q - 1], sl = s_sin[ty + 1][sc + q - 1];
@@ -150,11 +165,12 @@ k_half_sweep(HalfSweepArgs a) {
       }
     }
     if (full) {
-      *reinterpret_cast<float4*>(rowp + kq) = make_float4(th[0], th[1], th[2], th[3]);
+      if (XY_DCHECK(y >= 0 && y < L && kq >= 0, 2))
+        *reinterpret_cast<float4*>(rowp + kq) = make_float4(th[0], th[1], th[2], th[3]);
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (kq + j < W) rowp[kq + j] = th[j];
+        if (kq + j < W && XY_DCHECK(y >= 0 && y < L && kq + j >= 0, 2)) rowp[kq + j] = th[j];
     }
   }
 
@@ -177,7 +193,10 @@ __global__ void k_start(float* __restrict__ theta, int L, const xyd::RoundKeys r
       const uint4 w = xyd::philox4x32_10(make_uint4(y * (uint32_t)L + x, 0u, lattice_id, 0u), rk);
       t = (float)(w.x >> 8) * xyd::kHotScale;
     }
-    theta[i] = t;
+    // the split layout's index of (c, y, k) is i itself
+    if (XY_DCHECK(c < 2u && y < (uint32_t)L && k < W &&
+                  (size_t)c * (N / 2u) + (size_t)y * W + k == (size_t)i, 4))
+      theta[i] = t;
   }
 }
 
@@ -193,7 +212,8 @@ __global__ void k_natural_to_split(const float* __restrict__ nat, float* __restr
     if (v < 0.0) v += two_pi;
     float f = (float)v;
     if (f >= xyd::kTwoPi) f = 0.f;
-    split[(size_t)c * (N / 2u) + (size_t)y * W + (x >> 1)] = f;
+    const size_t d = (size_t)c * (N / 2u) + (size_t)y * W + (x >> 1);
+    if (XY_DCHECK(d < (size_t)N, 4)) split[d] = f;
   }
 }
 
@@ -203,7 +223,8 @@ __global__ void k_split_to_natural(const float* __restrict__ split, float* __res
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
     const uint32_t y = s / (uint32_t)L, x = s - y * (uint32_t)L;
     const uint32_t c = (x + y) & 1u;
-    nat[s] = split[(size_t)c * (N / 2u) + (size_t)y * W + (x >> 1)];
+    const size_t d = (size_t)c * (N / 2u) + (size_t)y * W + (x >> 1);
+    if (XY_DCHECK(d < (size_t)N, 4)) nat[s] = split[d];
   }
 }
 
@@ -316,5 +337,13 @@ cudaError_t launch_check_finite(const float* theta, int64_t n, unsigned int* fla
   k_check_finite<<<grid_for(n, 256), 256, 0, stream>>>(theta, n, flag);
   return cudaGetLastError();
 }
+
+}  // namespace xyk
+
+namespace xyk {
+
+// The debug word of this translation unit (two-pass sweep and layout
+// kernels; bits 0-4), read and cleared.  0 in the release build.
+unsigned int debug_take_sweep() { return xy_debug_take_word(); }
 
 }  // namespace xyk

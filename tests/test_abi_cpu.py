@@ -256,3 +256,12 @@ def test_batch_create_refuses_a_bad_work_plan(lib):
         setattr(p, field, bad)
         b = C.c_void_p()
         assert lib.xy_batch_create(C.byref(p), None, C.byref(b)) == X.XY_EINVAL, (field, bad)
+
+
+def test_release_build_has_no_device_checks(lib):
+    """The release library reports itself as such and its debug word is always 0
+    (no device access: the checks are compiled out)."""
+    assert lib.xy_debug_build() == 0
+    w = C.c_uint32(123)
+    assert lib.xy_debug_checks(C.byref(w)) == X.XY_OK and w.value == 0
+    assert lib.xy_debug_checks(None) == X.XY_EINVAL

@@ -10,6 +10,8 @@ test_gpu_parity.py).
 import numpy as np
 import pytest
 
+from gpu_util import record_tolerance
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -96,15 +98,20 @@ def test_work_plans_are_bit_identical(algorithm, sincos, reduce):
 def test_two_sweep_launches_equal_one_sweep_launches(L, sincos, reduce):
     """Temporal blocking (XY_ALGO_FUSED2: a tile staged with a halo of four, both
     sweeps' half-sweeps in shared memory on shrinking regions): angles, accept
-    counts and records bit for bit those of one launch per sweep, for an even
-    and an odd number of sweeps per call (the odd last one runs one-sweep).
+    counts and exact records bit for bit those of one launch per sweep (the
+    compensated sums to their tolerance), for an even and an odd number of
+    sweeps per call (the odd last one runs one-sweep).
     L = 128: the halo of one tile column wraps onto the tile itself."""
     s2, n2, o2 = _run(L, "fused2", (6, 3, 2), sincos, reduce)
     s1, n1, o1 = _run(L, "fused", (11,), sincos, reduce)
     assert n2 == n1 == 11
     assert np.array_equal(s2, s1)
     for k in FIELDS:
-        assert np.array_equal(o2[k], o1[k]), k
+        if reduce == "exact" or k in ("accepted", "beta"):
+            assert np.array_equal(o2[k], o1[k]), k
+        else:   # compensated FP32 partial sums depend on which thread holds which site
+            assert np.max(np.abs(o2[k] - o1[k])) <= record_tolerance(L * L, sincos=sincos,
+                                                                      reduce=reduce), k
 
 
 def test_calls_split_anywhere():
