@@ -73,7 +73,7 @@ def parse():
                          "hmc: HMC at L=4096, 10 trajectories of 80 leap-frog steps per step; "
                          "quad: four replicas per site at L=4096, 200 sweeps per step; "
                          "peaks: the instruction-rate microbenchmarks alone")
-    ap.add_argument("--ctas-per-sm", type=int, default=0, choices=[0, 2, 3],
+    ap.add_argument("--ctas-per-sm", type=int, default=0, choices=[0, 2, 3, 4],
                     help="work plan of the fused sweep: tile CTAs per SM (0: the library's "
                          "default)")
     ap.add_argument("--no-extra", action="store_true",

@@ -119,10 +119,11 @@ typedef struct {
     uint32_t lattice_id;  /* third Philox counter word                          */
     int32_t algorithm;    /* XY_ALGO_AUTO, _FUSED or _PERSISTENT (need L % 128 == 0), _TWO_PASS */
     int32_t ctas_per_sm;  /* work plan of the fused and persistent sweeps: 3 CTAs of the
-                             tile kernel per SM (at most 80 registers a thread), 2 (at
-                             most 128: more independent work in flight per warp, fewer
-                             warps), or 0 for the library's default (3).  Results do not
-                             depend on it; xy_tune-style callers time both. */
+                             tile kernel per SM (at most 80 registers a thread), 4 (at
+                             most 64: more warps per SM), 2 (at most 128: more
+                             independent work in flight per warp, fewer warps), or 0
+                             for the library's default (3).  Results do not depend on
+                             it; tuning callers time the plans (autotune.py). */
 } xy_params;
 
 /* Per-sweep record as stored on the device (64 bytes).  The five sums are
@@ -312,8 +313,8 @@ typedef struct {
                                    in the cluster kernel, two barriers per sweep */
     int32_t group_ctas;         /* work plan: CTAs per grouped tile launch (each group one
                                    graph branch; 0: 128, at most 4096)               */
-    int32_t ctas_per_sm;        /* work plan: the grouped tile kernel compiled for 3 or 2
-                                   CTAs per SM, as xy_params.ctas_per_sm (0: 3)      */
+    int32_t ctas_per_sm;        /* work plan: the grouped tile kernel compiled for 2, 3
+                                   or 4 CTAs per SM, as xy_params.ctas_per_sm (0: 3) */
 } xy_batch_params;
 
 /* Create and hot/cold-start all lattices; the plan, ladders and buffers are

@@ -10,8 +10,8 @@ version, workload shape, precision).
 Single lattices (``tune_lattice``; xy_params): the algorithm (all sweeps of
 a call in one persistent launch, one launch per sweep, or two sweeps per
 launch with temporal blocking) and the tile kernel's CTAs per SM (3 at up to
-80 registers a thread, or 2 at up to 128: more independent work in flight per
-warp, fewer warps).
+80 registers a thread, 4 at up to 64: more warps, or 2 at up to 128: more
+independent work in flight per warp, fewer warps).
 
 Batches (``tune_batch``; xy_batch_params): the CTAs per grouped tile launch
 (lattices of one side are launched in groups, one graph branch each, so
@@ -24,10 +24,10 @@ import hashlib
 import json
 import os
 
-LATTICE_CANDIDATES = (("persistent", 3), ("persistent", 2), ("fused", 3), ("fused", 2),
-                      ("fused2", 3))
+LATTICE_CANDIDATES = (("persistent", 3), ("persistent", 4), ("persistent", 2), ("fused", 3),
+                      ("fused", 4), ("fused", 2), ("fused2", 3))
 GROUP_CTAS = (64, 128, 256, 512)
-BATCH_CTAS_PER_SM = (3, 2)
+BATCH_CTAS_PER_SM = (3, 4, 2)
 BAND_TARGETS = (2048, 8192)
 
 

@@ -169,8 +169,8 @@ xy_status validate(const xy_params* p) {
     set_thread_msg("bad algorithm");
     return XY_EINVAL;
   }
-  if (p->ctas_per_sm != 0 && p->ctas_per_sm != 2 && p->ctas_per_sm != 3) {
-    set_thread_msg("ctas_per_sm must be 0 (default), 2 or 3; got %d", p->ctas_per_sm);
+  if (p->ctas_per_sm != 0 && (p->ctas_per_sm < 2 || p->ctas_per_sm > 4)) {
+    set_thread_msg("ctas_per_sm must be 0 (default), 2, 3 or 4; got %d", p->ctas_per_sm);
     return XY_EINVAL;
   }
   if ((p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_PERSISTENT ||

@@ -474,7 +474,7 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
       p->sweeps_per_round < 1 || p->sweeps_per_round > 1000000 || p->target_band_sites < 0 ||
       (p->algorithm != XY_ALGO_AUTO && p->algorithm != XY_ALGO_FUSED &&
        p->algorithm != XY_ALGO_TWO_PASS) || p->group_ctas < 0 || p->group_ctas > 4096 ||
-      (p->ctas_per_sm != 0 && p->ctas_per_sm != 2 && p->ctas_per_sm != 3)) {
+      (p->ctas_per_sm != 0 && (p->ctas_per_sm < 2 || p->ctas_per_sm > 4))) {
     bmsg("bad delta, J, start, sincos_mode, reduce_mode, sweeps_per_round, target_band_sites, "
          "algorithm, group_ctas or ctas_per_sm");
     return XY_EINVAL;

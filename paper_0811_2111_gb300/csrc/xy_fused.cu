@@ -36,19 +36,42 @@ constexpr int kTileRows = 32;
 constexpr int kTileK = 64;                   // plane columns (2 per lane)
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kSRows = kTileRows + 4;        // rows y0-2 .. y0+33
-constexpr int kSCols = kTileK + 8;           // plane cols k0-4 .. k0+67 (k0-1 .. k0+64 used)
-constexpr int kRing = 2 * kTileK + kTileRows;
-constexpr int kStageRowsTotal = kSRows + (kSRows - 2);   // black rows + red rows staged
+constexpr int kSRows = kTileRows + 4;        // stage rows: global rows y0-2 .. y0+33
+constexpr int kRedRows = kSRows - 2;         // the red plane's stage rows 1 .. 34
 
-constexpr size_t kThBytes = sizeof(float) * 2 * kSRows * kSCols;
-constexpr size_t kCsBytes = sizeof(float2) * 2 * kSRows * kSCols;
+// Shared memory of a tile, 55.1 KB (four CTAs fit an SM).  Stage row r is
+// global row y0 - 2 + r.  Only what the tile reads is kept:
+//   thr  red angles of stage rows 1..34, plane cols k0-4 .. k0+67 (column
+//        k - k0 + kThOff, so the staged float4 groups are 16-byte aligned;
+//        k0-1 .. k0+64 used)
+//   thb  black angles of the tile rows (stage rows 2..33), plane cols k0 .. k0+63
+//   csr  red unit vectors (cos, sin) of stage rows 1..34, plane cols k0-2 ..
+//        k0+65 (column k - k0 + kCsOff: lane l's pair at 2l + 2 is 16-byte
+//        aligned; k0-1 .. k0+64 used)
+//   csb  black unit vectors of stage rows 0..35, same columns
+// then the commit's per-warp partial sums and counters.
+constexpr int kCsOff = 2;
+constexpr int kThOff = 4;
+constexpr int kCsCols = kTileK + 4;
+constexpr int kThCols = kTileK + 8;
+typedef float2 CsRow[kCsCols];
+typedef float ThRow[kThCols];
+typedef float TbRow[kTileK];
+constexpr size_t kThrBytes = sizeof(ThRow) * kRedRows;
+constexpr size_t kThbBytes = sizeof(TbRow) * kTileRows;
+constexpr size_t kCsrBytes = sizeof(CsRow) * kRedRows;
+constexpr size_t kCsbBytes = sizeof(CsRow) * kSRows;
 constexpr size_t kPartBytes = sizeof(float) * kWarps * 5 * 2;
 constexpr size_t kCntBytes = sizeof(unsigned int) * kWarps;
-constexpr size_t kSmemBytes = kThBytes + kCsBytes + kPartBytes + kCntBytes;
-
-typedef float ThArr[kSRows][kSCols];
-typedef float2 CsArr[kSRows][kSCols];
+constexpr size_t kThbAt = kThrBytes;
+constexpr size_t kCsrAt = kThbAt + kThbBytes;
+constexpr size_t kCsbAt = kCsrAt + kCsrBytes;
+constexpr size_t kPartAt = kCsbAt + kCsbBytes;
+constexpr size_t kCntAt = kPartAt + kPartBytes;
+constexpr size_t kSmemBytes = kCntAt + kCntBytes;
+static_assert(kThbAt % 16 == 0 && kCsrAt % 16 == 0 && kCsbAt % 16 == 0 && kPartAt % 16 == 0,
+              "shared-memory regions must stay 16-byte aligned");
+static_assert(4 * (kSmemBytes + 1024) <= 228 * 1024, "four tiles must fit one SM");
 
 // Tiles of one sweep of side L (L % 128 == 0).
 inline int fused_tiles_of(int L) { return (L / 2 / kTileK) * (L / kTileRows); }
@@ -59,24 +82,26 @@ __device__ __forceinline__ int wrap_once(int v, int n) {
   return v;
 }
 
-// The four neighbour unit vectors of the two sites at stage columns c0, c0+1
-// (c0 even) of row r in plane `nb` (the other colour), where a site at column
-// c has its same-row neighbours at c+q-1 and c+q.  The three same-row columns
-// c0+q-1 .. c0+q+1 are the aligned pair (c0, c0+1) and one edge column, c0-1
-// (q = 0) or c0+2 (q = 1); q is a compile-time constant where the row loops
-// are unrolled (rows alternate q), so no selects are issued.
+// The four neighbour unit vectors of the two sites at columns c0, c0+1 (c0
+// even) of row i of the other colour's unit vectors `nb`, where a site at
+// column c has its same-row neighbours at c+q-1 and c+q.  The three same-row
+// columns c0+q-1 .. c0+q+1 are the aligned pair (c0, c0+1) and one edge
+// column, c0-1 (q = 0) or c0+2 (q = 1); q is a compile-time constant where the
+// row loops are unrolled (rows alternate q), so no selects are issued.  Rows
+// i-1 and i of the pair's columns come in as D and P (a warp walks its rows
+// downwards, so they are the previous row's P and U); row i+1 is loaded and
+// returned in U.
 struct PairNeighbours {
   float Sc[2], Ss[2];
   float2 l[2], r[2], d[2], u[2];
 };
 
-__device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, int q,
+__device__ __forceinline__ void pair_neighbours(const CsRow* nb, int i, int c0, int q,
+                                                const float4 D, const float4 P, float4& U,
                                                 PairNeighbours& n) {
-  const float4 P = *reinterpret_cast<const float4*>(&nb[r][c0]);
-  const float2 e = nb[r][q ? c0 + 2 : c0 - 1];
+  const float2 e = nb[i][q ? c0 + 2 : c0 - 1];
   const float2 p0 = make_float2(P.x, P.y), p1 = make_float2(P.z, P.w);
-  const float4 D = *reinterpret_cast<const float4*>(&nb[r - 1][c0]);
-  const float4 U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
+  U = *reinterpret_cast<const float4*>(&nb[i + 1][c0]);
   if (q) {
     n.l[0] = p0;
     n.r[0] = p1;
@@ -99,7 +124,12 @@ __device__ __forceinline__ void pair_neighbours(const CsArr& nb, int r, int c0, 
   }
 }
 
-// One ring site (red, stage (r, c)): same arithmetic as the tile sites.
+__device__ __forceinline__ float4 ld4(const float2* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
+__device__ __forceinline__ void st4(float2* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
 // The scalars of one fused sweep; the Philox round keys are passed separately
 // (by reference, so a kernel can leave them in its parameter space).
 struct FusedCore {
@@ -115,21 +145,23 @@ struct FusedCore {
   double beta;
 };
 
+// One red ring site at stage row r, unit-vector column c: the tile sites'
+// arithmetic, with the site's own Philox block.
 template <int MODE, class Args>
-__device__ __forceinline__ void red_ring_site(ThArr* th, CsArr* cs, int r, int c, int q,
-                                              uint32_t site, uint32_t x, const Args& a,
-                                              const xyd::RoundKeys& rk) {
-  const float2 l = cs[1][r][c + q - 1], rt = cs[1][r][c + q];
-  const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
+__device__ __forceinline__ void red_ring_site(ThRow* thr, CsRow* csr, const CsRow* csb, int r,
+                                              int c, int q, uint32_t site, uint32_t x,
+                                              const Args& a, const xyd::RoundKeys& rk) {
+  const float2 l = csb[r][c + q - 1], rt = csb[r][c + q];
+  const float2 d = csb[r - 1][c], u = csb[r + 1][c];
   const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
   const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
   const uint4 w = xyd::philox4x32_10(
       make_uint4(xyd::metropolis_counter(site, x), a.sweep, a.lattice_id, 1u), rk);
   const uint2 uw = xyd::metropolis_words(w, x);
-  const float2 own = cs[0][r][c];
-  const xyd::SiteResult res =
-      xyd::metropolis_step<MODE>(th[0][r][c], own.x, own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
-  cs[0][r][c] = make_float2(res.c, res.s);   // the black half reads the unit vector only
+  const float2 own = csr[r - 1][c];
+  const xyd::SiteResult res = xyd::metropolis_step<MODE>(thr[r - 1][c + kThOff - kCsOff], own.x,
+                                                         own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
+  csr[r - 1][c] = make_float2(res.c, res.s);   // the black half reads the unit vector only
 }
 
 // One sweep of the tile (bx, by) of one lattice.  Args is FusedArgs (the
@@ -153,10 +185,12 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
                                                  const MidHook& mid = MidHook(),
                                                  const EndHook& end = EndHook()) {
   extern __shared__ __align__(16) unsigned char smem[];
-  ThArr* th = reinterpret_cast<ThArr*>(smem);
-  CsArr* cs = reinterpret_cast<CsArr*>(smem + kThBytes);
-  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + kThBytes + kCsBytes);
-  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kThBytes + kCsBytes + kPartBytes);
+  ThRow* thr = reinterpret_cast<ThRow*>(smem);
+  TbRow* thb = reinterpret_cast<TbRow*>(smem + kThbAt);
+  CsRow* csr = reinterpret_cast<CsRow*>(smem + kCsrAt);
+  CsRow* csb = reinterpret_cast<CsRow*>(smem + kCsbAt);
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + kPartAt);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kCntAt);
 
   const int L = a.L, W = a.W;
   const int k0 = bx * kTileK;
@@ -174,7 +208,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   // 184..255 one or two halo sites: at most 19 unit vectors per thread against
   // a mean of 18.03.  Every load is issued before the first unit vector.
   {
-    const int t = threadIdx.x;
+    const int t = (int)threadIdx.x;
     const int cg = t & 15;
     float4 v[4];
 #pragma unroll
@@ -203,15 +237,15 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     for (int j = 0; j < 2; ++j) {
       if (j < nh) {
         const int h = t >= 192 ? (j == 0 ? t - 192 : t - 128) : t - 56;
-        const int p = h >= 2 * (kSRows - 2) ? 1 : 0;
-        const int rem = h - p * 2 * (kSRows - 2);
+        const int p = h >= 2 * kRedRows ? 1 : 0;
+        const int rem = h - p * 2 * kRedRows;
         const int r = 1 + (rem >> 1);
         const int side = rem & 1;
         const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W;
         const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
         hp[j] = p;
         hr[j] = r;
-        hcol[j] = side ? kTileK + 4 : 3;
+        hcol[j] = side ? kCsOff + kTileK : kCsOff - 1;
         vh[j] = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
       }
     }
@@ -220,46 +254,54 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       const int rr = (t >> 4) + 16 * i;
       const int p = rr < kSRows ? 1 : 0;
       const int r = rr < kSRows ? rr : rr - kSRows + 1;
-      const int col = 4 + 4 * cg;
       float s0, c0, s1, c1, s2, c2, s3, c3;
       xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
       xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
       xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
       xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
-      // angles are read only for the sites the tile updates: the red rows
-      // and the black tile rows 2..33 (a warp-uniform test)
-      if (p == 0 || (r >= 2 && r < kSRows - 2))
-        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
-      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+      // angles are kept only for the sites the tile updates: the red rows and
+      // the black tile rows 2..33 (uniform over each half warp)
+      if (p == 0)
+        *reinterpret_cast<float4*>(&thr[r - 1][kThOff + 4 * cg]) = v[i];
+      else if (r >= 2 && r < kSRows - 2)
+        *reinterpret_cast<float4*>(&thb[r - 2][4 * cg]) = v[i];
+      float2* u = p ? &csb[r][kCsOff + 4 * cg] : &csr[r - 1][kCsOff + 4 * cg];
+      st4(u, make_float4(c0, s0, c1, s1));
+      st4(u + 2, make_float4(c2, s2, c3, s3));
     }
     if (has_tail) {
       float s0, c0, s1, c1;
       xyd::unit_vector<MODE>(vt.x, &s0, &c0);
       xyd::unit_vector<MODE>(vt.y, &s1, &c1);
-      *reinterpret_cast<float2*>(&th[0][tail_r][4 + 2 * tail_c]) = vt;
-      *reinterpret_cast<float4*>(&cs[0][tail_r][4 + 2 * tail_c]) = make_float4(c0, s0, c1, s1);
+      *reinterpret_cast<float2*>(&thr[tail_r - 1][kThOff + 2 * tail_c]) = vt;
+      st4(&csr[tail_r - 1][kCsOff + 2 * tail_c], make_float4(c0, s0, c1, s1));
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       if (j < nh) {
         float sv, cv;
         xyd::unit_vector<MODE>(vh[j], &sv, &cv);
-        if (hp[j] == 0) th[0][hr[j]][hcol[j]] = vh[j];     // red side-ring angles
-        cs[hp[j]][hr[j]][hcol[j]] = make_float2(cv, sv);
+        if (hp[j] == 0) {                                  // red side-ring angles
+          thr[hr[j] - 1][hcol[j] + kThOff - kCsOff] = vh[j];
+          csr[hr[j] - 1][hcol[j]] = make_float2(cv, sv);
+        } else {
+          csb[hr[j]][hcol[j]] = make_float2(cv, sv);
+        }
       }
     }
   }
   pre();
   __syncthreads();
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
   const uint32_t uL = (uint32_t)L;
-  const int c0 = 2 * lane + 4;                             // stage column of the lane's pair
+  const int c0 = 2 * lane + kCsOff;                        // unit-vector column of the lane's pair
   const int kp = k0 + 2 * lane;                            // plane column of the pair
   unsigned int n_acc = 0;
 
   // ---- red half: the tile (counted, written to dst) ----
+  float4 nbD = ld4(&csb[warp * 4 + 1][c0]);
+  float4 nbP = ld4(&csb[warp * 4 + 2][c0]);
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -267,45 +309,54 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const int r = ty + 2;
     const int q = y & 1;                                   // red: x = 2k + (y & 1)
     PairNeighbours n;
-    pair_neighbours(cs[1], r, c0, q, n);
+    float4 nbU;
+    pair_neighbours(csb, r, c0, q, nbD, nbP, nbU, n);
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
     // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
     const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const float2 t = *reinterpret_cast<const float2*>(&th[0][r][c0]);
-    const float4 o = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
+    const float2 t = *reinterpret_cast<const float2*>(&thr[r - 1][c0 + kThOff - kCsOff]);
+    const float4 o = ld4(&csr[r - 1][c0]);
     const xyd::SiteResult r0 =
         xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
     const xyd::SiteResult r1 =
         xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, a.K, a.delta);
     n_acc += (r0.accept ? 1u : 0u) + (r1.accept ? 1u : 0u);
-    *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
+    st4(&csr[r - 1][c0], make_float4(r0.c, r0.s, r1.c, r1.s));
     *reinterpret_cast<float2*>(a.dst + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
-  // 160 sites on the first five warps, one per lane: the ring takes one site
-  // update's time whichever way it is spread, and full warps issue no idle
-  // lanes (the other three warps wait at the barrier and leave their issue
-  // slots to the SM's other CTAs)
-  {
-    const int i = threadIdx.x;
-    if (i < kRing) {
-      int ty, tk;
-      if (i < kTileK) {
-        ty = -1;
-        tk = i;
-      } else if (i < 2 * kTileK) {
-        ty = kTileRows;
-        tk = i - kTileK;
-      } else {
-        ty = i - 2 * kTileK;
-        tk = ((y0 + ty) & 1) ? -1 : kTileK;                // left ring on odd rows, right on even
-      }
-      const int y = wrap_once(y0 + ty, L);
-      const int k = wrap_once(k0 + tk, W);
-      const int q = y & 1;
-      const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
-      red_ring_site<MODE>(th, cs, ty + 2, tk + 4, q, (uint32_t)y * uL + x, x, a, rk);
-    }
+  // The ring rows above and below the tile are 32 pairs each (sites x and
+  // x + 2 share a Philox block, as in the tile): warp 0 takes the row above,
+  // warp 1 the row below; warp 2 takes the 32 side sites (left ring on odd
+  // rows, right on even), one per lane.  The other warps wait at the barrier
+  // and leave their issue slots to the SM's other CTAs.
+  if (warp < 2) {
+    const int ty = warp == 0 ? -1 : kTileRows;
+    const int y = wrap_once(y0 + ty, L);
+    const int r = ty + 2;
+    const int q = y & 1;
+    PairNeighbours n;
+    float4 U;
+    pair_neighbours(csb, r, c0, q, ld4(&csb[r - 1][c0]), ld4(&csb[r][c0]), U, n);
+    const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
+    const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
+    const float2 t = *reinterpret_cast<const float2*>(&thr[r - 1][c0 + kThOff - kCsOff]);
+    const float4 o = ld4(&csr[r - 1][c0]);
+    const xyd::SiteResult r0 =
+        xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
+    const xyd::SiteResult r1 =
+        xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w.z, w.w, a.K, a.delta);
+    st4(&csr[r - 1][c0], make_float4(r0.c, r0.s, r1.c, r1.s));
+  } else if (warp == 2) {
+    const int ty = lane;
+    const int tk = ((y0 + ty) & 1) ? -1 : kTileK;          // left ring on odd rows, right on even
+    const int y = wrap_once(y0 + ty, L);
+    const int k = wrap_once(k0 + tk, W);
+    const int q = y & 1;
+    const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
+    red_ring_site<MODE>(thr, csr, csb, ty + 2, tk + kCsOff, q, (uint32_t)y * uL + x, x, a, rk);
   }
   mid();
   __syncthreads();
@@ -314,6 +365,8 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   xyd::SweepSums<RED> sums;
   sums.init();
   float* dst_blk = a.dst + plane;
+  nbD = ld4(&csr[warp * 4][c0]);                           // red stage rows r - 1, r
+  nbP = ld4(&csr[warp * 4 + 1][c0]);
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -321,12 +374,16 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const int r = ty + 2;
     const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
     PairNeighbours n;
-    pair_neighbours(cs[0], r, c0, q, n);
+    float4 nbU;
+    pair_neighbours(csr, r - 1, c0, q, nbD, nbP, nbU, n);
+    const float4 m = nbP;                                  // the red pair of the same row
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
     // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
     const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const float2 t = *reinterpret_cast<const float2*>(&th[1][r][c0]);
-    const float4 o = *reinterpret_cast<const float4*>(&cs[1][r][c0]);
+    const float2 t = *reinterpret_cast<const float2*>(&thb[r - 2][c0 - kCsOff]);
+    const float4 o = ld4(&csb[r][c0]);
     const xyd::SiteResult r0 =
         xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
     const xyd::SiteResult r1 =
@@ -335,7 +392,6 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     *reinterpret_cast<float2*>(dst_blk + (size_t)y * W + kp) = make_float2(r0.th, r1.th);
 
     // red sites with the same (y, k): their spins enter M once each
-    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     float v0[5], v1[5];
     xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
@@ -350,8 +406,10 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
                                       bx == 0 && by == 0);
 }
 
-// MINB: CTAs per SM the kernel is compiled for (3: at most 80 registers a
-// thread; 2: at most 128, more independent work in flight per warp).
+// MINB: CTAs per SM the kernel is compiled for (4: at most 64 registers a
+// thread, 32 warps per SM; 3: at most 80; 2: at most 128, more independent
+// work in flight per warp, 16 warps).  The tile's 55.1 KB of shared memory
+// let four CTAs share an SM.
 template <int MODE, int RED, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused(FusedArgs a) {
   fused_sweep_body<MODE, RED>(a, a.rk, blockIdx.x, blockIdx.y);
@@ -549,8 +607,9 @@ cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
 
 template <int MODE, int RED>
 cudaError_t launch_fused_plan(const FusedArgs& a, cudaStream_t stream) {
-  return a.minb == 2 ? launch_fused_one<MODE, RED, 2>(a, stream)
-                     : launch_fused_one<MODE, RED, 3>(a, stream);
+  return a.minb == 2   ? launch_fused_one<MODE, RED, 2>(a, stream)
+         : a.minb == 4 ? launch_fused_one<MODE, RED, 4>(a, stream)
+                       : launch_fused_one<MODE, RED, 3>(a, stream);
 }
 
 template <int MODE, int RED>
@@ -559,6 +618,8 @@ cudaError_t launch_fused_batch_one(const FusedBatchArgs& b, int n_lattices, cuda
   const dim3 grid(b.L / 2 / kTileK, b.L / kTileRows, n_lattices);
   if (b.minb == 2)
     k_sweep_fused_batch<MODE, RED, 2><<<grid, kThreads, kSmemBytes, stream>>>(b);
+  else if (b.minb == 4)
+    k_sweep_fused_batch<MODE, RED, 4><<<grid, kThreads, kSmemBytes, stream>>>(b);
   else
     k_sweep_fused_batch<MODE, RED, 3><<<grid, kThreads, kSmemBytes, stream>>>(b);
   return cudaGetLastError();
@@ -577,7 +638,8 @@ cudaError_t prepare_plan() {
 template <int MODE, int RED>
 cudaError_t prepare_one() {
   cudaError_t e = prepare_plan<MODE, RED, 3>();
-  return e == cudaSuccess ? prepare_plan<MODE, RED, 2>() : e;
+  if (e == cudaSuccess) e = prepare_plan<MODE, RED, 2>();
+  return e == cudaSuccess ? prepare_plan<MODE, RED, 4>() : e;
 }
 
 template <int MODE, int RED, int MINB>
@@ -630,7 +692,9 @@ cudaError_t persist_plan(const FusedPersistArgs& a, cudaStream_t stream) {
 
 template <int MODE, int RED>
 cudaError_t persist_dispatch(const FusedPersistArgs& a, cudaStream_t stream) {
-  return a.minb == 2 ? persist_plan<MODE, RED, 2>(a, stream) : persist_plan<MODE, RED, 3>(a, stream);
+  return a.minb == 2   ? persist_plan<MODE, RED, 2>(a, stream)
+         : a.minb == 4 ? persist_plan<MODE, RED, 4>(a, stream)
+                       : persist_plan<MODE, RED, 3>(a, stream);
 }
 
 }  // namespace
@@ -648,7 +712,7 @@ cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode) {
 
 cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,
                                      int n_lattices, cudaStream_t stream) {
-  if (!fused_supported(b.L) || n_lattices < 1 || (b.minb != 2 && b.minb != 3))
+  if (!fused_supported(b.L) || n_lattices < 1 || (b.minb < 2 || b.minb > 4))
     return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   switch (sincos_mode) {
@@ -666,7 +730,7 @@ cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const Fus
 
 cudaError_t launch_fused_sweep(int sincos_mode, int reduce_mode, const FusedArgs& a,
                                cudaStream_t stream) {
-  if (!fused_supported(a.L) || (a.minb != 2 && a.minb != 3)) return cudaErrorInvalidValue;
+  if (!fused_supported(a.L) || (a.minb < 2 || a.minb > 4)) return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   switch (sincos_mode) {
     case 0: return comp ? launch_fused_plan<0, 1>(a, stream) : launch_fused_plan<0, 0>(a, stream);
@@ -694,7 +758,7 @@ cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const Fuse
   if (!fused_supported(a.L) || a.W * 2 != a.L || a.n_sweeps < 1 ||
       a.n_sweeps > fused_persistent_max_sweeps(a.L) || !a.flags || a.counter != a.flags + fused_tiles(a.L) ||
       !a.error || a.buf[0] == a.buf[1] || a.spin_limit < 1 || a.skip_items < 0 ||
-      a.skip_items > a.n_sweeps * fused_tiles(a.L) || (a.minb != 2 && a.minb != 3))
+      a.skip_items > a.n_sweeps * fused_tiles(a.L) || (a.minb < 2 || a.minb > 4))
     return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;
   switch (sincos_mode) {

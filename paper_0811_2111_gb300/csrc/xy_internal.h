@@ -64,7 +64,7 @@ struct FusedArgs {
   uint32_t sweep;
   xy_record* rec;
   double beta;
-  int minb = 3;          // tile kernel instances per SM (2 or 3: the register budget)
+  int minb = 3;          // tile kernel instances per SM (2, 3 or 4: the register budget)
 };
 
 // Whether the fused kernel handles side L (L a positive multiple of 128).
@@ -108,7 +108,7 @@ struct FusedPersistArgs {
   long long spin_limit;  // polls before a wait gives up (fused_persistent_spin_limit())
   int skip_items;        // work items not handed out (0; > 0 only to test the
                          // failure path: their counters are then never set)
-  int minb = 3;          // resident CTAs per SM the kernel is compiled for (2 or 3)
+  int minb = 3;          // resident CTAs per SM the kernel is compiled for (2, 3 or 4)
 };
 
 // The default bound of the persistent kernel's waits, in polls (about a second).
@@ -182,7 +182,7 @@ struct FusedBatchArgs {
   float delta;
   xyd::RoundKeys rk;
   uint32_t lattice_id0;
-  int minb = 3;                 // fused tiles: CTAs per SM the kernel is compiled for (2 or 3)
+  int minb = 3;                 // fused tiles: CTAs per SM the kernel is compiled for (2, 3 or 4)
 };
 cudaError_t prepare_fused_batch(int sincos_mode, int reduce_mode);
 cudaError_t launch_fused_batch_sweep(int sincos_mode, int reduce_mode, const FusedBatchArgs& b,

@@ -235,8 +235,8 @@ def test_peak_measure_refuses_bad_arguments_before_the_device(lib):
 
 
 def test_create_refuses_a_bad_work_plan(lib):
-    """ctas_per_sm must be 0 (default), 2 or 3; refused before the device is touched."""
-    for bad in (1, 4, -1):
+    """ctas_per_sm must be 0 (default), 2, 3 or 4; refused before the device is touched."""
+    for bad in (1, 5, -1):
         ctx = C.c_void_p()
         st = lib.xy_create(C.byref(_params(L=128, ctas_per_sm=bad)), None, None, C.byref(ctx))
         assert st == X.XY_EINVAL, bad
@@ -245,11 +245,11 @@ def test_create_refuses_a_bad_work_plan(lib):
 
 
 def test_batch_create_refuses_a_bad_work_plan(lib):
-    """group_ctas in [0, 4096] and ctas_per_sm in {0, 2, 3}, checked before the device."""
+    """group_ctas in [0, 4096] and ctas_per_sm in {0, 2, 3, 4}, checked before the device."""
     Ls = (C.c_int32 * 2)(16, 16)
     betas = (C.c_double * 2)(1.0, 1.1)
     for field, bad in (("group_ctas", -1), ("group_ctas", 4097), ("ctas_per_sm", 1),
-                       ("ctas_per_sm", 4)):
+                       ("ctas_per_sm", 5)):
         p = X.xy_batch_params()
         p.n, p.L, p.beta, p.J, p.delta, p.seed = 2, Ls, betas, 1.0, 3.14159, 1
         p.sweeps_per_round = 1

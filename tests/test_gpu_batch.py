@@ -113,7 +113,8 @@ def test_batch_is_independent_of_the_work_plan():
     for target, algorithm, group, ctas in ((256, "auto", 0, 0), (1024, "auto", 0, 0),
                                            (65536, "auto", 0, 0), (2048, "two_pass", 0, 0),
                                            (256, "two_pass", 0, 0), (8192, "auto", 1, 0),
-                                           (8192, "auto", 4096, 2), (8192, "auto", 64, 2)):
+                                           (8192, "auto", 4096, 2), (8192, "auto", 64, 2),
+                                           (8192, "auto", 128, 4)):
         states, obs, n = run_batch(target=target, algorithm=algorithm, group_ctas=group,
                                    ctas_per_sm=ctas)
         for i in range(len(LS)):

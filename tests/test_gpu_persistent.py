@@ -82,14 +82,17 @@ def test_bench_launch_configuration():
 @pytest.mark.parametrize("algorithm", ["persistent", "fused"])
 @pytest.mark.parametrize("sincos,reduce", [("accurate", "exact"), ("fast", "compensated")])
 def test_work_plans_are_bit_identical(algorithm, sincos, reduce):
-    """The tile kernel compiled for 2 CTAs per SM (up to 128 registers) and for 3
-    (up to 80): the same angles, accept counts and records; L = 4096, 20 sweeps."""
-    s2, n2, o2 = _run(4096, algorithm, (20,), sincos, reduce, ctas_per_sm=2)
+    """The tile kernel compiled for 2 CTAs per SM (up to 128 registers), for 3
+    (up to 80) and for 4 (up to 64): the same angles, accept counts and records;
+    L = 4096, 20 sweeps."""
     s3, n3, o3 = _run(4096, algorithm, (20,), sincos, reduce, ctas_per_sm=3)
-    assert n2 == n3 == 20
-    assert np.array_equal(s2, s3)
-    for k in FIELDS:
-        assert np.array_equal(o2[k], o3[k]), k
+    assert n3 == 20
+    for ctas in (2, 4):
+        s, n, o = _run(4096, algorithm, (20,), sincos, reduce, ctas_per_sm=ctas)
+        assert n == 20
+        assert np.array_equal(s, s3), ctas
+        for k in FIELDS:
+            assert np.array_equal(o[k], o3[k]), (ctas, k)
 
 
 @pytest.mark.parametrize("L", [128, 256, 512, 4096])
