@@ -69,6 +69,13 @@ constexpr size_t kCsbAt = kCsrAt + kCsrBytes;
 constexpr size_t kPartAt = kCsbAt + kCsbBytes;
 constexpr size_t kCntAt = kPartAt + kPartBytes;
 constexpr size_t kSmemBytes = kCntAt + kCntBytes;
+// The persistent kernel's next-tile buffer after them: the 64 float4-group
+// rows of the staging (black stage rows 0..35, red 1..28) as raw angles,
+// copied in by cp.async while the current tile's black half runs.
+constexpr size_t kRawAt = kSmemBytes;
+constexpr size_t kRawBytes = sizeof(float) * 64 * kTileK;
+constexpr size_t kPersistSmemBytes = kRawAt + kRawBytes;
+static_assert(3 * (kPersistSmemBytes + 1024) <= 228 * 1024, "three persistent tiles must fit one SM");
 static_assert(kThbAt % 16 == 0 && kCsrAt % 16 == 0 && kCsbAt % 16 == 0 && kPartAt % 16 == 0,
               "shared-memory regions must stay 16-byte aligned");
 static_assert(4 * (kSmemBytes + 1024) <= 228 * 1024, "four tiles must fit one SM");
@@ -124,6 +131,13 @@ __device__ __forceinline__ void pair_neighbours(const CsRow* nb, int i, int c0, 
   }
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ float4 ld4(const float2* p) {
   return *reinterpret_cast<const float4*>(p);
 }
@@ -170,20 +184,31 @@ __device__ __forceinline__ void red_ring_site(ThRow* thr, CsRow* csr, const CsRo
 // and persistent kernels); both have the fields used here.  COHERENT: the
 // source was written earlier in the same launch by other CTAs (persistent
 // kernel), so it is read through L2 (ld.global.cg) rather than the
-// non-coherent path.  `pre` runs in every thread before the barrier that ends
+// non-coherent path.  PREF: the staging's float4 groups (rows 0..63 of the
+// staged 70) are not loaded here but read from the raw buffer in shared
+// memory, where the caller had each thread copy its own groups by cp.async
+// (the persistent kernel does so for the next tile while the current one runs
+// its black half).  `pre` runs in every thread before the barrier that ends
 // the staging, `mid` before the barrier between the red and the black half,
-// `end` after the tile's last store to dst and before the CTA's closing
-// barrier.
+// `post` right after that barrier, `end` after the tile's last store to dst
+// and before the CTA's closing barrier.
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
-template <int MODE, int RED, bool COHERENT = false, class Args, class PreHook = NoHook,
-          class MidHook = NoHook, class EndHook = NoHook>
+__device__ __forceinline__ unsigned char* smem_base() {
+  extern __shared__ __align__(16) unsigned char smem[];
+  return smem;
+}
+
+template <int MODE, int RED, bool COHERENT = false, bool PREF = false, class Args,
+          class PreHook = NoHook, class MidHook = NoHook, class EndHook = NoHook,
+          class PostHook = NoHook>
 __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk, int bx,
                                                  int by, const PreHook& pre = PreHook(),
                                                  const MidHook& mid = MidHook(),
-                                                 const EndHook& end = EndHook()) {
+                                                 const EndHook& end = EndHook(),
+                                                 const PostHook& post = PostHook()) {
   extern __shared__ __align__(16) unsigned char smem[];
   ThRow* thr = reinterpret_cast<ThRow*>(smem);
   TbRow* thb = reinterpret_cast<TbRow*>(smem + kThbAt);
@@ -211,14 +236,16 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const int t = (int)threadIdx.x;
     const int cg = t & 15;
     float4 v[4];
+    if (!PREF) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int rr = (t >> 4) + 16 * i;
-      const int p = rr < kSRows ? 1 : 0;
-      const int r = rr < kSRows ? rr : rr - kSRows + 1;
-      const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * cg;
-      v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(a.src + row))
-                      : __ldg(reinterpret_cast<const float4*>(a.src + row));
+      for (int i = 0; i < 4; ++i) {
+        const int rr = (t >> 4) + 16 * i;
+        const int p = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * W + k0 + 4 * cg;
+        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(a.src + row))
+                        : __ldg(reinterpret_cast<const float4*>(a.src + row));
+      }
     }
     // the tail rows 64..69 are red stage rows 29..34
     const bool has_tail = t < 192;
@@ -248,6 +275,14 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
         hcol[j] = side ? kCsOff + kTileK : kCsOff - 1;
         vh[j] = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
       }
+    }
+    if (PREF) {
+      // this thread's own float4 groups, copied in by cp.async (during the
+      // previous tile, or at this tile's start)
+      const float4* rawb = reinterpret_cast<const float4*>(smem + kRawAt);
+      cp_async_wait_all();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = rawb[((t >> 4) + 16 * i) * (kTileK / 4) + cg];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -360,6 +395,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
   }
   mid();
   __syncthreads();
+  post();
 
   // ---- black half of the tile, with the sweep sums ----
   xyd::SweepSums<RED> sums;
@@ -481,11 +517,14 @@ __device__ __forceinline__ PersistItem decode_item(int item, int ntiles, int til
 // end too).  Dynamic hand-out keeps the SMs evenly loaded as a launch per
 // sweep does, without the launch's fill and drain.  Thread 0 fetches the next
 // item at the start of a tile and decodes it before the staging barrier; the
-// last warp, idle while the first five update the red ring, looks at that
+// last warp, idle while the first three update the red ring, looks at that
 // item's nine counters before the red/black barrier, and when all were set
-// the next tile starts without waiting or a barrier.  The arithmetic of a
-// tile is fused_sweep_body's, so the result is bit for bit that of n launches
-// of k_sweep_fused.
+// every thread copies its share of the next tile's staging rows into shared
+// memory by cp.async while the black half runs (those counters' acquire
+// loads precede the barrier), and the next tile starts without waiting or a
+// barrier; otherwise the next tile waits and then issues the same copies
+// itself.  The arithmetic of a tile is fused_sweep_body's, so the result is
+// bit for bit that of n launches of k_sweep_fused.
 template <int MODE, int RED, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPersistArgs p) {
   __shared__ int s_abort;
@@ -547,7 +586,26 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
     c.sweep = p.sweep0 + (uint32_t)s;
     c.rec = p.rec + s;
     PersistItem* slot = &s_item[par ^ 1];
-    fused_sweep_body<MODE, RED, true>(
+    // this thread's float4 staging groups of item `it`, by cp.async into the
+    // raw buffer (the same rows and columns as its staging loads)
+    auto copy_groups = [&](const PersistItem& it) {
+      const int t = threadIdx.x, cg = t & 15;
+      const float* nsrc = p.buf[it.s & 1];
+      const int ny0 = it.by * kTileRows, nk0 = it.bx * kTileK;
+      const size_t plane = (size_t)p.L * (size_t)p.W;
+      float4* rawb = reinterpret_cast<float4*>(smem_base() + kRawAt);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = (t >> 4) + 16 * i;
+        const int pl = rr < kSRows ? 1 : 0;
+        const int r = rr < kSRows ? rr : rr - kSRows + 1;
+        const size_t row = pl * plane + (size_t)wrap_once(ny0 - 2 + r, p.L) * p.W + nk0 + 4 * cg;
+        cp_async16(&rawb[rr * (kTileK / 4) + cg], nsrc + row);
+      }
+      cp_async_commit();
+    };
+    if (!ready) copy_groups(cur);
+    fused_sweep_body<MODE, RED, true, true>(
         c, p.rk, bx, by,
         // before the staging barrier: the next item, decoded, to the other slot
         // (the atomic was issued before the staging loads, so it has returned)
@@ -555,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
           if (threadIdx.x == 0) *slot = decode_item(next, ntiles, tiles_x, tiles_y);
         },
         // before the red/black barrier, in the last warp (idle while the first
-        // five update the ring): one early look at the next item's nine
+        // three update the ring): one early look at the next item's nine
         // counters, so that its wait usually costs nothing.  The acquire loads'
         // latency overlaps the ring instead of holding the CTA at its closing
         // barrier.
@@ -572,6 +630,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
             const unsigned int all = __ballot_sync(0xffffffffu, ok);
             if (l == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
           }
+        },
+        NoHook(),
+        // after the red/black barrier: when the next item's counters were all
+        // seen set, every thread copies the float4 groups it will stage for it
+        // into the raw buffer (the same rows and columns as its own staging
+        // loads), so the next tile's staging reads shared memory
+        [&]() {
+          const PersistItem ni = *slot;
+          if (s_ready[par ^ 1] != 0 && ni.item < total) copy_groups(ni);
         });
     if (threadIdx.x == kThreads - 64) {
       // a warp other than the pollers' publishes the tile: the closing barrier
@@ -647,7 +714,7 @@ cudaError_t launch_persist_one(const FusedPersistArgs& a, int grid, cudaStream_t
   void* args[] = {const_cast<FusedPersistArgs*>(&a)};
   return cudaLaunchCooperativeKernel(
       reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED, MINB>), dim3(grid),
-      dim3(kThreads), args, kSmemBytes, stream);
+      dim3(kThreads), args, kPersistSmemBytes, stream);
 }
 
 template <int MODE, int RED, int MINB>
@@ -658,12 +725,13 @@ cudaError_t persist_grid_one(int L, int* grid) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || per_sm[dev] == 0) {
     auto fn = k_sweep_fused_persist<MODE, RED, MINB>;
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPersistSmemBytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int n = 0;
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, kSmemBytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, kPersistSmemBytes);
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorCooperativeLaunchTooLarge;
     if (dev >= 0 && dev < 64) per_sm[dev] = n;
