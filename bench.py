@@ -521,16 +521,22 @@ def measure_table1_sizes(dev, sincos, cpu_seconds=1.0):
 # Hybrid Monte Carlo (the paper's own algorithm)
 # ---------------------------------------------------------------------------
 
-HMC_BYTES_PER_SITE_STEP = 16.0   # leap-frog step kernel: 4 B angle + 4 B momentum read and written
+# The full kick-drift steps run two per launch (k_hmc_tile2): each launch reads
+# and writes the angle and the momentum of every site once, 16 B per site for
+# two steps.
+HMC_BYTES_PER_SITE_STEP = 8.0
+# Algorithmic thread-instructions of one site-step: the new angle's unit
+# vector (25 accurate, 3 SFU, 27 libm, as for a Metropolis update), the two
+# neighbour sums 6, the force 3, kick and drift 2, the wrap into [0, 2 pi) 8.
+HMC_ALG_INSTR_PER_SITE_STEP = {"accurate": 44.0, "fast": 22.0, "libm": 46.0}
+# DRAM bytes of one L = 4096 two-step launch (ncu, caches flushed before the
+# capture: 134.4 MB read, 90.0 MB written; profiles/hmc_tile2_L4096_full.md),
+# per step.
+HMC_DRAM_BYTES_PER_STEP = 224.3e6 / 2
 
 
-# DRAM bytes of one L = 4096 HMC step launch with the caches as the program
-# leaves them (ncu --cache-control none, four launches: 79.6-84.2 MB read,
-# 110.8-112.3 MB written; profiles/hmc_step_tma_L4096_full.md).
-HMC_DRAM_BYTES_PER_STEP = 191.5e6
-
-
-def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
+def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0, issue_per_sm_clk=None,
+                clk_mhz=2070.0):
     """Leap-frog site-steps/s of HMC at L = 4096, beta = 1.12 (trajectories of 80
     steps of 0.0125, from a state thermalised by 2000 Metropolis sweeps and 30
     HMC trajectories), the step kernel's duration and HBM roofline, and the FP64
@@ -563,18 +569,21 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         o = h.observables(WL.HMC_THERM, trajectories)
-        # the step kernel alone: integrate(2) - integrate(1) = one step launch
+        # the step kernel alone: integrate(21) - integrate(1) = ten two-step launches
         reps = 20
         t = {}
-        for n in (1, 2):
+        for n in (1, 21):
             e0.record(h.stream)
             for _ in range(reps):
                 h.integrate(n)
             e1.record(h.stream)
             e1.synchronize()
             t[n] = e0.elapsed_time(e1) / reps
-    step_ms = t[2] - t[1]
+    step_ms = (t[21] - t[1]) / 20
     achieved = HMC_BYTES_PER_SITE_STEP * N / (step_ms * 1e-3) / 1e9
+    per_clk = issue_per_sm_clk or SMSP_PER_SM * LANES
+    alu_peak = SMS * per_clk * clk_mhz * 1e6 / 1e12
+    alu_achieved = HMC_ALG_INSTR_PER_SITE_STEP[sincos] * N / (step_ms * 1e-3) / 1e12
     hbm, peak_kind = measured_peaks()
     # FP64 oracle leap-frog on one core (L = 512 sample)
     Ls = 512
@@ -596,17 +605,18 @@ def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0):
             "trajectories_per_s": trajectories / (ms * 1e-3), "ms_per_trajectory": ms / trajectories,
             "begin_final_accept_ms": t[1], "acceptance": float(o["accepted"].mean()),
             "mean_exp_minus_dH": float(np.exp(-o["dH"]).mean()), "e": float(o["e"].mean()),
-            "roofline": {"kernel": "k_hmc_step_tma (one leap-frog step per launch, TMA-staged)",
-                         "bound": "hbm",
-                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / hbm,
-                         "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP, "ms_per_launch": step_ms,
-                         # consecutive steps walk the tiles in opposite orders, so a step
-                         # starts on what the last one left in L2: DRAM moves less than the
-                         # algorithmic bytes (ncu, profiles/hmc_step_tma_L4096_full.md)
-                         "dram_bytes_per_step": HMC_DRAM_BYTES_PER_STEP,
-                         "dram_achieved": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9,
-                         "dram_frac": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9 / hbm},
+            "roofline": {"kernel": "k_hmc_tile2 (two leap-frog steps per launch)",
+                         "bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "Tinstr/s", "frac": alu_achieved / alu_peak,
+                         "peak_kind": "measured" if issue_per_sm_clk else "nominal",
+                         "algorithmic_instr_per_site_step": HMC_ALG_INSTR_PER_SITE_STEP[sincos],
+                         "ms_per_step": step_ms,
+                         "hbm": {"achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                                 "unit": "GB/s", "frac": achieved / hbm,
+                                 "bytes_per_site_step": HMC_BYTES_PER_SITE_STEP,
+                                 "dram_bytes_per_step": HMC_DRAM_BYTES_PER_STEP,
+                                 "dram_achieved": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9,
+                                 "dram_frac": HMC_DRAM_BYTES_PER_STEP / (step_ms * 1e-3) / 1e9 / hbm}},
             "cpu_baseline": {"value": cpu, "unit": "site-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"FP64 leap-frog, L={Ls}, {n} steps"},
             "gain_vs_oracle_1core": value / cpu}
@@ -852,7 +862,8 @@ def run_ours(args):
                  "differentiation": measure_differentiation(dev, args.sincos),
                  "precision": measure_precision(dev),
                  "table1_sizes": measure_table1_sizes(dev, args.sincos),
-                 "hmc": measure_hmc(dev, args.sincos),
+                 "hmc": measure_hmc(dev, args.sincos, issue_per_sm_clk=issue_clk,
+                                    clk_mhz=clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0),
                  "quad": measure_quad(dev, args.sincos)}
         # the same issue-slot roofline as the main line, over a whole run of each
         # Metropolis workload (launch gaps included: a lower bound on the kernels')

@@ -826,137 +826,260 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
 
 // ---------------------------------------------------------------------------
 // Two full kick-drift steps per launch (temporal blocking).  A CTA of 256
-// threads owns 32 x 128 sites.  It stages the unit vectors of the tile plus a
-// halo of two (36 x 132) and the angles and momenta of the tile plus a halo of
-// one (34 x 130) in shared memory, runs the first step over tile + halo one,
-// then the second over the tile, and writes angles and momenta once: 8 bytes
-// read and 8 written per site for two steps (halo re-reads aside; the halo
-// rows are shared with the neighbouring tiles through L2).  The halo
-// steps recompute what the neighbouring CTAs compute, from the same inputs and
-// with the same arithmetic, so every copy agrees bit for bit.  Momenta are
-// read from one buffer and written to another (the halo reads old values).
+// threads owns 32 rows x 128 columns, a thread 4 rows x 4 columns in
+// registers as in k_hmc_tile.  The first step also updates the ring around
+// the tile (rows -1 and 32, columns -1 and 128: 320 sites that belong to the
+// neighbouring tiles, recomputed from the same inputs with the same
+// arithmetic, so every copy agrees bit for bit); the second updates the tile
+// and writes angles and momenta once: 8 bytes read and 8 written per site for
+// two steps.  Shared memory holds one frame of unit vectors, rows -2 .. 33 and
+// columns -4 .. 131 of the tile (cos and sin planes), of which only what
+// crosses a warp is written: the halo of two (rows -2 and 33, columns -2 and
+// 129, the four ring corners), the ring, each warp's first and last row and
+// the tile's first and last column; after the first step the ring and the
+// warps' edge rows are overwritten with their new values.  Horizontal
+// neighbours inside a warp's rows come by shuffle.  Momenta are read from one
+// buffer and written to another (the ring reads the neighbours' old momenta).
 // ---------------------------------------------------------------------------
 constexpr int kP2Rows = 32;
 constexpr int kP2Cols = 128;
 constexpr int kP2Threads = 256;
-constexpr int kR2Rows = kP2Rows + 4, kR2Cols = kP2Cols + 4;    // halo two
-constexpr int kR1Rows = kP2Rows + 2, kR1Cols = kP2Cols + 2;    // halo one
-constexpr int kR2Sites = kR2Rows * kR2Cols;
-constexpr int kR1Sites = kR1Rows * kR1Cols;
-constexpr int kThIter = (kR2Sites + kP2Threads - 1) / kP2Threads;
-constexpr int kPIter = (kR1Sites + kP2Threads - 1) / kP2Threads;
-constexpr int kAIter = (kR1Sites + kP2Threads - 1) / kP2Threads;
-constexpr int kBIter = kP2Rows * kP2Cols / kP2Threads;
-constexpr size_t kCsBytes = sizeof(float2) * kR2Rows * kR2Cols;
-constexpr size_t kR1Bytes = sizeof(float) * kR1Rows * kR1Cols;
-constexpr size_t kP2Smem = kCsBytes + 2 * kR1Bytes;
+constexpr int kP2Warps = kP2Threads / 32;
+constexpr int kP2Band = kP2Rows / kP2Warps;                  // 4 rows per warp
+constexpr int kFrRows = kP2Rows + 4;                         // tile rows -2 .. 33
+constexpr int kFrCols = kP2Cols + 8;                         // tile columns -4 .. 131
+constexpr size_t kP2Smem = sizeof(float) * 2 * kFrRows * kFrCols;
 
 __device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// One leap-frog step of a site: kick by a F(unit vector, neighbour sums),
+// drift by eps p, wrap (the per-site arithmetic of every HMC kernel).
+__device__ __forceinline__ void hmc_site_step(float c, float s, float Sc, float Ss, float K,
+                                              float a, float eps, float& p, float& t) {
+  p = __fmaf_rn(a, hmc_force(c, s, Sc, Ss, K), p);
+  t = hmc_wrap(__fmaf_rn(eps, p, t));
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kP2Threads, 3) k_hmc_tile2(HmcArgs a) {
+__global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float2 (*cs)[kR2Cols] = reinterpret_cast<float2 (*)[kR2Cols]>(smem);
-  float (*th)[kR1Cols] = reinterpret_cast<float (*)[kR1Cols]>(smem + kCsBytes);
-  float (*pm)[kR1Cols] = reinterpret_cast<float (*)[kR1Cols]>(smem + kCsBytes + kR1Bytes);
+  float (*fc)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem);
+  float (*fs)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem + sizeof(float) * kFrRows * kFrCols);
 
   const int L = a.L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = blockIdx.x * kP2Cols, y0 = blockIdx.y * kP2Rows;
-  const int tid = threadIdx.x;
   int src, dst;
   hmc_buffers(a, a.ctl->cur, &src, &dst);
   const float* __restrict__ th_src = hmc_buf(a, src);
 
-  // ---- staging: one site per thread and item, consecutive lanes on
-  // consecutive columns (coalesced loads, conflict-free shared stores);
-  // angles of tile + 2 -> unit vectors (and the angles of tile + 1), momenta
-  // of tile + 1.  All loads of a thread are issued before its sincos.
-  float tv[kThIter], pv[kPIter];
+  // ---- loads: own 4 x 4 block (angles and momenta), one site of the ring's
+  // top or bottom row (threads 0..255), one of its side columns (0..63), one
+  // halo-two site of rows -2 / 33 (0..255), of columns -2 / 129 (64..127) or a
+  // ring corner (128..131)
+  const int xb = x0 + 4 * lane;
+  const int rb = kP2Band * warp;                             // first tile row of the band
+  float4 t4[kP2Band], p4[kP2Band];
 #pragma unroll
-  for (int k = 0; k < kThIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR2Sites) {
-      const int row = i / kR2Cols, c = i - row * kR2Cols;
-      const int gy = wrap_near(y0 - 2 + row, L), gx = wrap_near(x0 - 2 + c, L);
-      tv[k] = th_src[(size_t)gy * L + gx];
+  for (int r = 0; r < kP2Band; ++r) {
+    const size_t g = (size_t)(y0 + rb + r) * L + xb;
+    t4[r] = *reinterpret_cast<const float4*>(th_src + g);
+    p4[r] = *reinterpret_cast<const float4*>(a.p_in + g);
+  }
+  // ring site A: row -1 (tid < 128) or 32, column tid & 127
+  const int ay = tid < kP2Cols ? -1 : kP2Rows, ax = tid & (kP2Cols - 1);
+  const size_t ga = (size_t)wrap_near(y0 + ay, L) * L + (x0 + ax);
+  float ta = th_src[ga], pa = a.p_in[ga];
+  // ring site B: column -1 (tid < 32) or 128, row tid & 31
+  const bool hasb = tid < 2 * kP2Rows;
+  const int bx = tid < kP2Rows ? -1 : kP2Cols, by = tid & (kP2Rows - 1);
+  float tb = 0.f, pb = 0.f;
+  if (hasb) {
+    const size_t gb = (size_t)(y0 + by) * L + wrap_near(x0 + bx, L);
+    tb = th_src[gb];
+    pb = a.p_in[gb];
+  }
+  // halo-two site H: rows -2 / 33; G: columns -2 / 129 or a corner
+  const int hy = tid < kP2Cols ? -2 : kP2Rows + 1;
+  const float th_h = th_src[(size_t)wrap_near(y0 + hy, L) * L + (x0 + ax)];
+  const bool hasg = tid >= 64 && tid < 132;
+  int gy = 0, gx = 0;
+  float th_g = 0.f;
+  if (hasg) {
+    if (tid < 128) {
+      gx = (tid - 64) < kP2Rows ? -2 : kP2Cols + 1;
+      gy = (tid - 64) & (kP2Rows - 1);
+    } else {
+      gy = (tid & 2) ? kP2Rows : -1;
+      gx = (tid & 1) ? kP2Cols : -1;
+    }
+    th_g = th_src[(size_t)wrap_near(y0 + gy, L) * L + wrap_near(x0 + gx, L)];
+  }
+
+  // ---- unit vectors of the old state; what crosses a warp goes to the frame
+  float c[kP2Band][4], s[kP2Band][4];
+#pragma unroll
+  for (int r = 0; r < kP2Band; ++r) {
+    xyd::unit_vector<MODE>(t4[r].x, &s[r][0], &c[r][0]);
+    xyd::unit_vector<MODE>(t4[r].y, &s[r][1], &c[r][1]);
+    xyd::unit_vector<MODE>(t4[r].z, &s[r][2], &c[r][2]);
+    xyd::unit_vector<MODE>(t4[r].w, &s[r][3], &c[r][3]);
+  }
+  float ca, sa, cb = 0.f, sb = 0.f;
+  xyd::unit_vector<MODE>(ta, &sa, &ca);
+  if (hasb) xyd::unit_vector<MODE>(tb, &sb, &cb);
+  {
+    float hs, hc;
+    xyd::unit_vector<MODE>(th_h, &hs, &hc);
+    fc[hy + 2][ax + 4] = hc;
+    fs[hy + 2][ax + 4] = hs;
+    if (hasg) {
+      xyd::unit_vector<MODE>(th_g, &hs, &hc);
+      fc[gy + 2][gx + 4] = hc;
+      fs[gy + 2][gx + 4] = hs;
     }
   }
-#pragma unroll
-  for (int k = 0; k < kPIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR1Sites) {
-      const int row = i / kR1Cols, c = i - row * kR1Cols;
-      const int gy = wrap_near(y0 - 1 + row, L), gx = wrap_near(x0 - 1 + c, L);
-      pv[k] = a.p_in[(size_t)gy * L + gx];
-    }
+  fc[ay + 2][ax + 4] = ca;
+  fs[ay + 2][ax + 4] = sa;
+  if (hasb) {
+    fc[by + 2][bx + 4] = cb;
+    fs[by + 2][bx + 4] = sb;
   }
+  // the band's first and last row, and the tile's first and last column
+  *reinterpret_cast<float4*>(&fc[rb + 2][4 * lane + 4]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
+  *reinterpret_cast<float4*>(&fs[rb + 2][4 * lane + 4]) = make_float4(s[0][0], s[0][1], s[0][2], s[0][3]);
+  *reinterpret_cast<float4*>(&fc[rb + kP2Band + 1][4 * lane + 4]) =
+      make_float4(c[kP2Band - 1][0], c[kP2Band - 1][1], c[kP2Band - 1][2], c[kP2Band - 1][3]);
+  *reinterpret_cast<float4*>(&fs[rb + kP2Band + 1][4 * lane + 4]) =
+      make_float4(s[kP2Band - 1][0], s[kP2Band - 1][1], s[kP2Band - 1][2], s[kP2Band - 1][3]);
+  if (lane == 0 || lane == 31) {
+    const int q = lane == 0 ? 4 : kP2Cols + 3;             // tile column 0 or 127
 #pragma unroll
-  for (int k = 0; k < kThIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR2Sites) {
-      const int row = i / kR2Cols, c = i - row * kR2Cols;
-      float sn, cn;
-      xyd::unit_vector<MODE>(tv[k], &sn, &cn);
-      cs[row][c] = make_float2(cn, sn);
-      if (row >= 1 && row <= kR1Rows && c >= 1 && c <= kR1Cols) th[row - 1][c - 1] = tv[k];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kPIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR1Sites) {
-      const int row = i / kR1Cols, c = i - row * kR1Cols;
-      pm[row][c] = pv[k];
+    for (int r = 1; r < kP2Band - 1; ++r) {
+      fc[rb + r + 2][q] = lane == 0 ? c[r][0] : c[r][3];
+      fs[rb + r + 2][q] = lane == 0 ? s[r][0] : s[r][3];
     }
   }
   __syncthreads();
 
-  // ---- first step over tile + 1 --------------------------------------------
-  float2 nv[kAIter];
-#pragma unroll
-  for (int k = 0; k < kAIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR1Sites) {
-      const int r = i / kR1Cols, c = i - r * kR1Cols;   // halo-one frame
-      const float2 o = cs[r + 1][c + 1], l = cs[r + 1][c], rt = cs[r + 1][c + 2];
-      const float2 dn = cs[r][c + 1], up = cs[r + 2][c + 1];
-      const float Sc = xyd::nb_sum(l.x, rt.x, dn.x, up.x);
-      const float Ss = xyd::nb_sum(l.y, rt.y, dn.y, up.y);
-      const float p = __fmaf_rn(a.a, hmc_force(o.x, o.y, Sc, Ss, a.K), pm[r][c]);
-      const float t = hmc_wrap(__fmaf_rn(a.eps, p, th[r][c]));
-      pm[r][c] = p;
-      th[r][c] = t;
-      float sn, cn;
-      xyd::unit_vector<MODE>(t, &sn, &cn);
-      nv[k] = make_float2(cn, sn);
-    }
+  // ---- first step: the ring sites (from the frame), then the tile --------
+  const float K = a.K, ka = a.a, eps = a.eps;
+  {
+    const int r = ay + 2, q = ax + 4;
+    const float Sc = xyd::nb_sum(fc[r][q - 1], fc[r][q + 1], fc[r - 1][q], fc[r + 1][q]);
+    const float Ss = xyd::nb_sum(fs[r][q - 1], fs[r][q + 1], fs[r - 1][q], fs[r + 1][q]);
+    hmc_site_step(ca, sa, Sc, Ss, K, ka, eps, pa, ta);
   }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kAIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    if (i < kR1Sites) {
-      const int r = i / kR1Cols, c = i - r * kR1Cols;
-      cs[r + 1][c + 1] = nv[k];
-    }
+  if (hasb) {
+    const int r = by + 2, q = bx + 4;
+    const float Sc = xyd::nb_sum(fc[r][q - 1], fc[r][q + 1], fc[r - 1][q], fc[r + 1][q]);
+    const float Ss = xyd::nb_sum(fs[r][q - 1], fs[r][q + 1], fs[r - 1][q], fs[r + 1][q]);
+    hmc_site_step(cb, sb, Sc, Ss, K, ka, eps, pb, tb);
   }
+  // the ring's new unit vectors (its momenta and angles are not needed again)
+  xyd::unit_vector<MODE>(ta, &sa, &ca);
+  if (hasb) xyd::unit_vector<MODE>(tb, &sb, &cb);
+  // vertical neighbours of the band: the row below its first and above its last
+  float4 cdn = *reinterpret_cast<const float4*>(&fc[rb + 1][4 * lane + 4]);
+  float4 sdn = *reinterpret_cast<const float4*>(&fs[rb + 1][4 * lane + 4]);
+  float4 cup = *reinterpret_cast<const float4*>(&fc[rb + kP2Band + 2][4 * lane + 4]);
+  float4 sup = *reinterpret_cast<const float4*>(&fs[rb + kP2Band + 2][4 * lane + 4]);
+#pragma unroll
+  for (int r = 0; r < kP2Band; ++r) {
+    float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
+    float sl = __shfl_up_sync(0xffffffffu, s[r][3], 1);
+    float cr = __shfl_down_sync(0xffffffffu, c[r][0], 1);
+    float sr = __shfl_down_sync(0xffffffffu, s[r][0], 1);
+    if (lane == 0) {
+      cl = fc[rb + r + 2][3];
+      sl = fs[rb + r + 2][3];
+    }
+    if (lane == 31) {
+      cr = fc[rb + r + 2][kP2Cols + 4];
+      sr = fs[rb + r + 2][kP2Cols + 4];
+    }
+    const float pr[4] = {p4[r].x, p4[r].y, p4[r].z, p4[r].w};
+    const float tr[4] = {t4[r].x, t4[r].y, t4[r].z, t4[r].w};
+    const float cd[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sd[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
+    const float cu[4] = {cup.x, cup.y, cup.z, cup.w}, su[4] = {sup.x, sup.y, sup.z, sup.w};
+    float po[4], to[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float nlc = j == 0 ? cl : c[r][j - 1], nls = j == 0 ? sl : s[r][j - 1];
+      const float nrc = j == 3 ? cr : c[r][j + 1], nrs = j == 3 ? sr : s[r][j + 1];
+      const float ndc = r == 0 ? cd[j] : c[r - 1][j], nds = r == 0 ? sd[j] : s[r - 1][j];
+      const float nuc = r == kP2Band - 1 ? cu[j] : c[r + 1][j];
+      const float nus = r == kP2Band - 1 ? su[j] : s[r + 1][j];
+      float p = pr[j], t = tr[j];
+      hmc_site_step(c[r][j], s[r][j], xyd::nb_sum(nlc, nrc, ndc, nuc),
+                    xyd::nb_sum(nls, nrs, nds, nus), K, ka, eps, p, t);
+      po[j] = p;
+      to[j] = t;
+    }
+    p4[r] = make_float4(po[0], po[1], po[2], po[3]);
+    t4[r] = make_float4(to[0], to[1], to[2], to[3]);
+  }
+  // new unit vectors (the old ones are no longer read by this thread)
+#pragma unroll
+  for (int r = 0; r < kP2Band; ++r) {
+    xyd::unit_vector<MODE>(t4[r].x, &s[r][0], &c[r][0]);
+    xyd::unit_vector<MODE>(t4[r].y, &s[r][1], &c[r][1]);
+    xyd::unit_vector<MODE>(t4[r].z, &s[r][2], &c[r][2]);
+    xyd::unit_vector<MODE>(t4[r].w, &s[r][3], &c[r][3]);
+  }
+  __syncthreads();   // every old frame value has been read
+  fc[ay + 2][ax + 4] = ca;
+  fs[ay + 2][ax + 4] = sa;
+  if (hasb) {
+    fc[by + 2][bx + 4] = cb;
+    fs[by + 2][bx + 4] = sb;
+  }
+  *reinterpret_cast<float4*>(&fc[rb + 2][4 * lane + 4]) = make_float4(c[0][0], c[0][1], c[0][2], c[0][3]);
+  *reinterpret_cast<float4*>(&fs[rb + 2][4 * lane + 4]) = make_float4(s[0][0], s[0][1], s[0][2], s[0][3]);
+  *reinterpret_cast<float4*>(&fc[rb + kP2Band + 1][4 * lane + 4]) =
+      make_float4(c[kP2Band - 1][0], c[kP2Band - 1][1], c[kP2Band - 1][2], c[kP2Band - 1][3]);
+  *reinterpret_cast<float4*>(&fs[rb + kP2Band + 1][4 * lane + 4]) =
+      make_float4(s[kP2Band - 1][0], s[kP2Band - 1][1], s[kP2Band - 1][2], s[kP2Band - 1][3]);
   __syncthreads();
 
-  // ---- second step over the tile, written out ---------------------------
-  float* __restrict__ thd = hmc_buf(a, dst);
-#pragma unroll 4
-  for (int k = 0; k < kBIter; ++k) {
-    const int i = tid + k * kP2Threads;
-    const int r = i / kP2Cols, c = i - r * kP2Cols;      // tile frame
-    const float2 o = cs[r + 2][c + 2], l = cs[r + 2][c + 1], rt = cs[r + 2][c + 3];
-    const float2 dn = cs[r + 1][c + 2], up = cs[r + 3][c + 2];
-    const float Sc = xyd::nb_sum(l.x, rt.x, dn.x, up.x);
-    const float Ss = xyd::nb_sum(l.y, rt.y, dn.y, up.y);
-    const float p = __fmaf_rn(a.a, hmc_force(o.x, o.y, Sc, Ss, a.K), pm[r + 1][c + 1]);
-    const float t = hmc_wrap(__fmaf_rn(a.eps, p, th[r + 1][c + 1]));
-    const size_t g = (size_t)(y0 + r) * L + x0 + c;
-    thd[g] = t;
-    a.p_out[g] = p;
+  // ---- second step: the tile, written out ----------------------------------
+  cdn = *reinterpret_cast<const float4*>(&fc[rb + 1][4 * lane + 4]);
+  sdn = *reinterpret_cast<const float4*>(&fs[rb + 1][4 * lane + 4]);
+  cup = *reinterpret_cast<const float4*>(&fc[rb + kP2Band + 2][4 * lane + 4]);
+  sup = *reinterpret_cast<const float4*>(&fs[rb + kP2Band + 2][4 * lane + 4]);
+  float* __restrict__ th_dst = hmc_buf(a, dst);
+#pragma unroll
+  for (int r = 0; r < kP2Band; ++r) {
+    float cl = __shfl_up_sync(0xffffffffu, c[r][3], 1);
+    float sl = __shfl_up_sync(0xffffffffu, s[r][3], 1);
+    float cr = __shfl_down_sync(0xffffffffu, c[r][0], 1);
+    float sr = __shfl_down_sync(0xffffffffu, s[r][0], 1);
+    if (lane == 0) {
+      cl = fc[rb + r + 2][3];
+      sl = fs[rb + r + 2][3];
+    }
+    if (lane == 31) {
+      cr = fc[rb + r + 2][kP2Cols + 4];
+      sr = fs[rb + r + 2][kP2Cols + 4];
+    }
+    const float cd[4] = {cdn.x, cdn.y, cdn.z, cdn.w}, sd[4] = {sdn.x, sdn.y, sdn.z, sdn.w};
+    const float cu[4] = {cup.x, cup.y, cup.z, cup.w}, su[4] = {sup.x, sup.y, sup.z, sup.w};
+    float po[4], to[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float nlc = j == 0 ? cl : c[r][j - 1], nls = j == 0 ? sl : s[r][j - 1];
+      const float nrc = j == 3 ? cr : c[r][j + 1], nrs = j == 3 ? sr : s[r][j + 1];
+      const float ndc = r == 0 ? cd[j] : c[r - 1][j], nds = r == 0 ? sd[j] : s[r - 1][j];
+      const float nuc = r == kP2Band - 1 ? cu[j] : c[r + 1][j];
+      const float nus = r == kP2Band - 1 ? su[j] : s[r + 1][j];
+      po[j] = (&p4[r].x)[j];
+      to[j] = (&t4[r].x)[j];
+      hmc_site_step(c[r][j], s[r][j], xyd::nb_sum(nlc, nrc, ndc, nuc),
+                    xyd::nb_sum(nls, nrs, nds, nus), K, ka, eps, po[j], to[j]);
+    }
+    const size_t g = (size_t)(y0 + rb + r) * L + xb;
+    *reinterpret_cast<float4*>(a.p_out + g) = make_float4(po[0], po[1], po[2], po[3]);
+    *reinterpret_cast<float4*>(th_dst + g) = make_float4(to[0], to[1], to[2], to[3]);
   }
 }
 

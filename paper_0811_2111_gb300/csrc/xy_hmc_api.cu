@@ -59,6 +59,7 @@ struct xy_hmc {
   bool use_persist;                  // a trajectory's steps in one cooperative TMA launch
   unsigned int* d_tiles;             // its per-tile step counters
   bool use_cluster;                  // whole trajectories in one cluster launch
+  bool use_pairs;                    // full steps two per launch (k_hmc_tile2)
   int tma_rows;                      // tile (and box) rows of the TMA step kernel: 32 or 16
   int tma_ctas;                      // persistent grid of the TMA step kernel
   uint32_t magic;
@@ -218,7 +219,7 @@ xyk::HmcArgs args_of(const xy_hmc* h) {
   a.tiled = h->p.kernel == XY_HMC_KERNEL_TILED || h->p.kernel == XY_HMC_KERNEL_TILED2 ||
             h->p.kernel == XY_HMC_KERNEL_TILED_TMA || h->p.kernel == XY_HMC_KERNEL_PERSISTENT ||
             (h->p.kernel == XY_HMC_KERNEL_AUTO && xyk::hmc_tiled_ok(h->p.L));
-  a.pairs = h->p.kernel == XY_HMC_KERNEL_TILED2;
+  a.pairs = h->use_pairs ? 1 : 0;
   return a;
 }
 
@@ -269,8 +270,12 @@ cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cuda
     } else {
       a.p_in = pcur;
       a.p_out = pcur;
-      e = h->use_tma ? xyk::launch_hmc_step_tma(m, a, h->maps, h->tma_rows, h->tma_ctas, s)
-                     : xyk::launch_hmc(xyk::kHmcStep, m, a, s);
+      // the TMA kernel's momentum tensor map is of d_p: after an odd number
+      // of two-step launches the momenta live in d_p2, and the plain tiled
+      // step takes the remaining single step
+      e = h->use_tma && pcur == h->d_p
+              ? xyk::launch_hmc_step_tma(m, a, h->maps, h->tma_rows, h->tma_ctas, s)
+              : xyk::launch_hmc(xyk::kHmcStep, m, a, s);
       left -= 1;
     }
     off = 3 - off;
@@ -410,6 +415,11 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
   // 128, 256); below that the per-launch cost of any kernel dominates
   h->use_cluster = p->kernel == XY_HMC_KERNEL_CLUSTER ||
                    (p->kernel == XY_HMC_KERNEL_AUTO && (p->L == 128 || p->L == 256));
+  // AUTO: full steps two per launch wherever the tiled kernels run (measured
+  // faster than one TMA-fed step per launch at L = 512 ... 4096); the odd
+  // step of a trajectory runs on the TMA kernel
+  h->use_pairs = p->kernel == XY_HMC_KERNEL_TILED2 ||
+                 (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster && xyk::hmc_tiled_ok(p->L));
   const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA || p->kernel == XY_HMC_KERNEL_PERSISTENT ||
                         (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster &&
                          xyk::hmc_tiled_ok(p->L));

@@ -144,6 +144,31 @@ def test_kernels_are_bit_identical(L, n_md):
         assert a[5] == b[5], name
 
 
+@pytest.mark.parametrize("L,n_md", [(512, 4), (512, 5), (1024, 8), (1024, 3)])
+def test_auto_kernel_equals_one_step_launches(L, n_md):
+    """AUTO at sides the tiled kernels take: the full steps two per launch
+    (momenta ping-ponged between two buffers) with an odd remaining step on
+    the TMA or the plain tiled kernel, against one tiled launch per step:
+    angles, momenta, records and sums bit for bit, over trajectories with an
+    even and an odd number of full steps and a plain integration."""
+    out = {}
+    for kernel in ("tiled", "auto"):
+        with HMC(L, 1.1, 17, 0.5 / n_md, n_md, kernel=kernel, lattice_id=3) as h:
+            h.run(5)
+            th, p, _ = h.state()
+            o = h.observables()
+            h.integrate(n_md + 1)
+            th2, p2, _ = h.state()
+            out[kernel] = (th, p, o, th2, p2, h.last_sums())
+    a, b = out["auto"], out["tiled"]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k in ("C", "Ix", "Iy", "Mx", "My", "dH", "accepted"):
+        assert np.array_equal(a[2][k], b[2][k]), k
+    assert np.all(np.isfinite(a[2]["dH"]))
+    assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4])
+    assert a[5] == b[5]
+
+
 @pytest.mark.parametrize("L,eps,n_md", [(8, 0.2, 5), (32, 0.1, 10), (128, 0.05, 12)])
 def test_trajectories_match_oracle_step_by_step(L, eps, n_md):
     """Each trajectory from the GPU's FP32 state: dH, decision and final state."""
