@@ -223,6 +223,91 @@ __device__ __forceinline__ void pair_nb(const CsArr& nb, int r, int c0, int q, P
   }
 }
 
+// Stage both planes of the tile (bx, by) as (angle, cos, sin): the black
+// plane's 36 rows (stage rows 0..35), then the red plane's 34 (stage rows
+// 1..34), 16 float4 (one site, four replicas) per row, plus the halo site on
+// each side of stage rows 1..34 of both planes (136 float4).  Thread t takes
+// the float4 column group t & 15 of staged rows (t >> 4) + 16 i, i = 0..3
+// (rows 0..63), then threads 0..95 one float4 of rows 64..69 and threads
+// 96..231 one halo site: at most 5 float4 (20 unit vectors) per thread
+// against a mean of 19.6.  Every load is issued before the first unit vector.
+// Angles are kept only where the tile reads them: the red rows (with their
+// halo sites) and the black tile rows 2..33.
+template <int MODE, bool COHERENT>
+__device__ __forceinline__ void quad_stage(const float* src, ThArr* th, CsArr* cs, int y0, int f0,
+                                           int ks0, int L, int W, int F, size_t plane) {
+  const int t = threadIdx.x, g = t & 15;
+  auto ld = [&](size_t at) {
+    return COHERENT ? __ldcg(reinterpret_cast<const float4*>(src + at))
+                    : __ldg(reinterpret_cast<const float4*>(src + at));
+  };
+  float4 v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = (t >> 4) + 16 * i;
+    const int p = rr < kSRows ? 1 : 0;
+    const int r = rr < kSRows ? rr : rr - kSRows + 1;
+    v[i] = ld(p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g);
+  }
+  const bool has_tail = t < 96;                            // rows 64..69: red stage rows 29..34
+  const int tail_r = 29 + (t >> 4);
+  float4 vt = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (has_tail) vt = ld((size_t)wrap_once(y0 - 2 + tail_r, L) * F + f0 + 4 * g);
+  const bool has_halo = t >= 96 && t < 96 + 4 * (kSRows - 2);
+  const int h = t - 96;                                    // plane h / 68, stage row 1 + (h % 68) / 2
+  const int hp = h >= 2 * (kSRows - 2) ? 1 : 0;
+  const int hrem = h - hp * 2 * (kSRows - 2);
+  const int hr = 1 + (hrem >> 1), hside = hrem & 1;
+  float4 vh = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (has_halo) {
+    const int ks = hside ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
+    vh = ld(hp * plane + (size_t)wrap_once(y0 - 2 + hr, L) * F + 4 * (size_t)ks);
+  }
+  auto put = [&](int p, int r, int col, float4 a, bool keep_angles) {
+    float s0, c0, s1, c1, s2, c2, s3, c3;
+    xyd::unit_vector<MODE>(a.x, &s0, &c0);
+    xyd::unit_vector<MODE>(a.y, &s1, &c1);
+    xyd::unit_vector<MODE>(a.z, &s2, &c2);
+    xyd::unit_vector<MODE>(a.w, &s3, &c3);
+    if (keep_angles) *reinterpret_cast<float4*>(&th[p][r][col]) = a;
+    *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
+    *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
+  };
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int rr = (t >> 4) + 16 * i;
+    const int p = rr < kSRows ? 1 : 0;
+    const int r = rr < kSRows ? rr : rr - kSRows + 1;
+    put(p, r, 4 + 4 * g, v[i], p == 0 || (r >= 2 && r < kSRows - 2));
+  }
+  if (has_tail) put(0, tail_r, 4 + 4 * g, vt, true);
+  if (has_halo) put(hp, hr, hside ? kTileF + 4 : 0, vh, hp == 0);
+}
+
+// pair_nb with the other colour's rows r - 1 and r of the pair's columns in
+// registers (D, P: the previous row's P and U, as a warp walks its rows
+// downwards): loads the same-row edge element and row r + 1 (returned in U).
+__device__ __forceinline__ void pair_nb_rolled(const CsArr& nb, int r, int c0, int q,
+                                               const float4 D, const float4 P, float4& U,
+                                               PairNb& n) {
+  const float4 E = *reinterpret_cast<const float4*>(&nb[r][q ? c0 + 4 : c0 - 4]);
+  U = *reinterpret_cast<const float4*>(&nb[r + 1][c0]);
+  const float4 Lf = q ? P : E, Rt = q ? E : P;
+  n.l[0] = make_float2(Lf.x, Lf.y);
+  n.l[1] = make_float2(Lf.z, Lf.w);
+  n.r[0] = make_float2(Rt.x, Rt.y);
+  n.r[1] = make_float2(Rt.z, Rt.w);
+  n.d[0] = make_float2(D.x, D.y);
+  n.d[1] = make_float2(D.z, D.w);
+  n.u[0] = make_float2(U.x, U.y);
+  n.u[1] = make_float2(U.z, U.w);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    n.Sc[j] = xyd::nb_sum(n.l[j].x, n.r[j].x, n.d[j].x, n.u[j].x);
+    n.Ss[j] = xyd::nb_sum(n.l[j].y, n.r[j].y, n.d[j].y, n.u[j].y);
+  }
+}
+
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
@@ -269,64 +354,7 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
   const size_t plane = (size_t)L * (size_t)F;
 
   // ---- stage both planes (angle + unit vector) ----
-  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
-  // (stage rows 1..34); 16 lanes per row, one float4 (one site, four
-  // replicas) per lane; the halo sites ks0 - 1 and ks0 + 16 (rows 1..34) are
-  // a separate pass taken by the last warps.
-  {
-    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
-    const int half = lane_s >> 4, g = lane_s & 15;
-    constexpr int kSteps = (kStageRowsTotal + 2 * kWarps - 1) / (2 * kWarps);
-    float4 v[kSteps];
-#pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g;
-        v[i] = COHERENT ? __ldcg(reinterpret_cast<const float4*>(item.src + row))
-                        : __ldg(reinterpret_cast<const float4*>(item.src + row));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const int col = 4 + 4 * g;
-        float s0, c0, s1, c1, s2, c2, s3, c3;
-        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
-        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
-        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
-        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
-        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
-        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-      }
-    }
-    for (int h = kThreads - 1 - threadIdx.x; h < 2 * (kSRows - 2) * 2; h += kThreads) {
-      const int p = h / ((kSRows - 2) * 2);
-      const int rem = h - p * ((kSRows - 2) * 2);
-      const int r = 1 + (rem >> 1);
-      const int side = rem & 1;
-      const int ks = side ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
-      const size_t at = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + 4 * (size_t)ks;
-      const int col = side ? kTileF + 4 : 0;
-      const float4 t = COHERENT ? __ldcg(reinterpret_cast<const float4*>(item.src + at))
-                                : __ldg(reinterpret_cast<const float4*>(item.src + at));
-      float s0, c0, s1, c1, s2, c2, s3, c3;
-      xyd::unit_vector<MODE>(t.x, &s0, &c0);
-      xyd::unit_vector<MODE>(t.y, &s1, &c1);
-      xyd::unit_vector<MODE>(t.z, &s2, &c2);
-      xyd::unit_vector<MODE>(t.w, &s3, &c3);
-      *reinterpret_cast<float4*>(&th[p][r][col]) = t;
-      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-    }
-  }
+  quad_stage<MODE, COHERENT>(item.src, th, cs, y0, f0, ks0, L, W, F, plane);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -341,6 +369,8 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
   unsigned int n_acc[2] = {0u, 0u};
 
   // ---- red half: the tile (counted, written to dst) ----
+  float4 nbD = *reinterpret_cast<const float4*>(&cs[1][warp * 4 + 1][c0]);
+  float4 nbP = *reinterpret_cast<const float4*>(&cs[1][warp * 4 + 2][c0]);
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -348,7 +378,10 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const int r = ty + 2;
     const int q = y & 1;                                   // red: x = 2k + (y & 1)
     PairNb n;
-    pair_nb(cs[1], r, c0, q, n);
+    float4 nbU;
+    pair_nb_rolled(cs[1], r, c0, q, nbD, nbP, nbU, n);
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
     // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
@@ -368,29 +401,45 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
         xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K1, a.delta);
     n_acc[0] += r0.accept ? 1u : 0u;
     n_acc[1] += r1.accept ? 1u : 0u;
-    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
     *reinterpret_cast<float2*>(item.dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
-  // elements 0..63: row -1; 64..127: row 32; 128..255: the halo site of rows
-  // 0..31 on the side the black tile reaches (left on odd rows, right on even)
-  {
-    const int i = threadIdx.x;
-    int ty, sc;
-    if (i < kTileF) {
-      ty = -1;
-      sc = 4 + i;
-    } else if (i < 2 * kTileF) {
-      ty = kTileRows;
-      sc = 4 + i - kTileF;
-    } else {
-      const int e = i - 2 * kTileF;
-      ty = e >> 2;
-      sc = (((y0 + ty) & 1) ? 0 : kTileF + 4) + (e & 3);
-    }
+  // rows -1 and 32 (64 elements each): one lane per pair of sites (sites 2j
+  // and 2j + 1 of the tile row share a Philox block, as in the tile) and
+  // replica, warps 0 and 1; the halo site of rows 0..31 on the side the black
+  // tile reaches (left on odd rows, right on even; 128 elements), one per lane
+  // of warps 2..5.  Warps 6 and 7 wait at the barrier.
+  if (threadIdx.x < 64) {
+    const int ty = threadIdx.x < 32 ? -1 : kTileRows;
+    const int j = threadIdx.x & 31;
+    const int rep = j & 3;                                 // replica
+    const int sc = 4 + 8 * (j >> 2) + rep;                 // element of site 2 (j >> 2)
     const int r = ty + 2;
     const int y = wrap_once(y0 + ty, L);
+    const int q = y & 1;
+    const uint32_t x = 2u * (uint32_t)(ks0 + 2 * (j >> 2)) + (uint32_t)q;   // x & 2 == 0
+    const uint4 w = xyd::philox4x32_10(
+        make_uint4((uint32_t)y * uL + x, item.sweep, a.lattice_id0 + (uint32_t)rep, 1u), a.rk);
+    const float K = replica_k(a, rep);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int c = sc + 4 * e;
+      const float2 l = cs[1][r][c + 4 * q - 4], rt = cs[1][r][c + 4 * q];
+      const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
+      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+      const float2 own = cs[0][r][c];
+      const xyd::SiteResult res = xyd::metropolis_step<MODE>(
+          th[0][r][c], own.x, own.y, Sc, Ss, e ? w.z : w.x, e ? w.w : w.y, K, a.delta);
+      cs[0][r][c] = make_float2(res.c, res.s);
+    }
+  } else if (threadIdx.x < 64 + kTileRows * kR) {
+    const int e = threadIdx.x - 64;
+    const int ty = e >> 2;
+    const int sc = (((y0 + ty) & 1) ? 0 : kTileF + 4) + (e & 3);
+    const int r = ty + 2;
+    const int y = y0 + ty;
     const int q = y & 1;
     const int ks = wrap_once(ks0 + ((sc - 4) >> 2), W);   // floor: stage columns 0..3 -> ks0 - 1
     const int j = sc & 3;
@@ -406,7 +455,6 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
                                                            uw.x, uw.y, replica_k(a, j), a.delta);
-    th[0][r][sc] = res.th;
     cs[0][r][sc] = make_float2(res.c, res.s);
   }
   mid();
@@ -416,6 +464,8 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
   QuadSums<RED> sums;
   sums.init();
   float* dst_blk = item.dst + plane;
+  nbD = *reinterpret_cast<const float4*>(&cs[0][warp * 4 + 1][c0]);
+  nbP = *reinterpret_cast<const float4*>(&cs[0][warp * 4 + 2][c0]);
 #pragma unroll 2
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
@@ -423,7 +473,11 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     const int r = ty + 2;
     const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
     PairNb n;
-    pair_nb(cs[0], r, c0, q, n);
+    float4 nbU;
+    pair_nb_rolled(cs[0], r, c0, q, nbD, nbP, nbU, n);
+    const float4 m = nbP;                                  // the red pair of the same row
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
     // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
@@ -446,7 +500,6 @@ __device__ __forceinline__ void quad_sweep_body(const Args& item, int bx, int by
     *reinterpret_cast<float2*>(dst_blk + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
 
     // red elements with the same (y, k, replica): their spins enter M once each
-    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     float v0[5], v1[5];
     xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
@@ -482,62 +535,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   const size_t plane = (size_t)L * (size_t)F;
 
   // ---- stage both planes (angle + unit vector) ----
-  // Rows: the black plane's 36 (stage rows 0..35) then the red plane's 34
-  // (stage rows 1..34); 16 lanes per row, one float4 (one site, four
-  // replicas) per lane; the halo sites ks0 - 1 and ks0 + 16 (rows 1..34) are
-  // a separate pass taken by the last warps.
-  {
-    const int warp_s = threadIdx.x >> 5, lane_s = threadIdx.x & 31;
-    const int half = lane_s >> 4, g = lane_s & 15;
-    constexpr int kSteps = (kStageRowsTotal + 2 * kWarps - 1) / (2 * kWarps);
-    float4 v[kSteps];
-#pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const size_t row = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + f0 + 4 * g;
-        v[i] = __ldg(reinterpret_cast<const float4*>(a.src + row));
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < kSteps; ++i) {
-      const int rr = 2 * warp_s + half + 2 * kWarps * i;
-      if (rr < kStageRowsTotal) {
-        const int p = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const int col = 4 + 4 * g;
-        float s0, c0, s1, c1, s2, c2, s3, c3;
-        xyd::unit_vector<MODE>(v[i].x, &s0, &c0);
-        xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
-        xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
-        xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
-        *reinterpret_cast<float4*>(&th[p][r][col]) = v[i];
-        *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-        *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-      }
-    }
-    for (int h = kThreads - 1 - threadIdx.x; h < 2 * (kSRows - 2) * 2; h += kThreads) {
-      const int p = h / ((kSRows - 2) * 2);
-      const int rem = h - p * ((kSRows - 2) * 2);
-      const int r = 1 + (rem >> 1);
-      const int side = rem & 1;
-      const int ks = side ? wrap_once(ks0 + kTileF / 4, W) : wrap_once(ks0 - 1, W);
-      const size_t at = p * plane + (size_t)wrap_once(y0 - 2 + r, L) * F + 4 * (size_t)ks;
-      const int col = side ? kTileF + 4 : 0;
-      const float4 t = __ldg(reinterpret_cast<const float4*>(a.src + at));
-      float s0, c0, s1, c1, s2, c2, s3, c3;
-      xyd::unit_vector<MODE>(t.x, &s0, &c0);
-      xyd::unit_vector<MODE>(t.y, &s1, &c1);
-      xyd::unit_vector<MODE>(t.z, &s2, &c2);
-      xyd::unit_vector<MODE>(t.w, &s3, &c3);
-      *reinterpret_cast<float4*>(&th[p][r][col]) = t;
-      *reinterpret_cast<float4*>(&cs[p][r][col]) = make_float4(c0, s0, c1, s1);
-      *reinterpret_cast<float4*>(&cs[p][r][col + 2]) = make_float4(c2, s2, c3, s3);
-    }
-  }
+  quad_stage<MODE, false>(a.src, th, cs, y0, f0, ks0, L, W, F, plane);
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -552,14 +550,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   unsigned int n_acc[2] = {0u, 0u};
 
   // ---- red half: the tile (counted, written to dst) ----
-#pragma unroll 2
+  float4 nbD = *reinterpret_cast<const float4*>(&cs[1][warp * 4 + 1][c0]);
+  float4 nbP = *reinterpret_cast<const float4*>(&cs[1][warp * 4 + 2][c0]);
+#pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
     const int y = y0 + ty;
     const int r = ty + 2;
     const int q = y & 1;                                   // red: x = 2k + (y & 1)
     PairNb n;
-    pair_nb(cs[1], r, c0, q, n);
+    float4 nbU;
+    pair_nb_rolled(cs[1], r, c0, q, nbD, nbP, nbU, n);
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
     // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
@@ -579,29 +582,45 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
         xyd::metropolis_step<MODE>(t.y, o.z, o.w, n.Sc[1], n.Ss[1], w1.x, w1.y, K1, a.delta);
     n_acc[0] += r0.accept ? 1u : 0u;
     n_acc[1] += r1.accept ? 1u : 0u;
-    *reinterpret_cast<float2*>(&th[0][r][c0]) = make_float2(r0.th, r1.th);
     *reinterpret_cast<float4*>(&cs[0][r][c0]) = make_float4(r0.c, r0.s, r1.c, r1.s);
     *reinterpret_cast<float2*>(a.dst + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
   }
   // ---- red half: the ring at distance one (recomputed, not counted) ----
-  // elements 0..63: row -1; 64..127: row 32; 128..255: the halo site of rows
-  // 0..31 on the side the black tile reaches (left on odd rows, right on even)
-  {
-    const int i = threadIdx.x;
-    int ty, sc;
-    if (i < kTileF) {
-      ty = -1;
-      sc = 4 + i;
-    } else if (i < 2 * kTileF) {
-      ty = kTileRows;
-      sc = 4 + i - kTileF;
-    } else {
-      const int e = i - 2 * kTileF;
-      ty = e >> 2;
-      sc = (((y0 + ty) & 1) ? 0 : kTileF + 4) + (e & 3);
-    }
+  // rows -1 and 32 (64 elements each): one lane per pair of sites (sites 2j
+  // and 2j + 1 of the tile row share a Philox block, as in the tile) and
+  // replica, warps 0 and 1; the halo site of rows 0..31 on the side the black
+  // tile reaches (left on odd rows, right on even; 128 elements), one per lane
+  // of warps 2..5.  Warps 6 and 7 wait at the barrier.
+  if (threadIdx.x < 64) {
+    const int ty = threadIdx.x < 32 ? -1 : kTileRows;
+    const int j = threadIdx.x & 31;
+    const int rep = j & 3;                                 // replica
+    const int sc = 4 + 8 * (j >> 2) + rep;                 // element of site 2 (j >> 2)
     const int r = ty + 2;
     const int y = wrap_once(y0 + ty, L);
+    const int q = y & 1;
+    const uint32_t x = 2u * (uint32_t)(ks0 + 2 * (j >> 2)) + (uint32_t)q;   // x & 2 == 0
+    const uint4 w = xyd::philox4x32_10(
+        make_uint4((uint32_t)y * uL + x, a.sweep, a.lattice_id0 + (uint32_t)rep, 1u), a.rk);
+    const float K = replica_k(a, rep);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int c = sc + 4 * e;
+      const float2 l = cs[1][r][c + 4 * q - 4], rt = cs[1][r][c + 4 * q];
+      const float2 d = cs[1][r - 1][c], u = cs[1][r + 1][c];
+      const float Sc = xyd::nb_sum(l.x, rt.x, d.x, u.x);
+      const float Ss = xyd::nb_sum(l.y, rt.y, d.y, u.y);
+      const float2 own = cs[0][r][c];
+      const xyd::SiteResult res = xyd::metropolis_step<MODE>(
+          th[0][r][c], own.x, own.y, Sc, Ss, e ? w.z : w.x, e ? w.w : w.y, K, a.delta);
+      cs[0][r][c] = make_float2(res.c, res.s);
+    }
+  } else if (threadIdx.x < 64 + kTileRows * kR) {
+    const int e = threadIdx.x - 64;
+    const int ty = e >> 2;
+    const int sc = (((y0 + ty) & 1) ? 0 : kTileF + 4) + (e & 3);
+    const int r = ty + 2;
+    const int y = y0 + ty;
     const int q = y & 1;
     const int ks = wrap_once(ks0 + ((sc - 4) >> 2), W);   // floor: stage columns 0..3 -> ks0 - 1
     const int j = sc & 3;
@@ -617,7 +636,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     const float2 own = cs[0][r][sc];
     const xyd::SiteResult res = xyd::metropolis_step<MODE>(th[0][r][sc], own.x, own.y, Sc, Ss,
                                                            uw.x, uw.y, replica_k(a, j), a.delta);
-    th[0][r][sc] = res.th;
     cs[0][r][sc] = make_float2(res.c, res.s);
   }
   __syncthreads();
@@ -626,14 +644,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
   QuadSums<RED> sums;
   sums.init();
   float* dst_blk = a.dst + plane;
-#pragma unroll 2
+  nbD = *reinterpret_cast<const float4*>(&cs[0][warp * 4 + 1][c0]);
+  nbP = *reinterpret_cast<const float4*>(&cs[0][warp * 4 + 2][c0]);
+#pragma unroll
   for (int rr = 0; rr < 4; ++rr) {
     const int ty = warp * 4 + rr;
     const int y = y0 + ty;
     const int r = ty + 2;
     const int q = (y + 1) & 1;                             // black: x = 2k + ((y + 1) & 1)
     PairNb n;
-    pair_nb(cs[0], r, c0, q, n);
+    float4 nbU;
+    pair_nb_rolled(cs[0], r, c0, q, nbD, nbP, nbU, n);
+    const float4 m = nbP;                                  // the red pair of the same row
+    nbD = nbP;
+    nbP = nbU;
     const uint32_t x = 2u * kq + (uint32_t)q;
     const uint32_t ctr = xyd::metropolis_counter((uint32_t)y * uL + x, x);
     // lanes l and l ^ 2 hold replicas j0, j0 + 1 of the pair's two sites
@@ -656,7 +680,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused(QuadFusedArgs a) {
     *reinterpret_cast<float2*>(dst_blk + (size_t)y * F + fp) = make_float2(r0.th, r1.th);
 
     // red elements with the same (y, k, replica): their spins enter M once each
-    const float4 m = *reinterpret_cast<const float4*>(&cs[0][r][c0]);
     float v0[5], v1[5];
     xyd::measure_terms(r0.c, r0.s, n.l[0].x, n.l[0].y, n.r[0].x, n.r[0].y, n.d[0].x, n.d[0].y,
                        n.u[0].x, n.u[0].y, n.Sc[0], n.Ss[0], m.x, m.y, v0);
@@ -751,26 +774,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_quad_fused_persist(QuadPersistA
           if (threadIdx.x == 0) *slot = next;
         },
         [&]() {
-          if (threadIdx.x < 32) {
-            bool ok = threadIdx.x >= 9;
+          if (threadIdx.x >= kThreads - 32) {
+            const int l = threadIdx.x - (kThreads - 32);
+            bool ok = l >= 9;
             const int ni = *slot;
-            if (threadIdx.x < 9 && ni < total) {
+            if (l < 9 && ni < total) {
               const int ns = ni / ntiles;
               const int nk = ni - ns * ntiles;
               const int nrow = nk / tiles_x;
               const int nbx = nk - nrow * tiles_x;
               const int nby = (nrow & 1) ? tiles_y - 1 - (nrow >> 1) : (nrow >> 1);
-              const int d = threadIdx.x;
+              const int d = l;
               const int nx = wrap_once(nbx + d % 3 - 1, tiles_x);
               const int ny = wrap_once(nby + d / 3 - 1, tiles_y);
               ok = ns == 0 || q_load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ns;
             }
             const unsigned int all = __ballot_sync(0xffffffffu, ok);
-            if (threadIdx.x == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
+            if (l == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
           }
         });
-    if (threadIdx.x == kThreads - 32) {
-      // the closing barrier orders every thread's stores to dst before this
+    if (threadIdx.x == kThreads - 64) {
+      // a warp other than the early look's publishes the tile: the closing
+      // barrier orders every thread's stores to dst before this
       // GPU-scope release, which is cumulative over the writes that happen
       // before it
       q_store_release(p.flags + (by * tiles_x + bx), (unsigned int)(s + 1));
