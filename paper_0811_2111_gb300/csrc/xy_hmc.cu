@@ -849,6 +849,32 @@ constexpr int kP2Band = kP2Rows / kP2Warps;                  // 4 rows per warp
 constexpr int kFrRows = kP2Rows + 4;                         // tile rows -2 .. 33
 constexpr int kFrCols = kP2Cols + 8;                         // tile columns -4 .. 131
 constexpr size_t kP2Smem = sizeof(float) * 2 * kFrRows * kFrCols;
+// The tile-walking form (PREF) adds each thread's slots for the next tile's
+// loads, copied in by cp.async while the current tile runs: its 4 angle and 4
+// momentum float4 rows, then six scalars (ring site A's angle and momentum,
+// ring site B's, the halo-two sites H and G).
+constexpr size_t kP2PreRowsAt = kP2Smem;
+constexpr size_t kP2PreScalarsAt = kP2PreRowsAt + sizeof(float4) * 2 * kP2Band * kP2Threads;
+constexpr size_t kP2SmemPref = kP2PreScalarsAt + sizeof(float) * 6 * kP2Threads;
+static_assert(2 * (kP2SmemPref + 1024) <= 228 * 1024, "two tile-walking CTAs must fit one SM");
+// The tile-walking form runs when every resident CTA gets at least this many
+// tiles of a launch (measured per unit trajectory: 3.44 against 3.56 ms at
+// L = 4096, 17.8 against 18.9 at 8192; a tie at 2048, about 3.4 tiles per
+// CTA; with a tile per CTA only the extra shared-memory round trip is left).
+constexpr int kP2PrefMinTilesPerCta = 4;
+
+__device__ __forceinline__ void hmc_cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void hmc_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
 
 __device__ __forceinline__ int wrap_near(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -860,48 +886,105 @@ __device__ __forceinline__ void hmc_site_step(float c, float s, float Sc, float 
   t = hmc_wrap(__fmaf_rn(eps, p, t));
 }
 
-template <int MODE>
+// PREF = false: one tile per CTA (grid = the tile columns x rows), its loads straight into
+// registers.  PREF = true: a grid of resident CTAs walks the tiles blockIdx.x,
+// + gridDim.x, ... (the tiles of a launch are independent: it reads one angle
+// and one momentum buffer and writes two others), each thread copying the next
+// tile's loads into its own shared-memory slots by cp.async right after the
+// current tile's staging barrier, so they arrive while the two steps run.
+// Both forms run the same arithmetic on the same values: bit-identical.
+template <int MODE, bool PREF>
 __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   float (*fc)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem);
   float (*fs)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem + sizeof(float) * kFrRows * kFrCols);
+  float4* pre_rows = reinterpret_cast<float4*>(smem + kP2PreRowsAt);   // [2 * kP2Band][threads]
+  float* pre_sc = reinterpret_cast<float*>(smem + kP2PreScalarsAt);     // [6][threads]
 
   const int L = a.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x0 = blockIdx.x * kP2Cols, y0 = blockIdx.y * kP2Rows;
+  const int tiles_x = L / kP2Cols, n_tiles = tiles_x * (L / kP2Rows);
   int src, dst;
   hmc_buffers(a, a.ctl->cur, &src, &dst);
   const float* __restrict__ th_src = hmc_buf(a, src);
 
+  const int rb = kP2Band * warp;                             // first tile row of the band
+  // the loads of tile t into this thread's slots (PREF): the same sites, in
+  // the same order, as the loads in the tile loop below
+  auto prefetch = [&](int t) {
+    const int px0 = (t % tiles_x) * kP2Cols, py0 = (t / tiles_x) * kP2Rows;
+    const int pxb = px0 + 4 * lane;
+#pragma unroll
+    for (int r = 0; r < kP2Band; ++r) {
+      const size_t g = (size_t)(py0 + rb + r) * L + pxb;
+      hmc_cp16(&pre_rows[r * kP2Threads + tid], th_src + g);
+      hmc_cp16(&pre_rows[(kP2Band + r) * kP2Threads + tid], a.p_in + g);
+    }
+    const int ay = tid < kP2Cols ? -1 : kP2Rows, ax = tid & (kP2Cols - 1);
+    const size_t ga = (size_t)wrap_near(py0 + ay, L) * L + (px0 + ax);
+    hmc_cp4(&pre_sc[0 * kP2Threads + tid], th_src + ga);
+    hmc_cp4(&pre_sc[1 * kP2Threads + tid], a.p_in + ga);
+    if (tid < 2 * kP2Rows) {
+      const int bx = tid < kP2Rows ? -1 : kP2Cols, by = tid & (kP2Rows - 1);
+      const size_t gb = (size_t)(py0 + by) * L + wrap_near(px0 + bx, L);
+      hmc_cp4(&pre_sc[2 * kP2Threads + tid], th_src + gb);
+      hmc_cp4(&pre_sc[3 * kP2Threads + tid], a.p_in + gb);
+    }
+    const int hy = tid < kP2Cols ? -2 : kP2Rows + 1;
+    hmc_cp4(&pre_sc[4 * kP2Threads + tid], th_src + (size_t)wrap_near(py0 + hy, L) * L + (px0 + ax));
+    if (tid >= 64 && tid < 132) {
+      int gy, gx;
+      if (tid < 128) {
+        gx = (tid - 64) < kP2Rows ? -2 : kP2Cols + 1;
+        gy = (tid - 64) & (kP2Rows - 1);
+      } else {
+        gy = (tid & 2) ? kP2Rows : -1;
+        gx = (tid & 1) ? kP2Cols : -1;
+      }
+      hmc_cp4(&pre_sc[5 * kP2Threads + tid],
+              th_src + (size_t)wrap_near(py0 + gy, L) * L + wrap_near(px0 + gx, L));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (PREF && (int)blockIdx.x < n_tiles) prefetch(blockIdx.x);
+  for (int tile = PREF ? (int)blockIdx.x : 0; tile < (PREF ? n_tiles : 1);
+       tile += PREF ? (int)gridDim.x : 1) {
+  const int x0 = PREF ? (tile % tiles_x) * kP2Cols : (int)blockIdx.x * kP2Cols;
+  const int y0 = PREF ? (tile / tiles_x) * kP2Rows : (int)blockIdx.y * kP2Rows;
+
   // ---- loads: own 4 x 4 block (angles and momenta), one site of the ring's
   // top or bottom row (threads 0..255), one of its side columns (0..63), one
   // halo-two site of rows -2 / 33 (0..255), of columns -2 / 129 (64..127) or a
-  // ring corner (128..131)
+  // ring corner (128..131); from this thread's slots (PREF) or from global
+  // memory
   const int xb = x0 + 4 * lane;
-  const int rb = kP2Band * warp;                             // first tile row of the band
   float4 t4[kP2Band], p4[kP2Band];
+  if (PREF) asm volatile("cp.async.wait_all;" ::: "memory");
 #pragma unroll
   for (int r = 0; r < kP2Band; ++r) {
     const size_t g = (size_t)(y0 + rb + r) * L + xb;
-    t4[r] = *reinterpret_cast<const float4*>(th_src + g);
-    p4[r] = *reinterpret_cast<const float4*>(a.p_in + g);
+    t4[r] = PREF ? pre_rows[r * kP2Threads + tid] : *reinterpret_cast<const float4*>(th_src + g);
+    p4[r] = PREF ? pre_rows[(kP2Band + r) * kP2Threads + tid]
+                 : *reinterpret_cast<const float4*>(a.p_in + g);
   }
   // ring site A: row -1 (tid < 128) or 32, column tid & 127
   const int ay = tid < kP2Cols ? -1 : kP2Rows, ax = tid & (kP2Cols - 1);
   const size_t ga = (size_t)wrap_near(y0 + ay, L) * L + (x0 + ax);
-  float ta = th_src[ga], pa = a.p_in[ga];
+  float ta = PREF ? pre_sc[0 * kP2Threads + tid] : th_src[ga];
+  float pa = PREF ? pre_sc[1 * kP2Threads + tid] : a.p_in[ga];
   // ring site B: column -1 (tid < 32) or 128, row tid & 31
   const bool hasb = tid < 2 * kP2Rows;
   const int bx = tid < kP2Rows ? -1 : kP2Cols, by = tid & (kP2Rows - 1);
   float tb = 0.f, pb = 0.f;
   if (hasb) {
     const size_t gb = (size_t)(y0 + by) * L + wrap_near(x0 + bx, L);
-    tb = th_src[gb];
-    pb = a.p_in[gb];
+    tb = PREF ? pre_sc[2 * kP2Threads + tid] : th_src[gb];
+    pb = PREF ? pre_sc[3 * kP2Threads + tid] : a.p_in[gb];
   }
   // halo-two site H: rows -2 / 33; G: columns -2 / 129 or a corner
   const int hy = tid < kP2Cols ? -2 : kP2Rows + 1;
-  const float th_h = th_src[(size_t)wrap_near(y0 + hy, L) * L + (x0 + ax)];
+  const float th_h =
+      PREF ? pre_sc[4 * kP2Threads + tid] : th_src[(size_t)wrap_near(y0 + hy, L) * L + (x0 + ax)];
   const bool hasg = tid >= 64 && tid < 132;
   int gy = 0, gx = 0;
   float th_g = 0.f;
@@ -913,7 +996,8 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
       gy = (tid & 2) ? kP2Rows : -1;
       gx = (tid & 1) ? kP2Cols : -1;
     }
-    th_g = th_src[(size_t)wrap_near(y0 + gy, L) * L + wrap_near(x0 + gx, L)];
+    th_g = PREF ? pre_sc[5 * kP2Threads + tid]
+                : th_src[(size_t)wrap_near(y0 + gy, L) * L + wrap_near(x0 + gx, L)];
   }
 
   // ---- unit vectors of the old state; what crosses a warp goes to the frame
@@ -961,6 +1045,10 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
     }
   }
   __syncthreads();
+
+  // every thread has read its slots before the barrier above: the next tile's
+  // copies land there while this one runs
+  if (PREF && tile + (int)gridDim.x < n_tiles) prefetch(tile + (int)gridDim.x);
 
   // ---- first step: the ring sites (from the frame), then the tile --------
   const float K = a.K, ka = a.a, eps = a.eps;
@@ -1081,6 +1169,8 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
     *reinterpret_cast<float4*>(a.p_out + g) = make_float4(po[0], po[1], po[2], po[3]);
     *reinterpret_cast<float4*>(th_dst + g) = make_float4(to[0], to[1], to[2], to[3]);
   }
+  if (PREF) __syncthreads();   // the next tile's staging rewrites the frame
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1188,8 +1278,17 @@ template <int MODE>
 cudaError_t launch_mode(int kind, const HmcArgs& a, cudaStream_t stream) {
   if (kind == kHmcStep2) {
     if (!a.tiled || !a.pairs || a.p_in == a.p_out) return cudaErrorInvalidValue;
-    const dim3 grid(a.L / kP2Cols, a.L / kP2Rows);
-    k_hmc_tile2<MODE><<<grid, kP2Threads, kP2Smem, stream>>>(a);
+    // two CTAs per SM (the registers' limit); the tile-walking form when each
+    // would get at least kP2PrefMinTilesPerCta tiles
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int n_tiles = (a.L / kP2Cols) * (a.L / kP2Rows);
+    if (n_tiles >= kP2PrefMinTilesPerCta * 2 * sms)
+      k_hmc_tile2<MODE, true><<<2 * sms, kP2Threads, kP2SmemPref, stream>>>(a);
+    else
+      k_hmc_tile2<MODE, false><<<dim3(a.L / kP2Cols, a.L / kP2Rows), kP2Threads, kP2Smem, stream>>>(a);
     return cudaGetLastError();
   }
   if (a.tiled) {
@@ -1224,11 +1323,19 @@ cudaError_t hmc_prepare(int sincos_mode) {
   if (e != cudaSuccess) return e;
   const int m = sincos_mode < 0 || sincos_mode > 2 ? 0 : sincos_mode;
   if (dev >= 0 && dev < 64 && done[m][dev]) return cudaSuccess;
-  const void* f = m == 0 ? (const void*)k_hmc_tile2<0>
-                         : (m == 1 ? (const void*)k_hmc_tile2<1> : (const void*)k_hmc_tile2<2>);
+  const void* f = m == 0 ? (const void*)k_hmc_tile2<0, false>
+                         : (m == 1 ? (const void*)k_hmc_tile2<1, false>
+                                   : (const void*)k_hmc_tile2<2, false>);
   e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const void* fp = m == 0 ? (const void*)k_hmc_tile2<0, true>
+                          : (m == 1 ? (const void*)k_hmc_tile2<1, true>
+                                    : (const void*)k_hmc_tile2<2, true>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2SmemPref);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fp, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   const void* g4 = m == 0 ? (const void*)k_hmc_step_tma<0, 4>
                           : (m == 1 ? (const void*)k_hmc_step_tma<1, 4> : (const void*)k_hmc_step_tma<2, 4>);
   if (e == cudaSuccess)

@@ -144,13 +144,16 @@ def test_kernels_are_bit_identical(L, n_md):
         assert a[5] == b[5], name
 
 
-@pytest.mark.parametrize("L,n_md", [(512, 4), (512, 5), (1024, 8), (1024, 3)])
+@pytest.mark.parametrize("L,n_md", [(512, 4), (512, 5), (1024, 8), (1024, 3), (4096, 6),
+                                    (4096, 5)])
 def test_auto_kernel_equals_one_step_launches(L, n_md):
     """AUTO at sides the tiled kernels take: the full steps two per launch
-    (momenta ping-ponged between two buffers) with an odd remaining step on
-    the TMA or the plain tiled kernel, against one tiled launch per step:
-    angles, momenta, records and sums bit for bit, over trajectories with an
-    even and an odd number of full steps and a plain integration."""
+    (momenta ping-ponged between two buffers; one tile per CTA at L = 512 and
+    1024, resident CTAs walking the tiles with the next tile's loads copied in
+    ahead at L = 4096) with an odd remaining step on the TMA or the plain
+    tiled kernel, against one tiled launch per step: angles, momenta, records
+    and sums bit for bit, over trajectories with an even and an odd number of
+    full steps and a plain integration."""
     out = {}
     for kernel in ("tiled", "auto"):
         with HMC(L, 1.1, 17, 0.5 / n_md, n_md, kernel=kernel, lattice_id=3) as h:

@@ -177,3 +177,27 @@ def test_persistent_calls_split_anywhere():
             sa, na = a.state(r)
             sb, nb = b.state(r)
             assert na == nb == 9 and np.array_equal(sa, sb)
+
+
+def test_throughput_configuration_replicas_equal_single_lattices():
+    """The four-replica throughput configuration as bench.py times it: L = 4096,
+    betas 1.00, 1.06, 1.12, 1.18, seed 7, AUTO (one fused launch per sweep,
+    16384 tiles).  Each replica is the single lattice with lattice id r (the
+    persistent single-lattice sweep, itself in lock step with the oracle at this
+    size): angles, accept counts and exact record sums bit for bit."""
+    L, betas, seed, sweeps = 4096, [1.0, 1.06, 1.12, 1.18], 7, 3
+    with Quad(L, betas, seed) as q:
+        assert q.algorithm == "fused"
+        q.sweep(sweeps)
+        states = [q.state(r)[0] for r in range(4)]
+        obs = [q.observables(r) for r in range(4)]
+    for r, beta in enumerate(betas):
+        with Lattice(L, beta, seed, lattice_id=r) as lat:
+            assert lat.algorithm == "persistent"
+            lat.sweep(sweeps)
+            s, n = lat.state()
+            o = lat.observables()
+        assert n == sweeps
+        assert np.array_equal(states[r], s), r
+        for k in ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta"):
+            assert np.array_equal(obs[r][k], o[k]), (r, k)
