@@ -73,7 +73,9 @@ typedef struct {
  * that streams each tile into double-buffered shared memory with the tensor
  * memory accelerator (needs L % 128 == 0 and the driver's tensor-map encoder;
  * begin and final launches as TILED); TILED2 runs the full steps two per
- * launch (temporal blocking: half the DRAM traffic, a recomputed halo of two);
+ * launch (temporal blocking: half the DRAM traffic, a recomputed halo of two;
+ * where every resident CTA gets at least four tiles, L >= 4096, two CTAs per
+ * SM walk the tiles and copy the next tile's loads in ahead);
  * SITE is one thread per site (any L); CLUSTER runs a whole trajectory in one
  * launch of one thread-block cluster that keeps the lattice in shared memory
  * (L a power of two in [16, 256]; strips of 16 rows per CTA, neighbouring strips
