@@ -1268,12 +1268,6 @@ __global__ void k_hmc_canon_reset(HmcCtl* ctl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctl->cur = 0u;
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > 152 * 16) g = 152 * 16;
-  return (int)(g < 1 ? 1 : g);
-}
-
 template <int MODE>
 cudaError_t launch_mode(int kind, const HmcArgs& a, cudaStream_t stream) {
   if (kind == kHmcStep2) {

@@ -13,6 +13,15 @@
 
 namespace xyk {
 
+// Blocks for a grid-stride loop over n items: a few waves over a GB300's 152
+// SMs at most (16 CTAs per SM), the loop covering the rest.
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = 152 * 16;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
 // Named range on the profiler timeline (NVTX) for the lifetime of the object:
 // the entry points that enqueue work open one, so nsys/ncu timelines show
 // which call launched which kernels.  Costs nothing without a tool attached.

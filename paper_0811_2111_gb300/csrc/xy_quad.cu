@@ -168,12 +168,6 @@ __global__ void k_quad_extract(const float4* __restrict__ theta, float* __restri
     out[i] = comp(theta[i], j);
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > 152 * 16) g = 152 * 16;
-  return (int)(g < 1 ? 1 : g);
-}
-
 template <int COLOUR, int MODE, int RED>
 cudaError_t launch_one(const QuadArgs& a, cudaStream_t s) {
   const dim3 grid((a.W + kTileCols - 1) / kTileCols, (a.L + kTileRows - 1) / kTileRows);
@@ -416,7 +410,7 @@ xy_status xy_quad_create(const xy_params* p, const double beta[4], void* cuda_st
   }
   if (e == cudaSuccess) {
     step = "start kernel";
-    k_quad_start<<<grid_for((int64_t)N, 256), 256, 0, q->stream>>>(
+    k_quad_start<<<xyk::grid_for((int64_t)N, 256), 256, 0, q->stream>>>(
         q->d_theta, p->L, xyd::make_round_keys(p->seed), p->lattice_id,
         p->start == XY_START_HOT ? 1 : 0);
     e = cudaGetLastError();
@@ -598,7 +592,7 @@ xy_status xy_quad_get_state(xy_quad* q, int32_t replica, float* host, uint64_t* 
   if (replica < 0 || replica >= kR) return fail(q, XY_EINVAL, "xy_quad_get_state: replica out of range");
   if (!host) return fail(q, XY_EINVAL, "xy_quad_get_state: NULL output");
   const int64_t N = (int64_t)q->p.L * q->p.L;
-  k_quad_extract<<<grid_for(N, 256), 256, 0, q->stream>>>(current(q), q->d_scratch, replica, N);
+  k_quad_extract<<<xyk::grid_for(N, 256), 256, 0, q->stream>>>(current(q), q->d_scratch, replica, N);
   Q_CUDA(q, cudaGetLastError(), "xy_quad_get_state: extract");
   Q_CUDA(q, xyk::launch_split_to_natural(q->d_scratch, q->d_nat, q->p.L, q->stream),
          "xy_quad_get_state: layout");

@@ -257,14 +257,6 @@ __global__ void k_check_finite(const float* __restrict__ v, int64_t n, unsigned 
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
-int grid_for(int64_t n, int threads) {
-  int64_t b = (n + threads - 1) / threads;
-  const int64_t cap = 152 * 16;   // a few waves over the 152 SMs, grid-stride beyond
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
 template <int COLOUR, int MODE, int RED>
 cudaError_t launch_one(const HalfSweepArgs& a, cudaStream_t stream) {
   const dim3 grid((a.W + kTileCols - 1) / kTileCols, (a.L + kTileRows - 1) / kTileRows);
