@@ -79,9 +79,12 @@ enum { XY_SINCOS_ACCURATE = 0, XY_SINCOS_FAST = 1, XY_SINCOS_LIBM = 2 };
  *                      sweep s once its eight neighbouring tiles have finished
  *                      sweep s - 1 (per-tile counters in device memory, bounded
  *                      waits; a wait that runs out is reported as XY_ETIMEOUT
- *                      at the next synchronizing call).  Needs L % 128 == 0
- *                      and every CTA of the grid resident (the launch fails
- *                      with XY_ECUDA otherwise);
+ *                      at the next synchronizing call); a tile's staged rows
+ *                      are copied by TMA (tensor maps of the two buffers,
+ *                      encoded at xy_create: XY_ECUDA there if the driver's
+ *                      encoder is unavailable).  Needs L % 128 == 0 and every
+ *                      CTA of the grid resident (the launch fails with XY_ECUDA
+ *                      otherwise);
  *   XY_ALGO_FUSED2     two sweeps per launch (temporal blocking): each tile is
  *                      staged with a halo of four rows and columns and runs
  *                      both sweeps' half-sweeps in shared memory on shrinking

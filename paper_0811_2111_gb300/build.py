@@ -79,7 +79,7 @@ def build(force=False, verbose=False, extra=(), debug=False):
 
 
 
-def source_hash(files=("xy_fused.cu", "xy_device.cuh")):
+def source_hash(files=("xy_fused.cu", "xy_device.cuh", "xy_tma.cuh")):
     """Hash of a kernel's own source files under csrc/ (ties an ncu capture to
     the kernel version it measured; the default is the fused sweep kernel)."""
     import hashlib

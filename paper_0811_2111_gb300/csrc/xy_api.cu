@@ -70,6 +70,7 @@ struct xy_ctx {
   bool persistent;         // ... all sweeps of an xy_sweep call in one cooperative launch
   bool auto_persistent;    // chosen by XY_ALGO_AUTO: per-sweep launches if it does not fit
   unsigned int* d_tiles;   // the persistent launch's per-tile sweep counters
+  xyk::FusedMaps maps;     // ... and its TMA tensor maps of d_theta and d_pong
   unsigned int* d_wait;    // set by a persistent launch whose bounded wait ran out
   xy_record* d_rec;        // records [0, rec_cap)
   int64_t rec_cap;
@@ -377,6 +378,8 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
     e = xyk::dev_malloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
     if (e == cudaSuccess) e = xyk::dev_malloc(&c->d_wait, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wait, 0, sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess && !xyk::encode_fused_maps(&c->maps, c->d_theta, c->d_pong, p->L))
+      e = cudaErrorNotSupported;
   }
   if (e != cudaSuccess) {
     st = (e == cudaErrorMemoryAllocation) ? XY_ENOMEM : XY_ECUDA;
@@ -478,6 +481,7 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.beta = c->p.beta;
     a.flags = c->d_tiles;
     a.counter = c->d_tiles + xyk::fused_tiles(c->p.L);
+    a.maps = &c->maps;
     a.error = c->d_wait;
     a.spin_limit = xyk::fused_persistent_spin_limit();
     a.skip_items = 0;
@@ -697,7 +701,10 @@ xy_status xy_selftest_persistent_wait(void* cuda_stream, int64_t polls) {
     a.error = words + tiles + 1;
     a.spin_limit = (long long)polls;
     a.skip_items = tiles;
-    e = xyk::launch_fused_persistent(XY_SINCOS_ACCURATE, XY_REDUCE_EXACT, a, s);
+    xyk::FusedMaps maps;
+    a.maps = &maps;
+    if (!xyk::encode_fused_maps(&maps, a.buf[0], a.buf[1], L)) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = xyk::launch_fused_persistent(XY_SINCOS_ACCURATE, XY_REDUCE_EXACT, a, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(&err, a.error, sizeof(err), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -27,6 +27,7 @@
 
 #include "xy_device.cuh"
 #include "xy_internal.h"
+#include "xy_tma.cuh"
 
 namespace xyk {
 
@@ -69,13 +70,17 @@ constexpr size_t kCsbAt = kCsrAt + kCsrBytes;
 constexpr size_t kPartAt = kCsbAt + kCsbBytes;
 constexpr size_t kCntAt = kPartAt + kPartBytes;
 constexpr size_t kSmemBytes = kCntAt + kCntBytes;
-// The persistent kernel's next-tile buffer after them: the 64 float4-group
-// rows of the staging (black stage rows 0..35, red 1..28) as raw angles,
-// copied in by cp.async while the current tile's black half runs.
-constexpr size_t kRawAt = kSmemBytes;
-constexpr size_t kRawBytes = sizeof(float) * 64 * kTileK;
+// The persistent kernel's next-tile buffer after them (128-byte aligned, for
+// TMA): the 70 staged rows as raw angles, black stage rows 0..35 then red
+// stage rows 1..34, 64 plane columns each, written by cp.async.bulk.tensor
+// while the current tile's black half runs.
+constexpr int kRawRows = kSRows + kRedRows;
+constexpr size_t kRawAt = (kSmemBytes + 127) & ~(size_t)127;
+constexpr size_t kRawRowBytes = sizeof(float) * kTileK;
+constexpr size_t kRawBytes = kRawRowBytes * kRawRows;
 constexpr size_t kPersistSmemBytes = kRawAt + kRawBytes;
-static_assert(3 * (kPersistSmemBytes + 1024) <= 228 * 1024, "three persistent tiles must fit one SM");
+static_assert(3 * (kPersistSmemBytes + 1024 + 512) <= 228 * 1024,
+              "three persistent tiles (and their static shared memory) must fit one SM");
 static_assert(kThbAt % 16 == 0 && kCsrAt % 16 == 0 && kCsbAt % 16 == 0 && kPartAt % 16 == 0,
               "shared-memory regions must stay 16-byte aligned");
 static_assert(4 * (kSmemBytes + 1024) <= 228 * 1024, "four tiles must fit one SM");
@@ -130,13 +135,6 @@ __device__ __forceinline__ void pair_neighbours(const CsRow* nb, int i, int c0, 
     n.Ss[j] = xyd::nb_sum(n.l[j].y, n.r[j].y, n.d[j].y, n.u[j].y);
   }
 }
-
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ float4 ld4(const float2* p) {
   return *reinterpret_cast<const float4*>(p);
@@ -197,19 +195,20 @@ struct NoHook {
 };
 
 __device__ __forceinline__ unsigned char* smem_base() {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   return smem;
 }
 
 template <int MODE, int RED, bool COHERENT = false, bool PREF = false, class Args,
           class PreHook = NoHook, class MidHook = NoHook, class EndHook = NoHook,
-          class PostHook = NoHook>
+          class PostHook = NoHook, class RawWait = NoHook>
 __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk, int bx,
                                                  int by, const PreHook& pre = PreHook(),
                                                  const MidHook& mid = MidHook(),
                                                  const EndHook& end = EndHook(),
-                                                 const PostHook& post = PostHook()) {
-  extern __shared__ __align__(16) unsigned char smem[];
+                                                 const PostHook& post = PostHook(),
+                                                 const RawWait& raw_wait = RawWait()) {
+  extern __shared__ __align__(128) unsigned char smem[];
   ThRow* thr = reinterpret_cast<ThRow*>(smem);
   TbRow* thb = reinterpret_cast<TbRow*>(smem + kThbAt);
   CsRow* csr = reinterpret_cast<CsRow*>(smem + kCsrAt);
@@ -251,7 +250,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const bool has_tail = t < 192;
     const int tail_r = 29 + (t >> 5), tail_c = t & 31;
     float2 vt = make_float2(0.f, 0.f);
-    if (has_tail) {
+    if (has_tail && !PREF) {
       const size_t row = (size_t)wrap_once(y0 - 2 + tail_r, L) * W + k0 + 2 * tail_c;
       vt = COHERENT ? __ldcg(reinterpret_cast<const float2*>(a.src + row))
                     : __ldg(reinterpret_cast<const float2*>(a.src + row));
@@ -277,12 +276,14 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       }
     }
     if (PREF) {
-      // this thread's own float4 groups, copied in by cp.async (during the
-      // previous tile, or at this tile's start)
+      // the staged rows, written by TMA (during the previous tile, or at this
+      // tile's start): wait for them, then read this thread's groups and tail
       const float4* rawb = reinterpret_cast<const float4*>(smem + kRawAt);
-      cp_async_wait_all();
+      raw_wait();
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = rawb[((t >> 4) + 16 * i) * (kTileK / 4) + cg];
+      if (has_tail)
+        vt = reinterpret_cast<const float2*>(smem + kRawAt)[(64 + (t >> 5)) * (kTileK / 2) + tail_c];
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -519,17 +520,22 @@ __device__ __forceinline__ PersistItem decode_item(int item, int ntiles, int til
 // item at the start of a tile and decodes it before the staging barrier; the
 // last warp, idle while the first three update the red ring, looks at that
 // item's nine counters before the red/black barrier, and when all were set
-// every thread copies its share of the next tile's staging rows into shared
-// memory by cp.async while the black half runs (those counters' acquire
-// loads precede the barrier), and the next tile starts without waiting or a
-// barrier; otherwise the next tile waits and then issues the same copies
-// itself.  The arithmetic of a tile is fused_sweep_body's, so the result is
-// bit for bit that of n launches of k_sweep_fused.
+// its first lane has TMA copy the next tile's 70 staged rows (six boxes of
+// the buffer's tensor map, the wrapped rows at the lattice's first and last
+// tile rows as boxes of their own) into shared memory while the black half
+// runs, and the next tile starts without waiting or a barrier; otherwise the
+// next tile waits and then issues the same copies itself.  The copies
+// complete on one mbarrier, one phase per tile; each wait for it is bounded
+// too.  The arithmetic of a tile is fused_sweep_body's, so the result is bit
+// for bit that of n launches of k_sweep_fused.
 template <int MODE, int RED, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPersistArgs p) {
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_sweep_fused_persist(FusedPersistArgs p, const __grid_constant__ FusedMaps maps) {
   __shared__ int s_abort;
   __shared__ PersistItem s_item[2];  // this tile's item and the next (alternating)
   __shared__ int s_ready[2];         // the next item's nine counters were all seen set
+  __shared__ __align__(8) uint64_t s_bar;   // the raw buffer's TMA completion
+  constexpr int kIssuer = kThreads - 32;    // lane 0 of the last warp
   const int tiles_x = p.W / kTileK, tiles_y = p.L / kTileRows;
   const int ntiles = tiles_x * tiles_y;
   const int total = p.n_sweeps * ntiles;          // < 2^31 - 2^20 (the host splits longer runs)
@@ -545,10 +551,33 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
     s_item[0] = decode_item((int)atomicAdd(p.counter, 1u) + p.skip_items, ntiles, tiles_x,
                             tiles_y);
     s_ready[0] = 0;
+    xyt::mbar_init(&s_bar, 1);
+    xyt::fence_mbarrier_init();
   }
   __syncthreads();
   int par = 0;
+  uint32_t phase = 0;                // parity of the raw buffer's next completion
   PersistItem cur = s_item[0];
+  // the 70 staged rows of item `it` into the raw buffer (by kIssuer): black
+  // stage rows 0..35 (array rows L + y0 - 2 .. L + y0 + 33) to raw rows 0..35,
+  // red stage rows 1..34 (rows y0 - 1 .. y0 + 32) to raw rows 36..69; the
+  // 32 tile rows are one box, the rows above and below boxes of 2 (black) and
+  // 1 (red) at their wrapped positions
+  auto issue_raw = [&](const PersistItem& it) {
+    const int b = it.s & 1;
+    const int y0 = it.by * kTileRows, x = it.bx * kTileK;
+    unsigned char* raw = smem_base() + kRawAt;
+    xyt::fence_proxy_async_global();
+    xyt::mbar_arrive_expect_tx(&s_bar, (uint32_t)kRawBytes);
+    xyt::tma_load_2d(raw, &maps.m[b][1], x, p.L + wrap_once(y0 - 2, p.L), &s_bar);
+    xyt::tma_load_2d(raw + 2 * kRawRowBytes, &maps.m[b][2], x, p.L + y0, &s_bar);
+    xyt::tma_load_2d(raw + 34 * kRawRowBytes, &maps.m[b][1], x, p.L + wrap_once(y0 + kTileRows, p.L),
+                &s_bar);
+    xyt::tma_load_2d(raw + 36 * kRawRowBytes, &maps.m[b][0], x, wrap_once(y0 - 1, p.L), &s_bar);
+    xyt::tma_load_2d(raw + 37 * kRawRowBytes, &maps.m[b][2], x, y0, &s_bar);
+    xyt::tma_load_2d(raw + 69 * kRawRowBytes, &maps.m[b][0], x, wrap_once(y0 + kTileRows, p.L),
+                &s_bar);
+  };
   while (cur.item < total) {
     const int s = cur.s, bx = cur.bx, by = cur.by;
     // when the previous tile's early look found all nine counters set, this
@@ -586,25 +615,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
     c.sweep = p.sweep0 + (uint32_t)s;
     c.rec = p.rec + s;
     PersistItem* slot = &s_item[par ^ 1];
-    // this thread's float4 staging groups of item `it`, by cp.async into the
-    // raw buffer (the same rows and columns as its staging loads)
-    auto copy_groups = [&](const PersistItem& it) {
-      const int t = threadIdx.x, cg = t & 15;
-      const float* nsrc = p.buf[it.s & 1];
-      const int ny0 = it.by * kTileRows, nk0 = it.bx * kTileK;
-      const size_t plane = (size_t)p.L * (size_t)p.W;
-      float4* rawb = reinterpret_cast<float4*>(smem_base() + kRawAt);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int rr = (t >> 4) + 16 * i;
-        const int pl = rr < kSRows ? 1 : 0;
-        const int r = rr < kSRows ? rr : rr - kSRows + 1;
-        const size_t row = pl * plane + (size_t)wrap_once(ny0 - 2 + r, p.L) * p.W + nk0 + 4 * cg;
-        cp_async16(&rawb[rr * (kTileK / 4) + cg], nsrc + row);
-      }
-      cp_async_commit();
-    };
-    if (!ready) copy_groups(cur);
+    if (!ready && threadIdx.x == kIssuer) issue_raw(cur);
     fused_sweep_body<MODE, RED, true, true>(
         c, p.rk, bx, by,
         // before the staging barrier: the next item, decoded, to the other slot
@@ -616,7 +627,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
         // three update the ring): one early look at the next item's nine
         // counters, so that its wait usually costs nothing.  The acquire loads'
         // latency overlaps the ring instead of holding the CTA at its closing
-        // barrier.
+        // barrier.  When all were set, the warp's first lane issues the next
+        // tile's TMA copies at once (this tile's staging reads of the raw
+        // buffer ended at the staging barrier; __syncwarp orders the other
+        // lanes' acquire loads before its proxy fence)
         [&]() {
           if (threadIdx.x >= kThreads - 32) {
             const int l = threadIdx.x - (kThreads - 32);
@@ -627,18 +641,20 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_persist(FusedPer
               const int ny = wrap_once(ni.by + l / 3 - 1, tiles_y);
               ok = ni.s == 0 || load_acquire(p.flags + (ny * tiles_x + nx)) >= (unsigned int)ni.s;
             }
-            const unsigned int all = __ballot_sync(0xffffffffu, ok);
-            if (l == 0) s_ready[par ^ 1] = (all == 0xffffffffu) ? 1 : 0;
+            const bool all = __ballot_sync(0xffffffffu, ok) == 0xffffffffu;
+            __syncwarp();
+            if (l == 0) {
+              s_ready[par ^ 1] = all ? 1 : 0;
+              if (all) issue_raw(ni);
+            }
           }
         },
-        NoHook(),
-        // after the red/black barrier: when the next item's counters were all
-        // seen set, every thread copies the float4 groups it will stage for it
-        // into the raw buffer (the same rows and columns as its own staging
-        // loads), so the next tile's staging reads shared memory
+        NoHook(), NoHook(),
+        // the staging's wait for the raw buffer (bounded: a wait that runs out
+        // sets the error word, and the tile goes on with what is there)
         [&]() {
-          const PersistItem ni = *slot;
-          if (s_ready[par ^ 1] != 0 && ni.item < total) copy_groups(ni);
+          if (!xyt::mbar_wait_bounded(&s_bar, phase, p.spin_limit)) atomicOr(p.error, 1u);
+          phase ^= 1u;
         });
     if (threadIdx.x == kThreads - 64) {
       // a warp other than the pollers' publishes the tile: the closing barrier
@@ -711,7 +727,7 @@ cudaError_t prepare_one() {
 
 template <int MODE, int RED, int MINB>
 cudaError_t launch_persist_one(const FusedPersistArgs& a, int grid, cudaStream_t stream) {
-  void* args[] = {const_cast<FusedPersistArgs*>(&a)};
+  void* args[] = {const_cast<FusedPersistArgs*>(&a), const_cast<FusedMaps*>(a.maps)};
   return cudaLaunchCooperativeKernel(
       reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED, MINB>), dim3(grid),
       dim3(kThreads), args, kPersistSmemBytes, stream);
@@ -815,6 +831,26 @@ int fused_tiles(int L) { return fused_supported(L) ? (L / 2 / kTileK) * (L / kTi
 
 long long fused_persistent_spin_limit() { return kPersistSpinLimit; }
 
+bool encode_fused_maps(FusedMaps* out, const float* buf0, const float* buf1, int L) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || !out || !fused_supported(L)) return false;
+  const float* bufs[2] = {buf0, buf1};
+  const cuuint32_t rows[3] = {1u, 2u, (cuuint32_t)kTileRows};
+  const cuuint64_t dims[2] = {(cuuint64_t)(L / 2), (cuuint64_t)(2 * L)};   // [2 L][W]
+  const cuuint64_t strides[1] = {(cuuint64_t)(L / 2) * sizeof(float)};
+  const cuuint32_t elem[2] = {1u, 1u};
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 3; ++k) {
+      const cuuint32_t box[2] = {(cuuint32_t)kTileK, rows[k]};
+      if (enc(&out->m[b][k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(bufs[b]), dims,
+              strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+  return true;
+}
+
 int fused_persistent_max_sweeps(int L) {
   const int t = fused_tiles(L);
   // n x tiles items, plus one fetch past the end per CTA, stay below 2^31
@@ -825,7 +861,7 @@ cudaError_t launch_fused_persistent(int sincos_mode, int reduce_mode, const Fuse
                                     cudaStream_t stream) {
   if (!fused_supported(a.L) || a.W * 2 != a.L || a.n_sweeps < 1 ||
       a.n_sweeps > fused_persistent_max_sweeps(a.L) || !a.flags || a.counter != a.flags + fused_tiles(a.L) ||
-      !a.error || a.buf[0] == a.buf[1] || a.spin_limit < 1 || a.skip_items < 0 ||
+      !a.error || a.buf[0] == a.buf[1] || !a.maps || a.spin_limit < 1 || a.skip_items < 0 ||
       a.skip_items > a.n_sweeps * fused_tiles(a.L) || (a.minb < 2 || a.minb > 4))
     return cudaErrorInvalidValue;
   const bool comp = reduce_mode != 0;

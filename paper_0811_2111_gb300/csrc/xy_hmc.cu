@@ -27,6 +27,7 @@
 
 #include "xy_hmc_device.cuh"
 #include "xy_internal.h"
+#include "xy_tma.cuh"
 
 namespace xyk {
 
@@ -234,56 +235,6 @@ struct TmaGeom {
 };
 constexpr long long kSpinLimit = 1ll << 22;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Poll an mbarrier phase at most `limit` times; false if it never completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
-  for (long long i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_async_shared() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
 template <int MODE, int ROWS>
 __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     k_hmc_step_tma(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
@@ -331,20 +282,20 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
   auto issue = [&](int t, int s) {
     const int tt = tile_at(t);
     const int x0 = (tt % tiles_x) * kTileCols, y0 = (tt / tiles_x) * TR;
-    mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
-    tma_load_2d(stage_th(s), mth, x0, y0, &bar[s]);
-    tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
+    xyt::mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
+    xyt::tma_load_2d(stage_th(s), mth, x0, y0, &bar[s]);
+    xyt::tma_load_2d(stage_p(s), &mapp, x0, y0, &bar[s]);
     ++issued[s];
   };
   auto bounded_wait = [&](int s, uint32_t parity) {
-    return mbar_wait_bounded(&bar[s], parity, kSpinLimit);
+    return xyt::mbar_wait_bounded(&bar[s], parity, kSpinLimit);
   };
 
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_barrier_init();
-    fence_async_shared();
+    xyt::mbar_init(&bar[0], 1);
+    xyt::mbar_init(&bar[1], 1);
+    xyt::fence_mbarrier_init();
+    xyt::fence_async_shared();
     for (int s = 0; s < 2; ++s) {
       const int t = blockIdx.x + s * gridDim.x;
       if (t < n_tiles) issue(t, s);
@@ -420,7 +371,7 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<ROWS>::kMinBlocks)
     if (tid == 0 && ok) {
       const int tn = t + 2 * gridDim.x;
       if (tn < n_tiles) {
-        fence_async_shared();
+        xyt::fence_async_shared();
         issue(tn, s);
       }
     }
@@ -523,11 +474,6 @@ __device__ __forceinline__ void hmc_store_release(unsigned int* p, unsigned int 
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Orders what this thread observed through the generic proxy (the counters
-// and the data they publish) before its later async-proxy (TMA) reads.
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
 
 __device__ __forceinline__ int hmc_wrap_tile(int v, int n) {
   v += (v < 0) ? n : 0;
@@ -589,16 +535,16 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
     decode(item, &j, &tx, &ty);
     const int sb = src_of(j);
     const CUtensorMap* mth = sb == 0 ? &map0 : (sb == 1 ? &map1 : &map2);
-    fence_proxy_async_global();
-    mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
-    tma_load_2d(stage_th(s), mth, tx * kTileCols, ty * TR, &bar[s]);
-    tma_load_2d(stage_p(s), &mapp, tx * kTileCols, ty * TR, &bar[s]);
+    xyt::fence_proxy_async_global();
+    xyt::mbar_arrive_expect_tx(&bar[s], kTmaStageBytes);
+    xyt::tma_load_2d(stage_th(s), mth, tx * kTileCols, ty * TR, &bar[s]);
+    xyt::tma_load_2d(stage_p(s), &mapp, tx * kTileCols, ty * TR, &bar[s]);
     ++issued[s];
   };
   auto drain = [&]() {
     if (tid == 0)
       for (int s = 0; s < 2; ++s)
-        if (issued[s] > 0) (void)mbar_wait_bounded(&bar[s], (uint32_t)((issued[s] - 1) & 1),
+        if (issued[s] > 0) (void)xyt::mbar_wait_bounded(&bar[s], (uint32_t)((issued[s] - 1) & 1),
                                                    q.spin_limit);
   };
   // the previous tile, stored but not yet published (its counter slot and value)
@@ -613,10 +559,10 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
 
   if (tid == 0) {
     s_abort = 0;
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_barrier_init();
-    fence_async_shared();
+    xyt::mbar_init(&bar[0], 1);
+    xyt::mbar_init(&bar[1], 1);
+    xyt::fence_mbarrier_init();
+    xyt::fence_async_shared();
     for (int s = 0; s < 2; ++s) {
       const int item = blockIdx.x + s * gridDim.x;
       s_issued[s] = 0;
@@ -681,7 +627,7 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
       const int sx = tid < TR ? (x0 == 0 ? L - 1 : x0 - 1) : (x0 + kTileCols == L ? 0 : x0 + kTileCols);
       th_side = __ldcg(th_src + (size_t)(y0 + (tid % TR)) * L + sx);
     }
-    if (!mbar_wait_bounded(&bar[s], parity, q.spin_limit)) {
+    if (!xyt::mbar_wait_bounded(&bar[s], parity, q.spin_limit)) {
       atomicOr(&a.ctl->error, 1u);
       s_abort = 1;
     }
@@ -804,7 +750,7 @@ __global__ void __launch_bounds__(kTileThreads, TmaGeom<4>::kMinBlocks)
         // the stores they publish visible to thread 0, and issue()'s proxy
         // fence to its TMA reads
         fence_acq_rel_gpu();
-        fence_async_shared();
+        xyt::fence_async_shared();
         issue(next, s);
         s_issued[s] = 1;
       }
@@ -1426,11 +1372,11 @@ namespace {
 __global__ void k_selftest_wait(unsigned int* error, long long polls) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    fence_barrier_init();
+    xyt::mbar_init(&bar, 1);
+    xyt::fence_mbarrier_init();
   }
   __syncthreads();
-  const bool done = mbar_wait_bounded(&bar, 0u, polls);   // no arrival: must run out
+  const bool done = xyt::mbar_wait_bounded(&bar, 0u, polls);   // no arrival: must run out
   if (!done && threadIdx.x == 0) atomicOr(error, 1u);
 }
 }  // namespace

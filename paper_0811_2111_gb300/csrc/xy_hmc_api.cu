@@ -125,6 +125,10 @@ xy_status check(const xy_hmc* h) {
   return XY_OK;
 }
 
+}  // namespace
+
+namespace xyk {
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -142,9 +146,13 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+}  // namespace xyk
+
+namespace {
+
 // Tensor map of one L x L float buffer, boxes of box_rows rows x 128 columns.
 bool encode_map(CUtensorMap* m, float* base, int L, int box_rows) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = xyk::tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)L};
   const cuuint64_t strides[1] = {(cuuint64_t)L * sizeof(float)};

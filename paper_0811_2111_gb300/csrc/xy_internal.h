@@ -2,6 +2,8 @@
 // kernel translation units.  Not part of the public C ABI.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -95,6 +97,21 @@ struct QuadFusedArgs {
   double beta[4];
 };
 
+// cuTensorMapEncodeTiled from the driver (through the runtime's entry-point
+// query; nullptr if unavailable).  Host only.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+// TMA tensor maps of the persistent sweep's two state buffers, each read as
+// one [2 L][W] float array (row p L + y: colour p, lattice row y), boxes of 64
+// plane columns and 1, 2 or 32 rows ([buffer][box]).
+struct FusedMaps {
+  CUtensorMap m[2][3];
+};
+
+// Encodes them for buffers buf0, buf1 of side L (host only; false if the
+// encoder is unavailable or refuses the buffers).
+bool encode_fused_maps(FusedMaps* out, const float* buf0, const float* buf1, int L);
+
 // All n sweeps of one lattice in one cooperative launch of the fused sweep
 // (tiles wait on their eight neighbours' per-tile sweep counters).
 struct FusedPersistArgs {
@@ -118,6 +135,7 @@ struct FusedPersistArgs {
   int skip_items;        // work items not handed out (0; > 0 only to test the
                          // failure path: their counters are then never set)
   int minb = 3;          // resident CTAs per SM the kernel is compiled for (2, 3 or 4)
+  const FusedMaps* maps = nullptr;   // tensor maps of buf[0], buf[1] (host memory, required)
 };
 
 // The default bound of the persistent kernel's waits, in polls (about a second).
