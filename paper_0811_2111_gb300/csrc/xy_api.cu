@@ -70,8 +70,8 @@ struct xy_ctx {
   bool persistent;         // ... all sweeps of an xy_sweep call in one cooperative launch
   bool auto_persistent;    // chosen by XY_ALGO_AUTO: per-sweep launches if it does not fit
   unsigned int* d_tiles;   // the persistent launch's per-tile sweep counters
-  xyk::FusedMaps maps;     // ... and its TMA tensor maps of d_theta and d_pong
-  unsigned int* d_wait;    // set by a persistent launch whose bounded wait ran out
+  xyk::FusedMaps maps;     // TMA tensor maps of d_theta and d_pong (fused kernels)
+  unsigned int* d_wait;    // set by a fused launch whose bounded wait ran out
   xy_record* d_rec;        // records [0, rec_cap)
   int64_t rec_cap;
   int64_t rec_count;       // records enqueued so far
@@ -254,13 +254,14 @@ cudaError_t timed_fused2(xy_ctx* c, const xyk::FusedArgs& a) {
   return e;
 }
 
-// After a synchronize: whether a persistent launch's bounded wait ran out.
+// After a synchronize: whether a fused launch's bounded wait ran out.
 xy_status check_waits(xy_ctx* c, const char* where) {
-  if (!c->persistent || !c->d_wait) return XY_OK;
+  if (!c->d_wait) return XY_OK;
   unsigned int w = 0;
   XY_CUDA(c, cudaMemcpyAsync(&w, c->d_wait, sizeof(w), cudaMemcpyDeviceToHost, c->stream), where);
   XY_CUDA(c, cudaStreamSynchronize(c->stream), where);
-  if (w) return fail(c, XY_ETIMEOUT, "%s: a persistent sweep's wait for a neighbouring tile ran out",
+  if (w) return fail(c, XY_ETIMEOUT,
+                     "%s: a fused sweep's bounded wait (a neighbouring tile, or its staged rows) ran out",
                      where);
   return XY_OK;
 }
@@ -373,14 +374,15 @@ xy_status xy_create(const xy_params* p, void* cuda_stream, void* d_angles, xy_ct
   c->auto_persistent = c->persistent && p->algorithm == XY_ALGO_AUTO;
   c->fused = p->algorithm == XY_ALGO_FUSED || p->algorithm == XY_ALGO_FUSED2 ||
              c->persistent || (p->algorithm == XY_ALGO_AUTO && xyk::fused_supported(p->L));
-  if (e == cudaSuccess && c->fused) e = xyk::dev_malloc(&c->d_pong, N * sizeof(float));
-  if (e == cudaSuccess && c->persistent) {
-    e = xyk::dev_malloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
+  if (e == cudaSuccess && c->fused) {
+    e = xyk::dev_malloc(&c->d_pong, N * sizeof(float));
     if (e == cudaSuccess) e = xyk::dev_malloc(&c->d_wait, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_wait, 0, sizeof(unsigned int), c->stream);
     if (e == cudaSuccess && !xyk::encode_fused_maps(&c->maps, c->d_theta, c->d_pong, p->L))
       e = cudaErrorNotSupported;
   }
+  if (e == cudaSuccess && c->persistent)
+    e = xyk::dev_malloc(&c->d_tiles, sizeof(unsigned int) * ((size_t)xyk::fused_tiles(p->L) + 1));
   if (e != cudaSuccess) {
     st = (e == cudaErrorMemoryAllocation) ? XY_ENOMEM : XY_ECUDA;
     set_thread_msg("xy_create: %s (%s)", cudaGetErrorName(e), cudaGetErrorString(e));
@@ -508,6 +510,8 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
         f.lattice_id = a.lattice_id;
         f.beta = a.beta;
         f.minb = a.minb;
+        f.maps = &c->maps;
+        f.error = c->d_wait;
         for (int64_t i = 0; i < m; ++i) {
           f.src = a.buf[i & 1];
           f.dst = a.buf[(i + 1) & 1];
@@ -542,6 +546,8 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     // with the SFU intrinsics (a tie) or compensated sums (188.3 against 186.3)
     const bool four = c->p.reduce_mode == XY_REDUCE_EXACT && c->p.sincos_mode != XY_SINCOS_FAST;
     a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : (four ? 4 : 3);
+    a.maps = &c->maps;
+    a.error = c->d_wait;
     float* cur = c->d_theta;
     float* nxt = c->d_pong;
     const bool two = c->p.algorithm == XY_ALGO_FUSED2;

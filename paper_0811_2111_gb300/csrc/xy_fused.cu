@@ -40,50 +40,48 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kSRows = kTileRows + 4;        // stage rows: global rows y0-2 .. y0+33
 constexpr int kRedRows = kSRows - 2;         // the red plane's stage rows 1 .. 34
 
-// Shared memory of a tile, 55.1 KB (four CTAs fit an SM).  Stage row r is
+// Shared memory of a tile, 55.3 KB (four CTAs fit an SM).  Stage row r is
 // global row y0 - 2 + r.  Only what the tile reads is kept:
-//   thr  red angles of stage rows 1..34, plane cols k0-4 .. k0+67 (column
-//        k - k0 + kThOff, so the staged float4 groups are 16-byte aligned;
-//        k0-1 .. k0+64 used)
-//   thb  black angles of the tile rows (stage rows 2..33), plane cols k0 .. k0+63
-//   csr  red unit vectors (cos, sin) of stage rows 1..34, plane cols k0-2 ..
-//        k0+65 (column k - k0 + kCsOff: lane l's pair at 2l + 2 is 16-byte
-//        aligned; k0-1 .. k0+64 used)
-//   csb  black unit vectors of stage rows 0..35, same columns
-// then the commit's per-warp partial sums and counters.
+//   ang   raw angles of the 70 staged rows, 64 plane columns each: black
+//         stage rows 0..35 as rows 0..35, red stage rows 1..34 as rows
+//         36..69 (the layout TMA writes; 128-byte aligned)
+//   angs  red angles of the halo columns k0-1 and k0+64, stage rows 1..34
+//   csr   red unit vectors (cos, sin) of stage rows 1..34, plane cols k0-2 ..
+//         k0+65 (column k - k0 + kCsOff: lane l's pair at 2l + 2 is 16-byte
+//         aligned; k0-1 .. k0+64 used)
+//   csb   black unit vectors of stage rows 0..35, same columns
+// then the commit's per-warp partial sums and counters.  The persistent
+// kernel keeps NANG = 2 ang buffers: the next tile's rows arrive in the other.
 constexpr int kCsOff = 2;
-constexpr int kThOff = 4;
 constexpr int kCsCols = kTileK + 4;
-constexpr int kThCols = kTileK + 8;
+constexpr int kRawRows = kSRows + kRedRows;
+constexpr int kRedRaw0 = kSRows - 1;        // ang row of red stage row r: kRedRaw0 + r
 typedef float2 CsRow[kCsCols];
-typedef float ThRow[kThCols];
-typedef float TbRow[kTileK];
-constexpr size_t kThrBytes = sizeof(ThRow) * kRedRows;
-constexpr size_t kThbBytes = sizeof(TbRow) * kTileRows;
+typedef float AngRow[kTileK];
+constexpr size_t kRawRowBytes = sizeof(AngRow);
+constexpr size_t kAngBytes = kRawRowBytes * kRawRows;
+constexpr size_t kAngsBytes = sizeof(float) * 2 * kRedRows;
 constexpr size_t kCsrBytes = sizeof(CsRow) * kRedRows;
 constexpr size_t kCsbBytes = sizeof(CsRow) * kSRows;
 constexpr size_t kPartBytes = sizeof(float) * kWarps * 5 * 2;
 constexpr size_t kCntBytes = sizeof(unsigned int) * kWarps;
-constexpr size_t kThbAt = kThrBytes;
-constexpr size_t kCsrAt = kThbAt + kThbBytes;
-constexpr size_t kCsbAt = kCsrAt + kCsrBytes;
-constexpr size_t kPartAt = kCsbAt + kCsbBytes;
-constexpr size_t kCntAt = kPartAt + kPartBytes;
-constexpr size_t kSmemBytes = kCntAt + kCntBytes;
-// The persistent kernel's next-tile buffer after them (128-byte aligned, for
-// TMA): the 70 staged rows as raw angles, black stage rows 0..35 then red
-// stage rows 1..34, 64 plane columns each, written by cp.async.bulk.tensor
-// while the current tile's black half runs.
-constexpr int kRawRows = kSRows + kRedRows;
-constexpr size_t kRawAt = (kSmemBytes + 127) & ~(size_t)127;
-constexpr size_t kRawRowBytes = sizeof(float) * kTileK;
-constexpr size_t kRawBytes = kRawRowBytes * kRawRows;
-constexpr size_t kPersistSmemBytes = kRawAt + kRawBytes;
+template <int NANG>
+struct Layout {
+  static constexpr size_t kAngsAt = NANG * kAngBytes;
+  static constexpr size_t kCsrAt = kAngsAt + kAngsBytes;
+  static constexpr size_t kCsbAt = kCsrAt + kCsrBytes;
+  static constexpr size_t kPartAt = kCsbAt + kCsbBytes;
+  static constexpr size_t kCntAt = kPartAt + kPartBytes;
+  static constexpr size_t kBytes = kCntAt + kCntBytes;
+  static_assert(kAngBytes % 128 == 0 && kCsrAt % 16 == 0 && kCsbAt % 16 == 0 && kPartAt % 16 == 0,
+                "shared-memory regions must stay aligned (ang: 128 bytes for TMA)");
+};
+constexpr size_t kSmemBytes = Layout<1>::kBytes;
+constexpr size_t kPersistSmemBytes = Layout<2>::kBytes;
+static_assert(4 * (kSmemBytes + 1024 + 128) <= 228 * 1024,
+              "four tiles (and their static shared memory) must fit one SM");
 static_assert(3 * (kPersistSmemBytes + 1024 + 512) <= 228 * 1024,
               "three persistent tiles (and their static shared memory) must fit one SM");
-static_assert(kThbAt % 16 == 0 && kCsrAt % 16 == 0 && kCsbAt % 16 == 0 && kPartAt % 16 == 0,
-              "shared-memory regions must stay 16-byte aligned");
-static_assert(4 * (kSmemBytes + 1024) <= 228 * 1024, "four tiles must fit one SM");
 
 // Tiles of one sweep of side L (L % 128 == 0).
 inline int fused_tiles_of(int L) { return (L / 2 / kTileK) * (L / kTileRows); }
@@ -160,7 +158,7 @@ struct FusedCore {
 // One red ring site at stage row r, unit-vector column c: the tile sites'
 // arithmetic, with the site's own Philox block.
 template <int MODE, class Args>
-__device__ __forceinline__ void red_ring_site(ThRow* thr, CsRow* csr, const CsRow* csb, int r,
+__device__ __forceinline__ void red_ring_site(float th, CsRow* csr, const CsRow* csb, int r,
                                               int c, int q, uint32_t site, uint32_t x,
                                               const Args& a, const xyd::RoundKeys& rk) {
   const float2 l = csb[r][c + q - 1], rt = csb[r][c + q];
@@ -171,8 +169,8 @@ __device__ __forceinline__ void red_ring_site(ThRow* thr, CsRow* csr, const CsRo
       make_uint4(xyd::metropolis_counter(site, x), a.sweep, a.lattice_id, 1u), rk);
   const uint2 uw = xyd::metropolis_words(w, x);
   const float2 own = csr[r - 1][c];
-  const xyd::SiteResult res = xyd::metropolis_step<MODE>(thr[r - 1][c + kThOff - kCsOff], own.x,
-                                                         own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
+  const xyd::SiteResult res =
+      xyd::metropolis_step<MODE>(th, own.x, own.y, Sc, Ss, uw.x, uw.y, a.K, a.delta);
   csr[r - 1][c] = make_float2(res.c, res.s);   // the black half reads the unit vector only
 }
 
@@ -182,14 +180,15 @@ __device__ __forceinline__ void red_ring_site(ThRow* thr, CsRow* csr, const CsRo
 // and persistent kernels); both have the fields used here.  COHERENT: the
 // source was written earlier in the same launch by other CTAs (persistent
 // kernel), so it is read through L2 (ld.global.cg) rather than the
-// non-coherent path.  PREF: the staging's float4 groups (rows 0..63 of the
-// staged 70) are not loaded here but read from the raw buffer in shared
-// memory, where the caller had each thread copy its own groups by cp.async
-// (the persistent kernel does so for the next tile while the current one runs
-// its black half).  `pre` runs in every thread before the barrier that ends
-// the staging, `mid` before the barrier between the red and the black half,
-// `post` right after that barrier, `end` after the tile's last store to dst
-// and before the CTA's closing barrier.
+// non-coherent path.  TMA: the 70 staged rows of raw angles are not loaded
+// here but arrive in the ang buffer by TMA, issued by the caller (the per-sweep
+// kernel at its start, the persistent kernel during the previous tile);
+// `raw_wait` waits for them.  Otherwise each thread loads its rows and stores
+// them there itself.  NANG: ang buffers in the layout (the persistent kernel's
+// two alternate, `ang_sel` picks this tile's).  `pre` runs in every thread
+// before the barrier that ends the staging, `mid` before the barrier between
+// the red and the black half, `post` right after that barrier, `end` after the
+// tile's last store to dst and before the CTA's closing barrier.
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
@@ -199,22 +198,24 @@ __device__ __forceinline__ unsigned char* smem_base() {
   return smem;
 }
 
-template <int MODE, int RED, bool COHERENT = false, bool PREF = false, class Args,
+template <int MODE, int RED, bool COHERENT = false, bool TMA = false, int NANG = 1, class Args,
           class PreHook = NoHook, class MidHook = NoHook, class EndHook = NoHook,
           class PostHook = NoHook, class RawWait = NoHook>
 __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::RoundKeys& rk, int bx,
-                                                 int by, const PreHook& pre = PreHook(),
+                                                 int by, int ang_sel = 0,
+                                                 const PreHook& pre = PreHook(),
                                                  const MidHook& mid = MidHook(),
                                                  const EndHook& end = EndHook(),
                                                  const PostHook& post = PostHook(),
                                                  const RawWait& raw_wait = RawWait()) {
+  using Lay = Layout<NANG>;
   extern __shared__ __align__(128) unsigned char smem[];
-  ThRow* thr = reinterpret_cast<ThRow*>(smem);
-  TbRow* thb = reinterpret_cast<TbRow*>(smem + kThbAt);
-  CsRow* csr = reinterpret_cast<CsRow*>(smem + kCsrAt);
-  CsRow* csb = reinterpret_cast<CsRow*>(smem + kCsbAt);
-  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + kPartAt);
-  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + kCntAt);
+  AngRow* ang = reinterpret_cast<AngRow*>(smem + (size_t)ang_sel * kAngBytes);
+  float* angs = reinterpret_cast<float*>(smem + Lay::kAngsAt);     // [34][2]
+  CsRow* csr = reinterpret_cast<CsRow*>(smem + Lay::kCsrAt);
+  CsRow* csb = reinterpret_cast<CsRow*>(smem + Lay::kCsbAt);
+  float(*part)[5][2] = reinterpret_cast<float(*)[5][2]>(smem + Lay::kPartAt);
+  unsigned int* cnt = reinterpret_cast<unsigned int*>(smem + Lay::kCntAt);
 
   const int L = a.L, W = a.W;
   const int k0 = bx * kTileK;
@@ -235,7 +236,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const int t = (int)threadIdx.x;
     const int cg = t & 15;
     float4 v[4];
-    if (!PREF) {
+    if (!TMA) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int rr = (t >> 4) + 16 * i;
@@ -250,7 +251,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const bool has_tail = t < 192;
     const int tail_r = 29 + (t >> 5), tail_c = t & 31;
     float2 vt = make_float2(0.f, 0.f);
-    if (has_tail && !PREF) {
+    if (has_tail && !TMA) {
       const size_t row = (size_t)wrap_once(y0 - 2 + tail_r, L) * W + k0 + 2 * tail_c;
       vt = COHERENT ? __ldcg(reinterpret_cast<const float2*>(a.src + row))
                     : __ldg(reinterpret_cast<const float2*>(a.src + row));
@@ -258,7 +259,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     // halo sites h = 0..135: plane h / 68, stage row 1 + (h % 68) / 2, side h & 1
     const int nh = t >= 192 ? 2 : (t >= 184 ? 1 : 0);
     float vh[2] = {0.f, 0.f};
-    int hp[2] = {0, 0}, hr[2] = {0, 0}, hcol[2] = {0, 0};
+    int hp[2] = {0, 0}, hr[2] = {0, 0}, hside[2] = {0, 0};
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       if (j < nh) {
@@ -271,19 +272,18 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
         const int kk = side ? wrap_once(k0 + kTileK, W) : wrap_once(k0 - 1, W);
         hp[j] = p;
         hr[j] = r;
-        hcol[j] = side ? kCsOff + kTileK : kCsOff - 1;
+        hside[j] = side;
         vh[j] = COHERENT ? __ldcg(a.src + row + kk) : __ldg(a.src + row + kk);
       }
     }
-    if (PREF) {
-      // the staged rows, written by TMA (during the previous tile, or at this
-      // tile's start): wait for them, then read this thread's groups and tail
-      const float4* rawb = reinterpret_cast<const float4*>(smem + kRawAt);
+    if (TMA) {
+      // the staged rows, written by TMA: wait for them, then read this
+      // thread's groups and tail
       raw_wait();
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = rawb[((t >> 4) + 16 * i) * (kTileK / 4) + cg];
-      if (has_tail)
-        vt = reinterpret_cast<const float2*>(smem + kRawAt)[(64 + (t >> 5)) * (kTileK / 2) + tail_c];
+      for (int i = 0; i < 4; ++i)
+        v[i] = *reinterpret_cast<const float4*>(&ang[(t >> 4) + 16 * i][4 * cg]);
+      if (has_tail) vt = *reinterpret_cast<const float2*>(&ang[64 + (t >> 5)][2 * tail_c]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -295,12 +295,11 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       xyd::unit_vector<MODE>(v[i].y, &s1, &c1);
       xyd::unit_vector<MODE>(v[i].z, &s2, &c2);
       xyd::unit_vector<MODE>(v[i].w, &s3, &c3);
-      // angles are kept only for the sites the tile updates: the red rows and
-      // the black tile rows 2..33 (uniform over each half warp)
-      if (p == 0)
-        *reinterpret_cast<float4*>(&thr[r - 1][kThOff + 4 * cg]) = v[i];
-      else if (r >= 2 && r < kSRows - 2)
-        *reinterpret_cast<float4*>(&thb[r - 2][4 * cg]) = v[i];
+      // the group's angles go to its ang row (staged row rr) unless TMA put
+      // them there; only the red rows and the black tile rows 2..33 are read
+      // (uniform over each half warp)
+      if (!TMA && (p == 0 || (r >= 2 && r < kSRows - 2)))
+        *reinterpret_cast<float4*>(&ang[rr][4 * cg]) = v[i];
       float2* u = p ? &csb[r][kCsOff + 4 * cg] : &csr[r - 1][kCsOff + 4 * cg];
       st4(u, make_float4(c0, s0, c1, s1));
       st4(u + 2, make_float4(c2, s2, c3, s3));
@@ -309,7 +308,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       float s0, c0, s1, c1;
       xyd::unit_vector<MODE>(vt.x, &s0, &c0);
       xyd::unit_vector<MODE>(vt.y, &s1, &c1);
-      *reinterpret_cast<float2*>(&thr[tail_r - 1][kThOff + 2 * tail_c]) = vt;
+      if (!TMA) *reinterpret_cast<float2*>(&ang[64 + (t >> 5)][2 * tail_c]) = vt;
       st4(&csr[tail_r - 1][kCsOff + 2 * tail_c], make_float4(c0, s0, c1, s1));
     }
 #pragma unroll
@@ -317,11 +316,12 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
       if (j < nh) {
         float sv, cv;
         xyd::unit_vector<MODE>(vh[j], &sv, &cv);
+        const int hcol = hside[j] ? kCsOff + kTileK : kCsOff - 1;
         if (hp[j] == 0) {                                  // red side-ring angles
-          thr[hr[j] - 1][hcol[j] + kThOff - kCsOff] = vh[j];
-          csr[hr[j] - 1][hcol[j]] = make_float2(cv, sv);
+          angs[2 * (hr[j] - 1) + hside[j]] = vh[j];
+          csr[hr[j] - 1][hcol] = make_float2(cv, sv);
         } else {
-          csb[hr[j]][hcol[j]] = make_float2(cv, sv);
+          csb[hr[j]][hcol] = make_float2(cv, sv);
         }
       }
     }
@@ -352,7 +352,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
     // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
     const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const float2 t = *reinterpret_cast<const float2*>(&thr[r - 1][c0 + kThOff - kCsOff]);
+    const float2 t = *reinterpret_cast<const float2*>(&ang[kRedRaw0 + r][2 * lane]);
     const float4 o = ld4(&csr[r - 1][c0]);
     const xyd::SiteResult r0 =
         xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
@@ -378,7 +378,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     pair_neighbours(csb, r, c0, q, ld4(&csb[r - 1][c0]), ld4(&csb[r][c0]), U, n);
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
     const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const float2 t = *reinterpret_cast<const float2*>(&thr[r - 1][c0 + kThOff - kCsOff]);
+    const float2 t = *reinterpret_cast<const float2*>(&ang[kRedRaw0 + r][2 * lane]);
     const float4 o = ld4(&csr[r - 1][c0]);
     const xyd::SiteResult r0 =
         xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
@@ -392,7 +392,8 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const int k = wrap_once(k0 + tk, W);
     const int q = y & 1;
     const uint32_t x = 2u * (uint32_t)k + (uint32_t)q;
-    red_ring_site<MODE>(thr, csr, csb, ty + 2, tk + kCsOff, q, (uint32_t)y * uL + x, x, a, rk);
+    red_ring_site<MODE>(angs[2 * (ty + 1) + (tk < 0 ? 0 : 1)], csr, csb, ty + 2, tk + kCsOff, q,
+                        (uint32_t)y * uL + x, x, a, rk);
   }
   mid();
   __syncthreads();
@@ -419,7 +420,7 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
     const uint32_t site0 = (uint32_t)y * uL + 2u * (uint32_t)kp + (uint32_t)q;
     // sites x and x + 2 of the pair (kp even, so x & 2 == 0): one block
     const uint4 w = xyd::philox4x32_10(make_uint4(site0, a.sweep, a.lattice_id, 1u), rk);
-    const float2 t = *reinterpret_cast<const float2*>(&thb[r - 2][c0 - kCsOff]);
+    const float2 t = *reinterpret_cast<const float2*>(&ang[r][2 * lane]);
     const float4 o = ld4(&csb[r][c0]);
     const xyd::SiteResult r0 =
         xyd::metropolis_step<MODE>(t.x, o.x, o.y, n.Sc[0], n.Ss[0], w.x, w.y, a.K, a.delta);
@@ -443,13 +444,60 @@ __device__ __forceinline__ void fused_sweep_body(const Args& a, const xyd::Round
                                       bx == 0 && by == 0);
 }
 
+// Polls of a neighbour's flag or of the staging's mbarrier before a wait gives
+// up (about a second in all).
+constexpr long long kPersistSpinLimit = 1ll << 22;
+
+// The TMA tensor maps of one state buffer read as a [2 L][W] float array
+// (row p L + y: colour p, lattice row y), boxes of 64 plane columns and 1, 2
+// and 32 rows; kernel parameters (__grid_constant__).
+struct SweepMaps {
+  CUtensorMap m[3];
+};
+struct PersistMaps {
+  CUtensorMap m[2][3];   // of buf[0] and buf[1]
+};
+
+// The 70 staged rows of the tile at plane column x, rows y0.. into the ang
+// buffer `dst` by TMA, completing on `bar` (one thread): black stage rows
+// 0..35 (rows L + y0 - 2 .. L + y0 + 33) to ang rows 0..35, red stage rows
+// 1..34 (rows y0 - 1 .. y0 + 32) to ang rows 36..69; the 32 tile rows of each
+// plane are one box, the rows above and below boxes of 2 (black) and 1 (red)
+// at their wrapped positions, so the lattice's first and last tile rows need
+// no special case.  x is a multiple of 64 floats (256 bytes).
+__device__ __forceinline__ void issue_tile_rows(uint64_t* bar, unsigned char* dst,
+                                                const CUtensorMap* m, int x, int y0, int L) {
+  xyt::mbar_arrive_expect_tx(bar, (uint32_t)kAngBytes);
+  xyt::tma_load_2d(dst, &m[1], x, L + wrap_once(y0 - 2, L), bar);
+  xyt::tma_load_2d(dst + 2 * kRawRowBytes, &m[2], x, L + y0, bar);
+  xyt::tma_load_2d(dst + 34 * kRawRowBytes, &m[1], x, L + wrap_once(y0 + kTileRows, L), bar);
+  xyt::tma_load_2d(dst + 36 * kRawRowBytes, &m[0], x, wrap_once(y0 - 1, L), bar);
+  xyt::tma_load_2d(dst + 37 * kRawRowBytes, &m[2], x, y0, bar);
+  xyt::tma_load_2d(dst + 69 * kRawRowBytes, &m[0], x, wrap_once(y0 + kTileRows, L), bar);
+}
+
 // MINB: CTAs per SM the kernel is compiled for (4: at most 64 registers a
 // thread, 32 warps per SM; 3: at most 80; 2: at most 128, more independent
-// work in flight per warp, 16 warps).  The tile's 55.1 KB of shared memory
-// let four CTAs share an SM.
+// work in flight per warp, 16 warps).  The tile's 55.3 KB of shared memory
+// let four CTAs share an SM.  Thread 0 has TMA copy the tile's staged rows
+// while every thread loads its halo sites; a bounded wait for them that runs
+// out sets *a.error.
 template <int MODE, int RED, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused(FusedArgs a) {
-  fused_sweep_body<MODE, RED>(a, a.rk, blockIdx.x, blockIdx.y);
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_sweep_fused(FusedArgs a, const __grid_constant__ SweepMaps maps) {
+  __shared__ __align__(8) uint64_t s_bar;
+  if (threadIdx.x == 0) {
+    xyt::mbar_init(&s_bar, 1);
+    xyt::fence_mbarrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    issue_tile_rows(&s_bar, smem_base(), maps.m, blockIdx.x * kTileK, blockIdx.y * kTileRows, a.L);
+  fused_sweep_body<MODE, RED, false, true>(
+      a, a.rk, blockIdx.x, blockIdx.y, 0, NoHook(), NoHook(), NoHook(), NoHook(), [&]() {
+        if (!xyt::mbar_wait_bounded(&s_bar, 0u, kPersistSpinLimit) && a.error)
+          atomicOr(a.error, 1u);
+      });
 }
 
 // Many lattices of one side in one launch (blockIdx.z = lattice of the group),
@@ -469,9 +517,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_sweep_fused_batch(FusedBatch
   fused_sweep_body<MODE, RED>(c, b.rk, blockIdx.x, blockIdx.y);
 }
 
-// Polls of a neighbour's flag before a wait gives up (with a short sleep
-// between polls: about a second in all).
-constexpr long long kPersistSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ unsigned int load_acquire(const unsigned int* p) {
   unsigned int v;
@@ -520,21 +565,20 @@ __device__ __forceinline__ PersistItem decode_item(int item, int ntiles, int til
 // item at the start of a tile and decodes it before the staging barrier; the
 // last warp, idle while the first three update the red ring, looks at that
 // item's nine counters before the red/black barrier, and when all were set
-// its first lane has TMA copy the next tile's 70 staged rows (six boxes of
-// the buffer's tensor map, the wrapped rows at the lattice's first and last
-// tile rows as boxes of their own) into shared memory while the black half
-// runs, and the next tile starts without waiting or a barrier; otherwise the
+// its first lane has TMA copy the next tile's 70 staged rows (issue_tile_rows)
+// into the other of the CTA's two ang buffers while the ring and the black
+// half run, and the next tile starts without waiting or a barrier; otherwise the
 // next tile waits and then issues the same copies itself.  The copies
 // complete on one mbarrier, one phase per tile; each wait for it is bounded
 // too.  The arithmetic of a tile is fused_sweep_body's, so the result is bit
 // for bit that of n launches of k_sweep_fused.
 template <int MODE, int RED, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
-    k_sweep_fused_persist(FusedPersistArgs p, const __grid_constant__ FusedMaps maps) {
+    k_sweep_fused_persist(FusedPersistArgs p, const __grid_constant__ PersistMaps maps) {
   __shared__ int s_abort;
   __shared__ PersistItem s_item[2];  // this tile's item and the next (alternating)
   __shared__ int s_ready[2];         // the next item's nine counters were all seen set
-  __shared__ __align__(8) uint64_t s_bar;   // the raw buffer's TMA completion
+  __shared__ __align__(8) uint64_t s_bar;   // the staged rows' TMA completion
   constexpr int kIssuer = kThreads - 32;    // lane 0 of the last warp
   const int tiles_x = p.W / kTileK, tiles_y = p.L / kTileRows;
   const int ntiles = tiles_x * tiles_y;
@@ -556,27 +600,14 @@ __global__ void __launch_bounds__(kThreads, MINB)
   }
   __syncthreads();
   int par = 0;
-  uint32_t phase = 0;                // parity of the raw buffer's next completion
+  uint32_t phase = 0;                // parity of the staged rows' next completion
   PersistItem cur = s_item[0];
-  // the 70 staged rows of item `it` into the raw buffer (by kIssuer): black
-  // stage rows 0..35 (array rows L + y0 - 2 .. L + y0 + 33) to raw rows 0..35,
-  // red stage rows 1..34 (rows y0 - 1 .. y0 + 32) to raw rows 36..69; the
-  // 32 tile rows are one box, the rows above and below boxes of 2 (black) and
-  // 1 (red) at their wrapped positions
-  auto issue_raw = [&](const PersistItem& it) {
-    const int b = it.s & 1;
-    const int y0 = it.by * kTileRows, x = it.bx * kTileK;
-    unsigned char* raw = smem_base() + kRawAt;
+  // the 70 staged rows of item `it` into ang buffer `buf` (by kIssuer; the
+  // tile with item slot par uses ang buffer par)
+  auto issue_raw = [&](const PersistItem& it, int buf) {
     xyt::fence_proxy_async_global();
-    xyt::mbar_arrive_expect_tx(&s_bar, (uint32_t)kRawBytes);
-    xyt::tma_load_2d(raw, &maps.m[b][1], x, p.L + wrap_once(y0 - 2, p.L), &s_bar);
-    xyt::tma_load_2d(raw + 2 * kRawRowBytes, &maps.m[b][2], x, p.L + y0, &s_bar);
-    xyt::tma_load_2d(raw + 34 * kRawRowBytes, &maps.m[b][1], x, p.L + wrap_once(y0 + kTileRows, p.L),
-                &s_bar);
-    xyt::tma_load_2d(raw + 36 * kRawRowBytes, &maps.m[b][0], x, wrap_once(y0 - 1, p.L), &s_bar);
-    xyt::tma_load_2d(raw + 37 * kRawRowBytes, &maps.m[b][2], x, y0, &s_bar);
-    xyt::tma_load_2d(raw + 69 * kRawRowBytes, &maps.m[b][0], x, wrap_once(y0 + kTileRows, p.L),
-                &s_bar);
+    issue_tile_rows(&s_bar, smem_base() + (size_t)buf * kAngBytes, maps.m[it.s & 1],
+                    it.bx * kTileK, it.by * kTileRows, p.L);
   };
   while (cur.item < total) {
     const int s = cur.s, bx = cur.bx, by = cur.by;
@@ -615,9 +646,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
     c.sweep = p.sweep0 + (uint32_t)s;
     c.rec = p.rec + s;
     PersistItem* slot = &s_item[par ^ 1];
-    if (!ready && threadIdx.x == kIssuer) issue_raw(cur);
-    fused_sweep_body<MODE, RED, true, true>(
-        c, p.rk, bx, by,
+    if (!ready && threadIdx.x == kIssuer) issue_raw(cur, par);
+    fused_sweep_body<MODE, RED, true, true, 2>(
+        c, p.rk, bx, by, par,
         // before the staging barrier: the next item, decoded, to the other slot
         // (the atomic was issued before the staging loads, so it has returned)
         [&]() {
@@ -628,9 +659,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
         // counters, so that its wait usually costs nothing.  The acquire loads'
         // latency overlaps the ring instead of holding the CTA at its closing
         // barrier.  When all were set, the warp's first lane issues the next
-        // tile's TMA copies at once (this tile's staging reads of the raw
-        // buffer ended at the staging barrier; __syncwarp orders the other
-        // lanes' acquire loads before its proxy fence)
+        // tile's TMA copies at once, into the ang buffer the previous tile
+        // used (free since that tile's closing barrier; __syncwarp orders the
+        // other lanes' acquire loads before its proxy fence)
         [&]() {
           if (threadIdx.x >= kThreads - 32) {
             const int l = threadIdx.x - (kThreads - 32);
@@ -645,12 +676,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
             __syncwarp();
             if (l == 0) {
               s_ready[par ^ 1] = all ? 1 : 0;
-              if (all) issue_raw(ni);
+              if (all) issue_raw(ni, par ^ 1);
             }
           }
         },
         NoHook(), NoHook(),
-        // the staging's wait for the raw buffer (bounded: a wait that runs out
+        // the staging's wait for its rows (bounded: a wait that runs out
         // sets the error word, and the tile goes on with what is there)
         [&]() {
           if (!xyt::mbar_wait_bounded(&s_bar, phase, p.spin_limit)) atomicOr(p.error, 1u);
@@ -669,6 +700,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
 
 template <int MODE, int RED, int MINB>
 cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
+  const int b = a.maps ? fused_map_index(*a.maps, a.src) : -1;
+  if (b < 0) return cudaErrorInvalidValue;
+  SweepMaps sm;
+  for (int k = 0; k < 3; ++k) sm.m[k] = a.maps->m[b][k];
   static bool configured[64] = {};   // attributes set once per instantiation and device
   int dev = 0;
   cudaError_t ge = cudaGetDevice(&dev);
@@ -684,7 +719,7 @@ cudaError_t launch_fused_one(const FusedArgs& a, cudaStream_t stream) {
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
   const dim3 grid(a.W / kTileK, a.L / kTileRows);
-  k_sweep_fused<MODE, RED, MINB><<<grid, kThreads, kSmemBytes, stream>>>(a);
+  k_sweep_fused<MODE, RED, MINB><<<grid, kThreads, kSmemBytes, stream>>>(a, sm);
   return cudaGetLastError();
 }
 
@@ -727,7 +762,14 @@ cudaError_t prepare_one() {
 
 template <int MODE, int RED, int MINB>
 cudaError_t launch_persist_one(const FusedPersistArgs& a, int grid, cudaStream_t stream) {
-  void* args[] = {const_cast<FusedPersistArgs*>(&a), const_cast<FusedMaps*>(a.maps)};
+  // the maps in buf order (the caller may have swapped the two buffers)
+  PersistMaps pm;
+  for (int b = 0; b < 2; ++b) {
+    const int i = fused_map_index(*a.maps, a.buf[b]);
+    if (i < 0) return cudaErrorInvalidValue;
+    for (int k = 0; k < 3; ++k) pm.m[b][k] = a.maps->m[i][k];
+  }
+  void* args[] = {const_cast<FusedPersistArgs*>(&a), &pm};
   return cudaLaunchCooperativeKernel(
       reinterpret_cast<const void*>(&k_sweep_fused_persist<MODE, RED, MINB>), dim3(grid),
       dim3(kThreads), args, kPersistSmemBytes, stream);
@@ -835,6 +877,8 @@ bool encode_fused_maps(FusedMaps* out, const float* buf0, const float* buf1, int
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc || !out || !fused_supported(L)) return false;
   const float* bufs[2] = {buf0, buf1};
+  out->base[0] = buf0;
+  out->base[1] = buf1;
   const cuuint32_t rows[3] = {1u, 2u, (cuuint32_t)kTileRows};
   const cuuint64_t dims[2] = {(cuuint64_t)(L / 2), (cuuint64_t)(2 * L)};   // [2 L][W]
   const cuuint64_t strides[1] = {(cuuint64_t)(L / 2) * sizeof(float)};

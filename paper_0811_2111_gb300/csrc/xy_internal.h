@@ -62,6 +62,8 @@ struct HalfSweepArgs {
   double beta;           // stored in the record by the black half
 };
 
+struct FusedMaps;
+
 // Arguments of one fused sweep (both colours and the measure) src -> dst.
 struct FusedArgs {
   const float* src;      // [2][L][W] state before the sweep
@@ -76,6 +78,8 @@ struct FusedArgs {
   xy_record* rec;
   double beta;
   int minb = 3;          // tile kernel instances per SM (2, 3 or 4: the register budget)
+  const FusedMaps* maps = nullptr;   // tensor maps of src (required; host memory)
+  unsigned int* error = nullptr;     // set nonzero if the wait for the staged rows runs out
 };
 
 // Whether the fused kernel handles side L (L a positive multiple of 128).
@@ -101,16 +105,22 @@ struct QuadFusedArgs {
 // query; nullptr if unavailable).  Host only.
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
-// TMA tensor maps of the persistent sweep's two state buffers, each read as
-// one [2 L][W] float array (row p L + y: colour p, lattice row y), boxes of 64
-// plane columns and 1, 2 or 32 rows ([buffer][box]).
+// TMA tensor maps of the fused sweep's two state buffers, each read as one
+// [2 L][W] float array (row p L + y: colour p, lattice row y), boxes of 64
+// plane columns and 1, 2 or 32 rows ([buffer][box]); host memory.
 struct FusedMaps {
   CUtensorMap m[2][3];
+  const float* base[2];  // the buffers they describe
 };
 
 // Encodes them for buffers buf0, buf1 of side L (host only; false if the
 // encoder is unavailable or refuses the buffers).
 bool encode_fused_maps(FusedMaps* out, const float* buf0, const float* buf1, int L);
+
+// Which of the two buffers p is (0 or 1), -1 if neither.
+inline int fused_map_index(const FusedMaps& m, const float* p) {
+  return p == m.base[0] ? 0 : (p == m.base[1] ? 1 : -1);
+}
 
 // All n sweeps of one lattice in one cooperative launch of the fused sweep
 // (tiles wait on their eight neighbours' per-tile sweep counters).

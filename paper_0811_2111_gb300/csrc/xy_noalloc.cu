@@ -87,7 +87,13 @@ xy_status xy_sweep_noalloc(const xy_params* p, float* d_angles, uint32_t first_s
   e = cudaMemsetAsync(d_records, 0, (size_t)n_sweeps * sizeof(xy_record), stream);
   if (e != cudaSuccess) return fail(XY_ECUDA, cudaGetErrorString(e));
 
+  // the tile kernel's staged rows come by TMA: tensor maps of both buffers
+  xyk::FusedMaps maps;
+  if (!xyk::encode_fused_maps(&maps, d_angles, pong, p->L))
+    return fail(XY_ECUDA, "tensor maps of the state buffers could not be encoded");
+
   xyk::FusedArgs a;
+  a.maps = &maps;
   a.L = p->L;
   a.W = p->L / 2;
   a.K = (float)(p->beta * p->J);
