@@ -125,11 +125,11 @@ typedef struct {
                              tile kernel per SM (at most 80 registers a thread), 4 (at
                              most 64: more warps per SM), 2 (at most 128: more
                              independent work in flight per warp, fewer warps), or 0
-                             for the library's default: 3 for the persistent sweep;
-                             for one fused launch per sweep 4 with XY_REDUCE_EXACT
-                             and accurate or libm sincos, else 3 (the faster plan at
-                             L = 8192 and 16384).  Results do not depend on it;
-                             tuning callers time the plans (autotune.py). */
+                             for the library's default: 3 for the persistent sweep,
+                             4 for one fused launch per sweep (the faster plans at
+                             L = 4096 and at L = 8192, 16384).  Results do not
+                             depend on it; tuning callers time the plans
+                             (autotune.py). */
 } xy_params;
 
 /* Per-sweep record as stored on the device (64 bytes).  The five sums are

@@ -540,12 +540,11 @@ xy_status xy_sweep(xy_ctx* c, int64_t n) {
     a.rk = rk;
     a.lattice_id = c->p.lattice_id;
     a.beta = c->p.beta;
-    // default plan of one launch per sweep, measured at L = 8192 and 16384:
-    // 4 CTAs per SM with exact sums and the accurate or libm unit vectors
-    // (210.8 against 207.8 and 176.0 against 166.5 G updates/s at 16384), 3
-    // with the SFU intrinsics (a tie) or compensated sums (188.3 against 186.3)
-    const bool four = c->p.reduce_mode == XY_REDUCE_EXACT && c->p.sincos_mode != XY_SINCOS_FAST;
-    a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : (four ? 4 : 3);
+    // default plan of one launch per sweep: 4 CTAs per SM, the faster plan at
+    // L = 8192 and 16384 for every precision mode (at 16384, against 3:
+    // accurate 217.8 / 213.3, SFU 295.0 / 283.4, libm 185.9 / 171.4,
+    // compensated sums 187.6 / 186.9 G updates/s)
+    a.minb = c->p.ctas_per_sm ? c->p.ctas_per_sm : 4;
     a.maps = &c->maps;
     a.error = c->d_wait;
     float* cur = c->d_theta;
