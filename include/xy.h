@@ -374,7 +374,9 @@ const char *xy_batch_last_error(const xy_batch *b);
 
 /* Unit vectors (cos, sin) of n device angles with the sweep kernels' own
  * sincos of precision `sincos_mode` (accuracy checks against CUDA and FP64):
- * d_theta, d_cos, d_sin are device arrays of n floats; runs on cuda_stream. */
+ * d_theta, d_cos, d_sin are device arrays of n floats; runs on cuda_stream.
+ * XY_SINCOS_ACCURATE takes angles in [-pi/4, 2 pi + pi/4] (the sweeps keep
+ * theirs in [0, 2 pi)); the other modes any finite angle. */
 xy_status xy_eval_unit_vector(int32_t sincos_mode, const float *d_theta, float *d_cos,
                               float *d_sin, int64_t n, void *cuda_stream);
 

@@ -114,7 +114,7 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 
 namespace xyd {
 
-// Unit vector of an angle in [0, 2 pi] (or a little outside), written from the
+// Unit vector of an angle in [0, 2 pi] (or up to pi/4 outside), written from the
 // mathematics: Cody-Waite reduction by pi/2 (W. J. Cody, W. Waite, "Software
 // Manual for the Elementary Functions", 1980) with a two-part constant whose
 // high part has three trailing zero bits (so q * hi is exact for |q| <= 7),
@@ -129,8 +129,7 @@ constexpr float kRoundMagic = 12582912.0f;               // 1.5 * 2^23: x + M - 
 
 __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out) {
   const float qt = __fmaf_rn(t, kTwoOverPi, kRoundMagic);
-  const int q = __float_as_int(qt);                       // low bits = rint(t * 2/pi)
-  const float qf = __fsub_rn(qt, kRoundMagic);
+  const float qf = __fsub_rn(qt, kRoundMagic);            // q = rint(t * 2/pi)
   float r = __fmaf_rn(-qf, kPio2Hi, t);                   // exact
   r = __fmaf_rn(-qf, kPio2Lo, r);
   const float r2 = __fmul_rn(r, r);
@@ -143,15 +142,17 @@ __device__ __forceinline__ void sincos_poly(float t, float* s_out, float* c_out)
   pc = __fmaf_rn(r2, pc, 0.04166662320494652f);
   pc = __fmaf_rn(r2, pc, -0.5f);
   const float cr = __fmaf_rn(r2, pc, 1.0f);
-  // quadrant: odd q swaps sin and cos; sin is negative for q mod 4 in {2, 3}
-  // (bit 1 of q) and cos for q mod 4 in {1, 2} (bit 1 of q + 1); both sign
-  // masks come from q << 30 (bit 31 = bit 1 of q).
-  const uint32_t qs = (uint32_t)q << 30;
-  const bool swap = (q & 1) != 0;
-  const float s0 = swap ? cr : sr;
-  const float c0 = swap ? sr : cr;
-  *s_out = __uint_as_float(__float_as_uint(s0) ^ (qs & 0x80000000u));
-  *c_out = __uint_as_float(__float_as_uint(c0) ^ ((qs + 0x40000000u) & 0x80000000u));
+  // quadrant, on the FMA pipes (the ALU pipe is the sweep kernels' busiest):
+  // with p = q - 2 in {-2, ..., 2} (t in [-pi/4, 2 pi + pi/4]),
+  // t = r + p pi/2 + pi, so (sin t, cos t) = -(a sr + b cr, a cr - b sr) with
+  // a = cos(p pi/2) = 1 - |p| and b = sin(p pi/2) = p (2 - |p|), both in
+  // {-1, 0, 1} and never both nonzero: every product and sum is exact, the
+  // same bits as swapping and negating sr and cr by the bits of q.
+  const float pq = __fsub_rn(qf, 2.0f);
+  const float a = __fsub_rn(1.0f, fabsf(pq));
+  const float b = __fmul_rn(pq, __fsub_rn(2.0f, fabsf(pq)));
+  *s_out = __fmaf_rn(-a, sr, __fmul_rn(-b, cr));
+  *c_out = __fmaf_rn(b, sr, __fmul_rn(-a, cr));
 }
 
 // Precision switch of the kernels: 0 = the polynomial above with CUDA's

@@ -193,7 +193,7 @@ def test_sincos_polynomial_constants_are_the_fit():
     cs, es, cc, ec = fs.fit()
     assert es < 2e-9 and ec < 1e-10
     src = open(os.path.join(ROOT, "paper_0811_2111_gb300", "csrc", "xy_device.cuh")).read()
-    body = src[src.index("sincos_poly"):src.index("quadrant: odd q")]
+    body = src[src.index("sincos_poly"):src.index("// quadrant")]
     consts = [float(v) for v in re.findall(r"(-?\d+\.\d+(?:e-?\d+)?)f", body)]
     for v in list(cs) + list(cc):
         assert any(np.float32(v) == np.float32(k) for k in consts), v
