@@ -221,6 +221,42 @@ def test_sincos_polynomial_constants_are_the_fit():
     assert worst < 7e-8, worst
 
 
+def test_fma_pipe_quadrant_step_gives_the_bits_of_the_swap_and_sign_step():
+    """The accurate unit vector's quadrant step runs on the FMA pipes as
+    -(a sr + b cr, a cr - b sr) with p = q - 2, a = 1 - |p|, b = p (2 - |p|):
+    FP32 products with a, b in {-1, 0, 1}, never both nonzero, are exact, so
+    the result is bit for bit the swap of (sr, cr) on odd q and the sign flips
+    by bits 1 of q and q + 1, including signed zeros; checked for every q the
+    angles in [-pi/4, 2 pi + pi/4] give, over the values the polynomials
+    return on |r| <= pi/4: cr = cos r in [0.70, 1] and sr = sin r in
+    [-0.71, 0.71], +0 included (sr is never -0: r = -0 gives r^3 ps = +0 as
+    ps < 0, and -0 + +0 = +0).  With a cr or sr of -0 the two forms would
+    differ in the sign of a zero."""
+    import numpy as np
+    f32 = np.float32
+    rng = np.random.default_rng(5)
+    srs = np.concatenate([rng.uniform(-0.71, 0.71, 20000), [0.0, np.float32(1e-30),
+                                                           -np.float32(1e-30), 0.7071068]])
+    crs = np.concatenate([rng.uniform(0.70, 1.0, 20000), [1.0, 0.7071068, 0.9999999, 0.75]])
+    srs, crs = srs.astype(np.float32), crs.astype(np.float32)
+
+    def fma(x, y, z):      # one FP32 rounding of the exact x * y + z
+        return f32(np.float64(x) * np.float64(y) + np.float64(z))
+
+    for q in range(0, 5):
+        pq = f32(f32(q) - f32(2.0))
+        a = f32(f32(1.0) - abs(pq))
+        b = f32(pq * f32(f32(2.0) - abs(pq)))
+        for sr, cr in zip(srs, crs):
+            s_fma = fma(-a, sr, f32(-b * cr))
+            c_fma = fma(b, sr, f32(-a * cr))
+            s0, c0 = (cr, sr) if q & 1 else (sr, cr)
+            s_bit = -s0 if (q & 2) else s0
+            c_bit = -c0 if ((q + 1) & 2) else c0
+            assert np.float32(s_fma).tobytes() == np.float32(s_bit).tobytes(), (q, sr, cr)
+            assert np.float32(c_fma).tobytes() == np.float32(c_bit).tobytes(), (q, sr, cr)
+
+
 def test_peak_measure_refuses_bad_arguments_before_the_device(lib):
     rate = C.c_double()
     for kind, iters, reps in ((-1, 16, 1), (len(X.PEAK_KINDS), 16, 1), (0, 0, 1),
