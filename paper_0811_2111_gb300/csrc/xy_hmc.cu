@@ -803,6 +803,8 @@ constexpr size_t kP2PreRowsAt = kP2Smem;
 constexpr size_t kP2PreScalarsAt = kP2PreRowsAt + sizeof(float4) * 2 * kP2Band * kP2Threads;
 constexpr size_t kP2SmemPref = kP2PreScalarsAt + sizeof(float) * 6 * kP2Threads;
 static_assert(2 * (kP2SmemPref + 1024) <= 228 * 1024, "two tile-walking CTAs must fit one SM");
+static_assert(kP2PreRowsAt % 128 == 0 && 2 * kP2Band * kP2Threads * 4 == 2 * kP2Rows * kP2Cols,
+              "the TMA boxes (two of 32 x 128 floats) fill the 128-byte aligned row slots");
 // The tile-walking form runs when every resident CTA gets at least this many
 // tiles of a launch (measured per unit trajectory: 3.44 against 3.56 ms at
 // L = 4096, 17.8 against 18.9 at 8192; a tie at 2048, about 3.4 tiles per
@@ -839,9 +841,18 @@ __device__ __forceinline__ void hmc_site_step(float c, float s, float Sc, float 
 // tile's loads into its own shared-memory slots by cp.async right after the
 // current tile's staging barrier, so they arrive while the two steps run.
 // Both forms run the same arithmetic on the same values: bit-identical.
+// The tile-walking form's tensor maps (boxes of 32 rows x 128 columns): the
+// three angle buffers (the launch reads the one the control block names) and
+// the momenta it reads; a kernel parameter.
+struct Tile2Maps {
+  CUtensorMap th[3];
+  CUtensorMap p;
+};
+
 template <int MODE, bool PREF>
-__global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__global__ void __launch_bounds__(kP2Threads, 2)
+    k_hmc_tile2(HmcArgs a, const __grid_constant__ Tile2Maps maps) {
+  extern __shared__ __align__(128) unsigned char smem[];
   float (*fc)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem);
   float (*fs)[kFrCols] = reinterpret_cast<float (*)[kFrCols]>(smem + sizeof(float) * kFrRows * kFrCols);
   float4* pre_rows = reinterpret_cast<float4*>(smem + kP2PreRowsAt);   // [2 * kP2Band][threads]
@@ -855,16 +866,25 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
   const float* __restrict__ th_src = hmc_buf(a, src);
 
   const int rb = kP2Band * warp;                             // first tile row of the band
-  // the loads of tile t into this thread's slots (PREF): the same sites, in
-  // the same order, as the loads in the tile loop below
+  // the loads of tile t (PREF): the tile's angle and momentum rows as two
+  // TMA boxes of 32 x 128 (thread 0, completing on s_bar), and this thread's
+  // ring and halo sites by cp.async into its own slots: the same sites as the
+  // loads in the tile loop below
+  __shared__ __align__(8) uint64_t s_bar;
+  uint32_t phase = 0;
+  if (PREF) {
+    if (tid == 0) {
+      xyt::mbar_init(&s_bar, 1);
+      xyt::fence_mbarrier_init();
+    }
+    __syncthreads();
+  }
   auto prefetch = [&](int t) {
     const int px0 = (t % tiles_x) * kP2Cols, py0 = (t / tiles_x) * kP2Rows;
-    const int pxb = px0 + 4 * lane;
-#pragma unroll
-    for (int r = 0; r < kP2Band; ++r) {
-      const size_t g = (size_t)(py0 + rb + r) * L + pxb;
-      hmc_cp16(&pre_rows[r * kP2Threads + tid], th_src + g);
-      hmc_cp16(&pre_rows[(kP2Band + r) * kP2Threads + tid], a.p_in + g);
+    if (tid == 0) {
+      xyt::mbar_arrive_expect_tx(&s_bar, (uint32_t)(2 * sizeof(float) * kP2Rows * kP2Cols));
+      xyt::tma_load_2d(pre_rows, &maps.th[src], px0, py0, &s_bar);
+      xyt::tma_load_2d(pre_rows + kP2Rows * kP2Cols / 4, &maps.p, px0, py0, &s_bar);
     }
     const int ay = tid < kP2Cols ? -1 : kP2Rows, ax = tid & (kP2Cols - 1);
     const size_t ga = (size_t)wrap_near(py0 + ay, L) * L + (px0 + ax);
@@ -905,12 +925,19 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_hmc_tile2(HmcArgs a) {
   // memory
   const int xb = x0 + 4 * lane;
   float4 t4[kP2Band], p4[kP2Band];
-  if (PREF) asm volatile("cp.async.wait_all;" ::: "memory");
+  if (PREF) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!xyt::mbar_wait_bounded(&s_bar, phase, kSpinLimit)) atomicOr(&a.ctl->error, 1u);
+    phase ^= 1u;
+  }
 #pragma unroll
   for (int r = 0; r < kP2Band; ++r) {
     const size_t g = (size_t)(y0 + rb + r) * L + xb;
-    t4[r] = PREF ? pre_rows[r * kP2Threads + tid] : *reinterpret_cast<const float4*>(th_src + g);
-    p4[r] = PREF ? pre_rows[(kP2Band + r) * kP2Threads + tid]
+    // the boxes: rows of 128 floats, the thread's 4 x 4 block at row rb + r,
+    // columns 4 lane .. 4 lane + 3
+    t4[r] = PREF ? pre_rows[(rb + r) * (kP2Cols / 4) + lane]
+                 : *reinterpret_cast<const float4*>(th_src + g);
+    p4[r] = PREF ? pre_rows[(kP2Rows + rb + r) * (kP2Cols / 4) + lane]
                  : *reinterpret_cast<const float4*>(a.p_in + g);
   }
   // ring site A: row -1 (tid < 128) or 32, column tid & 127
@@ -1214,23 +1241,34 @@ __global__ void k_hmc_canon_reset(HmcCtl* ctl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctl->cur = 0u;
 }
 
+// Two full steps per launch: two CTAs per SM (the registers' limit); the
+// tile-walking form when each would get at least kP2PrefMinTilesPerCta tiles
+// and the tensor maps are given, else one tile per CTA.
+template <int MODE>
+cudaError_t launch_step2(const HmcArgs& a, const CUtensorMap* th_maps, const CUtensorMap* p_map,
+                         cudaStream_t stream) {
+  if (!a.tiled || !a.pairs || a.p_in == a.p_out) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int n_tiles = (a.L / kP2Cols) * (a.L / kP2Rows);
+  Tile2Maps m;
+  if (th_maps && p_map && n_tiles >= kP2PrefMinTilesPerCta * 2 * sms) {
+    for (int i = 0; i < 3; ++i) m.th[i] = th_maps[i];
+    m.p = *p_map;
+    k_hmc_tile2<MODE, true><<<2 * sms, kP2Threads, kP2SmemPref, stream>>>(a, m);
+  } else {
+    memset(&m, 0, sizeof(m));
+    k_hmc_tile2<MODE, false>
+        <<<dim3(a.L / kP2Cols, a.L / kP2Rows), kP2Threads, kP2Smem, stream>>>(a, m);
+  }
+  return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_mode(int kind, const HmcArgs& a, cudaStream_t stream) {
-  if (kind == kHmcStep2) {
-    if (!a.tiled || !a.pairs || a.p_in == a.p_out) return cudaErrorInvalidValue;
-    // two CTAs per SM (the registers' limit); the tile-walking form when each
-    // would get at least kP2PrefMinTilesPerCta tiles
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int n_tiles = (a.L / kP2Cols) * (a.L / kP2Rows);
-    if (n_tiles >= kP2PrefMinTilesPerCta * 2 * sms)
-      k_hmc_tile2<MODE, true><<<2 * sms, kP2Threads, kP2SmemPref, stream>>>(a);
-    else
-      k_hmc_tile2<MODE, false><<<dim3(a.L / kP2Cols, a.L / kP2Rows), kP2Threads, kP2Smem, stream>>>(a);
-    return cudaGetLastError();
-  }
+  if (kind == kHmcStep2) return launch_step2<MODE>(a, nullptr, nullptr, stream);
   if (a.tiled) {
     const dim3 grid(a.L / kTileCols, a.L / kTileRows);
     switch (kind) {
@@ -1285,6 +1323,18 @@ cudaError_t hmc_prepare(int sincos_mode) {
 
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[m][dev] = true;
   return e;
+}
+
+cudaError_t launch_hmc_step2(int sincos_mode, const HmcArgs& a, const void* th_maps3,
+                             const void* p_map, cudaStream_t stream) {
+  if (!hmc_tiled_ok(a.L)) return cudaErrorInvalidValue;
+  const CUtensorMap* tm = static_cast<const CUtensorMap*>(th_maps3);
+  const CUtensorMap* pm = static_cast<const CUtensorMap*>(p_map);
+  switch (sincos_mode) {
+    case 0: return launch_step2<0>(a, tm, pm, stream);
+    case 1: return launch_step2<1>(a, tm, pm, stream);
+    default: return launch_step2<2>(a, tm, pm, stream);
+  }
 }
 
 cudaError_t launch_hmc(int kind, int sincos_mode, const HmcArgs& a, cudaStream_t stream) {

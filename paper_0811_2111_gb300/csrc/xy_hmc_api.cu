@@ -54,7 +54,7 @@ void tmsg(const char* fmt, ...) {
 }  // namespace
 
 struct xy_hmc {
-  alignas(64) CUtensorMap maps[4];   // TMA maps: angle buffers 0..2, momenta (32 x 128 boxes)
+  CUtensorMap maps[5];               // TMA maps (32 x 128 boxes): angle buffers 0..2, d_p, d_p2
   bool use_tma;
   bool use_persist;                  // a trajectory's steps in one cooperative TMA launch
   unsigned int* d_tiles;             // its per-tile step counters
@@ -257,7 +257,10 @@ cudaError_t enqueue_trajectory(const xy_hmc* h, int begin, int n, int mode, cuda
     if (a.pairs && left >= 2) {
       a.p_in = pcur;
       a.p_out = pother;
-      e = xyk::launch_hmc(xyk::kHmcStep2, m, a, s);
+      // the tile-walking form reads its rows by TMA: the angle buffers' maps
+      // and that of the momenta it reads
+      e = h->use_tma ? xyk::launch_hmc_step2(m, a, h->maps, pcur == h->d_p ? &h->maps[3] : &h->maps[4], s)
+                     : xyk::launch_hmc(xyk::kHmcStep2, m, a, s);
       float* t = pcur;
       pcur = pother;
       pother = t;
@@ -429,6 +432,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
   h->use_pairs = p->kernel == XY_HMC_KERNEL_TILED2 ||
                  (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster && xyk::hmc_tiled_ok(p->L));
   const bool want_tma = p->kernel == XY_HMC_KERNEL_TILED_TMA || p->kernel == XY_HMC_KERNEL_PERSISTENT ||
+                        p->kernel == XY_HMC_KERNEL_TILED2 ||
                         (p->kernel == XY_HMC_KERNEL_AUTO && !h->use_cluster &&
                          xyk::hmc_tiled_ok(p->L));
   if (e == cudaSuccess && want_tma) {
@@ -439,6 +443,7 @@ xy_status xy_hmc_create(const xy_hmc_params* p, void* cuda_stream, void* d_angle
     h->tma_rows = 32;   // 32 x 128 tiles measured faster than 16 x 128 (54.1 vs 57.4 us per step)
     for (int i = 0; i < 3 && ok; ++i) ok = encode_map(&h->maps[i], h->th[i], p->L, h->tma_rows);
     if (ok) ok = encode_map(&h->maps[3], h->d_p, p->L, h->tma_rows);
+    if (ok) ok = encode_map(&h->maps[4], h->d_p2, p->L, h->tma_rows);
     // AUTO falls back to the plain tiled kernel without the encoder
     if (e == cudaSuccess && !ok && p->kernel == XY_HMC_KERNEL_TILED_TMA) e = cudaErrorNotSupported;
     h->use_tma = ok;

@@ -445,6 +445,12 @@ cudaError_t launch_hmc_steps_persist(int sincos_mode, const HmcStepsArgs& q, con
 int hmc_persist_tiles(int L);
 long long hmc_persist_spin_limit();
 
+// Two full steps in one launch (kHmcStep2) with the tensor maps (32 x 128
+// boxes) of the three angle buffers and of a.p_in, which the tile-walking form
+// reads by TMA; launch_hmc(kHmcStep2, ...) runs without them.
+cudaError_t launch_hmc_step2(int sincos_mode, const HmcArgs& a, const void* th_maps3,
+                             const void* p_map, cudaStream_t stream);
+
 cudaError_t launch_hmc_step_tma(int sincos_mode, const HmcArgs& a, const void* maps4, int box_rows,
                                 int ctas, cudaStream_t stream);
 
