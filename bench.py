@@ -530,9 +530,9 @@ HMC_BYTES_PER_SITE_STEP = 8.0
 # neighbour sums 6, the force 3, kick and drift 2, the wrap into [0, 2 pi) 8.
 HMC_ALG_INSTR_PER_SITE_STEP = {"accurate": 44.0, "fast": 22.0, "libm": 46.0}
 # DRAM bytes of one L = 4096 two-step launch (ncu, caches flushed before the
-# capture: 134.4 MB read, 83.7 MB written; profiles/hmc_tile2_L4096_full.md),
+# capture: 134.4 MB read, 83.9 MB written; profiles/hmc_tile2_L4096_full.md),
 # per step.
-HMC_DRAM_BYTES_PER_STEP = 218.1e6 / 2
+HMC_DRAM_BYTES_PER_STEP = 218.2e6 / 2
 
 
 def measure_hmc(dev, sincos, trajectories=40, cpu_seconds=2.0, issue_per_sm_clk=None,

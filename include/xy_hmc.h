@@ -75,7 +75,8 @@ typedef struct {
  * begin and final launches as TILED); TILED2 runs the full steps two per
  * launch (temporal blocking: half the DRAM traffic, a recomputed halo of two;
  * where every resident CTA gets at least four tiles, L >= 4096, two CTAs per
- * SM walk the tiles and copy the next tile's loads in ahead);
+ * SM walk the tiles and bring the next tile's rows in ahead by TMA, which
+ * needs the driver's tensor-map encoder: without it one tile per CTA runs);
  * SITE is one thread per site (any L); CLUSTER runs a whole trajectory in one
  * launch of one thread-block cluster that keeps the lattice in shared memory
  * (L a power of two in [16, 256]; strips of 16 rows per CTA, neighbouring strips
