@@ -795,10 +795,10 @@ constexpr int kP2Band = kP2Rows / kP2Warps;                  // 4 rows per warp
 constexpr int kFrRows = kP2Rows + 4;                         // tile rows -2 .. 33
 constexpr int kFrCols = kP2Cols + 8;                         // tile columns -4 .. 131
 constexpr size_t kP2Smem = sizeof(float) * 2 * kFrRows * kFrCols;
-// The tile-walking form (PREF) adds each thread's slots for the next tile's
-// loads, copied in by cp.async while the current tile runs: its 4 angle and 4
-// momentum float4 rows, then six scalars (ring site A's angle and momentum,
-// ring site B's, the halo-two sites H and G).
+// The tile-walking form (PREF) adds the next tile's loads, brought in while the
+// current tile runs: its angle and momentum rows as two TMA boxes of 32 x 128
+// floats, then each thread's six scalars by cp.async (ring site A's angle and
+// momentum, ring site B's, the halo-two sites H and G).
 constexpr size_t kP2PreRowsAt = kP2Smem;
 constexpr size_t kP2PreScalarsAt = kP2PreRowsAt + sizeof(float4) * 2 * kP2Band * kP2Threads;
 constexpr size_t kP2SmemPref = kP2PreScalarsAt + sizeof(float) * 6 * kP2Threads;
@@ -806,17 +806,12 @@ static_assert(2 * (kP2SmemPref + 1024) <= 228 * 1024, "two tile-walking CTAs mus
 static_assert(kP2PreRowsAt % 128 == 0 && 2 * kP2Band * kP2Threads * 4 == 2 * kP2Rows * kP2Cols,
               "the TMA boxes (two of 32 x 128 floats) fill the 128-byte aligned row slots");
 // The tile-walking form runs when every resident CTA gets at least this many
-// tiles of a launch (measured per unit trajectory: 3.44 against 3.56 ms at
-// L = 4096, 17.8 against 18.9 at 8192; a tie at 2048, about 3.4 tiles per
-// CTA; with a tile per CTA only the extra shared-memory round trip is left).
+// tiles of a launch (measured per unit trajectory with the rows by per-thread
+// cp.async: 3.44 against 3.56 ms at L = 4096, 17.8 against 18.9 at 8192; a tie
+// at 2048, about 3.4 tiles per CTA; with a tile per CTA only the extra
+// shared-memory round trip is left).
 constexpr int kP2PrefMinTilesPerCta = 4;
 
-__device__ __forceinline__ void hmc_cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void hmc_cp4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
                    (uint32_t)__cvta_generic_to_shared(dst)),
@@ -837,10 +832,11 @@ __device__ __forceinline__ void hmc_site_step(float c, float s, float Sc, float 
 // PREF = false: one tile per CTA (grid = the tile columns x rows), its loads straight into
 // registers.  PREF = true: a grid of resident CTAs walks the tiles blockIdx.x,
 // + gridDim.x, ... (the tiles of a launch are independent: it reads one angle
-// and one momentum buffer and writes two others), each thread copying the next
-// tile's loads into its own shared-memory slots by cp.async right after the
-// current tile's staging barrier, so they arrive while the two steps run.
-// Both forms run the same arithmetic on the same values: bit-identical.
+// and one momentum buffer and writes two others); right after the current
+// tile's staging barrier thread 0 has TMA copy the next tile's rows and every
+// thread copies its ring and halo sites into its own shared-memory slots by
+// cp.async, so they arrive while the two steps run.  Both forms run the same
+// arithmetic on the same values: bit-identical.
 // The tile-walking form's tensor maps (boxes of 32 rows x 128 columns): the
 // three angle buffers (the launch reads the one the control block names) and
 // the momenta it reads; a kernel parameter.
