@@ -360,6 +360,44 @@ def test_max_side_runs():
     assert np.isfinite(obs["e"]).all() and -2.0 < obs["e"][0] < 0.0
 
 
+def test_library_max_side_algorithms_agree_and_match_oracle_statistics():
+    """The library's largest side, XY_MAX_L = 32768 (2^30 sites, 4 GiB of angles a
+    buffer), where the state is too large to hand to the oracle whole.
+
+    Two sweeps from the seed-7 hot start by the per-sweep fused, the
+    persistent and the two-pass kernels give bit-identical records (exact
+    fixed-point sums and accept counts).  Their energy per site and acceptance
+    after each sweep are averages over 2^30 sites of quantities that, starting
+    from i.i.d. uniform angles, depend only on a neighbourhood of a few sites,
+    so they match the oracle's on sixteen L = 512 lattices with their own hot
+    starts to within the sampling error of those (5 sigma)."""
+    L, beta, seed, n = X.XY_MAX_L, 1.12, 7, 2
+    recs = {}
+    for algo in ("fused", "persistent", "two_pass"):
+        with LT.Lattice(L, beta, seed, algorithm=algo) as lat:
+            assert lat.algorithm == algo
+            lat.sweep(n)
+            recs[algo] = lat.observables()
+    ref = recs["fused"]
+    for algo in ("persistent", "two_pass"):
+        for k in ref:
+            assert np.array_equal(recs[algo][k], ref[k]), (algo, k)
+    g_e = ref["e"]
+    g_acc = ref["accepted"].astype(np.float64) / float(L * L)
+
+    Lo, chains = 512, 16
+    rows = []
+    for c in range(chains):
+        rec, _ = oracle.run(Lo, Lo, beta, n, 100 + c, nthreads=oracle.max_threads())
+        e, _, _ = oracle.observables(rec[:, :5], Lo * Lo, beta)
+        rows.append(np.concatenate([e, rec[:, 5] / (Lo * Lo)]))
+    o = np.array(rows)
+    err = o.std(axis=0, ddof=1) * np.sqrt(1.0 / chains + (Lo / L) ** 2)
+    got = np.concatenate([g_e, g_acc])
+    print("L=32768 e, acceptance:", got, "oracle L=512:", o.mean(axis=0), "+-", err)
+    assert np.all(np.abs(got - o.mean(axis=0)) <= 5.0 * err)
+
+
 # ---------------------------------------------------------------------------
 # Error paths through the ABI
 # ---------------------------------------------------------------------------
