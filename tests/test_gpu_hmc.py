@@ -172,6 +172,48 @@ def test_auto_kernel_equals_one_step_launches(L, n_md):
     assert a[5] == b[5]
 
 
+def test_library_max_side_kernels_agree_and_match_oracle_statistics():
+    """The library's largest side, XY_MAX_L = 32768 (2^30 sites), where the
+    state is too large to hand to the oracle whole.
+
+    One trajectory of six leap-frog steps from the seed-17 hot start by one
+    tiled launch per step and by AUTO (two full steps per launch, resident
+    CTAs walking the tiles): records and start/end sums bit for bit.  The
+    kinetic and bond sums per site at the trajectory's start and end (before
+    the accept test) and dH per site are averages over 2^30 sites of
+    quantities that, from i.i.d. angles and momenta, depend only on a
+    neighbourhood of a few sites, so they match the oracle's trajectories on
+    sixteen L = 256 lattices to within the sampling error of those (5 sigma)."""
+    L, beta, n_md = X.XY_MAX_L, 1.1, 6
+    eps = 0.5 / n_md
+    out = {}
+    for kernel in ("tiled", "auto"):
+        with HMC(L, beta, 17, eps, n_md, kernel=kernel) as h:
+            h.run(1)
+            out[kernel] = (h.observables(), h.last_sums())
+    (oa, sa), (ob, sb) = out["auto"], out["tiled"]
+    for k in ("C", "Ix", "Iy", "Mx", "My", "dH", "accepted"):
+        assert np.array_equal(oa[k], ob[k]), k
+    assert sa == sb
+    N = float(L) * L
+    got = np.array([sa["start"]["K"] / N, sa["end"]["K"] / N, sa["start"]["C"] / N,
+                    sa["end"]["C"] / N, oa["dH"][0] / N])
+
+    Lo, chains = 256, 16
+    rows = []
+    for c in range(chains):
+        th0 = oracle.start(Lo, Lo, 100 + c)
+        _, _, d = oracle.hmc_trajectory(th0, Lo, Lo, beta, eps, n_md, 100 + c, 0)
+        No = float(Lo * Lo)
+        rows.append([d["K0"] / No, d["K1"] / No, -d["V0"] / beta / No, -d["V1"] / beta / No,
+                     d["dH"] / No])
+    o = np.array(rows)
+    err = o.std(axis=0, ddof=1) * np.sqrt(1.0 / chains + (Lo / L) ** 2)
+    print("L=32768 K0, K1, C0, C1, dH per site:", got, "oracle L=256:", o.mean(axis=0), "+-",
+          err)
+    assert np.all(np.abs(got - o.mean(axis=0)) <= 5.0 * err)
+
+
 @pytest.mark.parametrize("L,eps,n_md", [(8, 0.2, 5), (32, 0.1, 10), (128, 0.05, 12)])
 def test_trajectories_match_oracle_step_by_step(L, eps, n_md):
     """Each trajectory from the GPU's FP32 state: dH, decision and final state."""
