@@ -201,3 +201,22 @@ def test_throughput_configuration_replicas_equal_single_lattices():
         assert np.array_equal(states[r], s), r
         for k in ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta"):
             assert np.array_equal(obs[r][k], o[k]), (r, k)
+
+
+def test_library_max_side_replicas_equal_single_lattices():
+    """The library's largest side, XY_MAX_L = 32768 (2^30 sites, four replicas
+    a site: 16 GiB a buffer), two sweeps by AUTO's fused launch: each replica's
+    exact record sums and accept counts equal, bit for bit, those of the
+    single lattice with lattice id r at that side (itself checked across its
+    three sweep kernels and against oracle statistics there)."""
+    L, betas, seed, sweeps = X.XY_MAX_L, [1.0, 1.06, 1.12, 1.18], 7, 2
+    with Quad(L, betas, seed) as q:
+        assert q.algorithm == "fused"
+        q.sweep(sweeps)
+        obs = [q.observables(r) for r in range(4)]
+    for r, beta in enumerate(betas):
+        with Lattice(L, beta, seed, lattice_id=r) as lat:
+            lat.sweep(sweeps)
+            o = lat.observables()
+        for k in ("C", "Ix", "Iy", "Mx", "My", "accepted", "beta"):
+            assert np.array_equal(obs[r][k], o[k]), (r, k)
