@@ -284,7 +284,8 @@ xy_status xy_philox_words(uint64_t seed, uint32_t sweep, uint32_t lattice_id, ui
  * (p, p+1), p = round mod 2, round mod 2 + 2, ..., swap temperatures iff
  * u24(w0) < exp((beta_p - beta_{p+1})(E_p - E_{p+1})), E = -J C of the round's
  * last sweep, Philox domain 2 with counter (ladder * 65536 + p, round,
- * lattice_id0, 2).  Each round (round kernel + exchange kernel) is one
+ * lattice_id0, 2), ladder counted from 0 in increasing ladder id, so at most
+ * 65536 ladders of at most 65537 lattices each (else XY_EINVAL).  Each round (round kernel + exchange kernel) is one
  * captured CUDA graph replayed round after round.
  * ------------------------------------------------------------------------ */
 #define XY_BATCH_MAX_L 256

@@ -506,6 +506,17 @@ xy_status xy_batch_create(const xy_batch_params* p, void* cuda_stream, xy_batch*
           bmsg("ladder %d mixes lattice sides (replica exchange needs equal L)", kv.first);
           return XY_EINVAL;
         }
+    // the exchange's Philox counter is ladder * 65536 + pair position: more
+    // ladders, or longer ones, would reuse another pair's words
+    if (ladders.size() > 65536u) {
+      bmsg("more than 65536 ladders");
+      return XY_EINVAL;
+    }
+    for (auto& kv : ladders)
+      if (kv.second.size() > 65537u) {
+        bmsg("ladder %d has more than 65537 lattices", kv.first);
+        return XY_EINVAL;
+      }
   }
   xy_batch* b = new (std::nothrow) xy_batch();
   if (!b) {

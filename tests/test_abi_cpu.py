@@ -294,6 +294,23 @@ def test_batch_create_refuses_a_bad_work_plan(lib):
         assert lib.xy_batch_create(C.byref(p), None, C.byref(b)) == X.XY_EINVAL, (field, bad)
 
 
+def test_batch_create_refuses_ladders_past_the_exchange_counter(lib):
+    """The exchange's Philox counter is ladder * 65536 + pair position: a ladder
+    of 65538 lattices (65537 pairs), or 65537 ladders, would reuse another
+    pair's words, so either is refused before the device."""
+    n = 65538
+    Ls = (C.c_int32 * n)(*([2] * n))
+    betas = (C.c_double * n)(*[1.0 + 1e-6 * i for i in range(n)])
+    for ids, what in (([0] * n, b"65537 lattices"), (list(range(n)), b"65536 ladders")):
+        ladder = (C.c_int32 * n)(*ids)
+        p = X.xy_batch_params()
+        p.n, p.L, p.beta, p.ladder, p.J, p.delta, p.seed = n, Ls, betas, ladder, 1.0, 3.14159, 1
+        p.sweeps_per_round = 1
+        b = C.c_void_p()
+        assert lib.xy_batch_create(C.byref(p), None, C.byref(b)) == X.XY_EINVAL, what
+        assert what in lib.xy_batch_last_error(None), what
+
+
 def test_release_build_has_no_device_checks(lib):
     """The release library reports itself as such and its debug word is always 0
     (no device access: the checks are compiled out)."""
